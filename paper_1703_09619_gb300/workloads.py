@@ -1,0 +1,179 @@
+"""Seeded synthetic inputs for the element-matrix fill.
+
+This module only draws random inputs (geometry nodes, bulge, material
+parameters, per-axis orders, quadrature sizes).  It contains none of the
+fill's arithmetic, so both the CUDA path and the CPU oracle can be fed from
+it.  It imports nothing else from this package.
+
+Workload recipes (all on the reference element [-1,1]^3, Eq. (2) of
+arXiv:1703.09619; the paper's own tests are 2-D Chebyshev problems, so these
+3-D Legendre batches are synthetic stand-ins with the shape of the method's
+inputs):
+
+* ``c1``  1 element, 1 component, N = 4 on every axis, scalar coupling factor
+  alpha = 1 + 0.5 sin(pi u) cos(pi v) exp(w/2), 12-point rule.
+* ``c2``  4096 curved hexahedra, 3 components, N = 6, metric coupling
+  eps * detJ * J^-1 J^-T with eps = 1 + 0.5 sin(2 pi x.d), d one seeded unit
+  vector for the batch; 16-point rule.
+* ``c3``  512 elements, 1 component, N = 8, per-element scalar factor
+  alpha_e = 1 + 0.5 sin(pi (u + phi_e)) cos(pi (v + psi_e)) exp(w/2),
+  phi_e, psi_e ~ U[0,1); 24-point rule.
+* ``c4``  8192 elements, 3 components, per-component per-axis orders drawn
+  uniformly from {2..8}; eps = 1 + 0.5 sin(2 pi |k| x.d_e), |k| log-uniform
+  in [1, 8]; 16-point rule.
+* ``c5``  32768 elements, 3 components, N = 4, eps = 1 + 0.8 sin(k_e . x),
+  |k_e| log-uniform in [1, 40]; quadrature chosen per element (learned) or
+  48 points (plain).
+
+Geometry of every curved element: the 8 corners of the physical unit cube
+[0,1]^3 (node index iu + 2 iv + 4 iw) each moved by i.i.d. U(-0.15, 0.15)
+per coordinate, plus a bulge a * b_e * cos(pi u/2) cos(pi v/2) cos(pi w/2)
+with a = 0.1 and b_e a seeded unit vector (the bulge vanishes on the faces).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+SEED_BASE = 0x170309619
+
+KIND_SCALAR = 0
+KIND_METRIC_EPS = 1
+
+TYPES_ALL = 0xF
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    n_elem: int
+    n_comp: int
+    orders: np.ndarray  # int32 [E, n_comp, 3]
+    kind: int
+    params: np.ndarray  # float64 [E, 4]
+    nodes: np.ndarray  # float64 [E, 8, 3]
+    bulge: np.ndarray  # float64 [E, 4]
+    npts: np.ndarray  # int32 [E]
+    types_mask: int = TYPES_ALL
+    description: str = ""
+
+    def subset(self, idx) -> "Workload":
+        idx = np.asarray(idx, dtype=np.int64).reshape(-1)
+        return dataclasses.replace(
+            self,
+            name="%s[%d]" % (self.name, idx.size),
+            n_elem=int(idx.size),
+            orders=np.ascontiguousarray(self.orders[idx]),
+            params=np.ascontiguousarray(self.params[idx]),
+            nodes=np.ascontiguousarray(self.nodes[idx]),
+            bulge=np.ascontiguousarray(self.bulge[idx]),
+            npts=np.ascontiguousarray(self.npts[idx]),
+        )
+
+    def with_npts(self, npts) -> "Workload":
+        npts = np.broadcast_to(np.asarray(npts, dtype=np.int32), (self.n_elem,))
+        return dataclasses.replace(self, npts=np.ascontiguousarray(npts))
+
+    def ndof(self) -> np.ndarray:
+        return np.prod(self.orders, axis=2).sum(axis=1).astype(np.int64)
+
+    def entries(self) -> int:
+        nt = bin(self.types_mask & 0xF).count("1")
+        n = self.ndof()
+        return int(nt * (n * n).sum())
+
+
+def unit_vectors(rng, n):
+    v = rng.standard_normal((n, 3))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def cube_nodes(n):
+    """Corners of [0,1]^3, node index iu + 2 iv + 4 iw."""
+    c = np.array([[(i >> 0) & 1, (i >> 1) & 1, (i >> 2) & 1] for i in range(8)], dtype=np.float64)
+    return np.broadcast_to(c, (n, 8, 3)).copy()
+
+
+def curved_geometry(rng, n, jitter=0.15, bulge_amp=0.1):
+    nodes = cube_nodes(n) + rng.uniform(-jitter, jitter, size=(n, 8, 3))
+    b = unit_vectors(rng, n)
+    bulge = np.concatenate([np.full((n, 1), bulge_amp), b], axis=1)
+    return nodes, bulge
+
+
+def _scalar_params(n, A, phi, psi, c):
+    p = np.zeros((n, 4))
+    p[:, 0] = A
+    p[:, 1] = phi
+    p[:, 2] = psi
+    p[:, 3] = c
+    return p
+
+
+def make(name: str, n_elem: int | None = None) -> Workload:
+    """Build one of the named workloads (``c1`` .. ``c5``), optionally with fewer elements.
+
+    Elements are always drawn for the full workload size and then truncated,
+    so element e is the same whatever ``n_elem`` is."""
+    cid = {"c1": 1, "c2": 2, "c3": 3, "c4": 4, "c5": 5}[name]
+    rng = np.random.default_rng(SEED_BASE + cid)
+    if cid == 1:
+        E = 1
+        orders = np.full((E, 1, 3), 4, dtype=np.int32)
+        params = _scalar_params(E, 0.5, 0.0, 0.0, 0.5)
+        nodes, bulge = cube_nodes(E), np.zeros((E, 4))
+        w = Workload(name, E, 1, orders, KIND_SCALAR, params, nodes, bulge, np.full(E, 12, np.int32),
+                     description="1 element, N=4, scalar alpha, G=12")
+    elif cid == 2:
+        E = 4096
+        nodes, bulge = curved_geometry(rng, E)
+        d = unit_vectors(rng, 1)[0]
+        params = np.zeros((E, 4))
+        params[:, 0] = 0.5
+        params[:, 1:] = 2.0 * np.pi * d
+        orders = np.full((E, 3, 3), 6, dtype=np.int32)
+        w = Workload(name, E, 3, orders, KIND_METRIC_EPS, params, nodes, bulge, np.full(E, 16, np.int32),
+                     description="4096 curved hexahedra, 3 comp, N=6, metric*eps, G=16")
+    elif cid == 3:
+        E = 512
+        phi = rng.uniform(0.0, 1.0, E)
+        psi = rng.uniform(0.0, 1.0, E)
+        params = _scalar_params(E, 0.5, phi, psi, 0.5)
+        orders = np.full((E, 1, 3), 8, dtype=np.int32)
+        nodes, bulge = cube_nodes(E), np.zeros((E, 4))
+        w = Workload(name, E, 1, orders, KIND_SCALAR, params, nodes, bulge, np.full(E, 24, np.int32),
+                     description="512 elements, 1 comp, N=8, per-element scalar alpha, G=24")
+    elif cid == 4:
+        E = 8192
+        nodes, bulge = curved_geometry(rng, E)
+        kmag = np.exp(rng.uniform(np.log(1.0), np.log(8.0), E))
+        d = unit_vectors(rng, E)
+        params = np.zeros((E, 4))
+        params[:, 0] = 0.5
+        params[:, 1:] = 2.0 * np.pi * kmag[:, None] * d
+        orders = rng.integers(2, 9, size=(E, 3, 3)).astype(np.int32)
+        w = Workload(name, E, 3, orders, KIND_METRIC_EPS, params, nodes, bulge, np.full(E, 16, np.int32),
+                     description="8192 curved hexahedra, 3 comp, orders U{2..8} per comp/axis, G=16")
+    else:
+        E = 32768
+        nodes, bulge = curved_geometry(rng, E)
+        kmag = np.exp(rng.uniform(np.log(1.0), np.log(40.0), E))
+        d = unit_vectors(rng, E)
+        params = np.zeros((E, 4))
+        params[:, 0] = 0.8
+        params[:, 1:] = kmag[:, None] * d
+        orders = np.full((E, 3, 3), 4, dtype=np.int32)
+        w = Workload(name, E, 3, orders, KIND_METRIC_EPS, params, nodes, bulge, np.full(E, 48, np.int32),
+                     description="32768 curved hexahedra, 3 comp, N=4, eps=1+0.8 sin(k.x), |k| in [1,40]")
+    if n_elem is not None and n_elem < w.n_elem:
+        w = w.subset(np.arange(n_elem))
+        w.name = name
+    return w
+
+
+def judge_elements(n_elem: int, frac: float, seed: int) -> np.ndarray:
+    """Seeded, sorted sample of element indices re-filled by the full-order judge."""
+    k = int(np.ceil(frac * n_elem)) if frac > 0 else 0
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(n_elem, size=min(k, n_elem), replace=False)).astype(np.int32)
