@@ -1,0 +1,183 @@
+/*
+ * p2s.h -- C ABI of the GB300 product-to-sum element-matrix fill.
+ *
+ * Method: E. Khodapanah, "A Product to Sum Approach for Matrix Filling in a
+ * Hierarchical Finite-Element Method", arXiv:1703.09619, Sec. II.
+ *   Eq. (1)  hierarchical basis A^{mnp}_g = P_m(u) Q_n(v) R_p(w) per field component g;
+ *   Eq. (2)  matrix entries as 3-D integrals of basis/derivative products times a
+ *            coupling factor alpha (Jacobian and material);
+ *   Eq. (3)  product-to-sum (linearisation) of every same-variable product;
+ *   Eq. (4)  entries as triple sums of linearisation coefficients times the
+ *            "starting-point" moments  I_klq = iiint P_k(u) P_l(v) P_q(w) alpha.
+ * This library evaluates Eq. (4) on the GPU: alpha at Gauss-Legendre points,
+ * sum-factorised moments, and three sparse mode products that write M.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Basis: Legendre P_m with P_m(1) = 1, m = 0..N-1, on the reference element [-1,1]^3.
+ * Product types t (bit t of a types mask):  0 vv, 1 dv, 2 vd, 3 dd, where the first
+ *   letter is the test function (row) and the second the trial function (column), "d"
+ *   meaning the first derivative on all three axes and "v" the value.
+ * Output layout (one element): the selected types in the order vv, dv, vd, dd, each an
+ *   n x n row-major FP64 matrix, n = sum_g Nu_g Nv_g Nw_g; dof index = (offset of
+ *   component g) + (m Nv_g + n) Nw_g + p, rows = test (g_i, m1, n1, p1), columns = trial
+ *   (g_j, m2, n2, p2).  Elements follow each other without padding; element e starts at
+ *   entry offsets[e] as returned by p2s_output_entries.
+ * Moment layout (one element): the unique component pairs (gi <= gj) in the order
+ *   (0,0),(0,1),(0,2),(1,1),(1,2),(2,2) (three components) or (0,0) (one component),
+ *   each a row-major Ku x Kv x Kw FP64 tensor, K_axis = N_axis(gi) + N_axis(gj) - 1.
+ * Coupling factor kinds (p2s_material.kind), parameters [E][4] FP64:
+ *   P2S_ALPHA_SCALAR (one component): p = (A, phi, psi, c),
+ *       alpha = 1 + A sin(pi (u + phi)) cos(pi (v + psi)) exp(c w)   (reference coordinates);
+ *   P2S_ALPHA_METRIC_EPS (three components): p = (A, kx, ky, kz),
+ *       eps(x) = 1 + A sin(k . x),  alpha_{gi gj} = eps detJ (J^-1 J^-T)_{gi gj},
+ *       J = dx/d(u,v,w) of the trilinear-plus-bulge map below.
+ * Geometry (metric kind): nodes [E][8][3] FP64, node index iu + 2 iv + 4 iw (iu = 0 at
+ *   u = -1); bulge [E][4] FP64 = (a, bx, by, bz):
+ *       x(u,v,w) = sum_n N_n(u,v,w) X_n + a b cos(pi u/2) cos(pi v/2) cos(pi w/2).
+ * Memory: every pointer named "device" is caller-owned device memory, "host" is
+ *   caller-owned host memory.  The library never frees caller memory.  Contexts and plans
+ *   own the library's own tables and scratch.
+ * Streams: `stream` is a cudaStream_t passed as void*; NULL is the legacy default stream.
+ *   Entry points that launch work are asynchronous on that stream; their return value
+ *   reports argument and launch errors only.  Device-side errors (detJ <= 0, a wait that
+ *   gave up) are written to elem_status (if given) and to a per-context flag that
+ *   p2s_sync_status reads.
+ * Errors: every int-returning entry point returns P2S_OK (0) or a negative P2S_ERR_* code.
+ */
+#ifndef P2S_H
+#define P2S_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define P2S_OK 0
+#define P2S_ERR_ARG (-1)      /* bad pointer, size, kind or mask                         */
+#define P2S_ERR_ORDER (-2)    /* an order or quadrature size outside the supported range */
+#define P2S_ERR_JACOBIAN (-3) /* detJ <= 0 at a quadrature point of some element          */
+#define P2S_ERR_OOM (-4)      /* a library allocation failed                              */
+#define P2S_ERR_CUDA (-5)     /* a CUDA runtime call or launch failed                     */
+#define P2S_ERR_TIMEOUT (-6)  /* a bounded device wait gave up                            */
+#define P2S_ERR_BUFFER (-7)   /* a caller buffer is too small                             */
+
+#define P2S_MAX_ORDER 12 /* N per axis and component: 1..12            */
+#define P2S_MAX_NPTS 64  /* Gauss-Legendre points per axis: 1..64       */
+
+#define P2S_ALPHA_SCALAR 0
+#define P2S_ALPHA_METRIC_EPS 1
+
+#define P2S_FP64 0  /* every step in FP64                                          */
+#define P2S_MIXED 1 /* reduced-precision moments and contraction, FP64 output       */
+
+#define P2S_TYPE_VV 1u
+#define P2S_TYPE_DV 2u
+#define P2S_TYPE_VD 4u
+#define P2S_TYPE_DD 8u
+#define P2S_TYPES_ALL 15u
+
+typedef struct p2s_ctx p2s_ctx;
+typedef struct p2s_plan p2s_plan;
+
+typedef struct {
+    int64_t n_elem;      /* E                                                   */
+    const double* nodes; /* device [E][8][3]; may be NULL for P2S_ALPHA_SCALAR  */
+    const double* bulge; /* device [E][4];  may be NULL (no bulge)              */
+} p2s_geometry;
+
+typedef struct {
+    int kind;             /* P2S_ALPHA_SCALAR or P2S_ALPHA_METRIC_EPS */
+    const double* params; /* device [E][4]                           */
+} p2s_material;
+
+typedef struct {
+    int n_comp;            /* 1 (scalar kind) or 3 (metric kind)            */
+    const int32_t* orders; /* host [E][n_comp][3] = (Nu, Nv, Nw), 1..12    */
+} p2s_orders;
+
+typedef struct {
+    int npts_uniform;    /* G for every element, or 0 to use npts[]        */
+    const int32_t* npts; /* host [E], each 1..64 (read when npts_uniform=0) */
+} p2s_quadrature;
+
+typedef struct {
+    int precision;       /* P2S_FP64 or P2S_MIXED        */
+    uint32_t types_mask; /* subset of P2S_TYPES_ALL, != 0 */
+} p2s_fill_opts;
+
+/* Create a context on CUDA device `device` (uploads the Gauss-Legendre and
+ * linearisation tables).  *out receives the context.  Returns P2S_OK,
+ * P2S_ERR_ARG, P2S_ERR_CUDA or P2S_ERR_OOM. */
+int p2s_create(p2s_ctx** out, int device);
+
+/* Release a context and everything it owns (waits for its device work). */
+void p2s_destroy(p2s_ctx* ctx);
+
+/* Output size: total FP64 entries for E elements with the given orders and types
+ * (4 n^2 per element for all types).  If offsets (host, E+1) is non-NULL, it
+ * receives the first entry of every element and the total.  Returns the total,
+ * or a negative P2S_ERR_* code. */
+int64_t p2s_output_entries(int64_t n_elem, const p2s_orders* orders, uint32_t types_mask,
+                           int64_t* offsets);
+
+/* Moment scratch size: total FP64 moment entries for E elements (layout above).
+ * If offsets (host, E+1) is non-NULL it receives the per-element starts. */
+int64_t p2s_moment_entries(int64_t n_elem, const p2s_orders* orders, int64_t* offsets);
+
+/* Build a plan: per-element descriptors, the contraction work list and the launch
+ * shapes for a batch of E elements with these orders, quadrature sizes and options.
+ * A plan is reusable for any geometry/material of the same shape, and owns device
+ * scratch for the moments (p2s_plan_moment_entries doubles).  Orders and npts are
+ * read only during this call.  Errors: P2S_ERR_ARG, P2S_ERR_ORDER, P2S_ERR_OOM,
+ * P2S_ERR_CUDA. */
+int p2s_plan_create(p2s_ctx* ctx, int64_t n_elem, const p2s_orders* orders,
+                    const p2s_quadrature* quad, const p2s_fill_opts* opts, p2s_plan** out);
+void p2s_plan_destroy(p2s_plan* plan);
+int64_t p2s_plan_output_entries(const p2s_plan* plan);
+int64_t p2s_plan_moment_entries(const p2s_plan* plan);
+
+/* Steps a1+a2 (coupling factor at the G^3 points, Eq. (2); moments of Eq. (4)):
+ * writes the moment tensors of every element to `moments` (device, layout above,
+ * p2s_plan_moment_entries doubles).  alpha is never stored.  elem_status (device
+ * [E], optional) receives 0 or P2S_ERR_JACOBIAN per element. */
+int p2s_plan_moments(p2s_plan* plan, const p2s_geometry* geom, const p2s_material* mat,
+                     double* moments, int32_t* elem_status, void* stream);
+
+/* Step a4 (Eq. (3)-(4)): M = C^u x1 C^v x2 C^w x3 I for every element, block and
+ * selected type, from moment tensors in the layout above; writes `out` (device,
+ * p2s_plan_output_entries doubles).  Uses the plan's precision. */
+int p2s_plan_contract(p2s_plan* plan, const double* moments, double* out, void* stream);
+
+/* Steps a1-a4 in one call, moments kept in the plan's scratch. */
+int p2s_plan_fill(p2s_plan* plan, const p2s_geometry* geom, const p2s_material* mat, double* out,
+                  int32_t* elem_status, void* stream);
+
+/* One-shot fill: plan, fill, release.  Same arguments and errors as the plan calls;
+ * `out` must hold p2s_output_entries(...) doubles. */
+int p2s_fill_elements(p2s_ctx* ctx, const p2s_geometry* geom, const p2s_material* mat,
+                      const p2s_orders* orders, const p2s_quadrature* quad,
+                      const p2s_fill_opts* opts, double* out, int32_t* elem_status,
+                      void* stream);
+
+/* Wait for `stream`, then return and clear the context's device error flag:
+ * P2S_OK, P2S_ERR_JACOBIAN, P2S_ERR_TIMEOUT, or P2S_ERR_CUDA if the stream failed. */
+int p2s_sync_status(p2s_ctx* ctx, void* stream);
+
+/* Host copies of the library's tables (for inspection and tests).
+ * p2s_linearisation: C[0..kmax] with P^{(d1)}_{m1} P^{(d2)}_{m2} = sum_k C[k] P_k for
+ *   type t (d1 = t&1, d2 = t>>1), Eq. (3); Adams-Neumann products plus the expansion
+ *   P'_m = sum_{j=m-1,m-3,..} (2j+1) P_j.  Entries beyond the product's degree are 0.
+ * p2s_gauss_legendre: the G-point rule the kernels use (x ascending). */
+int p2s_linearisation(int t, int m1, int m2, int kmax, double* C);
+int p2s_gauss_legendre(int G, double* x, double* w);
+
+/* Static description of an error code. */
+const char* p2s_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* P2S_H */

@@ -1,0 +1,423 @@
+// C ABI of libp2s (declared in include/p2s.h): contexts, plans, launches, error reporting.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "p2s_internal.h"
+
+namespace p2s {
+cudaError_t moments_init_attributes();
+cudaError_t contract_init_attributes();
+cudaError_t init_kernel_attributes() {
+    cudaError_t e = moments_init_attributes();
+    if (e != cudaSuccess) return e;
+    return contract_init_attributes();
+}
+}  // namespace p2s
+
+using namespace p2s;
+
+struct p2s_ctx {
+    int device = 0;
+    int sm_count = 0;
+    size_t smem_optin = 0;
+    double* d_gl_x = nullptr;
+    double* d_gl_w = nullptr;
+    int32_t* d_lin_idx = nullptr;
+    double* d_lin_coef = nullptr;
+    int* d_err = nullptr;
+};
+
+struct p2s_plan {
+    p2s_ctx* ctx = nullptr;
+    int64_t n_elem = 0;
+    int n_comp = 0;
+    uint32_t types_mask = 0;
+    int precision = 0;
+    int64_t out_entries = 0;
+    int64_t mom_entries = 0;
+    int64_t n_units = 0;
+    ElemDesc* d_desc = nullptr;
+    ContractUnit* d_units = nullptr;
+    unsigned long long* d_counter = nullptr;
+    double* d_mom = nullptr;  // scratch for p2s_plan_fill
+    // launch shapes
+    int n_pairs = 1, kb = 1, gmax = 1, nmax = 1, kmax = 1;
+    int iacc_cap = 0;
+    size_t mom_smem = 0;
+    int mom_grid = 1;
+    int con_warps = 8;
+    size_t con_smem = 0;
+    int con_grid = 1;
+};
+
+namespace {
+
+int set_device(int dev) { return cudaSetDevice(dev) == cudaSuccess ? P2S_OK : P2S_ERR_CUDA; }
+
+int check_orders(int64_t E, const p2s_orders* o) {
+    if (E < 0 || !o || (o->n_comp != 1 && o->n_comp != 3) || (E > 0 && !o->orders)) return P2S_ERR_ARG;
+    for (int64_t i = 0; i < E * 3 * o->n_comp; ++i)
+        if (o->orders[i] < 1 || o->orders[i] > kMaxOrder) return P2S_ERR_ORDER;
+    return P2S_OK;
+}
+
+int64_t elem_ndof(const int32_t* ord, int nc) {
+    int64_t n = 0;
+    for (int g = 0; g < nc; ++g) n += (int64_t)ord[3 * g] * ord[3 * g + 1] * ord[3 * g + 2];
+    return n;
+}
+
+int ntypes(uint32_t m) { return __builtin_popcount(m & 0xFu); }
+
+void pair_of(int s, int nc, int& gi, int& gj) {
+    static const int tgi[6] = {0, 0, 0, 1, 1, 2}, tgj[6] = {0, 1, 2, 1, 2, 2};
+    if (nc == 1) { gi = gj = 0; return; }
+    gi = tgi[s];
+    gj = tgj[s];
+}
+
+int64_t elem_moments(const int32_t* ord, int nc) {
+    int np = nc == 1 ? 1 : 6;
+    int64_t m = 0;
+    for (int s = 0; s < np; ++s) {
+        int gi, gj;
+        pair_of(s, nc, gi, gj);
+        int64_t v = 1;
+        for (int ax = 0; ax < 3; ++ax) v *= ord[3 * gi + ax] + ord[3 * gj + ax] - 1;
+        m += v;
+    }
+    return m;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* p2s_error_string(int code) {
+    switch (code) {
+    case P2S_OK: return "ok";
+    case P2S_ERR_ARG: return "invalid argument";
+    case P2S_ERR_ORDER: return "order or quadrature size out of range";
+    case P2S_ERR_JACOBIAN: return "detJ <= 0 at a quadrature point";
+    case P2S_ERR_OOM: return "out of memory";
+    case P2S_ERR_CUDA: return "CUDA error";
+    case P2S_ERR_TIMEOUT: return "device wait timed out";
+    case P2S_ERR_BUFFER: return "buffer too small";
+    }
+    return "unknown error";
+}
+
+int p2s_gauss_legendre(int G, double* x, double* w) {
+    if (G < 1 || G > kMaxG || !x || !w) return P2S_ERR_ARG;
+    const HostTables& T = host_tables();
+    std::memcpy(x, T.gl_x[G], sizeof(double) * G);
+    std::memcpy(w, T.gl_w[G], sizeof(double) * G);
+    return P2S_OK;
+}
+
+int p2s_linearisation(int t, int m1, int m2, int kmax, double* C) {
+    if (t < 0 || t > 3 || m1 < 0 || m2 < 0 || m1 >= kMaxOrder || m2 >= kMaxOrder || kmax < 0 || !C)
+        return P2S_ERR_ARG;
+    const HostTables& T = host_tables();
+    for (int k = 0; k <= kmax; ++k) C[k] = 0.0;
+    int32_t li = T.lin_idx[lin_slot(t, m1, m2)];
+    for (int r = 0; r < lin_cnt(li); ++r) {
+        int k = lin_kmin(li) + 2 * r;
+        if (k <= kmax) C[k] = T.lin_coef[lin_off(li) + r];
+    }
+    return P2S_OK;
+}
+
+int p2s_create(p2s_ctx** out, int device) {
+    if (!out) return P2S_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return P2S_ERR_ARG;
+    if (set_device(device)) return P2S_ERR_CUDA;
+    p2s_ctx* c = new (std::nothrow) p2s_ctx();
+    if (!c) return P2S_ERR_OOM;
+    c->device = device;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { delete c; return P2S_ERR_CUDA; }
+    c->sm_count = prop.multiProcessorCount;
+    c->smem_optin = prop.sharedMemPerBlockOptin;
+    const HostTables& T = host_tables();
+    size_t glb = sizeof(double) * (kMaxG + 1) * kMaxG;
+    bool ok = cudaMalloc(&c->d_gl_x, glb) == cudaSuccess && cudaMalloc(&c->d_gl_w, glb) == cudaSuccess &&
+              cudaMalloc(&c->d_lin_idx, sizeof(T.lin_idx)) == cudaSuccess &&
+              cudaMalloc(&c->d_lin_coef, sizeof(double) * std::max(1, T.n_coef)) == cudaSuccess &&
+              cudaMalloc(&c->d_err, sizeof(int)) == cudaSuccess;
+    if (ok)
+        ok = cudaMemcpy(c->d_gl_x, T.gl_x, glb, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(c->d_gl_w, T.gl_w, glb, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(c->d_lin_idx, T.lin_idx, sizeof(T.lin_idx), cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(c->d_lin_coef, T.lin_coef, sizeof(double) * T.n_coef, cudaMemcpyHostToDevice) ==
+                 cudaSuccess &&
+             cudaMemset(c->d_err, 0, sizeof(int)) == cudaSuccess && init_kernel_attributes() == cudaSuccess;
+    if (!ok) {
+        p2s_destroy(c);
+        return P2S_ERR_CUDA;
+    }
+    *out = c;
+    return P2S_OK;
+}
+
+void p2s_destroy(p2s_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    cudaFree(c->d_gl_x);
+    cudaFree(c->d_gl_w);
+    cudaFree(c->d_lin_idx);
+    cudaFree(c->d_lin_coef);
+    cudaFree(c->d_err);
+    delete c;
+}
+
+int64_t p2s_output_entries(int64_t n_elem, const p2s_orders* orders, uint32_t types_mask, int64_t* offsets) {
+    int rc = check_orders(n_elem, orders);
+    if (rc) return rc;
+    if ((types_mask & 0xFu) == 0 || (types_mask & ~0xFu)) return P2S_ERR_ARG;
+    int nt = ntypes(types_mask);
+    int64_t off = 0;
+    for (int64_t e = 0; e < n_elem; ++e) {
+        if (offsets) offsets[e] = off;
+        int64_t n = elem_ndof(orders->orders + 3 * orders->n_comp * e, orders->n_comp);
+        off += nt * n * n;
+    }
+    if (offsets) offsets[n_elem] = off;
+    return off;
+}
+
+int64_t p2s_moment_entries(int64_t n_elem, const p2s_orders* orders, int64_t* offsets) {
+    int rc = check_orders(n_elem, orders);
+    if (rc) return rc;
+    int64_t off = 0;
+    for (int64_t e = 0; e < n_elem; ++e) {
+        if (offsets) offsets[e] = off;
+        off += elem_moments(orders->orders + 3 * orders->n_comp * e, orders->n_comp);
+    }
+    if (offsets) offsets[n_elem] = off;
+    return off;
+}
+
+void p2s_plan_destroy(p2s_plan* p) {
+    if (!p) return;
+    if (p->ctx) cudaSetDevice(p->ctx->device);
+    cudaFree(p->d_desc);
+    cudaFree(p->d_units);
+    cudaFree(p->d_counter);
+    cudaFree(p->d_mom);
+    delete p;
+}
+
+int p2s_plan_create(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, const p2s_quadrature* quad,
+                    const p2s_fill_opts* opts, p2s_plan** out) {
+    if (!ctx || !out || !quad || !opts) return P2S_ERR_ARG;
+    *out = nullptr;
+    int rc = check_orders(E, orders);
+    if (rc) return rc;
+    if ((opts->types_mask & 0xFu) == 0 || (opts->types_mask & ~0xFu)) return P2S_ERR_ARG;
+    if (opts->precision != P2S_FP64 && opts->precision != P2S_MIXED) return P2S_ERR_ARG;
+    if (quad->npts_uniform < 0 || quad->npts_uniform > kMaxG) return P2S_ERR_ORDER;
+    if (quad->npts_uniform == 0 && E > 0 && !quad->npts) return P2S_ERR_ARG;
+    if (set_device(ctx->device)) return P2S_ERR_CUDA;
+
+    const int nc = orders->n_comp;
+    std::vector<ElemDesc> desc((size_t)std::max<int64_t>(E, 1));
+    std::vector<ContractUnit> units;
+    p2s_plan* p = new (std::nothrow) p2s_plan();
+    if (!p) return P2S_ERR_OOM;
+    p->ctx = ctx;
+    p->n_elem = E;
+    p->n_comp = nc;
+    p->types_mask = opts->types_mask;
+    p->precision = opts->precision;
+    p->n_pairs = nc == 1 ? 1 : 6;
+    const int nt = ntypes(opts->types_mask);
+    int64_t out_off = 0, mom_off = 0;
+    int max_pair = 1, max_elem_mom = 1;
+    for (int64_t e = 0; e < E; ++e) {
+        const int32_t* ord = orders->orders + 3 * nc * e;
+        ElemDesc& d = desc[e];
+        std::memset(&d, 0, sizeof(d));
+        int G = quad->npts_uniform ? quad->npts_uniform : quad->npts[e];
+        if (G < 1 || G > kMaxG) { delete p; return P2S_ERR_ORDER; }
+        d.G = (int16_t)G;
+        d.n_comp = (int8_t)nc;
+        d.n_types = (int8_t)nt;
+        int dof = 0;
+        for (int g = 0; g < nc; ++g) {
+            d.dof_off[g] = dof;
+            for (int ax = 0; ax < 3; ++ax) d.ord[g][ax] = (int8_t)ord[3 * g + ax];
+            dof += ord[3 * g] * ord[3 * g + 1] * ord[3 * g + 2];
+        }
+        d.n = dof;
+        for (int ax = 0; ax < 3; ++ax) {
+            int mx = 0;
+            for (int g = 0; g < nc; ++g) mx = std::max(mx, (int)ord[3 * g + ax]);
+            d.kax[ax] = (int8_t)(2 * mx - 1);
+            p->kb = std::max(p->kb, 2 * mx - 1);
+            p->nmax = std::max(p->nmax, mx);
+        }
+        int po = 0;
+        for (int s = 0; s < p->n_pairs; ++s) {
+            int gi, gj;
+            pair_of(s, nc, gi, gj);
+            d.pair_off[s] = po;
+            int v = 1;
+            for (int ax = 0; ax < 3; ++ax) v *= ord[3 * gi + ax] + ord[3 * gj + ax] - 1;
+            po += v;
+        }
+        d.out_off = out_off;
+        d.mom_off = mom_off;
+        out_off += (int64_t)nt * dof * dof;
+        mom_off += po;
+        max_pair = std::max(max_pair, d.kax[0] * d.kax[1] * d.kax[2]);
+        max_elem_mom = std::max(max_elem_mom, p->n_pairs * d.kax[0] * d.kax[1] * d.kax[2]);
+        p->gmax = std::max(p->gmax, G);
+        for (int gi = 0; gi < nc; ++gi)
+            for (int gj = 0; gj < nc; ++gj)
+                for (int t = 0; t < 4; ++t) {
+                    if (!(opts->types_mask & (1u << t))) continue;
+                    for (int m1 = 0; m1 < ord[3 * gi]; ++m1)
+                        units.push_back(ContractUnit{(int32_t)e, (int8_t)gi, (int8_t)gj, (int8_t)t, (int8_t)m1});
+                }
+    }
+    p->kmax = p->kb;
+    p->out_entries = out_off;
+    p->mom_entries = mom_off;
+    p->n_units = (int64_t)units.size();
+
+    // moments launch shape: the accumulator takes what shared memory leaves, at least one pair
+    size_t base = moments_smem_bytes(p->n_pairs, p->kb, p->gmax, 0);
+    size_t limit = std::min<size_t>(ctx->smem_optin, 227 * 1024);
+    if (base + sizeof(double) * max_pair > limit) { delete p; return P2S_ERR_ORDER; }
+    p->iacc_cap = (int)std::min<size_t>((limit - base) / sizeof(double), (size_t)max_elem_mom);
+    // prefer two CTAs per SM when everything fits in half the shared memory
+    size_t half = limit / 2 - 1024;
+    if (base + sizeof(double) * max_elem_mom <= half) p->iacc_cap = max_elem_mom;
+    p->mom_smem = moments_smem_bytes(p->n_pairs, p->kb, p->gmax, p->iacc_cap);
+    int per_sm = moments_blocks_per_sm(p->mom_smem);
+    if (per_sm < 1) { delete p; return P2S_ERR_ORDER; }
+    p->mom_grid = (int)std::max<int64_t>(1, std::min<int64_t>(E, (int64_t)ctx->sm_count * per_sm));
+
+    // contraction launch shape
+    size_t wbytes = sizeof(double) * contract_warp_doubles(p->nmax, p->kmax);
+    int w = contract_max_warps_per_cta();
+    while (w > 1 && wbytes * w > limit) --w;
+    if (wbytes * w > limit) { delete p; return P2S_ERR_ORDER; }
+    p->con_warps = w;
+    p->con_smem = wbytes * w;
+    int con_per_sm = contract_blocks_per_sm(w, p->con_smem);
+    if (con_per_sm < 1) { delete p; return P2S_ERR_ORDER; }
+    p->con_grid = ctx->sm_count * con_per_sm;
+
+    bool ok = cudaMalloc(&p->d_desc, sizeof(ElemDesc) * desc.size()) == cudaSuccess &&
+              cudaMalloc(&p->d_units, sizeof(ContractUnit) * std::max<size_t>(1, units.size())) == cudaSuccess &&
+              cudaMalloc(&p->d_counter, sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMalloc(&p->d_mom, sizeof(double) * std::max<int64_t>(1, p->mom_entries)) == cudaSuccess;
+    if (!ok) { p2s_plan_destroy(p); return P2S_ERR_OOM; }
+    if (cudaMemcpy(p->d_desc, desc.data(), sizeof(ElemDesc) * desc.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        (units.size() && cudaMemcpy(p->d_units, units.data(), sizeof(ContractUnit) * units.size(),
+                                    cudaMemcpyHostToDevice) != cudaSuccess)) {
+        p2s_plan_destroy(p);
+        return P2S_ERR_CUDA;
+    }
+    *out = p;
+    return P2S_OK;
+}
+
+int64_t p2s_plan_output_entries(const p2s_plan* p) { return p ? p->out_entries : P2S_ERR_ARG; }
+int64_t p2s_plan_moment_entries(const p2s_plan* p) { return p ? p->mom_entries : P2S_ERR_ARG; }
+
+int p2s_plan_moments(p2s_plan* p, const p2s_geometry* geom, const p2s_material* mat, double* moments,
+                     int32_t* elem_status, void* stream) {
+    if (!p || !geom || !mat || !moments) return P2S_ERR_ARG;
+    if (geom->n_elem != p->n_elem || !mat->params) return P2S_ERR_ARG;
+    if (mat->kind == P2S_ALPHA_SCALAR) {
+        if (p->n_comp != 1) return P2S_ERR_ARG;
+    } else if (mat->kind == P2S_ALPHA_METRIC_EPS) {
+        if (p->n_comp != 3 || !geom->nodes) return P2S_ERR_ARG;
+    } else {
+        return P2S_ERR_ARG;
+    }
+    if (p->n_elem == 0) return P2S_OK;
+    if (set_device(p->ctx->device)) return P2S_ERR_CUDA;
+    MomentLaunch L;
+    L.desc = p->d_desc;
+    L.n_elem = p->n_elem;
+    L.kind = mat->kind;
+    L.params = mat->params;
+    L.nodes = geom->nodes;
+    L.bulge = geom->bulge;
+    L.gl_x = p->ctx->d_gl_x;
+    L.gl_w = p->ctx->d_gl_w;
+    L.mom = moments;
+    L.elem_status = elem_status;
+    L.err_flag = p->ctx->d_err;
+    L.n_pairs = p->n_pairs;
+    L.kb = p->kb;
+    L.gmax = p->gmax;
+    L.iacc_cap = p->iacc_cap;
+    cudaError_t e = launch_moments_fp64(L, p->mom_grid, p->mom_smem, (cudaStream_t)stream);
+    return e == cudaSuccess ? P2S_OK : P2S_ERR_CUDA;
+}
+
+int p2s_plan_contract(p2s_plan* p, const double* moments, double* out, void* stream) {
+    if (!p || !moments || !out) return P2S_ERR_ARG;
+    if (p->n_units == 0) return P2S_OK;
+    if (set_device(p->ctx->device)) return P2S_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned long long), s) != cudaSuccess) return P2S_ERR_CUDA;
+    ContractLaunch L;
+    L.desc = p->d_desc;
+    L.units = p->d_units;
+    L.n_units = p->n_units;
+    L.mom = moments;
+    L.lin_idx = p->ctx->d_lin_idx;
+    L.lin_coef = p->ctx->d_lin_coef;
+    L.out = out;
+    L.counter = p->d_counter;
+    L.types_mask = p->types_mask;
+    L.nmax = p->nmax;
+    L.kmax = p->kmax;
+    cudaError_t e = launch_contract_fp64(L, p->con_grid, p->con_warps, p->con_smem, s);
+    return e == cudaSuccess ? P2S_OK : P2S_ERR_CUDA;
+}
+
+int p2s_plan_fill(p2s_plan* p, const p2s_geometry* geom, const p2s_material* mat, double* out,
+                  int32_t* elem_status, void* stream) {
+    if (!p || !out) return P2S_ERR_ARG;
+    int rc = p2s_plan_moments(p, geom, mat, p->d_mom, elem_status, stream);
+    if (rc) return rc;
+    return p2s_plan_contract(p, p->d_mom, out, stream);
+}
+
+int p2s_fill_elements(p2s_ctx* ctx, const p2s_geometry* geom, const p2s_material* mat, const p2s_orders* orders,
+                      const p2s_quadrature* quad, const p2s_fill_opts* opts, double* out, int32_t* elem_status,
+                      void* stream) {
+    if (!geom) return P2S_ERR_ARG;
+    p2s_plan* p = nullptr;
+    int rc = p2s_plan_create(ctx, geom->n_elem, orders, quad, opts, &p);
+    if (rc) return rc;
+    rc = p2s_plan_fill(p, geom, mat, out, elem_status, stream);
+    if (rc == P2S_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) rc = P2S_ERR_CUDA;
+    p2s_plan_destroy(p);
+    return rc;
+}
+
+int p2s_sync_status(p2s_ctx* ctx, void* stream) {
+    if (!ctx) return P2S_ERR_ARG;
+    if (set_device(ctx->device)) return P2S_ERR_CUDA;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return P2S_ERR_CUDA;
+    int h = 0;
+    if (cudaMemcpy(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return P2S_ERR_CUDA;
+    if (h != 0 && cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess) return P2S_ERR_CUDA;
+    return h;
+}
+
+}  // extern "C"

@@ -1,0 +1,258 @@
+// Steps a1 + a2: coupling factor at the Gauss-Legendre points and the moment tensors
+//   I_s[k,l,q] = sum_{a,b,c} w_a w_b w_c P_k(u_a) P_l(v_b) P_q(w_c) alpha_s(u_a,v_b,w_c)
+// of Eq. (4) of arXiv:1703.09619 ("starting-point" integrals; Eq. (19) is the 2-D case),
+// sum-factorised as three mode products with B[k][a] = w_a P_k(x_a):
+//   T1[k][b]   = sum_a B[k][a] alpha[a,b,c]        (per w-plane c, in chunks of b)
+//   T2[k][l]  += sum_b B[l][b] T1[k][b]
+//   I[k][l][q] += B[q][c] T2[k][l]
+// alpha (Eq. (2) coupling factor) is evaluated in shared memory chunk by chunk and never
+// reaches global memory.  One CTA owns one element at a time (persistent loop).
+// Plain path: every operation in FP64.
+#include <cmath>
+
+#include "p2s_internal.h"
+
+namespace p2s {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kChunk = 256;  // alpha points per chunk
+constexpr int kNB = 16;      // max b-rows per chunk: min(G, 256/G) <= 16
+constexpr int kGeo = 48;
+
+__device__ __forceinline__ void pair_comps(int s, int n_comp, int& gi, int& gj) {
+    if (n_comp == 1) { gi = gj = 0; return; }
+    const int tgi[6] = {0, 0, 0, 1, 1, 2}, tgj[6] = {0, 1, 2, 1, 2, 2};
+    gi = tgi[s];
+    gj = tgj[s];
+}
+
+struct Smem {
+    double *B, *xq, *t0, *t1, *t2, *alpha, *T1, *T2, *Iacc, *geo;
+};
+
+__device__ __forceinline__ Smem carve(double* sm, int n_pairs, int kb, int gmax, int iacc_cap) {
+    Smem S;
+    S.B = sm;
+    S.xq = S.B + kb * gmax;
+    S.t0 = S.xq + gmax;
+    S.t1 = S.t0 + gmax;
+    S.t2 = S.t1 + gmax;
+    S.alpha = S.t2 + gmax;
+    S.T1 = S.alpha + n_pairs * kChunk;
+    S.T2 = S.T1 + n_pairs * kb * kNB;
+    S.Iacc = S.T2 + n_pairs * kb * kb;
+    S.geo = S.Iacc + iacc_cap;
+    return S;
+}
+
+// Coupling factors of the metric kind at one point; writes K[s] for the 6 unique pairs.
+// J = dx/d(u,v,w) of the trilinear-plus-bulge map; cofactors C; det = J row 0 . C row 0;
+// K = eps detJ J^-1 J^-T = (eps / det) C^T C  (since J^-1 = C^T / det).
+__device__ __forceinline__ bool metric_alpha(const double* geo, double u, double v, double w, double cu,
+                                             double su, double cv, double sv, double cw, double sw,
+                                             double* K) {
+    const double hp = -1.5707963267948966;  // -pi/2
+    double uv = u * v, uw = u * w, vw = v * w, uvw = uv * w;
+    double beta = cu * cv * cw;
+    double dbu = hp * su * cv * cw, dbv = hp * cu * sv * cw, dbw = hp * cu * cv * sw;
+    double J[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const double* c = geo + 8 * i;
+        double g = geo[24 + i];
+        J[i][0] = fma(g, dbu, fma(c[7], vw, fma(c[5], w, fma(c[4], v, c[1]))));
+        J[i][1] = fma(g, dbv, fma(c[7], uw, fma(c[6], w, fma(c[4], u, c[2]))));
+        J[i][2] = fma(g, dbw, fma(c[7], uv, fma(c[6], v, fma(c[5], u, c[3]))));
+    }
+    const double* th = geo + 31;
+    double theta = fma(geo[39], beta,
+                       fma(th[7], uvw, fma(th[6], vw, fma(th[5], uw, fma(th[4], uv,
+                           fma(th[3], w, fma(th[2], v, fma(th[1], u, th[0]))))))));
+    double eps = fma(geo[27], sin(theta), 1.0);
+    double C[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+            C[i][j] = fma(J[i1][j1], J[i2][j2], -J[i1][j2] * J[i2][j1]);
+        }
+    double det = fma(J[0][0], C[0][0], fma(J[0][1], C[0][1], J[0][2] * C[0][2]));
+    double sc = eps / det;
+    const int pi_[6] = {0, 0, 0, 1, 1, 2}, pj_[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+        int i = pi_[s], j = pj_[s];
+        K[s] = sc * fma(C[0][i], C[0][j], fma(C[1][i], C[1][j], C[2][i] * C[2][j]));
+    }
+    return det > 0.0;
+}
+
+__global__ void __launch_bounds__(kThreads) k_moments_fp64(MomentLaunch L) {
+    extern __shared__ double sm[];
+    const int tid = threadIdx.x;
+    Smem S = carve(sm, L.n_pairs, L.kb, L.gmax, L.iacc_cap);
+    __shared__ int bad_jac;
+    const int gstride = L.gmax;
+
+    for (int64_t e = blockIdx.x; e < L.n_elem; e += gridDim.x) {
+        const ElemDesc& d = L.desc[e];
+        const int G = d.G, nc = d.n_comp, np = (nc == 1) ? 1 : 6;
+        const int Ku = d.kax[0], Kv = d.kax[1], Kw = d.kax[2];
+        const int Kb = max(Ku, max(Kv, Kw));
+        if (tid == 0) bad_jac = 0;
+        // 1-D tables: nodes, B[k][a] = w_a P_k(x_a), per-axis factors
+        if (tid < G) {
+            double x = L.gl_x[G * kMaxG + tid], w = L.gl_w[G * kMaxG + tid];
+            S.xq[tid] = x;
+            double p0 = 1.0, p1 = x;
+            S.B[0 * gstride + tid] = w;
+            if (Kb > 1) S.B[1 * gstride + tid] = w * x;
+            for (int k = 1; k + 1 < Kb; ++k) {
+                double p2 = ((2 * k + 1) * x * p1 - k * p0) / (k + 1);
+                S.B[(k + 1) * gstride + tid] = w * p2;
+                p0 = p1;
+                p1 = p2;
+            }
+            const double* p = L.params + 4 * e;
+            if (L.kind == P2S_ALPHA_SCALAR) {
+                const double pi = 3.141592653589793;
+                S.t0[tid] = p[0] * sin(pi * (x + p[1]));
+                S.t1[tid] = cos(pi * (x + p[2]));
+                S.t2[tid] = exp(p[3] * x);
+            } else {
+                double sx, cx;
+                sincos(1.5707963267948966 * x, &sx, &cx);
+                S.t0[tid] = cx;
+                S.t1[tid] = sx;
+            }
+        }
+        if (L.kind == P2S_ALPHA_METRIC_EPS && tid < 3) {
+            // trilinear coefficients of coordinate i: x_i = sum_j c_ij * (1,u,v,w,uv,uw,vw,uvw)_j
+            const double* X = L.nodes + 24 * e;
+            double c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int nd = 0; nd < 8; ++nd) {
+                double su = (nd & 1) ? 1.0 : -1.0, sv = (nd & 2) ? 1.0 : -1.0, sw = (nd & 4) ? 1.0 : -1.0;
+                double xv = 0.125 * X[3 * nd + tid];
+                c[0] += xv; c[1] += su * xv; c[2] += sv * xv; c[3] += sw * xv;
+                c[4] += su * sv * xv; c[5] += su * sw * xv; c[6] += sv * sw * xv; c[7] += su * sv * sw * xv;
+            }
+            for (int j = 0; j < 8; ++j) S.geo[8 * tid + j] = c[j];
+            const double* bg = L.bulge ? L.bulge + 4 * e : nullptr;
+            S.geo[24 + tid] = bg ? bg[0] * bg[1 + tid] : 0.0;
+        }
+        __syncthreads();
+        if (L.kind == P2S_ALPHA_METRIC_EPS && tid < 8) {
+            const double* p = L.params + 4 * e;
+            // phase theta = k . x as trilinear coefficients plus k . (a b) for the bulge
+            S.geo[31 + tid] = p[1] * S.geo[tid] + p[2] * S.geo[8 + tid] + p[3] * S.geo[16 + tid];
+            if (tid == 0) {
+                S.geo[27] = p[0];
+                S.geo[39] = p[1] * S.geo[24] + p[2] * S.geo[25] + p[3] * S.geo[26];
+            }
+        }
+        __syncthreads();
+
+        const int per_pair = Ku * Kv * Kw;
+        const int ppg = max(1, min(np, L.iacc_cap / per_pair));
+        const int nb = max(1, min(G, kChunk / G));
+        for (int s0 = 0; s0 < np; s0 += ppg) {
+            const int ns = min(np, s0 + ppg) - s0;
+            for (int i = tid; i < ns * per_pair; i += kThreads) S.Iacc[i] = 0.0;
+            for (int c = 0; c < G; ++c) {
+                for (int i = tid; i < ns * Ku * Kv; i += kThreads) S.T2[i] = 0.0;
+                for (int b0 = 0; b0 < G; b0 += nb) {
+                    const int nbc = min(nb, G - b0);
+                    const int npts = nbc * G;
+                    // phase A: alpha at (a, b0 + bb, c)
+                    if (tid < npts) {
+                        const int bb = tid / G, a = tid - bb * G, b = b0 + bb;
+                        if (L.kind == P2S_ALPHA_SCALAR) {
+                            S.alpha[tid] = fma(S.t0[a] * S.t1[b], S.t2[c], 1.0);
+                        } else {
+                            double K[6];
+                            bool ok = metric_alpha(S.geo, S.xq[a], S.xq[b], S.xq[c], S.t0[a], S.t1[a], S.t0[b],
+                                                   S.t1[b], S.t0[c], S.t1[c], K);
+                            if (!ok) bad_jac = 1;
+                            for (int s = 0; s < ns; ++s) S.alpha[s * kChunk + tid] = K[s0 + s];
+                        }
+                    }
+                    __syncthreads();
+                    // phase B: T1[s][k][bb] = sum_a B[k][a] alpha[s][bb*G + a]
+                    for (int i = tid; i < ns * Ku * nbc; i += kThreads) {
+                        const int s = i / (Ku * nbc), r = i - s * Ku * nbc, k = r / nbc, bb = r - k * nbc;
+                        const double* al = S.alpha + s * kChunk + bb * G;
+                        const double* Bk = S.B + k * gstride;
+                        double acc = 0.0;
+                        for (int a = 0; a < G; ++a) acc = fma(Bk[a], al[a], acc);
+                        S.T1[(s * Kb + k) * kNB + bb] = acc;
+                    }
+                    __syncthreads();
+                    // phase C: T2[s][k][l] += sum_bb B[l][b0+bb] T1[s][k][bb]
+                    for (int i = tid; i < ns * Ku * Kv; i += kThreads) {
+                        const int s = i / (Ku * Kv), r = i - s * Ku * Kv, k = r / Kv, l = r - k * Kv;
+                        const double* t1 = S.T1 + (s * Kb + k) * kNB;
+                        const double* Bl = S.B + l * gstride + b0;
+                        double acc = S.T2[i];
+                        for (int bb = 0; bb < nbc; ++bb) acc = fma(Bl[bb], t1[bb], acc);
+                        S.T2[i] = acc;
+                    }
+                    __syncthreads();
+                }
+                // phase D: I[s][k][l][q] += B[q][c] T2[s][k][l]
+                for (int i = tid; i < ns * per_pair; i += kThreads) {
+                    const int skl = i / Kw, q = i - skl * Kw;
+                    S.Iacc[i] = fma(S.B[q * gstride + c], S.T2[skl], S.Iacc[i]);
+                }
+                __syncthreads();
+            }
+            // store each pair's own sub-tensor (K_axis = N_i + N_j - 1 <= element-wide K)
+            for (int s = 0; s < ns; ++s) {
+                int gi, gj;
+                pair_comps(s0 + s, nc, gi, gj);
+                const int ku = d.ord[gi][0] + d.ord[gj][0] - 1, kv = d.ord[gi][1] + d.ord[gj][1] - 1,
+                          kw = d.ord[gi][2] + d.ord[gj][2] - 1;
+                double* dst = L.mom + d.mom_off + d.pair_off[s0 + s];
+                const double* src = S.Iacc + s * per_pair;
+                for (int i = tid; i < ku * kv * kw; i += kThreads) {
+                    const int k = i / (kv * kw), r = i - k * kv * kw, l = r / kw, q = r - l * kw;
+                    dst[i] = src[(k * Kv + l) * Kw + q];
+                }
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            if (L.elem_status) L.elem_status[e] = bad_jac ? P2S_ERR_JACOBIAN : P2S_OK;
+            if (bad_jac && L.err_flag) atomicCAS(L.err_flag, 0, P2S_ERR_JACOBIAN);
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+size_t moments_smem_bytes(int n_pairs, int kb, int gmax, int iacc_cap) {
+    size_t d = (size_t)kb * gmax + 4 * (size_t)gmax + (size_t)n_pairs * kChunk + (size_t)n_pairs * kb * kNB +
+               (size_t)n_pairs * kb * kb + (size_t)iacc_cap + kGeo;
+    return d * sizeof(double);
+}
+
+cudaError_t launch_moments_fp64(const MomentLaunch& L, int grid, size_t smem, cudaStream_t s) {
+    k_moments_fp64<<<grid, kThreads, smem, s>>>(L);
+    return cudaGetLastError();
+}
+
+int moments_threads() { return kThreads; }
+
+int moments_blocks_per_sm(size_t smem) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_moments_fp64, kThreads, smem) != cudaSuccess) return 0;
+    return n;
+}
+
+cudaError_t moments_init_attributes() {
+    return cudaFuncSetAttribute(k_moments_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
+}  // namespace p2s

@@ -1,0 +1,275 @@
+"""Thin Python binding of libp2s (the C ABI in include/p2s.h).
+
+Argument marshalling only: torch tensors become raw device pointers, the current
+torch stream becomes the cudaStream_t, host arrays become host pointers.  Every
+step of the fill runs in the library's CUDA kernels.  Importing this module does
+not need a GPU; using it does, and it raises if libp2s.so has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libp2s.so")
+
+OK, ERR_ARG, ERR_ORDER, ERR_JACOBIAN, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_BUFFER = 0, -1, -2, -3, -4, -5, -6, -7
+MAX_ORDER, MAX_NPTS = 12, 64
+ALPHA_SCALAR, ALPHA_METRIC_EPS = 0, 1
+FP64, MIXED = 0, 1
+TYPES_ALL = 0xF
+TYPES = ("vv", "dv", "vd", "dd")
+
+
+class P2SError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        msg = error_string(code) if _lib is not None else str(code)
+        super().__init__("%s: %s (%d)" % (what, msg, code) if what else "%s (%d)" % (msg, code))
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("n_elem", ctypes.c_int64), ("nodes", ctypes.c_void_p), ("bulge", ctypes.c_void_p)]
+
+
+class Material(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("params", ctypes.c_void_p)]
+
+
+class Orders(ctypes.Structure):
+    _fields_ = [("n_comp", ctypes.c_int), ("orders", ctypes.c_void_p)]
+
+
+class Quadrature(ctypes.Structure):
+    _fields_ = [("npts_uniform", ctypes.c_int), ("npts", ctypes.c_void_p)]
+
+
+class FillOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("types_mask", ctypes.c_uint32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+# name -> (restype, argtypes); every symbol include/p2s.h declares
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+SIGNATURES = {
+    "p2s_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]),
+    "p2s_destroy": (None, [_P]),
+    "p2s_output_entries": (_I64, [_I64, ctypes.POINTER(Orders), ctypes.c_uint32, _P]),
+    "p2s_moment_entries": (_I64, [_I64, ctypes.POINTER(Orders), _P]),
+    "p2s_plan_create": (ctypes.c_int, [_P, _I64, ctypes.POINTER(Orders), ctypes.POINTER(Quadrature),
+                                       ctypes.POINTER(FillOpts), ctypes.POINTER(ctypes.c_void_p)]),
+    "p2s_plan_destroy": (None, [_P]),
+    "p2s_plan_output_entries": (_I64, [_P]),
+    "p2s_plan_moment_entries": (_I64, [_P]),
+    "p2s_plan_moments": (ctypes.c_int, [_P, ctypes.POINTER(Geometry), ctypes.POINTER(Material), _P, _P, _P]),
+    "p2s_plan_contract": (ctypes.c_int, [_P, _P, _P, _P]),
+    "p2s_plan_fill": (ctypes.c_int, [_P, ctypes.POINTER(Geometry), ctypes.POINTER(Material), _P, _P, _P]),
+    "p2s_fill_elements": (ctypes.c_int, [_P, ctypes.POINTER(Geometry), ctypes.POINTER(Material),
+                                         ctypes.POINTER(Orders), ctypes.POINTER(Quadrature),
+                                         ctypes.POINTER(FillOpts), _P, _P, _P]),
+    "p2s_sync_status": (ctypes.c_int, [_P, _P]),
+    "p2s_linearisation": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
+    "p2s_gauss_legendre": (ctypes.c_int, [ctypes.c_int, _P, _P]),
+    "p2s_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+def load():
+    """Load libp2s.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libp2s.so is not built (run __graft_entry__.build() or "
+                                   "python paper_1703_09619_gb300/build.py)")
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def error_string(code: int) -> str:
+    return load().p2s_error_string(int(code)).decode()
+
+
+def _check(rc, what):
+    if rc != OK:
+        raise P2SError(rc, what)
+
+
+def _hptr(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _dptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _orders_struct(orders):
+    orders = np.ascontiguousarray(orders, dtype=np.int32)
+    return Orders(int(orders.shape[1]), ctypes.c_void_p(orders.ctypes.data)), orders
+
+
+def output_entries(orders, types_mask=TYPES_ALL, offsets=False):
+    """Total FP64 entries (and optionally the per-element offsets) of a fill."""
+    o, keep = _orders_struct(orders)
+    E = keep.shape[0]
+    off = np.zeros(E + 1, dtype=np.int64) if offsets else None
+    n = load().p2s_output_entries(E, ctypes.byref(o), types_mask, _hptr(off))
+    if n < 0:
+        raise P2SError(int(n), "p2s_output_entries")
+    return (n, off) if offsets else n
+
+
+def moment_entries(orders, offsets=False):
+    o, keep = _orders_struct(orders)
+    E = keep.shape[0]
+    off = np.zeros(E + 1, dtype=np.int64) if offsets else None
+    n = load().p2s_moment_entries(E, ctypes.byref(o), _hptr(off))
+    if n < 0:
+        raise P2SError(int(n), "p2s_moment_entries")
+    return (n, off) if offsets else n
+
+
+def linearisation(t, m1, m2, kmax):
+    C = np.zeros(kmax + 1)
+    _check(load().p2s_linearisation(int(t), int(m1), int(m2), int(kmax), _hptr(C)), "p2s_linearisation")
+    return C
+
+
+def gauss_legendre(G):
+    x = np.zeros(G)
+    w = np.zeros(G)
+    _check(load().p2s_gauss_legendre(int(G), _hptr(x), _hptr(w)), "p2s_gauss_legendre")
+    return x, w
+
+
+class Context:
+    """A p2s_ctx on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.p2s_create(ctypes.byref(h), int(device)), "p2s_create")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().p2s_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync_status(self, stream=None) -> int:
+        return int(load().p2s_sync_status(self.handle, _stream(stream)))
+
+
+class Plan:
+    """A p2s_plan: descriptors, work list and launch shapes for one batch shape."""
+
+    def __init__(self, ctx: Context, orders, npts, precision=FP64, types_mask=TYPES_ALL):
+        lib = load()
+        self.ctx = ctx
+        o, self._orders = _orders_struct(orders)
+        E = self._orders.shape[0]
+        if np.isscalar(npts):
+            q = Quadrature(int(npts), None)
+            self._npts = None
+        else:
+            self._npts = np.ascontiguousarray(npts, dtype=np.int32).reshape(E)
+            q = Quadrature(0, ctypes.c_void_p(self._npts.ctypes.data))
+        opts = FillOpts(int(precision), int(types_mask))
+        h = ctypes.c_void_p()
+        _check(lib.p2s_plan_create(ctx.handle, E, ctypes.byref(o), ctypes.byref(q), ctypes.byref(opts),
+                                   ctypes.byref(h)), "p2s_plan_create")
+        self.handle = h
+        self.n_elem = E
+        self.n_comp = int(self._orders.shape[1])
+        self.types_mask = types_mask
+        self.precision = precision
+        self.output_entries = int(lib.p2s_plan_output_entries(h))
+        self.moment_entries = int(lib.p2s_plan_moment_entries(h))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().p2s_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _inputs(kind, params, nodes, bulge):
+        g = Geometry(int(params.shape[0]), _dptr(nodes), _dptr(bulge))
+        m = Material(int(kind), _dptr(params))
+        return g, m
+
+    def moments(self, kind, params, nodes, bulge, moments, elem_status=None, stream=None):
+        g, m = self._inputs(kind, params, nodes, bulge)
+        _check(load().p2s_plan_moments(self.handle, ctypes.byref(g), ctypes.byref(m), _dptr(moments),
+                                       _dptr(elem_status), _stream(stream)), "p2s_plan_moments")
+
+    def contract(self, moments, out, stream=None):
+        _check(load().p2s_plan_contract(self.handle, _dptr(moments), _dptr(out), _stream(stream)),
+               "p2s_plan_contract")
+
+    def fill(self, kind, params, nodes, bulge, out, elem_status=None, stream=None):
+        g, m = self._inputs(kind, params, nodes, bulge)
+        _check(load().p2s_plan_fill(self.handle, ctypes.byref(g), ctypes.byref(m), _dptr(out),
+                                    _dptr(elem_status), _stream(stream)), "p2s_plan_fill")
+
+
+def fill_elements(ctx: Context, orders, npts, kind, params, nodes, bulge, out, elem_status=None,
+                  precision=FP64, types_mask=TYPES_ALL, stream=None):
+    """One-shot fill through p2s_fill_elements (synchronises the stream)."""
+    lib = load()
+    o, keep = _orders_struct(orders)
+    E = keep.shape[0]
+    if np.isscalar(npts):
+        q = Quadrature(int(npts), None)
+        npk = None
+    else:
+        npk = np.ascontiguousarray(npts, dtype=np.int32).reshape(E)
+        q = Quadrature(0, ctypes.c_void_p(npk.ctypes.data))
+    g = Geometry(E, _dptr(nodes), _dptr(bulge))
+    m = Material(int(kind), _dptr(params))
+    opts = FillOpts(int(precision), int(types_mask))
+    _check(lib.p2s_fill_elements(ctx.handle, ctypes.byref(g), ctypes.byref(m), ctypes.byref(o), ctypes.byref(q),
+                                 ctypes.byref(opts), _dptr(out), _dptr(elem_status), _stream(stream)),
+           "p2s_fill_elements")
+
+
+def device_inputs(workload, device="cuda"):
+    """Copy a workloads.Workload's geometry/material arrays to the device (torch tensors)."""
+    import torch
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=device)
+    return t(workload.params), t(workload.nodes), t(workload.bulge)
