@@ -176,6 +176,11 @@ int p2s_gauss_legendre(int G, double* x, double* w);
 /* Static description of an error code. */
 const char* p2s_error_string(int code);
 
+/* Text of the most recent failure recorded on the calling host thread (the CUDA call
+ * and its error, or the argument check that failed); "" if none.  The pointer stays
+ * valid until the thread's next failing call. */
+const char* p2s_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

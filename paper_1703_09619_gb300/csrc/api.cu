@@ -55,7 +55,28 @@ struct p2s_plan {
 
 namespace {
 
-int set_device(int dev) { return cudaSetDevice(dev) == cudaSuccess ? P2S_OK : P2S_ERR_CUDA; }
+thread_local char g_last_error[256] = "";
+
+int fail(int code, const char* where, cudaError_t ce = cudaSuccess) {
+    if (ce != cudaSuccess)
+        std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", where, cudaGetErrorString(ce),
+                      cudaGetErrorName(ce));
+    else
+        std::snprintf(g_last_error, sizeof(g_last_error), "%s", where);
+    return code;
+}
+
+// Run a CUDA call; on failure record it and return P2S_ERR_CUDA from the caller.
+#define P2S_CUDA(call)                                                   \
+    do {                                                                 \
+        cudaError_t ce_ = (call);                                        \
+        if (ce_ != cudaSuccess) return fail(P2S_ERR_CUDA, #call, ce_);   \
+    } while (0)
+
+int set_device(int dev) {
+    cudaError_t e = cudaSetDevice(dev);
+    return e == cudaSuccess ? P2S_OK : fail(P2S_ERR_CUDA, "cudaSetDevice", e);
+}
 
 int check_orders(int64_t E, const p2s_orders* o) {
     if (E < 0 || !o || (o->n_comp != 1 && o->n_comp != 3) || (E > 0 && !o->orders)) return P2S_ERR_ARG;
@@ -96,6 +117,8 @@ int64_t elem_moments(const int32_t* ord, int nc) {
 
 extern "C" {
 
+const char* p2s_last_error(void) { return g_last_error; }
+
 const char* p2s_error_string(int code) {
     switch (code) {
     case P2S_OK: return "ok";
@@ -131,35 +154,42 @@ int p2s_linearisation(int t, int m1, int m2, int kmax, double* C) {
     return P2S_OK;
 }
 
-int p2s_create(p2s_ctx** out, int device) {
-    if (!out) return P2S_ERR_ARG;
-    *out = nullptr;
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return P2S_ERR_ARG;
-    if (set_device(device)) return P2S_ERR_CUDA;
-    p2s_ctx* c = new (std::nothrow) p2s_ctx();
-    if (!c) return P2S_ERR_OOM;
+static int ctx_init(p2s_ctx* c, int device) {
     c->device = device;
     cudaDeviceProp prop;
-    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { delete c; return P2S_ERR_CUDA; }
+    P2S_CUDA(cudaGetDeviceProperties(&prop, device));
     c->sm_count = prop.multiProcessorCount;
     c->smem_optin = prop.sharedMemPerBlockOptin;
     const HostTables& T = host_tables();
     size_t glb = sizeof(double) * (kMaxG + 1) * kMaxG;
-    bool ok = cudaMalloc(&c->d_gl_x, glb) == cudaSuccess && cudaMalloc(&c->d_gl_w, glb) == cudaSuccess &&
-              cudaMalloc(&c->d_lin_idx, sizeof(T.lin_idx)) == cudaSuccess &&
-              cudaMalloc(&c->d_lin_coef, sizeof(double) * std::max(1, T.n_coef)) == cudaSuccess &&
-              cudaMalloc(&c->d_err, sizeof(int)) == cudaSuccess;
-    if (ok)
-        ok = cudaMemcpy(c->d_gl_x, T.gl_x, glb, cudaMemcpyHostToDevice) == cudaSuccess &&
-             cudaMemcpy(c->d_gl_w, T.gl_w, glb, cudaMemcpyHostToDevice) == cudaSuccess &&
-             cudaMemcpy(c->d_lin_idx, T.lin_idx, sizeof(T.lin_idx), cudaMemcpyHostToDevice) == cudaSuccess &&
-             cudaMemcpy(c->d_lin_coef, T.lin_coef, sizeof(double) * T.n_coef, cudaMemcpyHostToDevice) ==
-                 cudaSuccess &&
-             cudaMemset(c->d_err, 0, sizeof(int)) == cudaSuccess && init_kernel_attributes() == cudaSuccess;
-    if (!ok) {
+    P2S_CUDA(cudaMalloc(&c->d_gl_x, glb));
+    P2S_CUDA(cudaMalloc(&c->d_gl_w, glb));
+    P2S_CUDA(cudaMalloc(&c->d_lin_idx, sizeof(T.lin_idx)));
+    P2S_CUDA(cudaMalloc(&c->d_lin_coef, sizeof(double) * std::max(1, T.n_coef)));
+    P2S_CUDA(cudaMalloc(&c->d_err, sizeof(int)));
+    P2S_CUDA(cudaMemcpy(c->d_gl_x, T.gl_x, glb, cudaMemcpyHostToDevice));
+    P2S_CUDA(cudaMemcpy(c->d_gl_w, T.gl_w, glb, cudaMemcpyHostToDevice));
+    P2S_CUDA(cudaMemcpy(c->d_lin_idx, T.lin_idx, sizeof(T.lin_idx), cudaMemcpyHostToDevice));
+    P2S_CUDA(cudaMemcpy(c->d_lin_coef, T.lin_coef, sizeof(double) * T.n_coef, cudaMemcpyHostToDevice));
+    P2S_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
+    P2S_CUDA(init_kernel_attributes());
+    return P2S_OK;
+}
+
+int p2s_create(p2s_ctx** out, int device) {
+    if (!out) return fail(P2S_ERR_ARG, "p2s_create: out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t ce = cudaGetDeviceCount(&ndev);
+    if (ce != cudaSuccess) return fail(P2S_ERR_CUDA, "cudaGetDeviceCount", ce);
+    if (device < 0 || device >= ndev) return fail(P2S_ERR_ARG, "p2s_create: no such device");
+    if (set_device(device)) return P2S_ERR_CUDA;
+    p2s_ctx* c = new (std::nothrow) p2s_ctx();
+    if (!c) return fail(P2S_ERR_OOM, "p2s_create: host allocation");
+    int rc = ctx_init(c, device);
+    if (rc) {
         p2s_destroy(c);
-        return P2S_ERR_CUDA;
+        return rc;
     }
     *out = c;
     return P2S_OK;
@@ -294,7 +324,7 @@ int p2s_plan_create(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, const p2s
 
     // moments launch shape: the accumulator takes what shared memory leaves, at least one pair
     size_t base = moments_smem_bytes(p->n_pairs, p->kb, p->gmax, 0);
-    size_t limit = std::min<size_t>(ctx->smem_optin, 227 * 1024);
+    size_t limit = std::min<size_t>(ctx->smem_optin, 227 * 1024) - 1024;  // room for static shared memory
     if (base + sizeof(double) * max_pair > limit) { delete p; return P2S_ERR_ORDER; }
     p->iacc_cap = (int)std::min<size_t>((limit - base) / sizeof(double), (size_t)max_elem_mom);
     // prefer two CTAs per SM when everything fits in half the shared memory
@@ -302,7 +332,7 @@ int p2s_plan_create(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, const p2s
     if (base + sizeof(double) * max_elem_mom <= half) p->iacc_cap = max_elem_mom;
     p->mom_smem = moments_smem_bytes(p->n_pairs, p->kb, p->gmax, p->iacc_cap);
     int per_sm = moments_blocks_per_sm(p->mom_smem);
-    if (per_sm < 1) { delete p; return P2S_ERR_ORDER; }
+    if (per_sm < 1) { delete p; return fail(P2S_ERR_ORDER, "p2s_plan_create: moment kernel does not fit"); }
     p->mom_grid = (int)std::max<int64_t>(1, std::min<int64_t>(E, (int64_t)ctx->sm_count * per_sm));
 
     // contraction launch shape
@@ -313,7 +343,7 @@ int p2s_plan_create(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, const p2s
     p->con_warps = w;
     p->con_smem = wbytes * w;
     int con_per_sm = contract_blocks_per_sm(w, p->con_smem);
-    if (con_per_sm < 1) { delete p; return P2S_ERR_ORDER; }
+    if (con_per_sm < 1) { delete p; return fail(P2S_ERR_ORDER, "p2s_plan_create: contraction kernel does not fit"); }
     p->con_grid = ctx->sm_count * con_per_sm;
 
     bool ok = cudaMalloc(&p->d_desc, sizeof(ElemDesc) * desc.size()) == cudaSuccess &&
@@ -336,8 +366,10 @@ int64_t p2s_plan_moment_entries(const p2s_plan* p) { return p ? p->mom_entries :
 
 int p2s_plan_moments(p2s_plan* p, const p2s_geometry* geom, const p2s_material* mat, double* moments,
                      int32_t* elem_status, void* stream) {
-    if (!p || !geom || !mat || !moments) return P2S_ERR_ARG;
-    if (geom->n_elem != p->n_elem || !mat->params) return P2S_ERR_ARG;
+    if (!p || !geom || !mat) return fail(P2S_ERR_ARG, "p2s_plan_moments: NULL plan, geometry or material");
+    if (geom->n_elem != p->n_elem) return fail(P2S_ERR_ARG, "p2s_plan_moments: n_elem differs from the plan");
+    if (p->n_elem == 0) return P2S_OK;
+    if (!moments || !mat->params) return fail(P2S_ERR_ARG, "p2s_plan_moments: NULL moments or params");
     if (mat->kind == P2S_ALPHA_SCALAR) {
         if (p->n_comp != 1) return P2S_ERR_ARG;
     } else if (mat->kind == P2S_ALPHA_METRIC_EPS) {
@@ -345,7 +377,6 @@ int p2s_plan_moments(p2s_plan* p, const p2s_geometry* geom, const p2s_material* 
     } else {
         return P2S_ERR_ARG;
     }
-    if (p->n_elem == 0) return P2S_OK;
     if (set_device(p->ctx->device)) return P2S_ERR_CUDA;
     MomentLaunch L;
     L.desc = p->d_desc;
@@ -363,16 +394,17 @@ int p2s_plan_moments(p2s_plan* p, const p2s_geometry* geom, const p2s_material* 
     L.kb = p->kb;
     L.gmax = p->gmax;
     L.iacc_cap = p->iacc_cap;
-    cudaError_t e = launch_moments_fp64(L, p->mom_grid, p->mom_smem, (cudaStream_t)stream);
-    return e == cudaSuccess ? P2S_OK : P2S_ERR_CUDA;
+    P2S_CUDA(launch_moments_fp64(L, p->mom_grid, p->mom_smem, (cudaStream_t)stream));
+    return P2S_OK;
 }
 
 int p2s_plan_contract(p2s_plan* p, const double* moments, double* out, void* stream) {
-    if (!p || !moments || !out) return P2S_ERR_ARG;
+    if (!p) return fail(P2S_ERR_ARG, "p2s_plan_contract: NULL plan");
     if (p->n_units == 0) return P2S_OK;
+    if (!moments || !out) return fail(P2S_ERR_ARG, "p2s_plan_contract: NULL moments or out");
     if (set_device(p->ctx->device)) return P2S_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    if (cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned long long), s) != cudaSuccess) return P2S_ERR_CUDA;
+    P2S_CUDA(cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned long long), s));
     ContractLaunch L;
     L.desc = p->d_desc;
     L.units = p->d_units;
@@ -385,13 +417,14 @@ int p2s_plan_contract(p2s_plan* p, const double* moments, double* out, void* str
     L.types_mask = p->types_mask;
     L.nmax = p->nmax;
     L.kmax = p->kmax;
-    cudaError_t e = launch_contract_fp64(L, p->con_grid, p->con_warps, p->con_smem, s);
-    return e == cudaSuccess ? P2S_OK : P2S_ERR_CUDA;
+    P2S_CUDA(launch_contract_fp64(L, p->con_grid, p->con_warps, p->con_smem, s));
+    return P2S_OK;
 }
 
 int p2s_plan_fill(p2s_plan* p, const p2s_geometry* geom, const p2s_material* mat, double* out,
                   int32_t* elem_status, void* stream) {
-    if (!p || !out) return P2S_ERR_ARG;
+    if (!p) return fail(P2S_ERR_ARG, "p2s_plan_fill: NULL plan");
+    if (!out && p->n_units) return fail(P2S_ERR_ARG, "p2s_plan_fill: NULL out");
     int rc = p2s_plan_moments(p, geom, mat, p->d_mom, elem_status, stream);
     if (rc) return rc;
     return p2s_plan_contract(p, p->d_mom, out, stream);
@@ -413,10 +446,10 @@ int p2s_fill_elements(p2s_ctx* ctx, const p2s_geometry* geom, const p2s_material
 int p2s_sync_status(p2s_ctx* ctx, void* stream) {
     if (!ctx) return P2S_ERR_ARG;
     if (set_device(ctx->device)) return P2S_ERR_CUDA;
-    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return P2S_ERR_CUDA;
+    P2S_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     int h = 0;
-    if (cudaMemcpy(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return P2S_ERR_CUDA;
-    if (h != 0 && cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess) return P2S_ERR_CUDA;
+    P2S_CUDA(cudaMemcpy(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h != 0) P2S_CUDA(cudaMemset(ctx->d_err, 0, sizeof(int)));
     return h;
 }
 

@@ -114,7 +114,14 @@ int contract_blocks_per_sm(int warps, size_t smem) {
 }
 
 cudaError_t contract_init_attributes() {
-    return cudaFuncSetAttribute(k_contract_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_contract_fp64);
+    if (e != cudaSuccess) return e;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_contract_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
 }
 
 }  // namespace p2s

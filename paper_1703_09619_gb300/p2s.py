@@ -28,7 +28,10 @@ class P2SError(RuntimeError):
     def __init__(self, code, what=""):
         self.code = code
         msg = error_string(code) if _lib is not None else str(code)
-        super().__init__("%s: %s (%d)" % (what, msg, code) if what else "%s (%d)" % (msg, code))
+        detail = _lib.p2s_last_error().decode() if _lib is not None else ""
+        self.detail = detail
+        text = "%s: %s (%d)" % (what, msg, code) if what else "%s (%d)" % (msg, code)
+        super().__init__(text + ("; " + detail if detail else ""))
 
 
 class Geometry(ctypes.Structure):
@@ -77,6 +80,7 @@ SIGNATURES = {
     "p2s_linearisation": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
     "p2s_gauss_legendre": (ctypes.c_int, [ctypes.c_int, _P, _P]),
     "p2s_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "p2s_last_error": (ctypes.c_char_p, []),
 }
 
 
