@@ -297,14 +297,14 @@ def run_ours(args, wl):
     achieved_flops = 2 * fmas / (con_avg * 1e-3) / 1e12
     achieved_gbs = bytes_written / (con_avg * 1e-3) / 1e9
     if prec == p2s.FP64:
-        roof = {"bound": "alu", "kernel": "k_contract_fp64", "achieved": achieved_flops,
+        roof = {"bound": "alu", "kernel": "k_contract<ArithF64>", "achieved": achieved_flops,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_flops / FP64_PEAK_TFLOPS,
                 "traffic": None,
                 "peak_source": "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (probe-measured 2 DFMA/clk/SM)",
                 "hbm_write_GBs": achieved_gbs, "hbm_frac_of_measured": achieved_gbs / peaks["hbm_gbs"],
                 "algorithmic_flop_per_launch": 2 * fmas, "algorithmic_bytes_per_launch": bytes_written}
     else:
-        roof = {"bound": "hbm", "kernel": "k_contract_mixed", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"],
+        roof = {"bound": "hbm", "kernel": "k_contract<ArithFF>", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved_gbs / peaks["hbm_gbs"], "traffic": None,
                 "peak_source": "%s (MEASURED_PEAKS.json copy bandwidth)" % src,
                 "algorithmic_bytes_per_launch": bytes_written}

@@ -27,6 +27,7 @@ struct p2s_ctx {
     double* d_gl_w = nullptr;
     int32_t* d_lin_idx = nullptr;
     double* d_lin_coef = nullptr;
+    float2* d_lin_coef_ff = nullptr;
     int* d_err = nullptr;
 };
 
@@ -44,12 +45,13 @@ struct p2s_plan {
     unsigned long long* d_counter = nullptr;
     double* d_mom = nullptr;  // scratch for p2s_plan_fill
     // launch shapes
-    int n_pairs = 1, kb = 1, gmax = 1, nmax = 1, kmax = 1;
+    int n_pairs = 1, kb = 1, gmax = 1;
     int iacc_cap = 0;
     size_t mom_smem = 0;
     int mom_grid = 1;
-    int con_warps = 8;
-    size_t con_smem = 0;
+    size_t a_cap = 1, b_cap = 1, tile_cap = 1;
+    int con_threads = 256;
+    size_t con_smem = 0, tile_off = 0;
     int con_grid = 1;
 };
 
@@ -113,6 +115,69 @@ int64_t elem_moments(const int32_t* ord, int nc) {
     return m;
 }
 
+
+// Contraction work list of one element.  Symmetry of the coupling factor
+// (alpha_{gi gj} = alpha_{gj gi}) and of the Eq. (3) coefficients gives
+//   vv(gj,gi) = vv(gi,gj)^T,  dd(gj,gi) = dd(gi,gj)^T,  vd(gj,gi) = dv(gi,gj)^T,
+// so each such pair of blocks is computed once and written twice.  Slabs of m1 and n1
+// keep one unit's shared-memory tile small and its thread count near one per
+// stage-3 combination.
+constexpr int kComboTarget = 256;
+constexpr size_t kUnitBytesTarget = 100 * 1024;
+
+void slab_sizes(const ElemDesc& d, int gi, int gj, int& m1n, int& n1n) {
+    const int8_t* Ni = d.ord[gi];
+    const int8_t* Nj = d.ord[gj];
+    n1n = Ni[1];
+    m1n = 1;
+    auto bytes = [&](int a, int b) {
+        ContractShape s = contract_shape(Ni, Nj, a, b);
+        return (s.a + s.b + s.tile) * sizeof(double);
+    };
+    while (n1n > 1 && (bytes(1, n1n) > kUnitBytesTarget || contract_shape(Ni, Nj, 1, n1n).combos > 2 * kComboTarget))
+        --n1n;
+    if (n1n == Ni[1])
+        while (m1n < Ni[0] && contract_shape(Ni, Nj, m1n + 1, n1n).combos <= kComboTarget &&
+               bytes(m1n + 1, n1n) <= kUnitBytesTarget)
+            ++m1n;
+}
+
+void push_block(const ElemDesc& d, int32_t e, int gi, int gj, int t, int tp, std::vector<ContractUnit>& units) {
+    int m1n, n1n;
+    slab_sizes(d, gi, gj, m1n, n1n);
+    const int Nu = d.ord[gi][0], Nv = d.ord[gi][1];
+    for (int m1a = 0; m1a < Nu; m1a += m1n)
+        for (int n1a = 0; n1a < Nv; n1a += n1n) {
+            ContractUnit u;
+            u.e = e;
+            u.gi = (int8_t)gi;
+            u.gj = (int8_t)gj;
+            u.t = (int8_t)t;
+            u.tp = (int8_t)tp;
+            u.m1a = (int8_t)m1a;
+            u.m1n = (int8_t)std::min(m1n, Nu - m1a);
+            u.n1a = (int8_t)n1a;
+            u.n1n = (int8_t)std::min(n1n, Nv - n1a);
+            u.pad = 0;
+            units.push_back(u);
+        }
+}
+
+void add_units(const ElemDesc& d, uint32_t mask, int32_t e, std::vector<ContractUnit>& units) {
+    const int nc = d.n_comp;
+    for (int t : {0, 3}) {  // vv, dd: upper blocks, transposed into the lower ones
+        if (!(mask & (1u << t))) continue;
+        for (int gi = 0; gi < nc; ++gi)
+            for (int gj = gi; gj < nc; ++gj) push_block(d, e, gi, gj, t, gi == gj ? -1 : t, units);
+    }
+    const bool dv = mask & 2u, vd = mask & 4u;
+    if (dv || vd) {  // dv(gi,gj) and its transpose vd(gj,gi)
+        const int t = dv ? 1 : 2, tp = (dv && vd) ? 2 : -1;
+        for (int gi = 0; gi < nc; ++gi)
+            for (int gj = 0; gj < nc; ++gj) push_block(d, e, gi, gj, t, tp, units);
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -166,11 +231,13 @@ static int ctx_init(p2s_ctx* c, int device) {
     P2S_CUDA(cudaMalloc(&c->d_gl_w, glb));
     P2S_CUDA(cudaMalloc(&c->d_lin_idx, sizeof(T.lin_idx)));
     P2S_CUDA(cudaMalloc(&c->d_lin_coef, sizeof(double) * std::max(1, T.n_coef)));
+    P2S_CUDA(cudaMalloc(&c->d_lin_coef_ff, sizeof(float2) * std::max(1, T.n_coef)));
     P2S_CUDA(cudaMalloc(&c->d_err, sizeof(int)));
     P2S_CUDA(cudaMemcpy(c->d_gl_x, T.gl_x, glb, cudaMemcpyHostToDevice));
     P2S_CUDA(cudaMemcpy(c->d_gl_w, T.gl_w, glb, cudaMemcpyHostToDevice));
     P2S_CUDA(cudaMemcpy(c->d_lin_idx, T.lin_idx, sizeof(T.lin_idx), cudaMemcpyHostToDevice));
     P2S_CUDA(cudaMemcpy(c->d_lin_coef, T.lin_coef, sizeof(double) * T.n_coef, cudaMemcpyHostToDevice));
+    P2S_CUDA(cudaMemcpy(c->d_lin_coef_ff, T.lin_coef_ff, sizeof(float2) * T.n_coef, cudaMemcpyHostToDevice));
     P2S_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
     P2S_CUDA(init_kernel_attributes());
     return P2S_OK;
@@ -203,6 +270,7 @@ void p2s_destroy(p2s_ctx* c) {
     cudaFree(c->d_gl_w);
     cudaFree(c->d_lin_idx);
     cudaFree(c->d_lin_coef);
+    cudaFree(c->d_lin_coef_ff);
     cudaFree(c->d_err);
     delete c;
 }
@@ -291,7 +359,6 @@ int p2s_plan_create(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, const p2s
             for (int g = 0; g < nc; ++g) mx = std::max(mx, (int)ord[3 * g + ax]);
             d.kax[ax] = (int8_t)(2 * mx - 1);
             p->kb = std::max(p->kb, 2 * mx - 1);
-            p->nmax = std::max(p->nmax, mx);
         }
         int po = 0;
         for (int s = 0; s < p->n_pairs; ++s) {
@@ -309,15 +376,8 @@ int p2s_plan_create(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, const p2s
         max_pair = std::max(max_pair, d.kax[0] * d.kax[1] * d.kax[2]);
         max_elem_mom = std::max(max_elem_mom, p->n_pairs * d.kax[0] * d.kax[1] * d.kax[2]);
         p->gmax = std::max(p->gmax, G);
-        for (int gi = 0; gi < nc; ++gi)
-            for (int gj = 0; gj < nc; ++gj)
-                for (int t = 0; t < 4; ++t) {
-                    if (!(opts->types_mask & (1u << t))) continue;
-                    for (int m1 = 0; m1 < ord[3 * gi]; ++m1)
-                        units.push_back(ContractUnit{(int32_t)e, (int8_t)gi, (int8_t)gj, (int8_t)t, (int8_t)m1});
-                }
+        add_units(d, opts->types_mask, (int32_t)e, units);
     }
-    p->kmax = p->kb;
     p->out_entries = out_off;
     p->mom_entries = mom_off;
     p->n_units = (int64_t)units.size();
@@ -335,14 +395,22 @@ int p2s_plan_create(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, const p2s
     if (per_sm < 1) { delete p; return fail(P2S_ERR_ORDER, "p2s_plan_create: moment kernel does not fit"); }
     p->mom_grid = (int)std::max<int64_t>(1, std::min<int64_t>(E, (int64_t)ctx->sm_count * per_sm));
 
-    // contraction launch shape
-    size_t wbytes = sizeof(double) * contract_warp_doubles(p->nmax, p->kmax);
-    int w = contract_max_warps_per_cta();
-    while (w > 1 && wbytes * w > limit) --w;
-    if (wbytes * w > limit) { delete p; return P2S_ERR_ORDER; }
-    p->con_warps = w;
-    p->con_smem = wbytes * w;
-    int con_per_sm = contract_blocks_per_sm(w, p->con_smem);
+    // contraction launch shape: buffers sized for the largest unit, one thread per
+    // stage-3 combination of the largest unit (rounded to whole warps)
+    int max_combos = 1;
+    for (const ContractUnit& u : units) {
+        const ElemDesc& d = desc[u.e];
+        ContractShape sh = contract_shape(d.ord[u.gi], d.ord[u.gj], u.m1n, u.n1n);
+        p->a_cap = std::max(p->a_cap, sh.a);
+        p->b_cap = std::max(p->b_cap, sh.b);
+        p->tile_cap = std::max(p->tile_cap, sh.tile);
+        max_combos = std::max(max_combos, sh.combos);
+    }
+    p->con_threads = std::min(512, std::max(64, (max_combos + 31) / 32 * 32));
+    p->tile_off = contract_tile_offset(p->precision, p->a_cap, p->b_cap);
+    p->con_smem = contract_smem_bytes(p->precision, p->a_cap, p->b_cap, p->tile_cap);
+    if (p->con_smem > limit) { delete p; return fail(P2S_ERR_ORDER, "p2s_plan_create: contraction tile too large"); }
+    int con_per_sm = contract_blocks_per_sm(p->precision, p->con_threads, p->con_smem);
     if (con_per_sm < 1) { delete p; return fail(P2S_ERR_ORDER, "p2s_plan_create: contraction kernel does not fit"); }
     p->con_grid = ctx->sm_count * con_per_sm;
 
@@ -394,6 +462,7 @@ int p2s_plan_moments(p2s_plan* p, const p2s_geometry* geom, const p2s_material* 
     L.kb = p->kb;
     L.gmax = p->gmax;
     L.iacc_cap = p->iacc_cap;
+    L.out_ff = p->precision == P2S_MIXED;
     P2S_CUDA(launch_moments_fp64(L, p->mom_grid, p->mom_smem, (cudaStream_t)stream));
     return P2S_OK;
 }
@@ -411,13 +480,14 @@ int p2s_plan_contract(p2s_plan* p, const double* moments, double* out, void* str
     L.n_units = p->n_units;
     L.mom = moments;
     L.lin_idx = p->ctx->d_lin_idx;
-    L.lin_coef = p->ctx->d_lin_coef;
+    L.lin_coef = p->precision == P2S_MIXED ? (const void*)p->ctx->d_lin_coef_ff : (const void*)p->ctx->d_lin_coef;
     L.out = out;
     L.counter = p->d_counter;
     L.types_mask = p->types_mask;
-    L.nmax = p->nmax;
-    L.kmax = p->kmax;
-    P2S_CUDA(launch_contract_fp64(L, p->con_grid, p->con_warps, p->con_smem, s));
+    L.a_cap = (int)p->a_cap;
+    L.b_cap = (int)p->b_cap;
+    L.tile_off = (int)p->tile_off;
+    P2S_CUDA(launch_contract(p->precision, L, p->con_grid, p->con_threads, p->con_smem, s));
     return P2S_OK;
 }
 

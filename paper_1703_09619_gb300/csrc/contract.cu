@@ -1,127 +1,257 @@
 // Step a4: the product-to-sum contraction of Eq. (4) of arXiv:1703.09619,
 //   M_t[(m1,n1,p1),(m2,n2,p2)] = sum_{k,l,q} C_t[m1,m2,k] C_t[n1,n2,l] C_t[p1,p2,q] I[k,l,q],
 // with the Eq. (3) linearisation coefficients C_t stored as runs k = kmin, kmin+2, ...
-// Three sparse mode products, one warp per work unit (element, block (gi,gj), type t,
-// test index m1):
-//   stage 1  A[m2][l][q]  = sum_k C_t[m1,m2,k] I[k][l][q]           (moments read from L2)
-//   stage 2  Bt[m2][n2][q] = sum_l C_t[n1,n2,l] A[m2][l][q]          (per n1)
-//   stage 3  M[(m1,n1,p1),(m2,n2,p2)] = sum_q C_t[p1,p2,q] Bt[m2][n2][q]
-// Stage 3 gives each lane one (m2,n2) and walks (p1,p2) in the same order on every lane,
-// so the coefficient runs are warp-uniform; a lane's Nw_j outputs of a row go through a
-// per-warp staging row and leave as one contiguous, coalesced span.
-// Plain path: every operation in FP64.
+//
+// One CTA per work unit = (element, block (gi,gj), type t, m1-slab, n1-slab):
+//   stage 1  A[m1][m2][l][q]        = sum_k C_t[m1,m2,k] I[k][l][q]
+//   stage 2  Bt[m1][n1][m2][n2][q]  = sum_l C_t[n1,n2,l] A[m1][m2][l][q]
+//   stage 3  tile[(m1,n1,p1)][(m2,n2,p2)] = sum_q C_t[p1,p2,q] Bt[m1][n1][m2][n2][q]
+// Stage 3 gives each thread one (m1,n1,m2,n2) combination and walks (p1,p2) in the same
+// order on every thread, so the coefficient runs are uniform across the CTA.  The tile is
+// staged in shared memory and leaves twice, both times as contiguous row segments:
+//   - as rows of M_t(gi,gj), and
+//   - transposed, as rows of the partner block M_t'(gj,gi) = M_t(gi,gj)^T, where
+//     t' = t for vv and dd (alpha symmetric) and t' = vd for t = dv.
+// The host builds the unit list so that every block is computed once and written to
+// both places.
+//
+// Two arithmetics share the structure:
+//   FP64   - every operation in FP64;
+//   mixed  - float-float (hi + lo FP32 pairs) products and sums with exact FMA product
+//            errors and TwoSum accumulation; moments arrive as (hi, lo) pairs; the FP64
+//            output bits are assembled from (hi, lo) with integer operations, so the hot
+//            loop issues no FP64 instruction (FP64 runs at 1/58 of FP32 on this part).
 #include "p2s_internal.h"
 
 namespace p2s {
 namespace {
 
-constexpr int kWarpsPerCta = 8;
+// ------------------------------------------------------------------ arithmetic
+struct ArithF64 {
+    using T = double;
+    using C = double;
+    __device__ static T zero() { return 0.0; }
+    __device__ static void fma_acc(T& acc, C c, T x) { acc = fma(c, x, acc); }
+    __device__ static T finish(T acc) { return acc; }
+    __device__ static double to_double(T v) { return v; }
+    __device__ static T load_moment(const void* p, size_t i) { return __ldg(reinterpret_cast<const double*>(p) + i); }
+    __device__ static C load_coef(const void* p, int i) { return __ldg(reinterpret_cast<const double*>(p) + i); }
+};
+
+// float-float value: x = hi + lo, |lo| <= ulp(hi)/2 after finish()
+struct ArithFF {
+    using T = float2;
+    using C = float2;
+    __device__ static T zero() { return make_float2(0.f, 0.f); }
+    // acc += c * x, with the exact error of the leading product (FMA) and of the leading
+    // sum (TwoSum); second-order terms go to the low word.
+    __device__ static void fma_acc(T& acc, C c, T x) {
+        float p = c.x * x.x;
+        float e = fmaf(c.x, x.x, -p);
+        e = fmaf(c.x, x.y, e);
+        e = fmaf(c.y, x.x, e);
+        float s = acc.x + p;
+        float bp = s - acc.x;
+        float err = (acc.x - (s - bp)) + (p - bp);
+        acc.x = s;
+        acc.y += err + e;
+    }
+    __device__ static T finish(T acc) {  // Fast2Sum renormalisation
+        float s = acc.x + acc.y;
+        float lo = acc.y - (s - acc.x);
+        return make_float2(s, lo);
+    }
+    // FP64 bits of hi + lo without FP64 instructions: hi's double pattern plus lo in units
+    // of the last place of hi's binade (lo < 2^29 such units, so no carry into the exponent;
+    // a borrow below a power of two is taken in the halved units of the lower binade).
+    __device__ static double to_double(T v) {
+        const uint32_t hb = __float_as_uint(v.x);
+        const uint32_t ah = hb & 0x7fffffffu;
+        // zero and subnormal hi (|hi + lo| < 2^-126) map to a signed zero; inf/nan to a quiet nan
+        if (ah < 0x00800000u) return __longlong_as_double((long long)((uint64_t)(hb & 0x80000000u) << 32));
+        if (ah >= 0x7f800000u) return __longlong_as_double(0x7ff8000000000000ll);
+        const uint32_t e = ah >> 23;
+        uint64_t pat = ((uint64_t)((hb & 0x80000000u) | ((e + 896u) << 20) | ((hb & 0x7fffffu) >> 3)) << 32) |
+                       (uint64_t)(hb << 29);
+        const uint32_t lb = __float_as_uint(v.y);
+        const uint32_t al = lb & 0x7fffffffu;
+        if (al >= 0x00800000u) {
+            const int sh = (int)(al >> 23) - (int)e + 29;
+            const uint32_t lm = (al & 0x7fffffu) | 0x800000u;
+            uint32_t u = sh >= 0 ? (lm << sh) : (sh > -32 ? (lm >> -sh) : 0u);
+            if ((lb ^ hb) & 0x80000000u) {
+                if ((hb & 0x7fffffu) == 0u) u <<= 1;
+                pat -= u;
+            } else {
+                pat += u;
+            }
+        }
+        return __longlong_as_double((long long)pat);
+    }
+    __device__ static T load_moment(const void* p, size_t i) { return __ldg(reinterpret_cast<const float2*>(p) + i); }
+    __device__ static C load_coef(const void* p, int i) { return __ldg(reinterpret_cast<const float2*>(p) + i); }
+};
 
 __device__ __forceinline__ int type_slot(uint32_t mask, int t) { return __popc(mask & ((1u << t) - 1u)); }
 
-__global__ void __launch_bounds__(kWarpsPerCta * 32) k_contract_fp64(ContractLaunch L) {
-    extern __shared__ double sm[];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const size_t wd = contract_warp_doubles(L.nmax, L.kmax);
-    double* A = sm + wid * wd;
-    double* Bt = A + (size_t)L.nmax * L.kmax * L.kmax;
-    double* stg = Bt + (size_t)L.nmax * L.nmax * L.kmax;
+template <class A>
+__global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
+    using T = typename A::T;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* sA = reinterpret_cast<T*>(smraw);
+    T* sB = sA + L.a_cap;
+    double* tile = reinterpret_cast<double*>(smraw + L.tile_off);
+    __shared__ ContractUnit cu;
+    __shared__ unsigned long long unit_id;
+    const int tid = threadIdx.x, nth = blockDim.x;
     const int32_t* __restrict__ lidx = L.lin_idx;
-    const double* __restrict__ lcoef = L.lin_coef;
+    const void* lcoef = L.lin_coef;
 
     for (;;) {
-        unsigned long long u = 0;
-        if (lane == 0) u = atomicAdd(L.counter, 1ull);
-        u = __shfl_sync(0xffffffffu, u, 0);
-        if (u >= (unsigned long long)L.n_units) break;
-        const ContractUnit cu = L.units[u];
+        if (tid == 0) {
+            unit_id = atomicAdd(L.counter, 1ull);
+            if (unit_id < (unsigned long long)L.n_units) cu = L.units[unit_id];
+        }
+        __syncthreads();
+        if (unit_id >= (unsigned long long)L.n_units) break;
         const ElemDesc* d = L.desc + cu.e;
-        const int gi = cu.gi, gj = cu.gj, t = cu.t, m1 = cu.m1;
+        const int gi = cu.gi, gj = cu.gj, t = cu.t;
+        const int m1a = cu.m1a, m1n = cu.m1n, n1a = cu.n1a, n1n = cu.n1n;
         const int Nv_i = d->ord[gi][1], Nw_i = d->ord[gi][2];
         const int Nu_j = d->ord[gj][0], Nv_j = d->ord[gj][1], Nw_j = d->ord[gj][2];
         const int Kv = Nv_i + Nv_j - 1, Kw = Nw_i + Nw_j - 1;
         const int n = d->n;
-        const double* __restrict__ I = L.mom + d->mom_off + d->pair_off[pair_index(gi, gj, d->n_comp)];
-        double* Mt = L.out + d->out_off + (int64_t)type_slot(L.types_mask, t) * n * n;
+        const int nj = Nu_j * Nv_j * Nw_j;
+        const int ld = nj + 1;  // padded tile row stride (doubles)
+        const size_t moff = d->mom_off + d->pair_off[pair_index(gi, gj, d->n_comp)];
 
-        // stage 1
+        // stage 1: A[m1][m2][l][q], m1 in the slab
         const int KvKw = Kv * Kw;
-        for (int idx = lane; idx < Nu_j * KvKw; idx += 32) {
-            const int m2 = idx / KvKw, lq = idx - m2 * KvKw;
-            const int32_t li = __ldg(lidx + lin_slot(t, m1, m2));
+        const int nA = m1n * Nu_j * KvKw;
+        for (int idx = tid; idx < nA; idx += nth) {
+            const int mm = idx / KvKw, lq = idx - mm * KvKw;
+            const int im1 = mm / Nu_j, m2 = mm - im1 * Nu_j;
+            const int32_t li = __ldg(lidx + lin_slot(t, m1a + im1, m2));
             const int k0 = lin_kmin(li), cnt = lin_cnt(li), off = lin_off(li);
-            double acc = 0.0;
-            for (int r = 0; r < cnt; ++r) acc = fma(__ldg(lcoef + off + r), __ldg(I + (k0 + 2 * r) * KvKw + lq), acc);
-            A[idx] = acc;
+            T acc = A::zero();
+            for (int r = 0; r < cnt; ++r)
+                A::fma_acc(acc, A::load_coef(lcoef, off + r), A::load_moment(L.mom, moff + (size_t)(k0 + 2 * r) * KvKw + lq));
+            sA[idx] = A::finish(acc);
         }
-        __syncwarp();
+        __syncthreads();
+        // stage 2: Bt[m1][n1][m2][n2][q], (m1, n1) in the slab
         const int NvKw = Nv_j * Kw;
-        const int ncombo = Nu_j * Nv_j;
-        for (int n1 = 0; n1 < Nv_i; ++n1) {
-            // stage 2
-            for (int idx = lane; idx < Nu_j * NvKw; idx += 32) {
-                const int m2 = idx / NvKw, r2 = idx - m2 * NvKw, n2 = r2 / Kw, q = r2 - n2 * Kw;
-                const int32_t li = __ldg(lidx + lin_slot(t, n1, n2));
-                const int l0 = lin_kmin(li), cnt = lin_cnt(li), off = lin_off(li);
-                const double* a = A + (m2 * Kv + l0) * Kw + q;
-                double acc = 0.0;
-                for (int r = 0; r < cnt; ++r) acc = fma(__ldg(lcoef + off + r), a[2 * r * Kw], acc);
-                Bt[idx] = acc;
-            }
-            __syncwarp();
-            // stage 3
+        const int per_n1 = Nu_j * NvKw;
+        const int nB = m1n * n1n * per_n1;
+        for (int idx = tid; idx < nB; idx += nth) {
+            const int mn = idx / per_n1, r2 = idx - mn * per_n1;
+            const int im1 = mn / n1n, in1 = mn - im1 * n1n;
+            const int m2 = r2 / NvKw, r3 = r2 - m2 * NvKw, n2 = r3 / Kw, q = r3 - n2 * Kw;
+            const int32_t li = __ldg(lidx + lin_slot(t, n1a + in1, n2));
+            const int l0 = lin_kmin(li), cnt = lin_cnt(li), off = lin_off(li);
+            const T* a = sA + ((im1 * Nu_j + m2) * Kv + l0) * Kw + q;
+            T acc = A::zero();
+            for (int r = 0; r < cnt; ++r) A::fma_acc(acc, A::load_coef(lcoef, off + r), a[2 * r * Kw]);
+            sB[idx] = A::finish(acc);
+        }
+        __syncthreads();
+        // stage 3: combos (m1, n1, m2, n2); each walks (p1, p2)
+        const int ncombo = m1n * n1n * Nu_j * Nv_j;
+        const int mjn = Nu_j * Nv_j;
+        for (int c = tid; c < ncombo; c += nth) {
+            const int mn = c / mjn, mj = c - mn * mjn;  // mn = im1 * n1n + in1, mj = m2 * Nv_j + n2
+            const T* bt = sB + (size_t)c * Kw;
+            double* trow = tile + (size_t)(mn * Nw_i) * ld + mj * Nw_j;
             for (int p1 = 0; p1 < Nw_i; ++p1) {
-                const int row = d->dof_off[gi] + (m1 * Nv_i + n1) * Nw_i + p1;
-                double* rowp = Mt + (int64_t)row * n + d->dof_off[gj];
-                for (int cb = 0; cb < ncombo; cb += 32) {
-                    const int combo = cb + lane;
-                    if (combo < ncombo) {
-                        const double* bt = Bt + combo * Kw;
-                        for (int p2 = 0; p2 < Nw_j; ++p2) {
-                            const int32_t li = __ldg(lidx + lin_slot(t, p1, p2));
-                            const int q0 = lin_kmin(li), cnt = lin_cnt(li), off = lin_off(li);
-                            double acc = 0.0;
-                            for (int r = 0; r < cnt; ++r) acc = fma(__ldg(lcoef + off + r), bt[q0 + 2 * r], acc);
-                            stg[lane * Nw_j + p2] = acc;
-                        }
-                    }
-                    __syncwarp();
-                    const int span = min(32, ncombo - cb) * Nw_j;
-                    double* dst = rowp + cb * Nw_j;
-                    for (int x = lane; x < span; x += 32) dst[x] = stg[x];
-                    __syncwarp();
+                for (int p2 = 0; p2 < Nw_j; ++p2) {
+                    const int32_t li = __ldg(lidx + lin_slot(t, p1, p2));
+                    const int q0 = lin_kmin(li), cnt = lin_cnt(li), off = lin_off(li);
+                    T acc = A::zero();
+                    for (int r = 0; r < cnt; ++r) A::fma_acc(acc, A::load_coef(lcoef, off + r), bt[q0 + 2 * r]);
+                    trow[p1 * ld + p2] = A::to_double(A::finish(acc));
                 }
             }
         }
-        __syncwarp();
+        __syncthreads();
+        // write-out 1: rows (m1, n1, p1) of M_t(gi, gj)
+        const int rows = m1n * n1n * Nw_i;
+        double* Mt = L.out + d->out_off + (int64_t)type_slot(L.types_mask, t) * n * n;
+        const int row0 = d->dof_off[gi];
+        const int col0 = d->dof_off[gj];
+        for (int idx = tid; idx < rows * nj; idx += nth) {
+            const int r = idx / nj, c = idx - r * nj;
+            const int im1 = r / (n1n * Nw_i), r2 = r - im1 * n1n * Nw_i, in1 = r2 / Nw_i, p1 = r2 - in1 * Nw_i;
+            const int grow = row0 + ((m1a + im1) * Nv_i + n1a + in1) * Nw_i + p1;
+            __stcs(Mt + (int64_t)grow * n + col0 + c, tile[r * ld + c]);
+        }
+        // write-out 2: the transpose into the partner block (gj, gi) of type tp
+        if (cu.tp >= 0) {
+            double* Mp = L.out + d->out_off + (int64_t)type_slot(L.types_mask, cu.tp) * n * n;
+            for (int idx = tid; idx < rows * nj; idx += nth) {
+                const int c = idx / rows, r = idx - c * rows;
+                const int im1 = r / (n1n * Nw_i), r2 = r - im1 * n1n * Nw_i, in1 = r2 / Nw_i, p1 = r2 - in1 * Nw_i;
+                const int gcol = row0 + ((m1a + im1) * Nv_i + n1a + in1) * Nw_i + p1;
+                __stcs(Mp + (int64_t)(col0 + c) * n + gcol, tile[r * ld + c]);
+            }
+        }
+        __syncthreads();
     }
 }
 
-}  // namespace
-
-cudaError_t launch_contract_fp64(const ContractLaunch& L, int grid, int warps_per_cta, size_t smem, cudaStream_t s) {
-    if (warps_per_cta < 1 || warps_per_cta > kWarpsPerCta) return cudaErrorInvalidValue;
-    k_contract_fp64<<<grid, warps_per_cta * 32, smem, s>>>(L);
-    return cudaGetLastError();
-}
-
-int contract_max_warps_per_cta() { return kWarpsPerCta; }
-
-int contract_blocks_per_sm(int warps, size_t smem) {
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_contract_fp64, warps * 32, smem) != cudaSuccess) return 0;
-    return n;
-}
-
-cudaError_t contract_init_attributes() {
+cudaError_t set_max_smem(const void* f) {
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, k_contract_fp64);
+    cudaError_t e = cudaFuncGetAttributes(&fa, f);
     if (e != cudaSuccess) return e;
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_contract_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
+}  // namespace
+
+ContractShape contract_shape(const int8_t* Ni, const int8_t* Nj, int m1n, int n1n) {
+    ContractShape s;
+    const int Kv = Ni[1] + Nj[1] - 1, Kw = Ni[2] + Nj[2] - 1;
+    s.a = (size_t)m1n * Nj[0] * Kv * Kw;
+    s.b = (size_t)m1n * n1n * Nj[0] * Nj[1] * Kw;
+    s.tile = (size_t)m1n * n1n * Ni[2] * (Nj[0] * Nj[1] * Nj[2] + 1);
+    s.combos = m1n * n1n * Nj[0] * Nj[1];
+    return s;
+}
+
+size_t contract_tile_offset(int precision, size_t a_cap, size_t b_cap) {
+    size_t el = precision == P2S_MIXED ? sizeof(float2) : sizeof(double);
+    return ((a_cap + b_cap) * el + 15) & ~(size_t)15;
+}
+
+size_t contract_smem_bytes(int precision, size_t a_cap, size_t b_cap, size_t tile_cap) {
+    return contract_tile_offset(precision, a_cap, b_cap) + tile_cap * sizeof(double);
+}
+
+cudaError_t launch_contract(int precision, const ContractLaunch& L, int grid, int threads, size_t smem,
+                            cudaStream_t s) {
+    if (threads < 32 || threads > 512 || threads % 32) return cudaErrorInvalidValue;
+    if (precision == P2S_MIXED)
+        k_contract<ArithFF><<<grid, threads, smem, s>>>(L);
+    else
+        k_contract<ArithF64><<<grid, threads, smem, s>>>(L);
+    return cudaGetLastError();
+}
+
+int contract_blocks_per_sm(int precision, int threads, size_t smem) {
+    int n = 0;
+    cudaError_t e = precision == P2S_MIXED
+                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_contract<ArithFF>, threads, smem)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_contract<ArithF64>, threads, smem);
+    return e == cudaSuccess ? n : 0;
+}
+
+cudaError_t contract_init_attributes() {
+    cudaError_t e = set_max_smem((const void*)k_contract<ArithF64>);
+    if (e != cudaSuccess) return e;
+    return set_max_smem((const void*)k_contract<ArithFF>);
 }
 
 }  // namespace p2s

@@ -217,7 +217,13 @@ __global__ void __launch_bounds__(kThreads) k_moments_fp64(MomentLaunch L) {
                 const double* src = S.Iacc + s * per_pair;
                 for (int i = tid; i < ku * kv * kw; i += kThreads) {
                     const int k = i / (kv * kw), r = i - k * kv * kw, l = r / kw, q = r - l * kw;
-                    dst[i] = src[(k * Kv + l) * Kw + q];
+                    const double v = src[(k * Kv + l) * Kw + q];
+                    if (L.out_ff) {
+                        const float hi = (float)v;
+                        reinterpret_cast<float2*>(dst)[i] = make_float2(hi, (float)(v - (double)hi));
+                    } else {
+                        dst[i] = v;
+                    }
                 }
             }
             __syncthreads();

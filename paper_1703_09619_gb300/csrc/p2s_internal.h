@@ -37,10 +37,13 @@ struct ElemDesc {
     int8_t kax[3];        // element-wide moment count per axis (max over pairs)
 };
 
-// One warp work item of the contraction: element, block (gi, gj), type, test index m1.
+// One CTA work item of the contraction: element, block (gi, gj), type t, the partner type
+// tp whose block (gj, gi) receives the transpose (-1: none), and the m1/n1 slab.
 struct ContractUnit {
     int32_t e;
-    int8_t gi, gj, t, m1;
+    int8_t gi, gj, t, tp;
+    int8_t m1a, m1n, n1a, n1n;
+    int32_t pad;
 };
 
 // Packed linearisation index: kmin | cnt << 8 | off << 16 into the coefficient array.
@@ -58,6 +61,7 @@ struct HostTables {
     int32_t lin_idx[kNumTypes * kMaxOrder * kMaxOrder];
     double lin_coef[kNumTypes * kMaxOrder * kMaxOrder * kMaxOrder];
     int n_coef;
+    float lin_coef_ff[2 * kNumTypes * kMaxOrder * kMaxOrder * kMaxOrder];  // (hi, lo) pairs
 };
 const HostTables& host_tables();
 
@@ -78,6 +82,7 @@ struct MomentLaunch {
     int kb;             // max moments per axis over the plan
     int gmax;           // max G over the plan
     int iacc_cap;       // doubles of the moment accumulator in shared memory
+    int out_ff;         // 1: store moments as (hi, lo) FP32 pairs (mixed path)
 };
 size_t moments_smem_bytes(int n_pairs, int kb, int gmax, int iacc_cap);
 cudaError_t launch_moments_fp64(const MomentLaunch& L, int grid, size_t smem, cudaStream_t s);
@@ -86,24 +91,27 @@ struct ContractLaunch {
     const ElemDesc* desc;
     const ContractUnit* units;
     int64_t n_units;
-    const double* mom;
+    const void* mom;       // FP64 moments, or (hi, lo) FP32 pairs for the mixed path
     const int32_t* lin_idx;
-    const double* lin_coef;
+    const void* lin_coef;  // double, or float2 pairs for the mixed path
     double* out;
     unsigned long long* counter;  // zeroed before the launch
     uint32_t types_mask;
-    int nmax;  // max order over the plan
-    int kmax;  // max moments per axis over the plan
+    int a_cap, b_cap;      // elements of the stage-1 / stage-2 buffers
+    int tile_off;          // byte offset of the FP64 tile in shared memory
 };
-__host__ __device__ inline size_t contract_warp_doubles(int nmax, int kmax) {
-    return (size_t)nmax * kmax * kmax + (size_t)nmax * nmax * kmax + 32 * (size_t)nmax;
-}
-int contract_max_warps_per_cta();
+struct ContractShape {
+    size_t a, b, tile;
+    int combos;
+};
+ContractShape contract_shape(const int8_t* Ni, const int8_t* Nj, int m1n, int n1n);
+size_t contract_tile_offset(int precision, size_t a_cap, size_t b_cap);
+size_t contract_smem_bytes(int precision, size_t a_cap, size_t b_cap, size_t tile_cap);
+cudaError_t launch_contract(int precision, const ContractLaunch& L, int grid, int threads, size_t smem,
+                            cudaStream_t s);
+int contract_blocks_per_sm(int precision, int threads, size_t smem);
 int moments_threads();
 int moments_blocks_per_sm(size_t smem);
-int contract_blocks_per_sm(int warps, size_t smem);
 cudaError_t init_kernel_attributes();
-cudaError_t launch_contract_fp64(const ContractLaunch& L, int grid, int warps_per_cta, size_t smem,
-                                 cudaStream_t s);
 
 }  // namespace p2s

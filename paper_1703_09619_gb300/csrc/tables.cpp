@@ -104,7 +104,13 @@ HostTables* build() {
                 int cnt = 0;
                 if (kmin >= 0) {
                     cnt = (kmax - kmin) / 2 + 1;
-                    for (int r = 0; r < cnt; ++r) T.lin_coef[off + r] = (double)dense[kmin + 2 * r];
+                    for (int r = 0; r < cnt; ++r) {
+                        double c = (double)dense[kmin + 2 * r];
+                        float hi = (float)c;
+                        T.lin_coef[off + r] = c;
+                        T.lin_coef_ff[2 * (off + r)] = hi;
+                        T.lin_coef_ff[2 * (off + r) + 1] = (float)(c - (double)hi);
+                    }
                 } else {
                     kmin = 0;
                 }

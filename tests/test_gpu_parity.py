@@ -1,8 +1,8 @@
-"""GPU parity of the plain FP64 fill against the CPU oracle (element by element).
+"""GPU parity of the fill against the CPU oracle (element by element).
 
 Bar (Eq. (2) vs Eq. (4) with the same quadrature rule): per element and product type,
-max|M_gpu - M_oracle| <= 1e-12 * max|M_oracle|.  The two paths share only the seeded
-input generators."""
+max|M_gpu - M_oracle| <= tol * max|M_oracle|, tol = 1e-12 for the FP64 path and 1e-8
+for the mixed-precision path.  The two paths share only the seeded input generators."""
 import numpy as np
 import pytest
 
@@ -12,6 +12,9 @@ from paper_1703_09619_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 TOL_FP64 = 1e-12
+TOL_MIXED = 1e-8
+TOL = {p2s.FP64: TOL_FP64, p2s.MIXED: TOL_MIXED}
+PRECS = [p2s.FP64, p2s.MIXED]
 
 
 @pytest.fixture(scope="module")
@@ -64,65 +67,76 @@ def per_type_errors(gpu, ref, off, orders, types_mask=0xF):
     return np.array(errs)
 
 
-def check(torch, ctx, wl, types_mask=0xF, tol=TOL_FP64, split=False):
-    g, status, rc = gpu_fill(torch, ctx, wl, types_mask=types_mask, split=split)
+def check(torch, ctx, wl, types_mask=0xF, precision=p2s.FP64, split=False):
+    tol = TOL[precision]
+    g, status, rc = gpu_fill(torch, ctx, wl, precision=precision, types_mask=types_mask, split=split)
     r, off = oracle_fill(wl, types_mask)
     assert g.shape == r.shape
     assert not np.isnan(g).any()
     err = per_type_errors(g, r, off, wl.orders, types_mask)
-    assert err.max() <= tol, (wl.name, err.max())
+    assert err.max() <= tol, (wl.name, precision, err.max())
     assert (status == 0).all() and rc == 0
     return err
 
 
-def test_c1_whole(torch_cuda, ctx):
-    err = check(torch_cuda, ctx, W.make("c1"))
+@pytest.mark.parametrize("prec", PRECS)
+def test_c1_whole(torch_cuda, ctx, prec):
+    err = check(torch_cuda, ctx, W.make("c1"), precision=prec)
     assert err.size == 4
 
 
-def test_c2_shape_small_orders_many_elements(torch_cuda, ctx):
+@pytest.mark.parametrize("prec", PRECS)
+def test_c2_shape_small_orders_many_elements(torch_cuda, ctx, prec):
     """3 components, curved elements, several CTAs/warps and a ragged last wave."""
     wl = W.make("c2", 37)
     wl.orders[:] = 3
     wl = wl.with_npts(5)
-    check(torch_cuda, ctx, wl)
+    check(torch_cuda, ctx, wl, precision=prec)
 
 
-def test_c2_full_order_two_elements(torch_cuda, ctx):
-    check(torch_cuda, ctx, W.make("c2", 2))
+@pytest.mark.parametrize("prec", PRECS)
+def test_c2_full_order_two_elements(torch_cuda, ctx, prec):
+    check(torch_cuda, ctx, W.make("c2", 2), precision=prec)
 
 
-def test_c4_uneven_orders(torch_cuda, ctx):
-    check(torch_cuda, ctx, W.make("c4", 6))
+@pytest.mark.parametrize("prec", PRECS)
+def test_c4_uneven_orders(torch_cuda, ctx, prec):
+    check(torch_cuda, ctx, W.make("c4", 6), precision=prec)
 
 
-def test_c3_order8(torch_cuda, ctx):
+@pytest.mark.parametrize("prec", PRECS)
+def test_c3_order8(torch_cuda, ctx, prec):
     wl = W.make("c3", 2).with_npts(12)
-    check(torch_cuda, ctx, wl)
+    check(torch_cuda, ctx, wl, precision=prec)
 
 
-def test_moments_then_contract_equals_fill(torch_cuda, ctx):
+@pytest.mark.parametrize("prec", PRECS)
+def test_moments_then_contract_equals_fill(torch_cuda, ctx, prec):
     wl = W.make("c4", 5)
-    a, _, _ = gpu_fill(torch_cuda, ctx, wl)
-    b, _, _ = gpu_fill(torch_cuda, ctx, wl, split=True)
+    a, _, _ = gpu_fill(torch_cuda, ctx, wl, precision=prec)
+    b, _, _ = gpu_fill(torch_cuda, ctx, wl, precision=prec, split=True)
     assert np.array_equal(a, b)
 
 
-def test_repeatable_bitwise(torch_cuda, ctx):
+@pytest.mark.parametrize("prec", PRECS)
+def test_repeatable_bitwise(torch_cuda, ctx, prec):
     wl = W.make("c2", 3)
-    a, _, _ = gpu_fill(torch_cuda, ctx, wl)
-    b, _, _ = gpu_fill(torch_cuda, ctx, wl)
+    a, _, _ = gpu_fill(torch_cuda, ctx, wl, precision=prec)
+    b, _, _ = gpu_fill(torch_cuda, ctx, wl, precision=prec)
     assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("mask", [0x1, 0x2, 0x4, 0x8, 0x6, 0x9])
-def test_type_subsets(torch_cuda, ctx, mask):
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("mask", [0x1, 0x2, 0x4, 0x8, 0x6, 0x9, 0x3, 0xC, 0xB])
+def test_type_subsets(torch_cuda, ctx, mask, prec):
+    """Every subset keeps the transpose partners consistent (dv alone, vd alone, both)."""
     wl = W.make("c4", 3)
     wl = wl.with_npts(6)
-    check(torch_cuda, ctx, wl, types_mask=mask)
+    check(torch_cuda, ctx, wl, types_mask=mask, precision=prec)
 
 
-def test_degenerate_orders_and_points(torch_cuda, ctx):
+@pytest.mark.parametrize("prec", PRECS)
+def test_degenerate_orders_and_points(torch_cuda, ctx, prec):
     """N = 1 on some axes, anisotropic orders, G = 1 and G = 2 quadrature."""
     wl = W.make("c4", 4)
     wl.orders[0] = [[1, 1, 1], [1, 2, 3], [3, 1, 2]]
@@ -130,19 +144,21 @@ def test_degenerate_orders_and_points(torch_cuda, ctx):
     wl.orders[2] = [[1, 1, 1], [1, 1, 1], [1, 1, 1]]
     wl.orders[3] = [[8, 1, 2], [2, 8, 1], [1, 2, 8]]
     for G in (1, 2, 7):
-        check(torch_cuda, ctx, wl.with_npts(G))
+        check(torch_cuda, ctx, wl.with_npts(G), precision=prec)
 
 
-def test_per_element_quadrature(torch_cuda, ctx):
+@pytest.mark.parametrize("prec", PRECS)
+def test_per_element_quadrature(torch_cuda, ctx, prec):
     wl = W.make("c5", 6)
     wl = wl.with_npts(np.array([4, 9, 16, 3, 24, 7]))
-    check(torch_cuda, ctx, wl)
+    check(torch_cuda, ctx, wl, precision=prec)
 
 
-def test_large_G_scalar(torch_cuda, ctx):
+@pytest.mark.parametrize("prec", PRECS)
+def test_large_G_scalar(torch_cuda, ctx, prec):
     wl = W.make("c3", 1)
     wl.orders[:] = 3
-    check(torch_cuda, ctx, wl.with_npts(64))
+    check(torch_cuda, ctx, wl.with_npts(64), precision=prec)
 
 
 def test_empty_batch(torch_cuda, ctx):
@@ -195,6 +211,28 @@ def test_one_shot_entry_point(torch_cuda, ctx):
     r, off = oracle_fill(wl)
     err = per_type_errors(out.cpu().numpy(), r, off, wl.orders)
     assert err.max() <= TOL_FP64
+
+
+def test_full_size_c5_mixed_sampled(torch_cuda, ctx):
+    """The full 32768-element three-component N=4 workload through the mixed path at a
+    fixed 12-point rule; three seeded elements checked entry by entry (<= 1e-8)."""
+    torch = torch_cuda
+    wl = W.make("c5").with_npts(12)
+    params, nodes, bulge = p2s.device_inputs(wl)
+    plan = p2s.Plan(ctx, wl.orders, 12, p2s.MIXED)
+    out = torch.empty(plan.output_entries, dtype=torch.float64, device="cuda")
+    plan.fill(wl.kind, params, nodes, bulge, out)
+    assert ctx.sync_status() == 0
+    off = oracle.output_offsets(wl.orders)
+    rng = np.random.default_rng(12)
+    for e in sorted(rng.choice(wl.n_elem, 3, replace=False)):
+        sub = wl.subset([e])
+        r, roff = oracle_fill(sub)
+        g = out[int(off[e]):int(off[e + 1])].cpu().numpy()
+        err = per_type_errors(g, r, roff, sub.orders)
+        assert err.max() <= TOL_MIXED, (e, err.max())
+    del out
+    plan.close()
 
 
 def test_full_size_c2_sampled(torch_cuda, ctx):
