@@ -15,51 +15,12 @@ cudaError_t init_kernel_attributes() {
     if (e != cudaSuccess) return e;
     return contract_init_attributes();
 }
-}  // namespace p2s
-
-using namespace p2s;
-
-struct p2s_ctx {
-    int device = 0;
-    int sm_count = 0;
-    size_t smem_optin = 0;
-    double* d_gl_x = nullptr;
-    double* d_gl_w = nullptr;
-    int32_t* d_lin_idx = nullptr;
-    double* d_lin_coef = nullptr;
-    float2* d_lin_coef_ff = nullptr;
-    int* d_err = nullptr;
-};
-
-struct p2s_plan {
-    p2s_ctx* ctx = nullptr;
-    int64_t n_elem = 0;
-    int n_comp = 0;
-    uint32_t types_mask = 0;
-    int precision = 0;
-    int64_t out_entries = 0;
-    int64_t mom_entries = 0;
-    int64_t n_units = 0;
-    ElemDesc* d_desc = nullptr;
-    ContractUnit* d_units = nullptr;
-    unsigned long long* d_counter = nullptr;
-    double* d_mom = nullptr;  // scratch for p2s_plan_fill
-    // launch shapes
-    int n_pairs = 1, kb = 1, gmax = 1;
-    int iacc_cap = 0;
-    size_t mom_smem = 0;
-    int mom_grid = 1;
-    size_t a_cap = 1, b_cap = 1, tile_cap = 1;
-    int con_threads = 256;
-    size_t con_smem = 0, tile_off = 0;
-    int con_grid = 1;
-};
 
 namespace {
-
 thread_local char g_last_error[256] = "";
+}
 
-int fail(int code, const char* where, cudaError_t ce = cudaSuccess) {
+int fail(int code, const char* where, cudaError_t ce) {
     if (ce != cudaSuccess)
         std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", where, cudaGetErrorString(ce),
                       cudaGetErrorName(ce));
@@ -68,12 +29,31 @@ int fail(int code, const char* where, cudaError_t ce = cudaSuccess) {
     return code;
 }
 
+}  // namespace p2s
+
+using namespace p2s;
+
+struct p2s_ctx {
+    DeviceTables T;
+};
+
+struct p2s_plan {
+    p2s_ctx* ctx = nullptr;
+    PlanLayout L;
+    ElemDesc* d_desc = nullptr;
+    ContractUnit* d_units = nullptr;
+    unsigned long long* d_counter = nullptr;
+    double* d_mom = nullptr;  // moment scratch of p2s_plan_fill
+};
+
 // Run a CUDA call; on failure record it and return P2S_ERR_CUDA from the caller.
-#define P2S_CUDA(call)                                                   \
-    do {                                                                 \
-        cudaError_t ce_ = (call);                                        \
-        if (ce_ != cudaSuccess) return fail(P2S_ERR_CUDA, #call, ce_);   \
+#define P2S_CUDA(call)                                                 \
+    do {                                                               \
+        cudaError_t ce_ = (call);                                      \
+        if (ce_ != cudaSuccess) return fail(P2S_ERR_CUDA, #call, ce_); \
     } while (0)
+
+namespace {
 
 int set_device(int dev) {
     cudaError_t e = cudaSetDevice(dev);
@@ -81,9 +61,10 @@ int set_device(int dev) {
 }
 
 int check_orders(int64_t E, const p2s_orders* o) {
-    if (E < 0 || !o || (o->n_comp != 1 && o->n_comp != 3) || (E > 0 && !o->orders)) return P2S_ERR_ARG;
+    if (E < 0 || !o || (o->n_comp != 1 && o->n_comp != 3) || (E > 0 && !o->orders))
+        return fail(P2S_ERR_ARG, "orders: bad count, component number or NULL array");
     for (int64_t i = 0; i < E * 3 * o->n_comp; ++i)
-        if (o->orders[i] < 1 || o->orders[i] > kMaxOrder) return P2S_ERR_ORDER;
+        if (o->orders[i] < 1 || o->orders[i] > kMaxOrder) return fail(P2S_ERR_ORDER, "orders: value outside 1..12");
     return P2S_OK;
 }
 
@@ -115,7 +96,6 @@ int64_t elem_moments(const int32_t* ord, int nc) {
     return m;
 }
 
-
 // Contraction work list of one element.  Symmetry of the coupling factor
 // (alpha_{gi gj} = alpha_{gj gi}) and of the Eq. (3) coefficients gives
 //   vv(gj,gi) = vv(gi,gj)^T,  dd(gj,gi) = dd(gi,gj)^T,  vd(gj,gi) = dv(gi,gj)^T,
@@ -142,7 +122,7 @@ void slab_sizes(const ElemDesc& d, int gi, int gj, int& m1n, int& n1n) {
             ++m1n;
 }
 
-void push_block(const ElemDesc& d, int32_t e, int gi, int gj, int t, int tp, std::vector<ContractUnit>& units) {
+void push_block(const ElemDesc& d, int32_t e, int gi, int gj, int t, int tp, UnitSink& units) {
     int m1n, n1n;
     slab_sizes(d, gi, gj, m1n, n1n);
     const int Nu = d.ord[gi][0], Nv = d.ord[gi][1];
@@ -159,11 +139,11 @@ void push_block(const ElemDesc& d, int32_t e, int gi, int gj, int t, int tp, std
             u.n1a = (int8_t)n1a;
             u.n1n = (int8_t)std::min(n1n, Nv - n1a);
             u.pad = 0;
-            units.push_back(u);
+            units.push(u);
         }
 }
 
-void add_units(const ElemDesc& d, uint32_t mask, int32_t e, std::vector<ContractUnit>& units) {
+void add_units(const ElemDesc& d, uint32_t mask, int32_t e, UnitSink& units) {
     const int nc = d.n_comp;
     for (int t : {0, 3}) {  // vv, dd: upper blocks, transposed into the lower ones
         if (!(mask & (1u << t))) continue;
@@ -179,6 +159,168 @@ void add_units(const ElemDesc& d, uint32_t mask, int32_t e, std::vector<Contract
 }
 
 }  // namespace
+
+namespace p2s {
+
+int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, const p2s_quadrature* quad,
+                 const p2s_fill_opts* opts, ElemDesc* desc, UnitSink& units, PlanLayout& L) {
+    if (!quad || !opts) return fail(P2S_ERR_ARG, "plan: NULL quadrature or options");
+    int rc = check_orders(E, orders);
+    if (rc) return rc;
+    if ((opts->types_mask & 0xFu) == 0 || (opts->types_mask & ~0xFu)) return fail(P2S_ERR_ARG, "plan: bad types_mask");
+    if (opts->precision != P2S_FP64 && opts->precision != P2S_MIXED) return fail(P2S_ERR_ARG, "plan: bad precision");
+    if (quad->npts_uniform < 0 || quad->npts_uniform > kMaxG) return fail(P2S_ERR_ORDER, "plan: npts outside 1..64");
+    if (quad->npts_uniform == 0 && E > 0 && !quad->npts) return fail(P2S_ERR_ARG, "plan: NULL npts array");
+
+    const int nc = orders->n_comp;
+    L = PlanLayout();
+    L.n_elem = E;
+    L.n_comp = nc;
+    L.types_mask = opts->types_mask;
+    L.precision = opts->precision;
+    L.n_pairs = nc == 1 ? 1 : 6;
+    const int nt = ntypes(opts->types_mask);
+    int64_t out_off = 0, mom_off = 0;
+    int max_pair = 1, max_elem_mom = 1;
+    for (int64_t e = 0; e < E; ++e) {
+        const int32_t* ord = orders->orders + 3 * nc * e;
+        ElemDesc& d = desc[e];
+        std::memset(&d, 0, sizeof(d));
+        int G = quad->npts_uniform ? quad->npts_uniform : quad->npts[e];
+        if (G < 1 || G > kMaxG) return fail(P2S_ERR_ORDER, "plan: npts outside 1..64");
+        d.G = (int16_t)G;
+        d.n_comp = (int8_t)nc;
+        d.n_types = (int8_t)nt;
+        int dof = 0;
+        for (int g = 0; g < nc; ++g) {
+            d.dof_off[g] = dof;
+            for (int ax = 0; ax < 3; ++ax) d.ord[g][ax] = (int8_t)ord[3 * g + ax];
+            dof += ord[3 * g] * ord[3 * g + 1] * ord[3 * g + 2];
+        }
+        d.n = dof;
+        for (int ax = 0; ax < 3; ++ax) {
+            int mx = 0;
+            for (int g = 0; g < nc; ++g) mx = std::max(mx, (int)ord[3 * g + ax]);
+            d.kax[ax] = (int8_t)(2 * mx - 1);
+            L.kb = std::max(L.kb, 2 * mx - 1);
+        }
+        int po = 0;
+        for (int s = 0; s < L.n_pairs; ++s) {
+            int gi, gj;
+            pair_of(s, nc, gi, gj);
+            d.pair_off[s] = po;
+            int v = 1;
+            for (int ax = 0; ax < 3; ++ax) v *= ord[3 * gi + ax] + ord[3 * gj + ax] - 1;
+            po += v;
+        }
+        d.out_off = out_off;
+        d.mom_off = mom_off;
+        out_off += (int64_t)nt * dof * dof;
+        mom_off += po;
+        max_pair = std::max(max_pair, d.kax[0] * d.kax[1] * d.kax[2]);
+        max_elem_mom = std::max(max_elem_mom, L.n_pairs * d.kax[0] * d.kax[1] * d.kax[2]);
+        L.gmax = std::max(L.gmax, G);
+        add_units(d, opts->types_mask, (int32_t)e, units);
+    }
+    L.out_entries = out_off;
+    L.mom_entries = mom_off;
+    L.n_units = units.n;
+
+    // moments launch shape: the accumulator takes what shared memory leaves, at least one pair
+    size_t base = moments_smem_bytes(L.n_pairs, L.kb, L.gmax, 0);
+    size_t limit = std::min<size_t>(T.smem_optin, 227 * 1024) - 1024;  // room for static shared memory
+    if (base + sizeof(double) * max_pair > limit) return fail(P2S_ERR_ORDER, "plan: moment accumulator too large");
+    L.iacc_cap = (int)std::min<size_t>((limit - base) / sizeof(double), (size_t)max_elem_mom);
+    size_t half = limit / 2 - 1024;  // two CTAs per SM when everything fits in half
+    if (base + sizeof(double) * max_elem_mom <= half) L.iacc_cap = max_elem_mom;
+    L.mom_smem = moments_smem_bytes(L.n_pairs, L.kb, L.gmax, L.iacc_cap);
+    int per_sm = moments_blocks_per_sm(L.mom_smem);
+    if (per_sm < 1) return fail(P2S_ERR_ORDER, "plan: moment kernel does not fit");
+    L.mom_grid = (int)std::max<int64_t>(1, std::min<int64_t>(E, (int64_t)T.sm_count * per_sm));
+
+    // contraction launch shape: buffers sized for the largest unit, one thread per
+    // stage-3 combination of the largest unit (rounded to whole warps)
+    int max_combos = 1;
+    for (int64_t e = 0; e < E; ++e) {
+        const ElemDesc& d = desc[e];
+        for (int gi = 0; gi < nc; ++gi)
+            for (int gj = 0; gj < nc; ++gj) {
+                int m1n, n1n;
+                slab_sizes(d, gi, gj, m1n, n1n);
+                ContractShape sh = contract_shape(d.ord[gi], d.ord[gj], m1n, n1n);
+                L.a_cap = std::max(L.a_cap, sh.a);
+                L.b_cap = std::max(L.b_cap, sh.b);
+                L.tile_cap = std::max(L.tile_cap, sh.tile);
+                max_combos = std::max(max_combos, sh.combos);
+            }
+    }
+    L.con_threads = std::min(512, std::max(64, (max_combos + 31) / 32 * 32));
+    L.tile_off = contract_tile_offset(L.precision, L.a_cap, L.b_cap);
+    L.con_smem = contract_smem_bytes(L.precision, L.a_cap, L.b_cap, L.tile_cap);
+    if (L.con_smem > limit) return fail(P2S_ERR_ORDER, "plan: contraction tile too large");
+    int con_per_sm = contract_blocks_per_sm(L.precision, L.con_threads, L.con_smem);
+    if (con_per_sm < 1) return fail(P2S_ERR_ORDER, "plan: contraction kernel does not fit");
+    L.con_grid = T.sm_count * con_per_sm;
+    return P2S_OK;
+}
+
+int run_moments(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_desc, const p2s_geometry* geom,
+                const p2s_material* mat, void* moments, int32_t* elem_status, cudaStream_t s) {
+    if (!geom || !mat) return fail(P2S_ERR_ARG, "moments: NULL geometry or material");
+    if (geom->n_elem != PL.n_elem) return fail(P2S_ERR_ARG, "moments: n_elem differs from the plan");
+    if (PL.n_elem == 0) return P2S_OK;
+    if (!moments || !mat->params) return fail(P2S_ERR_ARG, "moments: NULL moments or params");
+    if (mat->kind == P2S_ALPHA_SCALAR) {
+        if (PL.n_comp != 1) return fail(P2S_ERR_ARG, "moments: scalar coupling needs one component");
+    } else if (mat->kind == P2S_ALPHA_METRIC_EPS) {
+        if (PL.n_comp != 3 || !geom->nodes) return fail(P2S_ERR_ARG, "moments: metric coupling needs 3 components and nodes");
+    } else {
+        return fail(P2S_ERR_ARG, "moments: unknown coupling kind");
+    }
+    MomentLaunch M;
+    M.desc = d_desc;
+    M.n_elem = PL.n_elem;
+    M.kind = mat->kind;
+    M.params = mat->params;
+    M.nodes = geom->nodes;
+    M.bulge = geom->bulge;
+    M.gl_x = T.gl_x;
+    M.gl_w = T.gl_w;
+    M.mom = reinterpret_cast<double*>(moments);
+    M.elem_status = elem_status;
+    M.err_flag = T.err;
+    M.n_pairs = PL.n_pairs;
+    M.kb = PL.kb;
+    M.gmax = PL.gmax;
+    M.iacc_cap = PL.iacc_cap;
+    M.out_ff = PL.precision == P2S_MIXED;
+    P2S_CUDA(launch_moments_fp64(M, PL.mom_grid, PL.mom_smem, s));
+    return P2S_OK;
+}
+
+int run_contract(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_desc, const ContractUnit* d_units,
+                 unsigned long long* d_counter, const void* moments, double* out, cudaStream_t s) {
+    if (PL.n_units == 0) return P2S_OK;
+    if (!moments || !out) return fail(P2S_ERR_ARG, "contract: NULL moments or out");
+    P2S_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), s));
+    ContractLaunch C;
+    C.desc = d_desc;
+    C.units = d_units;
+    C.n_units = PL.n_units;
+    C.mom = moments;
+    C.lin_idx = T.lin_idx;
+    C.lin_coef = PL.precision == P2S_MIXED ? (const void*)T.lin_coef_ff : (const void*)T.lin_coef;
+    C.out = out;
+    C.counter = d_counter;
+    C.types_mask = PL.types_mask;
+    C.a_cap = (int)PL.a_cap;
+    C.b_cap = (int)PL.b_cap;
+    C.tile_off = (int)PL.tile_off;
+    P2S_CUDA(launch_contract(PL.precision, C, PL.con_grid, PL.con_threads, PL.con_smem, s));
+    return P2S_OK;
+}
+
+}  // namespace p2s
 
 extern "C" {
 
@@ -199,7 +341,7 @@ const char* p2s_error_string(int code) {
 }
 
 int p2s_gauss_legendre(int G, double* x, double* w) {
-    if (G < 1 || G > kMaxG || !x || !w) return P2S_ERR_ARG;
+    if (G < 1 || G > kMaxG || !x || !w) return fail(P2S_ERR_ARG, "p2s_gauss_legendre: bad G or NULL");
     const HostTables& T = host_tables();
     std::memcpy(x, T.gl_x[G], sizeof(double) * G);
     std::memcpy(w, T.gl_w[G], sizeof(double) * G);
@@ -208,7 +350,7 @@ int p2s_gauss_legendre(int G, double* x, double* w) {
 
 int p2s_linearisation(int t, int m1, int m2, int kmax, double* C) {
     if (t < 0 || t > 3 || m1 < 0 || m2 < 0 || m1 >= kMaxOrder || m2 >= kMaxOrder || kmax < 0 || !C)
-        return P2S_ERR_ARG;
+        return fail(P2S_ERR_ARG, "p2s_linearisation: bad type, index or NULL");
     const HostTables& T = host_tables();
     for (int k = 0; k <= kmax; ++k) C[k] = 0.0;
     int32_t li = T.lin_idx[lin_slot(t, m1, m2)];
@@ -220,25 +362,26 @@ int p2s_linearisation(int t, int m1, int m2, int kmax, double* C) {
 }
 
 static int ctx_init(p2s_ctx* c, int device) {
-    c->device = device;
+    DeviceTables& D = c->T;
+    D.device = device;
     cudaDeviceProp prop;
     P2S_CUDA(cudaGetDeviceProperties(&prop, device));
-    c->sm_count = prop.multiProcessorCount;
-    c->smem_optin = prop.sharedMemPerBlockOptin;
+    D.sm_count = prop.multiProcessorCount;
+    D.smem_optin = prop.sharedMemPerBlockOptin;
     const HostTables& T = host_tables();
     size_t glb = sizeof(double) * (kMaxG + 1) * kMaxG;
-    P2S_CUDA(cudaMalloc(&c->d_gl_x, glb));
-    P2S_CUDA(cudaMalloc(&c->d_gl_w, glb));
-    P2S_CUDA(cudaMalloc(&c->d_lin_idx, sizeof(T.lin_idx)));
-    P2S_CUDA(cudaMalloc(&c->d_lin_coef, sizeof(double) * std::max(1, T.n_coef)));
-    P2S_CUDA(cudaMalloc(&c->d_lin_coef_ff, sizeof(float2) * std::max(1, T.n_coef)));
-    P2S_CUDA(cudaMalloc(&c->d_err, sizeof(int)));
-    P2S_CUDA(cudaMemcpy(c->d_gl_x, T.gl_x, glb, cudaMemcpyHostToDevice));
-    P2S_CUDA(cudaMemcpy(c->d_gl_w, T.gl_w, glb, cudaMemcpyHostToDevice));
-    P2S_CUDA(cudaMemcpy(c->d_lin_idx, T.lin_idx, sizeof(T.lin_idx), cudaMemcpyHostToDevice));
-    P2S_CUDA(cudaMemcpy(c->d_lin_coef, T.lin_coef, sizeof(double) * T.n_coef, cudaMemcpyHostToDevice));
-    P2S_CUDA(cudaMemcpy(c->d_lin_coef_ff, T.lin_coef_ff, sizeof(float2) * T.n_coef, cudaMemcpyHostToDevice));
-    P2S_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
+    P2S_CUDA(cudaMalloc(&D.gl_x, glb));
+    P2S_CUDA(cudaMalloc(&D.gl_w, glb));
+    P2S_CUDA(cudaMalloc(&D.lin_idx, sizeof(T.lin_idx)));
+    P2S_CUDA(cudaMalloc(&D.lin_coef, sizeof(double) * std::max(1, T.n_coef)));
+    P2S_CUDA(cudaMalloc(&D.lin_coef_ff, sizeof(float2) * std::max(1, T.n_coef)));
+    P2S_CUDA(cudaMalloc(&D.err, sizeof(int)));
+    P2S_CUDA(cudaMemcpy(D.gl_x, T.gl_x, glb, cudaMemcpyHostToDevice));
+    P2S_CUDA(cudaMemcpy(D.gl_w, T.gl_w, glb, cudaMemcpyHostToDevice));
+    P2S_CUDA(cudaMemcpy(D.lin_idx, T.lin_idx, sizeof(T.lin_idx), cudaMemcpyHostToDevice));
+    P2S_CUDA(cudaMemcpy(D.lin_coef, T.lin_coef, sizeof(double) * T.n_coef, cudaMemcpyHostToDevice));
+    P2S_CUDA(cudaMemcpy(D.lin_coef_ff, T.lin_coef_ff, sizeof(float2) * T.n_coef, cudaMemcpyHostToDevice));
+    P2S_CUDA(cudaMemset(D.err, 0, sizeof(int)));
     P2S_CUDA(init_kernel_attributes());
     return P2S_OK;
 }
@@ -264,21 +407,21 @@ int p2s_create(p2s_ctx** out, int device) {
 
 void p2s_destroy(p2s_ctx* c) {
     if (!c) return;
-    cudaSetDevice(c->device);
+    cudaSetDevice(c->T.device);
     cudaDeviceSynchronize();
-    cudaFree(c->d_gl_x);
-    cudaFree(c->d_gl_w);
-    cudaFree(c->d_lin_idx);
-    cudaFree(c->d_lin_coef);
-    cudaFree(c->d_lin_coef_ff);
-    cudaFree(c->d_err);
+    cudaFree(c->T.gl_x);
+    cudaFree(c->T.gl_w);
+    cudaFree(c->T.lin_idx);
+    cudaFree(c->T.lin_coef);
+    cudaFree(c->T.lin_coef_ff);
+    cudaFree(c->T.err);
     delete c;
 }
 
 int64_t p2s_output_entries(int64_t n_elem, const p2s_orders* orders, uint32_t types_mask, int64_t* offsets) {
     int rc = check_orders(n_elem, orders);
     if (rc) return rc;
-    if ((types_mask & 0xFu) == 0 || (types_mask & ~0xFu)) return P2S_ERR_ARG;
+    if ((types_mask & 0xFu) == 0 || (types_mask & ~0xFu)) return fail(P2S_ERR_ARG, "p2s_output_entries: bad types_mask");
     int nt = ntypes(types_mask);
     int64_t off = 0;
     for (int64_t e = 0; e < n_elem; ++e) {
@@ -304,7 +447,7 @@ int64_t p2s_moment_entries(int64_t n_elem, const p2s_orders* orders, int64_t* of
 
 void p2s_plan_destroy(p2s_plan* p) {
     if (!p) return;
-    if (p->ctx) cudaSetDevice(p->ctx->device);
+    if (p->ctx) cudaSetDevice(p->ctx->T.device);
     cudaFree(p->d_desc);
     cudaFree(p->d_units);
     cudaFree(p->d_counter);
@@ -314,187 +457,61 @@ void p2s_plan_destroy(p2s_plan* p) {
 
 int p2s_plan_create(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, const p2s_quadrature* quad,
                     const p2s_fill_opts* opts, p2s_plan** out) {
-    if (!ctx || !out || !quad || !opts) return P2S_ERR_ARG;
+    if (!ctx || !out) return fail(P2S_ERR_ARG, "p2s_plan_create: NULL context or out");
     *out = nullptr;
-    int rc = check_orders(E, orders);
-    if (rc) return rc;
-    if ((opts->types_mask & 0xFu) == 0 || (opts->types_mask & ~0xFu)) return P2S_ERR_ARG;
-    if (opts->precision != P2S_FP64 && opts->precision != P2S_MIXED) return P2S_ERR_ARG;
-    if (quad->npts_uniform < 0 || quad->npts_uniform > kMaxG) return P2S_ERR_ORDER;
-    if (quad->npts_uniform == 0 && E > 0 && !quad->npts) return P2S_ERR_ARG;
-    if (set_device(ctx->device)) return P2S_ERR_CUDA;
-
-    const int nc = orders->n_comp;
+    if (E < 0) return fail(P2S_ERR_ARG, "p2s_plan_create: negative n_elem");
+    if (set_device(ctx->T.device)) return P2S_ERR_CUDA;
     std::vector<ElemDesc> desc((size_t)std::max<int64_t>(E, 1));
     std::vector<ContractUnit> units;
+    UnitSink sink;
+    sink.vec = &units;
     p2s_plan* p = new (std::nothrow) p2s_plan();
-    if (!p) return P2S_ERR_OOM;
+    if (!p) return fail(P2S_ERR_OOM, "p2s_plan_create: host allocation");
     p->ctx = ctx;
-    p->n_elem = E;
-    p->n_comp = nc;
-    p->types_mask = opts->types_mask;
-    p->precision = opts->precision;
-    p->n_pairs = nc == 1 ? 1 : 6;
-    const int nt = ntypes(opts->types_mask);
-    int64_t out_off = 0, mom_off = 0;
-    int max_pair = 1, max_elem_mom = 1;
-    for (int64_t e = 0; e < E; ++e) {
-        const int32_t* ord = orders->orders + 3 * nc * e;
-        ElemDesc& d = desc[e];
-        std::memset(&d, 0, sizeof(d));
-        int G = quad->npts_uniform ? quad->npts_uniform : quad->npts[e];
-        if (G < 1 || G > kMaxG) { delete p; return P2S_ERR_ORDER; }
-        d.G = (int16_t)G;
-        d.n_comp = (int8_t)nc;
-        d.n_types = (int8_t)nt;
-        int dof = 0;
-        for (int g = 0; g < nc; ++g) {
-            d.dof_off[g] = dof;
-            for (int ax = 0; ax < 3; ++ax) d.ord[g][ax] = (int8_t)ord[3 * g + ax];
-            dof += ord[3 * g] * ord[3 * g + 1] * ord[3 * g + 2];
-        }
-        d.n = dof;
-        for (int ax = 0; ax < 3; ++ax) {
-            int mx = 0;
-            for (int g = 0; g < nc; ++g) mx = std::max(mx, (int)ord[3 * g + ax]);
-            d.kax[ax] = (int8_t)(2 * mx - 1);
-            p->kb = std::max(p->kb, 2 * mx - 1);
-        }
-        int po = 0;
-        for (int s = 0; s < p->n_pairs; ++s) {
-            int gi, gj;
-            pair_of(s, nc, gi, gj);
-            d.pair_off[s] = po;
-            int v = 1;
-            for (int ax = 0; ax < 3; ++ax) v *= ord[3 * gi + ax] + ord[3 * gj + ax] - 1;
-            po += v;
-        }
-        d.out_off = out_off;
-        d.mom_off = mom_off;
-        out_off += (int64_t)nt * dof * dof;
-        mom_off += po;
-        max_pair = std::max(max_pair, d.kax[0] * d.kax[1] * d.kax[2]);
-        max_elem_mom = std::max(max_elem_mom, p->n_pairs * d.kax[0] * d.kax[1] * d.kax[2]);
-        p->gmax = std::max(p->gmax, G);
-        add_units(d, opts->types_mask, (int32_t)e, units);
+    int rc = build_layout(ctx->T, E, orders, quad, opts, desc.data(), sink, p->L);
+    if (rc) {
+        delete p;
+        return rc;
     }
-    p->out_entries = out_off;
-    p->mom_entries = mom_off;
-    p->n_units = (int64_t)units.size();
-
-    // moments launch shape: the accumulator takes what shared memory leaves, at least one pair
-    size_t base = moments_smem_bytes(p->n_pairs, p->kb, p->gmax, 0);
-    size_t limit = std::min<size_t>(ctx->smem_optin, 227 * 1024) - 1024;  // room for static shared memory
-    if (base + sizeof(double) * max_pair > limit) { delete p; return P2S_ERR_ORDER; }
-    p->iacc_cap = (int)std::min<size_t>((limit - base) / sizeof(double), (size_t)max_elem_mom);
-    // prefer two CTAs per SM when everything fits in half the shared memory
-    size_t half = limit / 2 - 1024;
-    if (base + sizeof(double) * max_elem_mom <= half) p->iacc_cap = max_elem_mom;
-    p->mom_smem = moments_smem_bytes(p->n_pairs, p->kb, p->gmax, p->iacc_cap);
-    int per_sm = moments_blocks_per_sm(p->mom_smem);
-    if (per_sm < 1) { delete p; return fail(P2S_ERR_ORDER, "p2s_plan_create: moment kernel does not fit"); }
-    p->mom_grid = (int)std::max<int64_t>(1, std::min<int64_t>(E, (int64_t)ctx->sm_count * per_sm));
-
-    // contraction launch shape: buffers sized for the largest unit, one thread per
-    // stage-3 combination of the largest unit (rounded to whole warps)
-    int max_combos = 1;
-    for (const ContractUnit& u : units) {
-        const ElemDesc& d = desc[u.e];
-        ContractShape sh = contract_shape(d.ord[u.gi], d.ord[u.gj], u.m1n, u.n1n);
-        p->a_cap = std::max(p->a_cap, sh.a);
-        p->b_cap = std::max(p->b_cap, sh.b);
-        p->tile_cap = std::max(p->tile_cap, sh.tile);
-        max_combos = std::max(max_combos, sh.combos);
-    }
-    p->con_threads = std::min(512, std::max(64, (max_combos + 31) / 32 * 32));
-    p->tile_off = contract_tile_offset(p->precision, p->a_cap, p->b_cap);
-    p->con_smem = contract_smem_bytes(p->precision, p->a_cap, p->b_cap, p->tile_cap);
-    if (p->con_smem > limit) { delete p; return fail(P2S_ERR_ORDER, "p2s_plan_create: contraction tile too large"); }
-    int con_per_sm = contract_blocks_per_sm(p->precision, p->con_threads, p->con_smem);
-    if (con_per_sm < 1) { delete p; return fail(P2S_ERR_ORDER, "p2s_plan_create: contraction kernel does not fit"); }
-    p->con_grid = ctx->sm_count * con_per_sm;
-
     bool ok = cudaMalloc(&p->d_desc, sizeof(ElemDesc) * desc.size()) == cudaSuccess &&
               cudaMalloc(&p->d_units, sizeof(ContractUnit) * std::max<size_t>(1, units.size())) == cudaSuccess &&
               cudaMalloc(&p->d_counter, sizeof(unsigned long long)) == cudaSuccess &&
-              cudaMalloc(&p->d_mom, sizeof(double) * std::max<int64_t>(1, p->mom_entries)) == cudaSuccess;
-    if (!ok) { p2s_plan_destroy(p); return P2S_ERR_OOM; }
-    if (cudaMemcpy(p->d_desc, desc.data(), sizeof(ElemDesc) * desc.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        (units.size() && cudaMemcpy(p->d_units, units.data(), sizeof(ContractUnit) * units.size(),
-                                    cudaMemcpyHostToDevice) != cudaSuccess)) {
+              cudaMalloc(&p->d_mom, sizeof(double) * std::max<int64_t>(1, p->L.mom_entries)) == cudaSuccess;
+    if (!ok) {
         p2s_plan_destroy(p);
-        return P2S_ERR_CUDA;
+        return fail(P2S_ERR_OOM, "p2s_plan_create: device allocation");
+    }
+    cudaError_t ce = cudaMemcpy(p->d_desc, desc.data(), sizeof(ElemDesc) * desc.size(), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess && units.size())
+        ce = cudaMemcpy(p->d_units, units.data(), sizeof(ContractUnit) * units.size(), cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) {
+        p2s_plan_destroy(p);
+        return fail(P2S_ERR_CUDA, "p2s_plan_create: upload", ce);
     }
     *out = p;
     return P2S_OK;
 }
 
-int64_t p2s_plan_output_entries(const p2s_plan* p) { return p ? p->out_entries : P2S_ERR_ARG; }
-int64_t p2s_plan_moment_entries(const p2s_plan* p) { return p ? p->mom_entries : P2S_ERR_ARG; }
+int64_t p2s_plan_output_entries(const p2s_plan* p) { return p ? p->L.out_entries : P2S_ERR_ARG; }
+int64_t p2s_plan_moment_entries(const p2s_plan* p) { return p ? p->L.mom_entries : P2S_ERR_ARG; }
 
 int p2s_plan_moments(p2s_plan* p, const p2s_geometry* geom, const p2s_material* mat, double* moments,
                      int32_t* elem_status, void* stream) {
-    if (!p || !geom || !mat) return fail(P2S_ERR_ARG, "p2s_plan_moments: NULL plan, geometry or material");
-    if (geom->n_elem != p->n_elem) return fail(P2S_ERR_ARG, "p2s_plan_moments: n_elem differs from the plan");
-    if (p->n_elem == 0) return P2S_OK;
-    if (!moments || !mat->params) return fail(P2S_ERR_ARG, "p2s_plan_moments: NULL moments or params");
-    if (mat->kind == P2S_ALPHA_SCALAR) {
-        if (p->n_comp != 1) return P2S_ERR_ARG;
-    } else if (mat->kind == P2S_ALPHA_METRIC_EPS) {
-        if (p->n_comp != 3 || !geom->nodes) return P2S_ERR_ARG;
-    } else {
-        return P2S_ERR_ARG;
-    }
-    if (set_device(p->ctx->device)) return P2S_ERR_CUDA;
-    MomentLaunch L;
-    L.desc = p->d_desc;
-    L.n_elem = p->n_elem;
-    L.kind = mat->kind;
-    L.params = mat->params;
-    L.nodes = geom->nodes;
-    L.bulge = geom->bulge;
-    L.gl_x = p->ctx->d_gl_x;
-    L.gl_w = p->ctx->d_gl_w;
-    L.mom = moments;
-    L.elem_status = elem_status;
-    L.err_flag = p->ctx->d_err;
-    L.n_pairs = p->n_pairs;
-    L.kb = p->kb;
-    L.gmax = p->gmax;
-    L.iacc_cap = p->iacc_cap;
-    L.out_ff = p->precision == P2S_MIXED;
-    P2S_CUDA(launch_moments_fp64(L, p->mom_grid, p->mom_smem, (cudaStream_t)stream));
-    return P2S_OK;
+    if (!p) return fail(P2S_ERR_ARG, "p2s_plan_moments: NULL plan");
+    if (set_device(p->ctx->T.device)) return P2S_ERR_CUDA;
+    return run_moments(p->ctx->T, p->L, p->d_desc, geom, mat, moments, elem_status, (cudaStream_t)stream);
 }
 
 int p2s_plan_contract(p2s_plan* p, const double* moments, double* out, void* stream) {
     if (!p) return fail(P2S_ERR_ARG, "p2s_plan_contract: NULL plan");
-    if (p->n_units == 0) return P2S_OK;
-    if (!moments || !out) return fail(P2S_ERR_ARG, "p2s_plan_contract: NULL moments or out");
-    if (set_device(p->ctx->device)) return P2S_ERR_CUDA;
-    cudaStream_t s = (cudaStream_t)stream;
-    P2S_CUDA(cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned long long), s));
-    ContractLaunch L;
-    L.desc = p->d_desc;
-    L.units = p->d_units;
-    L.n_units = p->n_units;
-    L.mom = moments;
-    L.lin_idx = p->ctx->d_lin_idx;
-    L.lin_coef = p->precision == P2S_MIXED ? (const void*)p->ctx->d_lin_coef_ff : (const void*)p->ctx->d_lin_coef;
-    L.out = out;
-    L.counter = p->d_counter;
-    L.types_mask = p->types_mask;
-    L.a_cap = (int)p->a_cap;
-    L.b_cap = (int)p->b_cap;
-    L.tile_off = (int)p->tile_off;
-    P2S_CUDA(launch_contract(p->precision, L, p->con_grid, p->con_threads, p->con_smem, s));
-    return P2S_OK;
+    if (set_device(p->ctx->T.device)) return P2S_ERR_CUDA;
+    return run_contract(p->ctx->T, p->L, p->d_desc, p->d_units, p->d_counter, moments, out, (cudaStream_t)stream);
 }
 
 int p2s_plan_fill(p2s_plan* p, const p2s_geometry* geom, const p2s_material* mat, double* out,
                   int32_t* elem_status, void* stream) {
     if (!p) return fail(P2S_ERR_ARG, "p2s_plan_fill: NULL plan");
-    if (!out && p->n_units) return fail(P2S_ERR_ARG, "p2s_plan_fill: NULL out");
+    if (!out && p->L.n_units) return fail(P2S_ERR_ARG, "p2s_plan_fill: NULL out");
     int rc = p2s_plan_moments(p, geom, mat, p->d_mom, elem_status, stream);
     if (rc) return rc;
     return p2s_plan_contract(p, p->d_mom, out, stream);
@@ -503,24 +520,31 @@ int p2s_plan_fill(p2s_plan* p, const p2s_geometry* geom, const p2s_material* mat
 int p2s_fill_elements(p2s_ctx* ctx, const p2s_geometry* geom, const p2s_material* mat, const p2s_orders* orders,
                       const p2s_quadrature* quad, const p2s_fill_opts* opts, double* out, int32_t* elem_status,
                       void* stream) {
-    if (!geom) return P2S_ERR_ARG;
+    if (!geom) return fail(P2S_ERR_ARG, "p2s_fill_elements: NULL geometry");
     p2s_plan* p = nullptr;
     int rc = p2s_plan_create(ctx, geom->n_elem, orders, quad, opts, &p);
     if (rc) return rc;
     rc = p2s_plan_fill(p, geom, mat, out, elem_status, stream);
-    if (rc == P2S_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) rc = P2S_ERR_CUDA;
+    if (rc == P2S_OK) {
+        cudaError_t ce = cudaStreamSynchronize((cudaStream_t)stream);
+        if (ce != cudaSuccess) rc = fail(P2S_ERR_CUDA, "p2s_fill_elements: stream", ce);
+    }
     p2s_plan_destroy(p);
     return rc;
 }
 
 int p2s_sync_status(p2s_ctx* ctx, void* stream) {
-    if (!ctx) return P2S_ERR_ARG;
-    if (set_device(ctx->device)) return P2S_ERR_CUDA;
+    if (!ctx) return fail(P2S_ERR_ARG, "p2s_sync_status: NULL context");
+    if (set_device(ctx->T.device)) return P2S_ERR_CUDA;
     P2S_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     int h = 0;
-    P2S_CUDA(cudaMemcpy(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (h != 0) P2S_CUDA(cudaMemset(ctx->d_err, 0, sizeof(int)));
+    P2S_CUDA(cudaMemcpy(&h, ctx->T.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h != 0) P2S_CUDA(cudaMemset(ctx->T.err, 0, sizeof(int)));
     return h;
 }
 
 }  // extern "C"
+
+namespace p2s {
+const DeviceTables* context_tables(const p2s_ctx* c) { return c ? &c->T : nullptr; }
+}  // namespace p2s

@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -113,5 +114,65 @@ int contract_blocks_per_sm(int precision, int threads, size_t smem);
 int moments_threads();
 int moments_blocks_per_sm(size_t smem);
 cudaError_t init_kernel_attributes();
+
+// ------------------------------------------------------------------ plan building (api.cu)
+// Device-resident tables of a context and the device facts the launch shapes need.
+struct DeviceTables {
+    int device = 0;
+    int sm_count = 0;
+    size_t smem_optin = 0;
+    double* gl_x = nullptr;
+    double* gl_w = nullptr;
+    int32_t* lin_idx = nullptr;
+    double* lin_coef = nullptr;
+    float2* lin_coef_ff = nullptr;
+    int* err = nullptr;
+};
+
+// Everything a fill needs besides device buffers: sizes and launch shapes.
+struct PlanLayout {
+    int64_t n_elem = 0;
+    int n_comp = 0;
+    uint32_t types_mask = 0;
+    int precision = 0;
+    int64_t out_entries = 0, mom_entries = 0, n_units = 0;
+    int n_pairs = 1, kb = 1, gmax = 1, iacc_cap = 0;
+    size_t mom_smem = 0;
+    int mom_grid = 1;
+    size_t a_cap = 1, b_cap = 1, tile_cap = 1;
+    int con_threads = 256;
+    size_t con_smem = 0, tile_off = 0;
+    int con_grid = 1;
+};
+
+// Destination of the contraction work list: a growing vector, or a fixed array that
+// reports overflow instead of growing.
+struct UnitSink {
+    std::vector<ContractUnit>* vec = nullptr;
+    ContractUnit* buf = nullptr;
+    int64_t cap = 0;
+    int64_t n = 0;
+    void push(const ContractUnit& u) {
+        if (vec) vec->push_back(u);
+        else if (buf && n < cap) buf[n] = u;
+        ++n;
+    }
+    bool overflow() const { return buf && n > cap; }
+};
+
+// Record a failure for p2s_last_error and return `code`.
+int fail(int code, const char* where, cudaError_t ce = cudaSuccess);
+// Validate the arguments and fill desc[0..E) (host), the work list and the layout.
+// The first call with units.buf == nullptr && units.vec == nullptr only counts units.
+int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, const p2s_quadrature* quad,
+                 const p2s_fill_opts* opts, ElemDesc* desc, UnitSink& units, PlanLayout& L);
+int run_moments(const DeviceTables& T, const PlanLayout& L, const ElemDesc* d_desc, const p2s_geometry* geom,
+                const p2s_material* mat, void* moments, int32_t* elem_status, cudaStream_t s);
+int run_contract(const DeviceTables& T, const PlanLayout& L, const ElemDesc* d_desc, const ContractUnit* d_units,
+                 unsigned long long* d_counter, const void* moments, double* out, cudaStream_t s);
+}  // namespace p2s
+struct p2s_ctx;
+namespace p2s {
+const DeviceTables* context_tables(const p2s_ctx* c);
 
 }  // namespace p2s
