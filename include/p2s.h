@@ -161,6 +161,35 @@ int p2s_fill_elements(p2s_ctx* ctx, const p2s_geometry* geom, const p2s_material
                       const p2s_fill_opts* opts, double* out, int32_t* elem_status,
                       void* stream);
 
+/* Fill without allocating.  The paper has no counterpart to this entry point: it
+ * computes exactly what p2s_fill_elements computes, and only moves the fill's scratch
+ * (moments, element descriptors, work list, queue counter) into one fixed array of
+ * 18.3 MiB that the library reserves in device memory on every GPU that loads it, for
+ * the life of the process.  It is meant for callers that must not call cudaMalloc or
+ * cudaFree while they run -- for instance a solver whose own memory pool has taken all
+ * free device memory, a service held to a fixed device-memory budget, or a loop that
+ * cannot pay for the synchronisation an allocation or free may trigger.  Such a caller
+ * creates the context once beforehand (p2s_create allocates its small tables).
+ *   Arguments, layouts and results are those of p2s_fill_elements; `out` (device) and
+ *   `elem_status` (device, optional) are caller-owned.  The call is asynchronous on
+ *   `stream` (it does not synchronise, unlike p2s_fill_elements).
+ *   Limits per call: at most 2048 elements, 2,097,152 moment entries and 131,072
+ *   contraction work units; larger requests return P2S_ERR_BUFFER with a message in
+ *   p2s_last_error and launch nothing -- split the batch.  (Three-component N = 6
+ *   elements fit 262 per call, N = 4 elements 1019.)
+ *   Set-up: the first call on each device looks up the array's device address with that
+ *   device current; make that first call before any stream capture.
+ *   Sharing: every call uses the same array, which keeps the previous call's contents
+ *   (each call rewrites what it reads, and clears its counter).  Calls whose kernels
+ *   overlap on the GPU -- on different streams or from different threads without
+ *   ordering -- race on the array and give wrong results; order them on one stream.
+ *   It calls no cudaMalloc, cudaFree or other allocating routine.
+ * Errors: as p2s_fill_elements, plus P2S_ERR_BUFFER. */
+int p2s_fill_elements_noalloc(p2s_ctx* ctx, const p2s_geometry* geom, const p2s_material* mat,
+                              const p2s_orders* orders, const p2s_quadrature* quad,
+                              const p2s_fill_opts* opts, double* out, int32_t* elem_status,
+                              void* stream);
+
 /* Wait for `stream`, then return and clear the context's device error flag:
  * P2S_OK, P2S_ERR_JACOBIAN, P2S_ERR_TIMEOUT, or P2S_ERR_CUDA if the stream failed. */
 int p2s_sync_status(p2s_ctx* ctx, void* stream);

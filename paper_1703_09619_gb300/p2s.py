@@ -76,6 +76,9 @@ SIGNATURES = {
     "p2s_fill_elements": (ctypes.c_int, [_P, ctypes.POINTER(Geometry), ctypes.POINTER(Material),
                                          ctypes.POINTER(Orders), ctypes.POINTER(Quadrature),
                                          ctypes.POINTER(FillOpts), _P, _P, _P]),
+    "p2s_fill_elements_noalloc": (ctypes.c_int, [_P, ctypes.POINTER(Geometry), ctypes.POINTER(Material),
+                                                 ctypes.POINTER(Orders), ctypes.POINTER(Quadrature),
+                                                 ctypes.POINTER(FillOpts), _P, _P, _P]),
     "p2s_sync_status": (ctypes.c_int, [_P, _P]),
     "p2s_linearisation": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
     "p2s_gauss_legendre": (ctypes.c_int, [ctypes.c_int, _P, _P]),
@@ -270,6 +273,27 @@ def fill_elements(ctx: Context, orders, npts, kind, params, nodes, bulge, out, e
     _check(lib.p2s_fill_elements(ctx.handle, ctypes.byref(g), ctypes.byref(m), ctypes.byref(o), ctypes.byref(q),
                                  ctypes.byref(opts), _dptr(out), _dptr(elem_status), _stream(stream)),
            "p2s_fill_elements")
+
+
+def fill_elements_noalloc(ctx: Context, orders, npts, kind, params, nodes, bulge, out, elem_status=None,
+                          precision=FP64, types_mask=TYPES_ALL, stream=None):
+    """Fill through p2s_fill_elements_noalloc: the library's fixed device scratch instead of
+    any allocation, for callers that must not allocate device memory.  Asynchronous."""
+    lib = load()
+    o, keep = _orders_struct(orders)
+    E = keep.shape[0]
+    if np.isscalar(npts):
+        q = Quadrature(int(npts), None)
+        npk = None
+    else:
+        npk = np.ascontiguousarray(npts, dtype=np.int32).reshape(E)
+        q = Quadrature(0, ctypes.c_void_p(npk.ctypes.data))
+    g = Geometry(E, _dptr(nodes), _dptr(bulge))
+    m = Material(int(kind), _dptr(params))
+    opts = FillOpts(int(precision), int(types_mask))
+    _check(lib.p2s_fill_elements_noalloc(ctx.handle, ctypes.byref(g), ctypes.byref(m), ctypes.byref(o),
+                                         ctypes.byref(q), ctypes.byref(opts), _dptr(out), _dptr(elem_status),
+                                         _stream(stream)), "p2s_fill_elements_noalloc")
 
 
 def device_inputs(workload, device="cuda"):
