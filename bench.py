@@ -405,10 +405,13 @@ def main():
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--elements", type=int, default=None, help="use only the first E elements")
+    ap.add_argument("--npts", type=int, default=None, help="override the quadrature size G")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     wl = W.make(args.workload, args.elements)
+    if args.npts:
+        wl = wl.with_npts(args.npts)
     if args.impl == "reference":
         run_reference(args, wl)
     else:

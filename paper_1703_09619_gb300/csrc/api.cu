@@ -105,11 +105,16 @@ int64_t elem_moments(const int32_t* ord, int nc) {
 constexpr int kComboTarget = 256;
 constexpr size_t kUnitBytesTarget = 100 * 1024;
 
-void slab_sizes(const ElemDesc& d, int gi, int gj, int& m1n, int& n1n) {
+void slab_sizes(const ElemDesc& d, int gi, int gj, int& m1n, int& n1n, int spec_n) {
     const int8_t* Ni = d.ord[gi];
     const int8_t* Nj = d.ord[gj];
     n1n = Ni[1];
     m1n = 1;
+    if (spec_n) {  // specialised kernel: full n1, one thread per stage-3 combination
+        const int n3 = spec_n * spec_n * spec_n;
+        while (m1n < spec_n && (m1n + 1) * n3 <= kComboTarget) ++m1n;
+        return;
+    }
     auto bytes = [&](int a, int b) {
         ContractShape s = contract_shape(Ni, Nj, a, b);
         return (s.a + s.b + s.tile) * sizeof(double);
@@ -122,9 +127,9 @@ void slab_sizes(const ElemDesc& d, int gi, int gj, int& m1n, int& n1n) {
             ++m1n;
 }
 
-void push_block(const ElemDesc& d, int32_t e, int gi, int gj, int t, int tp, UnitSink& units) {
+void push_block(const ElemDesc& d, int32_t e, int gi, int gj, int t, int tp, UnitSink& units, int spec_n) {
     int m1n, n1n;
-    slab_sizes(d, gi, gj, m1n, n1n);
+    slab_sizes(d, gi, gj, m1n, n1n, spec_n);
     const int Nu = d.ord[gi][0], Nv = d.ord[gi][1];
     for (int m1a = 0; m1a < Nu; m1a += m1n)
         for (int n1a = 0; n1a < Nv; n1a += n1n) {
@@ -143,18 +148,18 @@ void push_block(const ElemDesc& d, int32_t e, int gi, int gj, int t, int tp, Uni
         }
 }
 
-void add_units(const ElemDesc& d, uint32_t mask, int32_t e, UnitSink& units) {
+void add_units(const ElemDesc& d, uint32_t mask, int32_t e, UnitSink& units, int spec_n) {
     const int nc = d.n_comp;
     for (int t : {0, 3}) {  // vv, dd: upper blocks, transposed into the lower ones
         if (!(mask & (1u << t))) continue;
         for (int gi = 0; gi < nc; ++gi)
-            for (int gj = gi; gj < nc; ++gj) push_block(d, e, gi, gj, t, gi == gj ? -1 : t, units);
+            for (int gj = gi; gj < nc; ++gj) push_block(d, e, gi, gj, t, gi == gj ? -1 : t, units, spec_n);
     }
     const bool dv = mask & 2u, vd = mask & 4u;
     if (dv || vd) {  // dv(gi,gj) and its transpose vd(gj,gi)
         const int t = dv ? 1 : 2, tp = (dv && vd) ? 2 : -1;
         for (int gi = 0; gi < nc; ++gi)
-            for (int gj = 0; gj < nc; ++gj) push_block(d, e, gi, gj, t, tp, units);
+            for (int gj = 0; gj < nc; ++gj) push_block(d, e, gi, gj, t, tp, units, spec_n);
     }
 }
 
@@ -182,6 +187,15 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
     const int nt = ntypes(opts->types_mask);
     int64_t out_off = 0, mom_off = 0;
     int max_pair = 1, max_elem_mom = 1;
+    // the specialised mixed kernel (contract_ff.cu): every order of the batch equal to one
+    // N in 2..6 and the compile-time coefficient runs verified against the table
+    int spec_n = 0;
+    if (L.precision == P2S_MIXED && T.spec_ok && E > 0) {
+        const int N = orders->orders[0];
+        bool uniform = N >= 2 && N <= contract_ff_max_order();
+        for (int64_t i = 0; uniform && i < E * 3 * nc; ++i) uniform = orders->orders[i] == N;
+        if (uniform) spec_n = N;
+    }
     for (int64_t e = 0; e < E; ++e) {
         const int32_t* ord = orders->orders + 3 * nc * e;
         ElemDesc& d = desc[e];
@@ -220,7 +234,7 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
         max_pair = std::max(max_pair, d.kax[0] * d.kax[1] * d.kax[2]);
         max_elem_mom = std::max(max_elem_mom, L.n_pairs * d.kax[0] * d.kax[1] * d.kax[2]);
         L.gmax = std::max(L.gmax, G);
-        add_units(d, opts->types_mask, (int32_t)e, units);
+        add_units(d, opts->types_mask, (int32_t)e, units, spec_n);
     }
     L.out_entries = out_off;
     L.mom_entries = mom_off;
@@ -246,7 +260,7 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
         for (int gi = 0; gi < nc; ++gi)
             for (int gj = 0; gj < nc; ++gj) {
                 int m1n, n1n;
-                slab_sizes(d, gi, gj, m1n, n1n);
+                slab_sizes(d, gi, gj, m1n, n1n, 0);
                 ContractShape sh = contract_shape(d.ord[gi], d.ord[gj], m1n, n1n);
                 L.a_cap = std::max(L.a_cap, sh.a);
                 L.b_cap = std::max(L.b_cap, sh.b);
@@ -257,10 +271,32 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
     L.con_threads = std::min(512, std::max(64, (max_combos + 31) / 32 * 32));
     L.tile_off = contract_tile_offset(L.precision, L.a_cap, L.b_cap);
     L.con_smem = contract_smem_bytes(L.precision, L.a_cap, L.b_cap, L.tile_cap);
-    if (L.con_smem > limit) return fail(P2S_ERR_ORDER, "plan: contraction tile too large");
-    int con_per_sm = contract_blocks_per_sm(L.precision, L.con_threads, L.con_smem);
-    if (con_per_sm < 1) return fail(P2S_ERR_ORDER, "plan: contraction kernel does not fit");
-    L.con_grid = T.sm_count * con_per_sm;
+    if (!spec_n) {
+        if (L.con_smem > limit) return fail(P2S_ERR_ORDER, "plan: contraction tile too large");
+        int con_per_sm = contract_blocks_per_sm(L.precision, L.con_threads, L.con_smem);
+        if (con_per_sm < 1) return fail(P2S_ERR_ORDER, "plan: contraction kernel does not fit");
+        L.con_grid = T.sm_count * con_per_sm;
+    }
+
+    if (spec_n) {
+        int m1n, n1n;
+        slab_sizes(desc[0], 0, 0, m1n, n1n, spec_n);
+        size_t a, bcap, tl;
+        int combos;
+        contract_ff_shape(spec_n, m1n, a, bcap, tl, combos);
+        const int threads = std::min(512, std::max(64, (combos + 31) / 32 * 32));
+        const size_t smem = (a + bcap) * sizeof(float2);
+        const int per_sm = smem <= limit ? contract_ffn_blocks_per_sm(spec_n, threads, smem) : 0;
+        if (per_sm < 1) return fail(P2S_ERR_ORDER, "plan: specialised contraction kernel does not fit");
+        L.spec_n = spec_n;
+        L.a_cap = a;
+        L.b_cap = bcap;
+        L.tile_cap = 0;
+        L.tile_off = smem;
+        L.con_smem = smem;
+        L.con_threads = threads;
+        L.con_grid = T.sm_count * per_sm;
+    }
     return P2S_OK;
 }
 
@@ -316,7 +352,10 @@ int run_contract(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_
     C.a_cap = (int)PL.a_cap;
     C.b_cap = (int)PL.b_cap;
     C.tile_off = (int)PL.tile_off;
-    P2S_CUDA(launch_contract(PL.precision, C, PL.con_grid, PL.con_threads, PL.con_smem, s));
+    if (PL.spec_n)
+        P2S_CUDA(launch_contract_ffn(PL.spec_n, C, PL.con_grid, PL.con_threads, PL.con_smem, s));
+    else
+        P2S_CUDA(launch_contract(PL.precision, C, PL.con_grid, PL.con_threads, PL.con_smem, s));
     return P2S_OK;
 }
 
@@ -383,6 +422,8 @@ static int ctx_init(p2s_ctx* c, int device) {
     P2S_CUDA(cudaMemcpy(D.lin_coef_ff, T.lin_coef_ff, sizeof(float2) * T.n_coef, cudaMemcpyHostToDevice));
     P2S_CUDA(cudaMemset(D.err, 0, sizeof(int)));
     P2S_CUDA(init_kernel_attributes());
+    D.spec_ok = contract_ff_runs_match(T);
+    if (D.spec_ok) P2S_CUDA(contract_ff_upload(T));
     return P2S_OK;
 }
 

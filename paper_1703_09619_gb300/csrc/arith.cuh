@@ -1,0 +1,75 @@
+// Arithmetic of the contraction kernels: plain FP64 and float-float (hi + lo FP32 pairs).
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace p2s {
+
+struct ArithF64 {
+    using T = double;
+    using C = double;
+    __device__ static T zero() { return 0.0; }
+    __device__ static void fma_acc(T& acc, C c, T x) { acc = fma(c, x, acc); }
+    __device__ static T finish(T acc) { return acc; }
+    __device__ static double to_double(T v) { return v; }
+    __device__ static T load_moment(const void* p, size_t i) { return __ldg(reinterpret_cast<const double*>(p) + i); }
+    __device__ static C load_coef(const void* p, int i) { return __ldg(reinterpret_cast<const double*>(p) + i); }
+};
+
+// float-float value: x = hi + lo, |lo| <= ulp(hi)/2 after finish()
+struct ArithFF {
+    using T = float2;
+    using C = float2;
+    __device__ static T zero() { return make_float2(0.f, 0.f); }
+    // acc += c * x, with the exact error of the leading product (FMA) and of the leading
+    // sum (TwoSum); second-order terms go to the low word.
+    __device__ static void fma_acc(T& acc, C c, T x) {
+        float p = c.x * x.x;
+        float e = fmaf(c.x, x.x, -p);
+        e = fmaf(c.x, x.y, e);
+        e = fmaf(c.y, x.x, e);
+        float s = acc.x + p;
+        float bp = s - acc.x;
+        float err = (acc.x - (s - bp)) + (p - bp);
+        acc.x = s;
+        acc.y += err + e;
+    }
+    __device__ static T finish(T acc) {  // Fast2Sum renormalisation
+        float s = acc.x + acc.y;
+        float lo = acc.y - (s - acc.x);
+        return make_float2(s, lo);
+    }
+    // FP64 bits of hi + lo without FP64 instructions: hi's double pattern plus lo in units
+    // of the last place of hi's binade (lo < 2^29 such units, so no carry into the exponent;
+    // a borrow below a power of two is taken in the halved units of the lower binade).
+    __device__ static double to_double(T v) {
+        const uint32_t hb = __float_as_uint(v.x);
+        const uint32_t ah = hb & 0x7fffffffu;
+        // zero and subnormal hi (|hi + lo| < 2^-126) map to a signed zero; inf/nan to a quiet nan
+        if (ah < 0x00800000u) return __longlong_as_double((long long)((uint64_t)(hb & 0x80000000u) << 32));
+        if (ah >= 0x7f800000u) return __longlong_as_double(0x7ff8000000000000ll);
+        const uint32_t e = ah >> 23;
+        uint64_t pat = ((uint64_t)((hb & 0x80000000u) | ((e + 896u) << 20) | ((hb & 0x7fffffu) >> 3)) << 32) |
+                       (uint64_t)(hb << 29);
+        const uint32_t lb = __float_as_uint(v.y);
+        const uint32_t al = lb & 0x7fffffffu;
+        if (al >= 0x00800000u) {
+            const int sh = (int)(al >> 23) - (int)e + 29;
+            const uint32_t lm = (al & 0x7fffffu) | 0x800000u;
+            uint32_t u = sh >= 0 ? (lm << sh) : (sh > -32 ? (lm >> -sh) : 0u);
+            if ((lb ^ hb) & 0x80000000u) {
+                if ((hb & 0x7fffffu) == 0u) u <<= 1;
+                pat -= u;
+            } else {
+                pat += u;
+            }
+        }
+        return __longlong_as_double((long long)pat);
+    }
+    __device__ static T load_moment(const void* p, size_t i) { return __ldg(reinterpret_cast<const float2*>(p) + i); }
+    __device__ static C load_coef(const void* p, int i) { return __ldg(reinterpret_cast<const float2*>(p) + i); }
+};
+
+}  // namespace p2s

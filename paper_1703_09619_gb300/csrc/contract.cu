@@ -21,76 +21,11 @@
 //            errors and TwoSum accumulation; moments arrive as (hi, lo) pairs; the FP64
 //            output bits are assembled from (hi, lo) with integer operations, so the hot
 //            loop issues no FP64 instruction (FP64 runs at 1/58 of FP32 on this part).
+#include "arith.cuh"
 #include "p2s_internal.h"
 
 namespace p2s {
 namespace {
-
-// ------------------------------------------------------------------ arithmetic
-struct ArithF64 {
-    using T = double;
-    using C = double;
-    __device__ static T zero() { return 0.0; }
-    __device__ static void fma_acc(T& acc, C c, T x) { acc = fma(c, x, acc); }
-    __device__ static T finish(T acc) { return acc; }
-    __device__ static double to_double(T v) { return v; }
-    __device__ static T load_moment(const void* p, size_t i) { return __ldg(reinterpret_cast<const double*>(p) + i); }
-    __device__ static C load_coef(const void* p, int i) { return __ldg(reinterpret_cast<const double*>(p) + i); }
-};
-
-// float-float value: x = hi + lo, |lo| <= ulp(hi)/2 after finish()
-struct ArithFF {
-    using T = float2;
-    using C = float2;
-    __device__ static T zero() { return make_float2(0.f, 0.f); }
-    // acc += c * x, with the exact error of the leading product (FMA) and of the leading
-    // sum (TwoSum); second-order terms go to the low word.
-    __device__ static void fma_acc(T& acc, C c, T x) {
-        float p = c.x * x.x;
-        float e = fmaf(c.x, x.x, -p);
-        e = fmaf(c.x, x.y, e);
-        e = fmaf(c.y, x.x, e);
-        float s = acc.x + p;
-        float bp = s - acc.x;
-        float err = (acc.x - (s - bp)) + (p - bp);
-        acc.x = s;
-        acc.y += err + e;
-    }
-    __device__ static T finish(T acc) {  // Fast2Sum renormalisation
-        float s = acc.x + acc.y;
-        float lo = acc.y - (s - acc.x);
-        return make_float2(s, lo);
-    }
-    // FP64 bits of hi + lo without FP64 instructions: hi's double pattern plus lo in units
-    // of the last place of hi's binade (lo < 2^29 such units, so no carry into the exponent;
-    // a borrow below a power of two is taken in the halved units of the lower binade).
-    __device__ static double to_double(T v) {
-        const uint32_t hb = __float_as_uint(v.x);
-        const uint32_t ah = hb & 0x7fffffffu;
-        // zero and subnormal hi (|hi + lo| < 2^-126) map to a signed zero; inf/nan to a quiet nan
-        if (ah < 0x00800000u) return __longlong_as_double((long long)((uint64_t)(hb & 0x80000000u) << 32));
-        if (ah >= 0x7f800000u) return __longlong_as_double(0x7ff8000000000000ll);
-        const uint32_t e = ah >> 23;
-        uint64_t pat = ((uint64_t)((hb & 0x80000000u) | ((e + 896u) << 20) | ((hb & 0x7fffffu) >> 3)) << 32) |
-                       (uint64_t)(hb << 29);
-        const uint32_t lb = __float_as_uint(v.y);
-        const uint32_t al = lb & 0x7fffffffu;
-        if (al >= 0x00800000u) {
-            const int sh = (int)(al >> 23) - (int)e + 29;
-            const uint32_t lm = (al & 0x7fffffu) | 0x800000u;
-            uint32_t u = sh >= 0 ? (lm << sh) : (sh > -32 ? (lm >> -sh) : 0u);
-            if ((lb ^ hb) & 0x80000000u) {
-                if ((hb & 0x7fffffu) == 0u) u <<= 1;
-                pat -= u;
-            } else {
-                pat += u;
-            }
-        }
-        return __longlong_as_double((long long)pat);
-    }
-    __device__ static T load_moment(const void* p, size_t i) { return __ldg(reinterpret_cast<const float2*>(p) + i); }
-    __device__ static C load_coef(const void* p, int i) { return __ldg(reinterpret_cast<const float2*>(p) + i); }
-};
 
 __device__ __forceinline__ int type_slot(uint32_t mask, int t) { return __popc(mask & ((1u << t) - 1u)); }
 
@@ -103,6 +38,7 @@ __global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
     double* tile = reinterpret_cast<double*>(smraw + L.tile_off);
     __shared__ ContractUnit cu;
     __shared__ unsigned long long unit_id;
+    __shared__ int32_t s_lin[kMaxOrder * kMaxOrder];
     const int tid = threadIdx.x, nth = blockDim.x;
     const int32_t* __restrict__ lidx = L.lin_idx;
     const void* lcoef = L.lin_coef;
@@ -124,6 +60,9 @@ __global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
         const int nj = Nu_j * Nv_j * Nw_j;
         const int ld = nj + 1;  // padded tile row stride (doubles)
         const size_t moff = d->mom_off + d->pair_off[pair_index(gi, gj, d->n_comp)];
+
+        // the unit's stage-3 coefficient runs, shared by every thread
+        if (tid < Nw_i * Nw_j) s_lin[tid] = __ldg(lidx + lin_slot(t, tid / Nw_j, tid % Nw_j));
 
         // stage 1: A[m1][m2][l][q], m1 in the slab
         const int KvKw = Kv * Kw;
@@ -164,7 +103,7 @@ __global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
             double* trow = tile + (size_t)(mn * Nw_i) * ld + mj * Nw_j;
             for (int p1 = 0; p1 < Nw_i; ++p1) {
                 for (int p2 = 0; p2 < Nw_j; ++p2) {
-                    const int32_t li = __ldg(lidx + lin_slot(t, p1, p2));
+                    const int32_t li = s_lin[p1 * Nw_j + p2];
                     const int q0 = lin_kmin(li), cnt = lin_cnt(li), off = lin_off(li);
                     T acc = A::zero();
                     for (int r = 0; r < cnt; ++r) A::fma_acc(acc, A::load_coef(lcoef, off + r), bt[q0 + 2 * r]);
@@ -173,25 +112,25 @@ __global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
             }
         }
         __syncthreads();
-        // write-out 1: rows (m1, n1, p1) of M_t(gi, gj)
+        // The slabs the host builds are either full in n1 or a single m1, so the tile's rows
+        // (m1, n1, p1) are consecutive dofs: rows [rbase, rbase + rows) of block (gi, gj).
         const int rows = m1n * n1n * Nw_i;
-        double* Mt = L.out + d->out_off + (int64_t)type_slot(L.types_mask, t) * n * n;
-        const int row0 = d->dof_off[gi];
+        const int rbase = d->dof_off[gi] + (m1a * Nv_i + n1a) * Nw_i;
         const int col0 = d->dof_off[gj];
-        for (int idx = tid; idx < rows * nj; idx += nth) {
-            const int r = idx / nj, c = idx - r * nj;
-            const int im1 = r / (n1n * Nw_i), r2 = r - im1 * n1n * Nw_i, in1 = r2 / Nw_i, p1 = r2 - in1 * Nw_i;
-            const int grow = row0 + ((m1a + im1) * Nv_i + n1a + in1) * Nw_i + p1;
-            __stcs(Mt + (int64_t)grow * n + col0 + c, tile[r * ld + c]);
+        const int warp = tid >> 5, lane = tid & 31, nwarp = nth >> 5;
+        // write-out 1: one warp per tile row, lanes along the row of M_t(gi, gj)
+        double* Mt = L.out + d->out_off + (int64_t)type_slot(L.types_mask, t) * n * n + col0;
+        for (int r = warp; r < rows; r += nwarp) {
+            double* dst = Mt + (int64_t)(rbase + r) * n;
+            const double* src = tile + (size_t)r * ld;
+            for (int c = lane; c < nj; c += 32) __stcs(dst + c, src[c]);
         }
-        // write-out 2: the transpose into the partner block (gj, gi) of type tp
+        // write-out 2: the transpose, one warp per row of the partner block (gj, gi)
         if (cu.tp >= 0) {
-            double* Mp = L.out + d->out_off + (int64_t)type_slot(L.types_mask, cu.tp) * n * n;
-            for (int idx = tid; idx < rows * nj; idx += nth) {
-                const int c = idx / rows, r = idx - c * rows;
-                const int im1 = r / (n1n * Nw_i), r2 = r - im1 * n1n * Nw_i, in1 = r2 / Nw_i, p1 = r2 - in1 * Nw_i;
-                const int gcol = row0 + ((m1a + im1) * Nv_i + n1a + in1) * Nw_i + p1;
-                __stcs(Mp + (int64_t)(col0 + c) * n + gcol, tile[r * ld + c]);
+            double* Mp = L.out + d->out_off + (int64_t)type_slot(L.types_mask, cu.tp) * n * n + rbase;
+            for (int c = warp; c < nj; c += nwarp) {
+                double* dst = Mp + (int64_t)(col0 + c) * n;
+                for (int r = lane; r < rows; r += 32) __stcs(dst + r, tile[(size_t)r * ld + c]);
             }
         }
         __syncthreads();

@@ -113,6 +113,13 @@ cudaError_t launch_contract(int precision, const ContractLaunch& L, int grid, in
 int contract_blocks_per_sm(int precision, int threads, size_t smem);
 int moments_threads();
 int moments_blocks_per_sm(size_t smem);
+// contract_ff.cu: mixed contraction specialised for uniform orders 2..8
+bool contract_ff_runs_match(const HostTables& T);
+cudaError_t contract_ff_upload(const HostTables& T);
+int contract_ff_max_order();
+void contract_ff_shape(int N, int m1n, size_t& a_cap, size_t& b_cap, size_t& tile_cap, int& combos);
+cudaError_t launch_contract_ffn(int N, const ContractLaunch& L, int grid, int threads, size_t smem, cudaStream_t s);
+int contract_ffn_blocks_per_sm(int N, int threads, size_t smem);
 cudaError_t init_kernel_attributes();
 
 // ------------------------------------------------------------------ plan building (api.cu)
@@ -127,6 +134,7 @@ struct DeviceTables {
     double* lin_coef = nullptr;
     float2* lin_coef_ff = nullptr;
     int* err = nullptr;
+    bool spec_ok = false;  // the compile-time coefficient runs match the table (contract_ff.cu)
 };
 
 // Everything a fill needs besides device buffers: sizes and launch shapes.
@@ -143,6 +151,7 @@ struct PlanLayout {
     int con_threads = 256;
     size_t con_smem = 0, tile_off = 0;
     int con_grid = 1;
+    int spec_n = 0;  // > 0: the mixed contraction specialised for uniform order N
 };
 
 // Destination of the contraction work list: a growing vector, or a fixed array that
