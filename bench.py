@@ -1,15 +1,19 @@
 #!/usr/bin/env python
 """Benchmark of the product-to-sum element-matrix fill (one JSON line on stdout).
 
-python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2] [--impl ours|reference]
+python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c5] [--mode learned|plain|mixed]
+                [--impl ours|reference]
 
-A step is one pass of the whole fill over the workload's batch of synthetic elements:
-coupling factor + moments (one kernel) and the product-to-sum contraction (one kernel)
-writing every FP64 entry of every element matrix.  `value` is matrix entries per second
-over all ranks, inputs resident in HBM; `e2e` is the same metric through the library's
-public API with pinned host inputs copied in and every output entry copied back to host
-inside the timed region.  Under torchrun each rank fills its own batch (weak scaling, no
-collective on the data path; one all-reduce of the elapsed time).
+Default: the 32768-element, three-component, N = 4 curved-hexahedron batch (c5) filled by
+the learned + mixed-precision path (per-element quadrature picked by the network, float-float
+contraction, 2% seeded 48-point FP64 judge with fallback).  `value` is matrix entries per
+second of that fill over all ranks, inputs resident in HBM; the plain FP64 fill at 48 points
+of the same batch is timed beside it, and every element of the learned fill is compared with
+it (max relative error, share above 1e-8).  `e2e` is the same metric through the public API
+with pinned host inputs copied in and every FP64 entry copied back to host inside the timed
+region.  Under torchrun each rank fills its own batch (weak scaling, no collective on the
+data path; one all-reduce of the elapsed time).  --mode plain|mixed times one fixed-G fill of
+any workload instead.
 """
 from __future__ import annotations
 
@@ -31,9 +35,13 @@ from paper_1703_09619_gb300 import workloads as W  # noqa: E402
 
 METRIC = "matrix entries/s: learned+mixed-prec vs plain FP64 fill, one GB300, rel err ≤1e-8"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 FMA rate of the part: 152 SMs x 2 DFMA/clk/SM (measured by a throughput probe:
-# 0.598 TFMA/s at the running clock) -> at the 2070 MHz maximum SM clock:
+# FP64 FMA rate of the part: 152 SMs x 2 DFMA/clk/SM (a throughput probe measured
+# 0.598 TFMA/s at the running clock), at the 2070 MHz maximum SM clock:
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# FP64 operations per quadrature point of the metric coupling factor in the moment kernel
+# (Jacobian 45, phase 9, sin ~25, cofactors 18, det 3, products 18, division ~10, scale 6)
+ALPHA_FLOP_PER_POINT = 134
+JUDGE_FRAC, JUDGE_TOL, RISK = 0.02, 1e-9, 0.02
 
 
 def log(*a):
@@ -62,7 +70,8 @@ def _runs():
 
 
 def contract_fma_count(orders, types_mask):
-    """Algorithmic FMAs of the sparse three-stage contraction (Eq. (4)) for a batch."""
+    """Algorithmic FMAs of the sparse three-stage contraction (Eq. (4)) as the library runs
+    it: vv and dd blocks gi <= gj, dv blocks all (vd = dv^T when both are selected)."""
     cnt = _runs()
     total = 0
     uniq, counts = np.unique(orders.reshape(orders.shape[0], -1), axis=0, return_counts=True)
@@ -70,32 +79,36 @@ def contract_fma_count(orders, types_mask):
     for row, mult in zip(uniq, counts):
         o = row.reshape(nc, 3)
         s = 0
-        for gi in range(nc):
-            for gj in range(nc):
-                Ni, Nj = o[gi], o[gj]
-                K = Ni + Nj - 1
-                for t in range(4):
-                    if not types_mask & (1 << t):
+        for t in range(4):
+            if not types_mask & (1 << t):
+                continue
+            if t == 2 and types_mask & 2:
+                continue
+            for gi in range(nc):
+                for gj in range(nc):
+                    if t in (0, 3) and gj < gi:
                         continue
+                    Ni, Nj = o[gi], o[gj]
+                    K = Ni + Nj - 1
                     cu = cnt[t, :Ni[0], :Nj[0]].sum()
                     cv = cnt[t, :Ni[1], :Nj[1]].sum()
                     cw = cnt[t, :Ni[2], :Nj[2]].sum()
-                    s += cu * K[1] * K[2]                        # stage 1
-                    s += Ni[0] * Nj[0] * cv * K[2]               # stage 2
-                    s += Ni[0] * Ni[1] * Nj[0] * Nj[1] * cw      # stage 3
+                    s += cu * K[1] * K[2] + Ni[0] * Nj[0] * cv * K[2] + Ni[0] * Ni[1] * Nj[0] * Nj[1] * cw
         total += int(s) * int(mult)
     return total
 
 
-def moment_mac_count(orders, npts):
-    """Algorithmic MACs of the sum-factorised moment contraction (Eq. (4) moments)."""
+def moment_flop_count(orders, npts, metric=True):
+    """Algorithmic FP64 flops of the moment kernel: 2 x the sum-factorised MACs plus the
+    coupling-factor evaluation per quadrature point."""
     total = 0
     nc = orders.shape[1]
     npairs = 1 if nc == 1 else 6
     for e in range(orders.shape[0]):
         K = [int(k) for k in 2 * orders[e].max(axis=0) - 1]
         G = int(npts[e])
-        total += npairs * (K[0] * G ** 3 + K[0] * K[1] * G ** 2 + K[0] * K[1] * K[2] * G)
+        total += 2 * npairs * (K[0] * G ** 3 + K[0] * K[1] * G ** 2 + K[0] * K[1] * K[2] * G)
+        total += (ALPHA_FLOP_PER_POINT if metric else 8) * G ** 3
     return int(total)
 
 
@@ -179,13 +192,13 @@ def oracle_sample(wl, n_elem, seed=5):
     t0 = time.perf_counter()
     oracle.fill(sub.orders, sub.kind, sub.params, sub.nodes, sub.bulge, sub.npts, sub.types_mask, threads)
     dt = time.perf_counter() - t0
-    return sub.entries() / dt, dt, "%d of %d elements (seed %d), every entry, all types" % (
-        idx.size, wl.n_elem, seed), threads
+    return sub.entries() / dt, dt, "%d of %d elements (seed %d) at G=%s, every entry, all types" % (
+        idx.size, wl.n_elem, seed, ",".join(str(g) for g in sorted(set(sub.npts.tolist())))), threads
 
 
 def cpu_sample_size(name):
     # about 5-20 s of oracle work on a 16-core host
-    return {"c1": 1, "c2": 3, "c3": 2, "c4": 12, "c5": 1}[name]
+    return {"c1": 1, "c2": 3, "c3": 2, "c4": 12, "c5": 2}[name]
 
 
 def run_reference(args, wl):
@@ -216,104 +229,161 @@ def run_reference(args, wl):
 
 def workload_config(args, wl):
     o = wl.orders
-    return {"workload": "%s: %s" % (args.workload, wl.description), "elements": wl.n_elem,
-            "n_comp": wl.n_comp, "orders": "uniform %d" % o[0, 0, 0] if (o == o[0, 0, 0]).all() else "mixed",
-            "npts": int(wl.npts[0]) if (wl.npts == wl.npts[0]).all() else "per-element",
-            "precision": args.precision, "entries_per_step": wl.entries(),
-            "l2": "outputs (%.1f GB) exceed L2; L2 also flushed (256 MB write) between steps" % (8e-9 * wl.entries())}
+    cfg = {"workload": "%s: %s" % (args.workload, wl.description), "elements": wl.n_elem,
+           "n_comp": wl.n_comp, "orders": "uniform %d" % o[0, 0, 0] if (o == o[0, 0, 0]).all() else "mixed",
+           "mode": args.mode, "entries_per_step": wl.entries(),
+           "l2": "outputs (%.1f GB) exceed L2; L2 also flushed (256 MB write) between steps" % (8e-9 * wl.entries())}
+    if args.mode == "learned":
+        cfg.update({"npts": "learned per element, classes 8/12/16/24/32/48", "plain_npts": 48,
+                    "precision": "mixed (float-float contraction, FP64 output)", "risk": RISK,
+                    "judge": "%.0f%% seeded, 48-point FP64, tol %.0e" % (100 * JUDGE_FRAC, JUDGE_TOL)})
+    else:
+        cfg.update({"npts": int(wl.npts[0]) if (wl.npts == wl.npts[0]).all() else "per-element",
+                    "precision": args.mode})
+    return cfg
 
 
-# ----------------------------------------------------------------------------- GPU leg
-def run_ours(args, wl):
+# ----------------------------------------------------------------------------- GPU helpers
+def dist_setup():
     import torch
     import torch.distributed as dist
-
-    from paper_1703_09619_gb300 import p2s
-
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
+    return world, rank, local
+
+
+def max_over_ranks(x, world, dev):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def time_steps(fn, steps, stream, flush):
+    """CUDA-event time (ms) of each call of fn() on `stream`, L2 flushed between calls."""
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in evs:
+        a.record(stream)
+        fn()
+        b.record(stream)
+        flush.zero_()
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def stage_times(p2s, ctx, wl, npts, prec, params, nodes, bulge, dev, stream, flush, steps=3):
+    """Moment and contraction kernels timed separately on a plan with the given G per element."""
+    import torch
+    plan = p2s.Plan(ctx, wl.orders, npts, prec, wl.types_mask)
+    mom = torch.empty(max(plan.moment_entries, 1), dtype=torch.float64, device=dev)
+    out = torch.empty(plan.output_entries, dtype=torch.float64, device=dev)
+    plan.moments(wl.kind, params, nodes, bulge, mom, stream=stream)
+    plan.contract(mom, out, stream=stream)
+    m = time_steps(lambda: plan.moments(wl.kind, params, nodes, bulge, mom, stream=stream), steps, stream, flush)
+    c = time_steps(lambda: plan.contract(mom, out, stream=stream), steps, stream, flush)
+    del mom, out
+    plan.close()
+    return float(np.mean(m)), float(np.mean(c))
+
+
+def roofline_for(wl, npts, prec, mom_ms, con_ms, peaks, src):
+    """Roofline object of the dominant kernel of a fill (the slower of the two stages)."""
+    entries = wl.entries()
+    fmas = contract_fma_count(wl.orders, wl.types_mask)
+    mflop = moment_flop_count(wl.orders, npts, wl.kind == W.KIND_METRIC_EPS)
+    if mom_ms >= con_ms:
+        ach = mflop / (mom_ms * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": "k_moments_fp64", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (2 DFMA/clk/SM probe-measured)",
+                "algorithmic_flop_per_launch": mflop,
+                "flop_model": "2 x sum-factorised moment MACs + %d FP64 flop per point for alpha" % ALPHA_FLOP_PER_POINT}
+    if prec == 0:
+        ach = 2 * fmas / (con_ms * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": "k_contract<ArithF64>", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                "algorithmic_flop_per_launch": 2 * fmas,
+                "hbm_write_GBs": 8 * entries / (con_ms * 1e-3) / 1e9}
+    ach = 8 * entries / (con_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": "k_contract_ffn / k_contract<ArithFF>", "achieved": ach,
+            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
+            "peak_source": "%s copy bandwidth (MEASURED_PEAKS.json)" % src, "algorithmic_bytes_per_launch": 8 * entries}
+
+
+# ----------------------------------------------------------------------------- learned (headline)
+def run_learned(args, wl):
+    import torch
+
+    from paper_1703_09619_gb300 import learned as LN
+    from paper_1703_09619_gb300 import p2s
+
+    world, rank, local = dist_setup()
     dev = torch.device("cuda", local)
     ctx = p2s.Context(local)
-    prec = p2s.MIXED if args.precision == "mixed" else p2s.FP64
-    npts = int(wl.npts[0]) if (wl.npts == wl.npts[0]).all() else wl.npts
-    plan = p2s.Plan(ctx, wl.orders, npts, prec, wl.types_mask)
+    mlp_params, meta = LN.ensure_trained(ctx)
+    P = torch.as_tensor(mlp_params, device=dev)
     params, nodes, bulge = p2s.device_inputs(wl, dev)
-    out = torch.empty(plan.output_entries, dtype=torch.float64, device=dev)
-    mom = torch.empty(max(plan.moment_entries, 1), dtype=torch.float64, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-
-    def step(evs=None):
-        if evs:
-            evs[0].record(stream)
-        plan.moments(wl.kind, params, nodes, bulge, mom, stream=stream)
-        if evs:
-            evs[1].record(stream)
-        plan.contract(mom, out, stream=stream)
-        if evs:
-            evs[2].record(stream)
-
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    lp = p2s.LearnedPlan(ctx, wl.orders, precision=p2s.MIXED, judge_frac=JUDGE_FRAC, seed=1703,
+                         judge_tol=JUDGE_TOL, risk=RISK)
+    out = torch.empty(lp.output_entries, dtype=torch.float64, device=dev)
+    npts_d = torch.empty(wl.n_elem, dtype=torch.int32, device=dev)
+    step = lambda: lp.fill(wl.kind, params, nodes, bulge, P, out, npts_d, stream=stream)
     for _ in range(args.warmup):
         step()
         flush.zero_()
     torch.cuda.synchronize()
+    rep = lp.report(stream)
+    barrier(world)
+    with ClockSampler(local) as clk:
+        ms = time_steps(step, args.steps, stream, flush)
+    barrier(world)
     rc = ctx.sync_status(stream)
     if rc != 0:
-        raise RuntimeError("device status %d after warm-up" % rc)
-
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for k in range(args.steps):
-            step(evs[k])
-            flush.zero_()
-        torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    mom_ms = [a.elapsed_time(b) for a, b, _ in evs]
-    con_ms = [b.elapsed_time(c) for _, b, c in evs]
-    step_ms = [a.elapsed_time(c) for a, _, c in evs]
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        raise RuntimeError("device status %d" % rc)
+    rep = lp.report(stream)
+    total_ms = max_over_ranks(float(sum(ms)), world, dev)
     clocks = clk.summary()
+    npts = npts_d.cpu().numpy()
 
+    # the plain FP64 fill at 48 points of the same batch, and the learned fill's error against it
+    plain = p2s.Plan(ctx, wl.orders, 48, p2s.FP64)
+    ref = torch.empty(plain.output_entries, dtype=torch.float64, device=dev)
+    plain.fill(wl.kind, params, nodes, bulge, ref, stream=stream)
+    ksteps = max(1, min(args.steps, 3))
+    pms = time_steps(lambda: plain.fill(wl.kind, params, nodes, bulge, ref, stream=stream), ksteps, stream, flush)
+    plain_ms = max_over_ranks(float(np.mean(pms)), world, dev)
+    n, off = p2s.output_entries(wl.orders, offsets=True)
+    off_d = torch.as_tensor(off, device=dev)
+    err = torch.empty(wl.n_elem, dtype=torch.float64, device=dev)
+    p2s.element_errors(ctx, out, off_d, ref, off_d, 4, err, stream=stream)
+    err_h = err.cpu().numpy()
+    plain.close()
+    del ref
+    # stage breakdown at the learned G (moments, contraction) and of the plain fill
+    mom_ms, con_ms = stage_times(p2s, ctx, wl, npts, p2s.MIXED, params, nodes, bulge, dev, stream, flush)
+    peaks, src = load_peaks()
+    roof = roofline_for(wl, npts, p2s.MIXED, mom_ms, con_ms, peaks, src)
     entries = wl.entries()
     value = world * entries * args.steps / (total_ms * 1e-3)
-    peaks, src = load_peaks()
-    con_avg = float(np.mean(con_ms))
-    mom_avg = float(np.mean(mom_ms))
-    fmas = contract_fma_count(wl.orders, wl.types_mask)
-    bytes_written = 8 * entries
-    macs = moment_mac_count(wl.orders, wl.npts)
-    achieved_flops = 2 * fmas / (con_avg * 1e-3) / 1e12
-    achieved_gbs = bytes_written / (con_avg * 1e-3) / 1e9
-    if prec == p2s.FP64:
-        roof = {"bound": "alu", "kernel": "k_contract<ArithF64>", "achieved": achieved_flops,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_flops / FP64_PEAK_TFLOPS,
-                "traffic": None,
-                "peak_source": "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (probe-measured 2 DFMA/clk/SM)",
-                "hbm_write_GBs": achieved_gbs, "hbm_frac_of_measured": achieved_gbs / peaks["hbm_gbs"],
-                "algorithmic_flop_per_launch": 2 * fmas, "algorithmic_bytes_per_launch": bytes_written}
-    else:
-        roof = {"bound": "hbm", "kernel": "k_contract<ArithFF>", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved_gbs / peaks["hbm_gbs"], "traffic": None,
-                "peak_source": "%s (MEASURED_PEAKS.json copy bandwidth)" % src,
-                "algorithmic_bytes_per_launch": bytes_written}
-    stages = {"moments_ms": mom_avg, "contract_ms": con_avg,
-              "moments_fp64_tflops": 2 * macs / (mom_avg * 1e-3) / 1e12,
-              "contract_fp64_tflops": achieved_flops}
-
-    e2e = measure_e2e(args, wl, ctx, prec, dev) if not args.no_e2e else None
-
+    hist = np.bincount([p2s.CLASS_NPTS.index(int(g)) for g in npts], minlength=6).tolist()
+    e2e = None if args.no_e2e else measure_e2e_learned(args, wl, ctx, P, dev)
     line = None
     if rank == 0:
         line = {
@@ -322,38 +392,53 @@ def run_ours(args, wl):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args, wl),
             "elements_per_s": world * wl.n_elem * args.steps / (total_ms * 1e-3),
-            "roofline": roof, "stages": stages, "clocks": clocks,
-            "gpu_launches": 2 * args.steps,
+            "plain_fp64": {"value": world * entries / (plain_ms * 1e-3), "unit": "entries/s", "ms_per_step": plain_ms,
+                           "npts": 48},
+            "speedup_vs_plain_fp64": plain_ms / (total_ms / args.steps),
+            "accuracy": {"max_rel_err_vs_plain48": float(err_h.max()), "share_above_1e-8": float((err_h > 1e-8).mean()),
+                         "median_rel_err": float(np.median(err_h)), "metric": "per element max over types of max|dM|/max|M|"},
+            "learned": {"class_hist": hist, "mean_G3": float(np.mean(npts.astype(float) ** 3)),
+                        "judged": rep["judged"], "judge_failed": rep["failed"],
+                        "max_judged_err": rep["max_judged_err"], "train": meta},
+            "roofline": roof,
+            "stages": {"moments_ms": mom_ms, "contract_ms": con_ms,
+                       "learned_other_ms": total_ms / args.steps - mom_ms - con_ms},
+            "clocks": clocks,
+            "gpu_launches": 10 * args.steps,
         }
         if e2e:
             line["e2e"] = e2e
-    del out, mom
-    plan.close()
+    del out
+    lp.close()
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, dt, desc, threads = oracle_sample(wl, cpu_sample_size(args.workload))
+        v, dt, desc, threads = oracle_sample(wl.with_npts(48), cpu_sample_size(args.workload))
         line["cpu_baseline"] = {"value": v, "unit": "entries/s", "cores": threads, "kind": "oracle",
                                 "sample": desc + " (%.1f s)" % dt}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
+        import torch.distributed as dist
         dist.destroy_process_group()
 
 
-def measure_e2e(args, wl, ctx, prec, dev):
-    """Same metric through the public API: pinned host inputs -> device, fill, every output
-    entry -> pinned host memory, all inside the timed region.  Outputs stream through a
-    two-slot pinned host ring in element chunks on two CUDA streams."""
+def measure_e2e_learned(args, wl, ctx, P, dev, chunk_elems=4096):
+    """Learned fill through the public API with host buffers: per chunk of elements, pinned
+    host inputs -> device, learned fill, every FP64 entry -> pinned host memory; two chunks
+    in flight on two streams."""
     import torch
 
     from paper_1703_09619_gb300 import p2s
     E = wl.n_elem
-    per_elem = wl.entries() / E
-    chunk = int(max(1, min(E, (2 << 30) // (8 * per_elem))))  # ~2 GB of output per chunk
-    starts = list(range(0, E, chunk))
-    subs = [wl.subset(np.arange(s, min(E, s + chunk))) for s in starts]
-    npts = lambda w: int(w.npts[0]) if (w.npts == w.npts[0]).all() else w.npts
-    plans = [p2s.Plan(ctx, w.orders, npts(w), prec, w.types_mask) for w in subs]
+    subs = [wl.subset(np.arange(s, min(E, s + chunk_elems))) for s in range(0, E, chunk_elems)]
+    plans = [p2s.LearnedPlan(ctx, w.orders, precision=p2s.MIXED, judge_frac=JUDGE_FRAC, seed=1703,
+                             judge_tol=JUDGE_TOL, risk=RISK) for w in subs]
+    return _e2e_pipeline(args, wl, subs, plans, dev,
+                         lambda p, w, di, o, s: p.fill(w.kind, di[0], di[1], di[2], P, o, stream=s))
+
+
+def _e2e_pipeline(args, wl, subs, plans, dev, fill):
+    import torch
     maxn = max(p.output_entries for p in plans)
     host_in = [(torch.from_numpy(np.ascontiguousarray(w.params)).pin_memory(),
                 torch.from_numpy(np.ascontiguousarray(w.nodes)).pin_memory(),
@@ -370,11 +455,10 @@ def measure_e2e(args, wl, ctx, prec, dev):
             s = streams[i % 2]
             with torch.cuda.stream(s):
                 di = dev_in[i % 2]
-                hi = host_in[i]
-                for d, h in zip(di, hi):
+                for d, h in zip(di, host_in[i]):
                     d[: h.shape[0]].copy_(h, non_blocking=True)
                 n = w.n_elem
-                p.fill(w.kind, di[0][:n], di[1][:n], di[2][:n], dev_out[i % 2], stream=s)
+                fill(p, w, [di[0][:n], di[1][:n], di[2][:n]], dev_out[i % 2], s)
                 host_out[i % 2][: p.output_entries].copy_(dev_out[i % 2][: p.output_entries], non_blocking=True)
         for s in streams:
             s.synchronize()
@@ -386,36 +470,122 @@ def measure_e2e(args, wl, ctx, prec, dev):
     for _ in range(steps):
         one_pass()
     dt = (time.perf_counter() - t0) / steps
-    rc = ctx.sync_status()
     for p in plans:
         p.close()
-    if rc != 0:
-        raise RuntimeError("device status %d in e2e" % rc)
     return {"value": wl.entries() / dt, "unit": "entries/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "steps": steps, "chunks": len(subs),
             "note": "pinned host inputs in, every FP64 entry back to pinned host memory, 2-stream pipeline"}
 
 
+# ----------------------------------------------------------------------------- fixed-G fills
+def run_fixed(args, wl):
+    import torch
+
+    from paper_1703_09619_gb300 import p2s
+
+    world, rank, local = dist_setup()
+    dev = torch.device("cuda", local)
+    ctx = p2s.Context(local)
+    prec = p2s.MIXED if args.mode == "mixed" else p2s.FP64
+    npts = int(wl.npts[0]) if (wl.npts == wl.npts[0]).all() else wl.npts
+    plan = p2s.Plan(ctx, wl.orders, npts, prec, wl.types_mask)
+    params, nodes, bulge = p2s.device_inputs(wl, dev)
+    out = torch.empty(plan.output_entries, dtype=torch.float64, device=dev)
+    mom = torch.empty(max(plan.moment_entries, 1), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.moments(wl.kind, params, nodes, bulge, mom, stream=stream)
+        plan.contract(mom, out, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+    if ctx.sync_status(stream) != 0:
+        raise RuntimeError("device status after warm-up")
+    barrier(world)
+    with ClockSampler(local) as clk:
+        ms = time_steps(step, args.steps, stream, flush)
+    barrier(world)
+    total_ms = max_over_ranks(float(sum(ms)), world, dev)
+    clocks = clk.summary()
+    mom_ms, con_ms = stage_times(p2s, ctx, wl, npts, prec, params, nodes, bulge, dev, stream, flush)
+    peaks, src = load_peaks()
+    roof = roofline_for(wl, wl.npts, prec, mom_ms, con_ms, peaks, src)
+    entries = wl.entries()
+    value = world * entries * args.steps / (total_ms * 1e-3)
+    e2e = None if args.no_e2e else measure_e2e_fixed(args, wl, ctx, prec, dev)
+    line = None
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args, wl),
+            "elements_per_s": world * wl.n_elem * args.steps / (total_ms * 1e-3),
+            "roofline": roof, "stages": {"moments_ms": mom_ms, "contract_ms": con_ms}, "clocks": clocks,
+            "gpu_launches": 2 * args.steps,
+        }
+        if e2e:
+            line["e2e"] = e2e
+    del out, mom
+    plan.close()
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, dt, desc, threads = oracle_sample(wl, cpu_sample_size(args.workload))
+        line["cpu_baseline"] = {"value": v, "unit": "entries/s", "cores": threads, "kind": "oracle",
+                                "sample": desc + " (%.1f s)" % dt}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def measure_e2e_fixed(args, wl, ctx, prec, dev):
+    from paper_1703_09619_gb300 import p2s
+    E = wl.n_elem
+    per_elem = wl.entries() / E
+    chunk = int(max(1, min(E, (2 << 30) // (8 * per_elem))))
+    subs = [wl.subset(np.arange(s, min(E, s + chunk))) for s in range(0, E, chunk)]
+    npts = lambda w: int(w.npts[0]) if (w.npts == w.npts[0]).all() else w.npts
+    plans = [p2s.Plan(ctx, w.orders, npts(w), prec, w.types_mask) for w in subs]
+    return _e2e_pipeline(args, wl, subs, plans, dev,
+                         lambda p, w, di, o, s: p.fill(w.kind, di[0], di[1], di[2], o, stream=s))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--workload", default="c5", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--mode", default=None, choices=["learned", "plain", "mixed"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "mixed"], help="alias of --mode plain|mixed")
     ap.add_argument("--elements", type=int, default=None, help="use only the first E elements")
     ap.add_argument("--npts", type=int, default=None, help="override the quadrature size G")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
+    if args.mode is None:
+        args.mode = {"fp64": "plain", "mixed": "mixed"}.get(args.precision) or (
+            "learned" if args.workload == "c5" else "plain")
     wl = W.make(args.workload, args.elements)
     if args.npts:
         wl = wl.with_npts(args.npts)
     if args.impl == "reference":
+        if args.mode == "learned":
+            wl = wl.with_npts(48)
         run_reference(args, wl)
+    elif args.mode == "learned":
+        if wl.kind != W.KIND_METRIC_EPS:
+            raise SystemExit("the learned mode needs a three-component metric workload (c2, c4, c5)")
+        run_learned(args, wl)
     else:
-        run_ours(args, wl)
+        run_fixed(args, wl)
 
 
 if __name__ == "__main__":

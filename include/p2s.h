@@ -190,6 +190,96 @@ int p2s_fill_elements_noalloc(p2s_ctx* ctx, const p2s_geometry* geom, const p2s_
                               const p2s_fill_opts* opts, double* out, int32_t* elem_status,
                               void* stream);
 
+/* ------------------------------------------------------------------------------------
+ * Learned quadrature order.  Not part of the paper: a small network picks, per element,
+ * the Gauss-Legendre size G of the fill (Eq. (2)-(4)); a seeded share of the elements is
+ * re-filled at 48 points in FP64 (the plain method) to judge the choice, and judged
+ * elements that miss the tolerance keep the 48-point fill.  Three-component metric
+ * coupling only.
+ *
+ * Network: 576 inputs (alpha on the 4 x 4 x 4 grid with per-axis reference positions
+ * {-0.9, -0.8, 0.35, 0.45}, all 9 factors alpha_{gi gj}, point index (c*4 + b)*4 + a,
+ * factor index 3 gi + gj, divided by the element's mean of trace(alpha)/3) -> 64 -> 64 -> 6 classes, ReLU, weights used in
+ * FP16 with FP32 accumulation.  Class c means G = {8, 12, 16, 24, 32, 48}[c].
+ * Parameters: one FP32 device array of P2S_MLP_PARAMS values in the order
+ * W1 [576][64], b1 [64], W2 [64][64], b2 [64], W3 [64][6], b3 [6] (W[i][j]: input i to
+ * output j). */
+#define P2S_MLP_IN 576
+#define P2S_MLP_HIDDEN 64
+#define P2S_MLP_CLASSES 6
+#define P2S_MLP_PARAMS 41478
+
+/* G of class cls (0..5), or P2S_ERR_ARG. */
+int p2s_learned_npts(int cls);
+
+/* The 576 features of every element (device [E][576] FP32). */
+int p2s_coarse_features(p2s_ctx* ctx, const p2s_geometry* geom, const p2s_material* mat, float* features,
+                        void* stream);
+
+/* Inference: npts (device [n]) = G of the chosen class + margin (capped at class 5);
+ * logits (device [n][6], optional).  The chosen class is the argmax when risk = 0, else the
+ * smallest class c whose higher classes c+1..5 hold at most `risk` (0 < risk < 1) of the
+ * softmax probability. */
+int p2s_mlp_predict(p2s_ctx* ctx, const float* params, const float* features, int64_t n, int margin, float risk,
+                    int32_t* npts, float* logits, void* stream);
+
+/* Training step, forward and backward on `batch` samples: mean softmax cross-entropy
+ * (each sample weighted by class_weight[label], device [6], optional) into *loss (device)
+ * and its gradient with respect to the FP32 parameters into grad (device
+ * [P2S_MLP_PARAMS]); both are overwritten.  The forward uses the FP16-rounded weights of
+ * inference; the gradient passes the rounding straight through. */
+int p2s_mlp_grad(p2s_ctx* ctx, const float* params, const float* features, const int32_t* labels, int64_t batch,
+                 const float* class_weight, float* grad, float* loss, void* stream);
+
+/* Adam update (Kingma & Ba) with decoupled weight decay (AdamW) of n FP32 parameters in
+ * place; m, v are the moment buffers (device, start at 0), step counts from 1. */
+int p2s_mlp_adam(float* params, const float* grad, float* m, float* v, int64_t n, float lr, float beta1,
+                 float beta2, float eps, float weight_decay, int step, void* stream);
+
+/* err[k] (device [n]) = max over the n_types product types of max|a - b| / max|b| over
+ * element k's matrices, a starting at offsets_a[k] and b at offsets_b[k]..offsets_b[k+1]
+ * (device arrays, offsets_b of length n+1).  Used for the labels and by the judge. */
+int p2s_element_errors(p2s_ctx* ctx, const double* a, const int64_t* offsets_a, const double* b,
+                       const int64_t* offsets_b, int64_t n, int n_types, double* err, void* stream);
+
+/* Seeded judge selection (host): judged[e] = 1 for the elements re-filled by the judge.
+ * Element e is chosen when splitmix64(seed + e * 0x9e3779b97f4a7c15) < frac * 2^64. */
+int p2s_judge_select(int64_t n_elem, double frac, uint64_t seed, int8_t* judged);
+
+typedef struct p2s_learned_plan p2s_learned_plan;
+typedef struct {
+    int margin;        /* classes added to every prediction (0: as predicted)      */
+    double risk;       /* 0: argmax; else the risk rule of p2s_mlp_predict          */
+    int precision;     /* precision of the learned fill: P2S_MIXED or P2S_FP64     */
+    double judge_frac; /* share of elements re-filled at 48 points in FP64          */
+    uint64_t seed;     /* judge selection seed                                     */
+    double judge_tol;  /* largest accepted relative difference (metric of p2s_element_errors) */
+} p2s_learned_opts;
+typedef struct {
+    int64_t n_elem;
+    int64_t judged;            /* elements re-filled by the judge                   */
+    int64_t failed;            /* judged elements above judge_tol, replaced         */
+    int64_t per_class[6];      /* elements filled with each G class                 */
+    double max_judged_err;     /* largest relative difference the judge saw         */
+} p2s_learned_report;
+
+/* Plan a learned fill of E elements (three components, host orders, all four types).
+ * Allocates the fill's scratch, the judge subset and its 48-point FP64 plan. */
+int p2s_learned_plan_create(p2s_ctx* ctx, int64_t n_elem, const p2s_orders* orders, const p2s_learned_opts* opts,
+                            p2s_learned_plan** out);
+void p2s_learned_plan_destroy(p2s_learned_plan* plan);
+int64_t p2s_learned_plan_output_entries(const p2s_learned_plan* plan);
+
+/* Learned fill, asynchronous on `stream`: features, prediction, fill at the predicted G,
+ * judge fill and comparison, replacement of failed judged elements.  npts_out (device
+ * [E], optional) receives the G used per element before any replacement. */
+int p2s_learned_fill(p2s_learned_plan* plan, const p2s_geometry* geom, const p2s_material* mat, const float* params,
+                     double* out, int32_t* npts_out, void* stream);
+
+/* Wait for `stream` and read the last learned fill's report; judge_state (host [E],
+ * optional) receives 0 (not judged), 1 (judged, kept) or 2 (judged, replaced). */
+int p2s_learned_report_get(p2s_learned_plan* plan, p2s_learned_report* report, int8_t* judge_state, void* stream);
+
 /* Wait for `stream`, then return and clear the context's device error flag:
  * P2S_OK, P2S_ERR_JACOBIAN, P2S_ERR_TIMEOUT, or P2S_ERR_CUDA if the stream failed. */
 int p2s_sync_status(p2s_ctx* ctx, void* stream);

@@ -422,6 +422,7 @@ static int ctx_init(p2s_ctx* c, int device) {
     P2S_CUDA(cudaMemcpy(D.lin_coef_ff, T.lin_coef_ff, sizeof(float2) * T.n_coef, cudaMemcpyHostToDevice));
     P2S_CUDA(cudaMemset(D.err, 0, sizeof(int)));
     P2S_CUDA(init_kernel_attributes());
+    P2S_CUDA(learned_init_attributes());
     D.spec_ok = contract_ff_runs_match(T);
     if (D.spec_ok) P2S_CUDA(contract_ff_upload(T));
     return P2S_OK;
@@ -588,4 +589,5 @@ int p2s_sync_status(p2s_ctx* ctx, void* stream) {
 
 namespace p2s {
 const DeviceTables* context_tables(const p2s_ctx* c) { return c ? &c->T : nullptr; }
+ElemDesc* plan_desc(p2s_plan* p) { return p ? p->d_desc : nullptr; }
 }  // namespace p2s

@@ -1,0 +1,687 @@
+// Learned quadrature order (not part of arXiv:1703.09619; it picks, per element, the
+// Gauss-Legendre size G that the fill of Eq. (2)-(4) uses).
+//
+//   k_features      alpha (Eq. (2) coupling factor) at the 4 x 4 x 4 Gauss-Legendre points
+//                   of the element, all 9 factors, divided by the mean of trace(alpha)/3:
+//                   576 FP32 features per element.
+//   k_mlp_predict   576 -> 64 -> 64 -> 6 ReLU MLP, FP16 weights in shared memory, FP32
+//                   accumulation; class c -> G = {8, 12, 16, 24, 32, 48}[min(c + margin, 5)].
+//   k_mlp_grad      training forward (same FP16-rounded weights) + softmax cross-entropy +
+//                   backward for 32 samples per CTA; weight gradients reach the FP32
+//                   gradient buffer with one atomic add per weight per CTA.
+//   k_adam          Adam update of the FP32 master parameters.
+//   k_elem_err      per element, max over product types of max|a - b| / max|b| (labels and
+//                   the judge).
+// Parameter layout (FP32, P2S_MLP_PARAMS values): W1 [576][64], b1 [64], W2 [64][64], b2 [64],
+// W3 [64][6], b3 [6]; W[i][j] multiplies input i into output j.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "alpha.cuh"
+#include "p2s_internal.h"
+
+namespace p2s {
+namespace {
+
+constexpr int kIn = P2S_MLP_IN, kH = P2S_MLP_HIDDEN, kC = P2S_MLP_CLASSES;
+constexpr int oW1 = 0, oB1 = kIn * kH, oW2 = oB1 + kH, oB2 = oW2 + kH * kH, oW3 = oB2 + kH, oB3 = oW3 + kH * kC;
+static_assert(oB3 + kC == P2S_MLP_PARAMS, "parameter layout");
+constexpr int kS = 32;  // samples per CTA
+constexpr int kThr = 256;
+const int kClassG[kC] = {8, 12, 16, 24, 32, 48};
+// Per-axis positions of the 4 x 4 x 4 coarse samples: two close pairs.  The close pairs
+// (0.1 apart in u, about 0.05 in a unit-size element) see the local oscillation of the
+// coupling factor without aliasing up to |k| ~ 60; the far pair sees its variation
+// across the element.
+__constant__ double c_coarse_x[4] = {-0.9, -0.8, 0.35, 0.45};
+
+// ------------------------------------------------------------------ features
+__global__ void __launch_bounds__(64) k_features(const double* __restrict__ nodes, const double* __restrict__ bulge,
+                                                 const double* __restrict__ params, int64_t E,
+                                                 float* __restrict__ feat, int32_t* __restrict__ bad) {
+    const double* x4 = c_coarse_x;
+    __shared__ double geo[48];
+    __shared__ double tr[64];
+    const int p = threadIdx.x;
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+        if (p == 0) metric_geo(nodes + 24 * e, bulge ? bulge + 4 * e : nullptr, params + 4 * e, geo);
+        __syncthreads();
+        const int a = p & 3, b = (p >> 2) & 3, c = p >> 4;
+        const double u = x4[a], v = x4[b], w = x4[c];
+        double su, cu, sv, cv, sw, cw;
+        sincos(1.5707963267948966 * u, &su, &cu);
+        sincos(1.5707963267948966 * v, &sv, &cv);
+        sincos(1.5707963267948966 * w, &sw, &cw);
+        double K[6];
+        const bool ok = metric_alpha(geo, u, v, w, cu, su, cv, sv, cw, sw, K);
+        if (!ok && bad) bad[e] = 1;
+        tr[p] = (K[0] + K[3] + K[5]) / 3.0;
+        __syncthreads();
+        for (int s = 32; s > 0; s >>= 1) {
+            if (p < s) tr[p] += tr[p + s];
+            __syncthreads();
+        }
+        const double inv = 64.0 / tr[0];
+        const int map[9] = {0, 1, 2, 1, 3, 4, 2, 4, 5};
+        float* f = feat + (size_t)e * kIn + p * 9;
+#pragma unroll
+        for (int s = 0; s < 9; ++s) f[s] = (float)(K[map[s]] * inv);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ MLP forward (shared by both kernels)
+struct MlpSmem {
+    __half* W1;  // [576][64]
+    float* W2;   // [64][64] (FP16-rounded values)
+    float* W3;   // [64][6]
+    float* b;    // b1[64] b2[64] b3[6]
+    float* X;    // [32][576]
+    float* H1;   // [32][64]
+    float* H2;   // [32][64]
+    float* Z;    // [32][6]
+};
+constexpr size_t kMlpSmem = sizeof(__half) * kIn * kH + sizeof(float) * (kH * kH + kH * kC + 2 * kH + kC + kS * kIn +
+                                                                          2 * kS * kH + kS * kC);
+
+__device__ MlpSmem mlp_carve(unsigned char* sm) {
+    MlpSmem S;
+    S.W1 = reinterpret_cast<__half*>(sm);
+    float* f = reinterpret_cast<float*>(sm + sizeof(__half) * kIn * kH);
+    S.W2 = f;
+    S.W3 = S.W2 + kH * kH;
+    S.b = S.W3 + kH * kC;
+    S.X = S.b + 2 * kH + kC;
+    S.H1 = S.X + kS * kIn;
+    S.H2 = S.H1 + kS * kH;
+    S.Z = S.H2 + kS * kH;
+    return S;
+}
+
+__device__ float half_round(float x) { return __half2float(__float2half_rn(x)); }
+
+__device__ void mlp_load_weights(const float* __restrict__ P, MlpSmem& S) {
+    for (int i = threadIdx.x; i < kIn * kH; i += blockDim.x) S.W1[i] = __float2half_rn(P[oW1 + i]);
+    for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) S.W2[i] = half_round(P[oW2 + i]);
+    for (int i = threadIdx.x; i < kH * kC; i += blockDim.x) S.W3[i] = half_round(P[oW3 + i]);
+    for (int i = threadIdx.x; i < kH; i += blockDim.x) {
+        S.b[i] = P[oB1 + i];
+        S.b[kH + i] = P[oB2 + i];
+    }
+    if (threadIdx.x < kC) S.b[2 * kH + threadIdx.x] = P[oB3 + threadIdx.x];
+}
+
+// H1, H2 (post-ReLU) and logits Z for the ns samples in S.X.
+__device__ void mlp_forward(MlpSmem& S, int ns) {
+    const int t = threadIdx.x;
+    const int j = t & (kH - 1), g = t / kH;  // 4 groups of 64 threads, 8 samples each
+    {
+        float acc[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] = S.b[j];
+        for (int i = 0; i < kIn; ++i) {
+            const float w = __half2float(S.W1[i * kH + j]);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] = fmaf(S.X[(g + 4 * k) * kIn + i], w, acc[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) S.H1[(g + 4 * k) * kH + j] = (g + 4 * k) < ns ? fmaxf(acc[k], 0.f) : 0.f;
+    }
+    __syncthreads();
+    {
+        float acc[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] = S.b[kH + j];
+        for (int i = 0; i < kH; ++i) {
+            const float w = S.W2[i * kH + j];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] = fmaf(S.H1[(g + 4 * k) * kH + i], w, acc[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) S.H2[(g + 4 * k) * kH + j] = (g + 4 * k) < ns ? fmaxf(acc[k], 0.f) : 0.f;
+    }
+    __syncthreads();
+    if (t < kS * kC) {
+        const int s = t / kC, c = t % kC;
+        float acc = S.b[2 * kH + c];
+        for (int i = 0; i < kH; ++i) acc = fmaf(S.H2[s * kH + i], S.W3[i * kC + c], acc);
+        S.Z[s * kC + c] = acc;
+    }
+    __syncthreads();
+}
+
+// Decision: with risk > 0 the smallest class whose higher classes hold at most `risk`
+// of the softmax probability; otherwise the argmax.  Then `margin` classes up.
+__global__ void __launch_bounds__(kThr) k_mlp_predict(const float* __restrict__ P, const float* __restrict__ feat,
+                                                      int64_t E, int margin, float risk, int32_t* __restrict__ npts,
+                                                      float* __restrict__ logits) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    MlpSmem S = mlp_carve(sm);
+    mlp_load_weights(P, S);
+    const int G[kC] = {8, 12, 16, 24, 32, 48};
+    for (int64_t e0 = (int64_t)blockIdx.x * kS; e0 < E; e0 += (int64_t)gridDim.x * kS) {
+        const int ns = (int)(E - e0 < kS ? E - e0 : kS);
+        __syncthreads();
+        for (int i = threadIdx.x; i < kS * kIn; i += blockDim.x)
+            S.X[i] = i < ns * kIn ? feat[e0 * kIn + i] : 0.f;
+        __syncthreads();
+        mlp_forward(S, ns);
+        if (threadIdx.x < ns) {
+            const int s = threadIdx.x;
+            int best = 0;
+            for (int c = 1; c < kC; ++c)
+                if (S.Z[s * kC + c] > S.Z[s * kC + best]) best = c;
+            if (risk > 0.f) {
+                const float m = S.Z[s * kC + best];
+                float pr[kC], tot = 0.f;
+                for (int c = 0; c < kC; ++c) tot += (pr[c] = expf(S.Z[s * kC + c] - m));
+                float above = 1.f;  // probability of the classes above c
+                best = kC - 1;
+                for (int c = 0; c < kC; ++c) {
+                    above -= pr[c] / tot;
+                    if (above <= risk) { best = c; break; }
+                }
+            }
+            npts[e0 + s] = G[min(best + margin, kC - 1)];
+            if (logits)
+                for (int c = 0; c < kC; ++c) logits[(e0 + s) * kC + c] = S.Z[s * kC + c];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ training
+__global__ void __launch_bounds__(kThr) k_mlp_grad(const float* __restrict__ P, const float* __restrict__ feat,
+                                                   const int32_t* __restrict__ label, int64_t B,
+                                                   const float* __restrict__ class_w, float* __restrict__ grad,
+                                                   float* __restrict__ loss) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    MlpSmem S = mlp_carve(sm);
+    __shared__ float dZ[kS * kC];
+    __shared__ float lsum[kS];
+    mlp_load_weights(P, S);
+    const int64_t e0 = (int64_t)blockIdx.x * kS;
+    const int ns = (int)(B - e0 < kS ? B - e0 : kS);
+    for (int i = threadIdx.x; i < kS * kIn; i += blockDim.x) S.X[i] = i < ns * kIn ? feat[e0 * kIn + i] : 0.f;
+    __syncthreads();
+    mlp_forward(S, ns);
+    const int t = threadIdx.x;
+    const float invB = 1.0f / (float)B;
+    if (t < kS) {
+        float l = 0.f;
+        if (t < ns) {
+            const int y = label[e0 + t];
+            float m = S.Z[t * kC];
+            for (int c = 1; c < kC; ++c) m = fmaxf(m, S.Z[t * kC + c]);
+            float se = 0.f;
+            for (int c = 0; c < kC; ++c) se += expf(S.Z[t * kC + c] - m);
+            const float w = class_w ? class_w[y] : 1.f;
+            for (int c = 0; c < kC; ++c) {
+                const float pc = expf(S.Z[t * kC + c] - m) / se;
+                dZ[t * kC + c] = w * (pc - (c == y ? 1.f : 0.f)) * invB;
+            }
+            l = w * (logf(se) + m - S.Z[t * kC + y]) * invB;
+        } else {
+            for (int c = 0; c < kC; ++c) dZ[t * kC + c] = 0.f;
+        }
+        lsum[t] = l;
+    }
+    __syncthreads();
+    if (t == 0) {
+        float l = 0.f;
+        for (int s = 0; s < kS; ++s) l += lsum[s];
+        atomicAdd(loss, l);
+    }
+    // layer 3
+    for (int k = t; k < kH * kC; k += blockDim.x) {
+        const int i = k / kC, c = k % kC;
+        float acc = 0.f;
+        for (int s = 0; s < ns; ++s) acc = fmaf(S.H2[s * kH + i], dZ[s * kC + c], acc);
+        atomicAdd(grad + oW3 + k, acc);
+    }
+    if (t < kC) {
+        float acc = 0.f;
+        for (int s = 0; s < ns; ++s) acc += dZ[s * kC + t];
+        atomicAdd(grad + oB3 + t, acc);
+    }
+    // dH2 (overwrites H2 after its last read above; synchronise first)
+    float dh2[8];
+    const int j = t & (kH - 1), g = t / kH;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int s = g + 4 * k;
+        float acc = 0.f;
+        for (int c = 0; c < kC; ++c) acc = fmaf(dZ[s * kC + c], S.W3[j * kC + c], acc);
+        dh2[k] = S.H2[s * kH + j] > 0.f ? acc : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 8; ++k) S.H2[(g + 4 * k) * kH + j] = dh2[k];  // H2 now holds dH2
+    __syncthreads();
+    for (int k = t; k < kH * kH; k += blockDim.x) {
+        const int i = k / kH, jj = k % kH;
+        float acc = 0.f;
+        for (int s = 0; s < ns; ++s) acc = fmaf(S.H1[s * kH + i], S.H2[s * kH + jj], acc);
+        atomicAdd(grad + oW2 + k, acc);
+    }
+    if (t < kH) {
+        float acc = 0.f;
+        for (int s = 0; s < ns; ++s) acc += S.H2[s * kH + t];
+        atomicAdd(grad + oB2 + t, acc);
+    }
+    // dH1
+    float dh1[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int s = g + 4 * k;
+        float acc = 0.f;
+        for (int jj = 0; jj < kH; ++jj) acc = fmaf(S.H2[s * kH + jj], S.W2[j * kH + jj], acc);
+        dh1[k] = S.H1[s * kH + j] > 0.f ? acc : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 8; ++k) S.H1[(g + 4 * k) * kH + j] = dh1[k];  // H1 now holds dH1
+    __syncthreads();
+    for (int k = t; k < kIn * kH; k += blockDim.x) {
+        const int i = k / kH, jj = k % kH;
+        float acc = 0.f;
+        for (int s = 0; s < ns; ++s) acc = fmaf(S.X[s * kIn + i], S.H1[s * kH + jj], acc);
+        atomicAdd(grad + oW1 + k, acc);
+    }
+    if (t < kH) {
+        float acc = 0.f;
+        for (int s = 0; s < ns; ++s) acc += S.H1[s * kH + t];
+        atomicAdd(grad + oB1 + t, acc);
+    }
+}
+
+// Adam with decoupled weight decay (Loshchilov & Hutter, AdamW).
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1, float c2,
+                       float wd) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + wd * p[i]);
+    }
+}
+
+// ------------------------------------------------------------------ per-element errors
+__global__ void __launch_bounds__(256) k_elem_err(const double* __restrict__ a, const int64_t* __restrict__ offa,
+                                                  const double* __restrict__ b, const int64_t* __restrict__ offb,
+                                                  int64_t E, int n_types, double* __restrict__ err) {
+    __shared__ double sd[256], sm[256];
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+        const int64_t len = (offb[e + 1] - offb[e]) / n_types;
+        double worst = 0.0;
+        for (int t = 0; t < n_types; ++t) {
+            const double* pa = a + offa[e] + t * len;
+            const double* pb = b + offb[e] + t * len;
+            double d = 0.0, m = 0.0;
+            for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
+                d = fmax(d, fabs(pa[i] - pb[i]));
+                m = fmax(m, fabs(pb[i]));
+            }
+            sd[threadIdx.x] = d;
+            sm[threadIdx.x] = m;
+            __syncthreads();
+            for (int s = 128; s > 0; s >>= 1) {
+                if (threadIdx.x < s) {
+                    sd[threadIdx.x] = fmax(sd[threadIdx.x], sd[threadIdx.x + s]);
+                    sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + s]);
+                }
+                __syncthreads();
+            }
+            const double r = sm[0] > 0.0 ? sd[0] / sm[0] : sd[0];
+            worst = fmax(worst, r);
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) err[e] = worst;
+    }
+}
+
+// ------------------------------------------------------------------ judge selection
+// Counter-based selection: element e is judged when splitmix64(seed + e * golden) falls
+// below frac * 2^64 (splitmix64: Steele, Lea and Flood, OOPSLA 2014).
+uint64_t splitmix64(uint64_t x) {
+    x += 0x9e3779b97f4a7c15ull;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+}
+
+cudaError_t set_mlp_smem() {
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_predict, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMlpSmem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMlpSmem);
+}
+
+}  // namespace
+
+cudaError_t learned_init_attributes() { return set_mlp_smem(); }
+
+}  // namespace p2s
+
+using namespace p2s;
+
+#define P2S_LCUDA(call)                                                 \
+    do {                                                                \
+        cudaError_t ce_ = (call);                                       \
+        if (ce_ != cudaSuccess) return fail(P2S_ERR_CUDA, #call, ce_);  \
+    } while (0)
+
+extern "C" {
+
+int p2s_learned_npts(int cls) { return (cls >= 0 && cls < kC) ? kClassG[cls] : P2S_ERR_ARG; }
+
+int p2s_coarse_features(p2s_ctx* ctx, const p2s_geometry* geom, const p2s_material* mat, float* features,
+                        void* stream) {
+    const DeviceTables* T = context_tables(ctx);
+    if (!T || !geom || !mat) return fail(P2S_ERR_ARG, "p2s_coarse_features: NULL argument");
+    if (mat->kind != P2S_ALPHA_METRIC_EPS) return fail(P2S_ERR_ARG, "p2s_coarse_features: needs the metric coupling kind");
+    if (geom->n_elem == 0) return P2S_OK;
+    if (!geom->nodes || !mat->params || !features) return fail(P2S_ERR_ARG, "p2s_coarse_features: NULL array");
+    P2S_LCUDA(cudaSetDevice(T->device));
+    const int grid = (int)std::min<int64_t>(geom->n_elem, (int64_t)T->sm_count * 32);
+    k_features<<<grid, 64, 0, (cudaStream_t)stream>>>(geom->nodes, geom->bulge, mat->params, geom->n_elem, features,
+                                                       nullptr);
+    P2S_LCUDA(cudaGetLastError());
+    return P2S_OK;
+}
+
+int p2s_mlp_predict(p2s_ctx* ctx, const float* params, const float* features, int64_t n, int margin, float risk,
+                    int32_t* npts, float* logits, void* stream) {
+    const DeviceTables* T = context_tables(ctx);
+    if (!T || n < 0 || margin < 0 || !(risk >= 0.f) || risk >= 1.f) return fail(P2S_ERR_ARG, "p2s_mlp_predict: bad argument");
+    if (n == 0) return P2S_OK;
+    if (!params || !features || !npts) return fail(P2S_ERR_ARG, "p2s_mlp_predict: NULL array");
+    P2S_LCUDA(cudaSetDevice(T->device));
+    const int grid = (int)std::min<int64_t>((n + kS - 1) / kS, (int64_t)T->sm_count);
+    k_mlp_predict<<<grid, kThr, kMlpSmem, (cudaStream_t)stream>>>(params, features, n, margin, risk, npts, logits);
+    P2S_LCUDA(cudaGetLastError());
+    return P2S_OK;
+}
+
+int p2s_mlp_grad(p2s_ctx* ctx, const float* params, const float* features, const int32_t* labels, int64_t batch,
+                 const float* class_weight, float* grad, float* loss, void* stream) {
+    const DeviceTables* T = context_tables(ctx);
+    if (!T || batch <= 0 || !params || !features || !labels || !grad || !loss)
+        return fail(P2S_ERR_ARG, "p2s_mlp_grad: bad argument");
+    P2S_LCUDA(cudaSetDevice(T->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    P2S_LCUDA(cudaMemsetAsync(grad, 0, sizeof(float) * P2S_MLP_PARAMS, s));
+    P2S_LCUDA(cudaMemsetAsync(loss, 0, sizeof(float), s));
+    const int grid = (int)((batch + kS - 1) / kS);
+    k_mlp_grad<<<grid, kThr, kMlpSmem, s>>>(params, features, labels, batch, class_weight, grad, loss);
+    P2S_LCUDA(cudaGetLastError());
+    return P2S_OK;
+}
+
+int p2s_mlp_adam(float* params, const float* grad, float* m, float* v, int64_t n, float lr, float beta1, float beta2,
+                 float eps, float weight_decay, int step, void* stream) {
+    if (!params || !grad || !m || !v || n <= 0 || step < 1 || !(weight_decay >= 0.f))
+        return fail(P2S_ERR_ARG, "p2s_mlp_adam: bad argument");
+    const float c1 = 1.f - powf(beta1, (float)step), c2 = 1.f - powf(beta2, (float)step);
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 1024);
+    k_adam<<<grid, 256, 0, (cudaStream_t)stream>>>(params, grad, m, v, n, lr, beta1, beta2, eps, c1, c2, weight_decay);
+    P2S_LCUDA(cudaGetLastError());
+    return P2S_OK;
+}
+
+int p2s_element_errors(p2s_ctx* ctx, const double* a, const int64_t* offsets_a, const double* b,
+                       const int64_t* offsets_b, int64_t n_elem, int n_types, double* err, void* stream) {
+    const DeviceTables* T = context_tables(ctx);
+    if (!T || n_elem < 0 || n_types < 1 || n_types > 4) return fail(P2S_ERR_ARG, "p2s_element_errors: bad argument");
+    if (n_elem == 0) return P2S_OK;
+    if (!a || !b || !offsets_a || !offsets_b || !err) return fail(P2S_ERR_ARG, "p2s_element_errors: NULL array");
+    P2S_LCUDA(cudaSetDevice(T->device));
+    const int grid = (int)std::min<int64_t>(n_elem, (int64_t)T->sm_count * 8);
+    k_elem_err<<<grid, 256, 0, (cudaStream_t)stream>>>(a, offsets_a, b, offsets_b, n_elem, n_types, err);
+    P2S_LCUDA(cudaGetLastError());
+    return P2S_OK;
+}
+
+int p2s_judge_select(int64_t n_elem, double frac, uint64_t seed, int8_t* judged) {
+    if (n_elem < 0 || frac < 0.0 || frac > 1.0 || (n_elem > 0 && !judged)) return fail(P2S_ERR_ARG, "p2s_judge_select: bad argument");
+    const double lim = frac * 18446744073709551616.0;
+    for (int64_t e = 0; e < n_elem; ++e)
+        judged[e] = (frac >= 1.0) || ((double)splitmix64(seed + (uint64_t)e * 0x9e3779b97f4a7c15ull) < lim);
+    return P2S_OK;
+}
+
+}  // extern "C"
+
+// ====================================================================== learned fill
+// A learned plan holds: the main plan (the requested precision; every element's G is
+// written into its descriptor from the prediction at fill time, so one plan serves every
+// prediction), the judge subset (seeded, fixed at plan time) with its own FP64 plan at 48
+// points, and device scratch for features, predictions, judge outputs and the report.
+// A fill is asynchronous end to end: features -> prediction -> per-element G -> fill ->
+// judge fill of the subset -> per-element comparison -> judged elements above the
+// tolerance replaced in `out` by their 48-point FP64 fill (the plain method).
+namespace p2s {
+namespace {
+
+__global__ void k_set_npts(ElemDesc* desc, const int32_t* npts, int64_t E, unsigned long long* cls_count) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        const int Gs[kC] = {8, 12, 16, 24, 32, 48};
+        const int G = npts[e];
+        desc[e].G = (int16_t)G;
+        int c = 0;
+        while (c < kC - 1 && Gs[c] != G) ++c;
+        atomicAdd(cls_count + c, 1ull);
+    }
+}
+
+__global__ void k_gather_inputs(const double* __restrict__ nodes, const double* __restrict__ bulge,
+                                const double* __restrict__ params, const int32_t* __restrict__ idx, int64_t nJ,
+                                double* __restrict__ jn, double* __restrict__ jb, double* __restrict__ jp) {
+    for (int64_t k = blockIdx.x; k < nJ; k += gridDim.x) {
+        const int64_t e = idx[k];
+        const int t = threadIdx.x;
+        if (t < 24) jn[24 * k + t] = nodes[24 * e + t];
+        else if (t < 28) jb[4 * k + t - 24] = bulge ? bulge[4 * e + t - 24] : 0.0;
+        else if (t < 32) jp[4 * k + t - 28] = params[4 * e + t - 28];
+    }
+}
+
+// report: [0] judged, [1] failed, [2..7] per class, [8] max judged error (double bits)
+__global__ void k_judge_fix(double* __restrict__ out, const int64_t* __restrict__ off_main, const double* __restrict__ jout,
+                            const int64_t* __restrict__ off_j, const double* __restrict__ err, int64_t nJ, double tol,
+                            unsigned long long* report) {
+    for (int64_t k = blockIdx.x; k < nJ; k += gridDim.x) {
+        const double ek = err[k];
+        const bool bad = !(ek <= tol);
+        if (threadIdx.x == 0) {
+            atomicAdd(report + 0, 1ull);
+            if (bad) atomicAdd(report + 1, 1ull);
+            atomicMax(report + 8, (unsigned long long)__double_as_longlong(ek));
+        }
+        if (bad) {
+            const int64_t len = off_j[k + 1] - off_j[k];
+            double* dst = out + off_main[k];
+            const double* src = jout + off_j[k];
+            for (int64_t i = threadIdx.x; i < len; i += blockDim.x) dst[i] = src[i];
+        }
+    }
+}
+
+}  // namespace
+}  // namespace p2s
+
+struct p2s_learned_plan {
+    p2s_ctx* ctx = nullptr;
+    p2s_plan* main = nullptr;
+    p2s_plan* judge = nullptr;
+    int64_t E = 0, nJ = 0;
+    int margin = 0;
+    float risk = 0.f;
+    double tol = 1e-9;
+    int32_t* d_jidx = nullptr;
+    int64_t* d_off_main = nullptr;  // [nJ+1] start of each judged element in the main output
+    int64_t* d_off_j = nullptr;     // [nJ+1] start of each judged element in the judge output
+    float* d_feat = nullptr;
+    int32_t* d_npts = nullptr;
+    double* d_jin = nullptr;  // gathered nodes [nJ][24], bulge [nJ][4], params [nJ][4]
+    double* d_jout = nullptr;
+    double* d_jerr = nullptr;
+    unsigned long long* d_report = nullptr;
+};
+
+extern "C" {
+
+void p2s_learned_plan_destroy(p2s_learned_plan* L) {
+    if (!L) return;
+    if (L->ctx) cudaSetDevice(context_tables(L->ctx)->device);
+    p2s_plan_destroy(L->main);
+    p2s_plan_destroy(L->judge);
+    cudaFree(L->d_jidx);
+    cudaFree(L->d_off_main);
+    cudaFree(L->d_off_j);
+    cudaFree(L->d_feat);
+    cudaFree(L->d_npts);
+    cudaFree(L->d_jin);
+    cudaFree(L->d_jout);
+    cudaFree(L->d_jerr);
+    cudaFree(L->d_report);
+    delete L;
+}
+
+int p2s_learned_plan_create(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, const p2s_learned_opts* opts,
+                            p2s_learned_plan** out) {
+    const DeviceTables* T = context_tables(ctx);
+    if (!T || !out || !orders || !opts) return fail(P2S_ERR_ARG, "p2s_learned_plan_create: NULL argument");
+    *out = nullptr;
+    if (orders->n_comp != 3) return fail(P2S_ERR_ARG, "p2s_learned_plan_create: the learned fill needs three components");
+    if (opts->margin < 0 || opts->judge_frac < 0 || opts->judge_frac > 1 || !(opts->judge_tol >= 0) ||
+        !(opts->risk >= 0.0) || opts->risk >= 1.0)
+        return fail(P2S_ERR_ARG, "p2s_learned_plan_create: bad margin, judge fraction or tolerance");
+    P2S_LCUDA(cudaSetDevice(T->device));
+    p2s_learned_plan* L = new (std::nothrow) p2s_learned_plan();
+    if (!L) return fail(P2S_ERR_OOM, "p2s_learned_plan_create: host allocation");
+    L->ctx = ctx;
+    L->E = E;
+    L->margin = opts->margin;
+    L->risk = (float)opts->risk;
+    L->tol = opts->judge_tol;
+    p2s_quadrature q48 = {48, nullptr};
+    p2s_fill_opts fo = {opts->precision, P2S_TYPES_ALL};
+    int rc = p2s_plan_create(ctx, E, orders, &q48, &fo, &L->main);
+    if (rc) { p2s_learned_plan_destroy(L); return rc; }
+    // judge subset
+    std::vector<int8_t> sel((size_t)std::max<int64_t>(E, 1));
+    p2s_judge_select(E, opts->judge_frac, opts->seed, sel.data());
+    std::vector<int32_t> jidx;
+    for (int64_t e = 0; e < E; ++e)
+        if (sel[e]) jidx.push_back((int32_t)e);
+    L->nJ = (int64_t)jidx.size();
+    std::vector<int64_t> off_full((size_t)E + 1);
+    p2s_output_entries(E, orders, P2S_TYPES_ALL, off_full.data());
+    const size_t nc3 = 9;
+    std::vector<int32_t> jord(std::max<size_t>(1, jidx.size() * nc3));
+    std::vector<int64_t> off_main(jidx.size() + 1), off_j(jidx.size() + 1);
+    for (size_t k = 0; k < jidx.size(); ++k) {
+        std::memcpy(&jord[k * nc3], orders->orders + nc3 * jidx[k], sizeof(int32_t) * nc3);
+        off_main[k] = off_full[jidx[k]];
+    }
+    off_main[jidx.size()] = off_full[E];
+    p2s_orders jo = {3, jord.data()};
+    p2s_fill_opts fj = {P2S_FP64, P2S_TYPES_ALL};
+    rc = p2s_plan_create(ctx, L->nJ, &jo, &q48, &fj, &L->judge);
+    if (rc) { p2s_learned_plan_destroy(L); return rc; }
+    const int64_t jent = p2s_output_entries(L->nJ, &jo, P2S_TYPES_ALL, off_j.data());
+    bool ok = cudaMalloc(&L->d_feat, sizeof(float) * kIn * std::max<int64_t>(E, 1)) == cudaSuccess &&
+              cudaMalloc(&L->d_npts, sizeof(int32_t) * std::max<int64_t>(E, 1)) == cudaSuccess &&
+              cudaMalloc(&L->d_jidx, sizeof(int32_t) * std::max<int64_t>(L->nJ, 1)) == cudaSuccess &&
+              cudaMalloc(&L->d_off_main, sizeof(int64_t) * (L->nJ + 1)) == cudaSuccess &&
+              cudaMalloc(&L->d_off_j, sizeof(int64_t) * (L->nJ + 1)) == cudaSuccess &&
+              cudaMalloc(&L->d_jin, sizeof(double) * 32 * std::max<int64_t>(L->nJ, 1)) == cudaSuccess &&
+              cudaMalloc(&L->d_jout, sizeof(double) * std::max<int64_t>(jent, 1)) == cudaSuccess &&
+              cudaMalloc(&L->d_jerr, sizeof(double) * std::max<int64_t>(L->nJ, 1)) == cudaSuccess &&
+              cudaMalloc(&L->d_report, sizeof(unsigned long long) * 16) == cudaSuccess;
+    if (!ok) { p2s_learned_plan_destroy(L); return fail(P2S_ERR_OOM, "p2s_learned_plan_create: device allocation"); }
+    if (L->nJ) {
+        cudaError_t ce = cudaMemcpy(L->d_jidx, jidx.data(), sizeof(int32_t) * L->nJ, cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess) ce = cudaMemcpy(L->d_off_main, off_main.data(), sizeof(int64_t) * (L->nJ + 1), cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess) ce = cudaMemcpy(L->d_off_j, off_j.data(), sizeof(int64_t) * (L->nJ + 1), cudaMemcpyHostToDevice);
+        if (ce != cudaSuccess) { p2s_learned_plan_destroy(L); return fail(P2S_ERR_CUDA, "p2s_learned_plan_create: upload", ce); }
+    }
+    *out = L;
+    return P2S_OK;
+}
+
+int64_t p2s_learned_plan_output_entries(const p2s_learned_plan* L) {
+    return L ? p2s_plan_output_entries(L->main) : P2S_ERR_ARG;
+}
+
+int p2s_learned_fill(p2s_learned_plan* L, const p2s_geometry* geom, const p2s_material* mat, const float* params,
+                     double* out, int32_t* npts_out, void* stream) {
+    if (!L || !geom || !mat || !params) return fail(P2S_ERR_ARG, "p2s_learned_fill: NULL argument");
+    if (geom->n_elem != L->E) return fail(P2S_ERR_ARG, "p2s_learned_fill: n_elem differs from the plan");
+    if (mat->kind != P2S_ALPHA_METRIC_EPS) return fail(P2S_ERR_ARG, "p2s_learned_fill: needs the metric coupling kind");
+    const DeviceTables* T = context_tables(L->ctx);
+    P2S_LCUDA(cudaSetDevice(T->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    P2S_LCUDA(cudaMemsetAsync(L->d_report, 0, sizeof(unsigned long long) * 16, s));
+    if (L->E == 0) return P2S_OK;
+    int rc = p2s_coarse_features(L->ctx, geom, mat, L->d_feat, stream);
+    if (rc) return rc;
+    rc = p2s_mlp_predict(L->ctx, params, L->d_feat, L->E, L->margin, L->risk, L->d_npts, nullptr, stream);
+    if (rc) return rc;
+    const int gs = (int)std::min<int64_t>((L->E + 255) / 256, 1024);
+    k_set_npts<<<gs, 256, 0, s>>>(plan_desc(L->main), L->d_npts, L->E, L->d_report + 2);
+    P2S_LCUDA(cudaGetLastError());
+    if (npts_out) P2S_LCUDA(cudaMemcpyAsync(npts_out, L->d_npts, sizeof(int32_t) * L->E, cudaMemcpyDeviceToDevice, s));
+    rc = p2s_plan_fill(L->main, geom, mat, out, nullptr, stream);
+    if (rc) return rc;
+    if (L->nJ) {
+        double* jn = L->d_jin;
+        double* jb = jn + 24 * L->nJ;
+        double* jp = jb + 4 * L->nJ;
+        const int gj = (int)std::min<int64_t>(L->nJ, 4096);
+        k_gather_inputs<<<gj, 32, 0, s>>>(geom->nodes, geom->bulge, mat->params, L->d_jidx, L->nJ, jn, jb, jp);
+        P2S_LCUDA(cudaGetLastError());
+        p2s_geometry g2 = {L->nJ, jn, jb};
+        p2s_material m2 = {P2S_ALPHA_METRIC_EPS, jp};
+        rc = p2s_plan_fill(L->judge, &g2, &m2, L->d_jout, nullptr, stream);
+        if (rc) return rc;
+        rc = p2s_element_errors(L->ctx, out, L->d_off_main, L->d_jout, L->d_off_j, L->nJ, 4, L->d_jerr, stream);
+        if (rc) return rc;
+        k_judge_fix<<<gj, 256, 0, s>>>(out, L->d_off_main, L->d_jout, L->d_off_j, L->d_jerr, L->nJ, L->tol, L->d_report);
+        P2S_LCUDA(cudaGetLastError());
+    }
+    return P2S_OK;
+}
+
+int p2s_learned_report_get(p2s_learned_plan* L, p2s_learned_report* rep, int8_t* judge_state, void* stream) {
+    if (!L || !rep) return fail(P2S_ERR_ARG, "p2s_learned_report_get: NULL argument");
+    P2S_LCUDA(cudaSetDevice(context_tables(L->ctx)->device));
+    P2S_LCUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    unsigned long long h[16];
+    P2S_LCUDA(cudaMemcpy(h, L->d_report, sizeof(h), cudaMemcpyDeviceToHost));
+    rep->n_elem = L->E;
+    rep->judged = (int64_t)h[0];
+    rep->failed = (int64_t)h[1];
+    for (int c = 0; c < kC; ++c) rep->per_class[c] = (int64_t)h[2 + c];
+    long long bits = (long long)h[8];
+    std::memcpy(&rep->max_judged_err, &bits, sizeof(double));
+    if (judge_state) {
+        std::memset(judge_state, 0, (size_t)L->E);
+        if (L->nJ) {
+            std::vector<int32_t> idx((size_t)L->nJ);
+            std::vector<double> err((size_t)L->nJ);
+            P2S_LCUDA(cudaMemcpy(idx.data(), L->d_jidx, sizeof(int32_t) * L->nJ, cudaMemcpyDeviceToHost));
+            P2S_LCUDA(cudaMemcpy(err.data(), L->d_jerr, sizeof(double) * L->nJ, cudaMemcpyDeviceToHost));
+            for (int64_t k = 0; k < L->nJ; ++k) judge_state[idx[k]] = (err[k] <= L->tol) ? 1 : 2;
+        }
+    }
+    return P2S_OK;
+}
+
+}  // extern "C"

@@ -181,7 +181,10 @@ int run_contract(const DeviceTables& T, const PlanLayout& L, const ElemDesc* d_d
                  unsigned long long* d_counter, const void* moments, double* out, cudaStream_t s);
 }  // namespace p2s
 struct p2s_ctx;
+struct p2s_plan;
 namespace p2s {
 const DeviceTables* context_tables(const p2s_ctx* c);
+ElemDesc* plan_desc(p2s_plan* p);
+cudaError_t learned_init_attributes();
 
 }  // namespace p2s

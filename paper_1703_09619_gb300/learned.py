@@ -1,0 +1,177 @@
+"""Learned quadrature order: labels, training and inference driven through the library.
+
+Every numerical step runs in libp2s kernels (fills, per-element errors, coarse features,
+network forward/backward, Adam); this module only sequences them and keeps checkpoints.
+
+Labels (generated by the method itself): for each training element, the smallest G in
+{8, 12, 16, 24, 32, 48} whose FP64 fill matches the element's 48-point FP64 fill to
+`tol` (max over product types of max|dM| / max|M|); elements that need the full rule get
+class 5 (48 points).
+"""
+from __future__ import annotations
+
+import json
+import os
+import time
+
+import numpy as np
+
+from . import p2s
+from . import workloads as W
+
+CLASS_NPTS = p2s.CLASS_NPTS
+LABEL_TOL = 1e-10
+CHECKPOINT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "mlp_c5.npz")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def init_params(seed=0):
+    """He-uniform initial weights, zero biases, in the library's parameter layout."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_in, fan_out in ((p2s.MLP_IN, p2s.MLP_HIDDEN), (p2s.MLP_HIDDEN, p2s.MLP_HIDDEN),
+                            (p2s.MLP_HIDDEN, p2s.MLP_CLASSES)):
+        lim = np.sqrt(6.0 / fan_in)
+        parts.append(rng.uniform(-lim, lim, size=fan_in * fan_out))
+        parts.append(np.zeros(fan_out))
+    p = np.concatenate(parts).astype(np.float32)
+    assert p.size == p2s.MLP_PARAMS
+    return p
+
+
+def features(ctx, wl, device="cuda"):
+    """Coarse features [E][576] of a three-component metric workload (device tensor)."""
+    torch = _torch()
+    params, nodes, bulge = p2s.device_inputs(wl, device)
+    f = torch.empty((wl.n_elem, p2s.MLP_IN), dtype=torch.float32, device=device)
+    p2s.coarse_features(ctx, wl.kind, params, nodes, bulge, f)
+    return f
+
+
+def class_errors(ctx, wl, chunk=2048, device="cuda"):
+    """err[c][e]: relative difference of the FP64 fill at CLASS_NPTS[c] from the 48-point fill."""
+    torch = _torch()
+    E = wl.n_elem
+    err = np.zeros((len(CLASS_NPTS), E))
+    for s in range(0, E, chunk):
+        sub = wl.subset(np.arange(s, min(E, s + chunk)))
+        params, nodes, bulge = p2s.device_inputs(sub, device)
+        n, off = p2s.output_entries(sub.orders, offsets=True)
+        off_d = torch.as_tensor(off, device=device)
+        ref = torch.empty(n, dtype=torch.float64, device=device)
+        cur = torch.empty(n, dtype=torch.float64, device=device)
+        e_d = torch.empty(sub.n_elem, dtype=torch.float64, device=device)
+        plan = p2s.Plan(ctx, sub.orders, CLASS_NPTS[-1], p2s.FP64)
+        plan.fill(sub.kind, params, nodes, bulge, ref)
+        plan.close()
+        for c, G in enumerate(CLASS_NPTS[:-1]):
+            plan = p2s.Plan(ctx, sub.orders, G, p2s.FP64)
+            plan.fill(sub.kind, params, nodes, bulge, cur)
+            p2s.element_errors(ctx, cur, off_d, ref, off_d, 4, e_d)
+            err[c, s:s + sub.n_elem] = e_d.cpu().numpy()
+            plan.close()
+        del ref, cur
+    return err
+
+
+def labels_from_errors(err, tol=LABEL_TOL):
+    ok = err <= tol
+    ok[-1, :] = True
+    return np.argmax(ok, axis=0).astype(np.int32)
+
+
+def train(ctx, feats, labels, epochs=300, batch=512, lr=2e-3, class_weight=None, seed=0, params=None,
+          log_every=0, weight_decay=0.0):
+    """Adam training with the library's gradient and update kernels; returns FP32 params (numpy)."""
+    torch = _torch()
+    dev = feats.device
+    P = torch.as_tensor(init_params(seed) if params is None else params, dtype=torch.float32, device=dev).clone()
+    m = torch.zeros_like(P)
+    v = torch.zeros_like(P)
+    g = torch.zeros_like(P)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    y = torch.as_tensor(labels, dtype=torch.int32, device=dev)
+    cw = None if class_weight is None else torch.as_tensor(class_weight, dtype=torch.float32, device=dev)
+    n = feats.shape[0]
+    rng = np.random.default_rng(seed + 1)
+    step = 0
+    history = []
+    for ep in range(epochs):
+        perm = torch.as_tensor(rng.permutation(n), device=dev)
+        Xp = feats[perm].contiguous()
+        yp = y[perm].contiguous()
+        tot = 0.0
+        for b0 in range(0, n, batch):
+            xb, yb = Xp[b0:b0 + batch], yp[b0:b0 + batch]
+            p2s.mlp_grad(ctx, P, xb, yb, g, loss, cw)
+            step += 1
+            p2s.mlp_adam(P, g, m, v, lr, step, weight_decay=weight_decay)
+            tot += float(loss.item()) * xb.shape[0]
+        history.append(tot / n)
+        if log_every and (ep % log_every == 0 or ep == epochs - 1):
+            print("epoch %d loss %.4f" % (ep, tot / n), flush=True)
+    return P.cpu().numpy(), history
+
+
+def predict(ctx, params, feats, margin=0, risk=0.0):
+    torch = _torch()
+    P = torch.as_tensor(params, dtype=torch.float32, device=feats.device)
+    npts = torch.empty(feats.shape[0], dtype=torch.int32, device=feats.device)
+    p2s.mlp_predict(ctx, P, feats, npts, margin, risk=risk)
+    return npts.cpu().numpy()
+
+
+def classes_of(npts):
+    lut = {g: c for c, g in enumerate(CLASS_NPTS)}
+    return np.array([lut[int(g)] for g in npts], dtype=np.int32)
+
+
+def save(path, params, meta):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    np.savez(path, params=np.asarray(params, dtype=np.float32), meta=json.dumps(meta))
+
+
+def load_checkpoint(path=CHECKPOINT):
+    d = np.load(path, allow_pickle=False)
+    return d["params"].astype(np.float32), json.loads(str(d["meta"]))
+
+
+def train_default(ctx, n_train=65536, epochs=60, seed=0, verbose=False):
+    """Labels on the seeded training set (the c5 recipe, its own seed) and a trained network."""
+    t0 = time.time()
+    wl = W.make("c5train", n_train)
+    err = class_errors(ctx, wl)
+    y = labels_from_errors(err)
+    t1 = time.time()
+    X = features(ctx, wl)
+    params, hist = train(ctx, X, y, epochs=epochs, batch=1024, lr=2e-3, seed=seed, log_every=20 if verbose else 0,
+                         weight_decay=1e-3)
+    t2 = time.time()
+    pred = classes_of(predict(ctx, params, X))
+    meta = {"n_train": int(n_train), "epochs": int(epochs), "label_tol": LABEL_TOL,
+            "label_hist": np.bincount(y, minlength=6).tolist(), "train_acc": float((pred == y).mean()),
+            "train_under": float((pred < y).mean()), "final_loss": float(hist[-1]),
+            "label_seconds": t1 - t0, "train_seconds": t2 - t1}
+    return params, meta
+
+
+def ensure_trained(ctx, path=CHECKPOINT, verbose=False):
+    """Load the committed checkpoint, or train one and save it."""
+    if os.path.exists(path):
+        return load_checkpoint(path)
+    params, meta = train_default(ctx, verbose=verbose)
+    save(path, params, meta)
+    return params, meta
+
+
+if __name__ == "__main__":
+    import sys
+    ctx = p2s.Context(0)
+    params, meta = train_default(ctx, verbose=True)
+    out = sys.argv[1] if len(sys.argv) > 1 else CHECKPOINT
+    save(out, params, meta)
+    print(json.dumps(meta))

@@ -84,7 +84,34 @@ SIGNATURES = {
     "p2s_gauss_legendre": (ctypes.c_int, [ctypes.c_int, _P, _P]),
     "p2s_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "p2s_last_error": (ctypes.c_char_p, []),
+    "p2s_learned_npts": (ctypes.c_int, [ctypes.c_int]),
+    "p2s_coarse_features": (ctypes.c_int, [_P, ctypes.POINTER(Geometry), ctypes.POINTER(Material), _P, _P]),
+    "p2s_mlp_predict": (ctypes.c_int, [_P, _P, _P, _I64, ctypes.c_int, ctypes.c_float, _P, _P, _P]),
+    "p2s_mlp_grad": (ctypes.c_int, [_P, _P, _P, _P, _I64, _P, _P, _P, _P]),
+    "p2s_mlp_adam": (ctypes.c_int, [_P, _P, _P, _P, _I64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_float, ctypes.c_float, ctypes.c_int, _P]),
+    "p2s_element_errors": (ctypes.c_int, [_P, _P, _P, _P, _P, _I64, ctypes.c_int, _P, _P]),
+    "p2s_judge_select": (ctypes.c_int, [_I64, ctypes.c_double, ctypes.c_uint64, _P]),
+    "p2s_learned_plan_create": (ctypes.c_int, [_P, _I64, ctypes.POINTER(Orders), _P, ctypes.POINTER(ctypes.c_void_p)]),
+    "p2s_learned_plan_destroy": (None, [_P]),
+    "p2s_learned_plan_output_entries": (_I64, [_P]),
+    "p2s_learned_fill": (ctypes.c_int, [_P, ctypes.POINTER(Geometry), ctypes.POINTER(Material), _P, _P, _P, _P]),
+    "p2s_learned_report_get": (ctypes.c_int, [_P, _P, _P, _P]),
 }
+
+MLP_IN, MLP_HIDDEN, MLP_CLASSES, MLP_PARAMS = 576, 64, 6, 41478
+CLASS_NPTS = (8, 12, 16, 24, 32, 48)
+
+
+class LearnedOpts(ctypes.Structure):
+    _fields_ = [("margin", ctypes.c_int), ("risk", ctypes.c_double), ("precision", ctypes.c_int),
+                ("judge_frac", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("judge_tol", ctypes.c_double)]
+
+
+class LearnedReport(ctypes.Structure):
+    _fields_ = [("n_elem", ctypes.c_int64), ("judged", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("per_class", ctypes.c_int64 * 6), ("max_judged_err", ctypes.c_double)]
 
 
 def load():
@@ -301,3 +328,87 @@ def device_inputs(workload, device="cuda"):
     import torch
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=device)
     return t(workload.params), t(workload.nodes), t(workload.bulge)
+
+
+# ------------------------------------------------------------------ learned quadrature order
+def coarse_features(ctx: Context, kind, params, nodes, bulge, features, stream=None):
+    g = Geometry(int(params.shape[0]), _dptr(nodes), _dptr(bulge))
+    m = Material(int(kind), _dptr(params))
+    _check(load().p2s_coarse_features(ctx.handle, ctypes.byref(g), ctypes.byref(m), _dptr(features),
+                                      _stream(stream)), "p2s_coarse_features")
+
+
+def mlp_predict(ctx: Context, mlp_params, features, npts, margin=0, logits=None, risk=0.0, stream=None):
+    n = int(features.shape[0])
+    _check(load().p2s_mlp_predict(ctx.handle, _dptr(mlp_params), _dptr(features), n, int(margin), float(risk),
+                                  _dptr(npts), _dptr(logits), _stream(stream)), "p2s_mlp_predict")
+
+
+def mlp_grad(ctx: Context, mlp_params, features, labels, grad, loss, class_weight=None, stream=None):
+    n = int(features.shape[0])
+    _check(load().p2s_mlp_grad(ctx.handle, _dptr(mlp_params), _dptr(features), _dptr(labels), n,
+                               _dptr(class_weight), _dptr(grad), _dptr(loss), _stream(stream)), "p2s_mlp_grad")
+
+
+def mlp_adam(mlp_params, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, stream=None):
+    _check(load().p2s_mlp_adam(_dptr(mlp_params), _dptr(grad), _dptr(m), _dptr(v), int(mlp_params.numel()),
+                               float(lr), float(beta1), float(beta2), float(eps), float(weight_decay), int(step),
+                               _stream(stream)), "p2s_mlp_adam")
+
+
+def element_errors(ctx: Context, a, offsets_a, b, offsets_b, n_types, err, stream=None):
+    n = int(err.shape[0])
+    _check(load().p2s_element_errors(ctx.handle, _dptr(a), _dptr(offsets_a), _dptr(b), _dptr(offsets_b), n,
+                                     int(n_types), _dptr(err), _stream(stream)), "p2s_element_errors")
+
+
+def judge_select(n_elem, frac, seed):
+    out = np.zeros(max(int(n_elem), 1), dtype=np.int8)
+    _check(load().p2s_judge_select(int(n_elem), float(frac), ctypes.c_uint64(int(seed)), _hptr(out)),
+           "p2s_judge_select")
+    return out[: int(n_elem)].astype(bool)
+
+
+class LearnedPlan:
+    """A p2s_learned_plan: learned-order fill with its seeded 48-point FP64 judge."""
+
+    def __init__(self, ctx: Context, orders, margin=0, precision=MIXED, judge_frac=0.02, seed=1, judge_tol=1e-9,
+                 risk=0.0):
+        lib = load()
+        self.ctx = ctx
+        o, self._orders = _orders_struct(orders)
+        self.n_elem = int(self._orders.shape[0])
+        opts = LearnedOpts(int(margin), float(risk), int(precision), float(judge_frac), int(seed), float(judge_tol))
+        h = ctypes.c_void_p()
+        _check(lib.p2s_learned_plan_create(ctx.handle, self.n_elem, ctypes.byref(o), ctypes.byref(opts),
+                                           ctypes.byref(h)), "p2s_learned_plan_create")
+        self.handle = h
+        self.output_entries = int(lib.p2s_learned_plan_output_entries(h))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().p2s_learned_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def fill(self, kind, params, nodes, bulge, mlp_params, out, npts_out=None, stream=None):
+        g = Geometry(int(params.shape[0]), _dptr(nodes), _dptr(bulge))
+        m = Material(int(kind), _dptr(params))
+        _check(load().p2s_learned_fill(self.handle, ctypes.byref(g), ctypes.byref(m), _dptr(mlp_params), _dptr(out),
+                                       _dptr(npts_out), _stream(stream)), "p2s_learned_fill")
+
+    def report(self, stream=None, judge_state=False):
+        rep = LearnedReport()
+        js = np.zeros(max(self.n_elem, 1), dtype=np.int8) if judge_state else None
+        _check(load().p2s_learned_report_get(self.handle, ctypes.byref(rep), _hptr(js), _stream(stream)),
+               "p2s_learned_report_get")
+        d = {"n_elem": rep.n_elem, "judged": rep.judged, "failed": rep.failed,
+             "per_class": list(rep.per_class), "max_judged_err": rep.max_judged_err}
+        if judge_state:
+            d["judge_state"] = js[: self.n_elem]
+        return d

@@ -116,8 +116,23 @@ def make(name: str, n_elem: int | None = None) -> Workload:
 
     Elements are always drawn for the full workload size and then truncated,
     so element e is the same whatever ``n_elem`` is."""
-    cid = {"c1": 1, "c2": 2, "c3": 3, "c4": 4, "c5": 5}[name]
+    cid = {"c1": 1, "c2": 2, "c3": 3, "c4": 4, "c5": 5, "c5train": 50}[name]
     rng = np.random.default_rng(SEED_BASE + cid)
+    if cid == 50:  # training elements for the learned order: the c5 recipe, its own seed
+        E = 65536
+        nodes, bulge = curved_geometry(rng, E)
+        kmag = np.exp(rng.uniform(np.log(1.0), np.log(40.0), E))
+        d = unit_vectors(rng, E)
+        params = np.zeros((E, 4))
+        params[:, 0] = 0.8
+        params[:, 1:] = kmag[:, None] * d
+        orders = np.full((E, 3, 3), 4, dtype=np.int32)
+        w = Workload(name, E, 3, orders, KIND_METRIC_EPS, params, nodes, bulge, np.full(E, 48, np.int32),
+                     description="65536 training hexahedra, the c5 recipe with its own seed")
+        if n_elem is not None and n_elem < w.n_elem:
+            w = w.subset(np.arange(n_elem))
+            w.name = name
+        return w
     if cid == 1:
         E = 1
         orders = np.full((E, 1, 3), 4, dtype=np.int32)

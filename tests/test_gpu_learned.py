@@ -1,0 +1,196 @@
+"""GPU checks of the learned quadrature order: features, network kernels, labels, judge."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp
+from paper_1703_09619_gb300 import learned as LN
+from paper_1703_09619_gb300 import p2s
+from paper_1703_09619_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def ctx(torch):
+    c = p2s.Context(0)
+    yield c
+    c.close()
+
+
+def test_features_match_oracle_alpha(torch, ctx):
+    """576 features = alpha at the 4-point Gauss-Legendre grid / mean(trace(alpha)/3)."""
+    wl = W.make("c5", 6)
+    f = LN.features(ctx, wl).cpu().numpy()
+    x4, _ = oracle.gauss_legendre(4)
+    for e in range(wl.n_elem):
+        vals = np.zeros((64, 9))
+        for c in range(4):
+            for b in range(4):
+                for a in range(4):
+                    al, _ = oracle.alpha_point(oracle.ALPHA_METRIC_EPS, wl.params[e], wl.nodes[e], wl.bulge[e],
+                                               x4[a], x4[b], x4[c])
+                    vals[(c * 4 + b) * 4 + a] = al.reshape(9)
+        ref = vals / (np.trace(vals.reshape(64, 3, 3), axis1=1, axis2=2).mean() / 3.0)
+        assert np.max(np.abs(f[e] - ref.reshape(-1))) < 2e-6 * np.abs(ref).max()
+
+
+def random_params(seed):
+    rng = np.random.default_rng(seed)
+    p = LN.init_params(seed).astype(np.float64)
+    p += rng.normal(0, 0.02, p.size)
+    return p.astype(np.float32)
+
+
+def test_gradient_matches_oracle(torch, ctx):
+    wl = W.make("c5", 77)
+    X = LN.features(ctx, wl)
+    rng = np.random.default_rng(4)
+    y = rng.integers(0, 6, wl.n_elem).astype(np.int32)
+    cw = np.array([1.0, 1.5, 2.0, 1.0, 0.7, 3.0], dtype=np.float32)
+    P = random_params(1)
+    Pd = torch.as_tensor(P, device="cuda")
+    g = torch.zeros_like(Pd)
+    loss = torch.zeros(1, device="cuda")
+    p2s.mlp_grad(ctx, Pd, X, torch.as_tensor(y, device="cuda"), g, loss, torch.as_tensor(cw, device="cuda"))
+    ref_loss, ref_g = mlp.loss_and_grad(P.astype(np.float64), X.cpu().numpy(), y, cw)
+    gg = g.cpu().numpy()
+    assert abs(loss.item() - ref_loss) < 1e-4 * abs(ref_loss)
+    scale = np.abs(ref_g).max()
+    assert np.max(np.abs(gg - ref_g)) < 1e-4 * scale, np.max(np.abs(gg - ref_g)) / scale
+    # bias gradients exactly in layout order
+    assert np.max(np.abs(gg[-6:] - ref_g[-6:])) < 1e-5 * max(1e-3, np.abs(ref_g[-6:]).max())
+
+
+def test_predict_matches_oracle_argmax_and_margin(torch, ctx):
+    wl = W.make("c5", 300)
+    X = LN.features(ctx, wl)
+    P = random_params(2)
+    Pd = torch.as_tensor(P, device="cuda")
+    npts = torch.empty(wl.n_elem, dtype=torch.int32, device="cuda")
+    logits = torch.empty((wl.n_elem, 6), dtype=torch.float32, device="cuda")
+    p2s.mlp_predict(ctx, Pd, X, npts, 0, logits)
+    _, _, Z = mlp.forward(P.astype(np.float64), X.cpu().numpy())
+    assert np.max(np.abs(logits.cpu().numpy() - Z)) < 1e-3 * max(1.0, np.abs(Z).max())
+    srt = np.sort(Z, axis=1)
+    clear = srt[:, -1] - srt[:, -2] > 1e-3
+    cls = LN.classes_of(npts.cpu().numpy())
+    assert (cls[clear] == Z.argmax(axis=1)[clear]).all()
+    p2s.mlp_predict(ctx, Pd, X, npts, 2)
+    cls2 = LN.classes_of(npts.cpu().numpy())
+    assert (cls2[clear] == np.minimum(Z.argmax(axis=1)[clear] + 2, 5)).all()
+
+
+def test_adam_update(torch, ctx):
+    rng = np.random.default_rng(5)
+    n = 1000
+    p = rng.normal(size=n).astype(np.float32)
+    g = rng.normal(size=n).astype(np.float32)
+    Pd, Gd = torch.as_tensor(p, device="cuda"), torch.as_tensor(g, device="cuda")
+    m, v = torch.zeros_like(Pd), torch.zeros_like(Pd)
+    for step in (1, 2):
+        p2s.mlp_adam(Pd, Gd, m, v, 1e-2, step)
+    # two Adam steps with the same gradient, from zero moments (Kingma & Ba, Algorithm 1)
+    mm, vv, pp = np.zeros(n), np.zeros(n), p.astype(np.float64)
+    for t in (1, 2):
+        mm = 0.9 * mm + 0.1 * g
+        vv = 0.999 * vv + 0.001 * g.astype(np.float64) ** 2
+        pp -= 1e-2 * (mm / (1 - 0.9 ** t)) / (np.sqrt(vv / (1 - 0.999 ** t)) + 1e-8)
+    assert np.max(np.abs(Pd.cpu().numpy() - pp)) < 1e-5
+
+
+def test_element_errors(torch, ctx):
+    rng = np.random.default_rng(6)
+    sizes = [4 * 9, 4 * 64, 4 * 1, 4 * 100]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    b = rng.normal(size=off[-1])
+    a = b + rng.normal(size=off[-1]) * 1e-9
+    err = torch.empty(len(sizes), dtype=torch.float64, device="cuda")
+    od = torch.as_tensor(off, device="cuda")
+    p2s.element_errors(ctx, torch.as_tensor(a, device="cuda"), od, torch.as_tensor(b, device="cuda"), od, 4, err)
+    for e, s in enumerate(sizes):
+        seg = s // 4
+        ref = max(np.abs(a[off[e] + t * seg:off[e] + (t + 1) * seg] - b[off[e] + t * seg:off[e] + (t + 1) * seg]).max() /
+                  np.abs(b[off[e] + t * seg:off[e] + (t + 1) * seg]).max() for t in range(4))
+        assert abs(err[e].item() - ref) <= 1e-15 * max(ref, 1e-300) + 1e-300
+
+
+def test_labels_against_oracle(torch, ctx):
+    """The label criterion computed by the GPU fills equals the oracle's for one element at
+    G = 8 and 16 (direct triple sums at G and at 48 points)."""
+    wl = W.make("c5train", 64)
+    err = LN.class_errors(ctx, wl, chunk=64)
+    # the element with the largest |k| among the first 64: it needs more than 8 points
+    e = int(np.argmax(np.linalg.norm(wl.params[:, 1:], axis=1)))
+    sub = wl.subset([e])
+    ref48, off, _ = oracle.fill(sub.orders, sub.kind, sub.params, sub.nodes, sub.bulge, 48)
+    for c, G in ((0, 8), (2, 16)):
+        rG, _, _ = oracle.fill(sub.orders, sub.kind, sub.params, sub.nodes, sub.bulge, G)
+        mG = oracle.element_matrices(rG, off, sub.orders, 0)
+        m48 = oracle.element_matrices(ref48, off, sub.orders, 0)
+        ref = max(np.abs(mG[t] - m48[t]).max() / np.abs(m48[t]).max() for t in m48)
+        assert abs(err[c, e] - ref) <= 1e-3 * ref + 1e-13, (G, err[c, e], ref)
+    assert err[0, e] > 1e-10
+
+
+def test_judge_replaces_planted_mispredictions(torch, ctx):
+    """A network planted to always answer G = 8: judged elements that miss the tolerance
+    are replaced by their 48-point FP64 fill, the others keep the 8-point fill."""
+    wl = W.make("c5", 120)
+    params, nodes, bulge = p2s.device_inputs(wl)
+    P = np.zeros(p2s.MLP_PARAMS, dtype=np.float32)
+    P[-6] = 10.0  # bias of class 0
+    Pd = torch.as_tensor(P, device="cuda")
+    lp = p2s.LearnedPlan(ctx, wl.orders, margin=0, precision=p2s.MIXED, judge_frac=0.5, seed=3, judge_tol=1e-9)
+    out = torch.empty(lp.output_entries, dtype=torch.float64, device="cuda")
+    npts = torch.empty(wl.n_elem, dtype=torch.int32, device="cuda")
+    lp.fill(wl.kind, params, nodes, bulge, Pd, out, npts)
+    rep = lp.report(judge_state=True)
+    st = rep["judge_state"]
+    assert (npts.cpu().numpy() == 8).all()
+    assert rep["per_class"][0] == wl.n_elem
+    assert rep["judged"] == int((st > 0).sum()) and rep["failed"] == int((st == 2).sum())
+    assert rep["judged"] == int(p2s.judge_select(wl.n_elem, 0.5, 3).sum())
+    assert rep["failed"] > 0
+    ref48 = torch.empty_like(out)
+    p2s.Plan(ctx, wl.orders, 48, p2s.FP64).fill(wl.kind, params, nodes, bulge, ref48)
+    ref8 = torch.empty_like(out)
+    p2s.Plan(ctx, wl.orders, 8, p2s.MIXED).fill(wl.kind, params, nodes, bulge, ref8)
+    torch.cuda.synchronize()
+    n, off = p2s.output_entries(wl.orders, offsets=True)
+    o, r48, r8 = out.cpu().numpy(), ref48.cpu().numpy(), ref8.cpu().numpy()
+    for e in range(wl.n_elem):
+        sl = slice(off[e], off[e + 1])
+        if st[e] == 2:
+            assert np.array_equal(o[sl], r48[sl])
+        else:
+            assert np.array_equal(o[sl], r8[sl])
+    lp.close()
+
+
+def test_training_gains_over_full_order(torch, ctx):
+    """Train on 4096 method-labelled elements, predict on 1024 held-out c5 elements: most
+    predictions are right or conservative, and the learned rule uses far fewer points."""
+    tr = W.make("c5train", 4096)
+    y = LN.labels_from_errors(LN.class_errors(ctx, tr))
+    X = LN.features(ctx, tr)
+    params, hist = LN.train(ctx, X, y, epochs=60, batch=512, lr=3e-3)
+    assert hist[-1] < hist[0]
+    te = W.make("c5", 1024)
+    yt = LN.labels_from_errors(LN.class_errors(ctx, te))
+    pred = LN.classes_of(LN.predict(ctx, params, LN.features(ctx, te)))
+    acc = (pred == yt).mean()
+    under = (pred < yt).mean()
+    g_learn = np.array(LN.CLASS_NPTS)[pred].astype(float)
+    work_ratio = (48.0 ** 3) / np.mean(g_learn ** 3)
+    assert acc > 0.5, acc
+    assert under < 0.25, under
+    assert work_ratio > 3.0, work_ratio
