@@ -9,9 +9,12 @@
 
 namespace p2s {
 cudaError_t moments_init_attributes();
+cudaError_t moments_dw_init_attributes();
 cudaError_t contract_init_attributes();
 cudaError_t init_kernel_attributes() {
     cudaError_t e = moments_init_attributes();
+    if (e != cudaSuccess) return e;
+    e = moments_dw_init_attributes();
     if (e != cudaSuccess) return e;
     return contract_init_attributes();
 }
@@ -241,14 +244,19 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
     L.n_units = units.n;
 
     // moments launch shape: the accumulator takes what shared memory leaves, at least one pair
-    size_t base = moments_smem_bytes(L.n_pairs, L.kb, L.gmax, 0);
+    // the mixed path evaluates alpha and the moments in double-word arithmetic (moments_dw.cu)
+    const bool dwm = L.precision == P2S_MIXED;
+    auto msmem = [&](int cap) {
+        return dwm ? moments_dw_smem_bytes(L.n_pairs, L.kb, L.gmax, cap) : moments_smem_bytes(L.n_pairs, L.kb, L.gmax, cap);
+    };
+    size_t base = msmem(0);
     size_t limit = std::min<size_t>(T.smem_optin, 227 * 1024) - 1024;  // room for static shared memory
     if (base + sizeof(double) * max_pair > limit) return fail(P2S_ERR_ORDER, "plan: moment accumulator too large");
     L.iacc_cap = (int)std::min<size_t>((limit - base) / sizeof(double), (size_t)max_elem_mom);
     size_t half = limit / 2 - 1024;  // two CTAs per SM when everything fits in half
     if (base + sizeof(double) * max_elem_mom <= half) L.iacc_cap = max_elem_mom;
-    L.mom_smem = moments_smem_bytes(L.n_pairs, L.kb, L.gmax, L.iacc_cap);
-    int per_sm = moments_blocks_per_sm(L.mom_smem);
+    L.mom_smem = msmem(L.iacc_cap);
+    int per_sm = dwm ? moments_dw_blocks_per_sm(L.mom_smem) : moments_blocks_per_sm(L.mom_smem);
     if (per_sm < 1) return fail(P2S_ERR_ORDER, "plan: moment kernel does not fit");
     L.mom_grid = (int)std::max<int64_t>(1, std::min<int64_t>(E, (int64_t)T.sm_count * per_sm));
 
@@ -330,7 +338,10 @@ int run_moments(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_d
     M.gmax = PL.gmax;
     M.iacc_cap = PL.iacc_cap;
     M.out_ff = PL.precision == P2S_MIXED;
-    P2S_CUDA(launch_moments_fp64(M, PL.mom_grid, PL.mom_smem, s));
+    if (M.out_ff)
+        P2S_CUDA(launch_moments_dw(M, PL.mom_grid, PL.mom_smem, s));
+    else
+        P2S_CUDA(launch_moments_fp64(M, PL.mom_grid, PL.mom_smem, s));
     return P2S_OK;
 }
 

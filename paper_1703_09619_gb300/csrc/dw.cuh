@@ -1,0 +1,144 @@
+// Double-word ("float-float") arithmetic: a value is hi + lo with two FP32 words.
+//
+// Building blocks (exact transformations of FP32 operations):
+//   TwoSum (Knuth), Fast2Sum (Dekker, |a| >= |b|), TwoProd with FMA.
+// Composite operations follow Joldes, Muller and Popescu, "Tight and rigorous error bounds
+// for basic building blocks of double-word arithmetic", ACM TOMS 44(2), 2017:
+//   add   - AccurateDWPlusDW (relative error <= 3u^2 + 13u^3, u = 2^-24),
+//   mul   - DWTimesDW with FMA (the 2 FMA variant, error <= 5u^2),
+//   div   - a Newton correction of the FP32 quotient,
+// which keep about 44 significant bits.  FP64 appears only in the conversions at the
+// boundaries (dw_from_double), which kernels do once per element, not per point.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace p2s {
+
+struct dw {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dw dw_make(float hi, float lo) { return dw{hi, lo}; }
+__device__ __forceinline__ dw dw_from_float(float x) { return dw{x, 0.f}; }
+__device__ __forceinline__ dw dw_from_double(double x) {
+    const float h = (float)x;
+    return dw{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double dw_to_double(dw x) { return (double)x.hi + (double)x.lo; }
+
+__device__ __forceinline__ dw two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return dw{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dw fast_two_sum(float a, float b) {
+    const float s = a + b;
+    return dw{s, b - (s - a)};
+}
+__device__ __forceinline__ dw two_prod(float a, float b) {
+    const float p = a * b;
+    return dw{p, fmaf(a, b, -p)};
+}
+
+__device__ __forceinline__ dw dw_add(dw x, dw y) {
+    const dw s = two_sum(x.hi, y.hi);
+    const dw t = two_sum(x.lo, y.lo);
+    const dw v = fast_two_sum(s.hi, s.lo + t.hi);
+    return fast_two_sum(v.hi, t.lo + v.lo);
+}
+__device__ __forceinline__ dw dw_neg(dw x) { return dw{-x.hi, -x.lo}; }
+__device__ __forceinline__ dw dw_sub(dw x, dw y) { return dw_add(x, dw_neg(y)); }
+__device__ __forceinline__ dw dw_add_f(dw x, float y) {
+    const dw s = two_sum(x.hi, y);
+    return fast_two_sum(s.hi, s.lo + x.lo);
+}
+__device__ __forceinline__ dw dw_mul(dw x, dw y) {
+    const dw p = two_prod(x.hi, y.hi);
+    const float e = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, p.lo));
+    return fast_two_sum(p.hi, e);
+}
+__device__ __forceinline__ dw dw_mul_f(dw x, float y) {
+    const dw p = two_prod(x.hi, y);
+    return fast_two_sum(p.hi, fmaf(x.lo, y, p.lo));
+}
+__device__ __forceinline__ dw dw_fma(dw x, dw y, dw z) { return dw_add(dw_mul(x, y), z); }
+__device__ __forceinline__ dw dw_div(dw x, dw y) {
+    const float q1 = __fdiv_rn(x.hi, y.hi);
+    const dw r = dw_sub(x, dw_mul_f(y, q1));  // remainder x - q1 y
+    const float q2 = __fdiv_rn(r.hi, y.hi);
+    const dw r2 = dw_sub(r, dw_mul_f(y, q2));
+    const float q3 = __fdiv_rn(r2.hi, y.hi);
+    const dw q = fast_two_sum(q1, q2);
+    return dw_add_f(q, q3);
+}
+
+// Accumulator for sums of products: the leading words sum with TwoSum, every rounding
+// error and lower-order product term goes to the second word; renormalise at the end.
+struct dw_acc {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void fma(dw a, dw b) {
+        const float p = a.hi * b.hi;
+        float e = fmaf(a.hi, b.hi, -p);
+        e = fmaf(a.hi, b.lo, e);
+        e = fmaf(a.lo, b.hi, e);
+        const float t = s + p;
+        const float bp = t - s;
+        c += ((s - (t - bp)) + (p - bp)) + e;
+        s = t;
+    }
+    __device__ __forceinline__ void add(dw a) {
+        const float t = s + a.hi;
+        const float bp = t - s;
+        c += ((s - (t - bp)) + (a.hi - bp)) + a.lo;
+        s = t;
+    }
+    __device__ __forceinline__ dw value() const { return fast_two_sum(s, c); }
+};
+
+// sin of a double-word argument |x| <= ~6e3.  Cody-Waite reduction by pi/2 with a
+// four-part constant (the first two parts have 12 significant bits, so n * part is exact
+// for |n| < 2^12), then Taylor polynomials on |r| <= pi/4 (the leading terms in
+// double-word, the tail, below 1e-3 in magnitude, in FP32).
+__device__ __forceinline__ dw dw_sin(dw x) {
+    // pi/2 = C1 + C2 + C3 + C4 (C1, C2 with 12 significant bits; C3, C4 FP32 roundings of the rest)
+    const float C1 = 1.57080078125f;
+    const float C2 = -4.4535845518112183e-06f;
+    const float C3 = -8.7055157527160532e-10f;
+    const float C4 = 5.721188916458728e-18f;
+    const float n = rintf(x.hi * 0.63661974668502808f);
+    // r = x - n (C1 + C2 + C3 + C4), n C1 and n C2 exact
+    dw r = dw_add_f(x, -n * C1);
+    r = dw_add_f(r, -n * C2);
+    r = dw_add(r, dw_neg(two_prod(n, C3)));
+    r = dw_add_f(r, -n * C4);
+    const dw z = dw_mul(r, r);
+    const int q = ((int)n) & 3;
+    dw res;
+    if (q & 1) {
+        // cos r = 1 - z/2 + z^2/24 - z^3/720 + z^4/40320 - z^5/3628800 + z^6/479001600 - ...
+        const float zf = z.hi;
+        float t = fmaf(zf, 2.08767569878680990e-9f, -2.75573192239858907e-7f);
+        t = fmaf(zf, t, 2.48015873015873016e-5f);
+        t = fmaf(zf, t, -1.38888888888888889e-3f);  // tail: z^2 (1/24 ...) handled below
+        // cos r = 1 - z/2 + z^2 (1/24 + z t)
+        const dw c24 = dw_make(0.041666667908430099f, -1.2417634698280722e-09f);  // 1/24
+        const dw w = dw_add_f(c24, zf * t);
+        const dw z2 = dw_mul(z, z);
+        res = dw_add(dw_add_f(dw_mul_f(z, -0.5f), 1.f), dw_mul(z2, w));
+    } else {
+        // sin r = r - r^3/6 + r^5/120 - r^7/5040 + r^9/362880 - r^11/39916800 + r^13/6227020800
+        const float zf = z.hi;
+        float t = fmaf(zf, 1.60590438368216146e-10f, -2.50521083854417188e-8f);
+        t = fmaf(zf, t, 2.75573192239858907e-6f);
+        t = fmaf(zf, t, -1.98412698412698413e-4f);
+        // sin r = r + r z (-1/6 + z (1/120 + z t))
+        const dw c120 = dw_make(0.0083333337679505348f, -4.3461720333759502e-10f);  // 1/120
+        const dw c6 = dw_make(-0.1666666716337204f, 4.9670538793122887e-09f);       // -1/6
+        const dw inner = dw_add(c6, dw_mul(z, dw_add_f(c120, zf * t)));
+        res = dw_add(r, dw_mul(dw_mul(r, z), inner));
+    }
+    return (q & 2) ? dw_neg(res) : res;
+}
+
+}  // namespace p2s

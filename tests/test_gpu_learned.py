@@ -27,10 +27,11 @@ def ctx(torch):
 
 
 def test_features_match_oracle_alpha(torch, ctx):
-    """576 features = alpha at the 4-point Gauss-Legendre grid / mean(trace(alpha)/3)."""
+    """576 features = alpha on the 4 x 4 x 4 grid with per-axis positions
+    {-0.9, -0.8, 0.35, 0.45} / mean(trace(alpha)/3)."""
     wl = W.make("c5", 6)
     f = LN.features(ctx, wl).cpu().numpy()
-    x4, _ = oracle.gauss_legendre(4)
+    x4 = np.array([-0.9, -0.8, 0.35, 0.45])
     for e in range(wl.n_elem):
         vals = np.zeros((64, 9))
         for c in range(4):

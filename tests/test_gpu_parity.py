@@ -161,6 +161,19 @@ def test_large_G_scalar(torch_cuda, ctx, prec):
     check(torch_cuda, ctx, wl.with_npts(64), precision=prec)
 
 
+@pytest.mark.parametrize("name,G", [("c5", 16), ("c5", 48), ("c2", 24), ("c3", 12)])
+def test_mixed_close_to_fp64(torch_cuda, ctx, name, G):
+    """The double-word coupling factor, moments and contraction stay within 1e-10 of the
+    FP64 path (the learned fill's judge compares at 1e-9); c5 includes |k| up to 40, so the
+    double-word sine sees phases up to about 70 rad."""
+    wl = W.make(name, 48).with_npts(G)
+    a, _, _ = gpu_fill(torch_cuda, ctx, wl, precision=p2s.FP64)
+    b, _, _ = gpu_fill(torch_cuda, ctx, wl, precision=p2s.MIXED)
+    off = oracle.output_offsets(wl.orders)
+    err = per_type_errors(b, a, off, wl.orders)
+    assert err.max() <= 1e-10, err.max()
+
+
 def test_empty_batch(torch_cuda, ctx):
     wl = W.make("c4", 1).subset([])
     plan = p2s.Plan(ctx, wl.orders, 4)
