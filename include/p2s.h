@@ -193,9 +193,9 @@ int p2s_fill_elements_noalloc(p2s_ctx* ctx, const p2s_geometry* geom, const p2s_
 /* ------------------------------------------------------------------------------------
  * Learned quadrature order.  Not part of the paper: a small network picks, per element,
  * the Gauss-Legendre size G of the fill (Eq. (2)-(4)); a seeded share of the elements is
- * re-filled at 48 points in FP64 (the plain method) to judge the choice, and judged
- * elements that miss the tolerance keep the 48-point fill.  Three-component metric
- * coupling only.
+ * re-filled at 48 points (in the learned fill's precision) to judge the choice, and judged
+ * elements that miss the tolerance are replaced by their 48-point FP64 fill (the plain
+ * method).  Three-component metric coupling only.
  *
  * Network: 576 inputs (alpha on the 4 x 4 x 4 grid with per-axis reference positions
  * {-0.9, -0.8, 0.35, 0.45}, all 9 factors alpha_{gi gj}, point index (c*4 + b)*4 + a,
@@ -264,15 +264,17 @@ typedef struct {
 } p2s_learned_report;
 
 /* Plan a learned fill of E elements (three components, host orders, all four types).
- * Allocates the fill's scratch, the judge subset and its 48-point FP64 plan. */
+ * Allocates the fill's scratch, the judge subset, its 48-point plan and its 48-point FP64
+ * fallback plan. */
 int p2s_learned_plan_create(p2s_ctx* ctx, int64_t n_elem, const p2s_orders* orders, const p2s_learned_opts* opts,
                             p2s_learned_plan** out);
 void p2s_learned_plan_destroy(p2s_learned_plan* plan);
 int64_t p2s_learned_plan_output_entries(const p2s_learned_plan* plan);
 
 /* Learned fill, asynchronous on `stream`: features, prediction, fill at the predicted G,
- * judge fill and comparison, replacement of failed judged elements.  npts_out (device
- * [E], optional) receives the G used per element before any replacement. */
+ * judge fill at 48 points and comparison, FP64 fill of the judged elements that failed and
+ * their replacement in `out`.  npts_out (device [E], optional) receives the G used per
+ * element before any replacement. */
 int p2s_learned_fill(p2s_learned_plan* plan, const p2s_geometry* geom, const p2s_material* mat, const float* params,
                      double* out, int32_t* npts_out, void* stream);
 

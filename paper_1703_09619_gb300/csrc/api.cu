@@ -309,7 +309,9 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
 }
 
 int run_moments(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_desc, const p2s_geometry* geom,
-                const p2s_material* mat, void* moments, int32_t* elem_status, cudaStream_t s) {
+                const p2s_material* mat, void* moments, int32_t* elem_status, cudaStream_t s,
+                const int8_t* elem_mask) {
+    if (elem_mask && PL.precision != P2S_FP64) return fail(P2S_ERR_ARG, "moments: element masks need an FP64 plan");
     if (!geom || !mat) return fail(P2S_ERR_ARG, "moments: NULL geometry or material");
     if (geom->n_elem != PL.n_elem) return fail(P2S_ERR_ARG, "moments: n_elem differs from the plan");
     if (PL.n_elem == 0) return P2S_OK;
@@ -338,6 +340,7 @@ int run_moments(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_d
     M.gmax = PL.gmax;
     M.iacc_cap = PL.iacc_cap;
     M.out_ff = PL.precision == P2S_MIXED;
+    M.elem_mask = elem_mask;
     if (M.out_ff)
         P2S_CUDA(launch_moments_dw(M, PL.mom_grid, PL.mom_smem, s));
     else
@@ -346,7 +349,10 @@ int run_moments(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_d
 }
 
 int run_contract(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_desc, const ContractUnit* d_units,
-                 unsigned long long* d_counter, const void* moments, double* out, cudaStream_t s) {
+                 unsigned long long* d_counter, const void* moments, double* out, cudaStream_t s,
+                 const int8_t* elem_mask) {
+    if (elem_mask && (PL.precision != P2S_FP64 || PL.spec_n))
+        return fail(P2S_ERR_ARG, "contract: element masks need an FP64 plan");
     if (PL.n_units == 0) return P2S_OK;
     if (!moments || !out) return fail(P2S_ERR_ARG, "contract: NULL moments or out");
     P2S_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), s));
@@ -363,6 +369,7 @@ int run_contract(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_
     C.a_cap = (int)PL.a_cap;
     C.b_cap = (int)PL.b_cap;
     C.tile_off = (int)PL.tile_off;
+    C.elem_mask = elem_mask;
     if (PL.spec_n)
         P2S_CUDA(launch_contract_ffn(PL.spec_n, C, PL.con_grid, PL.con_threads, PL.con_smem, s));
     else
@@ -601,4 +608,12 @@ int p2s_sync_status(p2s_ctx* ctx, void* stream) {
 namespace p2s {
 const DeviceTables* context_tables(const p2s_ctx* c) { return c ? &c->T : nullptr; }
 ElemDesc* plan_desc(p2s_plan* p) { return p ? p->d_desc : nullptr; }
+
+int plan_fill_masked(p2s_plan* p, const p2s_geometry* geom, const p2s_material* mat, double* out,
+                     const int8_t* mask, cudaStream_t s) {
+    if (!p) return fail(P2S_ERR_ARG, "plan_fill_masked: NULL plan");
+    int rc = run_moments(p->ctx->T, p->L, p->d_desc, geom, mat, p->d_mom, nullptr, s, mask);
+    if (rc) return rc;
+    return run_contract(p->ctx->T, p->L, p->d_desc, p->d_units, p->d_counter, p->d_mom, out, s, mask);
+}
 }  // namespace p2s

@@ -50,6 +50,10 @@ __global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
         }
         __syncthreads();
         if (unit_id >= (unsigned long long)L.n_units) break;
+        if (L.elem_mask && !L.elem_mask[cu.e]) {  // every thread reads cu before tid 0 refills it
+            __syncthreads();
+            continue;
+        }
         const ElemDesc* d = L.desc + cu.e;
         const int gi = cu.gi, gj = cu.gj, t = cu.t;
         const int m1a = cu.m1a, m1n = cu.m1n, n1a = cu.n1a, n1n = cu.n1n;

@@ -491,7 +491,13 @@ __global__ void k_gather_inputs(const double* __restrict__ nodes, const double* 
     }
 }
 
-// report: [0] judged, [1] failed, [2..7] per class, [8] max judged error (double bits)
+__global__ void k_judge_mask(const double* __restrict__ err, int64_t nJ, double tol, int8_t* __restrict__ mask) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nJ; k += (int64_t)gridDim.x * blockDim.x)
+        mask[k] = !(err[k] <= tol);
+}
+
+// report: [0] judged, [1] failed, [2..7] per class, [8] max judged error (double bits).
+// Judged elements whose check failed take their 48-point FP64 fill (jout).
 __global__ void k_judge_fix(double* __restrict__ out, const int64_t* __restrict__ off_main, const double* __restrict__ jout,
                             const int64_t* __restrict__ off_j, const double* __restrict__ err, int64_t nJ, double tol,
                             unsigned long long* report) {
@@ -518,7 +524,8 @@ __global__ void k_judge_fix(double* __restrict__ out, const int64_t* __restrict_
 struct p2s_learned_plan {
     p2s_ctx* ctx = nullptr;
     p2s_plan* main = nullptr;
-    p2s_plan* judge = nullptr;
+    p2s_plan* judge = nullptr;     // judged subset, the learned fill's precision at 48 points
+    p2s_plan* fallback = nullptr;  // judged subset, FP64 at 48 points (the plain method), masked
     int64_t E = 0, nJ = 0;
     int margin = 0;
     float risk = 0.f;
@@ -529,7 +536,9 @@ struct p2s_learned_plan {
     float* d_feat = nullptr;
     int32_t* d_npts = nullptr;
     double* d_jin = nullptr;  // gathered nodes [nJ][24], bulge [nJ][4], params [nJ][4]
-    double* d_jout = nullptr;
+    double* d_jout = nullptr;  // judge fill
+    double* d_jfb = nullptr;   // plain-method fill of the judged elements that failed
+    int8_t* d_mask = nullptr;  // [nJ] judged element failed
     double* d_jerr = nullptr;
     unsigned long long* d_report = nullptr;
 };
@@ -541,6 +550,7 @@ void p2s_learned_plan_destroy(p2s_learned_plan* L) {
     if (L->ctx) cudaSetDevice(context_tables(L->ctx)->device);
     p2s_plan_destroy(L->main);
     p2s_plan_destroy(L->judge);
+    p2s_plan_destroy(L->fallback);
     cudaFree(L->d_jidx);
     cudaFree(L->d_off_main);
     cudaFree(L->d_off_j);
@@ -548,6 +558,8 @@ void p2s_learned_plan_destroy(p2s_learned_plan* L) {
     cudaFree(L->d_npts);
     cudaFree(L->d_jin);
     cudaFree(L->d_jout);
+    cudaFree(L->d_jfb);
+    cudaFree(L->d_mask);
     cudaFree(L->d_jerr);
     cudaFree(L->d_report);
     delete L;
@@ -592,8 +604,11 @@ int p2s_learned_plan_create(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, c
     }
     off_main[jidx.size()] = off_full[E];
     p2s_orders jo = {3, jord.data()};
-    p2s_fill_opts fj = {P2S_FP64, P2S_TYPES_ALL};
+    p2s_fill_opts fj = {opts->precision, P2S_TYPES_ALL};
     rc = p2s_plan_create(ctx, L->nJ, &jo, &q48, &fj, &L->judge);
+    if (rc) { p2s_learned_plan_destroy(L); return rc; }
+    p2s_fill_opts ff = {P2S_FP64, P2S_TYPES_ALL};
+    rc = p2s_plan_create(ctx, L->nJ, &jo, &q48, &ff, &L->fallback);
     if (rc) { p2s_learned_plan_destroy(L); return rc; }
     const int64_t jent = p2s_output_entries(L->nJ, &jo, P2S_TYPES_ALL, off_j.data());
     bool ok = cudaMalloc(&L->d_feat, sizeof(float) * kIn * std::max<int64_t>(E, 1)) == cudaSuccess &&
@@ -603,6 +618,8 @@ int p2s_learned_plan_create(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, c
               cudaMalloc(&L->d_off_j, sizeof(int64_t) * (L->nJ + 1)) == cudaSuccess &&
               cudaMalloc(&L->d_jin, sizeof(double) * 32 * std::max<int64_t>(L->nJ, 1)) == cudaSuccess &&
               cudaMalloc(&L->d_jout, sizeof(double) * std::max<int64_t>(jent, 1)) == cudaSuccess &&
+              cudaMalloc(&L->d_jfb, sizeof(double) * std::max<int64_t>(jent, 1)) == cudaSuccess &&
+              cudaMalloc(&L->d_mask, std::max<int64_t>(L->nJ, 1)) == cudaSuccess &&
               cudaMalloc(&L->d_jerr, sizeof(double) * std::max<int64_t>(L->nJ, 1)) == cudaSuccess &&
               cudaMalloc(&L->d_report, sizeof(unsigned long long) * 16) == cudaSuccess;
     if (!ok) { p2s_learned_plan_destroy(L); return fail(P2S_ERR_OOM, "p2s_learned_plan_create: device allocation"); }
@@ -653,7 +670,12 @@ int p2s_learned_fill(p2s_learned_plan* L, const p2s_geometry* geom, const p2s_ma
         if (rc) return rc;
         rc = p2s_element_errors(L->ctx, out, L->d_off_main, L->d_jout, L->d_off_j, L->nJ, 4, L->d_jerr, stream);
         if (rc) return rc;
-        k_judge_fix<<<gj, 256, 0, s>>>(out, L->d_off_main, L->d_jout, L->d_off_j, L->d_jerr, L->nJ, L->tol, L->d_report);
+        // judged elements above the tolerance: their plain-method fill, then the copy into out
+        k_judge_mask<<<(int)std::min<int64_t>((L->nJ + 255) / 256, 1024), 256, 0, s>>>(L->d_jerr, L->nJ, L->tol, L->d_mask);
+        P2S_LCUDA(cudaGetLastError());
+        rc = plan_fill_masked(L->fallback, &g2, &m2, L->d_jfb, L->d_mask, s);
+        if (rc) return rc;
+        k_judge_fix<<<gj, 256, 0, s>>>(out, L->d_off_main, L->d_jfb, L->d_off_j, L->d_jerr, L->nJ, L->tol, L->d_report);
         P2S_LCUDA(cudaGetLastError());
     }
     return P2S_OK;

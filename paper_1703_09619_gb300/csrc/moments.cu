@@ -35,7 +35,7 @@ struct Smem {
 __device__ __forceinline__ Smem carve(double* sm, int n_pairs, int kb, int gmax, int iacc_cap) {
     Smem S;
     S.B = sm;
-    S.xq = S.B + kb * gmax;
+    S.xq = S.B + kb * (gmax | 1);  // B rows padded to an odd stride (bank spread)
     S.t0 = S.xq + gmax;
     S.t1 = S.t0 + gmax;
     S.t2 = S.t1 + gmax;
@@ -52,9 +52,10 @@ __global__ void __launch_bounds__(kThreads) k_moments_fp64(MomentLaunch L) {
     const int tid = threadIdx.x;
     Smem S = carve(sm, L.n_pairs, L.kb, L.gmax, L.iacc_cap);
     __shared__ int bad_jac;
-    const int gstride = L.gmax;
+    const int gstride = L.gmax | 1;
 
     for (int64_t e = blockIdx.x; e < L.n_elem; e += gridDim.x) {
+        if (L.elem_mask && !L.elem_mask[e]) continue;  // uniform across the CTA
         const ElemDesc& d = L.desc[e];
         const int G = d.G, nc = d.n_comp, np = (nc == 1) ? 1 : 6;
         const int Ku = d.kax[0], Kv = d.kax[1], Kw = d.kax[2];
@@ -137,23 +138,24 @@ __global__ void __launch_bounds__(kThreads) k_moments_fp64(MomentLaunch L) {
                         }
                     }
                     __syncthreads();
-                    // phase B: T1[s][k][bb] = sum_a B[k][a] alpha[s][bb*G + a]
-                    for (int i = tid; i < ns * Ku * nbc; i += kThreads) {
-                        const int s = i / (Ku * nbc), r = i - s * Ku * nbc, k = r / nbc, bb = r - k * nbc;
+                    // phase B: T1[s][bb][k] = sum_a B[k][a] alpha[s][bb*G + a]; k fastest across
+                    // threads, so the alpha reads are broadcasts and the B rows (odd stride) spread
+                    for (int i = tid; i < ns * nbc * Ku; i += kThreads) {
+                        const int sb = i / Ku, k = i - sb * Ku, s = sb / nbc, bb = sb - s * nbc;
                         const double* al = S.alpha + s * kChunk + bb * G;
                         const double* Bk = S.B + k * gstride;
                         double acc = 0.0;
                         for (int a = 0; a < G; ++a) acc = fma(Bk[a], al[a], acc);
-                        S.T1[(s * Kb + k) * kNB + bb] = acc;
+                        S.T1[(s * kNB + bb) * Kb + k] = acc;
                     }
                     __syncthreads();
-                    // phase C: T2[s][k][l] += sum_bb B[l][b0+bb] T1[s][k][bb]
+                    // phase C: T2[s][k][l] += sum_bb B[l][b0+bb] T1[s][bb][k]
                     for (int i = tid; i < ns * Ku * Kv; i += kThreads) {
                         const int s = i / (Ku * Kv), r = i - s * Ku * Kv, k = r / Kv, l = r - k * Kv;
-                        const double* t1 = S.T1 + (s * Kb + k) * kNB;
+                        const double* t1 = S.T1 + s * kNB * Kb + k;
                         const double* Bl = S.B + l * gstride + b0;
                         double acc = S.T2[i];
-                        for (int bb = 0; bb < nbc; ++bb) acc = fma(Bl[bb], t1[bb], acc);
+                        for (int bb = 0; bb < nbc; ++bb) acc = fma(Bl[bb], t1[bb * Kb], acc);
                         S.T2[i] = acc;
                     }
                     __syncthreads();
@@ -197,7 +199,7 @@ __global__ void __launch_bounds__(kThreads) k_moments_fp64(MomentLaunch L) {
 }  // namespace
 
 size_t moments_smem_bytes(int n_pairs, int kb, int gmax, int iacc_cap) {
-    size_t d = (size_t)kb * gmax + 4 * (size_t)gmax + (size_t)n_pairs * kChunk + (size_t)n_pairs * kb * kNB +
+    size_t d = (size_t)kb * (gmax | 1) + 4 * (size_t)gmax + (size_t)n_pairs * kChunk + (size_t)n_pairs * kb * kNB +
                (size_t)n_pairs * kb * kb + (size_t)iacc_cap + kGeo;
     return d * sizeof(double);
 }

@@ -34,11 +34,15 @@ struct SmemDW {
     double* geo64;
 };
 
+// B-table rows are padded to an odd number of double-words so that threads reading the
+// same column of different rows hit different banks.
+__host__ __device__ __forceinline__ int padded_stride(int gmax) { return gmax | 1; }
+
 __device__ __forceinline__ SmemDW carve_dw(unsigned char* sm, int n_pairs, int kb, int gmax, int iacc_cap) {
     SmemDW S;
     dw* p = reinterpret_cast<dw*>(sm);
     S.B = p;
-    S.xq = S.B + kb * gmax;
+    S.xq = S.B + kb * padded_stride(gmax);
     S.t0 = S.xq + gmax;
     S.t1 = S.t0 + gmax;
     S.t2 = S.t1 + gmax;
@@ -102,7 +106,7 @@ __global__ void __launch_bounds__(kThreads) k_moments_dw(MomentLaunch L) {
     const int tid = threadIdx.x;
     SmemDW S = carve_dw(smraw, L.n_pairs, L.kb, L.gmax, L.iacc_cap);
     __shared__ int bad_jac;
-    const int gstride = L.gmax;
+    const int gstride = padded_stride(L.gmax);
     const bool metric = L.kind == P2S_ALPHA_METRIC_EPS;
 
     for (int64_t e = blockIdx.x; e < L.n_elem; e += gridDim.x) {
@@ -194,25 +198,26 @@ __global__ void __launch_bounds__(kThreads) k_moments_dw(MomentLaunch L) {
                         }
                     }
                     __syncthreads();
-                    // phase B: T1[s][k][bb] = sum_a B[k][a] alpha[s][bb*G + a]
-                    for (int i = tid; i < ns * Ku * nbc; i += kThreads) {
-                        const int s = i / (Ku * nbc), r = i - s * Ku * nbc, k = r / nbc, bb = r - k * nbc;
+                    // phase B: T1[s][bb][k] = sum_a B[k][a] alpha[s][bb*G + a]; k fastest across
+                    // threads, so the alpha reads are broadcasts and the B rows (odd stride) spread
+                    for (int i = tid; i < ns * nbc * Ku; i += kThreads) {
+                        const int sb = i / Ku, k = i - sb * Ku, s = sb / nbc, bb = sb - s * nbc;
                         const dw* al = S.alpha + s * kChunk + bb * G;
                         const dw* Bk = S.B + k * gstride;
                         dw_acc acc;
                         for (int a = 0; a < G; ++a) acc.fma(Bk[a], al[a]);
-                        S.T1[(s * Kb + k) * kNB + bb] = acc.value();
+                        S.T1[(s * kNB + bb) * Kb + k] = acc.value();
                     }
                     __syncthreads();
-                    // phase C: T2[s][k][l] += sum_bb B[l][b0+bb] T1[s][k][bb]
+                    // phase C: T2[s][k][l] += sum_bb B[l][b0+bb] T1[s][bb][k]
                     for (int i = tid; i < ns * Ku * Kv; i += kThreads) {
                         const int s = i / (Ku * Kv), r = i - s * Ku * Kv, k = r / Kv, l = r - k * Kv;
-                        const dw* t1 = S.T1 + (s * Kb + k) * kNB;
+                        const dw* t1 = S.T1 + s * kNB * Kb + k;
                         const dw* Bl = S.B + l * gstride + b0;
                         dw_acc acc;
                         acc.s = S.T2[i].hi;
                         acc.c = S.T2[i].lo;
-                        for (int bb = 0; bb < nbc; ++bb) acc.fma(Bl[bb], t1[bb]);
+                        for (int bb = 0; bb < nbc; ++bb) acc.fma(Bl[bb], t1[bb * Kb]);
                         S.T2[i] = acc.value();
                     }
                     __syncthreads();
@@ -254,7 +259,7 @@ __global__ void __launch_bounds__(kThreads) k_moments_dw(MomentLaunch L) {
 }  // namespace
 
 size_t moments_dw_smem_bytes(int n_pairs, int kb, int gmax, int iacc_cap) {
-    size_t d = (size_t)kb * gmax + 4 * (size_t)gmax + (size_t)n_pairs * kChunk + (size_t)n_pairs * kb * kNB +
+    size_t d = (size_t)kb * padded_stride(gmax) + 4 * (size_t)gmax + (size_t)n_pairs * kChunk + (size_t)n_pairs * kb * kNB +
                (size_t)n_pairs * kb * kb + (size_t)iacc_cap + kGeoDW + kNB * kRow + kPlane;
     return d * sizeof(dw) + 48 * sizeof(double);
 }

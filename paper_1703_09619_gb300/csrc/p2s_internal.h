@@ -84,6 +84,7 @@ struct MomentLaunch {
     int gmax;           // max G over the plan
     int iacc_cap;       // doubles of the moment accumulator in shared memory
     int out_ff;         // 1: store moments as (hi, lo) FP32 pairs (mixed path)
+    const int8_t* elem_mask;  // optional: elements with mask 0 are skipped (FP64 kernel)
 };
 size_t moments_smem_bytes(int n_pairs, int kb, int gmax, int iacc_cap);
 cudaError_t launch_moments_fp64(const MomentLaunch& L, int grid, size_t smem, cudaStream_t s);
@@ -104,6 +105,7 @@ struct ContractLaunch {
     uint32_t types_mask;
     int a_cap, b_cap;      // elements of the stage-1 / stage-2 buffers
     int tile_off;          // byte offset of the FP64 tile in shared memory
+    const int8_t* elem_mask;  // optional: units of elements with mask 0 are skipped (generic kernel)
 };
 struct ContractShape {
     size_t a, b, tile;
@@ -180,15 +182,21 @@ int fail(int code, const char* where, cudaError_t ce = cudaSuccess);
 int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, const p2s_quadrature* quad,
                  const p2s_fill_opts* opts, ElemDesc* desc, UnitSink& units, PlanLayout& L);
 int run_moments(const DeviceTables& T, const PlanLayout& L, const ElemDesc* d_desc, const p2s_geometry* geom,
-                const p2s_material* mat, void* moments, int32_t* elem_status, cudaStream_t s);
+                const p2s_material* mat, void* moments, int32_t* elem_status, cudaStream_t s,
+                const int8_t* elem_mask = nullptr);
 int run_contract(const DeviceTables& T, const PlanLayout& L, const ElemDesc* d_desc, const ContractUnit* d_units,
-                 unsigned long long* d_counter, const void* moments, double* out, cudaStream_t s);
+                 unsigned long long* d_counter, const void* moments, double* out, cudaStream_t s,
+                 const int8_t* elem_mask = nullptr);
 }  // namespace p2s
 struct p2s_ctx;
 struct p2s_plan;
 namespace p2s {
 const DeviceTables* context_tables(const p2s_ctx* c);
 ElemDesc* plan_desc(p2s_plan* p);
+// Fill of a plan restricted to the elements with mask != 0 (FP64 plans only; the others
+// are left untouched in `out`).
+int plan_fill_masked(p2s_plan* p, const p2s_geometry* geom, const p2s_material* mat, double* out,
+                     const int8_t* mask, cudaStream_t s);
 cudaError_t learned_init_attributes();
 
 }  // namespace p2s
