@@ -41,6 +41,16 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # FP64 operations per quadrature point of the metric coupling factor in the moment kernel
 # (Jacobian 45, phase 9, sin ~25, cofactors 18, det 3, products 18, division ~10, scale 6)
 ALPHA_FLOP_PER_POINT = 134
+# The mixed moment kernel runs in double-word (float-float) arithmetic and is bound by FP32
+# instruction issue: 152 SMs x 128 lanes x 2.07 GHz lane operations per second.  Its work is
+# counted as the FP32 instructions that the double-word algorithms need per operation of the
+# method (an FMA counts once):
+#   one multiply-accumulate into the lazy accumulator: 12;
+#   the metric coupling factor at one point: 1481 (Jacobian from row constants 433, phase 54,
+#   sin 134 + scale 17, cofactors 306, det 61, division 68, six products 408);
+#   the scalar coupling factor at one point: 17.
+FP32_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
+DW_MAC_OPS, DW_ALPHA_OPS_METRIC, DW_ALPHA_OPS_SCALAR = 12, 1481, 17
 # Learned-fill settings: judge share and tolerance; risk of the class rule (the largest
 # value of the sweep 0.02 .. 0.0005 with no element of the batch above 1e-8).
 JUDGE_FRAC, JUDGE_TOL, RISK = 0.02, 1e-9, 0.002
@@ -98,6 +108,19 @@ def contract_fma_count(orders, types_mask):
                     s += cu * K[1] * K[2] + Ni[0] * Nj[0] * cv * K[2] + Ni[0] * Ni[1] * Nj[0] * Nj[1] * cw
         total += int(s) * int(mult)
     return total
+
+
+def moment_mac_points(orders, npts):
+    """Sum-factorised moment MACs and quadrature points of a batch."""
+    macs = pts = 0
+    nc = orders.shape[1]
+    npairs = 1 if nc == 1 else 6
+    for e in range(orders.shape[0]):
+        K = [int(k) for k in 2 * orders[e].max(axis=0) - 1]
+        G = int(npts[e])
+        macs += npairs * (K[0] * G ** 3 + K[0] * K[1] * G ** 2 + K[0] * K[1] * K[2] * G)
+        pts += G ** 3
+    return macs, pts
 
 
 def moment_flop_count(orders, npts, metric=True):
@@ -306,8 +329,20 @@ def roofline_for(wl, npts, prec, mom_ms, con_ms, peaks, src):
     """Roofline object of the dominant kernel of a fill (the slower of the two stages)."""
     entries = wl.entries()
     fmas = contract_fma_count(wl.orders, wl.types_mask)
-    mflop = moment_flop_count(wl.orders, npts, wl.kind == W.KIND_METRIC_EPS)
+    metric = wl.kind == W.KIND_METRIC_EPS
+    npts = np.broadcast_to(np.asarray(npts), (wl.n_elem,))
+    if mom_ms >= con_ms and prec != 0:
+        macs, pts = moment_mac_points(wl.orders, npts)
+        ops = DW_MAC_OPS * macs + (DW_ALPHA_OPS_METRIC if metric else DW_ALPHA_OPS_SCALAR) * pts
+        ach = ops / (mom_ms * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": "k_moments_dw", "achieved": ach, "peak": FP32_PEAK_TOPS,
+                "unit": "T FP32 lane-op/s", "frac": ach / FP32_PEAK_TOPS, "traffic": None,
+                "peak_source": "FP32 issue: 152 SMs x 128 lanes x 2.07 GHz (recipe unit counts and clock)",
+                "algorithmic_ops_per_launch": int(ops),
+                "op_model": "%d per double-word MAC x %d MACs + %d per point x %d points" % (
+                    DW_MAC_OPS, macs, DW_ALPHA_OPS_METRIC if metric else DW_ALPHA_OPS_SCALAR, pts)}
     if mom_ms >= con_ms:
+        mflop = moment_flop_count(wl.orders, npts, metric)
         ach = mflop / (mom_ms * 1e-3) / 1e12
         return {"bound": "alu", "kernel": "k_moments_fp64", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
