@@ -46,11 +46,12 @@ ALPHA_FLOP_PER_POINT = 134
 # counted as the FP32 instructions that the double-word algorithms need per operation of the
 # method (an FMA counts once):
 #   one multiply-accumulate into the lazy accumulator: 12;
-#   the metric coupling factor at one point: 1481 (Jacobian from row constants 433, phase 54,
-#   sin 134 + scale 17, cofactors 306, det 61, division 68, six products 408);
-#   the scalar coupling factor at one point: 17.
+#   the metric coupling factor at one point, with the _fast double-word operations (add 11,
+#   product 4, fused 15, division 11): 839 (Jacobian from row constants 241, phase 30,
+#   sin 110 + scale 14, cofactors 171, det 34, division 11, six products 228);
+#   the scalar coupling factor at one point: 14.
 FP32_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
-DW_MAC_OPS, DW_ALPHA_OPS_METRIC, DW_ALPHA_OPS_SCALAR = 12, 1481, 17
+DW_MAC_OPS, DW_ALPHA_OPS_METRIC, DW_ALPHA_OPS_SCALAR = 12, 839, 14
 # Learned-fill settings: judge share and tolerance; risk of the class rule (the largest
 # value of the sweep 0.02 .. 0.0005 with no element of the batch above 1e-8).
 JUDGE_FRAC, JUDGE_TOL, RISK = 0.02, 1e-9, 0.002

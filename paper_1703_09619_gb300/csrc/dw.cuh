@@ -73,6 +73,34 @@ __device__ __forceinline__ dw dw_div(dw x, dw y) {
     return dw_add_f(q, q3);
 }
 
+// Cheaper variants whose error is bounded against the operands rather than the result:
+// absolute error O(u^2 (|x| + |y|)) for a sum, O(u^2 |x y|) for a product.  The coupling
+// factor feeds a normwise error measure (max|dM| / max|M| per element), so cancellation in
+// one of its sums may lose relative accuracy of that sum without harming the fill.
+//   dw_add_fast - SloppyDWPlusDW (Joldes, Muller and Popescu 2017): the high words add with
+//                 TwoSum, the low words join the rounding error, one Fast2Sum renormalises;
+//   dw_mul_fast - DWTimesDW with FMA, without the final renormalisation: the pair returned
+//                 has |lo| <= ~3u |hi| and every operation here accepts it as an operand;
+//   dw_div_fast - the FP32 quotient plus one Newton correction computed from the exact
+//                 remainder (x.hi - q y.hi is exact by Sterbenz): error about 5u^2.
+__device__ __forceinline__ dw dw_add_fast(dw x, dw y) {
+    const dw s = two_sum(x.hi, y.hi);
+    return fast_two_sum(s.hi, s.lo + (x.lo + y.lo));
+}
+__device__ __forceinline__ dw dw_sub_fast(dw x, dw y) { return dw_add_fast(x, dw_neg(y)); }
+__device__ __forceinline__ dw dw_mul_fast(dw x, dw y) {
+    const float p = x.hi * y.hi;
+    return dw{p, fmaf(x.lo, y.hi, fmaf(x.hi, y.lo, fmaf(x.hi, y.hi, -p)))};
+}
+__device__ __forceinline__ dw dw_fma_fast(dw x, dw y, dw z) { return dw_add_fast(dw_mul_fast(x, y), z); }
+__device__ __forceinline__ dw dw_div_fast(dw x, dw y) {
+    const float q1 = __fdiv_rn(x.hi, y.hi);
+    const float ph = y.hi * q1;
+    const float pl = fmaf(y.lo, q1, fmaf(y.hi, q1, -ph));
+    const float r = (x.hi - ph) + (x.lo - pl);
+    return fast_two_sum(q1, __fdiv_rn(r, y.hi));
+}
+
 // Accumulator for sums of products: the leading words sum with TwoSum, every rounding
 // error and lower-order product term goes to the second word; renormalise at the end.
 struct dw_acc {
@@ -99,7 +127,9 @@ struct dw_acc {
 // sin of a double-word argument |x| <= ~6e3.  Cody-Waite reduction by pi/2 with a
 // four-part constant (the first two parts have 12 significant bits, so n * part is exact
 // for |n| < 2^12), then Taylor polynomials on |r| <= pi/4 (the leading terms in
-// double-word, the tail, below 1e-3 in magnitude, in FP32).
+// double-word, the tail, below 1e-3 in magnitude, in FP32).  The reduction is accurate to
+// the last bit of the double word; the polynomials use the _fast operations (absolute error
+// a few u^2 on a result of magnitude <= 1).
 __device__ __forceinline__ dw dw_sin(dw x) {
     // pi/2 = C1 + C2 + C3 + C4 (C1, C2 with 12 significant bits; C3, C4 FP32 roundings of the rest)
     const float C1 = 1.57080078125f;
@@ -110,9 +140,9 @@ __device__ __forceinline__ dw dw_sin(dw x) {
     // r = x - n (C1 + C2 + C3 + C4), n C1 and n C2 exact
     dw r = dw_add_f(x, -n * C1);
     r = dw_add_f(r, -n * C2);
-    r = dw_add(r, dw_neg(two_prod(n, C3)));
+    r = dw_add_fast(r, dw_neg(two_prod(n, C3)));
     r = dw_add_f(r, -n * C4);
-    const dw z = dw_mul(r, r);
+    const dw z = dw_mul_fast(r, r);
     const int q = ((int)n) & 3;
     dw res;
     if (q & 1) {
@@ -124,8 +154,8 @@ __device__ __forceinline__ dw dw_sin(dw x) {
         // cos r = 1 - z/2 + z^2 (1/24 + z t)
         const dw c24 = dw_make(0.041666667908430099f, -1.2417634698280722e-09f);  // 1/24
         const dw w = dw_add_f(c24, zf * t);
-        const dw z2 = dw_mul(z, z);
-        res = dw_add(dw_add_f(dw_mul_f(z, -0.5f), 1.f), dw_mul(z2, w));
+        const dw z2 = dw_mul_fast(z, z);
+        res = dw_add_fast(dw_add_f(dw_make(-0.5f * z.hi, -0.5f * z.lo), 1.f), dw_mul_fast(z2, w));
     } else {
         // sin r = r - r^3/6 + r^5/120 - r^7/5040 + r^9/362880 - r^11/39916800 + r^13/6227020800
         const float zf = z.hi;
@@ -135,8 +165,8 @@ __device__ __forceinline__ dw dw_sin(dw x) {
         // sin r = r + r z (-1/6 + z (1/120 + z t))
         const dw c120 = dw_make(0.0083333337679505348f, -4.3461720333759502e-10f);  // 1/120
         const dw c6 = dw_make(-0.1666666716337204f, 4.9670538793122887e-09f);       // -1/6
-        const dw inner = dw_add(c6, dw_mul(z, dw_add_f(c120, zf * t)));
-        res = dw_add(r, dw_mul(dw_mul(r, z), inner));
+        const dw inner = dw_add_fast(c6, dw_mul_fast(z, dw_add_f(c120, zf * t)));
+        res = dw_add_fast(r, dw_mul_fast(dw_mul_fast(r, z), inner));
     }
     return (q & 2) ? dw_neg(res) : res;
 }

@@ -5,9 +5,20 @@
 // element to set up its constants (trilinear coefficients, 1-D node tables), which are
 // then split into double words.
 //
-// Same sum factorisation and data flow as k_moments_fp64 (moments.cu).  For the metric
-// kind, the parts of the Jacobian and of the phase k.x that do not depend on u are formed
-// once per (v, w) row:
+// Same sum factorisation as k_moments_fp64 (moments.cu): per chunk of up to 256 points
+// (rows b0 .. b0+nbc-1 of plane c)
+//   A: alpha at the chunk's points,
+//   B: T1[s][b][k] = sum_a B[k][a] alpha[s][b][a],
+//   C: T2_c[s][k][l] (+)= sum_b B[l][b] T1[s][b][k],
+//   D: after the last chunk of plane c, I[s][k][l][q] (+)= B[q][c] T2_c[s][k][l].
+// The steps are software-pipelined over the chunks of an element: in one interval between
+// two CTA barriers the threads compute the row constants of chunk t+1, A of chunk t, B of
+// chunk t-1, C of chunk t-2 and D of the plane whose last chunk was t-3, on double buffers
+// (row constants, alpha and T1 by chunk parity, T2 by plane parity), so an element of T
+// chunks takes T + 3 barriers and the B/C/D work is one balanced list over all threads.
+//
+// For the metric kind, the parts of the Jacobian and of the phase k.x that do not depend on
+// u are formed once per (v, w) row:
 //   J_iu = B_i(v,w) + g_i dbeta/du,
 //   J_iv = D_i(w) + u E_i(w) + g_i dbeta/dv,
 //   J_iw = F_i(v) + u H_i(v) + g_i dbeta/dw,
@@ -38,6 +49,14 @@ struct SmemDW {
 // same column of different rows hit different banks.
 __host__ __device__ __forceinline__ int padded_stride(int gmax) { return gmax | 1; }
 
+// Sizes (double-words) of one buffer of each double-buffered array.
+// alpha rows of a chunk have an odd stride (G | 1) so that the phase-B reads of different rows
+// fall in different banks; one pair's chunk then holds up to kChunk + kNB double-words.
+constexpr int kAlphaPair = kChunk + kNB;
+__host__ __device__ __forceinline__ int alpha_buf(int n_pairs) { return n_pairs * kAlphaPair; }
+__host__ __device__ __forceinline__ int t1_buf(int n_pairs, int kb) { return n_pairs * kNB * kb; }
+__host__ __device__ __forceinline__ int t2_buf(int n_pairs, int kb) { return n_pairs * kb * kb; }
+
 __device__ __forceinline__ SmemDW carve_dw(unsigned char* sm, int n_pairs, int kb, int gmax, int iacc_cap) {
     SmemDW S;
     dw* p = reinterpret_cast<dw*>(sm);
@@ -47,13 +66,13 @@ __device__ __forceinline__ SmemDW carve_dw(unsigned char* sm, int n_pairs, int k
     S.t1 = S.t0 + gmax;
     S.t2 = S.t1 + gmax;
     S.alpha = S.t2 + gmax;
-    S.T1 = S.alpha + n_pairs * kChunk;
-    S.T2 = S.T1 + n_pairs * kb * kNB;
-    S.Iacc = S.T2 + n_pairs * kb * kb;
+    S.T1 = S.alpha + 2 * alpha_buf(n_pairs);
+    S.T2 = S.T1 + 2 * t1_buf(n_pairs, kb);
+    S.Iacc = S.T2 + 2 * t2_buf(n_pairs, kb);
     S.geo = S.Iacc + iacc_cap;
     S.row = S.geo + kGeoDW;
-    S.plane = S.row + kNB * kRow;
-    S.geo64 = reinterpret_cast<double*>(S.plane + kPlane);
+    S.plane = S.row + 2 * kNB * kRow;
+    S.geo64 = reinterpret_cast<double*>(S.plane + 2 * kPlane);
     return S;
 }
 
@@ -64,52 +83,111 @@ __device__ __forceinline__ void pair_comps_dw(int s, int n_comp, int& gi, int& g
     gj = tgj[s];
 }
 
-// alpha (metric kind) at one point from the row/plane constants; returns detJ > 0.
+// alpha (metric kind) at one point from the row/plane constants; returns detJ > 0.  Every
+// operation is a _fast one (dw.cuh): the error of each factor is O(u^2) against the scale
+// of its operands, which the normwise error of the element matrices tolerates.
 __device__ __forceinline__ bool metric_alpha_dw(const dw* geo, const dw* row, const dw* plane, dw u, dw Ca,
                                                 dw Sa, dw* K) {
-    const dw beta = dw_mul(Ca, row[11]);
-    const dw dbu = dw_mul(Sa, row[11]);
-    const dw dbv = dw_mul(Ca, row[12]);
-    const dw dbw = dw_mul(Ca, row[13]);
+    const dw beta = dw_mul_fast(Ca, row[11]);
+    const dw dbu = dw_mul_fast(Sa, row[11]);
+    const dw dbv = dw_mul_fast(Ca, row[12]);
+    const dw dbw = dw_mul_fast(Ca, row[13]);
     dw J[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const dw g = geo[24 + i];
-        J[i][0] = dw_fma(g, dbu, row[i]);
-        J[i][1] = dw_fma(g, dbv, dw_fma(u, plane[3 + i], plane[i]));
-        J[i][2] = dw_fma(g, dbw, dw_fma(u, row[6 + i], row[3 + i]));
+        J[i][0] = dw_fma_fast(g, dbu, row[i]);
+        J[i][1] = dw_fma_fast(g, dbv, dw_fma_fast(u, plane[3 + i], plane[i]));
+        J[i][2] = dw_fma_fast(g, dbw, dw_fma_fast(u, row[6 + i], row[3 + i]));
     }
-    const dw theta = dw_fma(geo[39], beta, dw_fma(u, row[10], row[9]));
-    const dw eps = dw_add_f(dw_mul(geo[27], dw_sin(theta)), 1.f);
+    const dw theta = dw_fma_fast(geo[39], beta, dw_fma_fast(u, row[10], row[9]));
+    const dw eps = dw_add_f(dw_mul_fast(geo[27], dw_sin(theta)), 1.f);
     dw C[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
-            C[i][j] = dw_sub(dw_mul(J[i1][j1], J[i2][j2]), dw_mul(J[i1][j2], J[i2][j1]));
+            C[i][j] = dw_sub_fast(dw_mul_fast(J[i1][j1], J[i2][j2]), dw_mul_fast(J[i1][j2], J[i2][j1]));
         }
-    const dw det = dw_add(dw_mul(J[0][0], C[0][0]), dw_add(dw_mul(J[0][1], C[0][1]), dw_mul(J[0][2], C[0][2])));
-    const dw sc = dw_div(eps, det);
+    const dw det = dw_add_fast(dw_mul_fast(J[0][0], C[0][0]),
+                               dw_add_fast(dw_mul_fast(J[0][1], C[0][1]), dw_mul_fast(J[0][2], C[0][2])));
+    const dw sc = dw_div_fast(eps, det);
     const int pi_[6] = {0, 0, 0, 1, 1, 2}, pj_[6] = {0, 1, 2, 1, 2, 2};
 #pragma unroll
     for (int s = 0; s < 6; ++s) {
         const int i = pi_[s], j = pj_[s];
-        const dw g = dw_add(dw_mul(C[0][i], C[0][j]), dw_add(dw_mul(C[1][i], C[1][j]), dw_mul(C[2][i], C[2][j])));
-        K[s] = dw_mul(sc, g);
+        const dw g = dw_add_fast(dw_mul_fast(C[0][i], C[0][j]),
+                                 dw_add_fast(dw_mul_fast(C[1][i], C[1][j]), dw_mul_fast(C[2][i], C[2][j])));
+        K[s] = dw_mul_fast(sc, g);
     }
     return det.hi > 0.f;
 }
 
-__global__ void __launch_bounds__(kThreads) k_moments_dw(MomentLaunch L) {
+// n / d for 0 <= n < 2^20 and d >= 1, from the FP32 reciprocal rd of d: the product is
+// within 1/8 of n / d, so one correction step gives the exact quotient.
+__device__ __forceinline__ int div_small(int n, int d, float rd) {
+    int q = __float2int_rz(__int2float_rn(n) * rd);
+    const int r = n - q * d;
+    q += (r >= d) - (r < 0);
+    return q;
+}
+
+// Chunk t of an element: plane c, first row b0, nbc rows.
+struct Chunk {
+    int c, b0, nbc;
+};
+__device__ __forceinline__ Chunk chunk_of(int t, int ncp, int nb, int G) {
+    Chunk ch;
+    ch.c = t / ncp;
+    ch.b0 = (t - ch.c * ncp) * nb;
+    ch.nbc = min(nb, G - ch.b0);
+    return ch;
+}
+
+// One task of the row/plane constants of a chunk (metric kind): tasks 4 bb + i (i < 3) form
+// B_i, F_i, H_i of row bb, task 4 bb + 3 forms T0, T1 and the three cosine products of row
+// bb, tasks 4 nbc + i form D_i and E_i of the chunk's plane.
+__device__ __forceinline__ void metric_constants_task(const SmemDW& S, const Chunk& ch, int task, dw* row, dw* plane) {
+    const dw* cf = S.geo;
+    const dw w = S.xq[ch.c];
+    if (task < 4 * ch.nbc) {
+        const int bb = task >> 2, part = task & 3, b = ch.b0 + bb;
+        const dw v = S.xq[b];
+        dw* r = row + bb * kRow;
+        if (part < 3) {
+            const dw* ci = cf + 8 * part;
+            r[part] = dw_fma_fast(ci[7], dw_mul_fast(v, w), dw_fma_fast(ci[5], w, dw_fma_fast(ci[4], v, ci[1])));  // B_i
+            r[3 + part] = dw_fma_fast(ci[6], v, ci[3]);                                                         // F_i
+            r[6 + part] = dw_fma_fast(ci[7], v, ci[5]);                                                         // H_i
+        } else {
+            const dw* th = cf + 31;
+            const dw vw = dw_mul_fast(v, w);
+            r[9] = dw_fma_fast(th[6], vw, dw_fma_fast(th[3], w, dw_fma_fast(th[2], v, th[0])));   // T0
+            r[10] = dw_fma_fast(th[7], vw, dw_fma_fast(th[5], w, dw_fma_fast(th[4], v, th[1])));  // T1
+            r[11] = dw_mul_fast(S.t0[b], S.t0[ch.c]);  // cos cos      (beta / cos_u)
+            r[12] = dw_mul_fast(S.t1[b], S.t0[ch.c]);  // dcos_v cos_w
+            r[13] = dw_mul_fast(S.t0[b], S.t1[ch.c]);  // cos_v dcos_w
+        }
+    } else {
+        const int i = task - 4 * ch.nbc;  // plane constants D_i, E_i (J_iv = D_i + u E_i + ...)
+        const dw* ci = cf + 8 * i;
+        plane[i] = dw_fma_fast(ci[6], w, ci[2]);
+        plane[3 + i] = dw_fma_fast(ci[7], w, ci[4]);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 3) k_moments_dw(MomentLaunch L) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int tid = threadIdx.x;
     SmemDW S = carve_dw(smraw, L.n_pairs, L.kb, L.gmax, L.iacc_cap);
     __shared__ int bad_jac;
     const int gstride = padded_stride(L.gmax);
     const bool metric = L.kind == P2S_ALPHA_METRIC_EPS;
+    const int aS = alpha_buf(L.n_pairs), t1S = t1_buf(L.n_pairs, L.kb), t2S = t2_buf(L.n_pairs, L.kb);
 
     for (int64_t e = blockIdx.x; e < L.n_elem; e += gridDim.x) {
+        if (L.elem_mask && !L.elem_mask[e]) continue;
         const ElemDesc& d = L.desc[e];
         const int G = d.G, nc = d.n_comp, np = (nc == 1) ? 1 : 6;
         const int Ku = d.kax[0], Kv = d.kax[1], Kw = d.kax[2];
@@ -147,89 +225,108 @@ __global__ void __launch_bounds__(kThreads) k_moments_dw(MomentLaunch L) {
 
         const int per_pair = Ku * Kv * Kw;
         const int ppg = max(1, min(np, L.iacc_cap / per_pair));
+        const float rKu = 1.f / (float)Ku, rKv = 1.f / (float)Kv, rG = 1.f / (float)G;
+        const int ga = G | 1;
         const int nb = max(1, min(G, kChunk / G));
+        const int ncp = (G + nb - 1) / nb;  // chunks per plane
+        const int T = G * ncp;
         for (int s0 = 0; s0 < np; s0 += ppg) {
             const int ns = min(np, s0 + ppg) - s0;
-            for (int i = tid; i < ns * per_pair; i += kThreads) S.Iacc[i] = dw_from_float(0.f);
-            for (int c = 0; c < G; ++c) {
-                for (int i = tid; i < ns * Ku * Kv; i += kThreads) S.T2[i] = dw_from_float(0.f);
-                if (metric && tid < 3) {  // plane constants D_i, E_i (J_iv = D_i + u E_i + ...)
-                    const dw* cf = S.geo + 8 * tid;
-                    const dw w = S.xq[c];
-                    S.plane[tid] = dw_fma(cf[6], w, cf[2]);
-                    S.plane[3 + tid] = dw_fma(cf[7], w, cf[4]);
-                }
-                for (int b0 = 0; b0 < G; b0 += nb) {
-                    const int nbc = min(nb, G - b0);
-                    const int npts = nbc * G;
-                    if (metric && tid < nbc) {  // row constants for (b0 + tid, c)
-                        const int b = b0 + tid;
-                        const dw v = S.xq[b], w = S.xq[c], vw = dw_mul(v, w);
-                        dw* r = S.row + tid * kRow;
-                        const dw* cf = S.geo;
-#pragma unroll
-                        for (int i = 0; i < 3; ++i) {
-                            const dw* ci = cf + 8 * i;
-                            r[i] = dw_fma(ci[7], vw, dw_fma(ci[5], w, dw_fma(ci[4], v, ci[1])));  // B_i
-                            r[3 + i] = dw_fma(ci[6], v, ci[3]);                                  // F_i
-                            r[6 + i] = dw_fma(ci[7], v, ci[5]);                                  // H_i
-                        }
-                        const dw* th = cf + 31;
-                        r[9] = dw_fma(th[6], vw, dw_fma(th[3], w, dw_fma(th[2], v, th[0])));   // T0
-                        r[10] = dw_fma(th[7], vw, dw_fma(th[5], w, dw_fma(th[4], v, th[1])));  // T1
-                        r[11] = dw_mul(S.t0[b], S.t0[c]);  // cos cos      (beta / cos_u)
-                        r[12] = dw_mul(S.t1[b], S.t0[c]);  // dcos_v cos_w
-                        r[13] = dw_mul(S.t0[b], S.t1[c]);  // cos_v dcos_w
-                    } else if (!metric && tid < nbc) {
-                        S.row[tid * kRow] = dw_mul(S.t1[b0 + tid], S.t2[c]);
+            for (int step = -1; step < T + 3; ++step) {
+                // row / plane constants of chunk step + 1 (tasks on the highest threads)
+                if (step + 1 < T) {
+                    const int t = step + 1;
+                    const Chunk ch = chunk_of(t, ncp, nb, G);
+                    dw* row = S.row + (t & 1) * kNB * kRow;
+                    const int task = kThreads - 1 - tid;
+                    if (metric) {
+                        if (task < 4 * ch.nbc + 3) metric_constants_task(S, ch, task, row, S.plane + (t & 1) * kPlane);
+                    } else if (task < ch.nbc) {
+                        row[task * kRow] = dw_mul_fast(S.t1[ch.b0 + task], S.t2[ch.c]);
                     }
-                    __syncthreads();
-                    // phase A: alpha at (a, b0 + bb, c)
-                    if (tid < npts) {
-                        const int bb = tid / G, a = tid - bb * G;
+                }
+                // A: alpha of chunk step
+                if (step >= 0 && step < T) {
+                    const Chunk ch = chunk_of(step, ncp, nb, G);
+                    const dw* row = S.row + (step & 1) * kNB * kRow;
+                    dw* al = S.alpha + (step & 1) * aS;
+                    if (tid < ch.nbc * G) {
+                        const int bb = div_small(tid, G, rG), a = tid - bb * G, ia = bb * ga + a;
                         if (!metric) {
-                            S.alpha[tid] = dw_add_f(dw_mul(S.t0[a], S.row[bb * kRow]), 1.f);
+                            al[ia] = dw_add_f(dw_mul_fast(S.t0[a], row[bb * kRow]), 1.f);
                         } else {
                             dw K[6];
-                            const bool ok = metric_alpha_dw(S.geo, S.row + bb * kRow, S.plane, S.xq[a], S.t0[a],
-                                                            S.t1[a], K);
+                            const bool ok = metric_alpha_dw(S.geo, row + bb * kRow, S.plane + (step & 1) * kPlane,
+                                                            S.xq[a], S.t0[a], S.t1[a], K);
                             if (!ok) bad_jac = 1;
-                            for (int s = 0; s < ns; ++s) S.alpha[s * kChunk + tid] = K[s0 + s];
+#pragma unroll
+                            for (int s = 0; s < 6; ++s)
+                                if (s >= s0 && s < s0 + ns) al[(s - s0) * kAlphaPair + ia] = K[s];
                         }
                     }
-                    __syncthreads();
-                    // phase B: T1[s][bb][k] = sum_a B[k][a] alpha[s][bb*G + a]; k fastest across
-                    // threads, so the alpha reads are broadcasts and the B rows (odd stride) spread
-                    for (int i = tid; i < ns * nbc * Ku; i += kThreads) {
-                        const int sb = i / Ku, k = i - sb * Ku, s = sb / nbc, bb = sb - s * nbc;
-                        const dw* al = S.alpha + s * kChunk + bb * G;
+                }
+                // B of chunk step - 1, C of chunk step - 2, D of the plane whose last chunk is step - 3
+                const int tb = step - 1, tc = step - 2, td = step - 3;
+                Chunk cb{0, 0, 0}, cc{0, 0, 0};
+                int nB = 0, nC = 0, nD = 0, pd = 0;
+                if (tb >= 0 && tb < T) {
+                    cb = chunk_of(tb, ncp, nb, G);
+                    nB = ns * cb.nbc * Ku;
+                }
+                if (tc >= 0 && tc < T) {
+                    cc = chunk_of(tc, ncp, nb, G);
+                    nC = ns * Ku * Kv;
+                }
+                if (td >= 0 && td < T && td % ncp == ncp - 1) {
+                    pd = td / ncp;
+                    nD = ns * Ku * Kv;
+                }
+                const dw* alB = S.alpha + (tb & 1) * aS;
+                dw* t1B = S.T1 + (tb & 1) * t1S;
+                const dw* t1C = S.T1 + (tc & 1) * t1S;
+                dw* t2C = S.T2 + (cc.c & 1) * t2S;
+                const dw* t2D = S.T2 + (pd & 1) * t2S;
+                const float r_nbc = 1.f / (float)max(cb.nbc, 1);
+                for (int j = tid; j < nB + nC + nD; j += kThreads) {
+                    if (j < nB) {
+                        // T1[s][bb][k] = sum_a B[k][a] alpha[s][bb][a]; k fastest across threads, so
+                        // the alpha reads are broadcasts and the B rows (odd stride) spread
+                        const int sb = div_small(j, Ku, rKu), k = j - sb * Ku;
+                        const int s = div_small(sb, cb.nbc, r_nbc), bb = sb - s * cb.nbc;
+                        const dw* al = alB + s * kAlphaPair + bb * ga;
                         const dw* Bk = S.B + k * gstride;
                         dw_acc acc;
                         for (int a = 0; a < G; ++a) acc.fma(Bk[a], al[a]);
-                        S.T1[(s * kNB + bb) * Kb + k] = acc.value();
-                    }
-                    __syncthreads();
-                    // phase C: T2[s][k][l] += sum_bb B[l][b0+bb] T1[s][bb][k]
-                    for (int i = tid; i < ns * Ku * Kv; i += kThreads) {
-                        const int s = i / (Ku * Kv), r = i - s * Ku * Kv, k = r / Kv, l = r - k * Kv;
-                        const dw* t1 = S.T1 + s * kNB * Kb + k;
-                        const dw* Bl = S.B + l * gstride + b0;
+                        t1B[(s * kNB + bb) * Kb + k] = acc.value();
+                    } else if (j < nB + nC) {
+                        // T2[s][k][l] (+)= sum_bb B[l][b0 + bb] T1[s][bb][k]
+                        const int i = j - nB;
+                        const int sk = div_small(i, Kv, rKv), l = i - sk * Kv;
+                        const int s = div_small(sk, Ku, rKu), k = sk - s * Ku;
+                        const dw* t1 = t1C + s * kNB * Kb + k;
+                        const dw* Bl = S.B + l * gstride + cc.b0;
                         dw_acc acc;
-                        acc.s = S.T2[i].hi;
-                        acc.c = S.T2[i].lo;
-                        for (int bb = 0; bb < nbc; ++bb) acc.fma(Bl[bb], t1[bb * Kb]);
-                        S.T2[i] = acc.value();
+                        if (cc.b0 > 0) {
+                            acc.s = t2C[i].hi;
+                            acc.c = t2C[i].lo;
+                        }
+                        for (int bb = 0; bb < cc.nbc; ++bb) acc.fma(Bl[bb], t1[bb * Kb]);
+                        t2C[i] = acc.value();
+                    } else {
+                        // I[s][k][l][q] (+)= B[q][c] T2_c[s][k][l] for all q of one (s, k, l)
+                        const int skl = j - nB - nC;
+                        const dw t2 = t2D[skl];
+                        dw* I = S.Iacc + skl * Kw;
+                        for (int q = 0; q < Kw; ++q) {
+                            dw_acc acc;
+                            if (pd > 0) {
+                                acc.s = I[q].hi;
+                                acc.c = I[q].lo;
+                            }
+                            acc.fma(S.B[q * gstride + pd], t2);
+                            I[q] = acc.value();
+                        }
                     }
-                    __syncthreads();
-                }
-                // phase D: I[s][k][l][q] += B[q][c] T2[s][k][l]
-                for (int i = tid; i < ns * per_pair; i += kThreads) {
-                    const int skl = i / Kw, q = i - skl * Kw;
-                    dw_acc acc;
-                    acc.s = S.Iacc[i].hi;
-                    acc.c = S.Iacc[i].lo;
-                    acc.fma(S.B[q * gstride + c], S.T2[skl]);
-                    S.Iacc[i] = acc.value();
                 }
                 __syncthreads();
             }
@@ -259,8 +356,9 @@ __global__ void __launch_bounds__(kThreads) k_moments_dw(MomentLaunch L) {
 }  // namespace
 
 size_t moments_dw_smem_bytes(int n_pairs, int kb, int gmax, int iacc_cap) {
-    size_t d = (size_t)kb * padded_stride(gmax) + 4 * (size_t)gmax + (size_t)n_pairs * kChunk + (size_t)n_pairs * kb * kNB +
-               (size_t)n_pairs * kb * kb + (size_t)iacc_cap + kGeoDW + kNB * kRow + kPlane;
+    size_t d = (size_t)kb * padded_stride(gmax) + 4 * (size_t)gmax + 2 * (size_t)alpha_buf(n_pairs) +
+               2 * (size_t)t1_buf(n_pairs, kb) + 2 * (size_t)t2_buf(n_pairs, kb) + (size_t)iacc_cap + kGeoDW +
+               2 * kNB * kRow + 2 * kPlane;
     return d * sizeof(dw) + 48 * sizeof(double);
 }
 
