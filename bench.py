@@ -31,6 +31,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_1703_09619_gb300 import dist as D  # noqa: E402
 from paper_1703_09619_gb300 import workloads as W  # noqa: E402
 
 METRIC = "matrix entries/s: learned+mixed-prec vs plain FP64 fill, one GB300, rel err ≤1e-8"
@@ -272,30 +273,17 @@ def workload_config(args, wl):
 # ----------------------------------------------------------------------------- GPU helpers
 def dist_setup():
     import torch
-    import torch.distributed as dist
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
+    world, rank, local = D.init("nccl")
     torch.cuda.set_device(local)
     return world, rank, local
 
 
 def max_over_ranks(x, world, dev):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], device=dev, dtype=torch.float64)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return D.max_over_ranks(x, world, dev)
 
 
 def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    D.barrier(world)
 
 
 def time_steps(fn, steps, stream, flush):
@@ -419,7 +407,9 @@ def run_learned(args, wl):
     peaks, src = load_peaks()
     roof = roofline_for(wl, npts, p2s.MIXED, mom_ms, con_ms, peaks, src)
     entries = wl.entries()
-    value = world * entries * args.steps / (total_ms * 1e-3)
+    job_entries = D.sum_over_ranks(entries, world, dev)  # each rank fills a batch of its own
+    job_elems = D.sum_over_ranks(wl.n_elem, world, dev)
+    value = job_entries * args.steps / (total_ms * 1e-3)
     hist = np.bincount([p2s.CLASS_NPTS.index(int(g)) for g in npts], minlength=6).tolist()
     e2e = None if args.no_e2e else measure_e2e_learned(args, wl, ctx, P, dev)
     line = None
@@ -429,8 +419,8 @@ def run_learned(args, wl):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args, wl),
-            "elements_per_s": world * wl.n_elem * args.steps / (total_ms * 1e-3),
-            "plain_fp64": {"value": world * entries / (plain_ms * 1e-3), "unit": "entries/s", "ms_per_step": plain_ms,
+            "elements_per_s": job_elems * args.steps / (total_ms * 1e-3),
+            "plain_fp64": {"value": job_entries / (plain_ms * 1e-3), "unit": "entries/s", "ms_per_step": plain_ms,
                            "npts": 48},
             "speedup_vs_plain_fp64": plain_ms / (total_ms / args.steps),
             "accuracy": {"max_rel_err_vs_plain48": float(err_h.max()), "share_above_1e-8": float((err_h > 1e-8).mean()),
@@ -503,14 +493,16 @@ def _e2e_pipeline(args, wl, subs, plans, dev, fill):
 
     one_pass()
     steps = max(1, min(args.steps, 3))
+    world = D.env()[0]
     torch.cuda.synchronize()
+    D.barrier(world)
     t0 = time.perf_counter()
     for _ in range(steps):
         one_pass()
-    dt = (time.perf_counter() - t0) / steps
+    dt = D.max_over_ranks((time.perf_counter() - t0) / steps, world, dev)
     for p in plans:
         p.close()
-    return {"value": wl.entries() / dt, "unit": "entries/s", "h2d_bytes_per_step": int(h2d),
+    return {"value": D.sum_over_ranks(wl.entries(), world, dev) / dt, "unit": "entries/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "steps": steps, "chunks": len(subs),
             "note": "pinned host inputs in, every FP64 entry back to pinned host memory, 2-stream pipeline"}
 
@@ -553,7 +545,9 @@ def run_fixed(args, wl):
     peaks, src = load_peaks()
     roof = roofline_for(wl, wl.npts, prec, mom_ms, con_ms, peaks, src)
     entries = wl.entries()
-    value = world * entries * args.steps / (total_ms * 1e-3)
+    job_entries = D.sum_over_ranks(entries, world, dev)  # each rank fills a batch of its own
+    job_elems = D.sum_over_ranks(wl.n_elem, world, dev)
+    value = job_entries * args.steps / (total_ms * 1e-3)
     e2e = None if args.no_e2e else measure_e2e_fixed(args, wl, ctx, prec, dev)
     line = None
     if rank == 0:
@@ -562,7 +556,7 @@ def run_fixed(args, wl):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args, wl),
-            "elements_per_s": world * wl.n_elem * args.steps / (total_ms * 1e-3),
+            "elements_per_s": job_elems * args.steps / (total_ms * 1e-3),
             "roofline": roof, "stages": {"moments_ms": mom_ms, "contract_ms": con_ms}, "clocks": clocks,
             "gpu_launches": 2 * args.steps,
         }
@@ -611,7 +605,7 @@ def main():
     if args.mode is None:
         args.mode = {"fp64": "plain", "mixed": "mixed"}.get(args.precision) or (
             "learned" if args.workload == "c5" else "plain")
-    wl = W.make(args.workload, args.elements)
+    wl = W.make(args.workload, args.elements, shard=D.env()[1])  # weak scaling: a batch per rank
     if args.npts:
         wl = wl.with_npts(args.npts)
     if args.impl == "reference":

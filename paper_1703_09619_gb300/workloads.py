@@ -111,13 +111,20 @@ def _scalar_params(n, A, phi, psi, c):
     return p
 
 
-def make(name: str, n_elem: int | None = None) -> Workload:
+SHARD_SEED_STRIDE = 1000
+
+
+def make(name: str, n_elem: int | None = None, shard: int = 0) -> Workload:
     """Build one of the named workloads (``c1`` .. ``c5``), optionally with fewer elements.
 
     Elements are always drawn for the full workload size and then truncated,
-    so element e is the same whatever ``n_elem`` is."""
+    so element e is the same whatever ``n_elem`` is.  ``shard`` s > 0 draws another
+    batch of the same recipe from its own seed (the batch of rank s when every rank
+    of a multi-GPU run fills a batch of its own); shard 0 is the canonical batch."""
     cid = {"c1": 1, "c2": 2, "c3": 3, "c4": 4, "c5": 5, "c5train": 50}[name]
-    rng = np.random.default_rng(SEED_BASE + cid)
+    if shard < 0:
+        raise ValueError("shard must be >= 0")
+    rng = np.random.default_rng(SEED_BASE + cid + SHARD_SEED_STRIDE * shard)
     if cid == 50:  # training elements for the learned order: the c5 recipe, its own seed
         E = 65536
         nodes, bulge = curved_geometry(rng, E)
@@ -184,6 +191,8 @@ def make(name: str, n_elem: int | None = None) -> Workload:
     if n_elem is not None and n_elem < w.n_elem:
         w = w.subset(np.arange(n_elem))
         w.name = name
+    if shard:
+        w.name = "%s/shard%d" % (w.name, shard)
     return w
 
 
