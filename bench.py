@@ -299,10 +299,10 @@ def time_steps(fn, steps, stream, flush):
     return [a.elapsed_time(b) for a, b in evs]
 
 
-def stage_times(p2s, ctx, wl, npts, prec, params, nodes, bulge, dev, stream, flush, steps=3):
+def stage_times(p2s, ctx, wl, npts, prec, params, nodes, bulge, dev, stream, flush, steps=3, tile=None):
     """Moment and contraction kernels timed separately on a plan with the given G per element."""
     import torch
-    plan = p2s.Plan(ctx, wl.orders, npts, prec, wl.types_mask)
+    plan = p2s.Plan(ctx, wl.orders, npts, prec, wl.types_mask, tile=tile)
     mom = torch.empty(max(plan.moment_entries, 1), dtype=torch.float64, device=dev)
     out = torch.empty(plan.output_entries, dtype=torch.float64, device=dev)
     plan.moments(wl.kind, params, nodes, bulge, mom, stream=stream)
@@ -518,16 +518,24 @@ def run_fixed(args, wl):
     ctx = p2s.Context(local)
     prec = p2s.MIXED if args.mode == "mixed" else p2s.FP64
     npts = int(wl.npts[0]) if (wl.npts == wl.npts[0]).all() else wl.npts
-    plan = p2s.Plan(ctx, wl.orders, npts, prec, wl.types_mask)
     params, nodes, bulge = p2s.device_inputs(wl, dev)
+    # batches of uneven orders: tile shapes from the autotuner, launches replayed from a graph
+    tune = args.tune if args.tune is not None else not (wl.orders == wl.orders[0, 0, 0]).all()
+    tile = tune_info = None
+    if tune:
+        sample = min(wl.n_elem, 1024)
+        tile, best_ms, tried = p2s.autotune_tiles(ctx, wl.orders, npts, wl.kind, params, nodes, bulge, prec,
+                                                  wl.types_mask, sample=sample, reps=3)
+        tune_info = {"tile": tile, "candidates": tried, "sample_elements": sample,
+                     "sample_contract_ms": best_ms}
+        log("autotune: %s (%d candidates, %.3f ms on %d elements)" % (tile, tried, best_ms, sample))
+    plan = p2s.Plan(ctx, wl.orders, npts, prec, wl.types_mask, tile=tile, graph=tune)
     out = torch.empty(plan.output_entries, dtype=torch.float64, device=dev)
-    mom = torch.empty(max(plan.moment_entries, 1), dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        plan.moments(wl.kind, params, nodes, bulge, mom, stream=stream)
-        plan.contract(mom, out, stream=stream)
+        plan.fill(wl.kind, params, nodes, bulge, out, stream=stream)
 
     for _ in range(args.warmup):
         step()
@@ -541,14 +549,14 @@ def run_fixed(args, wl):
     barrier(world)
     total_ms = max_over_ranks(float(sum(ms)), world, dev)
     clocks = clk.summary()
-    mom_ms, con_ms = stage_times(p2s, ctx, wl, npts, prec, params, nodes, bulge, dev, stream, flush)
+    mom_ms, con_ms = stage_times(p2s, ctx, wl, npts, prec, params, nodes, bulge, dev, stream, flush, tile=tile)
     peaks, src = load_peaks()
     roof = roofline_for(wl, wl.npts, prec, mom_ms, con_ms, peaks, src)
     entries = wl.entries()
     job_entries = D.sum_over_ranks(entries, world, dev)  # each rank fills a batch of its own
     job_elems = D.sum_over_ranks(wl.n_elem, world, dev)
     value = job_entries * args.steps / (total_ms * 1e-3)
-    e2e = None if args.no_e2e else measure_e2e_fixed(args, wl, ctx, prec, dev)
+    e2e = None if args.no_e2e else measure_e2e_fixed(args, wl, ctx, prec, dev, tile, tune)
     line = None
     if rank == 0:
         line = {
@@ -560,9 +568,12 @@ def run_fixed(args, wl):
             "roofline": roof, "stages": {"moments_ms": mom_ms, "contract_ms": con_ms}, "clocks": clocks,
             "gpu_launches": 2 * args.steps,
         }
+        if tune_info:
+            line["config"]["launch"] = "one CUDA graph per step (queue reset, moment kernel, contraction kernel)"
+            line["autotune"] = tune_info
         if e2e:
             line["e2e"] = e2e
-    del out, mom
+    del out
     plan.close()
     if rank == 0 and world == 1 and not args.no_cpu:
         v, dt, desc, threads = oracle_sample(wl, cpu_sample_size(args.workload))
@@ -576,14 +587,14 @@ def run_fixed(args, wl):
         dist.destroy_process_group()
 
 
-def measure_e2e_fixed(args, wl, ctx, prec, dev):
+def measure_e2e_fixed(args, wl, ctx, prec, dev, tile=None, graph=False):
     from paper_1703_09619_gb300 import p2s
     E = wl.n_elem
     per_elem = wl.entries() / E
     chunk = int(max(1, min(E, (2 << 30) // (8 * per_elem))))
     subs = [wl.subset(np.arange(s, min(E, s + chunk))) for s in range(0, E, chunk)]
     npts = lambda w: int(w.npts[0]) if (w.npts == w.npts[0]).all() else w.npts
-    plans = [p2s.Plan(ctx, w.orders, npts(w), prec, w.types_mask) for w in subs]
+    plans = [p2s.Plan(ctx, w.orders, npts(w), prec, w.types_mask, tile=tile, graph=graph) for w in subs]
     return _e2e_pipeline(args, wl, subs, plans, dev,
                          lambda p, w, di, o, s: p.fill(w.kind, di[0], di[1], di[2], o, stream=s))
 
@@ -601,6 +612,10 @@ def main():
     ap.add_argument("--npts", type=int, default=None, help="override the quadrature size G")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tune", dest="tune", action="store_true", default=None,
+                    help="autotune the contraction tiles and replay fills from a CUDA graph "
+                         "(default: on for batches of uneven orders)")
+    ap.add_argument("--no-tune", dest="tune", action="store_false")
     args = ap.parse_args()
     if args.mode is None:
         args.mode = {"fp64": "plain", "mixed": "mixed"}.get(args.precision) or (

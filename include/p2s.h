@@ -154,6 +154,59 @@ int p2s_plan_contract(p2s_plan* plan, const double* moments, double* out, void* 
 int p2s_plan_fill(p2s_plan* plan, const p2s_geometry* geom, const p2s_material* mat, double* out,
                   int32_t* elem_status, void* stream);
 
+/* ------------------------------------------------------------------------------------
+ * Tile shapes and launch replay of a plan (batches of uneven per-axis orders).  Not part
+ * of the paper.  The contraction of step a4 splits each (element, block, type) into work
+ * units of m1/n1 slabs that a persistent kernel takes from a queue; these calls choose
+ * the unit shape and replay a plan's launches from a CUDA graph.  Neither changes any
+ * computed value: every unit shape computes each entry with the same operations in the
+ * same order.
+ *
+ * p2s_tile_config (zero fields take the library default):
+ *   combo_target  stage-3 (m1, n1, m2, n2) combinations per work unit: slabs grow until
+ *                 they would pass it (default 256; 1..4096);
+ *   unit_kbytes   shared memory of one work unit in KiB, stage-1/2 buffers plus the staged
+ *                 output tile (general kernel only; default 100; up to 227);
+ *   threads       threads per CTA of the contraction, 64..512 in steps of 32 (default:
+ *                 one per combination of the largest unit). */
+typedef struct {
+    int combo_target;
+    int unit_kbytes;
+    int threads;
+} p2s_tile_config;
+
+/* p2s_plan_create with a tile configuration (NULL: defaults).  Errors as
+ * p2s_plan_create; P2S_ERR_ARG for a field out of range, P2S_ERR_ORDER when a unit of
+ * the batch does not fit the shared-memory budget. */
+int p2s_plan_create_tuned(p2s_ctx* ctx, int64_t n_elem, const p2s_orders* orders,
+                          const p2s_quadrature* quad, const p2s_fill_opts* opts,
+                          const p2s_tile_config* tile, p2s_plan** out);
+
+/* The tile configuration a plan uses, defaults and the CTA size resolved (host out). */
+int p2s_plan_tile_config(const p2s_plan* plan, p2s_tile_config* out);
+
+/* Autotuner: builds a plan per candidate configuration (combo targets 64..512 x budgets
+ * 24/48/100 KiB x derived/128/256-thread CTAs) on the first `sample` elements of the batch
+ * (<= 0: all), computes their moments once, times `reps` contractions of each candidate
+ * with CUDA events on `stream` (median) and writes the fastest to *best (host), its time
+ * in ms to *best_ms and the number of candidates that fit to *n_tried (both optional).
+ * Synchronises `stream`; allocates device scratch for the sample's moments and output.
+ * Geometry, material, orders and quadrature are those of the whole batch (the sample is
+ * its leading elements).  Errors: P2S_ERR_ARG, P2S_ERR_OOM, P2S_ERR_CUDA, P2S_ERR_ORDER
+ * (no candidate fits). */
+int p2s_autotune_tiles(p2s_ctx* ctx, const p2s_geometry* geom, const p2s_material* mat,
+                       const p2s_orders* orders, const p2s_quadrature* quad,
+                       const p2s_fill_opts* opts, int64_t sample, int reps,
+                       p2s_tile_config* best, double* best_ms, int* n_tried, void* stream);
+
+/* Replay p2s_plan_fill from a CUDA graph (enable != 0) or launch directly (0, the
+ * default).  With replay on, the first fill captures the plan's launch sequence (queue
+ * reset, moment kernel, contraction kernel) on a private stream and each later fill
+ * launches the captured graph on the caller's stream as one unit; a fill whose
+ * geometry, material, out or elem_status pointers or kind differ from the captured ones
+ * re-captures and updates the graph in place.  The other plan calls are unaffected. */
+int p2s_plan_use_graph(p2s_plan* plan, int enable);
+
 /* One-shot fill: plan, fill, release.  Same arguments and errors as the plan calls;
  * `out` must hold p2s_output_entries(...) doubles. */
 int p2s_fill_elements(p2s_ctx* ctx, const p2s_geometry* geom, const p2s_material* mat,

@@ -47,6 +47,14 @@ struct p2s_plan {
     ContractUnit* d_units = nullptr;
     unsigned long long* d_counter = nullptr;
     double* d_mom = nullptr;  // moment scratch of p2s_plan_fill
+    // CUDA-graph replay of p2s_plan_fill: the launch sequence (queue reset, moments,
+    // contraction) captured on a private stream, re-captured when the arguments change
+    bool use_graph = false;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    const void* gkey[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    int gkind = -1;
+    int64_t gn = -1;
 };
 
 // Run a CUDA call; on failure record it and return P2S_ERR_CUDA from the caller.
@@ -105,10 +113,9 @@ int64_t elem_moments(const int32_t* ord, int nc) {
 // so each such pair of blocks is computed once and written twice.  Slabs of m1 and n1
 // keep one unit's shared-memory tile small and its thread count near one per
 // stage-3 combination.
-constexpr int kComboTarget = 256;
-constexpr size_t kUnitBytesTarget = 100 * 1024;
-
-void slab_sizes(const ElemDesc& d, int gi, int gj, int& m1n, int& n1n, int spec_n) {
+void slab_sizes(const ElemDesc& d, int gi, int gj, int& m1n, int& n1n, int spec_n, const TileParams& tp) {
+    const int kComboTarget = tp.combo_target;
+    const size_t kUnitBytesTarget = tp.unit_bytes;
     const int8_t* Ni = d.ord[gi];
     const int8_t* Nj = d.ord[gj];
     n1n = Ni[1];
@@ -130,9 +137,10 @@ void slab_sizes(const ElemDesc& d, int gi, int gj, int& m1n, int& n1n, int spec_
             ++m1n;
 }
 
-void push_block(const ElemDesc& d, int32_t e, int gi, int gj, int t, int tp, UnitSink& units, int spec_n) {
+void push_block(const ElemDesc& d, int32_t e, int gi, int gj, int t, int tp, UnitSink& units, int spec_n,
+                const TileParams& tile) {
     int m1n, n1n;
-    slab_sizes(d, gi, gj, m1n, n1n, spec_n);
+    slab_sizes(d, gi, gj, m1n, n1n, spec_n, tile);
     const int Nu = d.ord[gi][0], Nv = d.ord[gi][1];
     for (int m1a = 0; m1a < Nu; m1a += m1n)
         for (int n1a = 0; n1a < Nv; n1a += n1n) {
@@ -151,18 +159,18 @@ void push_block(const ElemDesc& d, int32_t e, int gi, int gj, int t, int tp, Uni
         }
 }
 
-void add_units(const ElemDesc& d, uint32_t mask, int32_t e, UnitSink& units, int spec_n) {
+void add_units(const ElemDesc& d, uint32_t mask, int32_t e, UnitSink& units, int spec_n, const TileParams& tile) {
     const int nc = d.n_comp;
     for (int t : {0, 3}) {  // vv, dd: upper blocks, transposed into the lower ones
         if (!(mask & (1u << t))) continue;
         for (int gi = 0; gi < nc; ++gi)
-            for (int gj = gi; gj < nc; ++gj) push_block(d, e, gi, gj, t, gi == gj ? -1 : t, units, spec_n);
+            for (int gj = gi; gj < nc; ++gj) push_block(d, e, gi, gj, t, gi == gj ? -1 : t, units, spec_n, tile);
     }
     const bool dv = mask & 2u, vd = mask & 4u;
     if (dv || vd) {  // dv(gi,gj) and its transpose vd(gj,gi)
         const int t = dv ? 1 : 2, tp = (dv && vd) ? 2 : -1;
         for (int gi = 0; gi < nc; ++gi)
-            for (int gj = 0; gj < nc; ++gj) push_block(d, e, gi, gj, t, tp, units, spec_n);
+            for (int gj = 0; gj < nc; ++gj) push_block(d, e, gi, gj, t, tp, units, spec_n, tile);
     }
 }
 
@@ -170,8 +178,20 @@ void add_units(const ElemDesc& d, uint32_t mask, int32_t e, UnitSink& units, int
 
 namespace p2s {
 
+int tile_params_from(const p2s_tile_config* c, TileParams& tp) {
+    tp = TileParams();
+    if (!c) return P2S_OK;
+    if (c->combo_target < 0 || c->combo_target > 4096 || c->unit_kbytes < 0 || c->unit_kbytes > 227 ||
+        c->threads < 0 || c->threads > 512 || (c->threads && (c->threads < 64 || c->threads % 32)))
+        return fail(P2S_ERR_ARG, "tile config: combo_target 0..4096, unit_kbytes 0..227, threads 0 or 64..512 in steps of 32");
+    if (c->combo_target) tp.combo_target = c->combo_target;
+    if (c->unit_kbytes) tp.unit_bytes = (size_t)c->unit_kbytes * 1024;
+    tp.threads = c->threads;
+    return P2S_OK;
+}
+
 int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, const p2s_quadrature* quad,
-                 const p2s_fill_opts* opts, ElemDesc* desc, UnitSink& units, PlanLayout& L) {
+                 const p2s_fill_opts* opts, ElemDesc* desc, UnitSink& units, PlanLayout& L, const TileParams& tile) {
     if (!quad || !opts) return fail(P2S_ERR_ARG, "plan: NULL quadrature or options");
     int rc = check_orders(E, orders);
     if (rc) return rc;
@@ -237,7 +257,7 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
         max_pair = std::max(max_pair, d.kax[0] * d.kax[1] * d.kax[2]);
         max_elem_mom = std::max(max_elem_mom, L.n_pairs * d.kax[0] * d.kax[1] * d.kax[2]);
         L.gmax = std::max(L.gmax, G);
-        add_units(d, opts->types_mask, (int32_t)e, units, spec_n);
+        add_units(d, opts->types_mask, (int32_t)e, units, spec_n, tile);
     }
     L.out_entries = out_off;
     L.mom_entries = mom_off;
@@ -268,7 +288,7 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
         for (int gi = 0; gi < nc; ++gi)
             for (int gj = 0; gj < nc; ++gj) {
                 int m1n, n1n;
-                slab_sizes(d, gi, gj, m1n, n1n, 0);
+                slab_sizes(d, gi, gj, m1n, n1n, 0, tile);
                 ContractShape sh = contract_shape(d.ord[gi], d.ord[gj], m1n, n1n);
                 L.a_cap = std::max(L.a_cap, sh.a);
                 L.b_cap = std::max(L.b_cap, sh.b);
@@ -276,7 +296,8 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
                 max_combos = std::max(max_combos, sh.combos);
             }
     }
-    L.con_threads = std::min(512, std::max(64, (max_combos + 31) / 32 * 32));
+    L.tile = tile;
+    L.con_threads = tile.threads ? tile.threads : std::min(512, std::max(64, (max_combos + 31) / 32 * 32));
     L.tile_off = contract_tile_offset(L.precision, L.a_cap, L.b_cap);
     L.con_smem = contract_smem_bytes(L.precision, L.a_cap, L.b_cap, L.tile_cap);
     if (!spec_n) {
@@ -288,11 +309,11 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
 
     if (spec_n) {
         int m1n, n1n;
-        slab_sizes(desc[0], 0, 0, m1n, n1n, spec_n);
+        slab_sizes(desc[0], 0, 0, m1n, n1n, spec_n, tile);
         size_t a, bcap, tl;
         int combos;
         contract_ff_shape(spec_n, m1n, a, bcap, tl, combos);
-        const int threads = std::min(512, std::max(64, (combos + 31) / 32 * 32));
+        const int threads = tile.threads ? tile.threads : std::min(512, std::max(64, (combos + 31) / 32 * 32));
         const size_t smem = (a + bcap) * sizeof(float2);
         const int per_sm = smem <= limit ? contract_ffn_blocks_per_sm(spec_n, threads, smem) : 0;
         if (per_sm < 1) return fail(P2S_ERR_ORDER, "plan: specialised contraction kernel does not fit");
@@ -508,6 +529,8 @@ int64_t p2s_moment_entries(int64_t n_elem, const p2s_orders* orders, int64_t* of
 void p2s_plan_destroy(p2s_plan* p) {
     if (!p) return;
     if (p->ctx) cudaSetDevice(p->ctx->T.device);
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     cudaFree(p->d_desc);
     cudaFree(p->d_units);
     cudaFree(p->d_counter);
@@ -517,9 +540,17 @@ void p2s_plan_destroy(p2s_plan* p) {
 
 int p2s_plan_create(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, const p2s_quadrature* quad,
                     const p2s_fill_opts* opts, p2s_plan** out) {
+    return p2s_plan_create_tuned(ctx, E, orders, quad, opts, nullptr, out);
+}
+
+int p2s_plan_create_tuned(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, const p2s_quadrature* quad,
+                          const p2s_fill_opts* opts, const p2s_tile_config* tile, p2s_plan** out) {
     if (!ctx || !out) return fail(P2S_ERR_ARG, "p2s_plan_create: NULL context or out");
     *out = nullptr;
     if (E < 0) return fail(P2S_ERR_ARG, "p2s_plan_create: negative n_elem");
+    TileParams tp;
+    int trc = tile_params_from(tile, tp);
+    if (trc) return trc;
     if (set_device(ctx->T.device)) return P2S_ERR_CUDA;
     std::vector<ElemDesc> desc((size_t)std::max<int64_t>(E, 1));
     std::vector<ContractUnit> units;
@@ -528,7 +559,7 @@ int p2s_plan_create(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, const p2s
     p2s_plan* p = new (std::nothrow) p2s_plan();
     if (!p) return fail(P2S_ERR_OOM, "p2s_plan_create: host allocation");
     p->ctx = ctx;
-    int rc = build_layout(ctx->T, E, orders, quad, opts, desc.data(), sink, p->L);
+    int rc = build_layout(ctx->T, E, orders, quad, opts, desc.data(), sink, p->L, tp);
     if (rc) {
         delete p;
         return rc;
@@ -568,10 +599,79 @@ int p2s_plan_contract(p2s_plan* p, const double* moments, double* out, void* str
     return run_contract(p->ctx->T, p->L, p->d_desc, p->d_units, p->d_counter, moments, out, (cudaStream_t)stream);
 }
 
+int p2s_plan_tile_config(const p2s_plan* p, p2s_tile_config* out) {
+    if (!p || !out) return fail(P2S_ERR_ARG, "p2s_plan_tile_config: NULL plan or out");
+    out->combo_target = p->L.tile.combo_target;
+    out->unit_kbytes = (int)(p->L.tile.unit_bytes / 1024);
+    out->threads = p->L.con_threads;
+    return P2S_OK;
+}
+
+int p2s_plan_use_graph(p2s_plan* p, int enable) {
+    if (!p) return fail(P2S_ERR_ARG, "p2s_plan_use_graph: NULL plan");
+    if (set_device(p->ctx->T.device)) return P2S_ERR_CUDA;
+    if (enable && !p->cap_stream) P2S_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+    p->use_graph = enable != 0;
+    return P2S_OK;
+}
+
+// Capture the plan's launch sequence for these arguments on the private stream and make
+// p->gexec replay it (instantiated once, then updated in place when the arguments change).
+static int plan_capture(p2s_plan* p, const p2s_geometry* geom, const p2s_material* mat, double* out,
+                        int32_t* elem_status) {
+    cudaStream_t cs = p->cap_stream;
+    P2S_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    int rc = run_moments(p->ctx->T, p->L, p->d_desc, geom, mat, p->d_mom, elem_status, cs);
+    if (rc == P2S_OK) rc = run_contract(p->ctx->T, p->L, p->d_desc, p->d_units, p->d_counter, p->d_mom, out, cs);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(cs, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (ce != cudaSuccess) return fail(P2S_ERR_CUDA, "p2s_plan_fill: graph capture", ce);
+    if (p->gexec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(p->gexec, g, &info) != cudaSuccess) {
+            cudaGetLastError();  // an update that does not fit is not an error: instantiate anew
+            cudaGraphExecDestroy(p->gexec);
+            p->gexec = nullptr;
+        }
+    }
+    if (!p->gexec) ce = cudaGraphInstantiate(&p->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) {
+        p->gexec = nullptr;
+        return fail(P2S_ERR_CUDA, "p2s_plan_fill: graph instantiate", ce);
+    }
+    p->gkey[0] = geom ? geom->nodes : nullptr;
+    p->gkey[1] = geom ? geom->bulge : nullptr;
+    p->gkey[2] = mat ? mat->params : nullptr;
+    p->gkey[3] = out;
+    p->gkey[4] = elem_status;
+    p->gkey[5] = p->d_mom;
+    p->gkind = mat ? mat->kind : -1;
+    p->gn = geom ? geom->n_elem : -1;
+    return P2S_OK;
+}
+
 int p2s_plan_fill(p2s_plan* p, const p2s_geometry* geom, const p2s_material* mat, double* out,
                   int32_t* elem_status, void* stream) {
     if (!p) return fail(P2S_ERR_ARG, "p2s_plan_fill: NULL plan");
     if (!out && p->L.n_units) return fail(P2S_ERR_ARG, "p2s_plan_fill: NULL out");
+    if (p->use_graph && p->L.n_elem > 0) {
+        if (set_device(p->ctx->T.device)) return P2S_ERR_CUDA;
+        if (!geom || !mat) return fail(P2S_ERR_ARG, "p2s_plan_fill: NULL geometry or material");
+        const bool same = p->gexec && p->gkey[0] == geom->nodes && p->gkey[1] == geom->bulge &&
+                          p->gkey[2] == mat->params && p->gkey[3] == out && p->gkey[4] == elem_status &&
+                          p->gkind == mat->kind && p->gn == geom->n_elem;
+        if (!same) {
+            int rc = plan_capture(p, geom, mat, out, elem_status);
+            if (rc) return rc;
+        }
+        P2S_CUDA(cudaGraphLaunch(p->gexec, (cudaStream_t)stream));
+        return P2S_OK;
+    }
     int rc = p2s_plan_moments(p, geom, mat, p->d_mom, elem_status, stream);
     if (rc) return rc;
     return p2s_plan_contract(p, p->d_mom, out, stream);

@@ -144,6 +144,13 @@ struct DeviceTables {
 };
 
 // Everything a fill needs besides device buffers: sizes and launch shapes.
+// Tile configuration of the contraction (the p2s_tile_config of the C ABI, defaults filled in).
+struct TileParams {
+    int combo_target = 256;             // stage-3 combinations per work unit
+    size_t unit_bytes = 100 * 1024;     // shared memory of one unit (generic kernel)
+    int threads = 0;                    // CTA size; 0: one thread per combination of the largest unit
+};
+
 struct PlanLayout {
     int64_t n_elem = 0;
     int n_comp = 0;
@@ -158,6 +165,7 @@ struct PlanLayout {
     size_t con_smem = 0, tile_off = 0;
     int con_grid = 1;
     int spec_n = 0;  // > 0: the mixed contraction specialised for uniform order N
+    TileParams tile;  // the tile configuration in effect
 };
 
 // Destination of the contraction work list: a growing vector, or a fixed array that
@@ -177,10 +185,13 @@ struct UnitSink {
 
 // Record a failure for p2s_last_error and return `code`.
 int fail(int code, const char* where, cudaError_t ce = cudaSuccess);
+// TileParams from a p2s_tile_config (NULL or zero fields: defaults); P2S_ERR_ARG if out of range.
+int tile_params_from(const p2s_tile_config* c, TileParams& tp);
 // Validate the arguments and fill desc[0..E) (host), the work list and the layout.
 // The first call with units.buf == nullptr && units.vec == nullptr only counts units.
 int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, const p2s_quadrature* quad,
-                 const p2s_fill_opts* opts, ElemDesc* desc, UnitSink& units, PlanLayout& L);
+                 const p2s_fill_opts* opts, ElemDesc* desc, UnitSink& units, PlanLayout& L,
+                 const TileParams& tile = TileParams());
 int run_moments(const DeviceTables& T, const PlanLayout& L, const ElemDesc* d_desc, const p2s_geometry* geom,
                 const p2s_material* mat, void* moments, int32_t* elem_status, cudaStream_t s,
                 const int8_t* elem_mask = nullptr);

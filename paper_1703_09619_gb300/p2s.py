@@ -54,6 +54,14 @@ class FillOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("types_mask", ctypes.c_uint32)]
 
 
+class TileConfig(ctypes.Structure):
+    """p2s_tile_config: contraction work-unit shape (zero fields: library default)."""
+    _fields_ = [("combo_target", ctypes.c_int), ("unit_kbytes", ctypes.c_int), ("threads", ctypes.c_int)]
+
+    def as_dict(self):
+        return {"combo_target": self.combo_target, "unit_kbytes": self.unit_kbytes, "threads": self.threads}
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -67,6 +75,14 @@ SIGNATURES = {
     "p2s_moment_entries": (_I64, [_I64, ctypes.POINTER(Orders), _P]),
     "p2s_plan_create": (ctypes.c_int, [_P, _I64, ctypes.POINTER(Orders), ctypes.POINTER(Quadrature),
                                        ctypes.POINTER(FillOpts), ctypes.POINTER(ctypes.c_void_p)]),
+    "p2s_plan_create_tuned": (ctypes.c_int, [_P, _I64, ctypes.POINTER(Orders), ctypes.POINTER(Quadrature),
+                                             ctypes.POINTER(FillOpts), _P, ctypes.POINTER(ctypes.c_void_p)]),
+    "p2s_plan_tile_config": (ctypes.c_int, [_P, ctypes.POINTER(TileConfig)]),
+    "p2s_autotune_tiles": (ctypes.c_int, [_P, ctypes.POINTER(Geometry), ctypes.POINTER(Material),
+                                          ctypes.POINTER(Orders), ctypes.POINTER(Quadrature),
+                                          ctypes.POINTER(FillOpts), _I64, ctypes.c_int, ctypes.POINTER(TileConfig),
+                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _P]),
+    "p2s_plan_use_graph": (ctypes.c_int, [_P, ctypes.c_int]),
     "p2s_plan_destroy": (None, [_P]),
     "p2s_plan_output_entries": (_I64, [_P]),
     "p2s_plan_moment_entries": (_I64, [_P]),
@@ -227,21 +243,23 @@ class Context:
 class Plan:
     """A p2s_plan: descriptors, work list and launch shapes for one batch shape."""
 
-    def __init__(self, ctx: Context, orders, npts, precision=FP64, types_mask=TYPES_ALL):
+    def __init__(self, ctx: Context, orders, npts, precision=FP64, types_mask=TYPES_ALL, tile=None, graph=False):
+        """tile: a TileConfig or dict (combo_target, unit_kbytes, threads) for
+        p2s_plan_create_tuned; graph: replay fills from a CUDA graph (p2s_plan_use_graph)."""
         lib = load()
         self.ctx = ctx
         o, self._orders = _orders_struct(orders)
         E = self._orders.shape[0]
-        if np.isscalar(npts):
-            q = Quadrature(int(npts), None)
-            self._npts = None
-        else:
-            self._npts = np.ascontiguousarray(npts, dtype=np.int32).reshape(E)
-            q = Quadrature(0, ctypes.c_void_p(self._npts.ctypes.data))
+        q, self._npts = _quadrature_struct(npts, E)
         opts = FillOpts(int(precision), int(types_mask))
         h = ctypes.c_void_p()
-        _check(lib.p2s_plan_create(ctx.handle, E, ctypes.byref(o), ctypes.byref(q), ctypes.byref(opts),
-                                   ctypes.byref(h)), "p2s_plan_create")
+        if tile is None:
+            _check(lib.p2s_plan_create(ctx.handle, E, ctypes.byref(o), ctypes.byref(q), ctypes.byref(opts),
+                                       ctypes.byref(h)), "p2s_plan_create")
+        else:
+            t = tile if isinstance(tile, TileConfig) else TileConfig(**tile)
+            _check(lib.p2s_plan_create_tuned(ctx.handle, E, ctypes.byref(o), ctypes.byref(q), ctypes.byref(opts),
+                                             ctypes.byref(t), ctypes.byref(h)), "p2s_plan_create_tuned")
         self.handle = h
         self.n_elem = E
         self.n_comp = int(self._orders.shape[1])
@@ -249,6 +267,16 @@ class Plan:
         self.precision = precision
         self.output_entries = int(lib.p2s_plan_output_entries(h))
         self.moment_entries = int(lib.p2s_plan_moment_entries(h))
+        if graph:
+            self.use_graph(True)
+
+    def tile_config(self) -> dict:
+        t = TileConfig()
+        _check(load().p2s_plan_tile_config(self.handle, ctypes.byref(t)), "p2s_plan_tile_config")
+        return t.as_dict()
+
+    def use_graph(self, enable=True):
+        _check(load().p2s_plan_use_graph(self.handle, int(bool(enable))), "p2s_plan_use_graph")
 
     def close(self):
         if getattr(self, "handle", None):
@@ -280,6 +308,33 @@ class Plan:
         g, m = self._inputs(kind, params, nodes, bulge)
         _check(load().p2s_plan_fill(self.handle, ctypes.byref(g), ctypes.byref(m), _dptr(out),
                                     _dptr(elem_status), _stream(stream)), "p2s_plan_fill")
+
+
+def _quadrature_struct(npts, E):
+    if np.isscalar(npts):
+        return Quadrature(int(npts), None), None
+    keep = np.ascontiguousarray(npts, dtype=np.int32).reshape(E)
+    return Quadrature(0, ctypes.c_void_p(keep.ctypes.data)), keep
+
+
+def autotune_tiles(ctx: Context, orders, npts, kind, params, nodes, bulge, precision=FP64, types_mask=TYPES_ALL,
+                   sample=0, reps=3, stream=None):
+    """p2s_autotune_tiles: the fastest contraction tile configuration on the leading
+    `sample` elements (0: all).  Returns (config dict, best ms, candidates tried)."""
+    lib = load()
+    o, keep = _orders_struct(orders)
+    E = keep.shape[0]
+    q, npk = _quadrature_struct(npts, E)
+    g = Geometry(E, _dptr(nodes), _dptr(bulge))
+    m = Material(int(kind), _dptr(params))
+    opts = FillOpts(int(precision), int(types_mask))
+    best = TileConfig()
+    ms = ctypes.c_double()
+    tried = ctypes.c_int()
+    _check(lib.p2s_autotune_tiles(ctx.handle, ctypes.byref(g), ctypes.byref(m), ctypes.byref(o), ctypes.byref(q),
+                                  ctypes.byref(opts), int(sample), int(reps), ctypes.byref(best), ctypes.byref(ms),
+                                  ctypes.byref(tried), _stream(stream)), "p2s_autotune_tiles")
+    return best.as_dict(), ms.value, tried.value
 
 
 def fill_elements(ctx: Context, orders, npts, kind, params, nodes, bulge, out, elem_status=None,
