@@ -519,8 +519,8 @@ def run_fixed(args, wl):
     prec = p2s.MIXED if args.mode == "mixed" else p2s.FP64
     npts = int(wl.npts[0]) if (wl.npts == wl.npts[0]).all() else wl.npts
     params, nodes, bulge = p2s.device_inputs(wl, dev)
-    # batches of uneven orders: tile shapes from the autotuner, launches replayed from a graph
-    tune = args.tune if args.tune is not None else not (wl.orders == wl.orders[0, 0, 0]).all()
+    # tile shapes from the autotuner, launches replayed from a graph (on by default)
+    tune = args.tune if args.tune is not None else True
     tile = tune_info = None
     if tune:
         sample = min(wl.n_elem, 1024)
@@ -613,8 +613,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tune", dest="tune", action="store_true", default=None,
-                    help="autotune the contraction tiles and replay fills from a CUDA graph "
-                         "(default: on for batches of uneven orders)")
+                    help="autotune the contraction tiles and replay fills from a CUDA graph (default: on)")
     ap.add_argument("--no-tune", dest="tune", action="store_false")
     args = ap.parse_args()
     if args.mode is None:

@@ -6,9 +6,11 @@
 //   stage 1  A[m1][m2][l][q]        = sum_k C_t[m1,m2,k] I[k][l][q]
 //   stage 2  Bt[m1][n1][m2][n2][q]  = sum_l C_t[n1,n2,l] A[m1][m2][l][q]
 //   stage 3  tile[(m1,n1,p1)][(m2,n2,p2)] = sum_q C_t[p1,p2,q] Bt[m1][n1][m2][n2][q]
-// Stage 3 gives each thread one (m1,n1,m2,n2) combination and walks (p1,p2) in the same
-// order on every thread, so the coefficient runs are uniform across the CTA.  The tile is
-// staged in shared memory and leaves twice, both times as contiguous row segments:
+// Stage 3 takes items (p1, combination (m1,n1,m2,n2)) with p1 outermost, so the lanes of a
+// warp share p1 and walk p2 in step: the coefficient runs are uniform across the warp.  The
+// tile is staged in shared memory with the columns of a row ordered p2-major (consecutive
+// lanes store consecutive doubles; odd strides keep the write-out reads conflict-free), and
+// it leaves twice, both times as contiguous row segments:
 //   - as rows of M_t(gi,gj), and
 //   - transposed, as rows of the partner block M_t'(gj,gi) = M_t(gi,gj)^T, where
 //     t' = t for vv and dd (alpha symmetric) and t' = vd for t = dv.
@@ -39,6 +41,7 @@ __global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
     __shared__ ContractUnit cu;
     __shared__ unsigned long long unit_id;
     __shared__ int32_t s_lin[kMaxOrder * kMaxOrder];
+    __shared__ int16_t s_col[kMaxOrder * kMaxOrder * kMaxOrder];  // tile offset of output column c
     const int tid = threadIdx.x, nth = blockDim.x;
     const int32_t* __restrict__ lidx = L.lin_idx;
     const void* lcoef = L.lin_coef;
@@ -62,11 +65,17 @@ __global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
         const int Kv = Nv_i + Nv_j - 1, Kw = Nw_i + Nw_j - 1;
         const int n = d->n;
         const int nj = Nu_j * Nv_j * Nw_j;
-        const int ld = nj + 1;  // padded tile row stride (doubles)
+        const int mjp = contract_mj_stride(Nu_j * Nv_j);
+        const int ld = contract_tile_ld(Nu_j * Nv_j, Nw_j);  // padded tile row stride (doubles)
         const size_t moff = d->mom_off + d->pair_off[pair_index(gi, gj, d->n_comp)];
 
-        // the unit's stage-3 coefficient runs, shared by every thread
+        // the unit's stage-3 coefficient runs, shared by every thread, and the tile offset of
+        // every output column (m2, n2, p2)
         if (tid < Nw_i * Nw_j) s_lin[tid] = __ldg(lidx + lin_slot(t, tid / Nw_j, tid % Nw_j));
+        for (int c = tid; c < nj; c += nth) {
+            const int mj = c / Nw_j;
+            s_col[c] = (int16_t)((c - mj * Nw_j) * mjp + mj);
+        }
 
         // stage 1: A[m1][m2][l][q], m1 in the slab
         const int KvKw = Kv * Kw;
@@ -98,21 +107,21 @@ __global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
             sB[idx] = A::finish(acc);
         }
         __syncthreads();
-        // stage 3: combos (m1, n1, m2, n2); each walks (p1, p2)
+        // stage 3: items (p1, combination (m1, n1, m2, n2)); each walks p2
         const int ncombo = m1n * n1n * Nu_j * Nv_j;
         const int mjn = Nu_j * Nv_j;
-        for (int c = tid; c < ncombo; c += nth) {
+        for (int it = tid; it < ncombo * Nw_i; it += nth) {
+            const int p1 = it / ncombo, c = it - p1 * ncombo;
             const int mn = c / mjn, mj = c - mn * mjn;  // mn = im1 * n1n + in1, mj = m2 * Nv_j + n2
             const T* bt = sB + (size_t)c * Kw;
-            double* trow = tile + (size_t)(mn * Nw_i) * ld + mj * Nw_j;
-            for (int p1 = 0; p1 < Nw_i; ++p1) {
-                for (int p2 = 0; p2 < Nw_j; ++p2) {
-                    const int32_t li = s_lin[p1 * Nw_j + p2];
-                    const int q0 = lin_kmin(li), cnt = lin_cnt(li), off = lin_off(li);
-                    T acc = A::zero();
-                    for (int r = 0; r < cnt; ++r) A::fma_acc(acc, A::load_coef(lcoef, off + r), bt[q0 + 2 * r]);
-                    trow[p1 * ld + p2] = A::to_double(A::finish(acc));
-                }
+            double* trow = tile + (size_t)(mn * Nw_i + p1) * ld + mj;
+            const int32_t* lrow = s_lin + p1 * Nw_j;
+            for (int p2 = 0; p2 < Nw_j; ++p2) {
+                const int32_t li = lrow[p2];
+                const int q0 = lin_kmin(li), cnt = lin_cnt(li), off = lin_off(li);
+                T acc = A::zero();
+                for (int r = 0; r < cnt; ++r) A::fma_acc(acc, A::load_coef(lcoef, off + r), bt[q0 + 2 * r]);
+                trow[p2 * mjp] = A::to_double(A::finish(acc));
             }
         }
         __syncthreads();
@@ -127,14 +136,15 @@ __global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
         for (int r = warp; r < rows; r += nwarp) {
             double* dst = Mt + (int64_t)(rbase + r) * n;
             const double* src = tile + (size_t)r * ld;
-            for (int c = lane; c < nj; c += 32) __stcs(dst + c, src[c]);
+            for (int c = lane; c < nj; c += 32) __stcs(dst + c, src[s_col[c]]);
         }
         // write-out 2: the transpose, one warp per row of the partner block (gj, gi)
         if (cu.tp >= 0) {
             double* Mp = L.out + d->out_off + (int64_t)type_slot(L.types_mask, cu.tp) * n * n + rbase;
             for (int c = warp; c < nj; c += nwarp) {
                 double* dst = Mp + (int64_t)(col0 + c) * n;
-                for (int r = lane; r < rows; r += 32) __stcs(dst + r, tile[(size_t)r * ld + c]);
+                const double* src = tile + s_col[c];
+                for (int r = lane; r < rows; r += 32) __stcs(dst + r, src[(size_t)r * ld]);
             }
         }
         __syncthreads();
@@ -159,7 +169,7 @@ ContractShape contract_shape(const int8_t* Ni, const int8_t* Nj, int m1n, int n1
     const int Kv = Ni[1] + Nj[1] - 1, Kw = Ni[2] + Nj[2] - 1;
     s.a = (size_t)m1n * Nj[0] * Kv * Kw;
     s.b = (size_t)m1n * n1n * Nj[0] * Nj[1] * Kw;
-    s.tile = (size_t)m1n * n1n * Ni[2] * (Nj[0] * Nj[1] * Nj[2] + 1);
+    s.tile = (size_t)m1n * n1n * Ni[2] * contract_tile_ld(Nj[0] * Nj[1], Nj[2]);
     s.combos = m1n * n1n * Nj[0] * Nj[1];
     return s;
 }

@@ -111,6 +111,12 @@ struct ContractShape {
     size_t a, b, tile;
     int combos;
 };
+// Staged contraction tile: within a row, output column (m2, n2, p2) sits at p2 * mjp + mj
+// (mj = m2 * Nv_j + n2, mjp = mjn rounded up to odd) and rows have an odd stride, so the
+// stage-3 stores (consecutive mj), the row reads (stride mjp) and the column reads (stride
+// ld) of the write-outs are all free of bank conflicts.
+__host__ __device__ __forceinline__ int contract_mj_stride(int mjn) { return mjn | 1; }
+__host__ __device__ __forceinline__ int contract_tile_ld(int mjn, int nw) { return (nw * contract_mj_stride(mjn)) | 1; }
 ContractShape contract_shape(const int8_t* Ni, const int8_t* Nj, int m1n, int n1n);
 size_t contract_tile_offset(int precision, size_t a_cap, size_t b_cap);
 size_t contract_smem_bytes(int precision, size_t a_cap, size_t b_cap, size_t tile_cap);
