@@ -50,9 +50,11 @@ ALPHA_FLOP_PER_POINT = 134
 #   the metric coupling factor at one point, with the _fast double-word operations (add 11,
 #   product 4, fused 15, division 11): 839 (Jacobian from row constants 241, phase 30,
 #   sin 110 + scale 14, cofactors 171, det 34, division 11, six products 228);
-#   the scalar coupling factor at one point: 14.
+#   the scalar coupling factor at one point: 14;
+#   the parity fold of the first mode product, per point and pair: one sum (11) and two
+#   shuffles; the first mode product then runs over ceil(G/2) points per row.
 FP32_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
-DW_MAC_OPS, DW_ALPHA_OPS_METRIC, DW_ALPHA_OPS_SCALAR = 12, 839, 14
+DW_MAC_OPS, DW_ALPHA_OPS_METRIC, DW_ALPHA_OPS_SCALAR, DW_FOLD_OPS = 12, 839, 14, 13
 # Learned-fill settings: judge share and tolerance; risk of the class rule (the largest
 # value of the sweep 0.02 .. 0.0005 with no element of the batch above 1e-8).
 JUDGE_FRAC, JUDGE_TOL, RISK = 0.02, 1e-9, 0.002
@@ -112,17 +114,19 @@ def contract_fma_count(orders, types_mask):
     return total
 
 
-def moment_mac_points(orders, npts):
-    """Sum-factorised moment MACs and quadrature points of a batch."""
+def moment_mac_points(orders, npts, folded=False):
+    """Sum-factorised moment MACs, quadrature points and pairs of a batch; with ``folded`` the
+    first mode product runs over ceil(G/2) points per row (parity fold of the symmetric rule)."""
     macs = pts = 0
     nc = orders.shape[1]
     npairs = 1 if nc == 1 else 6
     for e in range(orders.shape[0]):
         K = [int(k) for k in 2 * orders[e].max(axis=0) - 1]
         G = int(npts[e])
-        macs += npairs * (K[0] * G ** 3 + K[0] * K[1] * G ** 2 + K[0] * K[1] * K[2] * G)
+        ga = (G + 1) // 2 if folded else G
+        macs += npairs * (K[0] * ga * G ** 2 + K[0] * K[1] * G ** 2 + K[0] * K[1] * K[2] * G)
         pts += G ** 3
-    return macs, pts
+    return macs, pts, npairs
 
 
 def moment_flop_count(orders, npts, metric=True):
@@ -321,15 +325,16 @@ def roofline_for(wl, npts, prec, mom_ms, con_ms, peaks, src):
     metric = wl.kind == W.KIND_METRIC_EPS
     npts = np.broadcast_to(np.asarray(npts), (wl.n_elem,))
     if mom_ms >= con_ms and prec != 0:
-        macs, pts = moment_mac_points(wl.orders, npts)
-        ops = DW_MAC_OPS * macs + (DW_ALPHA_OPS_METRIC if metric else DW_ALPHA_OPS_SCALAR) * pts
+        macs, pts, npairs = moment_mac_points(wl.orders, npts, folded=True)
+        per_point = (DW_ALPHA_OPS_METRIC if metric else DW_ALPHA_OPS_SCALAR) + DW_FOLD_OPS * npairs
+        ops = DW_MAC_OPS * macs + per_point * pts
         ach = ops / (mom_ms * 1e-3) / 1e12
         return {"bound": "alu", "kernel": "k_moments_dw", "achieved": ach, "peak": FP32_PEAK_TOPS,
                 "unit": "T FP32 lane-op/s", "frac": ach / FP32_PEAK_TOPS, "traffic": None,
                 "peak_source": "FP32 issue: 152 SMs x 128 lanes x 2.07 GHz (recipe unit counts and clock)",
                 "algorithmic_ops_per_launch": int(ops),
-                "op_model": "%d per double-word MAC x %d MACs + %d per point x %d points" % (
-                    DW_MAC_OPS, macs, DW_ALPHA_OPS_METRIC if metric else DW_ALPHA_OPS_SCALAR, pts)}
+                "op_model": "%d per double-word MAC x %d MACs (first mode product folded) + %d per point x %d points" % (
+                    DW_MAC_OPS, macs, per_point, pts)}
     if mom_ms >= con_ms:
         mflop = moment_flop_count(wl.orders, npts, metric)
         ach = mflop / (mom_ms * 1e-3) / 1e12
@@ -502,9 +507,27 @@ def _e2e_pipeline(args, wl, subs, plans, dev, fill):
     dt = D.max_over_ranks((time.perf_counter() - t0) / steps, world, dev)
     for p in plans:
         p.close()
+    # the host link bounds this figure: every FP64 entry crosses it once
+    link = d2h_bandwidth(host_out[0], dev_out[0])
     return {"value": D.sum_over_ranks(wl.entries(), world, dev) / dt, "unit": "entries/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "steps": steps, "chunks": len(subs),
-            "note": "pinned host inputs in, every FP64 entry back to pinned host memory, 2-stream pipeline"}
+            "d2h_link_gbs": link, "d2h_achieved_gbs": d2h / dt / 1e9, "frac_of_link": d2h / dt / 1e9 / link,
+            "note": "pinned host inputs in, every FP64 entry back to pinned host memory, 2-stream pipeline; "
+                    "d2h_link_gbs = one large device-to-host copy measured in the same process"}
+
+
+def d2h_bandwidth(host, devbuf, nbytes=2 << 30):
+    """GB/s of one device-to-host copy of up to 2 GB between the given buffers (median of 3)."""
+    import torch
+    n = min(host.numel(), devbuf.numel(), nbytes // 8)
+    ts = []
+    for _ in range(4):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        host[:n].copy_(devbuf[:n], non_blocking=True)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    return 8 * n / sorted(ts[1:])[1] / 1e9
 
 
 # ----------------------------------------------------------------------------- fixed-G fills

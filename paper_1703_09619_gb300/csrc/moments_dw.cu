@@ -50,9 +50,13 @@ struct SmemDW {
 __host__ __device__ __forceinline__ int padded_stride(int gmax) { return gmax | 1; }
 
 // Sizes (double-words) of one buffer of each double-buffered array.
-// alpha rows of a chunk have an odd stride (G | 1) so that the phase-B reads of different rows
-// fall in different banks; one pair's chunk then holds up to kChunk + kNB double-words.
-constexpr int kAlphaPair = kChunk + kNB;
+// Folded alpha of a chunk, per pair: the even part E[bb][p] = alpha(p) + alpha(G-1-p) and the
+// odd part O[bb][p] = alpha(p) - alpha(G-1-p), p < H = ceil(G/2) (for odd G the middle point
+// has E = alpha, O = 0), each in rows of odd stride (H | 1) so that phase-B reads of different
+// rows fall in different banks.  nb * (H | 1) <= 160 for every G; the odd part starts 168
+// double-words (16 banks) after the even one, so the two parities of a row do not collide.
+constexpr int kFoldHalf = 168;
+constexpr int kAlphaPair = 2 * kFoldHalf;
 __host__ __device__ __forceinline__ int alpha_buf(int n_pairs) { return n_pairs * kAlphaPair; }
 __host__ __device__ __forceinline__ int t1_buf(int n_pairs, int kb) { return n_pairs * kNB * kb; }
 __host__ __device__ __forceinline__ int t2_buf(int n_pairs, int kb) { return n_pairs * kb * kb; }
@@ -225,9 +229,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_moments_dw(MomentLaunch L) {
 
         const int per_pair = Ku * Kv * Kw;
         const int ppg = max(1, min(np, L.iacc_cap / per_pair));
-        const float rKu = 1.f / (float)Ku, rKv = 1.f / (float)Kv, rG = 1.f / (float)G;
-        const int ga = G | 1;
-        const int nb = max(1, min(G, kChunk / G));
+        const int H = (G + 1) / 2, LR = 2 * H, Hs = H | 1;  // folded half, lanes per row, row stride
+        const float rKu = 1.f / (float)Ku, rKv = 1.f / (float)Kv, rLR = 1.f / (float)LR;
+        const int nb = max(1, min(G, kChunk / LR));
         const int ncp = (G + nb - 1) / nb;  // chunks per plane
         const int T = G * ncp;
         for (int s0 = 0; s0 < np; s0 += ppg) {
@@ -245,23 +249,38 @@ __global__ void __launch_bounds__(kThreads, 3) k_moments_dw(MomentLaunch L) {
                         row[task * kRow] = dw_mul_fast(S.t1[ch.b0 + task], S.t2[ch.c]);
                     }
                 }
-                // A: alpha of chunk step
+                // A: alpha of chunk step, at mirrored points in neighbouring lanes: lane pair
+                // (2 i, 2 i + 1) of row bb takes points p and G-1-p (p = i mod H), swaps values
+                // with one shuffle per word and stores the folded E (even lane) and O (odd lane)
                 if (step >= 0 && step < T) {
                     const Chunk ch = chunk_of(step, ncp, nb, G);
                     const dw* row = S.row + (step & 1) * kNB * kRow;
                     dw* al = S.alpha + (step & 1) * aS;
-                    if (tid < ch.nbc * G) {
-                        const int bb = div_small(tid, G, rG), a = tid - bb * G, ia = bb * ga + a;
+                    const bool lane_on = tid < ch.nbc * LR;
+                    const int bb = div_small(tid, LR, rLR), r = tid - bb * LR, p = r >> 1, side = r & 1;
+                    const bool middle = 2 * p + 1 == G;  // odd G: its middle point, taken by the even lane
+                    const bool active = lane_on && !(middle && side);
+                    const int a = side ? G - 1 - p : p;
+                    dw K[6];
+#pragma unroll
+                    for (int s = 0; s < 6; ++s) K[s] = dw_from_float(0.f);
+                    if (active) {
                         if (!metric) {
-                            al[ia] = dw_add_f(dw_mul_fast(S.t0[a], row[bb * kRow]), 1.f);
+                            K[0] = dw_add_f(dw_mul_fast(S.t0[a], row[bb * kRow]), 1.f);
                         } else {
-                            dw K[6];
                             const bool ok = metric_alpha_dw(S.geo, row + bb * kRow, S.plane + (step & 1) * kPlane,
                                                             S.xq[a], S.t0[a], S.t1[a], K);
                             if (!ok) bad_jac = 1;
+                        }
+                    }
+                    const int ia = (side ? kFoldHalf : 0) + bb * Hs + p;
 #pragma unroll
-                            for (int s = 0; s < 6; ++s)
-                                if (s >= s0 && s < s0 + ns) al[(s - s0) * kAlphaPair + ia] = K[s];
+                    for (int s = 0; s < 6; ++s) {
+                        if (s >= s0 && s < s0 + ns) {  // uniform across the CTA: every lane shuffles
+                            const dw o = dw_make(__shfl_xor_sync(0xffffffffu, K[s].hi, 1),
+                                                 __shfl_xor_sync(0xffffffffu, K[s].lo, 1));
+                            const dw f = side ? (middle ? dw_from_float(0.f) : dw_sub_fast(o, K[s])) : dw_add_fast(K[s], o);
+                            if (lane_on) al[(s - s0) * kAlphaPair + ia] = f;
                         }
                     }
                 }
@@ -289,14 +308,17 @@ __global__ void __launch_bounds__(kThreads, 3) k_moments_dw(MomentLaunch L) {
                 const float r_nbc = 1.f / (float)max(cb.nbc, 1);
                 for (int j = tid; j < nB + nC + nD; j += kThreads) {
                     if (j < nB) {
-                        // T1[s][bb][k] = sum_a B[k][a] alpha[s][bb][a]; k fastest across threads, so
-                        // the alpha reads are broadcasts and the B rows (odd stride) spread
+                        // T1[s][bb][k] = sum_a B[k][a] alpha[s][bb][a]
+                        //              = sum_{p<H} B[k][p] (k even ? E : O)[s][bb][p],
+                        // since B[k][G-1-p] = (-1)^k B[k][p] on the symmetric rule; k fastest
+                        // across threads, so the folded reads are near-broadcasts and the B rows
+                        // (odd stride) spread
                         const int sb = div_small(j, Ku, rKu), k = j - sb * Ku;
                         const int s = div_small(sb, cb.nbc, r_nbc), bb = sb - s * cb.nbc;
-                        const dw* al = alB + s * kAlphaPair + bb * ga;
+                        const dw* al = alB + s * kAlphaPair + (k & 1) * kFoldHalf + bb * Hs;
                         const dw* Bk = S.B + k * gstride;
                         dw_acc acc;
-                        for (int a = 0; a < G; ++a) acc.fma(Bk[a], al[a]);
+                        for (int p = 0; p < H; ++p) acc.fma(Bk[p], al[p]);
                         t1B[(s * kNB + bb) * Kb + k] = acc.value();
                     } else if (j < nB + nC) {
                         // T2[s][k][l] (+)= sum_bb B[l][b0 + bb] T1[s][bb][k]

@@ -10,7 +10,10 @@
 // (type, m1, m2) is stored as a contiguous run k = kmin, kmin+2, ..., kmax.
 //
 // Gauss-Legendre rules: Newton's method on P_G in long double, started from the
-// Tricomi asymptotic node estimate; weights 2 / ((1 - x^2) P'_G(x)^2).
+// Tricomi asymptotic node estimate; weights 2 / ((1 - x^2) P'_G(x)^2).  The rule is
+// symmetric (P_G has parity G): the non-negative roots are computed and mirrored, the
+// middle node of an odd rule is exactly 0, so x[G-1-a] = -x[a] and w[G-1-a] = w[a] hold
+// bit for bit (the double-word moment kernel folds its sums on that symmetry).
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -65,7 +68,7 @@ void legendre_ld(int n, long double x, long double* p_n, long double* p_nm1) {
 
 void gauss_legendre_ld(int G, double* x, double* w) {
     const long double pi = 3.141592653589793238462643383279502884L;
-    for (int i = 1; i <= G; ++i) {
+    for (int i = 1; i <= (G + 1) / 2; ++i) {
         // Tricomi estimate of the i-th largest root
         long double th = pi * (4.0L * i - 1.0L) / (4.0L * G + 2.0L);
         long double z = (1.0L - (G - 1.0L) / (8.0L * G * G * G)) * cosl(th);
@@ -78,11 +81,15 @@ void gauss_legendre_ld(int G, double* x, double* w) {
             z -= dz;
             if (fabsl(dz) < 1e-19L) break;
         }
+        if (2 * i - 1 == G) z = 0.0L;  // the middle node of an odd rule
         long double pn, pm;
         legendre_ld(G, z, &pn, &pm);
         dp = G * (z * pn - pm) / (z * z - 1.0L);
-        x[G - i] = (double)z;
-        w[G - i] = (double)(2.0L / ((1.0L - z * z) * dp * dp));
+        const double xd = (double)z, wd = (double)(2.0L / ((1.0L - z * z) * dp * dp));
+        x[G - i] = xd;
+        w[G - i] = wd;
+        x[i - 1] = -xd;
+        w[i - 1] = wd;
     }
 }
 

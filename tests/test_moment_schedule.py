@@ -6,12 +6,14 @@ plane whose last chunk was t-3, on buffers indexed by chunk parity (row constant
 T1) and plane parity (T2).  This test walks the same schedule for every G the library
 accepts and checks that no buffer is written and read by different steps in one interval,
 that every read sees the data of the chunk (or plane) it needs, and that the moments end
-complete.  The chunking (nb = max(1, min(G, 256 // G)) rows of one plane) is the kernel's."""
+complete.  The chunking is the kernel's: nb = max(1, min(G, 256 // (2 ceil(G/2)))) rows of
+one plane, a lane pair per mirrored pair of points of a row."""
 import pytest
 
 
 def schedule_ok(G, chunk=256):
-    nb = max(1, min(G, chunk // G))
+    lanes_per_row = 2 * ((G + 1) // 2)
+    nb = max(1, min(G, chunk // lanes_per_row))
     ncp = (G + nb - 1) // nb
     T = G * ncp
     state = {}
