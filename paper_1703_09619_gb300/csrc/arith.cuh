@@ -11,9 +11,11 @@ struct ArithF64 {
     using T = double;
     using C = double;
     __device__ static T zero() { return 0.0; }
+    __device__ static T mul(C c, T x) { return c * x; }  // the first term of a sum
     __device__ static void fma_acc(T& acc, C c, T x) { acc = fma(c, x, acc); }
     __device__ static T finish(T acc) { return acc; }
     __device__ static double to_double(T v) { return v; }
+    __device__ static double to_double_fast(T v) { return v; }
     __device__ static T load_moment(const void* p, size_t i) { return __ldg(reinterpret_cast<const double*>(p) + i); }
     __device__ static C load_coef(const void* p, int i) { return __ldg(reinterpret_cast<const double*>(p) + i); }
 };
@@ -23,6 +25,12 @@ struct ArithFF {
     using T = float2;
     using C = float2;
     __device__ static T zero() { return make_float2(0.f, 0.f); }
+    // The first term of a sum: c * x as (leading product, its exact FMA error plus the
+    // cross terms) -- what fma_acc gives from a zero accumulator, without the TwoSum.
+    __device__ static T mul(C c, T x) {
+        const float p = c.x * x.x;
+        return make_float2(p, fmaf(c.y, x.x, fmaf(c.x, x.y, fmaf(c.x, x.x, -p))));
+    }
     // acc += c * x, with the exact error of the leading product (FMA) and of the leading
     // sum (TwoSum); second-order terms go to the low word.
     __device__ static void fma_acc(T& acc, C c, T x) {
@@ -67,6 +75,23 @@ struct ArithFF {
             }
         }
         return __longlong_as_double((long long)pat);
+    }
+    // The same value by a shorter route for the common case 2^-74 <= |hi| < 2^128: lo, scaled
+    // by a power of two to units of hi's last double place (exact, |result| <= 2^29), is
+    // rounded once and added to the magnitude bits of hi's double pattern.  When hi is a
+    // power of two and lo reduces its magnitude, the result lies in the binade below, whose
+    // places are half as large, so lo is scaled by twice as much.  Zero, tiny, subnormal,
+    // infinite and NaN hi take the general route above.
+    __device__ static double to_double_fast(T v) {
+        const uint32_t hb = __float_as_uint(v.x);
+        const uint32_t e = (hb >> 23) & 0xffu;
+        if (e < 53u || e == 0xffu) return to_double(v);
+        const uint64_t pat = ((uint64_t)((hb & 0x80000000u) | ((e + 896u) << 20) | ((hb & 0x7fffffu) >> 3)) << 32) |
+                             (uint64_t)(hb << 29);
+        const bool below = (hb & 0x7fffffu) == 0u && ((__float_as_uint(v.y) ^ hb) & 0x80000000u);
+        int u = __float2int_rn(v.y * __uint_as_float((306u + (below ? 1u : 0u) - e) << 23));
+        if ((int32_t)hb < 0) u = -u;
+        return __longlong_as_double((long long)(pat + (uint64_t)(int64_t)u));
     }
     __device__ static T load_moment(const void* p, size_t i) { return __ldg(reinterpret_cast<const float2*>(p) + i); }
     __device__ static C load_coef(const void* p, int i) { return __ldg(reinterpret_cast<const float2*>(p) + i); }

@@ -85,9 +85,10 @@ __global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
             const int im1 = mm / Nu_j, m2 = mm - im1 * Nu_j;
             const int32_t li = __ldg(lidx + lin_slot(t, m1a + im1, m2));
             const int k0 = lin_kmin(li), cnt = lin_cnt(li), off = lin_off(li);
-            T acc = A::zero();
-            for (int r = 0; r < cnt; ++r)
-                A::fma_acc(acc, A::load_coef(lcoef, off + r), A::load_moment(L.mom, moff + (size_t)(k0 + 2 * r) * KvKw + lq));
+            const size_t mb = moff + (size_t)k0 * KvKw + lq;
+            T acc = cnt > 0 ? A::mul(A::load_coef(lcoef, off), A::load_moment(L.mom, mb)) : A::zero();
+            for (int r = 1; r < cnt; ++r)
+                A::fma_acc(acc, A::load_coef(lcoef, off + r), A::load_moment(L.mom, mb + (size_t)(2 * r) * KvKw));
             sA[idx] = A::finish(acc);
         }
         __syncthreads();
@@ -102,8 +103,8 @@ __global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
             const int32_t li = __ldg(lidx + lin_slot(t, n1a + in1, n2));
             const int l0 = lin_kmin(li), cnt = lin_cnt(li), off = lin_off(li);
             const T* a = sA + ((im1 * Nu_j + m2) * Kv + l0) * Kw + q;
-            T acc = A::zero();
-            for (int r = 0; r < cnt; ++r) A::fma_acc(acc, A::load_coef(lcoef, off + r), a[2 * r * Kw]);
+            T acc = cnt > 0 ? A::mul(A::load_coef(lcoef, off), a[0]) : A::zero();
+            for (int r = 1; r < cnt; ++r) A::fma_acc(acc, A::load_coef(lcoef, off + r), a[2 * r * Kw]);
             sB[idx] = A::finish(acc);
         }
         __syncthreads();
@@ -119,9 +120,9 @@ __global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
             for (int p2 = 0; p2 < Nw_j; ++p2) {
                 const int32_t li = lrow[p2];
                 const int q0 = lin_kmin(li), cnt = lin_cnt(li), off = lin_off(li);
-                T acc = A::zero();
-                for (int r = 0; r < cnt; ++r) A::fma_acc(acc, A::load_coef(lcoef, off + r), bt[q0 + 2 * r]);
-                trow[p2 * mjp] = A::to_double(A::finish(acc));
+                T acc = cnt > 0 ? A::mul(A::load_coef(lcoef, off), bt[q0]) : A::zero();
+                for (int r = 1; r < cnt; ++r) A::fma_acc(acc, A::load_coef(lcoef, off + r), bt[q0 + 2 * r]);
+                trow[p2 * mjp] = A::to_double_fast(A::finish(acc));
             }
         }
         __syncthreads();

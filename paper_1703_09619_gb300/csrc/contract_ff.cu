@@ -55,9 +55,16 @@ __device__ __forceinline__ void stages12(const float2* __restrict__ sI, float2* 
         const int m1 = m1a + im1;
         const int k0 = run_kmin(TT, m1, m2), cnt = run_cnt(TT, m1, m2);
         float2 A[K];
+        if (cnt > 0) {
+            const float2 c = c_runs[TT][m1][m2][0];
+            const float2* Ik = sI + k0 * K * K + q;
 #pragma unroll
-        for (int l = 0; l < K; ++l) A[l] = ArithFF::zero();
-        for (int r = 0; r < cnt; ++r) {
+            for (int l = 0; l < K; ++l) A[l] = ArithFF::mul(c, Ik[l * K]);
+        } else {
+#pragma unroll
+            for (int l = 0; l < K; ++l) A[l] = ArithFF::zero();
+        }
+        for (int r = 1; r < cnt; ++r) {
             const float2 c = c_runs[TT][m1][m2][r];
             const float2* Ik = sI + (k0 + 2 * r) * K * K + q;
 #pragma unroll
@@ -71,9 +78,9 @@ __device__ __forceinline__ void stages12(const float2* __restrict__ sI, float2* 
 #pragma unroll
             for (int n2 = 0; n2 < N; ++n2) {
                 const int l0 = run_kmin(TT, n1, n2), lc = run_cnt(TT, n1, n2);
-                float2 acc = ArithFF::zero();
+                float2 acc = lc > 0 ? ArithFF::mul(c_runs[TT][n1][n2][0], A[l0]) : ArithFF::zero();
 #pragma unroll
-                for (int r = 0; r < N; ++r)
+                for (int r = 1; r < N; ++r)
                     if (r < lc) ArithFF::fma_acc(acc, c_runs[TT][n1][n2][r], A[l0 + 2 * r]);
                 dst[((size_t)n1 * N * N + n2) * K] = ArithFF::finish(acc);
             }
@@ -83,9 +90,15 @@ __device__ __forceinline__ void stages12(const float2* __restrict__ sI, float2* 
 // Stage 3 and both write-outs for one (m1, n1, m2, n2) combination per thread.
 // Mt points at (row rbase, column col0) of M_t; Mp (or nullptr) at (row col0, column
 // rbase) of the partner block; n is the row stride of the element's matrices.
+// Streaming 256-bit store of four doubles (a whole 32-byte sector; p 32-byte aligned).  Two
+// 16-byte stores per sector would send each sector to L2 in two halves.
+__device__ __forceinline__ void st_cs_v4(double* p, double a, double b, double c, double d) {
+    asm volatile("st.global.cs.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(p), "d"(a), "d"(b), "d"(c), "d"(d) : "memory");
+}
+
 template <int N, int TT>
 __device__ __forceinline__ void stage3(const float2* __restrict__ sB, int m1n, int tid, int nth, double* Mt,
-                                       double* Mp, int64_t n, bool vec) {
+                                       double* Mp, int64_t n, bool vec, bool vec4) {
     constexpr int K = 2 * N - 1, MJ = N * N;
     const int ncombo = m1n * N * MJ;
     for (int c = tid; c < ncombo; c += nth) {
@@ -99,14 +112,17 @@ __device__ __forceinline__ void stage3(const float2* __restrict__ sB, int m1n, i
 #pragma unroll
             for (int p2 = 0; p2 < N; ++p2) {
                 const int q0 = run_kmin(TT, p1, p2), qc = run_cnt(TT, p1, p2);
-                float2 acc = ArithFF::zero();
+                float2 acc = qc > 0 ? ArithFF::mul(c_runs[TT][p1][p2][0], b[q0]) : ArithFF::zero();
 #pragma unroll
-                for (int r = 0; r < N; ++r)
+                for (int r = 1; r < N; ++r)
                     if (r < qc) ArithFF::fma_acc(acc, c_runs[TT][p1][p2][r], b[q0 + 2 * r]);
-                v[p1][p2] = ArithFF::to_double(ArithFF::finish(acc));
+                v[p1][p2] = ArithFF::to_double_fast(ArithFF::finish(acc));
             }
         double* r1 = Mt + (int64_t)(mn * N) * n + mj * N;  // row (m1,n1,p1=0), column (m2,n2,p2=0)
-        if (vec) {
+        if (N == 4 && vec4) {  // one whole 32-byte sector per store
+#pragma unroll
+            for (int p1 = 0; p1 < N; ++p1) st_cs_v4(r1 + p1 * n, v[p1][0], v[p1][1], v[p1][2], v[p1][3]);
+        } else if (vec) {
 #pragma unroll
             for (int p1 = 0; p1 < N; ++p1)
 #pragma unroll
@@ -120,7 +136,10 @@ __device__ __forceinline__ void stage3(const float2* __restrict__ sB, int m1n, i
         }
         if (Mp) {
             double* r2 = Mp + (int64_t)(mj * N) * n + mn * N;  // partner row (m2,n2,p2=0), column (m1,n1,p1=0)
-            if (vec) {
+            if (N == 4 && vec4) {
+#pragma unroll
+                for (int p2 = 0; p2 < N; ++p2) st_cs_v4(r2 + p2 * n, v[0][p2], v[1][p2], v[2][p2], v[3][p2]);
+            } else if (vec) {
 #pragma unroll
                 for (int p2 = 0; p2 < N; ++p2)
 #pragma unroll
@@ -149,6 +168,7 @@ __global__ void __launch_bounds__(512) k_contract_ffn(ContractLaunch L) {
     const int tid = threadIdx.x, nth = blockDim.x;
     const unsigned long long nu = (unsigned long long)L.n_units;
     const bool out_aligned = (reinterpret_cast<uintptr_t>(L.out) & 15) == 0;
+    const bool out_aligned32 = (reinterpret_cast<uintptr_t>(L.out) & 31) == 0;
 
     // Work queue with a two-deep prefetch held by thread 0: the unit used in the next
     // iteration is loaded, and the index after it claimed, while this one is computed.
@@ -187,14 +207,17 @@ __global__ void __launch_bounds__(512) k_contract_ffn(ContractLaunch L) {
         const int rbase = d->dof_off[gi] + m1a * N * N;
         const int col0 = d->dof_off[gj];
         const bool vec = out_aligned && (N % 2 == 0) && (n % 2 == 0) && (col0 % 2 == 0) && (rbase % 2 == 0);
+        // every 4-double segment 32-byte aligned: base, row stride, block corner, segment starts
+        const bool vec4 = out_aligned32 && (n % 4 == 0) && (col0 % 4 == 0) && (rbase % 4 == 0) &&
+                          ((d->out_off + (int64_t)type_slot_ff(L.types_mask, t) * n * n) % 4 == 0);
         double* Mt = L.out + d->out_off + type_slot_ff(L.types_mask, t) * n * n + rbase * n + col0;
         double* Mp = cu.tp >= 0 ? L.out + d->out_off + type_slot_ff(L.types_mask, cu.tp) * n * n + col0 * n + rbase
                                 : nullptr;
         switch (t) {
-        case 0: stage3<N, 0>(sB, m1n, tid, nth, Mt, Mp, n, vec); break;
-        case 1: stage3<N, 1>(sB, m1n, tid, nth, Mt, Mp, n, vec); break;
-        case 2: stage3<N, 2>(sB, m1n, tid, nth, Mt, Mp, n, vec); break;
-        default: stage3<N, 3>(sB, m1n, tid, nth, Mt, Mp, n, vec); break;
+        case 0: stage3<N, 0>(sB, m1n, tid, nth, Mt, Mp, n, vec, vec4); break;
+        case 1: stage3<N, 1>(sB, m1n, tid, nth, Mt, Mp, n, vec, vec4); break;
+        case 2: stage3<N, 2>(sB, m1n, tid, nth, Mt, Mp, n, vec, vec4); break;
+        default: stage3<N, 3>(sB, m1n, tid, nth, Mt, Mp, n, vec, vec4); break;
         }
         __syncthreads();
     }
