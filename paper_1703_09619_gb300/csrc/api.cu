@@ -45,7 +45,7 @@ struct p2s_plan {
     PlanLayout L;
     ElemDesc* d_desc = nullptr;
     ContractUnit* d_units = nullptr;
-    unsigned long long* d_counter = nullptr;
+    unsigned long long* d_counter = nullptr;  // [0] contraction unit queue, [1] moment element queue
     double* d_mom = nullptr;  // moment scratch of p2s_plan_fill
     // CUDA-graph replay of p2s_plan_fill: the launch sequence (queue reset, moments,
     // contraction) captured on a private stream, re-captured when the arguments change
@@ -331,7 +331,7 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
 
 int run_moments(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_desc, const p2s_geometry* geom,
                 const p2s_material* mat, void* moments, int32_t* elem_status, cudaStream_t s,
-                const int8_t* elem_mask) {
+                unsigned long long* counter, const int8_t* elem_mask) {
     if (elem_mask && PL.precision != P2S_FP64) return fail(P2S_ERR_ARG, "moments: element masks need an FP64 plan");
     if (!geom || !mat) return fail(P2S_ERR_ARG, "moments: NULL geometry or material");
     if (geom->n_elem != PL.n_elem) return fail(P2S_ERR_ARG, "moments: n_elem differs from the plan");
@@ -362,6 +362,8 @@ int run_moments(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_d
     M.iacc_cap = PL.iacc_cap;
     M.out_ff = PL.precision == P2S_MIXED;
     M.elem_mask = elem_mask;
+    M.counter = counter;
+    if (counter) P2S_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
     if (M.out_ff)
         P2S_CUDA(launch_moments_dw(M, PL.mom_grid, PL.mom_smem, s));
     else
@@ -566,7 +568,7 @@ int p2s_plan_create_tuned(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, con
     }
     bool ok = cudaMalloc(&p->d_desc, sizeof(ElemDesc) * desc.size()) == cudaSuccess &&
               cudaMalloc(&p->d_units, sizeof(ContractUnit) * std::max<size_t>(1, units.size())) == cudaSuccess &&
-              cudaMalloc(&p->d_counter, sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMalloc(&p->d_counter, 2 * sizeof(unsigned long long)) == cudaSuccess &&
               cudaMalloc(&p->d_mom, sizeof(double) * std::max<int64_t>(1, p->L.mom_entries)) == cudaSuccess;
     if (!ok) {
         p2s_plan_destroy(p);
@@ -590,7 +592,8 @@ int p2s_plan_moments(p2s_plan* p, const p2s_geometry* geom, const p2s_material* 
                      int32_t* elem_status, void* stream) {
     if (!p) return fail(P2S_ERR_ARG, "p2s_plan_moments: NULL plan");
     if (set_device(p->ctx->T.device)) return P2S_ERR_CUDA;
-    return run_moments(p->ctx->T, p->L, p->d_desc, geom, mat, moments, elem_status, (cudaStream_t)stream);
+    return run_moments(p->ctx->T, p->L, p->d_desc, geom, mat, moments, elem_status, (cudaStream_t)stream,
+                       p->d_counter + 1);
 }
 
 int p2s_plan_contract(p2s_plan* p, const double* moments, double* out, void* stream) {
@@ -621,7 +624,7 @@ static int plan_capture(p2s_plan* p, const p2s_geometry* geom, const p2s_materia
                         int32_t* elem_status) {
     cudaStream_t cs = p->cap_stream;
     P2S_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    int rc = run_moments(p->ctx->T, p->L, p->d_desc, geom, mat, p->d_mom, elem_status, cs);
+    int rc = run_moments(p->ctx->T, p->L, p->d_desc, geom, mat, p->d_mom, elem_status, cs, p->d_counter + 1);
     if (rc == P2S_OK) rc = run_contract(p->ctx->T, p->L, p->d_desc, p->d_units, p->d_counter, p->d_mom, out, cs);
     cudaGraph_t g = nullptr;
     cudaError_t ce = cudaStreamEndCapture(cs, &g);
@@ -712,7 +715,7 @@ ElemDesc* plan_desc(p2s_plan* p) { return p ? p->d_desc : nullptr; }
 int plan_fill_masked(p2s_plan* p, const p2s_geometry* geom, const p2s_material* mat, double* out,
                      const int8_t* mask, cudaStream_t s) {
     if (!p) return fail(P2S_ERR_ARG, "plan_fill_masked: NULL plan");
-    int rc = run_moments(p->ctx->T, p->L, p->d_desc, geom, mat, p->d_mom, nullptr, s, mask);
+    int rc = run_moments(p->ctx->T, p->L, p->d_desc, geom, mat, p->d_mom, nullptr, s, p->d_counter + 1, mask);
     if (rc) return rc;
     return run_contract(p->ctx->T, p->L, p->d_desc, p->d_units, p->d_counter, p->d_mom, out, s, mask);
 }

@@ -54,7 +54,16 @@ __global__ void __launch_bounds__(kThreads) k_moments_fp64(MomentLaunch L) {
     __shared__ int bad_jac;
     const int gstride = L.gmax | 1;
 
-    for (int64_t e = blockIdx.x; e < L.n_elem; e += gridDim.x) {
+    __shared__ long long s_elem;
+    for (int64_t es = blockIdx.x;; es += gridDim.x) {
+        int64_t e = es;
+        if (L.counter) {  // dynamic element queue: the next element to whichever CTA is free
+            __syncthreads();
+            if (threadIdx.x == 0) s_elem = (long long)atomicAdd(L.counter, 1ull);
+            __syncthreads();
+            e = s_elem;
+        }
+        if (e >= L.n_elem) break;
         if (L.elem_mask && !L.elem_mask[e]) continue;  // uniform across the CTA
         const ElemDesc& d = L.desc[e];
         const int G = d.G, nc = d.n_comp, np = (nc == 1) ? 1 : 6;

@@ -10,7 +10,8 @@
 // Where the scratch lives: one file-scope array in device memory (g_noalloc_scratch,
 // 18.3 MiB), present on every GPU that loads this library until the process exits.
 // It holds the moment tensors between the two kernels, the per-element descriptors,
-// the contraction work list and the work-queue counter.  Its device address is taken
+// the contraction work list and the two work-queue counters (contraction units, moment
+// elements).  Its device address is taken
 // once per device with cudaGetSymbolAddress (the host-side name of the array is only a
 // stand-in and must never be passed to a kernel).
 #include <cstring>
@@ -94,7 +95,7 @@ extern "C" int p2s_fill_elements_noalloc(p2s_ctx* ctx, const p2s_geometry* geom,
     if (ce == cudaSuccess && L.n_units)
         ce = cudaMemcpyAsync(d_units, g_na_units, sizeof(ContractUnit) * L.n_units, cudaMemcpyHostToDevice, s);
     if (ce != cudaSuccess) return fail(P2S_ERR_CUDA, "p2s_fill_elements_noalloc: upload", ce);
-    rc = run_moments(*T, L, d_desc, geom, mat, d_mom, elem_status, s);
+    rc = run_moments(*T, L, d_desc, geom, mat, d_mom, elem_status, s, d_counter + 1);
     if (rc) return rc;
     // run_contract clears the queue counter on the stream before its launch
     return run_contract(*T, L, d_desc, d_units, d_counter, d_mom, out, s);

@@ -85,6 +85,7 @@ struct MomentLaunch {
     int iacc_cap;       // doubles of the moment accumulator in shared memory
     int out_ff;         // 1: store moments as (hi, lo) FP32 pairs (mixed path)
     const int8_t* elem_mask;  // optional: elements with mask 0 are skipped (FP64 kernel)
+    unsigned long long* counter;  // element queue (zeroed before the launch), or nullptr: static
 };
 size_t moments_smem_bytes(int n_pairs, int kb, int gmax, int iacc_cap);
 cudaError_t launch_moments_fp64(const MomentLaunch& L, int grid, size_t smem, cudaStream_t s);
@@ -198,9 +199,11 @@ int tile_params_from(const p2s_tile_config* c, TileParams& tp);
 int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, const p2s_quadrature* quad,
                  const p2s_fill_opts* opts, ElemDesc* desc, UnitSink& units, PlanLayout& L,
                  const TileParams& tile = TileParams());
+// `counter` (device, one word, optional): the moment kernel's element queue; with it CTAs take
+// elements dynamically, which balances batches of uneven per-element cost.
 int run_moments(const DeviceTables& T, const PlanLayout& L, const ElemDesc* d_desc, const p2s_geometry* geom,
                 const p2s_material* mat, void* moments, int32_t* elem_status, cudaStream_t s,
-                const int8_t* elem_mask = nullptr);
+                unsigned long long* counter, const int8_t* elem_mask = nullptr);
 int run_contract(const DeviceTables& T, const PlanLayout& L, const ElemDesc* d_desc, const ContractUnit* d_units,
                  unsigned long long* d_counter, const void* moments, double* out, cudaStream_t s,
                  const int8_t* elem_mask = nullptr);
