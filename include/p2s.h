@@ -327,7 +327,10 @@ int64_t p2s_learned_plan_output_entries(const p2s_learned_plan* plan);
 /* Learned fill, asynchronous on `stream`: features, prediction, fill at the predicted G,
  * judge fill at 48 points and comparison, FP64 fill of the judged elements that failed and
  * their replacement in `out`.  npts_out (device [E], optional) receives the G used per
- * element before any replacement. */
+ * element before any replacement.  The judge's 48-point fill, which does not depend on the
+ * prediction, runs on a stream of the plan that is forked from `stream` when the call
+ * starts and joined to it before the comparison: work queued on `stream` after the call
+ * sees the whole fill.  Calls with one plan must be ordered (one stream, or synchronised). */
 int p2s_learned_fill(p2s_learned_plan* plan, const p2s_geometry* geom, const p2s_material* mat, const float* params,
                      double* out, int32_t* npts_out, void* stream);
 

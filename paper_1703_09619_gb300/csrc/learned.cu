@@ -541,6 +541,9 @@ struct p2s_learned_plan {
     int8_t* d_mask = nullptr;  // [nJ] judged element failed
     double* d_jerr = nullptr;
     unsigned long long* d_report = nullptr;
+    // the judge's 48-point fill runs on a side stream, forked from and joined to the caller's
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 extern "C" {
@@ -562,6 +565,10 @@ void p2s_learned_plan_destroy(p2s_learned_plan* L) {
     cudaFree(L->d_mask);
     cudaFree(L->d_jerr);
     cudaFree(L->d_report);
+    if (L->side) cudaStreamSynchronize(L->side);
+    if (L->ev_fork) cudaEventDestroy(L->ev_fork);
+    if (L->ev_join) cudaEventDestroy(L->ev_join);
+    if (L->side) cudaStreamDestroy(L->side);
     delete L;
 }
 
@@ -623,6 +630,12 @@ int p2s_learned_plan_create(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, c
               cudaMalloc(&L->d_jerr, sizeof(double) * std::max<int64_t>(L->nJ, 1)) == cudaSuccess &&
               cudaMalloc(&L->d_report, sizeof(unsigned long long) * 16) == cudaSuccess;
     if (!ok) { p2s_learned_plan_destroy(L); return fail(P2S_ERR_OOM, "p2s_learned_plan_create: device allocation"); }
+    {
+        cudaError_t ce = cudaStreamCreateWithFlags(&L->side, cudaStreamNonBlocking);
+        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&L->ev_fork, cudaEventDisableTiming);
+        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&L->ev_join, cudaEventDisableTiming);
+        if (ce != cudaSuccess) { p2s_learned_plan_destroy(L); return fail(P2S_ERR_CUDA, "p2s_learned_plan_create: stream", ce); }
+    }
     if (L->nJ) {
         cudaError_t ce = cudaMemcpy(L->d_jidx, jidx.data(), sizeof(int32_t) * L->nJ, cudaMemcpyHostToDevice);
         if (ce == cudaSuccess) ce = cudaMemcpy(L->d_off_main, off_main.data(), sizeof(int64_t) * (L->nJ + 1), cudaMemcpyHostToDevice);
@@ -647,27 +660,42 @@ int p2s_learned_fill(p2s_learned_plan* L, const p2s_geometry* geom, const p2s_ma
     cudaStream_t s = (cudaStream_t)stream;
     P2S_LCUDA(cudaMemsetAsync(L->d_report, 0, sizeof(unsigned long long) * 16, s));
     if (L->E == 0) return P2S_OK;
+    double* jn = L->d_jin;
+    double* jb = jn + 24 * L->nJ;
+    double* jp = jb + 4 * L->nJ;
+    const int gj = (int)std::min<int64_t>(std::max<int64_t>(L->nJ, 1), 4096);
+    p2s_geometry g2 = {L->nJ, jn, jb};
+    p2s_material m2 = {P2S_ALPHA_METRIC_EPS, jp};
+    // The judge's 48-point fill does not depend on the prediction: it starts first, on the
+    // side stream, and the main path's kernels fill the SMs its last elements leave idle.
+    if (L->nJ) {
+        P2S_LCUDA(cudaEventRecord(L->ev_fork, s));
+        P2S_LCUDA(cudaStreamWaitEvent(L->side, L->ev_fork, 0));
+        k_gather_inputs<<<gj, 32, 0, L->side>>>(geom->nodes, geom->bulge, mat->params, L->d_jidx, L->nJ, jn, jb, jp);
+        P2S_LCUDA(cudaGetLastError());
+        int jrc = p2s_plan_fill(L->judge, &g2, &m2, L->d_jout, nullptr, L->side);
+        P2S_LCUDA(cudaEventRecord(L->ev_join, L->side));
+        if (jrc) {
+            P2S_LCUDA(cudaStreamWaitEvent(s, L->ev_join, 0));
+            return jrc;
+        }
+    }
     int rc = p2s_coarse_features(L->ctx, geom, mat, L->d_feat, stream);
-    if (rc) return rc;
-    rc = p2s_mlp_predict(L->ctx, params, L->d_feat, L->E, L->margin, L->risk, L->d_npts, nullptr, stream);
-    if (rc) return rc;
-    const int gs = (int)std::min<int64_t>((L->E + 255) / 256, 1024);
-    k_set_npts<<<gs, 256, 0, s>>>(plan_desc(L->main), L->d_npts, L->E, L->d_report + 2);
-    P2S_LCUDA(cudaGetLastError());
-    if (npts_out) P2S_LCUDA(cudaMemcpyAsync(npts_out, L->d_npts, sizeof(int32_t) * L->E, cudaMemcpyDeviceToDevice, s));
-    rc = p2s_plan_fill(L->main, geom, mat, out, nullptr, stream);
+    if (rc == P2S_OK) rc = p2s_mlp_predict(L->ctx, params, L->d_feat, L->E, L->margin, L->risk, L->d_npts, nullptr, stream);
+    if (rc == P2S_OK) {
+        const int gs = (int)std::min<int64_t>((L->E + 255) / 256, 1024);
+        k_set_npts<<<gs, 256, 0, s>>>(plan_desc(L->main), L->d_npts, L->E, L->d_report + 2);
+        const cudaError_t ce = cudaGetLastError();
+        if (ce != cudaSuccess) rc = fail(P2S_ERR_CUDA, "p2s_learned_fill: k_set_npts", ce);
+    }
+    if (rc == P2S_OK && npts_out) {
+        const cudaError_t ce = cudaMemcpyAsync(npts_out, L->d_npts, sizeof(int32_t) * L->E, cudaMemcpyDeviceToDevice, s);
+        if (ce != cudaSuccess) rc = fail(P2S_ERR_CUDA, "p2s_learned_fill: npts copy", ce);
+    }
+    if (rc == P2S_OK) rc = p2s_plan_fill(L->main, geom, mat, out, nullptr, stream);
+    if (L->nJ) P2S_LCUDA(cudaStreamWaitEvent(s, L->ev_join, 0));  // joined on every path
     if (rc) return rc;
     if (L->nJ) {
-        double* jn = L->d_jin;
-        double* jb = jn + 24 * L->nJ;
-        double* jp = jb + 4 * L->nJ;
-        const int gj = (int)std::min<int64_t>(L->nJ, 4096);
-        k_gather_inputs<<<gj, 32, 0, s>>>(geom->nodes, geom->bulge, mat->params, L->d_jidx, L->nJ, jn, jb, jp);
-        P2S_LCUDA(cudaGetLastError());
-        p2s_geometry g2 = {L->nJ, jn, jb};
-        p2s_material m2 = {P2S_ALPHA_METRIC_EPS, jp};
-        rc = p2s_plan_fill(L->judge, &g2, &m2, L->d_jout, nullptr, stream);
-        if (rc) return rc;
         rc = p2s_element_errors(L->ctx, out, L->d_off_main, L->d_jout, L->d_off_j, L->nJ, 4, L->d_jerr, stream);
         if (rc) return rc;
         // judged elements above the tolerance: their plain-method fill, then the copy into out
