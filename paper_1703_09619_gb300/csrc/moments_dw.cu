@@ -141,9 +141,9 @@ __device__ __forceinline__ int div_small(int n, int d, float rd) {
 struct Chunk {
     int c, b0, nbc;
 };
-__device__ __forceinline__ Chunk chunk_of(int t, int ncp, int nb, int G) {
+__device__ __forceinline__ Chunk chunk_of(int t, int ncp, float rncp, int nb, int G) {
     Chunk ch;
-    ch.c = t / ncp;
+    ch.c = div_small(t, ncp, rncp);
     ch.b0 = (t - ch.c * ncp) * nb;
     ch.nbc = min(nb, G - ch.b0);
     return ch;
@@ -242,6 +242,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_moments_dw(MomentLaunch L) {
         const float rKu = 1.f / (float)Ku, rKv = 1.f / (float)Kv, rLR = 1.f / (float)LR;
         const int nb = max(1, min(G, kChunk / LR));
         const int ncp = (G + nb - 1) / nb;  // chunks per plane
+        const float rncp = 1.f / (float)ncp;
         const int T = G * ncp;
         for (int s0 = 0; s0 < np; s0 += ppg) {
             const int ns = min(np, s0 + ppg) - s0;
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_moments_dw(MomentLaunch L) {
                 // row / plane constants of chunk step + 1 (tasks on the highest threads)
                 if (step + 1 < T) {
                     const int t = step + 1;
-                    const Chunk ch = chunk_of(t, ncp, nb, G);
+                    const Chunk ch = chunk_of(t, ncp, rncp, nb, G);
                     dw* row = S.row + (t & 1) * kNB * kRow;
                     const int task = kThreads - 1 - tid;
                     if (metric) {
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_moments_dw(MomentLaunch L) {
                 // (2 i, 2 i + 1) of row bb takes points p and G-1-p (p = i mod H), swaps values
                 // with one shuffle per word and stores the folded E (even lane) and O (odd lane)
                 if (step >= 0 && step < T) {
-                    const Chunk ch = chunk_of(step, ncp, nb, G);
+                    const Chunk ch = chunk_of(step, ncp, rncp, nb, G);
                     const dw* row = S.row + (step & 1) * kNB * kRow;
                     dw* al = S.alpha + (step & 1) * aS;
                     const bool lane_on = tid < ch.nbc * LR;
@@ -296,17 +297,20 @@ __global__ void __launch_bounds__(kThreads, 3) k_moments_dw(MomentLaunch L) {
                 // B of chunk step - 1, C of chunk step - 2, D of the plane whose last chunk is step - 3
                 const int tb = step - 1, tc = step - 2, td = step - 3;
                 Chunk cb{0, 0, 0}, cc{0, 0, 0};
-                int nB = 0, nC = 0, nD = 0, pd = 0;
+                int nB = 0, nC = 0, nD = 0, pd = -1;
                 if (tb >= 0 && tb < T) {
-                    cb = chunk_of(tb, ncp, nb, G);
+                    cb = chunk_of(tb, ncp, rncp, nb, G);
                     nB = ns * cb.nbc * Ku;
                 }
                 if (tc >= 0 && tc < T) {
-                    cc = chunk_of(tc, ncp, nb, G);
+                    cc = chunk_of(tc, ncp, rncp, nb, G);
                     nC = ns * Ku * Kv;
                 }
-                if (td >= 0 && td < T && td % ncp == ncp - 1) {
-                    pd = td / ncp;
+                if (td >= 0 && td < T) {
+                    const int pt = div_small(td, ncp, rncp);
+                    if (td - pt * ncp == ncp - 1) pd = pt;
+                }
+                if (pd >= 0) {
                     nD = ns * Ku * Kv;
                 }
                 const dw* alB = S.alpha + (tb & 1) * aS;
