@@ -229,7 +229,7 @@ def oracle_sample(wl, n_elem, seed=5):
 
 def cpu_sample_size(name):
     # about 5-20 s of oracle work on a 16-core host
-    return {"c1": 1, "c2": 3, "c3": 2, "c4": 12, "c5": 2}[name]
+    return {"c1": 1, "c2": 3, "c3": 2, "c4": 12, "c5": 4}[name]
 
 
 def run_reference(args, wl):
@@ -407,8 +407,13 @@ def run_learned(args, wl):
     err_h = err.cpu().numpy()
     plain.close()
     del ref
-    # stage breakdown at the learned G (moments, contraction) and of the plain fill
-    mom_ms, con_ms = stage_times(p2s, ctx, wl, npts, p2s.MIXED, params, nodes, bulge, dev, stream, flush)
+    # stage breakdown at the learned G (moments, contraction); the learned fill's moment queue
+    # takes elements grouped by G, largest first, so the breakdown fills them in that order
+    order = np.argsort(-npts, kind="stable")
+    wls = wl.subset(order)
+    ps, ns_, bs = p2s.device_inputs(wls, dev)
+    mom_ms, con_ms = stage_times(p2s, ctx, wls, npts[order], p2s.MIXED, ps, ns_, bs, dev, stream, flush)
+    del ps, ns_, bs
     peaks, src = load_peaks()
     roof = roofline_for(wl, npts, p2s.MIXED, mom_ms, con_ms, peaks, src)
     entries = wl.entries()

@@ -47,6 +47,7 @@ struct p2s_plan {
     ContractUnit* d_units = nullptr;
     unsigned long long* d_counter = nullptr;  // [0] contraction unit queue, [1] moment element queue
     double* d_mom = nullptr;  // moment scratch of p2s_plan_fill
+    int32_t* d_order = nullptr;  // optional element order of the moment queue
     // CUDA-graph replay of p2s_plan_fill: the launch sequence (queue reset, moments,
     // contraction) captured on a private stream, re-captured when the arguments change
     bool use_graph = false;
@@ -331,7 +332,7 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
 
 int run_moments(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_desc, const p2s_geometry* geom,
                 const p2s_material* mat, void* moments, int32_t* elem_status, cudaStream_t s,
-                unsigned long long* counter, const int8_t* elem_mask) {
+                unsigned long long* counter, const int8_t* elem_mask, const int32_t* order) {
     if (elem_mask && PL.precision != P2S_FP64) return fail(P2S_ERR_ARG, "moments: element masks need an FP64 plan");
     if (!geom || !mat) return fail(P2S_ERR_ARG, "moments: NULL geometry or material");
     if (geom->n_elem != PL.n_elem) return fail(P2S_ERR_ARG, "moments: n_elem differs from the plan");
@@ -363,6 +364,7 @@ int run_moments(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_d
     M.out_ff = PL.precision == P2S_MIXED;
     M.elem_mask = elem_mask;
     M.counter = counter;
+    M.order = order;
     if (counter) P2S_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
     if (M.out_ff)
         P2S_CUDA(launch_moments_dw(M, PL.mom_grid, PL.mom_smem, s));
@@ -536,6 +538,7 @@ void p2s_plan_destroy(p2s_plan* p) {
     cudaFree(p->d_desc);
     cudaFree(p->d_units);
     cudaFree(p->d_counter);
+    cudaFree(p->d_order);
     cudaFree(p->d_mom);
     delete p;
 }
@@ -581,6 +584,21 @@ int p2s_plan_create_tuned(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, con
         p2s_plan_destroy(p);
         return fail(P2S_ERR_CUDA, "p2s_plan_create: upload", ce);
     }
+    // elements of several quadrature sizes: the moment queue hands them out grouped by G,
+    // largest first (concurrent CTAs then run the same specialised code; small ones fill the tail)
+    bool mixed_g = false;
+    for (int64_t e = 1; e < E && !mixed_g; ++e) mixed_g = desc[e].G != desc[0].G;
+    if (mixed_g) {
+        std::vector<int32_t> ord((size_t)E);
+        for (int64_t e = 0; e < E; ++e) ord[e] = (int32_t)e;
+        std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return desc[a].G > desc[b].G; });
+        int32_t* d_ord = plan_order(p);
+        ce = d_ord ? cudaMemcpy(d_ord, ord.data(), sizeof(int32_t) * E, cudaMemcpyHostToDevice) : cudaErrorMemoryAllocation;
+        if (ce != cudaSuccess) {
+            p2s_plan_destroy(p);
+            return fail(P2S_ERR_CUDA, "p2s_plan_create: element order", ce);
+        }
+    }
     *out = p;
     return P2S_OK;
 }
@@ -593,7 +611,7 @@ int p2s_plan_moments(p2s_plan* p, const p2s_geometry* geom, const p2s_material* 
     if (!p) return fail(P2S_ERR_ARG, "p2s_plan_moments: NULL plan");
     if (set_device(p->ctx->T.device)) return P2S_ERR_CUDA;
     return run_moments(p->ctx->T, p->L, p->d_desc, geom, mat, moments, elem_status, (cudaStream_t)stream,
-                       p->d_counter + 1);
+                       p->d_counter + 1, nullptr, p->d_order);
 }
 
 int p2s_plan_contract(p2s_plan* p, const double* moments, double* out, void* stream) {
@@ -624,7 +642,8 @@ static int plan_capture(p2s_plan* p, const p2s_geometry* geom, const p2s_materia
                         int32_t* elem_status) {
     cudaStream_t cs = p->cap_stream;
     P2S_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    int rc = run_moments(p->ctx->T, p->L, p->d_desc, geom, mat, p->d_mom, elem_status, cs, p->d_counter + 1);
+    int rc = run_moments(p->ctx->T, p->L, p->d_desc, geom, mat, p->d_mom, elem_status, cs, p->d_counter + 1, nullptr,
+                         p->d_order);
     if (rc == P2S_OK) rc = run_contract(p->ctx->T, p->L, p->d_desc, p->d_units, p->d_counter, p->d_mom, out, cs);
     cudaGraph_t g = nullptr;
     cudaError_t ce = cudaStreamEndCapture(cs, &g);
@@ -711,11 +730,20 @@ int p2s_sync_status(p2s_ctx* ctx, void* stream) {
 namespace p2s {
 const DeviceTables* context_tables(const p2s_ctx* c) { return c ? &c->T : nullptr; }
 ElemDesc* plan_desc(p2s_plan* p) { return p ? p->d_desc : nullptr; }
+int32_t* plan_order(p2s_plan* p) {
+    if (!p) return nullptr;
+    if (!p->d_order && cudaMalloc(&p->d_order, sizeof(int32_t) * std::max<int64_t>(1, p->L.n_elem)) != cudaSuccess) {
+        p->d_order = nullptr;
+        return nullptr;
+    }
+    return p->d_order;
+}
 
 int plan_fill_masked(p2s_plan* p, const p2s_geometry* geom, const p2s_material* mat, double* out,
                      const int8_t* mask, cudaStream_t s) {
     if (!p) return fail(P2S_ERR_ARG, "plan_fill_masked: NULL plan");
-    int rc = run_moments(p->ctx->T, p->L, p->d_desc, geom, mat, p->d_mom, nullptr, s, p->d_counter + 1, mask);
+    int rc = run_moments(p->ctx->T, p->L, p->d_desc, geom, mat, p->d_mom, nullptr, s, p->d_counter + 1, mask,
+                         p->d_order);
     if (rc) return rc;
     return run_contract(p->ctx->T, p->L, p->d_desc, p->d_units, p->d_counter, p->d_mom, out, s, mask);
 }

@@ -479,6 +479,22 @@ __global__ void k_set_npts(ElemDesc* desc, const int32_t* npts, int64_t E, unsig
     }
 }
 
+// Queue order of the main fill's moment kernel: elements grouped by class, largest G first
+// (the CTAs of an SM then mostly run the same specialised code, and the small elements fill
+// the tail).  cls_count holds the class sizes; cursor (zeroed) the fill position per class.
+__global__ void k_order_by_class(const int32_t* __restrict__ npts, int64_t E, const unsigned long long* cls_count,
+                                 unsigned long long* cursor, int32_t* __restrict__ order) {
+    const int Gs[kC] = {8, 12, 16, 24, 32, 48};
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        const int G = npts[e];
+        int c = 0;
+        while (c < kC - 1 && Gs[c] != G) ++c;
+        unsigned long long off = 0;
+        for (int c2 = c + 1; c2 < kC; ++c2) off += cls_count[c2];
+        order[off + atomicAdd(cursor + c, 1ull)] = (int32_t)e;
+    }
+}
+
 __global__ void k_gather_inputs(const double* __restrict__ nodes, const double* __restrict__ bulge,
                                 const double* __restrict__ params, const int32_t* __restrict__ idx, int64_t nJ,
                                 double* __restrict__ jn, double* __restrict__ jb, double* __restrict__ jp) {
@@ -544,6 +560,7 @@ struct p2s_learned_plan {
     // the judge's 48-point fill runs on a side stream, forked from and joined to the caller's
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    int32_t* order = nullptr;  // the main plan's moment-queue order (owned by the main plan)
 };
 
 extern "C" {
@@ -593,6 +610,8 @@ int p2s_learned_plan_create(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, c
     p2s_fill_opts fo = {opts->precision, P2S_TYPES_ALL};
     int rc = p2s_plan_create(ctx, E, orders, &q48, &fo, &L->main);
     if (rc) { p2s_learned_plan_destroy(L); return rc; }
+    L->order = plan_order(L->main);
+    if (!L->order) { p2s_learned_plan_destroy(L); return fail(P2S_ERR_OOM, "p2s_learned_plan_create: element order"); }
     // judge subset
     std::vector<int8_t> sel((size_t)std::max<int64_t>(E, 1));
     p2s_judge_select(E, opts->judge_frac, opts->seed, sel.data());
@@ -685,8 +704,12 @@ int p2s_learned_fill(p2s_learned_plan* L, const p2s_geometry* geom, const p2s_ma
     if (rc == P2S_OK) {
         const int gs = (int)std::min<int64_t>((L->E + 255) / 256, 1024);
         k_set_npts<<<gs, 256, 0, s>>>(plan_desc(L->main), L->d_npts, L->E, L->d_report + 2);
-        const cudaError_t ce = cudaGetLastError();
-        if (ce != cudaSuccess) rc = fail(P2S_ERR_CUDA, "p2s_learned_fill: k_set_npts", ce);
+        cudaError_t ce = cudaGetLastError();
+        if (ce == cudaSuccess) {
+            k_order_by_class<<<gs, 256, 0, s>>>(L->d_npts, L->E, L->d_report + 2, L->d_report + 9, L->order);
+            ce = cudaGetLastError();
+        }
+        if (ce != cudaSuccess) rc = fail(P2S_ERR_CUDA, "p2s_learned_fill: k_set_npts / k_order_by_class", ce);
     }
     if (rc == P2S_OK && npts_out) {
         const cudaError_t ce = cudaMemcpyAsync(npts_out, L->d_npts, sizeof(int32_t) * L->E, cudaMemcpyDeviceToDevice, s);

@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(kThreads) k_moments_fp64(MomentLaunch L) {
             __syncthreads();
             e = s_elem;
         }
+        if (e < L.n_elem && L.order) e = L.order[e];
         if (e >= L.n_elem) break;
         if (L.elem_mask && !L.elem_mask[e]) continue;  // uniform across the CTA
         const ElemDesc& d = L.desc[e];

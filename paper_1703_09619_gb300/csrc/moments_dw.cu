@@ -149,6 +149,23 @@ __device__ __forceinline__ Chunk chunk_of(int t, int ncp, float rncp, int nb, in
     return ch;
 }
 
+// n / d with d a compile-time constant when D > 0 (a multiply-shift), else by the FP32
+// reciprocal rd of the runtime d.
+template <int D>
+__device__ __forceinline__ int div_ct(int n, int d, float rd) {
+    if constexpr (D > 0) return n / D;
+    else return div_small(n, d, rd);
+}
+
+template <int NCP>
+__device__ __forceinline__ Chunk chunk_of_ct(int t, int ncp, float rncp, int nb, int G) {
+    Chunk ch;
+    ch.c = div_ct<NCP>(t, ncp, rncp);
+    ch.b0 = (t - ch.c * ncp) * nb;
+    ch.nbc = min(nb, G - ch.b0);
+    return ch;
+}
+
 // One task of the row/plane constants of a chunk (metric kind): tasks 4 bb + i (i < 3) form
 // B_i, F_i, H_i of row bb, task 4 bb + 3 forms T0, T1 and the three cosine products of row
 // bb, tasks 4 nbc + i form D_i and E_i of the chunk's plane.
@@ -181,6 +198,174 @@ __device__ __forceinline__ void metric_constants_task(const SmemDW& S, const Chu
     }
 }
 
+// The pipelined steps and the moment write-out of one element (the 1-D tables and element
+// constants are in shared memory).  GC, KC > 0 fix G and the moment count per axis (metric
+// kind, Ku = Kv = Kw = KC, all six pairs in one group) at compile time, which turns the chunk
+// shape, the item decoding and every loop bound into constants; GC = KC = 0 takes them from
+// the element at run time.
+template <int GC, int KC>
+__device__ __forceinline__ void element_pipeline(const MomentLaunch& L, const SmemDW& S, const ElemDesc& d, int Grt,
+                                                 bool metric_rt, int gstride, int aS, int t1S, int t2S, int* bad_jac) {
+    constexpr bool kSpec = GC > 0 && KC > 0;
+    const int tid = threadIdx.x;
+    const int G = kSpec ? GC : Grt;
+    const bool metric = kSpec ? true : metric_rt;
+    const int nc = d.n_comp, np = kSpec ? 6 : ((nc == 1) ? 1 : 6);
+    const int Ku = kSpec ? KC : d.kax[0], Kv = kSpec ? KC : d.kax[1], Kw = kSpec ? KC : d.kax[2];
+    const int Kb = kSpec ? KC : max(Ku, max(Kv, Kw));
+    constexpr int KCs = kSpec ? KC : 0;
+    constexpr int KK = kSpec ? KC * KC : 0;
+    constexpr int HC = kSpec ? (GC + 1) / 2 : 0, LRC = 2 * HC;
+    constexpr int NBC = kSpec ? (kChunk / LRC < GC ? (kChunk / LRC > 0 ? kChunk / LRC : 1) : GC) : 0;
+    constexpr int NCPC = kSpec ? (GC + NBC - 1) / NBC : 0;
+    const int per_pair = Ku * Kv * Kw;
+    const int ppg = kSpec ? 6 : max(1, min(np, L.iacc_cap / per_pair));
+    const int H = (G + 1) / 2, LR = 2 * H, Hs = H | 1;  // folded half, lanes per row, row stride
+    const float rKu = 1.f / (float)Ku, rKv = 1.f / (float)Kv, rLR = 1.f / (float)LR;
+    const int nb = kSpec ? NBC : max(1, min(G, kChunk / LR));
+    const int ncp = kSpec ? NCPC : (G + nb - 1) / nb;  // chunks per plane
+    const float rncp = 1.f / (float)ncp;
+    const int T = G * ncp;
+    for (int s0 = 0; s0 < np; s0 += ppg) {
+        const int ns = min(np, s0 + ppg) - s0;
+        for (int step = -1; step < T + 3; ++step) {
+            // row / plane constants of chunk step + 1 (tasks on the highest threads)
+            if (step + 1 < T) {
+                const int t = step + 1;
+                const Chunk ch = chunk_of_ct<NCPC>(t, ncp, rncp, nb, G);
+                dw* row = S.row + (t & 1) * kNB * kRow;
+                const int task = kThreads - 1 - tid;
+                if (metric) {
+                    if (task < 4 * ch.nbc + 3) metric_constants_task(S, ch, task, row, S.plane + (t & 1) * kPlane);
+                } else if (task < ch.nbc) {
+                    row[task * kRow] = dw_mul_fast(S.t1[ch.b0 + task], S.t2[ch.c]);
+                }
+            }
+            // A: alpha of chunk step, at mirrored points in neighbouring lanes: lane pair
+            // (2 i, 2 i + 1) of row bb takes points p and G-1-p (p = i mod H), swaps values
+            // with one shuffle per word and stores the folded E (even lane) and O (odd lane)
+            if (step >= 0 && step < T) {
+                const Chunk ch = chunk_of_ct<NCPC>(step, ncp, rncp, nb, G);
+                const dw* row = S.row + (step & 1) * kNB * kRow;
+                dw* al = S.alpha + (step & 1) * aS;
+                const bool lane_on = tid < ch.nbc * LR;
+                const int bb = div_ct<LRC>(tid, LR, rLR), r = tid - bb * LR, p = r >> 1, side = r & 1;
+                const bool middle = 2 * p + 1 == G;  // odd G: its middle point, taken by the even lane
+                const bool active = lane_on && !(middle && side);
+                const int a = side ? G - 1 - p : p;
+                dw K[6];
+#pragma unroll
+                for (int s = 0; s < 6; ++s) K[s] = dw_from_float(0.f);
+                if (active) {
+                    if (!metric) {
+                        K[0] = dw_add_f(dw_mul_fast(S.t0[a], row[bb * kRow]), 1.f);
+                    } else {
+                        const bool ok = metric_alpha_dw(S.geo, row + bb * kRow, S.plane + (step & 1) * kPlane,
+                                                        S.xq[a], S.t0[a], S.t1[a], K);
+                        if (!ok) *bad_jac = 1;
+                    }
+                }
+                const int ia = (side ? kFoldHalf : 0) + bb * Hs + p;
+#pragma unroll
+                for (int s = 0; s < 6; ++s) {
+                    if (s >= s0 && s < s0 + ns) {  // uniform across the CTA: every lane shuffles
+                        const dw o = dw_make(__shfl_xor_sync(0xffffffffu, K[s].hi, 1),
+                                             __shfl_xor_sync(0xffffffffu, K[s].lo, 1));
+                        const dw f = side ? (middle ? dw_from_float(0.f) : dw_sub_fast(o, K[s])) : dw_add_fast(K[s], o);
+                        if (lane_on) al[(s - s0) * kAlphaPair + ia] = f;
+                    }
+                }
+            }
+            // B of chunk step - 1, C of chunk step - 2, D of the plane whose last chunk is step - 3
+            const int tb = step - 1, tc = step - 2, td = step - 3;
+            Chunk cb{0, 0, 0}, cc{0, 0, 0};
+            int nB = 0, nC = 0, nD = 0, pd = -1;
+            if (tb >= 0 && tb < T) {
+                cb = chunk_of_ct<NCPC>(tb, ncp, rncp, nb, G);
+                nB = ns * cb.nbc * Ku;
+            }
+            if (tc >= 0 && tc < T) {
+                cc = chunk_of_ct<NCPC>(tc, ncp, rncp, nb, G);
+                nC = ns * Ku * Kv;
+            }
+            if (td >= 0 && td < T) {
+                const int pt = div_ct<NCPC>(td, ncp, rncp);
+                if (td - pt * ncp == ncp - 1) pd = pt;
+            }
+            if (pd >= 0) {
+                nD = ns * Ku * Kv;
+            }
+            const dw* alB = S.alpha + (tb & 1) * aS;
+            dw* t1B = S.T1 + (tb & 1) * t1S;
+            const dw* t1C = S.T1 + (tc & 1) * t1S;
+            dw* t2C = S.T2 + (cc.c & 1) * t2S;
+            const dw* t2D = S.T2 + (pd & 1) * t2S;
+            const float r_nbc = 1.f / (float)max(cb.nbc, 1);
+            for (int j = tid; j < nB + nC + nD; j += kThreads) {
+                if (j < nB) {
+                    // T1[s][bb][k] = sum_a B[k][a] alpha[s][bb][a]
+                    //              = sum_{p<H} B[k][p] (k even ? E : O)[s][bb][p],
+                    // since B[k][G-1-p] = (-1)^k B[k][p] on the symmetric rule; k fastest
+                    // across threads, so the folded reads are near-broadcasts and the B rows
+                    // (odd stride) spread
+                    const int sb = div_ct<KCs>(j, Ku, rKu), k = j - sb * Ku;
+                    const int s = div_small(sb, cb.nbc, r_nbc), bb = sb - s * cb.nbc;
+                    const dw* al = alB + s * kAlphaPair + (k & 1) * kFoldHalf + bb * Hs;
+                    const dw* Bk = S.B + k * gstride;
+                    dw_acc acc;
+#pragma unroll 4
+                    for (int p = 0; p < H; ++p) acc.fma(Bk[p], al[p]);
+                    t1B[(s * kNB + bb) * Kb + k] = acc.value();
+                } else if (j < nB + nC) {
+                    // T2[s][k][l] (+)= sum_bb B[l][b0 + bb] T1[s][bb][k]
+                    const int i = j - nB;
+                    const int sk = div_ct<KCs>(i, Kv, rKv), l = i - sk * Kv;
+                    const int s = div_ct<KCs>(sk, Ku, rKu), k = sk - s * Ku;
+                    const dw* t1 = t1C + s * kNB * Kb + k;
+                    const dw* Bl = S.B + l * gstride + cc.b0;
+                    dw_acc acc;
+                    if (cc.b0 > 0) {
+                        acc.s = t2C[i].hi;
+                        acc.c = t2C[i].lo;
+                    }
+                    for (int bb = 0; bb < cc.nbc; ++bb) acc.fma(Bl[bb], t1[bb * Kb]);
+                    t2C[i] = acc.value();
+                } else {
+                    // I[s][k][l][q] (+)= B[q][c] T2_c[s][k][l] for all q of one (s, k, l)
+                    const int skl = j - nB - nC;
+                    const dw t2 = t2D[skl];
+                    dw* I = S.Iacc + skl * Kw;
+#pragma unroll
+                    for (int q = 0; q < (kSpec ? KC : Kw); ++q) {
+                        dw_acc acc;
+                        if (pd > 0) {
+                            acc.s = I[q].hi;
+                            acc.c = I[q].lo;
+                        }
+                        acc.fma(S.B[q * gstride + pd], t2);
+                        I[q] = acc.value();
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        for (int s = 0; s < ns; ++s) {
+            int gi, gj;
+            pair_comps_dw(s0 + s, nc, gi, gj);
+            const int ku = d.ord[gi][0] + d.ord[gj][0] - 1, kv = d.ord[gi][1] + d.ord[gj][1] - 1,
+                      kw = d.ord[gi][2] + d.ord[gj][2] - 1;
+            float2* dst = reinterpret_cast<float2*>(L.mom + d.mom_off + d.pair_off[s0 + s]);
+            const dw* src = S.Iacc + s * per_pair;
+            for (int i = tid; i < ku * kv * kw; i += kThreads) {
+                const int k = i / (kv * kw), r = i - k * kv * kw, l = r / kw, q = r - l * kw;
+                const dw v = src[(k * Kv + l) * Kw + q];
+                dst[i] = make_float2(v.hi, v.lo);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 3) k_moments_dw(MomentLaunch L) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int tid = threadIdx.x;
@@ -199,6 +384,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_moments_dw(MomentLaunch L) {
             __syncthreads();
             e = s_elem;
         }
+        if (e < L.n_elem && L.order) e = L.order[e];
         if (e >= L.n_elem) break;
         if (L.elem_mask && !L.elem_mask[e]) continue;
         const ElemDesc& d = L.desc[e];
@@ -236,149 +422,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_moments_dw(MomentLaunch L) {
         if (metric && tid < kGeoDW) S.geo[tid] = dw_from_double(S.geo64[tid]);
         __syncthreads();
 
-        const int per_pair = Ku * Kv * Kw;
-        const int ppg = max(1, min(np, L.iacc_cap / per_pair));
-        const int H = (G + 1) / 2, LR = 2 * H, Hs = H | 1;  // folded half, lanes per row, row stride
-        const float rKu = 1.f / (float)Ku, rKv = 1.f / (float)Kv, rLR = 1.f / (float)LR;
-        const int nb = max(1, min(G, kChunk / LR));
-        const int ncp = (G + nb - 1) / nb;  // chunks per plane
-        const float rncp = 1.f / (float)ncp;
-        const int T = G * ncp;
-        for (int s0 = 0; s0 < np; s0 += ppg) {
-            const int ns = min(np, s0 + ppg) - s0;
-            for (int step = -1; step < T + 3; ++step) {
-                // row / plane constants of chunk step + 1 (tasks on the highest threads)
-                if (step + 1 < T) {
-                    const int t = step + 1;
-                    const Chunk ch = chunk_of(t, ncp, rncp, nb, G);
-                    dw* row = S.row + (t & 1) * kNB * kRow;
-                    const int task = kThreads - 1 - tid;
-                    if (metric) {
-                        if (task < 4 * ch.nbc + 3) metric_constants_task(S, ch, task, row, S.plane + (t & 1) * kPlane);
-                    } else if (task < ch.nbc) {
-                        row[task * kRow] = dw_mul_fast(S.t1[ch.b0 + task], S.t2[ch.c]);
-                    }
-                }
-                // A: alpha of chunk step, at mirrored points in neighbouring lanes: lane pair
-                // (2 i, 2 i + 1) of row bb takes points p and G-1-p (p = i mod H), swaps values
-                // with one shuffle per word and stores the folded E (even lane) and O (odd lane)
-                if (step >= 0 && step < T) {
-                    const Chunk ch = chunk_of(step, ncp, rncp, nb, G);
-                    const dw* row = S.row + (step & 1) * kNB * kRow;
-                    dw* al = S.alpha + (step & 1) * aS;
-                    const bool lane_on = tid < ch.nbc * LR;
-                    const int bb = div_small(tid, LR, rLR), r = tid - bb * LR, p = r >> 1, side = r & 1;
-                    const bool middle = 2 * p + 1 == G;  // odd G: its middle point, taken by the even lane
-                    const bool active = lane_on && !(middle && side);
-                    const int a = side ? G - 1 - p : p;
-                    dw K[6];
-#pragma unroll
-                    for (int s = 0; s < 6; ++s) K[s] = dw_from_float(0.f);
-                    if (active) {
-                        if (!metric) {
-                            K[0] = dw_add_f(dw_mul_fast(S.t0[a], row[bb * kRow]), 1.f);
-                        } else {
-                            const bool ok = metric_alpha_dw(S.geo, row + bb * kRow, S.plane + (step & 1) * kPlane,
-                                                            S.xq[a], S.t0[a], S.t1[a], K);
-                            if (!ok) bad_jac = 1;
-                        }
-                    }
-                    const int ia = (side ? kFoldHalf : 0) + bb * Hs + p;
-#pragma unroll
-                    for (int s = 0; s < 6; ++s) {
-                        if (s >= s0 && s < s0 + ns) {  // uniform across the CTA: every lane shuffles
-                            const dw o = dw_make(__shfl_xor_sync(0xffffffffu, K[s].hi, 1),
-                                                 __shfl_xor_sync(0xffffffffu, K[s].lo, 1));
-                            const dw f = side ? (middle ? dw_from_float(0.f) : dw_sub_fast(o, K[s])) : dw_add_fast(K[s], o);
-                            if (lane_on) al[(s - s0) * kAlphaPair + ia] = f;
-                        }
-                    }
-                }
-                // B of chunk step - 1, C of chunk step - 2, D of the plane whose last chunk is step - 3
-                const int tb = step - 1, tc = step - 2, td = step - 3;
-                Chunk cb{0, 0, 0}, cc{0, 0, 0};
-                int nB = 0, nC = 0, nD = 0, pd = -1;
-                if (tb >= 0 && tb < T) {
-                    cb = chunk_of(tb, ncp, rncp, nb, G);
-                    nB = ns * cb.nbc * Ku;
-                }
-                if (tc >= 0 && tc < T) {
-                    cc = chunk_of(tc, ncp, rncp, nb, G);
-                    nC = ns * Ku * Kv;
-                }
-                if (td >= 0 && td < T) {
-                    const int pt = div_small(td, ncp, rncp);
-                    if (td - pt * ncp == ncp - 1) pd = pt;
-                }
-                if (pd >= 0) {
-                    nD = ns * Ku * Kv;
-                }
-                const dw* alB = S.alpha + (tb & 1) * aS;
-                dw* t1B = S.T1 + (tb & 1) * t1S;
-                const dw* t1C = S.T1 + (tc & 1) * t1S;
-                dw* t2C = S.T2 + (cc.c & 1) * t2S;
-                const dw* t2D = S.T2 + (pd & 1) * t2S;
-                const float r_nbc = 1.f / (float)max(cb.nbc, 1);
-                for (int j = tid; j < nB + nC + nD; j += kThreads) {
-                    if (j < nB) {
-                        // T1[s][bb][k] = sum_a B[k][a] alpha[s][bb][a]
-                        //              = sum_{p<H} B[k][p] (k even ? E : O)[s][bb][p],
-                        // since B[k][G-1-p] = (-1)^k B[k][p] on the symmetric rule; k fastest
-                        // across threads, so the folded reads are near-broadcasts and the B rows
-                        // (odd stride) spread
-                        const int sb = div_small(j, Ku, rKu), k = j - sb * Ku;
-                        const int s = div_small(sb, cb.nbc, r_nbc), bb = sb - s * cb.nbc;
-                        const dw* al = alB + s * kAlphaPair + (k & 1) * kFoldHalf + bb * Hs;
-                        const dw* Bk = S.B + k * gstride;
-                        dw_acc acc;
-                        for (int p = 0; p < H; ++p) acc.fma(Bk[p], al[p]);
-                        t1B[(s * kNB + bb) * Kb + k] = acc.value();
-                    } else if (j < nB + nC) {
-                        // T2[s][k][l] (+)= sum_bb B[l][b0 + bb] T1[s][bb][k]
-                        const int i = j - nB;
-                        const int sk = div_small(i, Kv, rKv), l = i - sk * Kv;
-                        const int s = div_small(sk, Ku, rKu), k = sk - s * Ku;
-                        const dw* t1 = t1C + s * kNB * Kb + k;
-                        const dw* Bl = S.B + l * gstride + cc.b0;
-                        dw_acc acc;
-                        if (cc.b0 > 0) {
-                            acc.s = t2C[i].hi;
-                            acc.c = t2C[i].lo;
-                        }
-                        for (int bb = 0; bb < cc.nbc; ++bb) acc.fma(Bl[bb], t1[bb * Kb]);
-                        t2C[i] = acc.value();
-                    } else {
-                        // I[s][k][l][q] (+)= B[q][c] T2_c[s][k][l] for all q of one (s, k, l)
-                        const int skl = j - nB - nC;
-                        const dw t2 = t2D[skl];
-                        dw* I = S.Iacc + skl * Kw;
-                        for (int q = 0; q < Kw; ++q) {
-                            dw_acc acc;
-                            if (pd > 0) {
-                                acc.s = I[q].hi;
-                                acc.c = I[q].lo;
-                            }
-                            acc.fma(S.B[q * gstride + pd], t2);
-                            I[q] = acc.value();
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-            for (int s = 0; s < ns; ++s) {
-                int gi, gj;
-                pair_comps_dw(s0 + s, nc, gi, gj);
-                const int ku = d.ord[gi][0] + d.ord[gj][0] - 1, kv = d.ord[gi][1] + d.ord[gj][1] - 1,
-                          kw = d.ord[gi][2] + d.ord[gj][2] - 1;
-                float2* dst = reinterpret_cast<float2*>(L.mom + d.mom_off + d.pair_off[s0 + s]);
-                const dw* src = S.Iacc + s * per_pair;
-                for (int i = tid; i < ku * kv * kw; i += kThreads) {
-                    const int k = i / (kv * kw), r = i - k * kv * kw, l = r / kw, q = r - l * kw;
-                    const dw v = src[(k * Kv + l) * Kw + q];
-                    dst[i] = make_float2(v.hi, v.lo);
-                }
-            }
-            __syncthreads();
+        const bool spec = metric && np == 6 && Ku == 7 && Kv == 7 && Kw == 7 && L.iacc_cap >= 6 * 343;
+        switch (spec ? G : 0) {
+        case 8: element_pipeline<8, 7>(L, S, d, G, metric, gstride, aS, t1S, t2S, &bad_jac); break;
+        case 12: element_pipeline<12, 7>(L, S, d, G, metric, gstride, aS, t1S, t2S, &bad_jac); break;
+        case 16: element_pipeline<16, 7>(L, S, d, G, metric, gstride, aS, t1S, t2S, &bad_jac); break;
+        case 24: element_pipeline<24, 7>(L, S, d, G, metric, gstride, aS, t1S, t2S, &bad_jac); break;
+        case 32: element_pipeline<32, 7>(L, S, d, G, metric, gstride, aS, t1S, t2S, &bad_jac); break;
+        case 48: element_pipeline<48, 7>(L, S, d, G, metric, gstride, aS, t1S, t2S, &bad_jac); break;
+        default: element_pipeline<0, 0>(L, S, d, G, metric, gstride, aS, t1S, t2S, &bad_jac); break;
         }
         if (tid == 0) {
             if (L.elem_status) L.elem_status[e] = bad_jac ? P2S_ERR_JACOBIAN : P2S_OK;

@@ -86,6 +86,7 @@ struct MomentLaunch {
     int out_ff;         // 1: store moments as (hi, lo) FP32 pairs (mixed path)
     const int8_t* elem_mask;  // optional: elements with mask 0 are skipped (FP64 kernel)
     unsigned long long* counter;  // element queue (zeroed before the launch), or nullptr: static
+    const int32_t* order;         // queue position -> element (optional; identity without it)
 };
 size_t moments_smem_bytes(int n_pairs, int kb, int gmax, int iacc_cap);
 cudaError_t launch_moments_fp64(const MomentLaunch& L, int grid, size_t smem, cudaStream_t s);
@@ -201,9 +202,10 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
                  const TileParams& tile = TileParams());
 // `counter` (device, one word, optional): the moment kernel's element queue; with it CTAs take
 // elements dynamically, which balances batches of uneven per-element cost.
+// `order` (device [E], optional): the order in which the queue hands out elements.
 int run_moments(const DeviceTables& T, const PlanLayout& L, const ElemDesc* d_desc, const p2s_geometry* geom,
                 const p2s_material* mat, void* moments, int32_t* elem_status, cudaStream_t s,
-                unsigned long long* counter, const int8_t* elem_mask = nullptr);
+                unsigned long long* counter, const int8_t* elem_mask = nullptr, const int32_t* order = nullptr);
 int run_contract(const DeviceTables& T, const PlanLayout& L, const ElemDesc* d_desc, const ContractUnit* d_units,
                  unsigned long long* d_counter, const void* moments, double* out, cudaStream_t s,
                  const int8_t* elem_mask = nullptr);
@@ -213,6 +215,9 @@ struct p2s_plan;
 namespace p2s {
 const DeviceTables* context_tables(const p2s_ctx* c);
 ElemDesc* plan_desc(p2s_plan* p);
+// The plan's element order for the moment kernel's queue (device [E], allocated on the first
+// call; from then on the plan's moment launches follow it).  nullptr on allocation failure.
+int32_t* plan_order(p2s_plan* p);
 // Fill of a plan restricted to the elements with mask != 0 (FP64 plans only; the others
 // are left untouched in `out`).
 int plan_fill_masked(p2s_plan* p, const p2s_geometry* geom, const p2s_material* mat, double* out,
