@@ -263,6 +263,20 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
     L.out_entries = out_off;
     L.mom_entries = mom_off;
     L.n_units = units.n;
+    // The specialised contraction compiles one code path per product type; units taken in
+    // element order interleave the four, and CTAs running different paths on one SM starve
+    // on instruction fetch.  Within chunks of kTypeChunk elements (whose moments stay in L2
+    // across the passes) the units are ordered by type, elements in order within a type.
+    if (spec_n && !units.overflow()) {
+        ContractUnit* first = units.vec ? units.vec->data() : units.buf;
+        if (first) {
+            constexpr int32_t kTypeChunk = 1024;
+            std::stable_sort(first, first + units.n, [](const ContractUnit& a, const ContractUnit& b) {
+                const int32_t ca = a.e / kTypeChunk, cb = b.e / kTypeChunk;
+                return ca != cb ? ca < cb : a.t < b.t;
+            });
+        }
+    }
 
     // moments launch shape: the accumulator takes what shared memory leaves, at least one pair
     // the mixed path evaluates alpha and the moments in double-word arithmetic (moments_dw.cu)
