@@ -54,6 +54,10 @@ ALPHA_FLOP_PER_POINT = 134
 #   the parity fold of the first mode product, per point and pair: one sum (11) and two
 #   shuffles; the first mode product then runs over ceil(G/2) points per row.
 FP32_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
+# DRAM bytes (read + write) per element of the double-word moment kernel, from the full-size
+# ncu capture of the c5 learned fill (profiles/c5_learned_dram_full_size.md): 496,681,216
+# bytes for the 32,768-element launch.  It scales with elements (inputs in, moments out).
+MOMENTS_DW_DRAM_BYTES_PER_ELEMENT = 496681216 / 32768
 DW_MAC_OPS, DW_ALPHA_OPS_METRIC, DW_ALPHA_OPS_SCALAR, DW_FOLD_OPS = 12, 839, 14, 13
 # Learned-fill settings: judge share and tolerance; risk of the class rule (the largest
 # value of the sweep 0.02 .. 0.0005 with no element of the batch above 1e-8).
@@ -329,8 +333,11 @@ def roofline_for(wl, npts, prec, mom_ms, con_ms, peaks, src):
         per_point = (DW_ALPHA_OPS_METRIC if metric else DW_ALPHA_OPS_SCALAR) + DW_FOLD_OPS * npairs
         ops = DW_MAC_OPS * macs + per_point * pts
         ach = ops / (mom_ms * 1e-3) / 1e12
+        traffic = MOMENTS_DW_DRAM_BYTES_PER_ELEMENT * wl.n_elem if metric and (wl.orders == 4).all() else None
         return {"bound": "alu", "kernel": "k_moments_dw", "achieved": ach, "peak": FP32_PEAK_TOPS,
-                "unit": "T FP32 lane-op/s", "frac": ach / FP32_PEAK_TOPS, "traffic": None,
+                "unit": "T FP32 lane-op/s", "frac": ach / FP32_PEAK_TOPS, "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the full-size c5 learned launch, "
+                                  "per element" if traffic else None,
                 "peak_source": "FP32 issue: 152 SMs x 128 lanes x 2.07 GHz (recipe unit counts and clock)",
                 "algorithmic_ops_per_launch": int(ops),
                 "op_model": "%d per double-word MAC x %d MACs (first mode product folded) + %d per point x %d points" % (
