@@ -157,52 +157,67 @@ __device__ __forceinline__ void stage3(const float2* __restrict__ sB, int m1n, i
 
 __device__ __forceinline__ int type_slot_ff(uint32_t mask, int t) { return __popc(mask & ((1u << t) - 1u)); }
 
+__device__ __forceinline__ const float2* unit_moments(const ContractLaunch& L, const ContractUnit& u) {
+    const ElemDesc* d = L.desc + u.e;
+    return reinterpret_cast<const float2*>(L.mom) + d->mom_off + d->pair_off[pair_index(u.gi, u.gj, d->n_comp)];
+}
+
+// Persistent CTAs take units from the queue.  Thread 0 keeps the current and the next unit in
+// shared slots indexed by iteration parity.  While stage 3 of the current unit runs (it reads
+// no moments), every thread holds its share of the next unit's moments in registers (N <= 4;
+// larger orders load them after stage 3), and stores them once stage 3 is done: two barriers
+// per unit and the moment load off the critical path.
 template <int N>
 __global__ void __launch_bounds__(512) k_contract_ffn(ContractLaunch L) {
-    constexpr int K = 2 * N - 1;
+    constexpr int K = 2 * N - 1, K3 = K * K * K;
+    constexpr int kPre = N <= 4 ? (K3 + 127) / 128 : 1;  // prefetch registers per thread (>= 128 threads)
     extern __shared__ __align__(16) unsigned char smraw[];
     float2* sI = reinterpret_cast<float2*>(smraw);
     float2* sB = sI + L.a_cap;
-    __shared__ ContractUnit cu;
-    __shared__ unsigned long long s_id;
+    __shared__ ContractUnit s_cu[2], s_nx[2];  // e = -1: no unit
     const int tid = threadIdx.x, nth = blockDim.x;
     const unsigned long long nu = (unsigned long long)L.n_units;
     const bool out_aligned = (reinterpret_cast<uintptr_t>(L.out) & 15) == 0;
     const bool out_aligned32 = (reinterpret_cast<uintptr_t>(L.out) & 31) == 0;
+    const bool pre = N <= 4 && kPre * nth >= K3;
 
-    // Work queue with a two-deep prefetch held by thread 0: the unit used in the next
-    // iteration is loaded, and the index after it claimed, while this one is computed.
-    unsigned long long id0 = 0, id1 = 0;
-    ContractUnit u0{};
     if (tid == 0) {
-        id0 = atomicAdd(L.counter, 1ull);
-        id1 = atomicAdd(L.counter, 1ull);
-        if (id0 < nu) u0 = L.units[id0];
+        ContractUnit none{};
+        none.e = -1;
+        const unsigned long long a = atomicAdd(L.counter, 1ull), b = atomicAdd(L.counter, 1ull);
+        s_cu[0] = a < nu ? L.units[a] : none;
+        s_nx[0] = b < nu ? L.units[b] : none;
     }
-    for (;;) {
-        if (tid == 0) {
-            s_id = id0;
-            if (id0 < nu) cu = u0;
-            if (id1 < nu) u0 = L.units[id1];
-            id0 = id1;
-            id1 = atomicAdd(L.counter, 1ull);
-        }
-        __syncthreads();
-        if (s_id >= nu) break;
+    __syncthreads();
+    if (s_cu[0].e >= 0) {
+        const float2* gI = unit_moments(L, s_cu[0]);
+        for (int i = tid; i < K3; i += nth) sI[i] = __ldg(gI + i);
+    }
+    __syncthreads();
+    for (int iter = 0;; ++iter) {
+        const int par = iter & 1;
+        const ContractUnit cu = s_cu[par];
+        if (cu.e < 0) break;
         const ElemDesc* d = L.desc + cu.e;
         const int gi = cu.gi, gj = cu.gj, t = cu.t, m1a = cu.m1a, m1n = cu.m1n;
         const int64_t n = d->n;
-        const float2* gI =
-            reinterpret_cast<const float2*>(L.mom) + d->mom_off + d->pair_off[pair_index(gi, gj, d->n_comp)];
-        for (int i = tid; i < K * K * K; i += nth) sI[i] = __ldg(gI + i);
-        __syncthreads();
         switch (t) {
         case 0: stages12<N, 0>(sI, sB, m1a, m1n, tid, nth); break;
         case 1: stages12<N, 1>(sI, sB, m1a, m1n, tid, nth); break;
         case 2: stages12<N, 2>(sI, sB, m1a, m1n, tid, nth); break;
         default: stages12<N, 3>(sI, sB, m1a, m1n, tid, nth); break;
         }
-        __syncthreads();
+        __syncthreads();  // stage-2 results complete; the moment buffer is free
+        const ContractUnit nx = s_nx[par];
+        const float2* gN = nx.e >= 0 ? unit_moments(L, nx) : nullptr;
+        float2 pf[kPre];
+        if (pre && gN) {
+#pragma unroll
+            for (int j = 0; j < kPre; ++j) {
+                const int i = tid + j * nth;
+                if (i < K3) pf[j] = __ldg(gN + i);
+            }
+        }
         // the unit's results are rows [rbase, rbase + m1n N^2) x columns [col0, col0 + N^3)
         const int rbase = d->dof_off[gi] + m1a * N * N;
         const int col0 = d->dof_off[gj];
@@ -219,7 +234,25 @@ __global__ void __launch_bounds__(512) k_contract_ffn(ContractLaunch L) {
         case 2: stage3<N, 2>(sB, m1n, tid, nth, Mt, Mp, n, vec, vec4); break;
         default: stage3<N, 3>(sB, m1n, tid, nth, Mt, Mp, n, vec, vec4); break;
         }
-        __syncthreads();
+        if (tid == 0) {  // the unit after next, into the other slot
+            ContractUnit none{};
+            none.e = -1;
+            const unsigned long long c = atomicAdd(L.counter, 1ull);
+            s_cu[par ^ 1] = nx;
+            s_nx[par ^ 1] = c < nu ? L.units[c] : none;
+        }
+        if (gN) {
+            if (pre) {
+#pragma unroll
+                for (int j = 0; j < kPre; ++j) {
+                    const int i = tid + j * nth;
+                    if (i < K3) sI[i] = pf[j];
+                }
+            } else {
+                for (int i = tid; i < K3; i += nth) sI[i] = __ldg(gN + i);
+            }
+        }
+        __syncthreads();  // the next unit's moments in place; the stage-2 buffer free
     }
 }
 
