@@ -40,36 +40,52 @@ const int kClassG[kC] = {8, 12, 16, 24, 32, 48};
 __constant__ double c_coarse_x[4] = {-0.9, -0.8, 0.35, 0.45};
 
 // ------------------------------------------------------------------ features
-__global__ void __launch_bounds__(64) k_features(const double* __restrict__ nodes, const double* __restrict__ bulge,
-                                                 const double* __restrict__ params, int64_t E,
-                                                 float* __restrict__ feat, int32_t* __restrict__ bad) {
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Four elements per CTA, 64 threads (one coarse point each) per element.  The cosines and
+// sines of the four positions are computed once per CTA; the element constants by one
+// thread of each element; the trace mean by warp shuffles.
+constexpr int kFeatElems = 4;
+__global__ void __launch_bounds__(64 * kFeatElems) k_features(const double* __restrict__ nodes,
+                                                               const double* __restrict__ bulge,
+                                                               const double* __restrict__ params, int64_t E,
+                                                               float* __restrict__ feat, int32_t* __restrict__ bad) {
     const double* x4 = c_coarse_x;
-    __shared__ double geo[48];
-    __shared__ double tr[64];
-    const int p = threadIdx.x;
-    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
-        if (p == 0) metric_geo(nodes + 24 * e, bulge ? bulge + 4 * e : nullptr, params + 4 * e, geo);
+    __shared__ double geo[kFeatElems][48];
+    __shared__ double half_tr[kFeatElems][2];
+    __shared__ double cs4[4], sn4[4];
+    const int sub = threadIdx.x >> 6, p = threadIdx.x & 63, warp = p >> 5, lane = p & 31;
+    if (threadIdx.x < 4) sincos(1.5707963267948966 * x4[threadIdx.x], &sn4[threadIdx.x], &cs4[threadIdx.x]);
+    for (int64_t e0 = (int64_t)blockIdx.x * kFeatElems; e0 < E; e0 += (int64_t)gridDim.x * kFeatElems) {
+        const int64_t e = e0 + sub;
+        const bool on = e < E;
+        if (on && p == 0) metric_geo(nodes + 24 * e, bulge ? bulge + 4 * e : nullptr, params + 4 * e, geo[sub]);
         __syncthreads();
         const int a = p & 3, b = (p >> 2) & 3, c = p >> 4;
-        const double u = x4[a], v = x4[b], w = x4[c];
-        double su, cu, sv, cv, sw, cw;
-        sincos(1.5707963267948966 * u, &su, &cu);
-        sincos(1.5707963267948966 * v, &sv, &cv);
-        sincos(1.5707963267948966 * w, &sw, &cw);
-        double K[6];
-        const bool ok = metric_alpha(geo, u, v, w, cu, su, cv, sv, cw, sw, K);
-        if (!ok && bad) bad[e] = 1;
-        tr[p] = (K[0] + K[3] + K[5]) / 3.0;
-        __syncthreads();
-        for (int s = 32; s > 0; s >>= 1) {
-            if (p < s) tr[p] += tr[p + s];
-            __syncthreads();
+        double K[6] = {0, 0, 0, 0, 0, 0};
+        if (on) {
+            const bool ok = metric_alpha(geo[sub], x4[a], x4[b], x4[c], cs4[a], sn4[a], cs4[b], sn4[b], cs4[c], sn4[c], K);
+            if (!ok && bad) bad[e] = 1;
         }
-        const double inv = 64.0 / tr[0];
-        const int map[9] = {0, 1, 2, 1, 3, 4, 2, 4, 5};
-        float* f = feat + (size_t)e * kIn + p * 9;
+        const double t = warp_sum_d((K[0] + K[3] + K[5]) / 3.0);
+        if (lane == 0) half_tr[sub][warp] = t;
+        __syncthreads();
+        if (on) {
+            const double inv = 64.0 / (half_tr[sub][0] + half_tr[sub][1]);
+            const int map[9] = {0, 1, 2, 1, 3, 4, 2, 4, 5};
+            float* f = feat + (size_t)e * kIn + p * 9;
 #pragma unroll
-        for (int s = 0; s < 9; ++s) f[s] = (float)(K[map[s]] * inv);
+            for (int q = 0; q < 9; ++q) f[q] = (float)(K[map[q]] * inv);
+        }
         __syncthreads();
     }
 }
@@ -313,10 +329,13 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
 }
 
 // ------------------------------------------------------------------ per-element errors
+// One element per CTA of 256 threads; per type 16-byte loads (when both segments allow them)
+// four deep per thread, maxima reduced by warp shuffles.
 __global__ void __launch_bounds__(256) k_elem_err(const double* __restrict__ a, const int64_t* __restrict__ offa,
                                                   const double* __restrict__ b, const int64_t* __restrict__ offb,
                                                   int64_t E, int n_types, double* __restrict__ err) {
-    __shared__ double sd[256], sm[256];
+    __shared__ double sd[8], sm[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
         const int64_t len = (offb[e + 1] - offb[e]) / n_types;
         double worst = 0.0;
@@ -324,25 +343,54 @@ __global__ void __launch_bounds__(256) k_elem_err(const double* __restrict__ a, 
             const double* pa = a + offa[e] + t * len;
             const double* pb = b + offb[e] + t * len;
             double d = 0.0, m = 0.0;
-            for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
-                d = fmax(d, fabs(pa[i] - pb[i]));
-                m = fmax(m, fabs(pb[i]));
-            }
-            sd[threadIdx.x] = d;
-            sm[threadIdx.x] = m;
-            __syncthreads();
-            for (int s = 128; s > 0; s >>= 1) {
-                if (threadIdx.x < s) {
-                    sd[threadIdx.x] = fmax(sd[threadIdx.x], sd[threadIdx.x + s]);
-                    sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + s]);
+            if (((reinterpret_cast<uintptr_t>(pa) | reinterpret_cast<uintptr_t>(pb)) & 15) == 0) {
+                const double2* qa = reinterpret_cast<const double2*>(pa);
+                const double2* qb = reinterpret_cast<const double2*>(pb);
+                const int64_t n2 = len / 2;
+                int64_t i = tid;
+                for (; i + 768 < n2; i += 1024) {
+                    double2 va[4], vb[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        va[j] = __ldcs(qa + i + 256 * j);
+                        vb[j] = __ldcs(qb + i + 256 * j);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        d = fmax(d, fmax(fabs(va[j].x - vb[j].x), fabs(va[j].y - vb[j].y)));
+                        m = fmax(m, fmax(fabs(vb[j].x), fabs(vb[j].y)));
+                    }
                 }
-                __syncthreads();
+                for (; i < n2; i += 256) {
+                    const double2 va = __ldcs(qa + i), vb = __ldcs(qb + i);
+                    d = fmax(d, fmax(fabs(va.x - vb.x), fabs(va.y - vb.y)));
+                    m = fmax(m, fmax(fabs(vb.x), fabs(vb.y)));
+                }
+                if ((len & 1) && tid == 0) {
+                    d = fmax(d, fabs(pa[len - 1] - pb[len - 1]));
+                    m = fmax(m, fabs(pb[len - 1]));
+                }
+            } else {
+                for (int64_t i = tid; i < len; i += 256) {
+                    d = fmax(d, fabs(pa[i] - pb[i]));
+                    m = fmax(m, fabs(pb[i]));
+                }
             }
-            const double r = sm[0] > 0.0 ? sd[0] / sm[0] : sd[0];
-            worst = fmax(worst, r);
+            d = warp_max_d(d);
+            m = warp_max_d(m);
+            if (lane == 0) {
+                sd[warp] = d;
+                sm[warp] = m;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                d = warp_max_d(lane < 8 ? sd[lane] : 0.0);
+                m = warp_max_d(lane < 8 ? sm[lane] : 0.0);
+                worst = fmax(worst, m > 0.0 ? d / m : d);
+            }
             __syncthreads();
         }
-        if (threadIdx.x == 0) err[e] = worst;
+        if (tid == 0) err[e] = worst;
     }
 }
 
@@ -388,8 +436,8 @@ int p2s_coarse_features(p2s_ctx* ctx, const p2s_geometry* geom, const p2s_materi
     if (geom->n_elem == 0) return P2S_OK;
     if (!geom->nodes || !mat->params || !features) return fail(P2S_ERR_ARG, "p2s_coarse_features: NULL array");
     P2S_LCUDA(cudaSetDevice(T->device));
-    const int grid = (int)std::min<int64_t>(geom->n_elem, (int64_t)T->sm_count * 32);
-    k_features<<<grid, 64, 0, (cudaStream_t)stream>>>(geom->nodes, geom->bulge, mat->params, geom->n_elem, features,
+    const int grid = (int)std::min<int64_t>((geom->n_elem + kFeatElems - 1) / kFeatElems, (int64_t)T->sm_count * 8);
+    k_features<<<grid, 64 * kFeatElems, 0, (cudaStream_t)stream>>>(geom->nodes, geom->bulge, mat->params, geom->n_elem, features,
                                                        nullptr);
     P2S_LCUDA(cudaGetLastError());
     return P2S_OK;
