@@ -42,6 +42,7 @@ __global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
     __shared__ unsigned long long unit_id;
     __shared__ int32_t s_lin[kMaxOrder * kMaxOrder];
     __shared__ int16_t s_col[kMaxOrder * kMaxOrder * kMaxOrder];  // tile offset of output column c
+    __shared__ typename A::C s_coef[kMaxOrder * kMaxOrder * kMaxOrder];  // stage-3 runs, [p1][p2][r]
     const int tid = threadIdx.x, nth = blockDim.x;
     const int32_t* __restrict__ lidx = L.lin_idx;
     const void* lcoef = L.lin_coef;
@@ -63,6 +64,8 @@ __global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
         const int Nv_i = d->ord[gi][1], Nw_i = d->ord[gi][2];
         const int Nu_j = d->ord[gj][0], Nv_j = d->ord[gj][1], Nw_j = d->ord[gj][2];
         const int Kv = Nv_i + Nv_j - 1, Kw = Nw_i + Nw_j - 1;
+        const int Kwp = Kw | 1;  // stage-2 row stride: odd, so stage 3's row reads spread over banks
+        const int Nwm = max(Nw_i, Nw_j);  // s_coef run stride
         const int n = d->n;
         const int nj = Nu_j * Nv_j * Nw_j;
         const int mjp = contract_mj_stride(Nu_j * Nv_j);
@@ -71,18 +74,29 @@ __global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
 
         // the unit's stage-3 coefficient runs, shared by every thread, and the tile offset of
         // every output column (m2, n2, p2)
-        if (tid < Nw_i * Nw_j) s_lin[tid] = __ldg(lidx + lin_slot(t, tid / Nw_j, tid % Nw_j));
+        const float rNwj = 1.f / (float)Nw_j, rNwm = 1.f / (float)Nwm;
+        if (tid < Nw_i * Nw_j) {
+            const int p1 = div_small(tid, Nw_j, rNwj);
+            s_lin[tid] = __ldg(lidx + lin_slot(t, p1, tid - p1 * Nw_j));
+        }
+        for (int i = tid; i < Nw_i * Nw_j * Nwm; i += nth) {  // the runs' coefficient values
+            const int pp = div_small(i, Nwm, rNwm), r = i - pp * Nwm;
+            const int p1 = div_small(pp, Nw_j, rNwj);
+            const int32_t li = __ldg(lidx + lin_slot(t, p1, pp - p1 * Nw_j));
+            if (r < lin_cnt(li)) s_coef[i] = A::load_coef(lcoef, lin_off(li) + r);
+        }
         for (int c = tid; c < nj; c += nth) {
-            const int mj = c / Nw_j;
+            const int mj = div_small(c, Nw_j, rNwj);
             s_col[c] = (int16_t)((c - mj * Nw_j) * mjp + mj);
         }
 
         // stage 1: A[m1][m2][l][q], m1 in the slab
         const int KvKw = Kv * Kw;
         const int nA = m1n * Nu_j * KvKw;
+        const float rKvKw = 1.f / (float)KvKw, rNuj = 1.f / (float)Nu_j;
         for (int idx = tid; idx < nA; idx += nth) {
-            const int mm = idx / KvKw, lq = idx - mm * KvKw;
-            const int im1 = mm / Nu_j, m2 = mm - im1 * Nu_j;
+            const int mm = div_small(idx, KvKw, rKvKw), lq = idx - mm * KvKw;
+            const int im1 = div_small(mm, Nu_j, rNuj), m2 = mm - im1 * Nu_j;
             const int32_t li = __ldg(lidx + lin_slot(t, m1a + im1, m2));
             const int k0 = lin_kmin(li), cnt = lin_cnt(li), off = lin_off(li);
             const size_t mb = moff + (size_t)k0 * KvKw + lq;
@@ -96,32 +110,38 @@ __global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
         const int NvKw = Nv_j * Kw;
         const int per_n1 = Nu_j * NvKw;
         const int nB = m1n * n1n * per_n1;
+        const float rper = 1.f / (float)per_n1, rn1n = 1.f / (float)n1n, rNvKw = 1.f / (float)NvKw,
+                    rKw = 1.f / (float)Kw;
         for (int idx = tid; idx < nB; idx += nth) {
-            const int mn = idx / per_n1, r2 = idx - mn * per_n1;
-            const int im1 = mn / n1n, in1 = mn - im1 * n1n;
-            const int m2 = r2 / NvKw, r3 = r2 - m2 * NvKw, n2 = r3 / Kw, q = r3 - n2 * Kw;
+            const int mn = div_small(idx, per_n1, rper), r2 = idx - mn * per_n1;
+            const int im1 = div_small(mn, n1n, rn1n), in1 = mn - im1 * n1n;
+            const int m2 = div_small(r2, NvKw, rNvKw), r3 = r2 - m2 * NvKw;
+            const int n2 = div_small(r3, Kw, rKw), q = r3 - n2 * Kw;
             const int32_t li = __ldg(lidx + lin_slot(t, n1a + in1, n2));
             const int l0 = lin_kmin(li), cnt = lin_cnt(li), off = lin_off(li);
             const T* a = sA + ((im1 * Nu_j + m2) * Kv + l0) * Kw + q;
             T acc = cnt > 0 ? A::mul(A::load_coef(lcoef, off), a[0]) : A::zero();
             for (int r = 1; r < cnt; ++r) A::fma_acc(acc, A::load_coef(lcoef, off + r), a[2 * r * Kw]);
-            sB[idx] = A::finish(acc);
+            sB[((mn * Nu_j + m2) * Nv_j + n2) * Kwp + q] = A::finish(acc);
         }
         __syncthreads();
         // stage 3: items (p1, combination (m1, n1, m2, n2)); each walks p2
         const int ncombo = m1n * n1n * Nu_j * Nv_j;
         const int mjn = Nu_j * Nv_j;
+        const float rncombo = 1.f / (float)ncombo, rmjn = 1.f / (float)mjn;
         for (int it = tid; it < ncombo * Nw_i; it += nth) {
-            const int p1 = it / ncombo, c = it - p1 * ncombo;
-            const int mn = c / mjn, mj = c - mn * mjn;  // mn = im1 * n1n + in1, mj = m2 * Nv_j + n2
-            const T* bt = sB + (size_t)c * Kw;
+            const int p1 = div_small(it, ncombo, rncombo), c = it - p1 * ncombo;
+            const int mn = div_small(c, mjn, rmjn), mj = c - mn * mjn;  // mn = im1 * n1n + in1, mj = m2 * Nv_j + n2
+            const T* bt = sB + (size_t)c * Kwp;
             double* trow = tile + (size_t)(mn * Nw_i + p1) * ld + mj;
             const int32_t* lrow = s_lin + p1 * Nw_j;
+            const typename A::C* crow = s_coef + p1 * Nw_j * Nwm;
             for (int p2 = 0; p2 < Nw_j; ++p2) {
                 const int32_t li = lrow[p2];
-                const int q0 = lin_kmin(li), cnt = lin_cnt(li), off = lin_off(li);
-                T acc = cnt > 0 ? A::mul(A::load_coef(lcoef, off), bt[q0]) : A::zero();
-                for (int r = 1; r < cnt; ++r) A::fma_acc(acc, A::load_coef(lcoef, off + r), bt[q0 + 2 * r]);
+                const int q0 = lin_kmin(li), cnt = lin_cnt(li);
+                const typename A::C* cf = crow + p2 * Nwm;
+                T acc = cnt > 0 ? A::mul(cf[0], bt[q0]) : A::zero();
+                for (int r = 1; r < cnt; ++r) A::fma_acc(acc, cf[r], bt[q0 + 2 * r]);
                 trow[p2 * mjp] = A::to_double_fast(A::finish(acc));
             }
         }
@@ -169,7 +189,7 @@ ContractShape contract_shape(const int8_t* Ni, const int8_t* Nj, int m1n, int n1
     ContractShape s;
     const int Kv = Ni[1] + Nj[1] - 1, Kw = Ni[2] + Nj[2] - 1;
     s.a = (size_t)m1n * Nj[0] * Kv * Kw;
-    s.b = (size_t)m1n * n1n * Nj[0] * Nj[1] * Kw;
+    s.b = (size_t)m1n * n1n * Nj[0] * Nj[1] * (Kw | 1);
     s.tile = (size_t)m1n * n1n * Ni[2] * contract_tile_ld(Nj[0] * Nj[1], Nj[2]);
     s.combos = m1n * n1n * Nj[0] * Nj[1];
     return s;

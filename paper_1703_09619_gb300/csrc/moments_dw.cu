@@ -128,15 +128,6 @@ __device__ __forceinline__ bool metric_alpha_dw(const dw* geo, const dw* row, co
     return det.hi > 0.f;
 }
 
-// n / d for 0 <= n < 2^20 and d >= 1, from the FP32 reciprocal rd of d: the product is
-// within 1/8 of n / d, so one correction step gives the exact quotient.
-__device__ __forceinline__ int div_small(int n, int d, float rd) {
-    int q = __float2int_rz(__int2float_rn(n) * rd);
-    const int r = n - q * d;
-    q += (r >= d) - (r < 0);
-    return q;
-}
-
 // Chunk t of an element: plane c, first row b0, nbc rows.
 struct Chunk {
     int c, b0, nbc;

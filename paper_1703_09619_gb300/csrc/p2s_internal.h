@@ -113,6 +113,18 @@ struct ContractShape {
     size_t a, b, tile;
     int combos;
 };
+#ifdef __CUDACC__
+// n / d for 0 <= n < 2^20 and d >= 1, from the FP32 reciprocal rd of d: the product is
+// within 1/8 of n / d, so one correction step gives the exact quotient (an integer
+// division by a runtime divisor is a long dependent sequence).
+__device__ __forceinline__ int div_small(int n, int d, float rd) {
+    int q = __float2int_rz(__int2float_rn(n) * rd);
+    const int r = n - q * d;
+    q += (r >= d) - (r < 0);
+    return q;
+}
+#endif
+
 // Staged contraction tile: within a row, output column (m2, n2, p2) sits at p2 * mjp + mj
 // (mj = m2 * Nv_j + n2, mjp = mjn rounded up to odd) and rows have an odd stride, so the
 // stage-3 stores (consecutive mj), the row reads (stride mjp) and the column reads (stride
