@@ -557,14 +557,18 @@ def run_fixed(args, wl):
     # tile shapes from the autotuner, launches replayed from a graph (on by default)
     tune = args.tune if args.tune is not None else True
     tile = tune_info = None
-    if tune:
+    if args.tile:
+        co, kb, th = (int(x) for x in args.tile.split(","))
+        tile = {"combo_target": co, "unit_kbytes": kb, "threads": th}
+        tune_info = {"tile": tile, "candidates": 0, "note": "given on the command line"}
+    elif tune:
         sample = min(wl.n_elem, 1024)
         tile, best_ms, tried = p2s.autotune_tiles(ctx, wl.orders, npts, wl.kind, params, nodes, bulge, prec,
                                                   wl.types_mask, sample=sample, reps=3)
         tune_info = {"tile": tile, "candidates": tried, "sample_elements": sample,
                      "sample_contract_ms": best_ms}
         log("autotune: %s (%d candidates, %.3f ms on %d elements)" % (tile, tried, best_ms, sample))
-    plan = p2s.Plan(ctx, wl.orders, npts, prec, wl.types_mask, tile=tile, graph=tune)
+    plan = p2s.Plan(ctx, wl.orders, npts, prec, wl.types_mask, tile=tile, graph=bool(tune or args.tile))
     out = torch.empty(plan.output_entries, dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -591,7 +595,7 @@ def run_fixed(args, wl):
     job_entries = D.sum_over_ranks(entries, world, dev)  # each rank fills a batch of its own
     job_elems = D.sum_over_ranks(wl.n_elem, world, dev)
     value = job_entries * args.steps / (total_ms * 1e-3)
-    e2e = None if args.no_e2e else measure_e2e_fixed(args, wl, ctx, prec, dev, tile, tune)
+    e2e = None if args.no_e2e else measure_e2e_fixed(args, wl, ctx, prec, dev, tile, bool(tune or args.tile))
     line = None
     if rank == 0:
         line = {
@@ -650,6 +654,7 @@ def main():
     ap.add_argument("--tune", dest="tune", action="store_true", default=None,
                     help="autotune the contraction tiles and replay fills from a CUDA graph (default: on)")
     ap.add_argument("--no-tune", dest="tune", action="store_false")
+    ap.add_argument("--tile", default=None, help="contraction tile combo_target,unit_kbytes,threads (skips the autotuner)")
     args = ap.parse_args()
     if args.mode is None:
         args.mode = {"fp64": "plain", "mixed": "mixed"}.get(args.precision) or (
