@@ -313,8 +313,9 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
     }
     L.tile = tile;
     L.con_threads = tile.threads ? tile.threads : std::min(512, std::max(64, (max_combos + 31) / 32 * 32));
+    L.combo_cap = (size_t)max_combos;
     L.tile_off = contract_tile_offset(L.precision, L.a_cap, L.b_cap);
-    L.con_smem = contract_smem_bytes(L.precision, L.a_cap, L.b_cap, L.tile_cap);
+    L.con_smem = contract_smem_bytes(L.precision, L.a_cap, L.b_cap, L.tile_cap, L.combo_cap);
     if (!spec_n) {
         if (L.con_smem > limit) return fail(P2S_ERR_ORDER, "plan: contraction tile too large");
         int con_per_sm = contract_blocks_per_sm(L.precision, L.con_threads, L.con_smem);
@@ -408,6 +409,8 @@ int run_contract(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_
     C.a_cap = (int)PL.a_cap;
     C.b_cap = (int)PL.b_cap;
     C.tile_off = (int)PL.tile_off;
+    C.combo_off = (int)contract_combo_offset(PL.precision, PL.a_cap, PL.b_cap, PL.tile_cap);
+    C.combo_cap = (int)PL.combo_cap;
     C.elem_mask = elem_mask;
     if (PL.spec_n)
         P2S_CUDA(launch_contract_ffn(PL.spec_n, C, PL.con_grid, PL.con_threads, PL.con_smem, s));

@@ -38,6 +38,8 @@ __global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
     T* sA = reinterpret_cast<T*>(smraw);
     T* sB = sA + L.a_cap;
     double* tile = reinterpret_cast<double*>(smraw + L.tile_off);
+    uint32_t* s_cmb = reinterpret_cast<uint32_t*>(smraw + L.combo_off);  // im1 | in1 << 8 | m2 << 16 | n2 << 24
+    int32_t* s_cli = reinterpret_cast<int32_t*>(s_cmb + L.combo_cap);     // stage-2 run of (n1, n2)
     __shared__ ContractUnit cu;
     __shared__ unsigned long long unit_id;
     __shared__ int32_t s_lin[kMaxOrder * kMaxOrder];
@@ -89,6 +91,20 @@ __global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
             const int mj = div_small(c, Nw_j, rNwj);
             s_col[c] = (int16_t)((c - mj * Nw_j) * mjp + mj);
         }
+        // every combination (m1, n1, m2, n2) of the unit, decoded once: c = mn * mjn + mj with
+        // mn = im1 * n1n + in1, mj = m2 * Nv_j + n2
+        const int ncombo = m1n * n1n * Nu_j * Nv_j;
+        const int mjn = Nu_j * Nv_j;
+        {
+            const float rmjn = 1.f / (float)mjn, rn1n = 1.f / (float)n1n, rNvj = 1.f / (float)Nv_j;
+            for (int c = tid; c < ncombo; c += nth) {
+                const int mn = div_small(c, mjn, rmjn), mj = c - mn * mjn;
+                const int im1 = div_small(mn, n1n, rn1n), in1 = mn - im1 * n1n;
+                const int m2 = div_small(mj, Nv_j, rNvj), n2 = mj - m2 * Nv_j;
+                s_cmb[c] = (uint32_t)im1 | ((uint32_t)in1 << 8) | ((uint32_t)m2 << 16) | ((uint32_t)n2 << 24);
+                s_cli[c] = __ldg(lidx + lin_slot(t, n1a + in1, n2));
+            }
+        }
 
         // stage 1: A[m1][m2][l][q], m1 in the slab
         const int KvKw = Kv * Kw;
@@ -107,31 +123,27 @@ __global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
         }
         __syncthreads();
         // stage 2: Bt[m1][n1][m2][n2][q], (m1, n1) in the slab
-        const int NvKw = Nv_j * Kw;
-        const int per_n1 = Nu_j * NvKw;
-        const int nB = m1n * n1n * per_n1;
-        const float rper = 1.f / (float)per_n1, rn1n = 1.f / (float)n1n, rNvKw = 1.f / (float)NvKw,
-                    rKw = 1.f / (float)Kw;
+        const int nB = ncombo * Kw;
+        const float rKw = 1.f / (float)Kw;
         for (int idx = tid; idx < nB; idx += nth) {
-            const int mn = div_small(idx, per_n1, rper), r2 = idx - mn * per_n1;
-            const int im1 = div_small(mn, n1n, rn1n), in1 = mn - im1 * n1n;
-            const int m2 = div_small(r2, NvKw, rNvKw), r3 = r2 - m2 * NvKw;
-            const int n2 = div_small(r3, Kw, rKw), q = r3 - n2 * Kw;
-            const int32_t li = __ldg(lidx + lin_slot(t, n1a + in1, n2));
+            const int c = div_small(idx, Kw, rKw), q = idx - c * Kw;
+            const uint32_t w = s_cmb[c];
+            const int im1 = w & 0xffu, m2 = (w >> 16) & 0xffu;
+            const int32_t li = s_cli[c];
             const int l0 = lin_kmin(li), cnt = lin_cnt(li), off = lin_off(li);
             const T* a = sA + ((im1 * Nu_j + m2) * Kv + l0) * Kw + q;
             T acc = cnt > 0 ? A::mul(A::load_coef(lcoef, off), a[0]) : A::zero();
             for (int r = 1; r < cnt; ++r) A::fma_acc(acc, A::load_coef(lcoef, off + r), a[2 * r * Kw]);
-            sB[((mn * Nu_j + m2) * Nv_j + n2) * Kwp + q] = A::finish(acc);
+            sB[c * Kwp + q] = A::finish(acc);
         }
         __syncthreads();
         // stage 3: items (p1, combination (m1, n1, m2, n2)); each walks p2
-        const int ncombo = m1n * n1n * Nu_j * Nv_j;
-        const int mjn = Nu_j * Nv_j;
-        const float rncombo = 1.f / (float)ncombo, rmjn = 1.f / (float)mjn;
+        const float rncombo = 1.f / (float)ncombo;
         for (int it = tid; it < ncombo * Nw_i; it += nth) {
             const int p1 = div_small(it, ncombo, rncombo), c = it - p1 * ncombo;
-            const int mn = div_small(c, mjn, rmjn), mj = c - mn * mjn;  // mn = im1 * n1n + in1, mj = m2 * Nv_j + n2
+            const uint32_t w = s_cmb[c];
+            const int mn = (int)(w & 0xffu) * n1n + (int)((w >> 8) & 0xffu);       // im1 * n1n + in1
+            const int mj = (int)((w >> 16) & 0xffu) * Nv_j + (int)(w >> 24);      // m2 * Nv_j + n2
             const T* bt = sB + (size_t)c * Kwp;
             double* trow = tile + (size_t)(mn * Nw_i + p1) * ld + mj;
             const int32_t* lrow = s_lin + p1 * Nw_j;
@@ -200,8 +212,12 @@ size_t contract_tile_offset(int precision, size_t a_cap, size_t b_cap) {
     return ((a_cap + b_cap) * el + 15) & ~(size_t)15;
 }
 
-size_t contract_smem_bytes(int precision, size_t a_cap, size_t b_cap, size_t tile_cap) {
+size_t contract_combo_offset(int precision, size_t a_cap, size_t b_cap, size_t tile_cap) {
     return contract_tile_offset(precision, a_cap, b_cap) + tile_cap * sizeof(double);
+}
+
+size_t contract_smem_bytes(int precision, size_t a_cap, size_t b_cap, size_t tile_cap, size_t combo_cap) {
+    return contract_combo_offset(precision, a_cap, b_cap, tile_cap) + 2 * sizeof(uint32_t) * combo_cap;
 }
 
 cudaError_t launch_contract(int precision, const ContractLaunch& L, int grid, int threads, size_t smem,

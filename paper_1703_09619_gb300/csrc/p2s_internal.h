@@ -107,6 +107,8 @@ struct ContractLaunch {
     uint32_t types_mask;
     int a_cap, b_cap;      // elements of the stage-1 / stage-2 buffers
     int tile_off;          // byte offset of the FP64 tile in shared memory
+    int combo_off;         // general kernel: byte offset of the per-unit combination tables
+    int combo_cap;         // entries of each combination table
     const int8_t* elem_mask;  // optional: units of elements with mask 0 are skipped (generic kernel)
 };
 struct ContractShape {
@@ -133,7 +135,10 @@ __host__ __device__ __forceinline__ int contract_mj_stride(int mjn) { return mjn
 __host__ __device__ __forceinline__ int contract_tile_ld(int mjn, int nw) { return (nw * contract_mj_stride(mjn)) | 1; }
 ContractShape contract_shape(const int8_t* Ni, const int8_t* Nj, int m1n, int n1n);
 size_t contract_tile_offset(int precision, size_t a_cap, size_t b_cap);
-size_t contract_smem_bytes(int precision, size_t a_cap, size_t b_cap, size_t tile_cap);
+// Shared memory of the general contraction: stage-1/2 buffers, the tile, then two 4-byte
+// tables of combo_cap entries (packed combination indices, stage-2 run descriptors).
+size_t contract_smem_bytes(int precision, size_t a_cap, size_t b_cap, size_t tile_cap, size_t combo_cap = 0);
+size_t contract_combo_offset(int precision, size_t a_cap, size_t b_cap, size_t tile_cap);
 cudaError_t launch_contract(int precision, const ContractLaunch& L, int grid, int threads, size_t smem,
                             cudaStream_t s);
 int contract_blocks_per_sm(int precision, int threads, size_t smem);
@@ -180,7 +185,7 @@ struct PlanLayout {
     int n_pairs = 1, kb = 1, gmax = 1, iacc_cap = 0;
     size_t mom_smem = 0;
     int mom_grid = 1;
-    size_t a_cap = 1, b_cap = 1, tile_cap = 1;
+    size_t a_cap = 1, b_cap = 1, tile_cap = 1, combo_cap = 1;
     int con_threads = 256;
     size_t con_smem = 0, tile_off = 0;
     int con_grid = 1;
