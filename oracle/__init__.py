@@ -65,6 +65,9 @@ def _load():
             lib.or_output_offsets.argtypes = [i64, ctypes.c_int, P, u32, P]
             lib.or_output_offsets.restype = i64
             lib.or_fill.argtypes = [i64, ctypes.c_int, P, ctypes.c_int, P, P, P, P, u32, P, ctypes.c_int]
+            lib.or_fill_terms.restype = ctypes.c_int
+            lib.or_fill_terms.argtypes = [i64, ctypes.c_int, P, ctypes.c_int, P, P, P, P, ctypes.c_int, P, P, P,
+                                          ctypes.c_int]
             lib.or_fill.restype = ctypes.c_int
             lib.or_linearisation.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_int, P]
@@ -157,6 +160,39 @@ def fill(orders, kind, params, nodes, bulge, npts, types_mask=0xF, nthreads=None
                      types_mask, _ptr(out), int(nthreads or default_threads()))
     if rc not in (0, -3):
         raise RuntimeError("oracle fill failed: %d" % rc)
+    return out, off, rc
+
+
+def fill_terms(orders, kind, params, nodes, bulge, npts, terms, scales, nthreads=None):
+    """Direct triple Gauss-Legendre fill of an operator given as a term list (Eq. (2) with
+    the value/derivative choice per axis and several coupling-factor entries summed).
+
+    terms: int [T, 10] rows (gi, gj, sa, sb, du, dv, dw, eu, ev, ew): block (gi, gj),
+    coupling entry alpha[sa][sb], derivative orders of the test (d*) and trial (e*)
+    functions per axis; scales: float [T].  Returns (flat output: one n x n matrix per
+    element, offsets[E+1], status)."""
+    lib = _load()
+    orders = np.ascontiguousarray(orders, dtype=np.int32)
+    E, nc = orders.shape[0], orders.shape[1]
+    params = np.ascontiguousarray(params, dtype=np.float64).reshape(E, -1)
+    if nodes is None:
+        nodes = np.zeros((E, 8, 3))
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64).reshape(E, 8, 3)
+    if bulge is not None:
+        bulge = np.ascontiguousarray(bulge, dtype=np.float64).reshape(E, 4)
+    if np.isscalar(npts):
+        npts = np.full(E, int(npts), dtype=np.int32)
+    npts = np.ascontiguousarray(npts, dtype=np.int32).reshape(E)
+    terms = np.ascontiguousarray(terms, dtype=np.int32).reshape(-1, 10)
+    scales = np.ascontiguousarray(scales, dtype=np.float64).reshape(-1)
+    if terms.shape[0] != scales.shape[0]:
+        raise ValueError("terms and scales differ in length")
+    off = output_offsets(orders, 1)
+    out = np.zeros(int(off[-1]), dtype=np.float64)
+    rc = lib.or_fill_terms(E, nc, _ptr(orders), int(kind), _ptr(params), _ptr(nodes), _ptr(bulge), _ptr(npts),
+                           int(terms.shape[0]), _ptr(terms), _ptr(scales), _ptr(out), int(nthreads or default_threads()))
+    if rc not in (0, -3):
+        raise RuntimeError("oracle term fill failed: %d" % rc)
     return out, off, rc
 
 

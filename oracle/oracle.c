@@ -441,6 +441,194 @@ int or_fill(int64_t E, int n_comp, const int32_t* orders, int kind, const double
 }
 
 /* ----------------------------------------------------------------------- */
+/* Operators given as term lists (Eq. (2) in full generality).                */
+/* A term adds to the block (gi, gj) of the element matrix
+ *
+ *   scale * sum_{a,b,c} w_a w_b w_c  f_u(a) f_v(b) f_w(c)  alpha_{sa sb}(u_a, v_b, w_c)
+ *
+ * with f_u(a) = P^{(du)}_{m1}(u_a) P^{(eu)}_{m2}(u_a), (du, eu) the term's derivative
+ * orders of the test and trial functions on u (likewise v, w), so the value /
+ * derivative choice may differ per axis.  alpha_{sa sb} is an entry of the coupling
+ * factor matrix: for the metric kind eps detJ (J^{-1} J^{-T})_{sa sb} (sa, sb < 3, any
+ * number of field components), for the scalar and POLY kinds the scalar (sa = sb = 0).
+ * terms: n_terms rows of 10 ints (gi, gj, sa, sb, du, dv, dw, eu, ev, ew); scales[n_terms].
+ * Output per element: one n x n row-major matrix, n = sum_g Nu_g Nv_g Nw_g, rows test
+ * dofs, columns trial dofs (same dof numbering as or_fill); every entry is the sum over
+ * the terms of its block, all terms and points in one Neumaier accumulator.          */
+typedef struct {
+    or_job jb;           /* elements, geometry, quadrature, output (types_mask unused) */
+    int nalpha;          /* entries of the coupling factor matrix per side: 3 or 1 */
+    int n_terms;
+    const int32_t* terms;
+    const double* scales;
+} or_opjob;
+
+static int build_cache_op(or_opjob* oj, or_cache* ch, int64_t e)
+{
+    or_job* jb = &oj->jb;
+    int G = jb->npts[e];
+    if (G < 1 || G > OR_MAXG) return -1;
+    ch->e = e;
+    ch->G = G;
+    or_gauss_legendre(G, ch->xg, ch->wg);
+    int nmax = 0;
+    const int32_t* ord = jb->orders + 3 * jb->n_comp * e;
+    for (int i = 0; i < 3 * jb->n_comp; ++i) if (ord[i] > nmax) nmax = ord[i];
+    if (nmax < 1 || nmax > OR_MAXN) return -2;
+    for (int a = 0; a < G; ++a) {
+        double P[OR_MAXN], dP[OR_MAXN];
+        or_legendre(nmax, ch->xg[a], P, dP);
+        for (int j = 0; j < nmax; ++j) { ch->P[j][a] = P[j]; ch->dP[j][a] = dP[j]; }
+    }
+    int na = oj->nalpha;
+    size_t need = (size_t)G * G * G * na * na;
+    if (need > ch->alpha_cap) {
+        free(ch->alpha);
+        ch->alpha = (double*)malloc(need * sizeof(double));
+        if (!ch->alpha) { ch->alpha_cap = 0; return -4; }
+        ch->alpha_cap = need;
+    }
+    int np = or_alpha_nparams(jb->kind);
+    const double* p = jb->params + (size_t)np * e;
+    const double* nodes = jb->nodes ? jb->nodes + 24 * e : NULL;
+    const double* bulge = jb->bulge ? jb->bulge + 4 * e : NULL;
+    ch->bad_jac = 0;
+    for (int c = 0; c < G; ++c)
+        for (int b = 0; b < G; ++b)
+            for (int a = 0; a < G; ++a) {
+                double al[9];
+                double det = or_alpha(jb->kind, p, nodes, bulge, ch->xg[a], ch->xg[b], ch->xg[c], al);
+                if (!(det > 0.0)) ch->bad_jac = 1;
+                memcpy(ch->alpha + ((size_t)(c * G + b) * G + a) * na * na, al, sizeof(double) * na * na);
+            }
+    return 0;
+}
+
+static double fac(const or_cache* ch, int d, int m, int a) { return d ? ch->dP[m][a] : ch->P[m][a]; }
+
+static void fill_row_op(or_opjob* oj, or_cache* ch, int64_t e, int row)
+{
+    or_job* jb = &oj->jb;
+    const int32_t* ord = jb->orders + 3 * jb->n_comp * e;
+    int nc = jb->n_comp, na = oj->nalpha;
+    int G = ch->G;
+    int64_t n = elem_ndof(nc, ord);
+    int gi = 0, r = row;
+    while (r >= ord[3 * gi] * ord[3 * gi + 1] * ord[3 * gi + 2]) {
+        r -= ord[3 * gi] * ord[3 * gi + 1] * ord[3 * gi + 2];
+        ++gi;
+    }
+    int Nv_i = ord[3 * gi + 1], Nw_i = ord[3 * gi + 2];
+    int m1 = r / (Nv_i * Nw_i), n1 = (r / Nw_i) % Nv_i, p1 = r % Nw_i;
+    double* orow = jb->out + jb->offsets[e] + (int64_t)row * n;
+    int64_t col = 0;
+    for (int gj = 0; gj < nc; ++gj) {
+        int Nu_j = ord[3 * gj], Nv_j = ord[3 * gj + 1], Nw_j = ord[3 * gj + 2];
+        for (int m2 = 0; m2 < Nu_j; ++m2)
+            for (int n2 = 0; n2 < Nv_j; ++n2)
+                for (int p2 = 0; p2 < Nw_j; ++p2) {
+                    or_acc acc = {0.0, 0.0};
+                    for (int k = 0; k < oj->n_terms; ++k) {
+                        const int32_t* tm = oj->terms + 10 * k;
+                        if (tm[0] != gi || tm[1] != gj) continue;
+                        int sa = tm[2], sb = tm[3];
+                        for (int c = 0; c < G; ++c) {
+                            double fw = fac(ch, tm[6], p1, c) * fac(ch, tm[9], p2, c);
+                            for (int b = 0; b < G; ++b) {
+                                double fv = fac(ch, tm[5], n1, b) * fac(ch, tm[8], n2, b);
+                                for (int a = 0; a < G; ++a) {
+                                    double fu = fac(ch, tm[4], m1, a) * fac(ch, tm[7], m2, a);
+                                    double al = ch->alpha[((size_t)(c * G + b) * G + a) * na * na + sa * na + sb];
+                                    acc_add(&acc, oj->scales[k] * (ch->wg[a] * ch->wg[b] * ch->wg[c] * fu * fv * fw * al));
+                                }
+                            }
+                        }
+                    }
+                    orow[col++] = acc.s + acc.c;
+                }
+    }
+}
+
+static void* worker_op(void* arg)
+{
+    or_opjob* oj = (or_opjob*)arg;
+    or_job* jb = &oj->jb;
+    or_cache* ch = (or_cache*)calloc(1, sizeof(or_cache));
+    if (!ch) { jb->status = -4; return NULL; }
+    ch->e = -1;
+    for (;;) {
+        pthread_mutex_lock(&jb->mu);
+        int64_t t = jb->next_task++;
+        pthread_mutex_unlock(&jb->mu);
+        if (t >= jb->n_tasks) break;
+        int64_t e = jb->task_elem[t];
+        if (ch->e != e) {
+            int rc = build_cache_op(oj, ch, e);
+            if (rc) { jb->status = rc; continue; }
+            if (ch->bad_jac) jb->status = -3;
+        }
+        fill_row_op(oj, ch, e, jb->task_row[t]);
+    }
+    free(ch->alpha);
+    free(ch);
+    return NULL;
+}
+
+/* Term-list fill of E elements; out holds sum_e n_e^2 doubles (or_output_offsets with
+ * types_mask = 1).  Returns as or_fill; -1 also for a term out of range.             */
+int or_fill_terms(int64_t E, int n_comp, const int32_t* orders, int kind, const double* params,
+                  const double* nodes, const double* bulge, const int32_t* npts, int n_terms,
+                  const int32_t* terms, const double* scales, double* out, int nthreads)
+{
+    if (E < 0 || n_comp < 1 || n_comp > 3 || !orders || !params || !npts || !out || n_terms < 0) return -1;
+    if (n_terms > 0 && (!terms || !scales)) return -1;
+    if (kind < 0 || kind > 2) return -1;
+    if (kind == OR_ALPHA_METRIC_EPS && !nodes) return -1;
+    int na = kind == OR_ALPHA_METRIC_EPS ? 3 : 1;
+    for (int k = 0; k < n_terms; ++k) {
+        const int32_t* tm = terms + 10 * k;
+        if (tm[0] < 0 || tm[0] >= n_comp || tm[1] < 0 || tm[1] >= n_comp) return -1;
+        if (tm[2] < 0 || tm[2] >= na || tm[3] < 0 || tm[3] >= na) return -1;
+        for (int i = 4; i < 10; ++i) if (tm[i] != 0 && tm[i] != 1) return -1;
+    }
+    for (int64_t i = 0; i < E * 3 * n_comp; ++i)
+        if (orders[i] < 1 || orders[i] > OR_MAXN) return -2;
+    or_opjob oj;
+    memset(&oj, 0, sizeof(oj));
+    or_job* jb = &oj.jb;
+    jb->E = E; jb->n_comp = n_comp; jb->orders = orders; jb->kind = kind; jb->params = params;
+    jb->nodes = nodes; jb->bulge = bulge; jb->npts = npts; jb->types_mask = 1u; jb->out = out;
+    oj.nalpha = na; oj.n_terms = n_terms; oj.terms = terms; oj.scales = scales;
+    int64_t* offsets = (int64_t*)malloc(sizeof(int64_t) * (E + 1));
+    if (!offsets) return -4;
+    or_output_offsets(E, n_comp, orders, 1u, offsets);
+    jb->offsets = offsets;
+    int64_t ntask = 0;
+    for (int64_t e = 0; e < E; ++e) ntask += elem_ndof(n_comp, orders + 3 * n_comp * e);
+    jb->task_elem = (int64_t*)malloc(sizeof(int64_t) * (ntask + 1));
+    jb->task_row = (int32_t*)malloc(sizeof(int32_t) * (ntask + 1));
+    if (!jb->task_elem || !jb->task_row) { free(offsets); free(jb->task_elem); free(jb->task_row); return -4; }
+    int64_t t = 0;
+    for (int64_t e = 0; e < E; ++e) {
+        int64_t n = elem_ndof(n_comp, orders + 3 * n_comp * e);
+        for (int64_t r = 0; r < n; ++r) { jb->task_elem[t] = e; jb->task_row[t] = (int32_t)r; ++t; }
+    }
+    jb->n_tasks = ntask;
+    pthread_mutex_init(&jb->mu, NULL);
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    pthread_t th[256];
+    int started = 0;
+    for (int i = 0; i < nthreads; ++i)
+        if (pthread_create(&th[i], NULL, worker_op, &oj) == 0) ++started;
+    if (started == 0) worker_op(&oj);
+    for (int i = 0; i < started; ++i) pthread_join(th[i], NULL);
+    pthread_mutex_destroy(&jb->mu);
+    free(offsets); free(jb->task_elem); free(jb->task_row);
+    return jb->status;
+}
+
+/* ----------------------------------------------------------------------- */
 /* Linearisation coefficients by projection (Eq. (3)).                       */
 /* C[k] for k = 0..kmax, with P^{(d1)}_{m1} P^{(d2)}_{m2} = sum_k C[k] P_k:
  *   C[k] = (2k+1)/2 * int_{-1}^{1} P^{(d1)}_{m1} P^{(d2)}_{m2} P_k,

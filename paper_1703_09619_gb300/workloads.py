@@ -196,6 +196,23 @@ def make(name: str, n_elem: int | None = None, shard: int = 0) -> Workload:
     return w
 
 
+def diffusion_terms(component: int = 0, scale: float = 1.0):
+    """Term list of the diffusion stiffness sum_ab alpha_ab d_a(test) d_b(trial) on one
+    field component, with alpha the metric coupling factor eps detJ J^-1 J^-T: nine
+    terms (a, b), derivative on axis a of the test and on axis b of the trial function.
+    Rows (gi, gj, sa, sb, du, dv, dw, eu, ev, ew) and scales; input data only."""
+    terms, scales = [], []
+    for a in range(3):
+        for b in range(3):
+            d = [0, 0, 0]
+            f = [0, 0, 0]
+            d[a] = 1
+            f[b] = 1
+            terms.append([component, component, a, b] + d + f)
+            scales.append(scale)
+    return np.array(terms, dtype=np.int32), np.array(scales, dtype=np.float64)
+
+
 def judge_elements(n_elem: int, frac: float, seed: int) -> np.ndarray:
     """Seeded, sorted sample of element indices re-filled by the full-order judge."""
     k = int(np.ceil(frac * n_elem)) if frac > 0 else 0

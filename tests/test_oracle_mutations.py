@@ -6,6 +6,7 @@ import pytest
 
 import oracle
 from tests import test_oracle_pins as pins
+from tests import test_oracle_terms as term_pins
 
 MUTATIONS = {
     "inverse_transposed": ("inv[3 * i + j] = C[3 * j + i] / det;", "inv[3 * i + j] = C[3 * i + j] / det;"),
@@ -25,6 +26,12 @@ MUTATIONS = {
                         "P[j + 1] = ((2.0 * j + 1.0) * x * P[j] + j * P[j - 1]) / (j + 1.0);"),
     "trilinear_shape_sign": ("double s[3] = {(n & 1) ? 1.0 : -1.0,", "double s[3] = {(n & 1) ? -1.0 : 1.0,"),
     "projection_norm": ("C[k] = (2.0 * k + 1.0) / 2.0 * (acc.s + acc.c);", "C[k] = (2.0 * k + 1.0) * (acc.s + acc.c);"),
+    # the term-list fill
+    "term_block_filter": ("if (tm[0] != gi || tm[1] != gj) continue;", "if (tm[0] != gi) continue;"),
+    "term_scale_dropped": ("acc_add(&acc, oj->scales[k] * (", "acc_add(&acc, 1.0 * ("),
+    "term_alpha_entry": ("+ sa * na + sb];", "+ sa * na + sa];"),
+    "term_test_trial_w": ("double fw = fac(ch, tm[6], p1, c) * fac(ch, tm[9], p2, c);",
+                          "double fw = fac(ch, tm[9], p1, c) * fac(ch, tm[6], p2, c);"),
 }
 
 PIN_CALLS = [
@@ -39,6 +46,9 @@ PIN_CALLS = [
     lambda: pins.test_metric_coupling_defining_identity(),
     lambda: pins.test_direct_equals_product_to_sum_small_orders("metric"),
     lambda: pins.test_invariants_on_curved_metric_element(),
+    lambda: term_pins.test_diffusion_on_unit_cube_closed_form(),
+    lambda: term_pins.test_random_terms_match_brute_force_metric(),
+    lambda: term_pins.test_random_terms_match_brute_force_scalar(),
 ]
 
 
