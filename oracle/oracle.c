@@ -519,7 +519,9 @@ static void fill_row_op(or_opjob* oj, or_cache* ch, int64_t e, int row)
         ++gi;
     }
     int Nv_i = ord[3 * gi + 1], Nw_i = ord[3 * gi + 2];
-    int m1 = r / (Nv_i * Nw_i), n1 = (r / Nw_i) % Nv_i, p1 = r % Nw_i;
+    int m1 = r / (Nv_i * Nw_i);       /* row r of block gi = (m1 * Nv + n1) * Nw + p1 */
+    int n1 = (r / Nw_i) % Nv_i;
+    int p1 = r % Nw_i;
     double* orow = jb->out + jb->offsets[e] + (int64_t)row * n;
     int64_t col = 0;
     for (int gj = 0; gj < nc; ++gj) {

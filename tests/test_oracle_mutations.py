@@ -30,6 +30,7 @@ MUTATIONS = {
     "term_block_filter": ("if (tm[0] != gi || tm[1] != gj) continue;", "if (tm[0] != gi) continue;"),
     "term_scale_dropped": ("acc_add(&acc, oj->scales[k] * (", "acc_add(&acc, 1.0 * ("),
     "term_alpha_entry": ("+ sa * na + sb];", "+ sa * na + sa];"),
+    "term_row_index": ("int n1 = (r / Nw_i) % Nv_i;\n    int p1 = r % Nw_i;", "int p1 = (r / Nw_i) % Nv_i;\n    int n1 = r % Nw_i;"),
     "term_test_trial_w": ("double fw = fac(ch, tm[6], p1, c) * fac(ch, tm[9], p2, c);",
                           "double fw = fac(ch, tm[9], p1, c) * fac(ch, tm[6], p2, c);"),
 }
