@@ -207,6 +207,47 @@ int p2s_autotune_tiles(p2s_ctx* ctx, const p2s_geometry* geom, const p2s_materia
  * re-captures and updates the graph in place.  The other plan calls are unaffected. */
 int p2s_plan_use_graph(p2s_plan* plan, int enable);
 
+/* ------------------------------------------------------------------------------------
+ * Operators given as term lists: Eq. (2) in full generality.  Each term adds to the block
+ * (gi, gj) of an element matrix
+ *
+ *   scale * int P^(d_test[0])_{m1}(u) P^(d_trial[0])_{m2}(u) * (same in v) * (same in w)
+ *                 * alpha_{sa sb}(u, v, w) du dv dw
+ *
+ * (Gauss-Legendre quadrature of the plan's G), so the value/derivative choice may differ per
+ * axis and several coupling-factor entries may sum into one matrix.  alpha is the coupling
+ * factor of the material kind: P2S_ALPHA_METRIC_EPS gives the 3 x 3 matrix
+ * eps detJ J^-1 J^-T (sa, sb < 3, for any number of field components), P2S_ALPHA_SCALAR the
+ * scalar (sa = sb = 0).  Example: the diffusion stiffness sum_ab alpha_ab d_a phi_i d_b phi_j
+ * of one scalar field is nine terms (a, b) with d_test = e_a, d_trial = e_b.
+ * The moments of Eq. (4) are computed once per element for every coupling entry at the
+ * element's largest K per axis and shared by all terms; the product-to-sum contraction runs
+ * the terms of a block one after the other into one staged tile.  A term list closed under
+ * the mirror (gi,gj,sa,sb,d_test,d_trial,scale) -> (gj,gi,sb,sa,d_trial,d_test,scale) gives a
+ * symmetric matrix: then only the blocks gi <= gj are computed and written twice.
+ * Output per element: one n x n row-major matrix (n = sum_g Nu_g Nv_g Nw_g, rows test dofs,
+ * columns trial dofs, dof numbering as above); blocks without terms are zero. */
+typedef struct {
+    int32_t gi, gj;      /* test / trial field component of the block the term adds to    */
+    int32_t sa, sb;      /* coupling-factor entry alpha[sa][sb]                            */
+    int32_t d_test[3];   /* derivative order (0 or 1) of the test function on u, v, w      */
+    int32_t d_trial[3];  /* derivative order (0 or 1) of the trial function on u, v, w     */
+    double scale;
+} p2s_term;
+
+/* Plan an operator fill of E elements: orders of the field (1..3 components, host),
+ * quadrature, precision (P2S_FP64 or P2S_MIXED), material kind, n_terms terms (host, read
+ * during the call), optional tile configuration.  The plan works with p2s_plan_fill,
+ * p2s_plan_moments / p2s_plan_contract (moments in the plan's own layout, sized by
+ * p2s_plan_moment_entries), p2s_plan_output_entries, p2s_plan_use_graph and
+ * p2s_plan_tile_config; the material passed to the fill must have `kind`.  Errors:
+ * P2S_ERR_ARG (NULL, term out of range, n_terms outside 1..4096), P2S_ERR_ORDER,
+ * P2S_ERR_OOM, P2S_ERR_CUDA. */
+int p2s_operator_plan_create(p2s_ctx* ctx, int64_t n_elem, const p2s_orders* orders,
+                             const p2s_quadrature* quad, int precision, int kind,
+                             const p2s_term* terms, int n_terms, const p2s_tile_config* tile,
+                             p2s_plan** out);
+
 /* One-shot fill: plan, fill, release.  Same arguments and errors as the plan calls;
  * `out` must hold p2s_output_entries(...) doubles. */
 int p2s_fill_elements(p2s_ctx* ctx, const p2s_geometry* geom, const p2s_material* mat,

@@ -1,5 +1,6 @@
 // C ABI of libp2s (declared in include/p2s.h): contexts, plans, launches, error reporting.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -48,6 +49,16 @@ struct p2s_plan {
     unsigned long long* d_counter = nullptr;  // [0] contraction unit queue, [1] moment element queue
     double* d_mom = nullptr;  // moment scratch of p2s_plan_fill
     int32_t* d_order = nullptr;  // optional element order of the moment queue
+    // moment view: an operator plan computes its moments on a virtual element (every coupling
+    // entry at the element's largest K); other plans alias L and d_desc
+    PlanLayout Lm;
+    ElemDesc* d_mdesc = nullptr;
+    // operator plans: terms grouped by block, packed (see ContractLaunch), their scales, and
+    // the (start, count) of each block (gi, gj) at 2 (3 gi + gj)
+    int32_t* d_op_terms = nullptr;
+    double* d_op_scales = nullptr;
+    int32_t* d_op_block = nullptr;
+    int op_nalpha = 0;
     // CUDA-graph replay of p2s_plan_fill: the launch sequence (queue reset, moments,
     // contraction) captured on a private stream, re-captured when the arguments change
     bool use_graph = false;
@@ -179,6 +190,40 @@ void add_units(const ElemDesc& d, uint32_t mask, int32_t e, UnitSink& units, int
 
 namespace p2s {
 
+// Launch shape of the general contraction for E elements with nc field components: the
+// buffers sized for the largest unit, one thread per stage-3 combination of the largest unit
+// (rounded to whole warps) unless the tile configuration fixes the CTA size.  With `check`
+// the shared memory must fit (`limit`) and at least one CTA per SM.
+int general_contract_shape(const DeviceTables& T, int64_t E, const ElemDesc* desc, int nc, const TileParams& tile,
+                           bool check, size_t limit, PlanLayout& L) {
+    int max_combos = 1;
+    for (int64_t e = 0; e < E; ++e) {
+        const ElemDesc& d = desc[e];
+        for (int gi = 0; gi < nc; ++gi)
+            for (int gj = 0; gj < nc; ++gj) {
+                int m1n, n1n;
+                slab_sizes(d, gi, gj, m1n, n1n, 0, tile);
+                ContractShape sh = contract_shape(d.ord[gi], d.ord[gj], m1n, n1n);
+                L.a_cap = std::max(L.a_cap, sh.a);
+                L.b_cap = std::max(L.b_cap, sh.b);
+                L.tile_cap = std::max(L.tile_cap, sh.tile);
+                max_combos = std::max(max_combos, sh.combos);
+            }
+    }
+    L.tile = tile;
+    L.con_threads = tile.threads ? tile.threads : std::min(512, std::max(64, (max_combos + 31) / 32 * 32));
+    L.combo_cap = (size_t)max_combos;
+    L.tile_off = contract_tile_offset(L.precision, L.a_cap, L.b_cap);
+    L.con_smem = contract_smem_bytes(L.precision, L.a_cap, L.b_cap, L.tile_cap, L.combo_cap);
+    if (check) {
+        if (L.con_smem > limit) return fail(P2S_ERR_ORDER, "plan: contraction tile too large");
+        int con_per_sm = contract_blocks_per_sm(L.precision, L.con_threads, L.con_smem);
+        if (con_per_sm < 1) return fail(P2S_ERR_ORDER, "plan: contraction kernel does not fit");
+        L.con_grid = T.sm_count * con_per_sm;
+    }
+    return P2S_OK;
+}
+
 int tile_params_from(const p2s_tile_config* c, TileParams& tp) {
     tp = TileParams();
     if (!c) return P2S_OK;
@@ -192,7 +237,8 @@ int tile_params_from(const p2s_tile_config* c, TileParams& tp) {
 }
 
 int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, const p2s_quadrature* quad,
-                 const p2s_fill_opts* opts, ElemDesc* desc, UnitSink& units, PlanLayout& L, const TileParams& tile) {
+                 const p2s_fill_opts* opts, ElemDesc* desc, UnitSink& units, PlanLayout& L, const TileParams& tile,
+                 bool moments_only) {
     if (!quad || !opts) return fail(P2S_ERR_ARG, "plan: NULL quadrature or options");
     int rc = check_orders(E, orders);
     if (rc) return rc;
@@ -258,7 +304,7 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
         max_pair = std::max(max_pair, d.kax[0] * d.kax[1] * d.kax[2]);
         max_elem_mom = std::max(max_elem_mom, L.n_pairs * d.kax[0] * d.kax[1] * d.kax[2]);
         L.gmax = std::max(L.gmax, G);
-        add_units(d, opts->types_mask, (int32_t)e, units, spec_n, tile);
+        if (!moments_only) add_units(d, opts->types_mask, (int32_t)e, units, spec_n, tile);
     }
     L.out_entries = out_off;
     L.mom_entries = mom_off;
@@ -295,33 +341,10 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
     if (per_sm < 1) return fail(P2S_ERR_ORDER, "plan: moment kernel does not fit");
     L.mom_grid = (int)std::max<int64_t>(1, std::min<int64_t>(E, (int64_t)T.sm_count * per_sm));
 
-    // contraction launch shape: buffers sized for the largest unit, one thread per
-    // stage-3 combination of the largest unit (rounded to whole warps)
-    int max_combos = 1;
-    for (int64_t e = 0; e < E; ++e) {
-        const ElemDesc& d = desc[e];
-        for (int gi = 0; gi < nc; ++gi)
-            for (int gj = 0; gj < nc; ++gj) {
-                int m1n, n1n;
-                slab_sizes(d, gi, gj, m1n, n1n, 0, tile);
-                ContractShape sh = contract_shape(d.ord[gi], d.ord[gj], m1n, n1n);
-                L.a_cap = std::max(L.a_cap, sh.a);
-                L.b_cap = std::max(L.b_cap, sh.b);
-                L.tile_cap = std::max(L.tile_cap, sh.tile);
-                max_combos = std::max(max_combos, sh.combos);
-            }
-    }
-    L.tile = tile;
-    L.con_threads = tile.threads ? tile.threads : std::min(512, std::max(64, (max_combos + 31) / 32 * 32));
-    L.combo_cap = (size_t)max_combos;
-    L.tile_off = contract_tile_offset(L.precision, L.a_cap, L.b_cap);
-    L.con_smem = contract_smem_bytes(L.precision, L.a_cap, L.b_cap, L.tile_cap, L.combo_cap);
-    if (!spec_n) {
-        if (L.con_smem > limit) return fail(P2S_ERR_ORDER, "plan: contraction tile too large");
-        int con_per_sm = contract_blocks_per_sm(L.precision, L.con_threads, L.con_smem);
-        if (con_per_sm < 1) return fail(P2S_ERR_ORDER, "plan: contraction kernel does not fit");
-        L.con_grid = T.sm_count * con_per_sm;
-    }
+    // contraction launch shape of the general kernel (the specialised one replaces it below)
+    if (moments_only) return P2S_OK;
+    rc = general_contract_shape(T, E, desc, nc, tile, !spec_n, limit, L);
+    if (rc) return rc;
 
     if (spec_n) {
         int m1n, n1n;
@@ -390,7 +413,7 @@ int run_moments(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_d
 
 int run_contract(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_desc, const ContractUnit* d_units,
                  unsigned long long* d_counter, const void* moments, double* out, cudaStream_t s,
-                 const int8_t* elem_mask) {
+                 const int8_t* elem_mask, const OpArrays* op) {
     if (elem_mask && (PL.precision != P2S_FP64 || PL.spec_n))
         return fail(P2S_ERR_ARG, "contract: element masks need an FP64 plan");
     if (PL.n_units == 0) return P2S_OK;
@@ -412,6 +435,10 @@ int run_contract(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_
     C.combo_off = (int)contract_combo_offset(PL.precision, PL.a_cap, PL.b_cap, PL.tile_cap);
     C.combo_cap = (int)PL.combo_cap;
     C.elem_mask = elem_mask;
+    C.op_terms = op ? op->terms : nullptr;
+    C.op_scales = op ? op->scales : nullptr;
+    C.op_block = op ? op->block : nullptr;
+    C.op_nalpha = op ? op->nalpha : 0;
     if (PL.spec_n)
         P2S_CUDA(launch_contract_ffn(PL.spec_n, C, PL.con_grid, PL.con_threads, PL.con_smem, s));
     else
@@ -556,6 +583,10 @@ void p2s_plan_destroy(p2s_plan* p) {
     cudaFree(p->d_units);
     cudaFree(p->d_counter);
     cudaFree(p->d_order);
+    if (p->d_mdesc && p->d_mdesc != p->d_desc) cudaFree(p->d_mdesc);
+    cudaFree(p->d_op_terms);
+    cudaFree(p->d_op_scales);
+    cudaFree(p->d_op_block);
     cudaFree(p->d_mom);
     delete p;
 }
@@ -616,25 +647,29 @@ int p2s_plan_create_tuned(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, con
             return fail(P2S_ERR_CUDA, "p2s_plan_create: element order", ce);
         }
     }
+    p->Lm = p->L;
+    p->d_mdesc = p->d_desc;
     *out = p;
     return P2S_OK;
 }
 
 int64_t p2s_plan_output_entries(const p2s_plan* p) { return p ? p->L.out_entries : P2S_ERR_ARG; }
-int64_t p2s_plan_moment_entries(const p2s_plan* p) { return p ? p->L.mom_entries : P2S_ERR_ARG; }
+int64_t p2s_plan_moment_entries(const p2s_plan* p) { return p ? p->Lm.mom_entries : P2S_ERR_ARG; }
 
 int p2s_plan_moments(p2s_plan* p, const p2s_geometry* geom, const p2s_material* mat, double* moments,
                      int32_t* elem_status, void* stream) {
     if (!p) return fail(P2S_ERR_ARG, "p2s_plan_moments: NULL plan");
     if (set_device(p->ctx->T.device)) return P2S_ERR_CUDA;
-    return run_moments(p->ctx->T, p->L, p->d_desc, geom, mat, moments, elem_status, (cudaStream_t)stream,
+    return run_moments(p->ctx->T, p->Lm, p->d_mdesc, geom, mat, moments, elem_status, (cudaStream_t)stream,
                        p->d_counter + 1, nullptr, p->d_order);
 }
 
 int p2s_plan_contract(p2s_plan* p, const double* moments, double* out, void* stream) {
     if (!p) return fail(P2S_ERR_ARG, "p2s_plan_contract: NULL plan");
     if (set_device(p->ctx->T.device)) return P2S_ERR_CUDA;
-    return run_contract(p->ctx->T, p->L, p->d_desc, p->d_units, p->d_counter, moments, out, (cudaStream_t)stream);
+    OpArrays op{p->d_op_terms, p->d_op_scales, p->d_op_block, p->op_nalpha};
+    return run_contract(p->ctx->T, p->L, p->d_desc, p->d_units, p->d_counter, moments, out, (cudaStream_t)stream,
+                        nullptr, p->L.op ? &op : nullptr);
 }
 
 int p2s_plan_tile_config(const p2s_plan* p, p2s_tile_config* out) {
@@ -659,9 +694,12 @@ static int plan_capture(p2s_plan* p, const p2s_geometry* geom, const p2s_materia
                         int32_t* elem_status) {
     cudaStream_t cs = p->cap_stream;
     P2S_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    int rc = run_moments(p->ctx->T, p->L, p->d_desc, geom, mat, p->d_mom, elem_status, cs, p->d_counter + 1, nullptr,
+    int rc = run_moments(p->ctx->T, p->Lm, p->d_mdesc, geom, mat, p->d_mom, elem_status, cs, p->d_counter + 1, nullptr,
                          p->d_order);
-    if (rc == P2S_OK) rc = run_contract(p->ctx->T, p->L, p->d_desc, p->d_units, p->d_counter, p->d_mom, out, cs);
+    OpArrays op{p->d_op_terms, p->d_op_scales, p->d_op_block, p->op_nalpha};
+    if (rc == P2S_OK)
+        rc = run_contract(p->ctx->T, p->L, p->d_desc, p->d_units, p->d_counter, p->d_mom, out, cs, nullptr,
+                          p->L.op ? &op : nullptr);
     cudaGraph_t g = nullptr;
     cudaError_t ce = cudaStreamEndCapture(cs, &g);
     if (rc) {
@@ -732,6 +770,172 @@ int p2s_fill_elements(p2s_ctx* ctx, const p2s_geometry* geom, const p2s_material
     return rc;
 }
 
+int p2s_operator_plan_create(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, const p2s_quadrature* quad,
+                             int precision, int kind, const p2s_term* terms, int n_terms,
+                             const p2s_tile_config* tile, p2s_plan** out) {
+    if (!ctx || !out || !orders || !quad || (n_terms > 0 && !terms)) return fail(P2S_ERR_ARG, "p2s_operator_plan_create: NULL argument");
+    *out = nullptr;
+    if (E < 0 || n_terms < 1 || n_terms > 4096) return fail(P2S_ERR_ARG, "p2s_operator_plan_create: n_elem < 0 or n_terms outside 1..4096");
+    const int nc = orders->n_comp;
+    if (nc < 1 || nc > 3 || (E > 0 && !orders->orders)) return fail(P2S_ERR_ARG, "p2s_operator_plan_create: 1..3 field components");
+    for (int64_t i = 0; i < E * 3 * nc; ++i)
+        if (orders->orders[i] < 1 || orders->orders[i] > kMaxOrder) return fail(P2S_ERR_ORDER, "orders: value outside 1..12");
+    if (kind != P2S_ALPHA_SCALAR && kind != P2S_ALPHA_METRIC_EPS) return fail(P2S_ERR_ARG, "p2s_operator_plan_create: bad kind");
+    if (precision != P2S_FP64 && precision != P2S_MIXED) return fail(P2S_ERR_ARG, "p2s_operator_plan_create: bad precision");
+    const int na = kind == P2S_ALPHA_METRIC_EPS ? 3 : 1;
+    for (int k = 0; k < n_terms; ++k) {
+        const p2s_term& tm = terms[k];
+        bool ok = tm.gi >= 0 && tm.gi < nc && tm.gj >= 0 && tm.gj < nc && tm.sa >= 0 && tm.sa < na && tm.sb >= 0 &&
+                  tm.sb < na && std::isfinite(tm.scale);
+        for (int x = 0; x < 3; ++x) ok = ok && (tm.d_test[x] == 0 || tm.d_test[x] == 1) && (tm.d_trial[x] == 0 || tm.d_trial[x] == 1);
+        if (!ok) return fail(P2S_ERR_ARG, "p2s_operator_plan_create: term out of range");
+    }
+    TileParams tp;
+    int rc = tile_params_from(tile, tp);
+    if (rc) return rc;
+    if (set_device(ctx->T.device)) return P2S_ERR_CUDA;
+
+    // moments: a virtual element whose na components all have the field's largest order per
+    // axis, so every coupling entry (sa, sb) is a moment pair with K = 2 N_max - 1 per axis
+    const int nv = na;
+    std::vector<int32_t> vord((size_t)std::max<int64_t>(E, 1) * 3 * nv);
+    for (int64_t e = 0; e < E; ++e)
+        for (int x = 0; x < 3; ++x) {
+            int mx = 1;
+            for (int g = 0; g < nc; ++g) mx = std::max(mx, (int)orders->orders[(e * nc + g) * 3 + x]);
+            for (int g = 0; g < nv; ++g) vord[(e * nv + g) * 3 + x] = mx;
+        }
+    p2s_orders vo = {nv, vord.data()};
+    p2s_fill_opts fo = {precision, 1u};
+    std::vector<ElemDesc> mdesc((size_t)std::max<int64_t>(E, 1));
+    UnitSink count_only;
+    PlanLayout Lm;
+    rc = build_layout(ctx->T, E, &vo, quad, &fo, mdesc.data(), count_only, Lm, tp, true);
+    if (rc) return rc;
+
+    // contraction: the field's own components and orders, one n x n matrix per element
+    std::vector<ElemDesc> cdesc(mdesc);
+    int64_t out_off = 0;
+    for (int64_t e = 0; e < E; ++e) {
+        ElemDesc& d = cdesc[e];
+        d.n_comp = (int8_t)nc;
+        d.n_types = 1;
+        int dof = 0;
+        for (int g = 0; g < 3; ++g)
+            for (int x = 0; x < 3; ++x) d.ord[g][x] = g < nc ? (int8_t)orders->orders[(e * nc + g) * 3 + x] : 0;
+        for (int g = 0; g < nc; ++g) {
+            d.dof_off[g] = dof;
+            dof += d.ord[g][0] * d.ord[g][1] * d.ord[g][2];
+        }
+        d.n = dof;
+        d.out_off = out_off;
+        out_off += (int64_t)dof * dof;
+    }
+    // terms grouped by block; a list closed under (gi,gj,sa,sb,d,e,scale) -> (gj,gi,sb,sa,e,d,scale)
+    // gives M = M^T (alpha is symmetric), so only blocks gi <= gj are computed and the others
+    // written as their transposes
+    auto packed = [](const p2s_term& tm) {
+        const int tu = tm.d_test[0] + 2 * tm.d_trial[0], tv = tm.d_test[1] + 2 * tm.d_trial[1],
+                  tw = tm.d_test[2] + 2 * tm.d_trial[2];
+        return (int32_t)(tm.sa | (tm.sb << 4) | (tu << 8) | (tv << 12) | (tw << 16));
+    };
+    std::vector<int32_t> h_terms;
+    std::vector<double> h_scales;
+    std::vector<int32_t> h_block(18, 0);
+    for (int gi = 0; gi < 3; ++gi)
+        for (int gj = 0; gj < 3; ++gj) {
+            h_block[2 * (3 * gi + gj)] = (int32_t)h_terms.size();
+            for (int k = 0; k < n_terms; ++k)
+                if (terms[k].gi == gi && terms[k].gj == gj) {
+                    h_terms.push_back(packed(terms[k]));
+                    h_scales.push_back(terms[k].scale);
+                }
+            h_block[2 * (3 * gi + gj) + 1] = (int32_t)h_terms.size() - h_block[2 * (3 * gi + gj)];
+        }
+    std::vector<bool> used((size_t)n_terms, false);
+    bool symmetric = true;
+    for (int k = 0; k < n_terms && symmetric; ++k) {
+        const p2s_term& a = terms[k];
+        bool found = false;
+        for (int j = 0; j < n_terms && !found; ++j) {
+            const p2s_term& b = terms[j];
+            if (used[j]) continue;
+            const bool alpha_match = (a.sa == b.sb && a.sb == b.sa) || (a.sa == b.sa && a.sb == b.sb && a.sa == a.sb);
+            bool m = b.gi == a.gj && b.gj == a.gi && alpha_match && b.scale == a.scale;
+            for (int x = 0; x < 3; ++x) m = m && b.d_test[x] == a.d_trial[x] && b.d_trial[x] == a.d_test[x];
+            if (m) {
+                used[j] = true;
+                found = true;
+            }
+        }
+        symmetric = found;
+    }
+    std::vector<ContractUnit> units;
+    UnitSink sink;
+    sink.vec = &units;
+    for (int64_t e = 0; e < E; ++e)
+        for (int gi = 0; gi < nc; ++gi)
+            for (int gj = symmetric ? gi : 0; gj < nc; ++gj)
+                push_block(cdesc[e], (int32_t)e, gi, gj, 0, (symmetric && gi != gj) ? 0 : -1, sink, 0, tp);
+    PlanLayout L = Lm;  // moment fields for reference; the contraction fields are set below
+    L.n_comp = nc;
+    L.types_mask = 1u;
+    L.out_entries = out_off;
+    L.n_units = (int64_t)units.size();
+    L.spec_n = 0;
+    L.op = 1;
+    L.a_cap = L.b_cap = L.tile_cap = L.combo_cap = 1;
+    const size_t limit = std::min<size_t>(ctx->T.smem_optin, 227 * 1024) - 1024;
+    rc = general_contract_shape(ctx->T, E, cdesc.data(), nc, tp, true, limit, L);
+    if (rc) return rc;
+
+    p2s_plan* p = new (std::nothrow) p2s_plan();
+    if (!p) return fail(P2S_ERR_OOM, "p2s_operator_plan_create: host allocation");
+    p->ctx = ctx;
+    p->L = L;
+    p->Lm = Lm;
+    p->op_nalpha = na;
+    const size_t nd = cdesc.size();
+    bool ok = cudaMalloc(&p->d_desc, sizeof(ElemDesc) * nd) == cudaSuccess &&
+              cudaMalloc(&p->d_mdesc, sizeof(ElemDesc) * nd) == cudaSuccess &&
+              cudaMalloc(&p->d_units, sizeof(ContractUnit) * std::max<size_t>(1, units.size())) == cudaSuccess &&
+              cudaMalloc(&p->d_counter, 2 * sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMalloc(&p->d_mom, sizeof(double) * std::max<int64_t>(1, Lm.mom_entries)) == cudaSuccess &&
+              cudaMalloc(&p->d_op_terms, sizeof(int32_t) * h_terms.size()) == cudaSuccess &&
+              cudaMalloc(&p->d_op_scales, sizeof(double) * h_scales.size()) == cudaSuccess &&
+              cudaMalloc(&p->d_op_block, sizeof(int32_t) * h_block.size()) == cudaSuccess;
+    if (!ok) {
+        p2s_plan_destroy(p);
+        return fail(P2S_ERR_OOM, "p2s_operator_plan_create: device allocation");
+    }
+    cudaError_t ce = cudaMemcpy(p->d_desc, cdesc.data(), sizeof(ElemDesc) * nd, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(p->d_mdesc, mdesc.data(), sizeof(ElemDesc) * nd, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess && units.size())
+        ce = cudaMemcpy(p->d_units, units.data(), sizeof(ContractUnit) * units.size(), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(p->d_op_terms, h_terms.data(), sizeof(int32_t) * h_terms.size(), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(p->d_op_scales, h_scales.data(), sizeof(double) * h_scales.size(), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(p->d_op_block, h_block.data(), sizeof(int32_t) * h_block.size(), cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) {
+        p2s_plan_destroy(p);
+        return fail(P2S_ERR_CUDA, "p2s_operator_plan_create: upload", ce);
+    }
+    bool mixed_g = false;
+    for (int64_t e = 1; e < E && !mixed_g; ++e) mixed_g = mdesc[e].G != mdesc[0].G;
+    if (mixed_g) {  // the moment queue grouped by G, largest first (as for ordinary plans)
+        std::vector<int32_t> ord((size_t)E);
+        for (int64_t e = 0; e < E; ++e) ord[e] = (int32_t)e;
+        std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return mdesc[a].G > mdesc[b].G; });
+        int32_t* d_ord = plan_order(p);
+        ce = d_ord ? cudaMemcpy(d_ord, ord.data(), sizeof(int32_t) * E, cudaMemcpyHostToDevice) : cudaErrorMemoryAllocation;
+        if (ce != cudaSuccess) {
+            p2s_plan_destroy(p);
+            return fail(P2S_ERR_CUDA, "p2s_operator_plan_create: element order", ce);
+        }
+    }
+    *out = p;
+    return P2S_OK;
+}
+
 int p2s_sync_status(p2s_ctx* ctx, void* stream) {
     if (!ctx) return fail(P2S_ERR_ARG, "p2s_sync_status: NULL context");
     if (set_device(ctx->T.device)) return P2S_ERR_CUDA;
@@ -759,7 +963,7 @@ int32_t* plan_order(p2s_plan* p) {
 int plan_fill_masked(p2s_plan* p, const p2s_geometry* geom, const p2s_material* mat, double* out,
                      const int8_t* mask, cudaStream_t s) {
     if (!p) return fail(P2S_ERR_ARG, "plan_fill_masked: NULL plan");
-    int rc = run_moments(p->ctx->T, p->L, p->d_desc, geom, mat, p->d_mom, nullptr, s, p->d_counter + 1, mask,
+    int rc = run_moments(p->ctx->T, p->Lm, p->d_mdesc, geom, mat, p->d_mom, nullptr, s, p->d_counter + 1, mask,
                          p->d_order);
     if (rc) return rc;
     return run_contract(p->ctx->T, p->L, p->d_desc, p->d_units, p->d_counter, p->d_mom, out, s, mask);

@@ -72,21 +72,7 @@ __global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
         const int nj = Nu_j * Nv_j * Nw_j;
         const int mjp = contract_mj_stride(Nu_j * Nv_j);
         const int ld = contract_tile_ld(Nu_j * Nv_j, Nw_j);  // padded tile row stride (doubles)
-        const size_t moff = d->mom_off + d->pair_off[pair_index(gi, gj, d->n_comp)];
-
-        // the unit's stage-3 coefficient runs, shared by every thread, and the tile offset of
-        // every output column (m2, n2, p2)
         const float rNwj = 1.f / (float)Nw_j, rNwm = 1.f / (float)Nwm;
-        if (tid < Nw_i * Nw_j) {
-            const int p1 = div_small(tid, Nw_j, rNwj);
-            s_lin[tid] = __ldg(lidx + lin_slot(t, p1, tid - p1 * Nw_j));
-        }
-        for (int i = tid; i < Nw_i * Nw_j * Nwm; i += nth) {  // the runs' coefficient values
-            const int pp = div_small(i, Nwm, rNwm), r = i - pp * Nwm;
-            const int p1 = div_small(pp, Nw_j, rNwj);
-            const int32_t li = __ldg(lidx + lin_slot(t, p1, pp - p1 * Nw_j));
-            if (r < lin_cnt(li)) s_coef[i] = A::load_coef(lcoef, lin_off(li) + r);
-        }
         for (int c = tid; c < nj; c += nth) {
             const int mj = div_small(c, Nw_j, rNwj);
             s_col[c] = (int16_t)((c - mj * Nw_j) * mjp + mj);
@@ -102,65 +88,109 @@ __global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
                 const int im1 = div_small(mn, n1n, rn1n), in1 = mn - im1 * n1n;
                 const int m2 = div_small(mj, Nv_j, rNvj), n2 = mj - m2 * Nv_j;
                 s_cmb[c] = (uint32_t)im1 | ((uint32_t)in1 << 8) | ((uint32_t)m2 << 16) | ((uint32_t)n2 << 24);
-                s_cli[c] = __ldg(lidx + lin_slot(t, n1a + in1, n2));
             }
         }
+        // The terms summed into this block: the single uniform type t, or the operator's list
+        // (per-axis types, coupling entry, scale); each term is stages 1-3 with its own runs,
+        // stage 3 adding its share to the staged tile.
+        const bool op = L.op_terms != nullptr;
+        const int bslot = 2 * (3 * gi + gj);
+        const int term0 = op ? L.op_block[bslot] : 0, n_terms = op ? L.op_block[bslot + 1] : 1;
+        const int Kvm = op ? d->kax[1] : Kv, Kwm = op ? d->kax[2] : Kw;  // moment tensor extents
+        const int KvKwm = Kvm * Kwm;
+        for (int kt = 0; kt < n_terms; ++kt) {
+            int tu = t, tv = t, tw = t, sp = pair_index(gi, gj, d->n_comp);
+            double scale = 1.0;
+            if (op) {
+                const int32_t pk = __ldg(L.op_terms + term0 + kt);
+                const int sa = pk & 15, sb = (pk >> 4) & 15;
+                tu = (pk >> 8) & 15;
+                tv = (pk >> 12) & 15;
+                tw = (pk >> 16) & 15;
+                sp = pair_index(sa, sb, L.op_nalpha);
+                scale = __ldg(L.op_scales + term0 + kt);
+            }
+            const size_t moff = d->mom_off + d->pair_off[sp];
+            // the term's stage-3 coefficient runs (type tw) and stage-2 runs per combination (tv)
+            if (tid < Nw_i * Nw_j) {
+                const int p1 = div_small(tid, Nw_j, rNwj);
+                s_lin[tid] = __ldg(lidx + lin_slot(tw, p1, tid - p1 * Nw_j));
+            }
+            for (int i = tid; i < Nw_i * Nw_j * Nwm; i += nth) {  // the runs' coefficient values
+                const int pp = div_small(i, Nwm, rNwm), r = i - pp * Nwm;
+                const int p1 = div_small(pp, Nw_j, rNwj);
+                const int32_t li = __ldg(lidx + lin_slot(tw, p1, pp - p1 * Nw_j));
+                if (r < lin_cnt(li)) s_coef[i] = A::load_coef(lcoef, lin_off(li) + r);
+            }
+            for (int c = tid; c < ncombo; c += nth) {
+                const uint32_t w = s_cmb[c];
+                s_cli[c] = __ldg(lidx + lin_slot(tv, n1a + (int)((w >> 8) & 0xffu), (int)(w >> 24)));
+            }
 
-        // stage 1: A[m1][m2][l][q], m1 in the slab
-        const int KvKw = Kv * Kw;
-        const int nA = m1n * Nu_j * KvKw;
-        const float rKvKw = 1.f / (float)KvKw, rNuj = 1.f / (float)Nu_j;
-        for (int idx = tid; idx < nA; idx += nth) {
-            const int mm = div_small(idx, KvKw, rKvKw), lq = idx - mm * KvKw;
-            const int im1 = div_small(mm, Nu_j, rNuj), m2 = mm - im1 * Nu_j;
-            const int32_t li = __ldg(lidx + lin_slot(t, m1a + im1, m2));
-            const int k0 = lin_kmin(li), cnt = lin_cnt(li), off = lin_off(li);
-            const size_t mb = moff + (size_t)k0 * KvKw + lq;
-            T acc = cnt > 0 ? A::mul(A::load_coef(lcoef, off), A::load_moment(L.mom, mb)) : A::zero();
-            for (int r = 1; r < cnt; ++r)
-                A::fma_acc(acc, A::load_coef(lcoef, off + r), A::load_moment(L.mom, mb + (size_t)(2 * r) * KvKw));
-            sA[idx] = A::finish(acc);
-        }
-        __syncthreads();
-        // stage 2: Bt[m1][n1][m2][n2][q], (m1, n1) in the slab
-        const int nB = ncombo * Kw;
-        const float rKw = 1.f / (float)Kw;
-        for (int idx = tid; idx < nB; idx += nth) {
-            const int c = div_small(idx, Kw, rKw), q = idx - c * Kw;
-            const uint32_t w = s_cmb[c];
-            const int im1 = w & 0xffu, m2 = (w >> 16) & 0xffu;
-            const int32_t li = s_cli[c];
-            const int l0 = lin_kmin(li), cnt = lin_cnt(li), off = lin_off(li);
-            const T* a = sA + ((im1 * Nu_j + m2) * Kv + l0) * Kw + q;
-            T acc = cnt > 0 ? A::mul(A::load_coef(lcoef, off), a[0]) : A::zero();
-            for (int r = 1; r < cnt; ++r) A::fma_acc(acc, A::load_coef(lcoef, off + r), a[2 * r * Kw]);
-            sB[c * Kwp + q] = A::finish(acc);
-        }
-        __syncthreads();
-        // stage 3: items (p1, combination (m1, n1, m2, n2)); each walks p2
-        const float rncombo = 1.f / (float)ncombo;
-        for (int it = tid; it < ncombo * Nw_i; it += nth) {
-            const int p1 = div_small(it, ncombo, rncombo), c = it - p1 * ncombo;
-            const uint32_t w = s_cmb[c];
-            const int mn = (int)(w & 0xffu) * n1n + (int)((w >> 8) & 0xffu);       // im1 * n1n + in1
-            const int mj = (int)((w >> 16) & 0xffu) * Nv_j + (int)(w >> 24);      // m2 * Nv_j + n2
-            const T* bt = sB + (size_t)c * Kwp;
-            double* trow = tile + (size_t)(mn * Nw_i + p1) * ld + mj;
-            const int32_t* lrow = s_lin + p1 * Nw_j;
-            const typename A::C* crow = s_coef + p1 * Nw_j * Nwm;
-            for (int p2 = 0; p2 < Nw_j; ++p2) {
-                const int32_t li = lrow[p2];
-                const int q0 = lin_kmin(li), cnt = lin_cnt(li);
-                const typename A::C* cf = crow + p2 * Nwm;
-                T acc = cnt > 0 ? A::mul(cf[0], bt[q0]) : A::zero();
-                for (int r = 1; r < cnt; ++r) A::fma_acc(acc, cf[r], bt[q0 + 2 * r]);
-                trow[p2 * mjp] = A::to_double_fast(A::finish(acc));
+            // stage 1: A[m1][m2][l][q], m1 in the slab
+            const int KvKw = Kv * Kw;
+            const int nA = m1n * Nu_j * KvKw;
+            const float rKvKw = 1.f / (float)KvKw, rNuj = 1.f / (float)Nu_j, rKw1 = 1.f / (float)Kw;
+            for (int idx = tid; idx < nA; idx += nth) {
+                const int mm = div_small(idx, KvKw, rKvKw), lq = idx - mm * KvKw;
+                const int im1 = div_small(mm, Nu_j, rNuj), m2 = mm - im1 * Nu_j;
+                const int l = div_small(lq, Kw, rKw1), q = lq - l * Kw;
+                const int32_t li = __ldg(lidx + lin_slot(tu, m1a + im1, m2));
+                const int k0 = lin_kmin(li), cnt = lin_cnt(li), off = lin_off(li);
+                const size_t mb = moff + (size_t)k0 * KvKwm + (size_t)l * Kwm + q;
+                T acc = cnt > 0 ? A::mul(A::load_coef(lcoef, off), A::load_moment(L.mom, mb)) : A::zero();
+                for (int r = 1; r < cnt; ++r)
+                    A::fma_acc(acc, A::load_coef(lcoef, off + r), A::load_moment(L.mom, mb + (size_t)(2 * r) * KvKwm));
+                sA[idx] = A::finish(acc);
             }
+            __syncthreads();
+            // stage 2: Bt[m1][n1][m2][n2][q], (m1, n1) in the slab
+            const int nB = ncombo * Kw;
+            const float rKw = 1.f / (float)Kw;
+            for (int idx = tid; idx < nB; idx += nth) {
+                const int c = div_small(idx, Kw, rKw), q = idx - c * Kw;
+                const uint32_t w = s_cmb[c];
+                const int im1 = w & 0xffu, m2 = (w >> 16) & 0xffu;
+                const int32_t li = s_cli[c];
+                const int l0 = lin_kmin(li), cnt = lin_cnt(li), off = lin_off(li);
+                const T* a = sA + ((im1 * Nu_j + m2) * Kv + l0) * Kw + q;
+                T acc = cnt > 0 ? A::mul(A::load_coef(lcoef, off), a[0]) : A::zero();
+                for (int r = 1; r < cnt; ++r) A::fma_acc(acc, A::load_coef(lcoef, off + r), a[2 * r * Kw]);
+                sB[c * Kwp + q] = A::finish(acc);
+            }
+            __syncthreads();
+            // stage 3: items (p1, combination (m1, n1, m2, n2)); each walks p2
+            const float rncombo = 1.f / (float)ncombo;
+            for (int it = tid; it < ncombo * Nw_i; it += nth) {
+                const int p1 = div_small(it, ncombo, rncombo), c = it - p1 * ncombo;
+                const uint32_t w = s_cmb[c];
+                const int mn = (int)(w & 0xffu) * n1n + (int)((w >> 8) & 0xffu);       // im1 * n1n + in1
+                const int mj = (int)((w >> 16) & 0xffu) * Nv_j + (int)(w >> 24);      // m2 * Nv_j + n2
+                const T* bt = sB + (size_t)c * Kwp;
+                double* trow = tile + (size_t)(mn * Nw_i + p1) * ld + mj;
+                const int32_t* lrow = s_lin + p1 * Nw_j;
+                const typename A::C* crow = s_coef + p1 * Nw_j * Nwm;
+                for (int p2 = 0; p2 < Nw_j; ++p2) {
+                    const int32_t li = lrow[p2];
+                    const int q0 = lin_kmin(li), cnt = lin_cnt(li);
+                    const typename A::C* cf = crow + p2 * Nwm;
+                    T acc = cnt > 0 ? A::mul(cf[0], bt[q0]) : A::zero();
+                    for (int r = 1; r < cnt; ++r) A::fma_acc(acc, cf[r], bt[q0 + 2 * r]);
+                    const double v = A::to_double_fast(A::finish(acc));
+                    if (!op) trow[p2 * mjp] = v;
+                    else if (kt == 0) trow[p2 * mjp] = scale * v;
+                    else trow[p2 * mjp] = fma(scale, v, trow[p2 * mjp]);
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
         // The slabs the host builds are either full in n1 or a single m1, so the tile's rows
         // (m1, n1, p1) are consecutive dofs: rows [rbase, rbase + rows) of block (gi, gj).
         const int rows = m1n * n1n * Nw_i;
+        if (n_terms == 0) {  // an operator block without terms is zero
+            for (int i = tid; i < rows * ld; i += nth) tile[i] = 0.0;
+            __syncthreads();
+        }
         const int rbase = d->dof_off[gi] + (m1a * Nv_i + n1a) * Nw_i;
         const int col0 = d->dof_off[gj];
         const int warp = tid >> 5, lane = tid & 31, nwarp = nth >> 5;

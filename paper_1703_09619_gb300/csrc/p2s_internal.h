@@ -110,6 +110,14 @@ struct ContractLaunch {
     int combo_off;         // general kernel: byte offset of the per-unit combination tables
     int combo_cap;         // entries of each combination table
     const int8_t* elem_mask;  // optional: units of elements with mask 0 are skipped (generic kernel)
+    // operator mode (general kernel; op_terms == nullptr: the four uniform types): the terms of
+    // block (gi, gj) are op_terms[op_block[2 (3 gi + gj)] + k], k < op_block[2 (3 gi + gj) + 1],
+    // each packed as sa | sb << 4 | tu << 8 | tv << 12 | tw << 16 (per-axis product types),
+    // with op_scales alongside; the moments of every pair then have kax[] entries per axis.
+    const int32_t* op_terms;
+    const double* op_scales;
+    const int32_t* op_block;
+    int op_nalpha;            // 3 (metric kind) or 1
 };
 struct ContractShape {
     size_t a, b, tile;
@@ -190,6 +198,7 @@ struct PlanLayout {
     size_t con_smem = 0, tile_off = 0;
     int con_grid = 1;
     int spec_n = 0;  // > 0: the mixed contraction specialised for uniform order N
+    int op = 0;      // 1: an operator plan (term list), one n x n matrix per element
     TileParams tile;  // the tile configuration in effect
 };
 
@@ -216,16 +225,23 @@ int tile_params_from(const p2s_tile_config* c, TileParams& tp);
 // The first call with units.buf == nullptr && units.vec == nullptr only counts units.
 int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, const p2s_quadrature* quad,
                  const p2s_fill_opts* opts, ElemDesc* desc, UnitSink& units, PlanLayout& L,
-                 const TileParams& tile = TileParams());
+                 const TileParams& tile = TileParams(), bool moments_only = false);
 // `counter` (device, one word, optional): the moment kernel's element queue; with it CTAs take
 // elements dynamically, which balances batches of uneven per-element cost.
 // `order` (device [E], optional): the order in which the queue hands out elements.
 int run_moments(const DeviceTables& T, const PlanLayout& L, const ElemDesc* d_desc, const p2s_geometry* geom,
                 const p2s_material* mat, void* moments, int32_t* elem_status, cudaStream_t s,
                 unsigned long long* counter, const int8_t* elem_mask = nullptr, const int32_t* order = nullptr);
+// Device arrays of an operator plan's term list (see ContractLaunch).
+struct OpArrays {
+    const int32_t* terms;
+    const double* scales;
+    const int32_t* block;
+    int nalpha;
+};
 int run_contract(const DeviceTables& T, const PlanLayout& L, const ElemDesc* d_desc, const ContractUnit* d_units,
                  unsigned long long* d_counter, const void* moments, double* out, cudaStream_t s,
-                 const int8_t* elem_mask = nullptr);
+                 const int8_t* elem_mask = nullptr, const OpArrays* op = nullptr);
 }  // namespace p2s
 struct p2s_ctx;
 struct p2s_plan;

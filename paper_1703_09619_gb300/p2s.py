@@ -54,6 +54,12 @@ class FillOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("types_mask", ctypes.c_uint32)]
 
 
+class Term(ctypes.Structure):
+    """p2s_term: one term of an operator (block, coupling entry, per-axis derivatives, scale)."""
+    _fields_ = [("gi", ctypes.c_int32), ("gj", ctypes.c_int32), ("sa", ctypes.c_int32), ("sb", ctypes.c_int32),
+                ("d_test", ctypes.c_int32 * 3), ("d_trial", ctypes.c_int32 * 3), ("scale", ctypes.c_double)]
+
+
 class TileConfig(ctypes.Structure):
     """p2s_tile_config: contraction work-unit shape (zero fields: library default)."""
     _fields_ = [("combo_target", ctypes.c_int), ("unit_kbytes", ctypes.c_int), ("threads", ctypes.c_int)]
@@ -78,6 +84,9 @@ SIGNATURES = {
     "p2s_plan_create_tuned": (ctypes.c_int, [_P, _I64, ctypes.POINTER(Orders), ctypes.POINTER(Quadrature),
                                              ctypes.POINTER(FillOpts), _P, ctypes.POINTER(ctypes.c_void_p)]),
     "p2s_plan_tile_config": (ctypes.c_int, [_P, ctypes.POINTER(TileConfig)]),
+    "p2s_operator_plan_create": (ctypes.c_int, [_P, _I64, ctypes.POINTER(Orders), ctypes.POINTER(Quadrature),
+                                                ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P,
+                                                ctypes.POINTER(ctypes.c_void_p)]),
     "p2s_autotune_tiles": (ctypes.c_int, [_P, ctypes.POINTER(Geometry), ctypes.POINTER(Material),
                                           ctypes.POINTER(Orders), ctypes.POINTER(Quadrature),
                                           ctypes.POINTER(FillOpts), _I64, ctypes.c_int, ctypes.POINTER(TileConfig),
@@ -335,6 +344,53 @@ def autotune_tiles(ctx: Context, orders, npts, kind, params, nodes, bulge, preci
                                   ctypes.byref(opts), int(sample), int(reps), ctypes.byref(best), ctypes.byref(ms),
                                   ctypes.byref(tried), _stream(stream)), "p2s_autotune_tiles")
     return best.as_dict(), ms.value, tried.value
+
+
+def terms_struct(terms, scales):
+    """A p2s_term array from rows (gi, gj, sa, sb, du, dv, dw, eu, ev, ew) and scales."""
+    terms = np.asarray(terms, dtype=np.int64).reshape(-1, 10)
+    scales = np.asarray(scales, dtype=np.float64).reshape(-1)
+    if terms.shape[0] != scales.shape[0]:
+        raise ValueError("terms and scales differ in length")
+    arr = (Term * max(1, terms.shape[0]))()
+    for k, (row, sc) in enumerate(zip(terms, scales)):
+        arr[k].gi, arr[k].gj, arr[k].sa, arr[k].sb = (int(x) for x in row[:4])
+        for x in range(3):
+            arr[k].d_test[x] = int(row[4 + x])
+            arr[k].d_trial[x] = int(row[7 + x])
+        arr[k].scale = float(sc)
+    return arr, terms.shape[0]
+
+
+class OperatorPlan(Plan):
+    """A p2s_plan of an operator given as a term list (p2s_operator_plan_create): one n x n
+    matrix per element, the sum of its terms.  terms: rows (gi, gj, sa, sb, du, dv, dw, eu, ev,
+    ew) -- block, coupling entry alpha[sa][sb], derivative orders of the test (d*) and trial
+    (e*) functions per axis; scales alongside."""
+
+    def __init__(self, ctx: Context, orders, npts, terms, scales, kind, precision=FP64, tile=None, graph=False):
+        lib = load()
+        self.ctx = ctx
+        o, self._orders = _orders_struct(orders)
+        E = self._orders.shape[0]
+        q, self._npts = _quadrature_struct(npts, E)
+        self._terms, nt = terms_struct(terms, scales)
+        t = None if tile is None else (tile if isinstance(tile, TileConfig) else TileConfig(**tile))
+        h = ctypes.c_void_p()
+        _check(lib.p2s_operator_plan_create(ctx.handle, E, ctypes.byref(o), ctypes.byref(q), int(precision), int(kind),
+                                            ctypes.cast(self._terms, ctypes.c_void_p), nt,
+                                            ctypes.byref(t) if t is not None else None, ctypes.byref(h)),
+               "p2s_operator_plan_create")
+        self.handle = h
+        self.n_elem = E
+        self.n_comp = int(self._orders.shape[1])
+        self.types_mask = 1
+        self.precision = precision
+        self.kind = kind
+        self.output_entries = int(lib.p2s_plan_output_entries(h))
+        self.moment_entries = int(lib.p2s_plan_moment_entries(h))
+        if graph:
+            self.use_graph(True)
 
 
 def fill_elements(ctx: Context, orders, npts, kind, params, nodes, bulge, out, elem_status=None,
