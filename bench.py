@@ -118,6 +118,32 @@ def contract_fma_count(orders, types_mask):
     return total
 
 
+def operator_fma_count(orders, terms, symmetric):
+    """Algorithmic FMAs of the operator contraction: for every element, block and term, the
+    three sparse stages with the term's per-axis product types (blocks gi <= gj only when the
+    term list is mirror-closed)."""
+    cnt = _runs()
+    total = 0
+    uniq, counts = np.unique(orders.reshape(orders.shape[0], -1), axis=0, return_counts=True)
+    nc = orders.shape[1]
+    for row, mult in zip(uniq, counts):
+        o = row.reshape(nc, 3)
+        s = 0
+        for tm in terms:
+            gi, gj = int(tm[0]), int(tm[1])
+            if symmetric and gi > gj:
+                continue
+            tu, tv, tw = (int(tm[4 + x]) + 2 * int(tm[7 + x]) for x in range(3))
+            Ni, Nj = o[gi], o[gj]
+            Kv, Kw = Ni[1] + Nj[1] - 1, Ni[2] + Nj[2] - 1
+            cu = cnt[tu, :Ni[0], :Nj[0]].sum()
+            cv = cnt[tv, :Ni[1], :Nj[1]].sum()
+            cw = cnt[tw, :Ni[2], :Nj[2]].sum()
+            s += cu * Kv * Kw + Ni[0] * Nj[0] * cv * Kw + Ni[0] * Ni[1] * Nj[0] * Nj[1] * cw
+        total += int(s) * int(mult)
+    return total
+
+
 def moment_mac_points(orders, npts, folded=False):
     """Sum-factorised moment MACs, quadrature points and pairs of a batch; with ``folded`` the
     first mode product runs over ceil(G/2) points per row (parity fold of the symmetric rule)."""
@@ -626,6 +652,94 @@ def run_fixed(args, wl):
         dist.destroy_process_group()
 
 
+def run_operator(args, wl):
+    """The diffusion stiffness sum_ab alpha_ab d_a phi_i d_b phi_j of one scalar field (the
+    workload's first component) as a term-list operator: one n x n matrix per element."""
+    import torch
+
+    from paper_1703_09619_gb300 import p2s
+
+    world, rank, local = dist_setup()
+    dev = torch.device("cuda", local)
+    ctx = p2s.Context(local)
+    prec = p2s.MIXED if args.precision == "mixed" else p2s.FP64
+    orders = np.ascontiguousarray(wl.orders[:, :1, :])
+    terms, scales = W.diffusion_terms()
+    npts = int(wl.npts[0]) if (wl.npts == wl.npts[0]).all() else wl.npts
+    params, nodes, bulge = p2s.device_inputs(wl, dev)
+    tile = None
+    if args.tile:
+        co, kb, th = (int(x) for x in args.tile.split(","))
+        tile = {"combo_target": co, "unit_kbytes": kb, "threads": th}
+    plan = p2s.OperatorPlan(ctx, orders, npts, terms, scales, wl.kind, prec, tile=tile, graph=True)
+    out = torch.empty(plan.output_entries, dtype=torch.float64, device=dev)
+    mom = torch.empty(max(plan.moment_entries, 1), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.fill(wl.kind, params, nodes, bulge, out, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+    if ctx.sync_status(stream) != 0:
+        raise RuntimeError("device status after warm-up")
+    barrier(world)
+    with ClockSampler(local) as clk:
+        ms = time_steps(step, args.steps, stream, flush)
+    barrier(world)
+    total_ms = max_over_ranks(float(sum(ms)), world, dev)
+    clocks = clk.summary()
+    m = time_steps(lambda: plan.moments(wl.kind, params, nodes, bulge, mom, stream=stream), 3, stream, flush)
+    c = time_steps(lambda: plan.contract(mom, out, stream=stream), 3, stream, flush)
+    mom_ms, con_ms = float(np.mean(m)), float(np.mean(c))
+    entries = plan.output_entries
+    job_entries = D.sum_over_ranks(entries, world, dev)
+    value = job_entries * args.steps / (total_ms * 1e-3)
+    fmas = operator_fma_count(orders, terms, symmetric=True)
+    if prec == p2s.FP64:
+        ach = 2 * fmas / (con_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_contract<ArithF64> (operator terms)", "achieved": ach,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                "algorithmic_flop_per_launch": 2 * fmas}
+    else:  # float-float MACs: bound by FP32 issue (12 lane operations per MAC, as the moment kernel)
+        ops = DW_MAC_OPS * fmas
+        ach = ops / (con_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_contract<ArithFF> (operator terms)", "achieved": ach,
+                "peak": FP32_PEAK_TOPS, "unit": "T FP32 lane-op/s", "frac": ach / FP32_PEAK_TOPS, "traffic": None,
+                "peak_source": "FP32 issue: 152 SMs x 128 lanes x 2.07 GHz (recipe unit counts and clock)",
+                "algorithmic_ops_per_launch": ops,
+                "op_model": "%d per float-float MAC x %d MACs of the three sparse stages" % (DW_MAC_OPS, fmas),
+                "hbm_write_GBs": 8 * entries / (con_ms * 1e-3) / 1e9}
+    line = None
+    if rank == 0:
+        cfg = workload_config(args, wl)
+        cfg.update({"operator": "diffusion stiffness of one scalar field, 9 terms alpha_ab d_a d_b (symmetric)",
+                    "orders": "uniform %d" % orders[0, 0, 0] if (orders == orders[0, 0, 0]).all() else "mixed",
+                    "n_comp": 1, "entries_per_step": entries, "precision": args.precision or "fp64",
+                    "launch": "one CUDA graph per step"})
+        line = {
+            "metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == p2s.FP64 else "f32x2",
+            "data": "synthetic", "config": cfg,
+            "elements_per_s": D.sum_over_ranks(wl.n_elem, world, dev) * args.steps / (total_ms * 1e-3),
+            "roofline": roof, "stages": {"moments_ms": mom_ms, "contract_ms": con_ms}, "clocks": clocks,
+            "gpu_launches": 2 * args.steps,
+        }
+    del out, mom
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def measure_e2e_fixed(args, wl, ctx, prec, dev, tile=None, graph=False):
     from paper_1703_09619_gb300 import p2s
     E = wl.n_elem
@@ -645,7 +759,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c5", choices=["c1", "c2", "c3", "c4", "c5"])
-    ap.add_argument("--mode", default=None, choices=["learned", "plain", "mixed"])
+    ap.add_argument("--mode", default=None, choices=["learned", "plain", "mixed", "operator"])
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"], help="alias of --mode plain|mixed")
     ap.add_argument("--elements", type=int, default=None, help="use only the first E elements")
     ap.add_argument("--npts", type=int, default=None, help="override the quadrature size G")
@@ -666,6 +780,10 @@ def main():
         if args.mode == "learned":
             wl = wl.with_npts(48)
         run_reference(args, wl)
+    elif args.mode == "operator":
+        if wl.kind != W.KIND_METRIC_EPS:
+            raise SystemExit("the operator mode takes the metric coupling of a curved workload (c2, c4, c5)")
+        run_operator(args, wl)
     elif args.mode == "learned":
         if wl.kind != W.KIND_METRIC_EPS:
             raise SystemExit("the learned mode needs a three-component metric workload (c2, c4, c5)")

@@ -12,6 +12,9 @@ struct ArithF64 {
     using C = double;
     __device__ static T zero() { return 0.0; }
     __device__ static T mul(C c, T x) { return c * x; }  // the first term of a sum
+    __device__ static T add(T a, T b) { return a + b; }
+    // a * s; the scale is given as FP64 s and as its (hi, lo) FP32 split sh, sl
+    __device__ static T scaled(T a, double s, float, float) { return a * s; }
     __device__ static void fma_acc(T& acc, C c, T x) { acc = fma(c, x, acc); }
     __device__ static T finish(T acc) { return acc; }
     __device__ static double to_double(T v) { return v; }
@@ -30,6 +33,25 @@ struct ArithFF {
     __device__ static T mul(C c, T x) {
         const float p = c.x * x.x;
         return make_float2(p, fmaf(c.y, x.x, fmaf(c.x, x.y, fmaf(c.x, x.x, -p))));
+    }
+    // a + b of two finished values: both leading words by TwoSum, the low words and the
+    // rounding error joined, renormalised (accurate double-word sum, Joldes, Muller and
+    // Popescu 2017)
+    __device__ static T add(T a, T b) {
+        const float s = a.x + b.x, bp = s - a.x, e = (a.x - (s - bp)) + (b.x - bp);
+        const float t = a.y + b.y, tp = t - a.y, f = (a.y - (t - tp)) + (b.y - tp);
+        float h = s + (e + t);
+        float l = (e + t) - (h - s);
+        const float h2 = h + (l + f);
+        l = (l + f) - (h2 - h);
+        return make_float2(h2, l);
+    }
+    // a * s with s an FP64 scale given by its (hi, lo) FP32 split sh, sl
+    __device__ static T scaled(T a, double, float sh, float sl) {
+        const float p = a.x * sh;
+        const float e = fmaf(a.y, sh, fmaf(a.x, sl, fmaf(a.x, sh, -p)));
+        const float h = p + e;
+        return make_float2(h, e - (h - p));
     }
     // acc += c * x, with the exact error of the leading product (FMA) and of the leading
     // sum (TwoSum); second-order terms go to the low word.

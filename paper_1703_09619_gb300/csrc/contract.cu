@@ -23,6 +23,8 @@
 //            errors and TwoSum accumulation; moments arrive as (hi, lo) pairs; the FP64
 //            output bits are assembled from (hi, lo) with integer operations, so the hot
 //            loop issues no FP64 instruction (FP64 runs at 1/58 of FP32 on this part).
+#include <type_traits>
+
 #include "arith.cuh"
 #include "p2s_internal.h"
 
@@ -34,6 +36,8 @@ __device__ __forceinline__ int type_slot(uint32_t mask, int t) { return __popc(m
 template <class A>
 __global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
     using T = typename A::T;
+    constexpr bool kFP64 = sizeof(T) == sizeof(double) && alignof(T) == alignof(double) &&
+                           !std::is_same<T, float2>::value;
     extern __shared__ __align__(16) unsigned char smraw[];
     T* sA = reinterpret_cast<T*>(smraw);
     T* sB = sA + L.a_cap;
@@ -111,6 +115,9 @@ __global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
                 scale = __ldg(L.op_scales + term0 + kt);
             }
             const size_t moff = d->mom_off + d->pair_off[sp];
+            // the scale, tested and split once per term (FP64 work runs on a narrow pipe)
+            const bool rescale = op && scale != 1.0;
+            const float scale_hi = (float)scale, scale_lo = (float)(scale - (double)scale_hi);
             // the term's stage-3 coefficient runs (type tw) and stage-2 runs per combination (tv)
             if (tid < Nw_i * Nw_j) {
                 const int p1 = div_small(tid, Nw_j, rNwj);
@@ -176,10 +183,17 @@ __global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
                     const typename A::C* cf = crow + p2 * Nwm;
                     T acc = cnt > 0 ? A::mul(cf[0], bt[q0]) : A::zero();
                     for (int r = 1; r < cnt; ++r) A::fma_acc(acc, cf[r], bt[q0 + 2 * r]);
-                    const double v = A::to_double_fast(A::finish(acc));
-                    if (!op) trow[p2 * mjp] = v;
-                    else if (kt == 0) trow[p2 * mjp] = scale * v;
-                    else trow[p2 * mjp] = fma(scale, v, trow[p2 * mjp]);
+                    if (!op) {
+                        trow[p2 * mjp] = A::to_double_fast(A::finish(acc));
+                    } else if constexpr (kFP64) {  // operator terms: FP64 sums in the tile
+                        const double v = A::finish(acc);
+                        trow[p2 * mjp] = kt == 0 ? scale * v : fma(scale, v, trow[p2 * mjp]);
+                    } else {  // float-float: the terms add in the tile, converted once at the end
+                        T* tr = reinterpret_cast<T*>(trow + p2 * mjp);
+                        T v = A::finish(acc);
+                        if (rescale) v = A::scaled(v, scale, scale_hi, scale_lo);
+                        *tr = kt == 0 ? v : A::add(*tr, v);
+                    }
                 }
             }
             __syncthreads();
@@ -189,6 +203,10 @@ __global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
         const int rows = m1n * n1n * Nw_i;
         if (n_terms == 0) {  // an operator block without terms is zero
             for (int i = tid; i < rows * ld; i += nth) tile[i] = 0.0;
+            __syncthreads();
+        } else if (op && !kFP64) {  // the summed terms to FP64, once per entry, in place
+            const T* tT = reinterpret_cast<const T*>(tile);
+            for (int i = tid; i < rows * ld; i += nth) tile[i] = A::to_double_fast(tT[i]);
             __syncthreads();
         }
         const int rbase = d->dof_off[gi] + (m1a * Nv_i + n1a) * Nw_i;
