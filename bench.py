@@ -189,7 +189,7 @@ class ClockSampler:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -297,7 +297,8 @@ def workload_config(args, wl):
     if args.mode == "learned":
         cfg.update({"npts": "learned per element, classes 8/12/16/24/32/48", "plain_npts": 48,
                     "precision": "mixed (float-float contraction, FP64 output)", "risk": RISK,
-                    "judge": "%.0f%% seeded, 48-point FP64, tol %.0e" % (100 * JUDGE_FRAC, JUDGE_TOL)})
+                    "judge": "%.0f%% seeded, re-filled at 48 points in the fill's precision (side stream), tol %.0e; "
+                             "failures replaced by the 48-point FP64 fill" % (100 * JUDGE_FRAC, JUDGE_TOL)})
     else:
         cfg.update({"npts": int(wl.npts[0]) if (wl.npts == wl.npts[0]).all() else "per-element",
                     "precision": args.mode})
