@@ -196,6 +196,49 @@ def make(name: str, n_elem: int | None = None, shard: int = 0) -> Workload:
     return w
 
 
+@dataclasses.dataclass
+class Mesh:
+    """A conforming structured mesh of curved hexahedra: element (i, j, k) (index
+    (k ny + j) nx + i) has the 8 lattice vertices around it, node index iu + 2 iv + 4 iw."""
+    nx: int
+    ny: int
+    nz: int
+    vertices: np.ndarray  # float64 [(nz+1)(ny+1)(nx+1), 3], vertex (i, j, k) at ((k (ny+1) + j)(nx+1) + i)
+    workload: Workload    # the elements (nodes from the shared vertices), one scalar field component
+
+
+def make_mesh(nx: int, ny: int, nz: int, order: int, npts: int, seed: int = 7, jitter: float = 0.15,
+              bulge_amp: float = 0.1, eps_amp: float = 0.5, kmag: float = 2.0) -> Mesh:
+    """Seeded conforming mesh: lattice vertices (i, j, k) moved by i.i.d. U(-jitter, jitter) per
+    coordinate (shared by the elements around them), a per-element bulge that vanishes on the
+    faces, one material eps = 1 + eps_amp sin(k . x) for the whole mesh (|k| = kmag); one scalar
+    field with `order` per axis and `npts` Gauss-Legendre points."""
+    rng = np.random.default_rng(SEED_BASE + 60 + SHARD_SEED_STRIDE * seed)
+    ii, jj, kk = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), np.arange(nz + 1), indexing="ij")
+    lattice = np.stack([ii, jj, kk], axis=-1).astype(np.float64)          # [nx+1][ny+1][nz+1][3]
+    verts = lattice.transpose(2, 1, 0, 3).reshape(-1, 3).copy()          # ((k (ny+1) + j)(nx+1) + i)
+    verts += rng.uniform(-jitter, jitter, size=verts.shape)
+    E = nx * ny * nz
+    nodes = np.zeros((E, 8, 3))
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                e = (k * ny + j) * nx + i
+                for nd in range(8):
+                    a, b, c = nd & 1, (nd >> 1) & 1, (nd >> 2) & 1
+                    nodes[e, nd] = verts[((k + c) * (ny + 1) + (j + b)) * (nx + 1) + (i + a)]
+    bulge = np.concatenate([np.full((E, 1), bulge_amp), unit_vectors(rng, E)], axis=1)
+    d = unit_vectors(rng, 1)[0]
+    params = np.zeros((E, 4))
+    params[:, 0] = eps_amp
+    params[:, 1:] = kmag * d
+    orders = np.full((E, 1, 3), order, dtype=np.int32)
+    w = Workload("mesh%dx%dx%d" % (nx, ny, nz), E, 1, orders, KIND_METRIC_EPS, params, nodes, bulge,
+                 np.full(E, npts, np.int32),
+                 description="%dx%dx%d conforming curved hexahedra, 1 scalar field, N=%d, G=%d" % (nx, ny, nz, order, npts))
+    return Mesh(nx, ny, nz, verts, w)
+
+
 def diffusion_terms(component: int = 0, scale: float = 1.0):
     """Term list of the diffusion stiffness sum_ab alpha_ab d_a(test) d_b(trial) on one
     field component, with alpha the metric coupling factor eps detJ J^-1 J^-T: nine
