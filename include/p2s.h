@@ -379,6 +379,53 @@ int p2s_learned_fill(p2s_learned_plan* plan, const p2s_geometry* geom, const p2s
  * optional) receives 0 (not judged), 1 (judged, kept) or 2 (judged, replaced). */
 int p2s_learned_report_get(p2s_learned_plan* plan, p2s_learned_report* report, int8_t* judge_state, void* stream);
 
+/* ------------------------------------------------------------------------------------
+ * Global assembly on a conforming structured mesh (the "total" step after the fill,
+ * Sec. V).  The mesh has nx x ny x nz hexahedra, element (i, j, k) at (k ny + j) nx + i, and
+ * shares vertices with its lattice neighbours (geometry: its 8 corners in the order of
+ * p2s_geometry); one scalar field of order N on every axis.  The element matrices of the
+ * fill (Legendre basis) are changed to the hierarchic C0 basis
+ *   l_0 = (P_0 - P_1)/2, l_1 = (P_0 + P_1)/2, l_k = (P_k - P_{k-2}) / sqrt(2 (2k - 1)),
+ * (vertex functions of u = -1 and +1, then integrated-Legendre bubbles) and summed into one
+ * global CSR matrix.  Axis dof numbering: vertex i (0..n_el), then bubble k of interval i at
+ * n_el + 1 + i (N - 2) + k - 2; global dof (gu Ngv + gv) Ngw + gw, Ng = n_el (N - 1) + 1.
+ * Row r holds the columns coupled to r in increasing order.  The sums are deterministic:
+ * elements are added in 8 colours of lattice parity, no atomics. */
+typedef struct p2s_assembly p2s_assembly;
+
+/* CSR structure of the global matrix (host, no device needed): *rows, *nnz, and, where
+ * non-NULL, row_ptr [rows + 1] and col_idx [nnz] (caller-owned host arrays).  Errors:
+ * P2S_ERR_ARG (a mesh size < 1, N outside 2..12, or 2^31 rows or more). */
+int p2s_assembly_structure_host(int nx, int ny, int nz, int order, int64_t* rows, int64_t* nnz,
+                                int64_t* row_ptr, int32_t* col_idx);
+
+/* Plan the assembly: an operator plan of the mesh's elements (npts-point rule, precision,
+ * material kind, n_terms terms of field component 0, host, read during the call), the CSR
+ * row pointers and 1-D rank tables on the device, and scratch for the element matrices
+ * (E N^6 doubles).  Errors: as p2s_operator_plan_create and p2s_assembly_structure_host. */
+int p2s_assembly_create(p2s_ctx* ctx, int nx, int ny, int nz, int order, int npts, int precision,
+                        int kind, const p2s_term* terms, int n_terms, p2s_assembly** out);
+void p2s_assembly_destroy(p2s_assembly* A);
+int64_t p2s_assembly_rows(const p2s_assembly* A);
+int64_t p2s_assembly_nnz(const p2s_assembly* A);
+/* The assembly's operator plan (owned by the assembly), e.g. for p2s_plan_use_graph. */
+p2s_plan* p2s_assembly_plan(p2s_assembly* A);
+
+/* Add element matrices to a global matrix: emat (device [E][n][n], n = N^3, Legendre basis,
+ * row-major, element order above; read only) is changed to the hierarchic basis and added
+ * into values (device, p2s_assembly_nnz doubles, CSR order above; not zeroed first).  emat
+ * may be the output of any fill with these orders (one field component).  Asynchronous on
+ * `stream`; uses the assembly's scratch, so calls on one assembly must not overlap.
+ * Errors: P2S_ERR_ARG (NULL), P2S_ERR_CUDA. */
+int p2s_assembly_add(p2s_assembly* A, const double* emat, double* values, void* stream);
+
+/* Fill the element matrices (device inputs as for p2s_plan_fill, E elements) and assemble:
+ * values (device, p2s_assembly_nnz doubles) is overwritten with the global matrix in the
+ * CSR order above.  Asynchronous on `stream`; Jacobian failures set the context's error
+ * flag (p2s_sync_status).  Errors: P2S_ERR_ARG, P2S_ERR_CUDA, those of p2s_plan_fill. */
+int p2s_assembly_fill(p2s_assembly* A, const p2s_geometry* geom, const p2s_material* mat,
+                      double* values, void* stream);
+
 /* Wait for `stream`, then return and clear the context's device error flag:
  * P2S_OK, P2S_ERR_JACOBIAN, P2S_ERR_TIMEOUT, or P2S_ERR_CUDA if the stream failed. */
 int p2s_sync_status(p2s_ctx* ctx, void* stream);

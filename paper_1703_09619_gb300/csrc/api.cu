@@ -69,12 +69,6 @@ struct p2s_plan {
     int64_t gn = -1;
 };
 
-// Run a CUDA call; on failure record it and return P2S_ERR_CUDA from the caller.
-#define P2S_CUDA(call)                                                 \
-    do {                                                               \
-        cudaError_t ce_ = (call);                                      \
-        if (ce_ != cudaSuccess) return fail(P2S_ERR_CUDA, #call, ce_); \
-    } while (0)
 
 namespace {
 

@@ -219,6 +219,12 @@ struct UnitSink {
 
 // Record a failure for p2s_last_error and return `code`.
 int fail(int code, const char* where, cudaError_t ce = cudaSuccess);
+// Run a CUDA call; on failure record it and return P2S_ERR_CUDA from the caller.
+#define P2S_CUDA(call)                                                 \
+    do {                                                               \
+        cudaError_t ce_ = (call);                                      \
+        if (ce_ != cudaSuccess) return fail(P2S_ERR_CUDA, #call, ce_); \
+    } while (0)
 // TileParams from a p2s_tile_config (NULL or zero fields: defaults); P2S_ERR_ARG if out of range.
 int tile_params_from(const p2s_tile_config* c, TileParams& tp);
 // Validate the arguments and fill desc[0..E) (host), the work list and the layout.

@@ -104,6 +104,17 @@ SIGNATURES = {
     "p2s_fill_elements_noalloc": (ctypes.c_int, [_P, ctypes.POINTER(Geometry), ctypes.POINTER(Material),
                                                  ctypes.POINTER(Orders), ctypes.POINTER(Quadrature),
                                                  ctypes.POINTER(FillOpts), _P, _P, _P]),
+    "p2s_assembly_structure_host": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   _P, _P, _P, _P]),
+    "p2s_assembly_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_int, _P, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_void_p)]),
+    "p2s_assembly_destroy": (None, [_P]),
+    "p2s_assembly_rows": (_I64, [_P]),
+    "p2s_assembly_nnz": (_I64, [_P]),
+    "p2s_assembly_plan": (_P, [_P]),
+    "p2s_assembly_fill": (ctypes.c_int, [_P, ctypes.POINTER(Geometry), ctypes.POINTER(Material), _P, _P]),
+    "p2s_assembly_add": (ctypes.c_int, [_P, _P, _P, _P]),
     "p2s_sync_status": (ctypes.c_int, [_P, _P]),
     "p2s_linearisation": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
     "p2s_gauss_legendre": (ctypes.c_int, [ctypes.c_int, _P, _P]),
@@ -391,6 +402,66 @@ class OperatorPlan(Plan):
         self.moment_entries = int(lib.p2s_plan_moment_entries(h))
         if graph:
             self.use_graph(True)
+
+
+def assembly_structure(nx, ny, nz, order):
+    """CSR structure (row_ptr int64 [rows + 1], col_idx int32 [nnz]) of the global matrix of an
+    nx x ny x nz structured mesh with `order` per axis (p2s_assembly_structure_host, host only)."""
+    lib = load()
+    rows, nnz = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib.p2s_assembly_structure_host(nx, ny, nz, order, ctypes.byref(rows), ctypes.byref(nnz), None, None),
+           "p2s_assembly_structure_host")
+    row_ptr = np.zeros(rows.value + 1, dtype=np.int64)
+    col_idx = np.zeros(nnz.value, dtype=np.int32)
+    _check(lib.p2s_assembly_structure_host(nx, ny, nz, order, None, None, _hptr(row_ptr), _hptr(col_idx)),
+           "p2s_assembly_structure_host")
+    return row_ptr, col_idx
+
+
+class Assembly:
+    """A p2s_assembly: operator fill of a structured mesh's elements plus the deterministic
+    scatter into one global CSR matrix in the hierarchic C0 basis."""
+
+    def __init__(self, ctx: Context, nx, ny, nz, order, npts, terms, scales, kind, precision=FP64, graph=False):
+        lib = load()
+        self.ctx = ctx
+        self._terms, nt = terms_struct(terms, scales)
+        h = ctypes.c_void_p()
+        _check(lib.p2s_assembly_create(ctx.handle, nx, ny, nz, order, int(npts), int(precision), int(kind),
+                                       ctypes.cast(self._terms, ctypes.c_void_p), nt, ctypes.byref(h)),
+               "p2s_assembly_create")
+        self.handle = h
+        self.shape = (nx, ny, nz)
+        self.order = order
+        self.n_elem = nx * ny * nz
+        self.rows = int(lib.p2s_assembly_rows(h))
+        self.nnz = int(lib.p2s_assembly_nnz(h))
+        if graph:
+            _check(lib.p2s_plan_use_graph(lib.p2s_assembly_plan(h), 1), "p2s_plan_use_graph")
+
+    def structure(self):
+        return assembly_structure(*self.shape, self.order)
+
+    def fill(self, kind, params, nodes, bulge, values, stream=None):
+        g, m = Plan._inputs(kind, params, nodes, bulge)
+        _check(load().p2s_assembly_fill(self.handle, ctypes.byref(g), ctypes.byref(m), _dptr(values),
+                                        _stream(stream)), "p2s_assembly_fill")
+
+    def add(self, emat, values, stream=None):
+        """Add Legendre-basis element matrices (device [E][n][n]) to `values` (not zeroed)."""
+        _check(load().p2s_assembly_add(self.handle, _dptr(emat), _dptr(values), _stream(stream)),
+               "p2s_assembly_add")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().p2s_assembly_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def fill_elements(ctx: Context, orders, npts, kind, params, nodes, bulge, out, elem_status=None,
