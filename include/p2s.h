@@ -390,7 +390,9 @@ int p2s_learned_report_get(p2s_learned_plan* plan, p2s_learned_report* report, i
  * global CSR matrix.  Axis dof numbering: vertex i (0..n_el), then bubble k of interval i at
  * n_el + 1 + i (N - 2) + k - 2; global dof (gu Ngv + gv) Ngw + gw, Ng = n_el (N - 1) + 1.
  * Row r holds the columns coupled to r in increasing order.  The sums are deterministic:
- * elements are added in 8 colours of lattice parity, no atomics. */
+ * elements are added in 8 colours of lattice parity, so within one colour every position
+ * receives at most one addition.  A mixed-precision assembly (N <= 5) keeps the fill's
+ * float-float values through the basis change and rounds each to FP64 once before adding. */
 typedef struct p2s_assembly p2s_assembly;
 
 /* CSR structure of the global matrix (host, no device needed): *rows, *nnz, and, where
@@ -408,8 +410,8 @@ int p2s_assembly_create(p2s_ctx* ctx, int nx, int ny, int nz, int order, int npt
 void p2s_assembly_destroy(p2s_assembly* A);
 int64_t p2s_assembly_rows(const p2s_assembly* A);
 int64_t p2s_assembly_nnz(const p2s_assembly* A);
-/* The assembly's operator plan (owned by the assembly), e.g. for p2s_plan_use_graph. */
-p2s_plan* p2s_assembly_plan(p2s_assembly* A);
+/* Replay the element fill of p2s_assembly_fill from a CUDA graph (as p2s_plan_use_graph). */
+int p2s_assembly_use_graph(p2s_assembly* A, int enable);
 
 /* Add element matrices to a global matrix: emat (device [E][n][n], n = N^3, Legendre basis,
  * row-major, element order above; read only) is changed to the hierarchic basis and added

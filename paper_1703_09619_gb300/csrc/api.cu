@@ -433,6 +433,7 @@ int run_contract(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_
     C.op_scales = op ? op->scales : nullptr;
     C.op_block = op ? op->block : nullptr;
     C.op_nalpha = op ? op->nalpha : 0;
+    C.out_ff = op ? PL.out_ff : 0;
     if (PL.spec_n)
         P2S_CUDA(launch_contract_ffn(PL.spec_n, C, PL.con_grid, PL.con_threads, PL.con_smem, s));
     else
@@ -945,6 +946,13 @@ int p2s_sync_status(p2s_ctx* ctx, void* stream) {
 namespace p2s {
 const DeviceTables* context_tables(const p2s_ctx* c) { return c ? &c->T : nullptr; }
 ElemDesc* plan_desc(p2s_plan* p) { return p ? p->d_desc : nullptr; }
+int plan_set_output_ff(p2s_plan* p, bool on) {
+    if (!p || !p->L.op || p->L.precision != P2S_MIXED || p->L.spec_n)
+        return fail(P2S_ERR_ARG, "plan_set_output_ff: a mixed-precision operator plan is required");
+    p->L.out_ff = on ? 1 : 0;
+    p->gkey[3] = nullptr;  // a captured replay has the old setting: capture again on the next fill
+    return P2S_OK;
+}
 int32_t* plan_order(p2s_plan* p) {
     if (!p) return nullptr;
     if (!p->d_order && cudaMalloc(&p->d_order, sizeof(int32_t) * std::max<int64_t>(1, p->L.n_elem)) != cudaSuccess) {

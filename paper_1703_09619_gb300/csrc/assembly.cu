@@ -25,6 +25,8 @@
 #include <new>
 #include <vector>
 
+#include "arith.cuh"
+#include "dw.cuh"
 #include "p2s_internal.h"
 
 namespace p2s {
@@ -83,16 +85,19 @@ struct AsmLaunch {
     const int64_t* row_ptr;  // [rows + 1]
     AxisDev ax[3];
     double ck[kMaxOrder];    // 1 / sqrt(2 (2k - 1)): the bubble normalisation
+    float ckf[2 * kMaxOrder];  // the same as (hi, lo) FP32 pairs
     int nx, ny, nz, N, colour;
 };
 
 // y = T x on the N values X[base + k s] (in place): y_0 = (x_0 - x_1)/2, y_1 = (x_0 + x_1)/2,
-// y_k = c_k (x_k - x_{k-2}); one thread per line, the N values held in registers.
-// Lines are disjoint, so src == X is allowed.
+// y_k = c_k (x_k - x_{k-2}); one thread per line, the N values held in registers.  Line
+// `line` starts at base = hi s N + lo with (hi, lo) = divmod(line, s), stepped without
+// divisions.  Lines are disjoint, so src == X is allowed.
 __device__ __forceinline__ void hier_lines(const double* src, double* X, int s, int nn, const AsmLaunch& L) {
     const int N = L.N, lines = nn / N;
+    const int step_hi = div_small((int)blockDim.x, s, 1.0f / (float)s), step_lo = (int)blockDim.x - step_hi * s;
+    int hi = div_small((int)threadIdx.x, s, 1.0f / (float)s), lo = (int)threadIdx.x - hi * s;
     for (int line = threadIdx.x; line < lines; line += blockDim.x) {
-        const int lo = line % s, hi = line / s;
         const int base = hi * s * N + lo;
         double* p = X + base;
         double x[kMaxOrder];
@@ -104,46 +109,262 @@ __device__ __forceinline__ void hier_lines(const double* src, double* X, int s, 
 #pragma unroll
         for (int k = 2; k < kMaxOrder; ++k)
             if (k < N) p[k * s] = L.ck[k] * (x[k] - x[k - 2]);
+        hi += step_hi;
+        lo += step_lo;
+        if (lo >= s) { lo -= s; ++hi; }
     }
 }
 
-// One CTA per element of the colour (grid-stride).  Tk M Tk^T by sum factorisation: T along the
-// three test axes and the three trial axes of the n x n matrix, 2 products per entry and pass;
-// then every entry is added to its CSR position.  kSmem: the matrix is staged in shared memory
-// (n^2 doubles); otherwise it is transformed in place in the fill's scratch.
-template <bool kSmem>
-__global__ void __launch_bounds__(kAsmThreads, 4) k_assemble(AsmLaunch L) {
-    extern __shared__ double s_mat[];
-    const int N = L.N, n = N * N * N, nn = n * n;
+// Shared-memory tables of one element for the scatter (n = N^3 local dofs):
+//   base[r]  CSR start of the global row of local row r,
+//   cvw[r]   neighbour counts (cnt_v(gv), cnt_w(gw)) of that row,
+//   dec[r]   the digits (m, n, p) of r packed in bytes,
+//   rank[a][x][y]  rank of the element's axis-a dof y among the neighbours of its dof x,
+// so the position of entry (r, c) is base[r] + (ru cnt_v + rv) cnt_w + rw.
+__host__ __device__ constexpr size_t asm_table_bytes_staged(int N) {
+    return sizeof(int64_t) * (N * N * N) + sizeof(int2) * (N * N * N) + sizeof(int) * 3 * N * N;
+}
+__host__ __device__ inline size_t asm_table_bytes(int N) {
+    const int n = N * N * N;
+    return sizeof(int64_t) * n + sizeof(int2) * n + sizeof(int) * n + sizeof(int) * 3 * N * N;
+}
+
+// T applied in place to x[0], x[S], ..., x[(N-1) S] (compile-time indices, so x stays in
+// registers); k descends so that x[(k-2) S] is still the input when x[k S] is formed.
+template <int N, int S>
+__device__ __forceinline__ void hier_T(double* x, const AsmLaunch& L) {
+    const double y0 = 0.5 * (x[0] - x[S]), y1 = 0.5 * (x[0] + x[S]);
+#pragma unroll
+    for (int k = N - 1; k >= 2; --k) x[k * S] = L.ck[k] * (x[k * S] - x[(k - 2) * S]);
+    x[0] = y0;
+    x[S] = y1;
+}
+// The same in float-float (SloppyDWPlusDW sums, normalised products): absolute error
+// O(u^2 (|x_a| + |x_b|)) per output, u = 2^-24, and every result normalised (|lo| <= ulp(hi)/2),
+// as the conversion to FP64 requires.  Halving is exact.
+template <int N, int S>
+__device__ __forceinline__ void hier_T(dw* x, const AsmLaunch& L) {
+    const dw d = dw_sub_fast(x[0], x[S]), a = dw_add_fast(x[0], x[S]);
+#pragma unroll
+    for (int k = N - 1; k >= 2; --k)
+        x[k * S] = dw_mul(dw_sub_fast(x[k * S], x[(k - 2) * S]), dw{L.ckf[2 * k], L.ckf[2 * k + 1]});
+    x[0] = dw{0.5f * d.hi, 0.5f * d.lo};
+    x[S] = dw{0.5f * a.hi, 0.5f * a.lo};
+}
+
+// Values of the staged kernel: FP64, or float-float pairs (the mixed fill's output kept as
+// (hi, lo) FP32 words in each 8-byte slot).  R in registers, M in memory.
+template <bool kFF>
+struct AsmVal {
+    using R = double;
+    using M = double;
+    __device__ static R ld(const M* p) { return *p; }
+    __device__ static void st(M* p, R v) { *p = v; }
+    __device__ static R ldg(const double* p) { return __ldg(p); }
+    __device__ static double out(const M* p) { return *p; }
+};
+template <>
+struct AsmVal<true> {
+    using R = dw;
+    using M = float2;
+    __device__ static R ld(const M* p) {
+        const float2 f = *p;
+        return dw{f.x, f.y};
+    }
+    __device__ static void st(M* p, R v) { *p = make_float2(v.hi, v.lo); }
+    __device__ static R ldg(const double* p) {
+        const float2 f = __ldg(reinterpret_cast<const float2*>(p));
+        return dw{f.x, f.y};
+    }
+    __device__ static double out(const M* p) { return ArithFF::to_double_fast(*p); }
+};
+
+// Element matrices staged in shared memory, order N (2..5) known at compile time.  Layout of the
+// staged matrix: entry (r, c), c = m2 N^2 + j, at (r N + m2) P + j with P = N^2 rounded up to
+// odd, so rows of N^2 trial entries start on distinct banks.  Four passes, each holding its
+// values in registers:
+//   A  test u: read from HBM (coalesced along c and the other test axes), T, store;
+//   B  test v and w of one (m, c): N^2 values, stride P N between p;
+//   C  trial u of one (r, j): N values, stride P;
+//   D  trial v and w of one (r, m2): the N^2 contiguous values of a padded row;
+// then every entry is added to its CSR position (tables as in k_assemble).  kFF: the input holds
+// float-float pairs and the passes run in float-float on the FP32 pipe (FP64 arithmetic runs at
+// a small fraction of the FP32 rate), the entries going to FP64 by integer operations at the end.
+// The additions into the values are L2 reductions (red.global.add.f64): within one colour every
+// position receives at most one, so the sums are the same on every run.
+template <int N, bool kFF>
+__global__ void __launch_bounds__(kAsmThreads, N <= 4 ? 4 : 1) k_assemble_staged(AsmLaunch L) {
+    constexpr int NN = N * N, n = NN * N, nn = n * n, P = NN | 1, G = n * N;
+    using AV = AsmVal<kFF>;
+    using R = typename AV::R;
+    using M = typename AV::M;
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    M* s_x = reinterpret_cast<M*>(s_raw);  // [G][P]
+    int64_t* s_base = reinterpret_cast<int64_t*>(s_x + G * P);
+    int2* s_cvw = reinterpret_cast<int2*>(s_base + n);
+    int* s_rank = reinterpret_cast<int*>(s_cvw + n);
+    const int tid = threadIdx.x;
     const int cx = L.colour & 1, cy = (L.colour >> 1) & 1, cz = (L.colour >> 2) & 1;
     const int hx = (L.nx - cx + 1) / 2, hy = (L.ny - cy + 1) / 2, hz = (L.nz - cz + 1) / 2;
     const int64_t count = (int64_t)hx * hy * hz;
     for (int64_t q = blockIdx.x; q < count; q += gridDim.x) {
         const int qi = (int)(q % hx), qj = (int)((q / hx) % hy), qk = (int)(q / ((int64_t)hx * hy));
         const int i = 2 * qi + cx, j = 2 * qj + cy, k = 2 * qk + cz;
+        const double* __restrict__ src = L.emat + (((int64_t)k * L.ny + j) * L.nx + i) * (int64_t)nn;
+        for (int t = tid; t < 3 * NN; t += kAsmThreads) {
+            const int a = t / NN, xy = t - a * NN;
+            s_rank[t] = L.ax[a].rank[(a == 0 ? i : (a == 1 ? j : k)) * NN + xy];
+        }
+        for (int r = tid; r < n; r += kAsmThreads) {
+            const int gu = axis_g(L.ax[0], i, r / NN), gv = axis_g(L.ax[1], j, (r / N) % N),
+                      gw = axis_g(L.ax[2], k, r % N);
+            s_base[r] = L.row_ptr[((int64_t)gu * L.ax[1].ng + gv) * L.ax[2].ng + gw];
+            s_cvw[r] = make_int2(L.ax[1].cnt[gv], L.ax[2].cnt[gw]);
+        }
+        // A: lines lo = rr n + c (rr: test v, w digits), the N values at m n N^2 + lo
+#pragma unroll 4
+        for (int lo = tid; lo < n * NN; lo += kAsmThreads) {
+            R x[N];
+#pragma unroll
+            for (int m = 0; m < N; ++m) x[m] = AV::ldg(src + m * (n * NN) + lo);
+            hier_T<N, 1>(x, L);
+            const int rr = lo / n, c = lo - rr * n, m2 = c / NN, jj = c - m2 * NN;
+#pragma unroll
+            for (int m = 0; m < N; ++m) AV::st(s_x + ((m * NN + rr) * N + m2) * P + jj, x[m]);
+        }
+        __syncthreads();
+        // B: one (m, c) per thread
+        for (int g = tid; g < N * n; g += kAsmThreads) {
+            const int m = g / n, c = g - m * n, m2 = c / NN, jj = c - m2 * NN;
+            M* base = s_x + ((m * NN) * N + m2) * P + jj;  // row (m, 0, 0)
+            R x[NN];
+#pragma unroll
+            for (int v = 0; v < NN; ++v) x[v] = AV::ld(base + v * N * P);  // row (m, v / N, v % N)
+#pragma unroll
+            for (int a = 0; a < N; ++a) hier_T<N, 1>(x + a * N, L);  // w
+#pragma unroll
+            for (int b = 0; b < N; ++b) hier_T<N, N>(x + b, L);      // v
+#pragma unroll
+            for (int v = 0; v < NN; ++v) AV::st(base + v * N * P, x[v]);
+        }
+        __syncthreads();
+        // C: one (r, j) per thread
+        for (int l = tid; l < n * NN; l += kAsmThreads) {
+            const int r = l / NN, jj = l - r * NN;
+            M* base = s_x + r * N * P + jj;
+            R x[N];
+#pragma unroll
+            for (int m2 = 0; m2 < N; ++m2) x[m2] = AV::ld(base + m2 * P);
+            hier_T<N, 1>(x, L);
+#pragma unroll
+            for (int m2 = 0; m2 < N; ++m2) AV::st(base + m2 * P, x[m2]);
+        }
+        __syncthreads();
+        // D: one padded row (r, m2) per thread
+        for (int g = tid; g < G; g += kAsmThreads) {
+            M* base = s_x + g * P;
+            R x[NN];
+#pragma unroll
+            for (int v = 0; v < NN; ++v) x[v] = AV::ld(base + v);
+#pragma unroll
+            for (int a = 0; a < N; ++a) hier_T<N, 1>(x + a * N, L);  // w
+#pragma unroll
+            for (int b = 0; b < N; ++b) hier_T<N, N>(x + b, L);      // v
+#pragma unroll
+            for (int v = 0; v < NN; ++v) AV::st(base + v, x[v]);
+        }
+        __syncthreads();
+        // scatter: one L2 reduction per entry
+        for (int t = tid; t < nn; t += kAsmThreads) {
+            const int r = t / n, c = t - r * n, m2 = c / NN, jj = c - m2 * NN;
+            const int ru = s_rank[(r / NN) * N + m2];
+            const int rv = s_rank[NN + ((r / N) % N) * N + jj / N];
+            const int rw = s_rank[2 * NN + (r % N) * N + jj % N];
+            const int2 cvw = s_cvw[r];
+            atomicAdd(L.values + s_base[r] + ((ru * cvw.x + rv) * cvw.y + rw), AV::out(s_x + (r * N + m2) * P + jj));
+        }
+        __syncthreads();  // the staged matrix and the tables are reused by the next element
+    }
+}
+
+constexpr int kMaxStagedOrder = 5;
+using AsmKernel = void (*)(AsmLaunch);
+template <bool kFF>
+AsmKernel staged_kernel(int N) {
+    switch (N) {
+        case 2: return k_assemble_staged<2, kFF>;
+        case 3: return k_assemble_staged<3, kFF>;
+        case 4: return k_assemble_staged<4, kFF>;
+        default: return k_assemble_staged<5, kFF>;
+    }
+}
+
+__host__ __device__ constexpr size_t staged_smem_bytes(int N) {
+    return sizeof(double) * (size_t)(N * N * N * N) * (size_t)((N * N) | 1) + asm_table_bytes_staged(N);
+}
+
+// Any order (used for N >= 6, whose n^2 doubles do not fit in shared memory): one CTA per element
+// of the colour (grid-stride).  Tk M Tk^T by sum factorisation in the assembly's scratch: T along
+// the three test axes and the three trial axes of the n x n matrix, 2 products per entry and
+// pass; then every entry is added to its CSR position.
+__global__ void __launch_bounds__(kAsmThreads, 4) k_assemble(AsmLaunch L) {
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    const int N = L.N, NN = N * N, n = NN * N, nn = n * n;
+    int64_t* s_base = reinterpret_cast<int64_t*>(s_raw);
+    int2* s_cvw = reinterpret_cast<int2*>(s_base + n);
+    int* s_dec = reinterpret_cast<int*>(s_cvw + n);
+    int* s_rank = s_dec + n;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        const int m = r / NN, nv = (r / N) % N, p = r % N;
+        s_dec[r] = m | (nv << 8) | (p << 16);
+    }
+    // (r, c) of entry t = r n + c, stepped by blockDim
+    const int step_r = (int)blockDim.x / n, step_c = (int)blockDim.x - step_r * n;
+    const int r0 = (int)threadIdx.x / n, c0 = (int)threadIdx.x - r0 * n;
+    const int cx = L.colour & 1, cy = (L.colour >> 1) & 1, cz = (L.colour >> 2) & 1;
+    const int hx = (L.nx - cx + 1) / 2, hy = (L.ny - cy + 1) / 2, hz = (L.nz - cz + 1) / 2;
+    const int64_t count = (int64_t)hx * hy * hz;
+    __syncthreads();
+    for (int64_t q = blockIdx.x; q < count; q += gridDim.x) {
+        const int qi = (int)(q % hx), qj = (int)((q / hx) % hy), qk = (int)(q / ((int64_t)hx * hy));
+        const int i = 2 * qi + cx, j = 2 * qj + cy, k = 2 * qk + cz;
         const int64_t e = ((int64_t)k * L.ny + j) * L.nx + i;
         const double* src = L.emat + e * (int64_t)nn;
-        double* X = kSmem ? s_mat : L.work + e * (int64_t)nn;
+        double* X = L.work + e * (int64_t)nn;
+        // the element's tables (the previous element's scatter ended at a barrier)
+        for (int t = threadIdx.x; t < 3 * NN; t += blockDim.x) {
+            const int a = t / NN, xy = t - a * NN;
+            const int el = a == 0 ? i : (a == 1 ? j : k);
+            s_rank[t] = L.ax[a].rank[el * NN + xy];
+        }
+        for (int r = threadIdx.x; r < n; r += blockDim.x) {
+            const int d = s_dec[r];
+            const int gu = axis_g(L.ax[0], i, d & 0xff), gv = axis_g(L.ax[1], j, (d >> 8) & 0xff),
+                      gw = axis_g(L.ax[2], k, d >> 16);
+            s_base[r] = L.row_ptr[((int64_t)gu * L.ax[1].ng + gv) * L.ax[2].ng + gw];
+            s_cvw[r] = make_int2(L.ax[1].cnt[gv], L.ax[2].cnt[gw]);
+        }
         // test u, v, w (strides n N^2, n N, n), then trial u, v, w (N^2, N, 1); the first pass
         // reads the input
 #pragma unroll 1
-        for (int pass = 0, st = n * N * N; pass < 6; ++pass, st = pass == 3 ? N * N : st / N) {
+        for (int pass = 0, st = n * NN; pass < 6; ++pass, st = pass == 3 ? NN : st / N) {
             hier_lines(pass == 0 ? src : X, X, st, nn, L);
             __syncthreads();
         }
+        // scatter: one L2 reduction per entry (at most one per position within a colour)
+        int r = r0, c = c0;
         for (int t = threadIdx.x; t < nn; t += blockDim.x) {
-            const int r = t / n, c = t - r * n;
-            const int m = r / (N * N), nv = (r / N) % N, p = r % N;
-            const int m2 = c / (N * N), n2 = (c / N) % N, p2 = c % N;
-            const int gu = axis_g(L.ax[0], i, m), gv = axis_g(L.ax[1], j, nv), gw = axis_g(L.ax[2], k, p);
-            const int64_t row = ((int64_t)gu * L.ax[1].ng + gv) * L.ax[2].ng + gw;
-            const int ru = L.ax[0].rank[(i * N + m) * N + m2];
-            const int rv = L.ax[1].rank[(j * N + nv) * N + n2];
-            const int rw = L.ax[2].rank[(k * N + p) * N + p2];
-            const int64_t pos = L.row_ptr[row] + ((int64_t)ru * L.ax[1].cnt[gv] + rv) * L.ax[2].cnt[gw] + rw;
-            L.values[pos] += X[t];
+            const int dr = s_dec[r], dc = s_dec[c];
+            const int ru = s_rank[(dr & 0xff) * N + (dc & 0xff)];
+            const int rv = s_rank[NN + ((dr >> 8) & 0xff) * N + ((dc >> 8) & 0xff)];
+            const int rw = s_rank[2 * NN + (dr >> 16) * N + (dc >> 16)];
+            const int2 cvw = s_cvw[r];
+            atomicAdd(L.values + s_base[r] + ((ru * cvw.x + rv) * cvw.y + rw), X[t]);
+            r += step_r;
+            c += step_c;
+            if (c >= n) { c -= n; ++r; }
         }
-        __syncthreads();  // X is reused by the next element
+        __syncthreads();  // X and the tables are reused by the next element
     }
 }
 
@@ -163,7 +384,11 @@ struct p2s_assembly {
     int64_t* d_row_ptr = nullptr;
     int32_t* d_axis = nullptr;  // cnt and rank tables of the three axes, back to back
     AxisDev dev[3];
-    size_t smem = 0;  // > 0: element matrices staged in shared memory (n^2 doubles)
+    bool staged = false;  // element matrices staged in shared memory (k_assemble_staged<N>)
+    bool ff = false;      // the fill writes float-float pairs, transformed in float-float
+    void (*kernel)(AsmLaunch) = nullptr;       // p2s_assembly_add: FP64 element matrices
+    void (*kernel_fill)(AsmLaunch) = nullptr;  // p2s_assembly_fill: the plan's own output
+    size_t smem = 0;      // dynamic shared memory of k_assemble
     int grid = 1;     // CTAs of a colour launch: the resident capacity of the device
 };
 
@@ -282,15 +507,18 @@ int p2s_assembly_create(p2s_ctx* ctx, int nx, int ny, int nz, int order, int npt
         off += X.rank.size();
     }
     if (ce != cudaSuccess) { p2s_assembly_destroy(A); return fail(P2S_ERR_CUDA, "p2s_assembly_create: upload", ce); }
-    const size_t mat_bytes = sizeof(double) * (size_t)(n * n);
     int per_sm = 0;
-    if (mat_bytes <= T->smem_optin) {
-        A->smem = mat_bytes;
-        ce = cudaFuncSetAttribute(k_assemble<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mat_bytes);
-        if (ce == cudaSuccess) ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_assemble<true>, kAsmThreads, mat_bytes);
-    } else {
-        ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_assemble<false>, kAsmThreads, 0);
-    }
+    A->staged = order <= kMaxStagedOrder && staged_smem_bytes(order) <= T->smem_optin;
+    // a mixed fill hands its float-float pairs to the staged kernel without converting them
+    A->ff = A->staged && precision == P2S_MIXED;
+    if (A->ff && (rc = plan_set_output_ff(A->plan, true)) != P2S_OK) { p2s_assembly_destroy(A); return rc; }
+    A->kernel = A->staged ? staged_kernel<false>(order) : k_assemble;
+    A->kernel_fill = A->ff ? staged_kernel<true>(order) : A->kernel;
+    A->smem = A->staged ? staged_smem_bytes(order) : asm_table_bytes(order);
+    ce = cudaFuncSetAttribute(A->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)A->smem);
+    if (ce == cudaSuccess)
+        ce = cudaFuncSetAttribute(A->kernel_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)A->smem);
+    if (ce == cudaSuccess) ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, A->kernel, kAsmThreads, A->smem);
     if (ce != cudaSuccess) { p2s_assembly_destroy(A); return fail(P2S_ERR_CUDA, "p2s_assembly_create: kernel attributes", ce); }
     A->grid = std::max(1, per_sm) * T->sm_count;
     *out = A;
@@ -299,11 +527,18 @@ int p2s_assembly_create(p2s_ctx* ctx, int nx, int ny, int nz, int order, int npt
 
 int64_t p2s_assembly_rows(const p2s_assembly* A) { return A ? A->rows : P2S_ERR_ARG; }
 int64_t p2s_assembly_nnz(const p2s_assembly* A) { return A ? A->nnz : P2S_ERR_ARG; }
-p2s_plan* p2s_assembly_plan(p2s_assembly* A) { return A ? A->plan : nullptr; }
+int p2s_assembly_use_graph(p2s_assembly* A, int enable) {
+    if (!A) return fail(P2S_ERR_ARG, "p2s_assembly_use_graph: NULL assembly");
+    return p2s_plan_use_graph(A->plan, enable);
+}
 
-int p2s_assembly_add(p2s_assembly* A, const double* emat, double* values, void* stream) {
-    if (!A || !emat || !values) return fail(P2S_ERR_ARG, "p2s_assembly_add: NULL assembly, matrices or values");
-    cudaStream_t s = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace {
+
+// The 8 colour launches of `kernel` over the element matrices `emat`.
+int assemble_colours(p2s_assembly* A, AsmKernel kernel, const double* emat, double* values, cudaStream_t s) {
+    P2S_CUDA(cudaSetDevice(context_tables(A->ctx)->device));
     P2S_CUDA(cudaSetDevice(context_tables(A->ctx)->device));
     AsmLaunch L;
     L.emat = emat;
@@ -315,18 +550,30 @@ int p2s_assembly_add(p2s_assembly* A, const double* emat, double* values, void* 
     L.ny = A->ny;
     L.nz = A->nz;
     L.N = A->N;
-    for (int k = 0; k < kMaxOrder; ++k) L.ck[k] = k >= 2 ? 1.0 / std::sqrt(2.0 * (2 * k - 1)) : 0.0;
+    for (int k = 0; k < kMaxOrder; ++k) {
+        L.ck[k] = k >= 2 ? 1.0 / std::sqrt(2.0 * (2 * k - 1)) : 0.0;
+        L.ckf[2 * k] = (float)L.ck[k];
+        L.ckf[2 * k + 1] = (float)(L.ck[k] - (double)L.ckf[2 * k]);
+    }
     for (int c = 0; c < 8; ++c) {  // colours one after the other: no two elements in flight share a dof
         L.colour = c;
         const int64_t cnt = (int64_t)((A->nx - (c & 1) + 1) / 2) * ((A->ny - ((c >> 1) & 1) + 1) / 2) *
                             ((A->nz - ((c >> 2) & 1) + 1) / 2);
         if (cnt == 0) continue;
         const int grid = (int)std::min<int64_t>(cnt, A->grid);
-        if (A->smem) k_assemble<true><<<grid, kAsmThreads, A->smem, s>>>(L);
-        else k_assemble<false><<<grid, kAsmThreads, 0, s>>>(L);
+        kernel<<<grid, kAsmThreads, A->smem, s>>>(L);
         P2S_CUDA(cudaGetLastError());
     }
     return P2S_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int p2s_assembly_add(p2s_assembly* A, const double* emat, double* values, void* stream) {
+    if (!A || !emat || !values) return fail(P2S_ERR_ARG, "p2s_assembly_add: NULL assembly, matrices or values");
+    return assemble_colours(A, A->kernel, emat, values, (cudaStream_t)stream);
 }
 
 int p2s_assembly_fill(p2s_assembly* A, const p2s_geometry* geom, const p2s_material* mat, double* values, void* stream) {
@@ -335,7 +582,7 @@ int p2s_assembly_fill(p2s_assembly* A, const p2s_geometry* geom, const p2s_mater
     int rc = p2s_plan_fill(A->plan, geom, mat, A->d_emat, nullptr, stream);
     if (rc) return rc;
     P2S_CUDA(cudaMemsetAsync(values, 0, sizeof(double) * A->nnz, (cudaStream_t)stream));
-    return p2s_assembly_add(A, A->d_emat, values, stream);
+    return assemble_colours(A, A->kernel_fill, A->d_emat, values, (cudaStream_t)stream);
 }
 
 }  // extern "C"

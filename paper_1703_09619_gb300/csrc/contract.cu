@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(512) k_contract(ContractLaunch L) {
         if (n_terms == 0) {  // an operator block without terms is zero
             for (int i = tid; i < rows * ld; i += nth) tile[i] = 0.0;
             __syncthreads();
-        } else if (op && !kFP64) {  // the summed terms to FP64, once per entry, in place
+        } else if (op && !kFP64 && !L.out_ff) {  // the summed terms to FP64, once per entry, in place
             const T* tT = reinterpret_cast<const T*>(tile);
             for (int i = tid; i < rows * ld; i += nth) tile[i] = A::to_double_fast(tT[i]);
             __syncthreads();

@@ -118,6 +118,8 @@ struct ContractLaunch {
     const double* op_scales;
     const int32_t* op_block;
     int op_nalpha;            // 3 (metric kind) or 1
+    int out_ff;               // operator mode, mixed precision: write each entry's (hi, lo) FP32 pair
+                              // into its 8-byte slot instead of converting it to FP64
 };
 struct ContractShape {
     size_t a, b, tile;
@@ -199,6 +201,7 @@ struct PlanLayout {
     int con_grid = 1;
     int spec_n = 0;  // > 0: the mixed contraction specialised for uniform order N
     int op = 0;      // 1: an operator plan (term list), one n x n matrix per element
+    int out_ff = 0;  // operator plans, mixed precision: entries written as (hi, lo) FP32 pairs
     TileParams tile;  // the tile configuration in effect
 };
 
@@ -259,6 +262,10 @@ ElemDesc* plan_desc(p2s_plan* p);
 int32_t* plan_order(p2s_plan* p);
 // Fill of a plan restricted to the elements with mask != 0 (FP64 plans only; the others
 // are left untouched in `out`).
+// Operator plans of mixed precision only: write each output entry as its (hi, lo) FP32 pair
+// (float2 in the entry's 8 bytes) rather than the FP64 value, for a consumer that continues in
+// float-float.  P2S_ERR_ARG for other plans.
+int plan_set_output_ff(p2s_plan* p, bool on);
 int plan_fill_masked(p2s_plan* p, const p2s_geometry* geom, const p2s_material* mat, double* out,
                      const int8_t* mask, cudaStream_t s);
 cudaError_t learned_init_attributes();

@@ -112,7 +112,7 @@ SIGNATURES = {
     "p2s_assembly_destroy": (None, [_P]),
     "p2s_assembly_rows": (_I64, [_P]),
     "p2s_assembly_nnz": (_I64, [_P]),
-    "p2s_assembly_plan": (_P, [_P]),
+    "p2s_assembly_use_graph": (ctypes.c_int, [_P, ctypes.c_int]),
     "p2s_assembly_fill": (ctypes.c_int, [_P, ctypes.POINTER(Geometry), ctypes.POINTER(Material), _P, _P]),
     "p2s_assembly_add": (ctypes.c_int, [_P, _P, _P, _P]),
     "p2s_sync_status": (ctypes.c_int, [_P, _P]),
@@ -437,7 +437,7 @@ class Assembly:
         self.rows = int(lib.p2s_assembly_rows(h))
         self.nnz = int(lib.p2s_assembly_nnz(h))
         if graph:
-            _check(lib.p2s_plan_use_graph(lib.p2s_assembly_plan(h), 1), "p2s_plan_use_graph")
+            _check(lib.p2s_assembly_use_graph(h, 1), "p2s_assembly_use_graph")
 
     def structure(self):
         return assembly_structure(*self.shape, self.order)

@@ -75,12 +75,22 @@ def test_assembly_matches_oracle_fp64(torch, ctx, nx, ny, nz, N, G):
     assert np.abs(K - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
-def test_assembly_matches_oracle_mixed(torch, ctx):
-    mesh = W.make_mesh(2, 2, 2, 4, 8, seed=3)
-    (vals,), row_ptr, col_idx, rc = gpu_assemble(torch, ctx, mesh, 4, 8, p2s.MIXED)
-    assert rc == 0
-    ref = oracle_global(mesh, 4, 8)
+@pytest.mark.parametrize("nx,ny,nz,N,G", [(2, 2, 2, 4, 8), (3, 1, 2, 2, 4), (2, 2, 1, 3, 5), (1, 2, 2, 5, 7),
+                                          (2, 1, 1, 6, 7)])
+def test_assembly_matches_oracle_mixed(torch, ctx, nx, ny, nz, N, G):
+    """Mixed fills: N <= 5 keep float-float through the basis change, N = 6 converts first."""
+    mesh = W.make_mesh(nx, ny, nz, N, G, seed=3 + N)
+    (vals,), row_ptr, col_idx, rc = gpu_assemble(torch, ctx, mesh, N, G, p2s.MIXED)
+    assert rc == 0 and not np.isnan(vals).any()
+    ref = oracle_global(mesh, N, G)
     assert np.abs(dense(row_ptr, col_idx, vals) - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+def test_mixed_assembly_close_to_fp64(torch, ctx):
+    mesh = W.make_mesh(4, 3, 3, 4, 12, seed=9)
+    (a,), _, _, _ = gpu_assemble(torch, ctx, mesh, 4, 12, p2s.FP64)
+    (b,), _, _, _ = gpu_assemble(torch, ctx, mesh, 4, 12, p2s.MIXED)
+    assert np.abs(a - b).max() <= 1e-10 * np.abs(a).max()
 
 
 def test_assembly_deterministic_and_graph_replay(torch, ctx):
