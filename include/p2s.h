@@ -428,6 +428,11 @@ int p2s_assembly_add(p2s_assembly* A, const double* emat, double* values, void* 
 int p2s_assembly_fill(p2s_assembly* A, const p2s_geometry* geom, const p2s_material* mat,
                       double* values, void* stream);
 
+/* Assemble the element matrices of the most recent p2s_assembly_fill on this assembly again:
+ * values (device, p2s_assembly_nnz doubles) is overwritten.  Stream-ordered after that fill.
+ * Errors: P2S_ERR_ARG, P2S_ERR_CUDA. */
+int p2s_assembly_reassemble(p2s_assembly* A, double* values, void* stream);
+
 /* Wait for `stream`, then return and clear the context's device error flag:
  * P2S_OK, P2S_ERR_JACOBIAN, P2S_ERR_TIMEOUT, or P2S_ERR_CUDA if the stream failed. */
 int p2s_sync_status(p2s_ctx* ctx, void* stream);

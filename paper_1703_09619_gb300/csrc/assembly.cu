@@ -576,13 +576,19 @@ int p2s_assembly_add(p2s_assembly* A, const double* emat, double* values, void* 
     return assemble_colours(A, A->kernel, emat, values, (cudaStream_t)stream);
 }
 
+int p2s_assembly_reassemble(p2s_assembly* A, double* values, void* stream) {
+    if (!A || !values) return fail(P2S_ERR_ARG, "p2s_assembly_reassemble: NULL assembly or values");
+    P2S_CUDA(cudaSetDevice(context_tables(A->ctx)->device));
+    P2S_CUDA(cudaMemsetAsync(values, 0, sizeof(double) * A->nnz, (cudaStream_t)stream));
+    return assemble_colours(A, A->kernel_fill, A->d_emat, values, (cudaStream_t)stream);
+}
+
 int p2s_assembly_fill(p2s_assembly* A, const p2s_geometry* geom, const p2s_material* mat, double* values, void* stream) {
     if (!A || !values) return fail(P2S_ERR_ARG, "p2s_assembly_fill: NULL assembly or values");
     P2S_CUDA(cudaSetDevice(context_tables(A->ctx)->device));
     int rc = p2s_plan_fill(A->plan, geom, mat, A->d_emat, nullptr, stream);
     if (rc) return rc;
-    P2S_CUDA(cudaMemsetAsync(values, 0, sizeof(double) * A->nnz, (cudaStream_t)stream));
-    return assemble_colours(A, A->kernel_fill, A->d_emat, values, (cudaStream_t)stream);
+    return p2s_assembly_reassemble(A, values, stream);
 }
 
 }  // extern "C"

@@ -115,6 +115,7 @@ SIGNATURES = {
     "p2s_assembly_use_graph": (ctypes.c_int, [_P, ctypes.c_int]),
     "p2s_assembly_fill": (ctypes.c_int, [_P, ctypes.POINTER(Geometry), ctypes.POINTER(Material), _P, _P]),
     "p2s_assembly_add": (ctypes.c_int, [_P, _P, _P, _P]),
+    "p2s_assembly_reassemble": (ctypes.c_int, [_P, _P, _P]),
     "p2s_sync_status": (ctypes.c_int, [_P, _P]),
     "p2s_linearisation": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
     "p2s_gauss_legendre": (ctypes.c_int, [ctypes.c_int, _P, _P]),
@@ -446,6 +447,11 @@ class Assembly:
         g, m = Plan._inputs(kind, params, nodes, bulge)
         _check(load().p2s_assembly_fill(self.handle, ctypes.byref(g), ctypes.byref(m), _dptr(values),
                                         _stream(stream)), "p2s_assembly_fill")
+
+    def reassemble(self, values, stream=None):
+        """Assemble the element matrices of the last fill again into `values` (overwritten)."""
+        _check(load().p2s_assembly_reassemble(self.handle, _dptr(values), _stream(stream)),
+               "p2s_assembly_reassemble")
 
     def add(self, emat, values, stream=None):
         """Add Legendre-basis element matrices (device [E][n][n]) to `values` (not zeroed)."""

@@ -102,6 +102,22 @@ def test_assembly_deterministic_and_graph_replay(torch, ctx):
     assert all(np.array_equal(outs[0], o) for o in outs_g)
 
 
+@pytest.mark.parametrize("prec", [p2s.FP64, p2s.MIXED])
+def test_reassemble_equals_fill(torch, ctx, prec):
+    mesh = W.make_mesh(2, 3, 2, 4, 6, seed=13)
+    wl = mesh.workload
+    T, S = W.diffusion_terms()
+    asm = p2s.Assembly(ctx, 2, 3, 2, 4, 6, T, S, wl.kind, prec)
+    dp, dn, db = (torch.as_tensor(np.ascontiguousarray(a), device="cuda") for a in (wl.params, wl.nodes, wl.bulge))
+    a = torch.empty(asm.nnz, dtype=torch.float64, device="cuda")
+    b = torch.full((asm.nnz,), 7.0, dtype=torch.float64, device="cuda")
+    asm.fill(wl.kind, dp, dn, db, a)
+    asm.reassemble(b)
+    assert ctx.sync_status() == 0
+    assert torch.equal(a, b)
+    asm.close()
+
+
 def oracle_row(mesh, N, G, r):
     """Row r of the global matrix from the oracle, built from the elements that hold dof r."""
     nx, ny, nz = mesh.nx, mesh.ny, mesh.nz
