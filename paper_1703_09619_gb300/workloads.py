@@ -261,3 +261,42 @@ def judge_elements(n_elem: int, frac: float, seed: int) -> np.ndarray:
     k = int(np.ceil(frac * n_elem)) if frac > 0 else 0
     rng = np.random.default_rng(seed)
     return np.sort(rng.choice(n_elem, size=min(k, n_elem), replace=False)).astype(np.int32)
+
+
+# ----------------------------------------------------------------------------- 2-D curl-curl example
+@dataclasses.dataclass
+class Mesh2D:
+    """Structured mesh of the curved quadrilateral domain of the paper's Sec. III example: the image
+    of [-1,1]^2 under X(s, t) = (s g(t), t f(s)) with f(x) = 1 - 0.2 (x^2-1)^2 and g(y) = 1 + 0.2
+    (y^2-1)^2, so the boundary is x = +-g(y), y = +-f(x).  Element (i, j) (index j nx + i) is the
+    image of the cell [s_i, s_i+1] x [t_j, t_j+1] of a uniform nx x ny grid; params[e] = (s_lo, s_hi,
+    t_lo, t_hi, filled): the material eps_r = 2 exp(x + y + 2) fills the lower half (t < 0), eps_r = 1
+    elsewhere, mu_r = 1.  M = N = order; G Gauss-Legendre points per axis."""
+    nx: int
+    ny: int
+    order: int
+    npts: int
+    params: np.ndarray  # float64 [E][5]
+
+    @property
+    def n_elem(self):
+        return self.nx * self.ny
+
+
+def make_mesh2d(nx: int, ny: int, order: int, npts: int) -> Mesh2D:
+    if ny % 2:
+        raise ValueError("ny must be even (the material interface t = 0 lies on element edges)")
+    s = np.linspace(-1.0, 1.0, nx + 1)
+    t = np.linspace(-1.0, 1.0, ny + 1)
+    params = np.zeros((nx * ny, 5))
+    for j in range(ny):
+        for i in range(nx):
+            e = j * nx + i
+            params[e] = (s[i], s[i + 1], t[j], t[j + 1], 1.0 if t[j + 1] <= 0.0 else 0.0)
+    return Mesh2D(nx, ny, order, npts, params)
+
+
+def cheb2d_npts(order: int) -> int:
+    """Quadrature points per axis for the 2-D example: 1.5 M + 2 (the paper assumes about 2 D =
+    2 M N points per element for the direct integration, i.e. sqrt(2) M per axis)."""
+    return (3 * order + 1) // 2 + 2
