@@ -834,6 +834,91 @@ def run_assembly(args):
         dist.destroy_process_group()
 
 
+# Table I of the paper (M = N): matrix-filling reduction factor, direct / product-to-sum, measured on
+# its CPU ("from the left columns") and predicted by the Sec. IV operation count (D/15).
+TABLE_I_REDUCTION = {3: (0.96, 0.6), 4: (1.22, 1.0), 6: (2.5, 2.4), 8: (4.8, 4.25), 10: (7.25, 6.7),
+                     12: (10.0, 9.6), 14: (13.0, 13.0), 16: (15.0, 17.0), 18: (17.0, 21.6)}
+
+
+def run_cheb2d(args):
+    """The paper's 2-D curl-curl example (Sec. III): stiffness and mass element matrices of the
+    Fig. 1 domain meshed into nx x ny curved quadrilaterals, orders M = N of Table I; the
+    product-to-sum fill (FP64 and mixed) against direct numerical integration (FP64), same rule."""
+    import torch
+
+    from paper_1703_09619_gb300 import p2s
+
+    world, rank, local = dist_setup()
+    dev = torch.device("cuda", local)
+    ctx = p2s.Context(local)
+    nx, ny = (int(x) for x in args.mesh2d.split(","))
+    orders = [int(x) for x in args.orders.split(",")]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    rows, head = [], None
+    with ClockSampler(local) as clk:
+        for M in orders:
+            G = W.cheb2d_npts(M)
+            mesh = W.make_mesh2d(nx, ny, M, G)
+            n = p2s.cheb2d_dofs(M, M)
+            E = mesh.n_elem
+            dp = torch.as_tensor(mesh.params, device=dev)
+            S = torch.empty((E, n, n), dtype=torch.float64, device=dev)
+            Mm = torch.empty_like(S)
+            fill = lambda method, prec: p2s.cheb2d_fill(ctx, dp, M, M, G, S, Mm, method, prec, stream=stream)
+            times = {}
+            for key, method, prec, reps in (("p2s_mixed", p2s.CHEB2D_P2S, p2s.MIXED, args.steps),
+                                            ("p2s_fp64", p2s.CHEB2D_P2S, p2s.FP64, args.steps),
+                                            ("direct_fp64", p2s.CHEB2D_DIRECT, p2s.FP64, 1 if M >= 14 else 2)):
+                for _ in range(args.warmup if method == p2s.CHEB2D_P2S else 1):
+                    fill(method, prec)
+                torch.cuda.synchronize()
+                barrier(world)
+                ms = time_steps(lambda: fill(method, prec), reps, stream, flush)
+                times[key] = max_over_ranks(float(np.median(ms)), world, dev)
+            if ctx.sync_status(stream) != 0:
+                raise RuntimeError("device status after the %d-order fills" % M)
+            entries = 2 * E * n * n
+            ti = TABLE_I_REDUCTION.get(M)
+            rows.append({"M": M, "G": G, "dofs": n, "entries": entries, "ms": times,
+                         "gpu_reduction_fp64": times["direct_fp64"] / times["p2s_fp64"],
+                         "gpu_reduction_mixed": times["direct_fp64"] / times["p2s_mixed"],
+                         "table_I_reduction": ti[0] if ti else None, "table_I_model_D_over_15": ti[1] if ti else None})
+            head = (M, G, n, E, entries, times)
+            del S, Mm
+    clocks = clk.summary()
+    M, G, n, E, entries, times = head
+    peaks, src = load_peaks()
+    job = D.sum_over_ranks(entries, world, dev)
+    ach = 8 * entries / (times["p2s_mixed"] * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": "k_cheb2d_p2s<float-float> (order %d)" % M, "achieved": ach,
+            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
+            "peak_source": "%s copy bandwidth (MEASURED_PEAKS.json)" % src,
+            "algorithmic_bytes_per_launch": 8 * entries, "bytes_model": "every FP64 entry of S and M written once"}
+    macs = entries * G * G  # the direct method: one multiply-add per point and entry (Sec. IV)
+    dach = 2 * macs / (times["direct_fp64"] * 1e-3) / 1e12
+    roof_direct = {"bound": "alu", "kernel": "k_cheb2d_direct (order %d)" % M, "achieved": dach,
+                   "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": dach / FP64_PEAK_TFLOPS,
+                   "flop_model": "2 flop per Gauss point and entry (the paper's direct count)"}
+    if rank == 0:
+        line = {
+            "metric": "2-D curl-curl element-matrix entries/s (Sec. III example), product to sum, order %d" % M,
+            "value": job / (times["p2s_mixed"] * 1e-3), "unit": "entries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": times["p2s_mixed"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32x2", "data": "synthetic",
+            "config": {"workload": "Fig. 1 domain, %dx%d curved quadrilaterals, M = N = %d, G = %d, S and M" % (nx, ny, M, G),
+                       "elements": E, "dofs_per_element": n, "orders": orders,
+                       "l2": "outputs exceed L2 at the larger orders; L2 flushed (256 MB write) between steps"},
+            "orders": rows, "roofline": roof, "roofline_direct": roof_direct, "clocks": clocks,
+            "gpu_launches": 1,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def measure_e2e_fixed(args, wl, ctx, prec, dev, tile=None, graph=False):
     from paper_1703_09619_gb300 import p2s
     E = wl.n_elem
@@ -853,7 +938,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c5", choices=["c1", "c2", "c3", "c4", "c5"])
-    ap.add_argument("--mode", default=None, choices=["learned", "plain", "mixed", "operator", "assembly"])
+    ap.add_argument("--mode", default=None, choices=["learned", "plain", "mixed", "operator", "assembly", "cheb2d"])
+    ap.add_argument("--mesh2d", default="32,32", help="cheb2d mode: elements nx,ny (ny even)")
+    ap.add_argument("--orders", default="3,4,6,8,10,12,14,16,18", help="cheb2d mode: orders M = N (Table I)")
     ap.add_argument("--mesh", default="32,32,32", help="assembly mode: elements per axis nx,ny,nz")
     ap.add_argument("--order", type=int, default=4, help="assembly mode: order N per axis")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"], help="alias of --mode plain|mixed")
@@ -871,6 +958,9 @@ def main():
             "learned" if args.workload == "c5" else "plain")
     if args.mode == "assembly" and args.impl == "ours":
         run_assembly(args)
+        return
+    if args.mode == "cheb2d" and args.impl == "ours":
+        run_cheb2d(args)
         return
     wl = W.make(args.workload, args.elements, shard=D.env()[1])  # weak scaling: a batch per rank
     if args.npts:

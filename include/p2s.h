@@ -433,6 +433,33 @@ int p2s_assembly_fill(p2s_assembly* A, const p2s_geometry* geom, const p2s_mater
  * Errors: P2S_ERR_ARG, P2S_ERR_CUDA. */
 int p2s_assembly_reassemble(p2s_assembly* A, double* values, void* stream);
 
+/* ------------------------------------------------------------------------------------
+ * The paper's 2-D example (Sec. III): stiffness and mass element matrices of the curl-curl
+ * equation (Eq. (5)) on curved quadrilaterals, curl-conforming Chebyshev basis (Eq. (6))
+ *   E_u = U_m(u) T_n(v) (m < M, n <= N), E_v = T_m(u) U_n(v) (m <= M, n < N),
+ * S and M of Eq. (7)-(15) with mu_r = 1.  Geometry (Fig. 1): element e is the image of the
+ * cell [s_lo, s_hi] x [t_lo, t_hi] under X(s, t) = (s g(t), t f(s)), f(x) = 1 - 0.2 (x^2 - 1)^2,
+ * g(y) = 1 + 0.2 (y^2 - 1)^2; params (device [E][5]) = (s_lo, s_hi, t_lo, t_hi, filled), and
+ * eps_r = 2 exp(x + y + 2) where filled != 0, else 1.  Dofs per element: n = M (N+1) + (M+1) N,
+ * the E_u functions (m, n) at m (N+1) + n, then the E_v functions at M (N+1) + m N + n.  S and Mass
+ * (device, caller-owned, [E][n][n] row-major each, rows = testing functions) are overwritten.
+ * method P2S_CHEB2D_P2S: the product-to-sum fill (Eq. (16)-(19)): four moment sets per element
+ * then every entry as a signed sum of four moments; P2S_CHEB2D_DIRECT: direct numerical
+ * integration of every entry over the npts x npts Gauss-Legendre points (the paper's
+ * comparison method).  Both use the same rule, so they agree to rounding.  precision: P2S_FP64,
+ * or P2S_MIXED for the product-to-sum method (moments and v-axis sums in FP64, each entry formed
+ * in double-word FP32 arithmetic and rounded to FP64 once: relative error ~1e-14).  Asynchronous
+ * on `stream`; J <= 0 at a point sets the context's error flag (p2s_sync_status).  Errors:
+ * P2S_ERR_ARG (NULL, method, precision), P2S_ERR_ORDER (M, N outside 1..24, npts outside 1..48),
+ * P2S_ERR_CUDA. */
+#define P2S_CHEB2D_MAX_ORDER 24
+#define P2S_CHEB2D_MAX_NPTS 48
+#define P2S_CHEB2D_P2S 0
+#define P2S_CHEB2D_DIRECT 1
+int64_t p2s_cheb2d_dofs(int M, int N);
+int p2s_cheb2d_fill(p2s_ctx* ctx, int64_t n_elem, const double* params, int M, int N, int npts, int method,
+                    int precision, double* S, double* Mass, void* stream);
+
 /* Wait for `stream`, then return and clear the context's device error flag:
  * P2S_OK, P2S_ERR_JACOBIAN, P2S_ERR_TIMEOUT, or P2S_ERR_CUDA if the stream failed. */
 int p2s_sync_status(p2s_ctx* ctx, void* stream);

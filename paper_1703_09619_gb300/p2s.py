@@ -116,6 +116,9 @@ SIGNATURES = {
     "p2s_assembly_fill": (ctypes.c_int, [_P, ctypes.POINTER(Geometry), ctypes.POINTER(Material), _P, _P]),
     "p2s_assembly_add": (ctypes.c_int, [_P, _P, _P, _P]),
     "p2s_assembly_reassemble": (ctypes.c_int, [_P, _P, _P]),
+    "p2s_cheb2d_dofs": (_I64, [ctypes.c_int, ctypes.c_int]),
+    "p2s_cheb2d_fill": (ctypes.c_int, [_P, _I64, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, _P, _P, _P]),
     "p2s_sync_status": (ctypes.c_int, [_P, _P]),
     "p2s_linearisation": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
     "p2s_gauss_legendre": (ctypes.c_int, [ctypes.c_int, _P, _P]),
@@ -468,6 +471,24 @@ class Assembly:
             self.close()
         except Exception:
             pass
+
+
+CHEB2D_P2S, CHEB2D_DIRECT = 0, 1
+
+
+def cheb2d_dofs(M, N):
+    n = load().p2s_cheb2d_dofs(int(M), int(N))
+    if n < 0:
+        raise P2SError(int(n), "p2s_cheb2d_dofs")
+    return int(n)
+
+
+def cheb2d_fill(ctx: Context, params, M, N, npts, S, Mass, method=CHEB2D_P2S, precision=FP64, stream=None):
+    """p2s_cheb2d_fill: stiffness and mass matrices of the 2-D curl-curl example (device params
+    [E][5], outputs [E][n][n] float64 each)."""
+    _check(load().p2s_cheb2d_fill(ctx.handle, int(params.shape[0]), _dptr(params), int(M), int(N), int(npts),
+                                  int(method), int(precision), _dptr(S), _dptr(Mass), _stream(stream)),
+           "p2s_cheb2d_fill")
 
 
 def fill_elements(ctx: Context, orders, npts, kind, params, nodes, bulge, out, elem_status=None,
