@@ -434,7 +434,9 @@ int run_contract(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_
     C.op_block = op ? op->block : nullptr;
     C.op_nalpha = op ? op->nalpha : 0;
     C.out_ff = op ? PL.out_ff : 0;
-    if (PL.spec_n)
+    if (PL.spec_op)
+        P2S_CUDA(launch_contract_opn(PL.spec_op, C, PL.con_grid, PL.con_threads, PL.con_smem, s));
+    else if (PL.spec_n)
         P2S_CUDA(launch_contract_ffn(PL.spec_n, C, PL.con_grid, PL.con_threads, PL.con_smem, s));
     else
         P2S_CUDA(launch_contract(PL.precision, C, PL.con_grid, PL.con_threads, PL.con_smem, s));
@@ -865,13 +867,37 @@ int p2s_operator_plan_create(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, 
         }
         symmetric = found;
     }
+    // one component of uniform order N <= 6, mixed precision: the specialised operator kernel
+    // (compile-time runs; units are m1 slabs of at most 256 stage-3 combinations)
+    int spec_op = 0;
+    if (precision == P2S_MIXED && nc == 1 && E > 0 && ctx->T.spec_ok && !tile) {
+        const int N0 = cdesc[0].ord[0][0];
+        bool uni = N0 >= 2 && N0 <= contract_ff_max_order();
+        for (int64_t e = 0; e < E && uni; ++e)
+            for (int x = 0; x < 3; ++x) uni = uni && cdesc[e].ord[0][x] == N0;
+        if (uni) spec_op = N0;
+    }
     std::vector<ContractUnit> units;
     UnitSink sink;
     sink.vec = &units;
-    for (int64_t e = 0; e < E; ++e)
+    const int m1s = spec_op ? std::max(1, std::min(spec_op, 256 / (spec_op * spec_op * spec_op))) : 0;
+    for (int64_t e = 0; e < E; ++e) {
+        if (spec_op) {
+            for (int m1a = 0; m1a < spec_op; m1a += m1s) {
+                ContractUnit u{};
+                u.e = (int32_t)e;
+                u.tp = -1;
+                u.m1a = (int8_t)m1a;
+                u.m1n = (int8_t)std::min(m1s, spec_op - m1a);
+                u.n1n = (int8_t)spec_op;
+                sink.push(u);
+            }
+            continue;
+        }
         for (int gi = 0; gi < nc; ++gi)
             for (int gj = symmetric ? gi : 0; gj < nc; ++gj)
                 push_block(cdesc[e], (int32_t)e, gi, gj, 0, (symmetric && gi != gj) ? 0 : -1, sink, 0, tp);
+    }
     PlanLayout L = Lm;  // moment fields for reference; the contraction fields are set below
     L.n_comp = nc;
     L.types_mask = 1u;
@@ -883,6 +909,29 @@ int p2s_operator_plan_create(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, 
     const size_t limit = std::min<size_t>(ctx->T.smem_optin, 227 * 1024) - 1024;
     rc = general_contract_shape(ctx->T, E, cdesc.data(), nc, tp, true, limit, L);
     if (rc) return rc;
+    if (spec_op) {
+        size_t a, bcap, tl;
+        int combos;
+        contract_ff_shape(spec_op, m1s, a, bcap, tl, combos);
+        const int threads = (combos + 31) / 32 * 32;
+        const size_t smem = (a + bcap) * sizeof(float2);
+        const int per_sm = smem <= limit ? contract_opn_blocks_per_sm(spec_op, threads, smem) : 0;
+        if (per_sm >= 1) {
+            L.spec_op = spec_op;
+            L.a_cap = a;
+            L.b_cap = bcap;
+            L.tile_cap = 0;
+            L.con_smem = smem;
+            L.con_threads = threads;
+            L.con_grid = ctx->T.sm_count * per_sm;
+        } else {  // does not fit: the general kernel's units instead
+            units.clear();
+            sink.n = 0;
+            for (int64_t e = 0; e < E; ++e)
+                push_block(cdesc[e], (int32_t)e, 0, 0, 0, -1, sink, 0, tp);
+            L.n_units = (int64_t)units.size();
+        }
+    }
 
     p2s_plan* p = new (std::nothrow) p2s_plan();
     if (!p) return fail(P2S_ERR_OOM, "p2s_operator_plan_create: host allocation");

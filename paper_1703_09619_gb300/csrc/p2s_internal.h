@@ -161,6 +161,9 @@ int contract_ff_max_order();
 void contract_ff_shape(int N, int m1n, size_t& a_cap, size_t& b_cap, size_t& tile_cap, int& combos);
 cudaError_t launch_contract_ffn(int N, const ContractLaunch& L, int grid, int threads, size_t smem, cudaStream_t s);
 int contract_ffn_blocks_per_sm(int N, int threads, size_t smem);
+// operator plans of one component and uniform order N (2..6), mixed precision (contract_ff.cu)
+cudaError_t launch_contract_opn(int N, const ContractLaunch& L, int grid, int threads, size_t smem, cudaStream_t s);
+int contract_opn_blocks_per_sm(int N, int threads, size_t smem);
 cudaError_t init_kernel_attributes();
 
 // ------------------------------------------------------------------ plan building (api.cu)
@@ -202,6 +205,7 @@ struct PlanLayout {
     int spec_n = 0;  // > 0: the mixed contraction specialised for uniform order N
     int op = 0;      // 1: an operator plan (term list), one n x n matrix per element
     int out_ff = 0;  // operator plans, mixed precision: entries written as (hi, lo) FP32 pairs
+    int spec_op = 0; // > 0: an operator plan of one component and uniform order spec_op (k_contract_opn)
     TileParams tile;  // the tile configuration in effect
 };
 

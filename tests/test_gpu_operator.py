@@ -122,6 +122,24 @@ def test_mixed_operator_close_to_fp64(torch, ctx):
     assert rel_err(b, a, off) <= 1e-10
 
 
+@pytest.mark.parametrize("N", [2, 3, 4, 5, 6])
+def test_uniform_scalar_field_specialised_path(torch, ctx, N):
+    """One component of uniform order N <= 6, mixed: the specialised operator kernel (compile-time
+    runs, terms summed in registers), for random per-axis types and coupling entries, against the
+    oracle and against the FP64 general path."""
+    rng = np.random.default_rng(50 + N)
+    wl = W.make("c5", 3)
+    orders = np.full((3, 1, 3), N, dtype=np.int32)
+    T, S = random_terms(rng, 1, 3, 12)
+    G = N + 3
+    got, rc = gpu_op(torch, ctx, orders, wl.kind, wl.params, wl.nodes, wl.bulge, G, T, S, p2s.MIXED)
+    ref, off, _ = oracle.fill_terms(orders, wl.kind, wl.params, wl.nodes, wl.bulge, G, T, S)
+    assert rc == 0 and not np.isnan(got).any()
+    assert rel_err(got, ref, off) <= TOL[p2s.MIXED]
+    f64, _ = gpu_op(torch, ctx, orders, wl.kind, wl.params, wl.nodes, wl.bulge, G, T, S, p2s.FP64)
+    assert rel_err(got, f64, off) <= 1e-10
+
+
 def test_blocks_without_terms_are_zero(torch, ctx):
     wl = W.make("c4", 2)
     orders = np.minimum(wl.orders, 3)
