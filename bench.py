@@ -709,7 +709,9 @@ def run_operator(args, wl):
     else:  # float-float MACs: bound by FP32 issue (12 lane operations per MAC, as the moment kernel)
         ops = DW_MAC_OPS * fmas
         ach = ops / (con_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": "k_contract<ArithFF> (operator terms)", "achieved": ach,
+        uniform = bool((orders == orders[0, 0, 0]).all()) and 2 <= int(orders[0, 0, 0]) <= 6
+        kname = "k_contract_opn<%d> (operator terms)" % orders[0, 0, 0] if uniform else "k_contract<ArithFF> (operator terms)"
+        roof = {"bound": "alu", "kernel": kname, "achieved": ach,
                 "peak": FP32_PEAK_TOPS, "unit": "T FP32 lane-op/s", "frac": ach / FP32_PEAK_TOPS, "traffic": None,
                 "peak_source": "FP32 issue: 152 SMs x 128 lanes x 2.07 GHz (recipe unit counts and clock)",
                 "algorithmic_ops_per_launch": ops,
