@@ -872,7 +872,7 @@ int p2s_operator_plan_create(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, 
     int spec_op = 0;
     if (precision == P2S_MIXED && nc == 1 && E > 0 && ctx->T.spec_ok && !tile) {
         const int N0 = cdesc[0].ord[0][0];
-        bool uni = N0 >= 2 && N0 <= contract_ff_max_order();
+        bool uni = N0 >= 2 && N0 <= contract_opn_max_order();
         for (int64_t e = 0; e < E && uni; ++e)
             for (int x = 0; x < 3; ++x) uni = uni && cdesc[e].ord[0][x] == N0;
         if (uni) spec_op = N0;

@@ -16,88 +16,100 @@
 //     consecutive doubles of a row of M_t(gi,gj) per p1 (consecutive threads write
 //     consecutive chunks, so a warp's stores are contiguous), and N consecutive doubles
 //     of a row of the transposed partner block per p2.  No shared-memory tile.
-#include "arith.cuh"
-#include "p2s_internal.h"
+#include "contract_ff_stages.cuh"
 
 namespace p2s {
-
-__host__ __device__ constexpr int run_kmin(int t, int a, int b) {
-    return t == 2 ? run_kmin(1, b, a)
-         : t == 0 ? (a > b ? a - b : b - a)
-         : t == 1 ? (a == 0 ? 0 : (b >= a - 1 ? b - a + 1 : ((a - 1 - b) & 1)))
-                  : ((a == 0 || b == 0) ? 0 : ((a > b ? a - b : b - a) & 1));
-}
-
-__host__ __device__ constexpr int run_cnt(int t, int a, int b) {
-    return t == 2 ? run_cnt(1, b, a)
-         : t == 0 ? (a < b ? a : b) + 1
-         : t == 1 ? (a == 0 ? 0 : (a + b - 1 - run_kmin(1, a, b)) / 2 + 1)
-                  : ((a == 0 || b == 0) ? 0 : (a + b - 2 - run_kmin(3, a, b)) / 2 + 1);
-}
-
 namespace {
 
-constexpr int kSpec = 8;     // coefficient table extent
-constexpr int kSpecMax = 6;  // largest specialised order (N^2 FP64 results per thread in registers)
-__constant__ float2 c_runs[4][kSpec][kSpec][kSpec];  // [t][a][b][r]: coefficient of P_{kmin + 2r}
-
-// Stages 1 and 2 for one (m1, m2, q) per thread (product type TT on u, TV on v):
-//   A[l]                      = sum_k C[m1,m2,k] I[k][l][q]
-//   Bt[m1][n1][m2][n2][q]     = sum_l C[n1,n2,l] A[l]      (all n1, n2)
-template <int N, int TT, int TV = TT>
-__device__ __forceinline__ void stages12(const float2* __restrict__ sI, float2* __restrict__ sB, int m1a, int m1n,
-                                         int tid, int nth) {
-    constexpr int K = 2 * N - 1;
-    const int items = m1n * N * K;
-    for (int it = tid; it < items; it += nth) {
-        const int q = it % K, mm = it / K;
-        const int m2 = mm % N, im1 = mm / N;
-        const int m1 = m1a + im1;
-        const int k0 = run_kmin(TT, m1, m2), cnt = run_cnt(TT, m1, m2);
-        float2 A[K];
-        if (cnt > 0) {
-            const float2 c = c_runs[TT][m1][m2][0];
-            const float2* Ik = sI + k0 * K * K + q;
+// Rows p1 in [P1A, P1A + NP) of one combination: v[i][p2] = sum_q C_TT[p1,p2,q] b[q], p1 = P1A + i.
+template <int N, int TT, int P1A, int NP>
+__device__ __forceinline__ void stage3_rows(const float2 (&b)[2 * N - 1], double (&v)[NP][N]) {
 #pragma unroll
-            for (int l = 0; l < K; ++l) A[l] = ArithFF::mul(c, Ik[l * K]);
+    for (int i = 0; i < NP; ++i)
+#pragma unroll
+        for (int p2 = 0; p2 < N; ++p2) {
+            const int p1 = P1A + i;
+            const int q0 = run_kmin(TT, p1, p2), qc = run_cnt(TT, p1, p2);
+            float2 acc = qc > 0 ? ArithFF::mul(c_runs[TT][p1][p2][0], b[q0]) : ArithFF::zero();
+#pragma unroll
+            for (int r = 1; r < N; ++r)
+                if (r < qc) ArithFF::fma_acc(acc, c_runs[TT][p1][p2][r], b[q0 + 2 * r]);
+            v[i][p2] = ArithFF::to_double_fast(ArithFF::finish(acc));
+        }
+}
+
+// Store rows [P1A, P1A + NP) of one combination in both orientations.
+template <int N, int P1A, int NP>
+__device__ __forceinline__ void stage3_store(const double (&v)[NP][N], double* r1, double* r2, int64_t n, bool vec,
+                                             bool vec4) {
+    if (N == 4 && NP == 4 && vec4) {  // one whole 32-byte sector per store
+#pragma unroll
+        for (int i = 0; i < NP; ++i) st_cs_v4(r1 + (P1A + i) * n, v[i][0], v[i][1 % N], v[i][2 % N], v[i][3 % N]);
+    } else if (vec) {
+#pragma unroll
+        for (int i = 0; i < NP; ++i)
+#pragma unroll
+            for (int p2 = 0; p2 < N; p2 += 2)
+                __stcs(reinterpret_cast<double2*>(r1 + (P1A + i) * n + p2), make_double2(v[i][p2], v[i][(p2 + 1) % N]));
+    } else {
+#pragma unroll
+        for (int i = 0; i < NP; ++i)
+#pragma unroll
+            for (int p2 = 0; p2 < N; ++p2) __stcs(r1 + (P1A + i) * n + p2, v[i][p2]);
+    }
+    if (r2) {
+        if (N == 4 && NP == 4 && vec4) {
+#pragma unroll
+            for (int p2 = 0; p2 < N; ++p2)
+                st_cs_v4(r2 + p2 * n, v[0][p2], v[1 % NP][p2], v[2 % NP][p2], v[3 % NP][p2]);
+        } else if (vec && P1A % 2 == 0 && NP % 2 == 0) {
+#pragma unroll
+            for (int p2 = 0; p2 < N; ++p2)
+#pragma unroll
+                for (int i = 0; i < NP; i += 2)
+                    __stcs(reinterpret_cast<double2*>(r2 + p2 * n + P1A + i), make_double2(v[i][p2], v[(i + 1) % NP][p2]));
         } else {
 #pragma unroll
-            for (int l = 0; l < K; ++l) A[l] = ArithFF::zero();
+            for (int p2 = 0; p2 < N; ++p2)
+#pragma unroll
+                for (int i = 0; i < NP; ++i) __stcs(r2 + p2 * n + P1A + i, v[i][p2]);
         }
-        for (int r = 1; r < cnt; ++r) {
-            const float2 c = c_runs[TT][m1][m2][r];
-            const float2* Ik = sI + (k0 + 2 * r) * K * K + q;
-#pragma unroll
-            for (int l = 0; l < K; ++l) ArithFF::fma_acc(A[l], c, Ik[l * K]);
-        }
-#pragma unroll
-        for (int l = 0; l < K; ++l) A[l] = ArithFF::finish(A[l]);
-        float2* dst = sB + ((size_t)(im1 * N) * N + m2) * N * K + q;
-#pragma unroll
-        for (int n1 = 0; n1 < N; ++n1)
-#pragma unroll
-            for (int n2 = 0; n2 < N; ++n2) {
-                const int l0 = run_kmin(TV, n1, n2), lc = run_cnt(TV, n1, n2);
-                float2 acc = lc > 0 ? ArithFF::mul(c_runs[TV][n1][n2][0], A[l0]) : ArithFF::zero();
-#pragma unroll
-                for (int r = 1; r < N; ++r)
-                    if (r < lc) ArithFF::fma_acc(acc, c_runs[TV][n1][n2][r], A[l0 + 2 * r]);
-                dst[((size_t)n1 * N * N + n2) * K] = ArithFF::finish(acc);
-            }
     }
 }
 
-// Stage 3 and both write-outs for one (m1, n1, m2, n2) combination per thread.
+// Stage 3 and both write-outs; one (m1, n1, m2, n2) combination per item.  Orders N >= 7 split
+// each combination's p1 rows over two items (halves of ceil(N/2) and floor(N/2) rows), so a
+// thread holds at most ceil(N/2) x N results in registers.
 // Mt points at (row rbase, column col0) of M_t; Mp (or nullptr) at (row col0, column
 // rbase) of the partner block; n is the row stride of the element's matrices.
-// Streaming 256-bit store of four doubles (a whole 32-byte sector; p 32-byte aligned).  Two
-// 16-byte stores per sector would send each sector to L2 in two halves.
-__device__ __forceinline__ void st_cs_v4(double* p, double a, double b, double c, double d) {
-    asm volatile("st.global.cs.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(p), "d"(a), "d"(b), "d"(c), "d"(d) : "memory");
+template <int N, int TT>
+__device__ __forceinline__ void stage3_split(const float2* __restrict__ sB, int m1n, int tid, int nth, double* Mt,
+                                             double* Mp, int64_t n, bool vec, bool vec4) {
+    constexpr int K = 2 * N - 1, MJ = N * N, H = N >= 7 ? 2 : 1, P0 = (N + H - 1) / H, P1 = N - P0;
+    const int ncombo = m1n * N * MJ;
+    for (int it = tid; it < ncombo * H; it += nth) {
+        const int c = H == 2 ? it >> 1 : it, h = H == 2 ? it & 1 : 0;
+        const int mn = c / MJ, mj = c - mn * MJ;  // mn = im1 * N + n1, mj = m2 * N + n2
+        float2 b[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q) b[q] = sB[(size_t)c * K + q];
+        double* r1 = Mt + (int64_t)(mn * N) * n + mj * N;                // row (m1,n1,p1=0), column (m2,n2,p2=0)
+        double* r2 = Mp ? Mp + (int64_t)(mj * N) * n + mn * N : nullptr;  // partner row (m2,n2,p2=0)
+        if (h == 0) {
+            double v[P0][N];
+            stage3_rows<N, TT, 0, P0>(b, v);
+            stage3_store<N, 0, P0>(v, r1, r2, n, vec, vec4);
+        } else if constexpr (P1 > 0) {
+            double v[P1 > 0 ? P1 : 1][N];
+            stage3_rows<N, TT, P0, (P1 > 0 ? P1 : 1)>(b, v);
+            stage3_store<N, P0, (P1 > 0 ? P1 : 1)>(v, r1, r2, n, vec, vec4);
+        }
+    }
 }
 
+// Orders up to 6 keep all N x N results of a combination in one thread (stage3_full).
 template <int N, int TT>
-__device__ __forceinline__ void stage3(const float2* __restrict__ sB, int m1n, int tid, int nth, double* Mt,
+__device__ __forceinline__ void stage3_full(const float2* __restrict__ sB, int m1n, int tid, int nth, double* Mt,
                                        double* Mp, int64_t n, bool vec, bool vec4) {
     constexpr int K = 2 * N - 1, MJ = N * N;
     const int ncombo = m1n * N * MJ;
@@ -153,6 +165,13 @@ __device__ __forceinline__ void stage3(const float2* __restrict__ sB, int m1n, i
             }
         }
     }
+}
+
+template <int N, int TT>
+__device__ __forceinline__ void stage3(const float2* __restrict__ sB, int m1n, int tid, int nth, double* Mt,
+                                       double* Mp, int64_t n, bool vec, bool vec4) {
+    if constexpr (N >= 7) stage3_split<N, TT>(sB, m1n, tid, nth, Mt, Mp, n, vec, vec4);
+    else stage3_full<N, TT>(sB, m1n, tid, nth, Mt, Mp, n, vec, vec4);
 }
 
 __device__ __forceinline__ int type_slot_ff(uint32_t mask, int t) { return __popc(mask & ((1u << t) - 1u)); }
@@ -256,156 +275,6 @@ __global__ void __launch_bounds__(512) k_contract_ffn(ContractLaunch L) {
     }
 }
 
-// ---------------------------------------------------------------------------------------------
-// Operator fills (term lists) of one field component of uniform order N: the same stages with
-// each term's per-axis product types (tu on u, tv on v in stages 1-2, tw on w in stage 3).  A
-// unit is an m1 slab of the element's single block; every thread owns one (m1, n1, m2, n2)
-// combination and keeps its N x N (p1, p2) results in float-float registers across the terms, so
-// the terms add without a shared-memory tile and the rows are written once.  Each term's
-// moments (its coupling pair) are staged with the term's scale folded in.
-
-// acc[p1][p2] += sum_q C_tw[p1,p2,q] b[q] for one combination
-template <int N, int TW>
-__device__ __forceinline__ void stage3_acc(const float2* __restrict__ b, float2 (&acc)[N][N]) {
-#pragma unroll
-    for (int p1 = 0; p1 < N; ++p1)
-#pragma unroll
-        for (int p2 = 0; p2 < N; ++p2) {
-            const int q0 = run_kmin(TW, p1, p2), qc = run_cnt(TW, p1, p2);
-#pragma unroll
-            for (int r = 0; r < N; ++r)
-                if (r < qc) ArithFF::fma_acc(acc[p1][p2], c_runs[TW][p1][p2][r], b[q0 + 2 * r]);
-        }
-}
-
-template <int N>
-__device__ __forceinline__ void stages12_op(int tu, int tv, const float2* sI, float2* sB, int m1a, int m1n, int tid,
-                                            int nth) {
-    switch (tu * 4 + tv) {
-#define P2S_S12(a, b) case a * 4 + b: stages12<N, a, b>(sI, sB, m1a, m1n, tid, nth); break;
-        P2S_S12(0, 0) P2S_S12(0, 1) P2S_S12(0, 2) P2S_S12(0, 3)
-        P2S_S12(1, 0) P2S_S12(1, 1) P2S_S12(1, 2) P2S_S12(1, 3)
-        P2S_S12(2, 0) P2S_S12(2, 1) P2S_S12(2, 2) P2S_S12(2, 3)
-        P2S_S12(3, 0) P2S_S12(3, 1) P2S_S12(3, 2) P2S_S12(3, 3)
-#undef P2S_S12
-    default: break;
-    }
-}
-
-template <int N>
-__global__ void __launch_bounds__(256, 2) k_contract_opn(ContractLaunch L) {
-    constexpr int K = 2 * N - 1, K3 = K * K * K, MJ = N * N;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    float2* sI = reinterpret_cast<float2*>(smraw);
-    float2* sB = sI + L.a_cap;
-    __shared__ ContractUnit s_cu;
-    __shared__ int s_term[64];
-    __shared__ float s_scale[64][2];
-    const int tid = threadIdx.x, nth = blockDim.x;
-    const unsigned long long nu = (unsigned long long)L.n_units;
-    const bool out_aligned32 = (reinterpret_cast<uintptr_t>(L.out) & 31) == 0;
-    const int term0 = L.op_block[0], n_terms = L.op_block[1];
-    for (;;) {
-        if (tid == 0) {
-            const unsigned long long a = atomicAdd(L.counter, 1ull);
-            ContractUnit u{};
-            u.e = -1;
-            s_cu = a < nu ? L.units[a] : u;
-        }
-        __syncthreads();
-        const ContractUnit cu = s_cu;
-        if (cu.e < 0) break;
-        const ElemDesc* d = L.desc + cu.e;
-        const int m1a = cu.m1a, m1n = cu.m1n;
-        const int64_t n = d->n;
-        const int ncombo = m1n * N * MJ;
-        float2 acc[N][N];
-#pragma unroll
-        for (int p1 = 0; p1 < N; ++p1)
-#pragma unroll
-            for (int p2 = 0; p2 < N; ++p2) acc[p1][p2] = ArithFF::zero();
-        for (int kt0 = 0; kt0 < n_terms; kt0 += 64) {
-            const int nk = min(64, n_terms - kt0);
-            if (tid < nk) {  // the terms of this batch: packed types and the scale as (hi, lo)
-                s_term[tid] = __ldg(L.op_terms + term0 + kt0 + tid);
-                const double sc = __ldg(L.op_scales + term0 + kt0 + tid);
-                const float hi = (float)sc;
-                s_scale[tid][0] = hi;
-                s_scale[tid][1] = (float)(sc - (double)hi);
-            }
-            __syncthreads();
-            for (int kt = 0; kt < nk; ++kt) {
-                const int32_t pk = s_term[kt];
-                const int sp = pair_index(pk & 15, (pk >> 4) & 15, L.op_nalpha);
-                const int tu = (pk >> 8) & 15, tv = (pk >> 12) & 15, tw = (pk >> 16) & 15;
-                const float sh = s_scale[kt][0], sl = s_scale[kt][1];
-                const float2* gI = reinterpret_cast<const float2*>(L.mom) + d->mom_off + d->pair_off[sp];
-                for (int i = tid; i < K3; i += nth) sI[i] = ArithFF::scaled(__ldg(gI + i), 0.0, sh, sl);
-                __syncthreads();
-                stages12_op<N>(tu, tv, sI, sB, m1a, m1n, tid, nth);
-                __syncthreads();
-                if (tid < ncombo) {
-                    float2 b[K];
-#pragma unroll
-                    for (int q = 0; q < K; ++q) b[q] = sB[(size_t)tid * K + q];
-                    switch (tw) {
-                    case 0: stage3_acc<N, 0>(b, acc); break;
-                    case 1: stage3_acc<N, 1>(b, acc); break;
-                    case 2: stage3_acc<N, 2>(b, acc); break;
-                    default: stage3_acc<N, 3>(b, acc); break;
-                    }
-                }
-                __syncthreads();  // sI and sB are reused by the next term
-            }
-        }
-        if (tid < ncombo) {
-            const int mn = tid / MJ, mj = tid - mn * MJ;  // mn = im1 * N + n1, mj = m2 * N + n2
-            double* r1 = L.out + d->out_off + (int64_t)(m1a * MJ + mn * N) * n + mj * N;
-            if (L.out_ff) {  // float-float pairs in the 8-byte slots, for a float-float consumer
-#pragma unroll
-                for (int p1 = 0; p1 < N; ++p1)
-#pragma unroll
-                    for (int p2 = 0; p2 < N; ++p2)
-                        __stcs(reinterpret_cast<float2*>(r1 + p1 * n + p2), ArithFF::finish(acc[p1][p2]));
-            } else {
-                double v[N][N];
-#pragma unroll
-                for (int p1 = 0; p1 < N; ++p1)
-#pragma unroll
-                    for (int p2 = 0; p2 < N; ++p2) v[p1][p2] = ArithFF::to_double_fast(ArithFF::finish(acc[p1][p2]));
-                bool done = false;
-                if constexpr (N == 4) {  // one whole 32-byte sector per store
-                    if (out_aligned32 && (n % 4 == 0) && (d->out_off % 4 == 0)) {
-#pragma unroll
-                        for (int p1 = 0; p1 < N; ++p1) st_cs_v4(r1 + p1 * n, v[p1][0], v[p1][1], v[p1][2], v[p1][3]);
-                        done = true;
-                    }
-                }
-                if (!done) {
-#pragma unroll
-                    for (int p1 = 0; p1 < N; ++p1)
-#pragma unroll
-                        for (int p2 = 0; p2 < N; ++p2) __stcs(r1 + p1 * n + p2, v[p1][p2]);
-                }
-            }
-        }
-        __syncthreads();  // s_cu is replaced by thread 0
-    }
-}
-
-template <int N>
-cudaError_t set_attr_op() {
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e != cudaSuccess) return e;
-    cudaFuncAttributes fa;
-    e = cudaFuncGetAttributes(&fa, k_contract_opn<N>);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_contract_opn<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                optin - (int)fa.sharedSizeBytes);
-}
-
 template <int N>
 cudaError_t set_attr() {
     cudaFuncAttributes fa;
@@ -446,13 +315,16 @@ cudaError_t contract_ff_upload(const HostTables& T) {
                 }
     cudaError_t e = cudaMemcpyToSymbol(c_runs, h, sizeof(h));
     if (e != cudaSuccess) return e;
-    for (cudaError_t r : {set_attr<2>(), set_attr<3>(), set_attr<4>(), set_attr<5>(), set_attr<6>(), set_attr_op<2>(),
-                          set_attr_op<3>(), set_attr_op<4>(), set_attr_op<5>(), set_attr_op<6>()})
+    for (cudaError_t r : {set_attr<2>(), set_attr<3>(), set_attr<4>(), set_attr<5>(), set_attr<6>(), set_attr<7>(),
+                          set_attr<8>()})
         if (r != cudaSuccess) return r;
+    e = contract_opn_upload(h, sizeof(h));
+    if (e != cudaSuccess) return e;
     return cudaSuccess;
 }
 
 int contract_ff_max_order() { return kSpecMax; }
+int contract_opn_max_order() { return kSpecOpMax; }
 
 void contract_ff_shape(int N, int m1n, size_t& a_cap, size_t& b_cap, size_t& tile_cap, int& combos) {
     const int K = 2 * N - 1;
@@ -462,7 +334,7 @@ void contract_ff_shape(int N, int m1n, size_t& a_cap, size_t& b_cap, size_t& til
     combos = m1n * N * N * N;
 }
 
-#define P2S_FFN_CASES(X) X(2) X(3) X(4) X(5) X(6)
+#define P2S_FFN_CASES(X) X(2) X(3) X(4) X(5) X(6) X(7) X(8)
 
 cudaError_t launch_contract_ffn(int N, const ContractLaunch& L, int grid, int threads, size_t smem, cudaStream_t s) {
     switch (N) {
@@ -472,28 +344,6 @@ cudaError_t launch_contract_ffn(int N, const ContractLaunch& L, int grid, int th
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
-}
-
-cudaError_t launch_contract_opn(int N, const ContractLaunch& L, int grid, int threads, size_t smem, cudaStream_t s) {
-    switch (N) {
-#define X(n) case n: k_contract_opn<n><<<grid, threads, smem, s>>>(L); break;
-        P2S_FFN_CASES(X)
-#undef X
-    default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
-
-int contract_opn_blocks_per_sm(int N, int threads, size_t smem) {
-    int nb = 0;
-    cudaError_t e = cudaErrorInvalidValue;
-    switch (N) {
-#define X(n) case n: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_contract_opn<n>, threads, smem); break;
-        P2S_FFN_CASES(X)
-#undef X
-    default: break;
-    }
-    return e == cudaSuccess ? nb : 0;
 }
 
 int contract_ffn_blocks_per_sm(int N, int threads, size_t smem) {

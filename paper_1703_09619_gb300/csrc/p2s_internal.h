@@ -158,12 +158,15 @@ int moments_blocks_per_sm(size_t smem);
 bool contract_ff_runs_match(const HostTables& T);
 cudaError_t contract_ff_upload(const HostTables& T);
 int contract_ff_max_order();
+int contract_opn_max_order();
 void contract_ff_shape(int N, int m1n, size_t& a_cap, size_t& b_cap, size_t& tile_cap, int& combos);
 cudaError_t launch_contract_ffn(int N, const ContractLaunch& L, int grid, int threads, size_t smem, cudaStream_t s);
 int contract_ffn_blocks_per_sm(int N, int threads, size_t smem);
 // operator plans of one component and uniform order N (2..6), mixed precision (contract_ff.cu)
 cudaError_t launch_contract_opn(int N, const ContractLaunch& L, int grid, int threads, size_t smem, cudaStream_t s);
 int contract_opn_blocks_per_sm(int N, int threads, size_t smem);
+// fills contract_opn.cu's copy of the coefficient runs ([4][8][8][8] (hi, lo) pairs)
+cudaError_t contract_opn_upload(const void* runs, size_t bytes);
 cudaError_t init_kernel_attributes();
 
 // ------------------------------------------------------------------ plan building (api.cu)
