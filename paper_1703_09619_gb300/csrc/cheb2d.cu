@@ -263,6 +263,19 @@ __device__ __forceinline__ dw c2_combine_dw(const float2* V, Fac<float> f) {
     const float2 x = V[f.o0], y = V[f.o1];
     return dw_mul_f(dw_add_fast(dw{x.x, x.y}, dw{f.sgn * y.x, f.sgn * y.y}), f.c);
 }
+// A factor in one int (o0, o1 < 2^15; the sign as 0, 1 = +1, 2 = -1 in bits 30-31) and its scale.
+__device__ __forceinline__ int pack_fac(Fac<float> f) {
+    return f.o0 | (f.o1 << 15) | ((f.sgn == 0.f ? 0 : (f.sgn > 0.f ? 1 : 2)) << 30);
+}
+__device__ __forceinline__ Fac<float> unpack_fac(int p, float c) {
+    Fac<float> f;
+    f.o0 = p & 0x7fff;
+    f.o1 = (p >> 15) & 0x7fff;
+    const int g = (p >> 30) & 3;
+    f.c = c;
+    f.sgn = g == 0 ? 0.f : (g == 1 ? 1.f : -1.f);
+    return f;
+}
 __device__ __forceinline__ double c2_combine(const float2* V, Fac<float> f) {
     const dw r = c2_combine_dw(V, f);
     return ArithFF::to_double_fast(make_float2(r.hi, r.lo));
@@ -341,9 +354,26 @@ __global__ void __launch_bounds__(kC2P2SThreads, 2) k_cheb2d_p2s(C2Launch L) {
                 double* Mrow = Me + (int64_t)r * n + c0;
                 const VT* VS = sV + (0 * 2 + cb) * VB;
                 const VT* VM = sV + (1 * 2 + cb) * VB;
-                for (int j = lane; j < count; j += 32) {
-                    __stcs(Srow + j, c2_combine(VS + n2, to_fac(s_axis_u<CT>(rb, cb, m1, m2), N + 1)));
-                    __stcs(Mrow + j, c2_combine(VM + n2, to_fac(m_axis_u<CT>(rb, cb, m1, m2), N + 1)));
+                // the row's u-axis factors for every m2, lane m2 holding those of m2 (m2 <= M <= 24);
+                // each entry takes its own by two shuffles per matrix (uniform trip counts below)
+                int pS = 0, pM = 0;
+                float cS = 0.f, cM = 0.f;
+                if (lane <= M) {
+                    const Fac<CT> fs = to_fac(s_axis_u<CT>(rb, cb, m1, lane), N + 1);
+                    const Fac<CT> fm = to_fac(m_axis_u<CT>(rb, cb, m1, lane), N + 1);
+                    pS = pack_fac(fs);
+                    cS = fs.c;
+                    pM = pack_fac(fm);
+                    cM = fm.c;
+                }
+                for (int j0 = 0; j0 < count; j0 += 32) {
+                    const int j = j0 + lane, src = min(m2, M);
+                    const Fac<CT> fs = unpack_fac(__shfl_sync(0xffffffffu, pS, src), __shfl_sync(0xffffffffu, cS, src));
+                    const Fac<CT> fm = unpack_fac(__shfl_sync(0xffffffffu, pM, src), __shfl_sync(0xffffffffu, cM, src));
+                    if (j < count) {
+                        __stcs(Srow + j, c2_combine(VS + n2, fs));
+                        __stcs(Mrow + j, c2_combine(VM + n2, fm));
+                    }
                     m2 += sm2;
                     n2 += sn2;
                     if (n2 >= cw) { n2 -= cw; ++m2; }
