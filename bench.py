@@ -735,6 +735,16 @@ def run_operator(args, wl):
         }
     del out, mom
     plan.close()
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        sub = wl.subset(np.arange(min(16, wl.n_elem)))
+        threads = oracle.default_threads()
+        t0 = time.perf_counter()
+        _, off, _ = oracle.fill_terms(np.ascontiguousarray(sub.orders[:, :1, :]), sub.kind, sub.params, sub.nodes,
+                                      sub.bulge, npts if np.isscalar(npts) else sub.npts, terms, scales, threads)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": float(off[-1]) / dt, "unit": "entries/s", "cores": threads, "kind": "oracle",
+                                "sample": "first %d elements, every entry of the operator (%.1f s)" % (sub.n_elem, dt)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -828,6 +838,18 @@ def run_assembly(args):
         }
     del vals
     asm.close()
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        from oracle import assembly as oasm
+        sm = W.make_mesh(4, 4, 4, N, G, seed=7)
+        sw = sm.workload
+        threads = oracle.default_threads()
+        t0 = time.perf_counter()
+        out, _, _ = oracle.fill_terms(sw.orders, sw.kind, sw.params, sw.nodes, sw.bulge, G, terms, scales, threads)
+        oasm.assemble(4, 4, 4, N, out.reshape(sw.n_elem, n, n))
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": sw.n_elem * n * n / dt, "unit": "entries/s", "cores": threads, "kind": "oracle",
+                                "sample": "a 4x4x4 mesh of the same recipe: oracle fill + dense assembly (%.1f s)" % dt}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -914,6 +936,14 @@ def run_cheb2d(args):
             "orders": rows, "roofline": roof, "roofline_direct": roof_direct, "clocks": clocks,
             "gpu_launches": 1,
         }
+        if world == 1 and not args.no_cpu:
+            from oracle import cheb2d as oc2
+            mesh = W.make_mesh2d(nx, ny, M, G)
+            t0 = time.perf_counter()
+            oc2.element_matrices(mesh.params[0], M, M, G)
+            dt = time.perf_counter() - t0
+            line["cpu_baseline"] = {"value": 2 * n * n / dt, "unit": "entries/s", "cores": 1, "kind": "oracle",
+                                    "sample": "element 0 at order %d: S and M by direct sums in numpy (%.1f s)" % (M, dt)}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
