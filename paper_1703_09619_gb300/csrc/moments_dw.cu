@@ -367,6 +367,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_moments_dw(MomentLaunch L) {
     const int aS = alpha_buf(L.n_pairs), t1S = t1_buf(L.n_pairs, L.kb), t2S = t2_buf(L.n_pairs, L.kb);
 
     __shared__ long long s_elem;
+    __shared__ int s_tabG, s_tabK;  // G and K of the 1-D tables in shared memory (-1: none yet)
+    if (tid == 0) {
+        s_tabG = -1;
+        s_tabK = -1;
+    }
+    __syncthreads();
     for (int64_t es = blockIdx.x;; es += gridDim.x) {
         int64_t e = es;
         if (L.counter) {  // dynamic element queue: the next element to whichever CTA is free
@@ -384,7 +390,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_moments_dw(MomentLaunch L) {
         const int Kb = max(Ku, max(Kv, Kw));
         if (tid == 0) bad_jac = 0;
         const double* prm = L.params + 4 * e;
-        if (tid < G) {  // 1-D tables, FP64 once per node, then split
+        // the 1-D tables depend on G and K alone for the metric kind: kept while consecutive
+        // elements of this CTA share them (the queue hands out elements grouped by G)
+        const bool keep = metric && s_tabG == G && s_tabK == Kb;
+        if (tid < G && !keep) {  // 1-D tables, FP64 once per node, then split
             const double x = L.gl_x[G * kMaxG + tid], w = L.gl_w[G * kMaxG + tid];
             S.xq[tid] = dw_from_double(x);
             double p0 = 1.0, p1 = x;
@@ -408,9 +417,38 @@ __global__ void __launch_bounds__(kThreads, 3) k_moments_dw(MomentLaunch L) {
                 S.t1[tid] = dw_from_double(-1.5707963267948966 * sx);  // d/dx cos(pi x / 2)
             }
         }
-        if (metric && tid == 0) metric_geo(L.nodes + 24 * e, L.bulge ? L.bulge + 4 * e : nullptr, prm, S.geo64);
+        if (metric) {  // trilinear coefficients, one (coordinate, monomial) per thread, then the rest
+            const double* X = L.nodes + 24 * e;
+            if (tid < 24) {
+                const int i = tid >> 3, j = tid & 7;
+                double c = 0.0;
+                for (int nd = 0; nd < 8; ++nd) {
+                    const double su = (nd & 1) ? 1.0 : -1.0, sv = (nd & 2) ? 1.0 : -1.0, sw = (nd & 4) ? 1.0 : -1.0;
+                    const double sgn = j == 0 ? 1.0 : j == 1 ? su : j == 2 ? sv : j == 3 ? sw
+                                     : j == 4 ? su * sv : j == 5 ? su * sw : j == 6 ? sv * sw : su * sv * sw;
+                    c += sgn * (0.125 * X[3 * nd + i]);
+                }
+                S.geo64[tid] = c;
+            } else if (tid < 27) {
+                const double* bg = L.bulge ? L.bulge + 4 * e : nullptr;
+                S.geo64[tid] = bg ? bg[0] * bg[1 + (tid - 24)] : 0.0;
+            }
+        }
         __syncthreads();
-        if (metric && tid < kGeoDW) S.geo[tid] = dw_from_double(S.geo64[tid]);
+        if (metric && tid < kGeoDW) {
+            // geo layout: 0..23 coefficients of x, y, z; 24..26 bulge vector; 27 eps amplitude;
+            // 31..38 coefficients of the phase k.x; 39 the phase of the bulge
+            double g = 0.0;
+            if (tid < 27) g = S.geo64[tid];
+            else if (tid == 27) g = prm[0];
+            else if (tid >= 31 && tid < 39) g = prm[1] * S.geo64[tid - 31] + prm[2] * S.geo64[tid - 23] + prm[3] * S.geo64[tid - 15];
+            else if (tid == 39) g = prm[1] * S.geo64[24] + prm[2] * S.geo64[25] + prm[3] * S.geo64[26];
+            S.geo[tid] = dw_from_double(g);
+        }
+        if (tid == 0) {
+            s_tabG = metric ? G : -1;
+            s_tabK = Kb;
+        }
         __syncthreads();
 
         const bool spec = metric && np == 6 && Ku == 7 && Kv == 7 && Kw == 7 && L.iacc_cap >= 6 * 343;
