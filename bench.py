@@ -791,14 +791,26 @@ def run_assembly(args):
     barrier(world)
     total_ms = max_over_ranks(float(sum(ms)), world, dev)
     clocks = clk.summary()
-    # the assembly stage alone (memset + 8 colour launches) on the last fill's element matrices
+    # the assembly stage alone on the last fill: memset + 8 colour launches (fused: the operator
+    # contraction from the kept moments + basis change + scatter; otherwise the assembly kernel)
     a = time_steps(lambda: asm.reassemble(vals, stream=stream), 3, stream, flush)
     add_ms = float(np.mean(a))
     fill_ms = total_ms / args.steps - add_ms
     n = N ** 3
     E = wl.n_elem
     contributions = E * n * n
-    if prec == p2s.MIXED:
+    if asm.fused:  # contraction + basis change + scatter in one kernel: the double-word MACs dominate
+        fmas = operator_fma_count(wl.orders, terms, symmetric=True)
+        ops = DW_MAC_OPS * fmas
+        ach = ops / (add_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_opn_assemble<%d> (memset + 8 colour launches)" % N, "achieved": ach,
+                "peak": FP32_PEAK_TOPS, "unit": "T FP32 lane-op/s", "frac": ach / FP32_PEAK_TOPS, "traffic": None,
+                "peak_source": "FP32 issue: 152 SMs x 128 lanes x 2.07 GHz (recipe unit counts and clock)",
+                "algorithmic_ops_per_launch": ops,
+                "op_model": "%d per float-float MAC x %d MACs of the operator contraction (basis change and "
+                            "scatter not counted)" % (DW_MAC_OPS, fmas),
+                "hbm_values_GBs": 16 * asm.nnz / (add_ms * 1e-3) / 1e9}
+    elif prec == p2s.MIXED:
         peaks, src = load_peaks()
         alg_bytes = 8 * contributions + 8 * asm.nnz
         ach = alg_bytes / (add_ms * 1e-3) / 1e9
@@ -823,7 +835,9 @@ def run_assembly(args):
                "element_entries": contributions, "precision": "fp64" if prec == p2s.FP64 else "mixed",
                "basis": "hierarchic C0 (vertex + integrated Legendre)",
                "scatter": "8 lattice colours, one red.global.add.f64 per entry (at most one per position and colour)",
-               "launch": "fill from a CUDA graph, memset, 8 colour launches",
+               "launch": ("moments, memset, 8 colour launches of the fused contraction + assembly" if asm.fused
+                          else "fill from a CUDA graph, memset, 8 colour launches"),
+               "path": "fused (no element-matrix scratch)" if asm.fused else "fill, then assembly",
                "l2": "global values (%.2f GB) and element matrices (%.2f GB) exceed L2; L2 flushed between steps"
                      % (8e-9 * asm.nnz, 8e-9 * contributions)}
         line = {
@@ -834,22 +848,22 @@ def run_assembly(args):
             "dtype": "f64" if prec == p2s.FP64 else "f32x2", "data": "synthetic", "config": cfg,
             "nnz_per_s": D.sum_over_ranks(asm.nnz, world, dev) * args.steps / (total_ms * 1e-3),
             "roofline": roof, "stages": {"fill_ms": fill_ms, "assemble_ms": add_ms}, "clocks": clocks,
-            "gpu_launches": 10 * args.steps,  # moments, contraction, 8 colours
+            "gpu_launches": (9 if asm.fused else 10) * args.steps,  # moments (+ contraction), 8 colours
         }
     del vals
     asm.close()
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
         from oracle import assembly as oasm
-        sm = W.make_mesh(4, 4, 4, N, G, seed=7)
+        sm = W.make_mesh(6, 6, 6, N, G, seed=7)
         sw = sm.workload
         threads = oracle.default_threads()
         t0 = time.perf_counter()
         out, _, _ = oracle.fill_terms(sw.orders, sw.kind, sw.params, sw.nodes, sw.bulge, G, terms, scales, threads)
-        oasm.assemble(4, 4, 4, N, out.reshape(sw.n_elem, n, n))
+        oasm.assemble(6, 6, 6, N, out.reshape(sw.n_elem, n, n))
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": sw.n_elem * n * n / dt, "unit": "entries/s", "cores": threads, "kind": "oracle",
-                                "sample": "a 4x4x4 mesh of the same recipe: oracle fill + dense assembly (%.1f s)" % dt}
+                                "sample": "a 6x6x6 mesh of the same recipe: oracle fill + dense assembly (%.1f s)" % dt}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

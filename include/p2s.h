@@ -404,14 +404,22 @@ int p2s_assembly_structure_host(int nx, int ny, int nz, int order, int64_t* rows
 /* Plan the assembly: an operator plan of the mesh's elements (npts-point rule, precision,
  * material kind, n_terms terms of field component 0, host, read during the call), the CSR
  * row pointers and 1-D rank tables on the device, and scratch for the element matrices
- * (E N^6 doubles).  Errors: as p2s_operator_plan_create and p2s_assembly_structure_host. */
+ * (E N^6 doubles; none on the fused path, see p2s_assembly_fused).  Errors: as
+ * p2s_operator_plan_create and p2s_assembly_structure_host. */
 int p2s_assembly_create(p2s_ctx* ctx, int nx, int ny, int nz, int order, int npts, int precision,
                         int kind, const p2s_term* terms, int n_terms, p2s_assembly** out);
 void p2s_assembly_destroy(p2s_assembly* A);
 int64_t p2s_assembly_rows(const p2s_assembly* A);
 int64_t p2s_assembly_nnz(const p2s_assembly* A);
-/* Replay the element fill of p2s_assembly_fill from a CUDA graph (as p2s_plan_use_graph). */
+/* Replay the element fill of p2s_assembly_fill from a CUDA graph (as p2s_plan_use_graph; no
+ * effect on the fused path). */
 int p2s_assembly_use_graph(p2s_assembly* A, int enable);
+
+/* 1 if the assembly runs fused: mixed precision, N <= 4, where each element's matrix goes from the
+ * operator contraction's registers through the basis change into the CSR values in one kernel
+ * (launched per colour), with no element-matrix scratch; 0 for the two-step path (fill into E N^6
+ * doubles of scratch, then the assembly kernel); P2S_ERR_ARG for NULL. */
+int p2s_assembly_fused(const p2s_assembly* A);
 
 /* Add element matrices to a global matrix: emat (device [E][n][n], n = N^3, Legendre basis,
  * row-major, element order above; read only) is changed to the hierarchic basis and added
@@ -429,7 +437,8 @@ int p2s_assembly_fill(p2s_assembly* A, const p2s_geometry* geom, const p2s_mater
                       double* values, void* stream);
 
 /* Assemble the element matrices of the most recent p2s_assembly_fill on this assembly again:
- * values (device, p2s_assembly_nnz doubles) is overwritten.  Stream-ordered after that fill.
+ * values (device, p2s_assembly_nnz doubles) is overwritten.  Stream-ordered after that fill.  On
+ * the fused path the element matrices are formed again from the moments the fill kept.
  * Errors: P2S_ERR_ARG, P2S_ERR_CUDA. */
 int p2s_assembly_reassemble(p2s_assembly* A, double* values, void* stream);
 

@@ -995,6 +995,36 @@ int p2s_sync_status(p2s_ctx* ctx, void* stream) {
 namespace p2s {
 const DeviceTables* context_tables(const p2s_ctx* c) { return c ? &c->T : nullptr; }
 ElemDesc* plan_desc(p2s_plan* p) { return p ? p->d_desc : nullptr; }
+int plan_spec_op(const p2s_plan* p) { return p ? p->L.spec_op : 0; }
+unsigned long long* plan_counter(p2s_plan* p) { return p ? p->d_counter : nullptr; }
+int plan_run_moments(p2s_plan* p, const p2s_geometry* geom, const p2s_material* mat, cudaStream_t s) {
+    if (!p || !p->L.op) return fail(P2S_ERR_ARG, "plan_run_moments: an operator plan is required");
+    if (set_device(p->ctx->T.device)) return P2S_ERR_CUDA;
+    return run_moments(p->ctx->T, p->Lm, p->d_mdesc, geom, mat, p->d_mom, nullptr, s, p->d_counter + 1, nullptr,
+                       p->d_order);
+}
+int plan_op_launch(p2s_plan* p, ContractLaunch& C) {
+    if (!p || !p->L.op) return fail(P2S_ERR_ARG, "plan_op_launch: an operator plan is required");
+    const DeviceTables& T = p->ctx->T;
+    const PlanLayout& PL = p->L;
+    C = ContractLaunch{};
+    C.desc = p->d_desc;
+    C.units = p->d_units;
+    C.n_units = PL.n_units;
+    C.mom = p->d_mom;
+    C.lin_idx = T.lin_idx;
+    C.lin_coef = PL.precision == P2S_MIXED ? (const void*)T.lin_coef_ff : (const void*)T.lin_coef;
+    C.counter = p->d_counter;
+    C.types_mask = PL.types_mask;
+    C.a_cap = (int)PL.a_cap;
+    C.b_cap = (int)PL.b_cap;
+    C.op_terms = p->d_op_terms;
+    C.op_scales = p->d_op_scales;
+    C.op_block = p->d_op_block;
+    C.op_nalpha = p->op_nalpha;
+    C.out_ff = PL.out_ff;
+    return P2S_OK;
+}
 int plan_set_output_ff(p2s_plan* p, bool on) {
     if (!p || !p->L.op || p->L.precision != P2S_MIXED || p->L.spec_n)
         return fail(P2S_ERR_ARG, "plan_set_output_ff: a mixed-precision operator plan is required");

@@ -25,9 +25,7 @@
 #include <new>
 #include <vector>
 
-#include "arith.cuh"
-#include "dw.cuh"
-#include "p2s_internal.h"
+#include "asm_stages.cuh"
 
 namespace p2s {
 namespace {
@@ -67,26 +65,12 @@ void build_axis(Axis1D& A, int n_el, int N) {
         }
 }
 
-// Device view of one axis.
-struct AxisDev {
-    int n_el, N, ng;
-    const int32_t* cnt;
-    const int32_t* rank;
-};
-
-__device__ __forceinline__ int axis_g(const AxisDev& A, int i, int m) {
-    return m == 0 ? i : (m == 1 ? i + 1 : A.n_el + 1 + i * (A.N - 2) + (m - 2));
-}
-
 struct AsmLaunch {
-    const double* emat;      // [E][n n] Legendre-basis element matrices (read only)
-    double* work;            // [E][n n] scratch, used when the matrices are not staged in shared memory
-    double* values;          // CSR values
-    const int64_t* row_ptr;  // [rows + 1]
-    AxisDev ax[3];
-    double ck[kMaxOrder];    // 1 / sqrt(2 (2k - 1)): the bubble normalisation
-    float ckf[2 * kMaxOrder];  // the same as (hi, lo) FP32 pairs
-    int nx, ny, nz, N, colour;
+    const double* emat;  // [E][n n] Legendre-basis element matrices (read only)
+    double* work;        // [E][n n] scratch, used when the matrices are not staged in shared memory
+    AsmMeshDev mesh;
+    AsmCoef coef;
+    int N, colour;
 };
 
 // y = T x on the N values X[base + k s] (in place): y_0 = (x_0 - x_1)/2, y_1 = (x_0 + x_1)/2,
@@ -108,76 +92,17 @@ __device__ __forceinline__ void hier_lines(const double* src, double* X, int s, 
         p[s] = 0.5 * (x[0] + x[1]);
 #pragma unroll
         for (int k = 2; k < kMaxOrder; ++k)
-            if (k < N) p[k * s] = L.ck[k] * (x[k] - x[k - 2]);
+            if (k < N) p[k * s] = L.coef.ck[k] * (x[k] - x[k - 2]);
         hi += step_hi;
         lo += step_lo;
         if (lo >= s) { lo -= s; ++hi; }
     }
 }
 
-// Shared-memory tables of one element for the scatter (n = N^3 local dofs):
-//   base[r]  CSR start of the global row of local row r,
-//   cvw[r]   neighbour counts (cnt_v(gv), cnt_w(gw)) of that row,
-//   dec[r]   the digits (m, n, p) of r packed in bytes,
-//   rank[a][x][y]  rank of the element's axis-a dof y among the neighbours of its dof x,
-// so the position of entry (r, c) is base[r] + (ru cnt_v + rv) cnt_w + rw.
-__host__ __device__ constexpr size_t asm_table_bytes_staged(int N) {
-    return sizeof(int64_t) * (N * N * N) + sizeof(int2) * (N * N * N) + sizeof(int) * 3 * N * N;
-}
 __host__ __device__ inline size_t asm_table_bytes(int N) {
     const int n = N * N * N;
     return sizeof(int64_t) * n + sizeof(int2) * n + sizeof(int) * n + sizeof(int) * 3 * N * N;
 }
-
-// T applied in place to x[0], x[S], ..., x[(N-1) S] (compile-time indices, so x stays in
-// registers); k descends so that x[(k-2) S] is still the input when x[k S] is formed.
-template <int N, int S>
-__device__ __forceinline__ void hier_T(double* x, const AsmLaunch& L) {
-    const double y0 = 0.5 * (x[0] - x[S]), y1 = 0.5 * (x[0] + x[S]);
-#pragma unroll
-    for (int k = N - 1; k >= 2; --k) x[k * S] = L.ck[k] * (x[k * S] - x[(k - 2) * S]);
-    x[0] = y0;
-    x[S] = y1;
-}
-// The same in float-float (SloppyDWPlusDW sums, normalised products): absolute error
-// O(u^2 (|x_a| + |x_b|)) per output, u = 2^-24, and every result normalised (|lo| <= ulp(hi)/2),
-// as the conversion to FP64 requires.  Halving is exact.
-template <int N, int S>
-__device__ __forceinline__ void hier_T(dw* x, const AsmLaunch& L) {
-    const dw d = dw_sub_fast(x[0], x[S]), a = dw_add_fast(x[0], x[S]);
-#pragma unroll
-    for (int k = N - 1; k >= 2; --k)
-        x[k * S] = dw_mul(dw_sub_fast(x[k * S], x[(k - 2) * S]), dw{L.ckf[2 * k], L.ckf[2 * k + 1]});
-    x[0] = dw{0.5f * d.hi, 0.5f * d.lo};
-    x[S] = dw{0.5f * a.hi, 0.5f * a.lo};
-}
-
-// Values of the staged kernel: FP64, or float-float pairs (the mixed fill's output kept as
-// (hi, lo) FP32 words in each 8-byte slot).  R in registers, M in memory.
-template <bool kFF>
-struct AsmVal {
-    using R = double;
-    using M = double;
-    __device__ static R ld(const M* p) { return *p; }
-    __device__ static void st(M* p, R v) { *p = v; }
-    __device__ static R ldg(const double* p) { return __ldg(p); }
-    __device__ static double out(const M* p) { return *p; }
-};
-template <>
-struct AsmVal<true> {
-    using R = dw;
-    using M = float2;
-    __device__ static R ld(const M* p) {
-        const float2 f = *p;
-        return dw{f.x, f.y};
-    }
-    __device__ static void st(M* p, R v) { *p = make_float2(v.hi, v.lo); }
-    __device__ static R ldg(const double* p) {
-        const float2 f = __ldg(reinterpret_cast<const float2*>(p));
-        return dw{f.x, f.y};
-    }
-    __device__ static double out(const M* p) { return ArithFF::to_double_fast(*p); }
-};
 
 // Element matrices staged in shared memory, order N (2..5) known at compile time.  Layout of the
 // staged matrix: entry (r, c), c = m2 N^2 + j, at (r N + m2) P + j with P = N^2 rounded up to
@@ -192,101 +117,39 @@ struct AsmVal<true> {
 // a small fraction of the FP32 rate), the entries going to FP64 by integer operations at the end.
 // The additions into the values are L2 reductions (red.global.add.f64): within one colour every
 // position receives at most one, so the sums are the same on every run.
+// Element matrices staged in shared memory, order N (2..5) known at compile time (layout and
+// passes in asm_stages.cuh): pass A (test u) reads the matrix from HBM, passes B, C, D finish the
+// change of basis, and every entry is added to its CSR position.  kFF: the input holds
+// float-float pairs and the passes run in float-float on the FP32 pipe (FP64 arithmetic runs at
+// a small fraction of the FP32 rate), the entries going to FP64 by integer operations at the end.
+// The additions into the values are L2 reductions (red.global.add.f64): within one colour every
+// position receives at most one, so the sums are the same on every run.
 template <int N, bool kFF>
 __global__ void __launch_bounds__(kAsmThreads, N <= 4 ? 4 : 1) k_assemble_staged(AsmLaunch L) {
     constexpr int NN = N * N, n = NN * N, nn = n * n, P = NN | 1, G = n * N;
-    using AV = AsmVal<kFF>;
-    using R = typename AV::R;
-    using M = typename AV::M;
+    using M = typename AsmVal<kFF>::M;
     extern __shared__ __align__(16) unsigned char s_raw[];
     M* s_x = reinterpret_cast<M*>(s_raw);  // [G][P]
     int64_t* s_base = reinterpret_cast<int64_t*>(s_x + G * P);
     int2* s_cvw = reinterpret_cast<int2*>(s_base + n);
     int* s_rank = reinterpret_cast<int*>(s_cvw + n);
     const int tid = threadIdx.x;
+    const AsmMeshDev& ms = L.mesh;
     const int cx = L.colour & 1, cy = (L.colour >> 1) & 1, cz = (L.colour >> 2) & 1;
-    const int hx = (L.nx - cx + 1) / 2, hy = (L.ny - cy + 1) / 2, hz = (L.nz - cz + 1) / 2;
+    const int hx = (ms.nx - cx + 1) / 2, hy = (ms.ny - cy + 1) / 2, hz = (ms.nz - cz + 1) / 2;
     const int64_t count = (int64_t)hx * hy * hz;
     for (int64_t q = blockIdx.x; q < count; q += gridDim.x) {
         const int qi = (int)(q % hx), qj = (int)((q / hx) % hy), qk = (int)(q / ((int64_t)hx * hy));
         const int i = 2 * qi + cx, j = 2 * qj + cy, k = 2 * qk + cz;
-        const double* __restrict__ src = L.emat + (((int64_t)k * L.ny + j) * L.nx + i) * (int64_t)nn;
-        for (int t = tid; t < 3 * NN; t += kAsmThreads) {
-            const int a = t / NN, xy = t - a * NN;
-            s_rank[t] = L.ax[a].rank[(a == 0 ? i : (a == 1 ? j : k)) * NN + xy];
-        }
-        for (int r = tid; r < n; r += kAsmThreads) {
-            const int gu = axis_g(L.ax[0], i, r / NN), gv = axis_g(L.ax[1], j, (r / N) % N),
-                      gw = axis_g(L.ax[2], k, r % N);
-            s_base[r] = L.row_ptr[((int64_t)gu * L.ax[1].ng + gv) * L.ax[2].ng + gw];
-            s_cvw[r] = make_int2(L.ax[1].cnt[gv], L.ax[2].cnt[gw]);
-        }
-        // A: lines lo = rr n + c (rr: test v, w digits), the N values at m n N^2 + lo
-#pragma unroll 4
-        for (int lo = tid; lo < n * NN; lo += kAsmThreads) {
-            R x[N];
-#pragma unroll
-            for (int m = 0; m < N; ++m) x[m] = AV::ldg(src + m * (n * NN) + lo);
-            hier_T<N, 1>(x, L);
-            const int rr = lo / n, c = lo - rr * n, m2 = c / NN, jj = c - m2 * NN;
-#pragma unroll
-            for (int m = 0; m < N; ++m) AV::st(s_x + ((m * NN + rr) * N + m2) * P + jj, x[m]);
-        }
+        const double* __restrict__ src = L.emat + (((int64_t)k * ms.ny + j) * ms.nx + i) * (int64_t)nn;
+        asm_element_tables<N>(ms, i, j, k, s_base, s_cvw, s_rank, tid, kAsmThreads);
+        asm_pass_a_global<N, kFF>(src, s_x, L.coef, tid, kAsmThreads);
         __syncthreads();
-        // B: one (m, c) per thread
-        for (int g = tid; g < N * n; g += kAsmThreads) {
-            const int m = g / n, c = g - m * n, m2 = c / NN, jj = c - m2 * NN;
-            M* base = s_x + ((m * NN) * N + m2) * P + jj;  // row (m, 0, 0)
-            R x[NN];
-#pragma unroll
-            for (int v = 0; v < NN; ++v) x[v] = AV::ld(base + v * N * P);  // row (m, v / N, v % N)
-#pragma unroll
-            for (int a = 0; a < N; ++a) hier_T<N, 1>(x + a * N, L);  // w
-#pragma unroll
-            for (int b = 0; b < N; ++b) hier_T<N, N>(x + b, L);      // v
-#pragma unroll
-            for (int v = 0; v < NN; ++v) AV::st(base + v * N * P, x[v]);
-        }
-        __syncthreads();
-        // C: one (r, j) per thread
-        for (int l = tid; l < n * NN; l += kAsmThreads) {
-            const int r = l / NN, jj = l - r * NN;
-            M* base = s_x + r * N * P + jj;
-            R x[N];
-#pragma unroll
-            for (int m2 = 0; m2 < N; ++m2) x[m2] = AV::ld(base + m2 * P);
-            hier_T<N, 1>(x, L);
-#pragma unroll
-            for (int m2 = 0; m2 < N; ++m2) AV::st(base + m2 * P, x[m2]);
-        }
-        __syncthreads();
-        // D: one padded row (r, m2) per thread
-        for (int g = tid; g < G; g += kAsmThreads) {
-            M* base = s_x + g * P;
-            R x[NN];
-#pragma unroll
-            for (int v = 0; v < NN; ++v) x[v] = AV::ld(base + v);
-#pragma unroll
-            for (int a = 0; a < N; ++a) hier_T<N, 1>(x + a * N, L);  // w
-#pragma unroll
-            for (int b = 0; b < N; ++b) hier_T<N, N>(x + b, L);      // v
-#pragma unroll
-            for (int v = 0; v < NN; ++v) AV::st(base + v, x[v]);
-        }
-        __syncthreads();
-        // scatter: one L2 reduction per entry
-        for (int t = tid; t < nn; t += kAsmThreads) {
-            const int r = t / n, c = t - r * n, m2 = c / NN, jj = c - m2 * NN;
-            const int ru = s_rank[(r / NN) * N + m2];
-            const int rv = s_rank[NN + ((r / N) % N) * N + jj / N];
-            const int rw = s_rank[2 * NN + (r % N) * N + jj % N];
-            const int2 cvw = s_cvw[r];
-            atomicAdd(L.values + s_base[r] + ((ru * cvw.x + rv) * cvw.y + rw), AV::out(s_x + (r * N + m2) * P + jj));
-        }
+        asm_passes_bcd<N, kFF>(s_x, L.coef, tid, kAsmThreads);
+        asm_scatter<N, kFF>(s_x, s_base, s_cvw, s_rank, ms.values, tid, kAsmThreads);
         __syncthreads();  // the staged matrix and the tables are reused by the next element
     }
 }
-
 constexpr int kMaxStagedOrder = 5;
 using AsmKernel = void (*)(AsmLaunch);
 template <bool kFF>
@@ -299,9 +162,6 @@ AsmKernel staged_kernel(int N) {
     }
 }
 
-__host__ __device__ constexpr size_t staged_smem_bytes(int N) {
-    return sizeof(double) * (size_t)(N * N * N * N) * (size_t)((N * N) | 1) + asm_table_bytes_staged(N);
-}
 
 // Any order (used for N >= 6, whose n^2 doubles do not fit in shared memory): one CTA per element
 // of the colour (grid-stride).  Tk M Tk^T by sum factorisation in the assembly's scratch: T along
@@ -322,27 +182,27 @@ __global__ void __launch_bounds__(kAsmThreads, 4) k_assemble(AsmLaunch L) {
     const int step_r = (int)blockDim.x / n, step_c = (int)blockDim.x - step_r * n;
     const int r0 = (int)threadIdx.x / n, c0 = (int)threadIdx.x - r0 * n;
     const int cx = L.colour & 1, cy = (L.colour >> 1) & 1, cz = (L.colour >> 2) & 1;
-    const int hx = (L.nx - cx + 1) / 2, hy = (L.ny - cy + 1) / 2, hz = (L.nz - cz + 1) / 2;
+    const int hx = (L.mesh.nx - cx + 1) / 2, hy = (L.mesh.ny - cy + 1) / 2, hz = (L.mesh.nz - cz + 1) / 2;
     const int64_t count = (int64_t)hx * hy * hz;
     __syncthreads();
     for (int64_t q = blockIdx.x; q < count; q += gridDim.x) {
         const int qi = (int)(q % hx), qj = (int)((q / hx) % hy), qk = (int)(q / ((int64_t)hx * hy));
         const int i = 2 * qi + cx, j = 2 * qj + cy, k = 2 * qk + cz;
-        const int64_t e = ((int64_t)k * L.ny + j) * L.nx + i;
+        const int64_t e = ((int64_t)k * L.mesh.ny + j) * L.mesh.nx + i;
         const double* src = L.emat + e * (int64_t)nn;
         double* X = L.work + e * (int64_t)nn;
         // the element's tables (the previous element's scatter ended at a barrier)
         for (int t = threadIdx.x; t < 3 * NN; t += blockDim.x) {
             const int a = t / NN, xy = t - a * NN;
             const int el = a == 0 ? i : (a == 1 ? j : k);
-            s_rank[t] = L.ax[a].rank[el * NN + xy];
+            s_rank[t] = L.mesh.ax[a].rank[el * NN + xy];
         }
         for (int r = threadIdx.x; r < n; r += blockDim.x) {
             const int d = s_dec[r];
-            const int gu = axis_g(L.ax[0], i, d & 0xff), gv = axis_g(L.ax[1], j, (d >> 8) & 0xff),
-                      gw = axis_g(L.ax[2], k, d >> 16);
-            s_base[r] = L.row_ptr[((int64_t)gu * L.ax[1].ng + gv) * L.ax[2].ng + gw];
-            s_cvw[r] = make_int2(L.ax[1].cnt[gv], L.ax[2].cnt[gw]);
+            const int gu = axis_g(L.mesh.ax[0], i, d & 0xff), gv = axis_g(L.mesh.ax[1], j, (d >> 8) & 0xff),
+                      gw = axis_g(L.mesh.ax[2], k, d >> 16);
+            s_base[r] = L.mesh.row_ptr[((int64_t)gu * L.mesh.ax[1].ng + gv) * L.mesh.ax[2].ng + gw];
+            s_cvw[r] = make_int2(L.mesh.ax[1].cnt[gv], L.mesh.ax[2].cnt[gw]);
         }
         // test u, v, w (strides n N^2, n N, n), then trial u, v, w (N^2, N, 1); the first pass
         // reads the input
@@ -359,7 +219,7 @@ __global__ void __launch_bounds__(kAsmThreads, 4) k_assemble(AsmLaunch L) {
             const int rv = s_rank[NN + ((dr >> 8) & 0xff) * N + ((dc >> 8) & 0xff)];
             const int rw = s_rank[2 * NN + (dr >> 16) * N + (dc >> 16)];
             const int2 cvw = s_cvw[r];
-            atomicAdd(L.values + s_base[r] + ((ru * cvw.x + rv) * cvw.y + rw), X[t]);
+            atomicAdd(L.mesh.values + s_base[r] + ((ru * cvw.x + rv) * cvw.y + rw), X[t]);
             r += step_r;
             c += step_c;
             if (c >= n) { c -= n; ++r; }
@@ -390,6 +250,13 @@ struct p2s_assembly {
     void (*kernel_fill)(AsmLaunch) = nullptr;  // p2s_assembly_fill: the plan's own output
     size_t smem = 0;      // dynamic shared memory of k_assemble
     int grid = 1;     // CTAs of a colour launch: the resident capacity of the device
+    // fused operator fill + assembly (mixed, N <= 4, the plan on the specialised operator path):
+    // the elements as whole-element units, colour by colour
+    bool fused = false;
+    ContractUnit* d_units = nullptr;
+    int64_t colour_off[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    int fused_threads = 0, fused_grid = 0;
+    size_t fused_smem = 0;
 };
 
 namespace {
@@ -456,6 +323,7 @@ void p2s_assembly_destroy(p2s_assembly* A) {
     if (A->ctx) cudaSetDevice(context_tables(A->ctx)->device);
     p2s_plan_destroy(A->plan);
     cudaFree(A->d_emat);
+    cudaFree(A->d_units);
     cudaFree(A->d_row_ptr);
     cudaFree(A->d_axis);
     delete A;
@@ -487,7 +355,45 @@ int p2s_assembly_create(p2s_ctx* ctx, int nx, int ny, int nz, int order, int npt
     size_t ntab = 0;
     for (int a = 0; a < 3; ++a) ntab += A->ax[a].cnt.size() + A->ax[a].rank.size();
     const int64_t n = (int64_t)order * order * order;
-    bool ok = cudaMalloc(&A->d_emat, sizeof(double) * std::max<int64_t>(1, E * n * n)) == cudaSuccess &&
+    // the fused path keeps no element matrices: it needs a mixed plan on the specialised operator
+    // kernel with whole-element units (N^4 <= 256) and the launch must fit
+    if (precision == P2S_MIXED && order <= 4 && plan_spec_op(A->plan) == order) {
+        const size_t fsmem = opn_assemble_smem_bytes(order);
+        const int fthreads = (order * order * order * order + 31) / 32 * 32;
+        const int per_sm = fsmem <= T->smem_optin ? opn_assemble_blocks_per_sm(order, fthreads, fsmem) : 0;
+        if (per_sm >= 1) {
+            std::vector<ContractUnit> units;
+            units.reserve((size_t)E);
+            for (int c = 0; c < 8; ++c) {
+                A->colour_off[c] = (int64_t)units.size();
+                for (int k = (c >> 2) & 1; k < nz; k += 2)
+                    for (int j = (c >> 1) & 1; j < ny; j += 2)
+                        for (int i = c & 1; i < nx; i += 2) {
+                            ContractUnit u{};
+                            u.e = (int32_t)(((int64_t)k * ny + j) * nx + i);
+                            u.tp = -1;
+                            u.m1n = (int8_t)order;
+                            u.n1n = (int8_t)order;
+                            units.push_back(u);
+                        }
+            }
+            A->colour_off[8] = (int64_t)units.size();
+            if (cudaMalloc(&A->d_units, sizeof(ContractUnit) * std::max<size_t>(1, units.size())) != cudaSuccess) {
+                p2s_assembly_destroy(A);
+                return fail(P2S_ERR_OOM, "p2s_assembly_create: device allocation");
+            }
+            if (cudaMemcpy(A->d_units, units.data(), sizeof(ContractUnit) * units.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess) {
+                p2s_assembly_destroy(A);
+                return fail(P2S_ERR_CUDA, "p2s_assembly_create: upload");
+            }
+            A->fused = true;
+            A->fused_smem = fsmem;
+            A->fused_threads = fthreads;
+            A->fused_grid = per_sm * T->sm_count;
+        }
+    }
+    bool ok = (A->fused || cudaMalloc(&A->d_emat, sizeof(double) * std::max<int64_t>(1, E * n * n)) == cudaSuccess) &&
               cudaMalloc(&A->d_row_ptr, sizeof(int64_t) * (A->rows + 1)) == cudaSuccess &&
               cudaMalloc(&A->d_axis, sizeof(int32_t) * ntab) == cudaSuccess;
     if (!ok) { p2s_assembly_destroy(A); return fail(P2S_ERR_OOM, "p2s_assembly_create: device allocation"); }
@@ -527,6 +433,8 @@ int p2s_assembly_create(p2s_ctx* ctx, int nx, int ny, int nz, int order, int npt
 
 int64_t p2s_assembly_rows(const p2s_assembly* A) { return A ? A->rows : P2S_ERR_ARG; }
 int64_t p2s_assembly_nnz(const p2s_assembly* A) { return A ? A->nnz : P2S_ERR_ARG; }
+int p2s_assembly_fused(const p2s_assembly* A) { return A ? (A->fused ? 1 : 0) : P2S_ERR_ARG; }
+
 int p2s_assembly_use_graph(p2s_assembly* A, int enable) {
     if (!A) return fail(P2S_ERR_ARG, "p2s_assembly_use_graph: NULL assembly");
     return p2s_plan_use_graph(A->plan, enable);
@@ -536,25 +444,51 @@ int p2s_assembly_use_graph(p2s_assembly* A, int enable) {
 
 namespace {
 
+// The device views of the mesh (into `values`) and of the bubble normalisation.
+void mesh_views(const p2s_assembly* A, double* values, AsmMeshDev& ms, AsmCoef& coef) {
+    ms.values = values;
+    ms.row_ptr = A->d_row_ptr;
+    for (int a = 0; a < 3; ++a) ms.ax[a] = A->dev[a];
+    ms.nx = A->nx;
+    ms.ny = A->ny;
+    ms.nz = A->nz;
+    for (int k = 0; k < kMaxOrder; ++k) {
+        coef.ck[k] = k >= 2 ? 1.0 / std::sqrt(2.0 * (2 * k - 1)) : 0.0;
+        coef.ckf[2 * k] = (float)coef.ck[k];
+        coef.ckf[2 * k + 1] = (float)(coef.ck[k] - (double)coef.ckf[2 * k]);
+    }
+}
+
+// The fused path: 8 colour launches of the operator contraction + assembly over the moments in the
+// plan's scratch.
+int assemble_fused(p2s_assembly* A, double* values, cudaStream_t s) {
+    P2S_CUDA(cudaSetDevice(context_tables(A->ctx)->device));
+    ContractLaunch C;
+    int rc = plan_op_launch(A->plan, C);
+    if (rc) return rc;
+    AsmMeshDev ms;
+    AsmCoef coef;
+    mesh_views(A, values, ms, coef);
+    for (int c = 0; c < 8; ++c) {
+        const int64_t cnt = A->colour_off[c + 1] - A->colour_off[c];
+        if (cnt == 0) continue;
+        P2S_CUDA(cudaMemsetAsync(C.counter, 0, sizeof(unsigned long long), s));
+        C.units = A->d_units + A->colour_off[c];
+        C.n_units = cnt;
+        const int grid = (int)std::min<int64_t>(cnt, A->fused_grid);
+        P2S_CUDA(launch_opn_assemble(A->N, C, ms, coef, grid, A->fused_threads, A->fused_smem, s));
+    }
+    return P2S_OK;
+}
+
 // The 8 colour launches of `kernel` over the element matrices `emat`.
 int assemble_colours(p2s_assembly* A, AsmKernel kernel, const double* emat, double* values, cudaStream_t s) {
-    P2S_CUDA(cudaSetDevice(context_tables(A->ctx)->device));
     P2S_CUDA(cudaSetDevice(context_tables(A->ctx)->device));
     AsmLaunch L;
     L.emat = emat;
     L.work = A->d_emat;
-    L.values = values;
-    L.row_ptr = A->d_row_ptr;
-    for (int a = 0; a < 3; ++a) L.ax[a] = A->dev[a];
-    L.nx = A->nx;
-    L.ny = A->ny;
-    L.nz = A->nz;
+    mesh_views(A, values, L.mesh, L.coef);
     L.N = A->N;
-    for (int k = 0; k < kMaxOrder; ++k) {
-        L.ck[k] = k >= 2 ? 1.0 / std::sqrt(2.0 * (2 * k - 1)) : 0.0;
-        L.ckf[2 * k] = (float)L.ck[k];
-        L.ckf[2 * k + 1] = (float)(L.ck[k] - (double)L.ckf[2 * k]);
-    }
     for (int c = 0; c < 8; ++c) {  // colours one after the other: no two elements in flight share a dof
         L.colour = c;
         const int64_t cnt = (int64_t)((A->nx - (c & 1) + 1) / 2) * ((A->ny - ((c >> 1) & 1) + 1) / 2) *
@@ -580,13 +514,15 @@ int p2s_assembly_reassemble(p2s_assembly* A, double* values, void* stream) {
     if (!A || !values) return fail(P2S_ERR_ARG, "p2s_assembly_reassemble: NULL assembly or values");
     P2S_CUDA(cudaSetDevice(context_tables(A->ctx)->device));
     P2S_CUDA(cudaMemsetAsync(values, 0, sizeof(double) * A->nnz, (cudaStream_t)stream));
+    if (A->fused) return assemble_fused(A, values, (cudaStream_t)stream);  // from the kept moments
     return assemble_colours(A, A->kernel_fill, A->d_emat, values, (cudaStream_t)stream);
 }
 
 int p2s_assembly_fill(p2s_assembly* A, const p2s_geometry* geom, const p2s_material* mat, double* values, void* stream) {
     if (!A || !values) return fail(P2S_ERR_ARG, "p2s_assembly_fill: NULL assembly or values");
     P2S_CUDA(cudaSetDevice(context_tables(A->ctx)->device));
-    int rc = p2s_plan_fill(A->plan, geom, mat, A->d_emat, nullptr, stream);
+    int rc = A->fused ? plan_run_moments(A->plan, geom, mat, (cudaStream_t)stream)
+                      : p2s_plan_fill(A->plan, geom, mat, A->d_emat, nullptr, stream);
     if (rc) return rc;
     return p2s_assembly_reassemble(A, values, stream);
 }

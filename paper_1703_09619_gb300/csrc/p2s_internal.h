@@ -167,6 +167,13 @@ cudaError_t launch_contract_opn(int N, const ContractLaunch& L, int grid, int th
 int contract_opn_blocks_per_sm(int N, int threads, size_t smem);
 // fills contract_opn.cu's copy of the coefficient runs ([4][8][8][8] (hi, lo) pairs)
 cudaError_t contract_opn_upload(const void* runs, size_t bytes);
+// fused operator fill + global assembly, N = 2..4 (contract_opn.cu; mesh views in asm_stages.cuh)
+struct AsmMeshDev;
+struct AsmCoef;
+size_t opn_assemble_smem_bytes(int N);
+cudaError_t launch_opn_assemble(int N, const ContractLaunch& L, const AsmMeshDev& ms, const AsmCoef& coef, int grid,
+                                int threads, size_t smem, cudaStream_t s);
+int opn_assemble_blocks_per_sm(int N, int threads, size_t smem);
 cudaError_t init_kernel_attributes();
 
 // ------------------------------------------------------------------ plan building (api.cu)
@@ -273,6 +280,12 @@ int32_t* plan_order(p2s_plan* p);
 // (float2 in the entry's 8 bytes) rather than the FP64 value, for a consumer that continues in
 // float-float.  P2S_ERR_ARG for other plans.
 int plan_set_output_ff(p2s_plan* p, bool on);
+// operator plans: the order of the specialised path (0: none); the moments of a fill into the
+// plan's scratch; the contraction launch parameters over that scratch
+int plan_spec_op(const p2s_plan* p);
+int plan_run_moments(p2s_plan* p, const p2s_geometry* geom, const p2s_material* mat, cudaStream_t s);
+int plan_op_launch(p2s_plan* p, ContractLaunch& C);
+unsigned long long* plan_counter(p2s_plan* p);
 int plan_fill_masked(p2s_plan* p, const p2s_geometry* geom, const p2s_material* mat, double* out,
                      const int8_t* mask, cudaStream_t s);
 cudaError_t learned_init_attributes();

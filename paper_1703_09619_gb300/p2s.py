@@ -113,6 +113,7 @@ SIGNATURES = {
     "p2s_assembly_rows": (_I64, [_P]),
     "p2s_assembly_nnz": (_I64, [_P]),
     "p2s_assembly_use_graph": (ctypes.c_int, [_P, ctypes.c_int]),
+    "p2s_assembly_fused": (ctypes.c_int, [_P]),
     "p2s_assembly_fill": (ctypes.c_int, [_P, ctypes.POINTER(Geometry), ctypes.POINTER(Material), _P, _P]),
     "p2s_assembly_add": (ctypes.c_int, [_P, _P, _P, _P]),
     "p2s_assembly_reassemble": (ctypes.c_int, [_P, _P, _P]),
@@ -440,6 +441,7 @@ class Assembly:
         self.n_elem = nx * ny * nz
         self.rows = int(lib.p2s_assembly_rows(h))
         self.nnz = int(lib.p2s_assembly_nnz(h))
+        self.fused = bool(lib.p2s_assembly_fused(h))
         if graph:
             _check(lib.p2s_assembly_use_graph(h, 1), "p2s_assembly_use_graph")
 
