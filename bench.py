@@ -349,7 +349,17 @@ def stage_times(p2s, ctx, wl, npts, prec, params, nodes, bulge, dev, stream, flu
     return float(np.mean(m)), float(np.mean(c))
 
 
-def roofline_for(wl, npts, prec, mom_ms, con_ms, peaks, src):
+def mixed_contract_kernel(orders, kernel=0):
+    """The mixed contraction kernel a plan takes (the library's rule for tile kernel 0)."""
+    o = np.asarray(orders)
+    if kernel == 1 or o.max() > 8:
+        return "k_contract<ArithFF>"
+    if kernel == 2 or not (o == o.flat[0]).all() or o.flat[0] < 2:
+        return "k_contract_ffb"
+    return "k_contract_ffn<%d>" % o.flat[0]
+
+
+def roofline_for(wl, npts, prec, mom_ms, con_ms, peaks, src, kernel=0):
     """Roofline object of the dominant kernel of a fill (the slower of the two stages)."""
     entries = wl.entries()
     fmas = contract_fma_count(wl.orders, wl.types_mask)
@@ -385,7 +395,8 @@ def roofline_for(wl, npts, prec, mom_ms, con_ms, peaks, src):
                 "algorithmic_flop_per_launch": 2 * fmas,
                 "hbm_write_GBs": 8 * entries / (con_ms * 1e-3) / 1e9}
     ach = 8 * entries / (con_ms * 1e-3) / 1e9
-    return {"bound": "hbm", "kernel": "k_contract_ffn / k_contract<ArithFF>", "achieved": ach,
+    kname = mixed_contract_kernel(wl.orders, kernel)
+    return {"bound": "hbm", "kernel": kname, "achieved": ach,
             "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
             "peak_source": "%s copy bandwidth (MEASURED_PEAKS.json)" % src, "algorithmic_bytes_per_launch": 8 * entries}
 
@@ -585,8 +596,8 @@ def run_fixed(args, wl):
     tune = args.tune if args.tune is not None else True
     tile = tune_info = None
     if args.tile:
-        co, kb, th = (int(x) for x in args.tile.split(","))
-        tile = {"combo_target": co, "unit_kbytes": kb, "threads": th}
+        vals = [int(x) for x in args.tile.split(",")]
+        tile = dict(zip(("combo_target", "unit_kbytes", "threads", "kernel"), vals))
         tune_info = {"tile": tile, "candidates": 0, "note": "given on the command line"}
     elif tune:
         sample = min(wl.n_elem, 1024)
@@ -617,7 +628,7 @@ def run_fixed(args, wl):
     clocks = clk.summary()
     mom_ms, con_ms = stage_times(p2s, ctx, wl, npts, prec, params, nodes, bulge, dev, stream, flush, tile=tile)
     peaks, src = load_peaks()
-    roof = roofline_for(wl, wl.npts, prec, mom_ms, con_ms, peaks, src)
+    roof = roofline_for(wl, wl.npts, prec, mom_ms, con_ms, peaks, src, kernel=plan.tile_config()["kernel"])
     entries = wl.entries()
     job_entries = D.sum_over_ranks(entries, world, dev)  # each rank fills a batch of its own
     job_elems = D.sum_over_ranks(wl.n_elem, world, dev)
@@ -670,8 +681,8 @@ def run_operator(args, wl):
     params, nodes, bulge = p2s.device_inputs(wl, dev)
     tile = None
     if args.tile:
-        co, kb, th = (int(x) for x in args.tile.split(","))
-        tile = {"combo_target": co, "unit_kbytes": kb, "threads": th}
+        vals = [int(x) for x in args.tile.split(",")]
+        tile = dict(zip(("combo_target", "unit_kbytes", "threads", "kernel"), vals))
     plan = p2s.OperatorPlan(ctx, orders, npts, terms, scales, wl.kind, prec, tile=tile, graph=True)
     out = torch.empty(plan.output_entries, dtype=torch.float64, device=dev)
     mom = torch.empty(max(plan.moment_entries, 1), dtype=torch.float64, device=dev)
@@ -997,7 +1008,8 @@ def main():
     ap.add_argument("--tune", dest="tune", action="store_true", default=None,
                     help="autotune the contraction tiles and replay fills from a CUDA graph (default: on)")
     ap.add_argument("--no-tune", dest="tune", action="store_false")
-    ap.add_argument("--tile", default=None, help="contraction tile combo_target,unit_kbytes,threads (skips the autotuner)")
+    ap.add_argument("--tile", default=None,
+                    help="contraction tile combo_target,unit_kbytes,threads[,kernel] (skips the autotuner)")
     args = ap.parse_args()
     if args.mode is None:
         args.mode = {"fp64": "plain", "mixed": "mixed"}.get(args.precision) or (

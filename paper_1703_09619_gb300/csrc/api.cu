@@ -119,7 +119,17 @@ int64_t elem_moments(const int32_t* ord, int nc) {
 // so each such pair of blocks is computed once and written twice.  Slabs of m1 and n1
 // keep one unit's shared-memory tile small and its thread count near one per
 // stage-3 combination.
-void slab_sizes(const ElemDesc& d, int gi, int gj, int& m1n, int& n1n, int spec_n, const TileParams& tp) {
+// m1 slab of the bounded-order kernel: full n1, as many m1 as keep the unit's stage-3
+// combinations within the target (at least one)
+int ffb_m1_slab(const int8_t* Ni, const int8_t* Nj, const TileParams& tp) {
+    const int per_m1 = Ni[1] * Nj[0] * Nj[1];
+    int m1n = 1;
+    while (m1n < Ni[0] && (m1n + 1) * per_m1 <= tp.combo_target) ++m1n;
+    return m1n;
+}
+
+void slab_sizes(const ElemDesc& d, int gi, int gj, int& m1n, int& n1n, int spec_n, const TileParams& tp,
+                bool ffb = false) {
     const int kComboTarget = tp.combo_target;
     const size_t kUnitBytesTarget = tp.unit_bytes;
     const int8_t* Ni = d.ord[gi];
@@ -129,6 +139,10 @@ void slab_sizes(const ElemDesc& d, int gi, int gj, int& m1n, int& n1n, int spec_
     if (spec_n) {  // specialised kernel: full n1, one thread per stage-3 combination
         const int n3 = spec_n * spec_n * spec_n;
         while (m1n < spec_n && (m1n + 1) * n3 <= kComboTarget) ++m1n;
+        return;
+    }
+    if (ffb) {
+        m1n = ffb_m1_slab(Ni, Nj, tp);
         return;
     }
     auto bytes = [&](int a, int b) {
@@ -144,9 +158,9 @@ void slab_sizes(const ElemDesc& d, int gi, int gj, int& m1n, int& n1n, int spec_
 }
 
 void push_block(const ElemDesc& d, int32_t e, int gi, int gj, int t, int tp, UnitSink& units, int spec_n,
-                const TileParams& tile) {
+                const TileParams& tile, bool ffb = false) {
     int m1n, n1n;
-    slab_sizes(d, gi, gj, m1n, n1n, spec_n, tile);
+    slab_sizes(d, gi, gj, m1n, n1n, spec_n, tile, ffb);
     const int Nu = d.ord[gi][0], Nv = d.ord[gi][1];
     for (int m1a = 0; m1a < Nu; m1a += m1n)
         for (int n1a = 0; n1a < Nv; n1a += n1n) {
@@ -165,19 +179,60 @@ void push_block(const ElemDesc& d, int32_t e, int gi, int gj, int t, int tp, Uni
         }
 }
 
-void add_units(const ElemDesc& d, uint32_t mask, int32_t e, UnitSink& units, int spec_n, const TileParams& tile) {
+void add_units(const ElemDesc& d, uint32_t mask, int32_t e, UnitSink& units, int spec_n, const TileParams& tile,
+               bool ffb) {
     const int nc = d.n_comp;
     for (int t : {0, 3}) {  // vv, dd: upper blocks, transposed into the lower ones
         if (!(mask & (1u << t))) continue;
         for (int gi = 0; gi < nc; ++gi)
-            for (int gj = gi; gj < nc; ++gj) push_block(d, e, gi, gj, t, gi == gj ? -1 : t, units, spec_n, tile);
+            for (int gj = gi; gj < nc; ++gj)
+                push_block(d, e, gi, gj, t, gi == gj ? -1 : t, units, spec_n, tile, ffb);
     }
     const bool dv = mask & 2u, vd = mask & 4u;
     if (dv || vd) {  // dv(gi,gj) and its transpose vd(gj,gi)
         const int t = dv ? 1 : 2, tp = (dv && vd) ? 2 : -1;
         for (int gi = 0; gi < nc; ++gi)
-            for (int gj = 0; gj < nc; ++gj) push_block(d, e, gi, gj, t, tp, units, spec_n, tile);
+            for (int gj = 0; gj < nc; ++gj) push_block(d, e, gi, gj, t, tp, units, spec_n, tile, ffb);
     }
+}
+
+// Launch shape of the bounded-order mixed contraction (contract_ffb.cu) for a batch: moment
+// and stage-2 buffers sized for the largest unit, one thread per stage-3 combination of the
+// largest unit (rounded to whole warps) unless the tile configuration fixes the CTA size.
+// False when an order passes the kernel's bound or the buffers or the CTA do not fit.
+struct FfbLaunch {
+    size_t a_cap = 1, s1_cap = 1, b_cap = 1, smem = 0;
+    int combos = 1, threads = 0, grid = 0;
+};
+bool ffb_launch_shape(const DeviceTables& T, int64_t E, const p2s_orders* orders, const TileParams& tile,
+                      size_t limit, FfbLaunch& F) {
+    const int nc = orders->n_comp;
+    for (int64_t e = 0; e < E; ++e) {
+        const int32_t* ord = orders->orders + 3 * nc * e;
+        for (int gi = 0; gi < nc; ++gi)
+            for (int gj = 0; gj < nc; ++gj) {
+                int8_t Ni[3], Nj[3];
+                for (int ax = 0; ax < 3; ++ax) {
+                    Ni[ax] = (int8_t)ord[3 * gi + ax];
+                    Nj[ax] = (int8_t)ord[3 * gj + ax];
+                }
+                if (!contract_ffb_fits(Ni, Nj)) return false;
+                size_t a, s1, b;
+                int combos;
+                contract_ffb_shape(Ni, Nj, ffb_m1_slab(Ni, Nj, tile), a, s1, b, combos);
+                F.a_cap = std::max(F.a_cap, a);
+                F.s1_cap = std::max(F.s1_cap, s1);
+                F.b_cap = std::max(F.b_cap, b);
+                F.combos = std::max(F.combos, combos);
+            }
+    }
+    F.threads = tile.threads ? tile.threads : std::min(512, std::max(64, (F.combos + 31) / 32 * 32));
+    F.smem = (F.a_cap + F.s1_cap + F.b_cap) * sizeof(float2);
+    if (F.smem > limit) return false;
+    const int per_sm = contract_ffb_blocks_per_sm(F.threads, F.smem);
+    if (per_sm < 1) return false;
+    F.grid = T.sm_count * per_sm;
+    return true;
 }
 
 }  // namespace
@@ -224,9 +279,11 @@ int tile_params_from(const p2s_tile_config* c, TileParams& tp) {
     if (c->combo_target < 0 || c->combo_target > 4096 || c->unit_kbytes < 0 || c->unit_kbytes > 227 ||
         c->threads < 0 || c->threads > 512 || (c->threads && (c->threads < 64 || c->threads % 32)))
         return fail(P2S_ERR_ARG, "tile config: combo_target 0..4096, unit_kbytes 0..227, threads 0 or 64..512 in steps of 32");
+    if (c->kernel < 0 || c->kernel > 2) return fail(P2S_ERR_ARG, "tile config: kernel 0, 1 or 2");
     if (c->combo_target) tp.combo_target = c->combo_target;
     if (c->unit_kbytes) tp.unit_bytes = (size_t)c->unit_kbytes * 1024;
     tp.threads = c->threads;
+    tp.kernel = c->kernel;
     return P2S_OK;
 }
 
@@ -251,14 +308,23 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
     const int nt = ntypes(opts->types_mask);
     int64_t out_off = 0, mom_off = 0;
     int max_pair = 1, max_elem_mom = 1;
-    // the specialised mixed kernel (contract_ff.cu): every order of the batch equal to one
-    // N in 2..6 and the compile-time coefficient runs verified against the table
+    // the specialised mixed kernels, once the compile-time coefficient runs are verified
+    // against the table: every order of the batch equal to one N in 2..8 (contract_ff.cu),
+    // else every order at most 8 (contract_ffb.cu), unless the tile configuration names one
+    const size_t limit = std::min<size_t>(T.smem_optin, 227 * 1024) - 1024;  // room for static shared memory
     int spec_n = 0;
-    if (L.precision == P2S_MIXED && T.spec_ok && E > 0) {
+    bool ffb = false;
+    FfbLaunch ffl;
+    if (tile.kernel == 2 && !moments_only) {
+        if (!(L.precision == P2S_MIXED && T.spec_ok && E > 0 && ffb_launch_shape(T, E, orders, tile, limit, ffl)))
+            return fail(P2S_ERR_ORDER, "plan: the bounded-order kernel needs mixed precision, orders <= 8 and a fitting unit");
+        ffb = true;
+    } else if (L.precision == P2S_MIXED && T.spec_ok && E > 0 && tile.kernel == 0 && !moments_only) {
         const int N = orders->orders[0];
         bool uniform = N >= 2 && N <= contract_ff_max_order();
         for (int64_t i = 0; uniform && i < E * 3 * nc; ++i) uniform = orders->orders[i] == N;
         if (uniform) spec_n = N;
+        else ffb = ffb_launch_shape(T, E, orders, tile, limit, ffl);
     }
     for (int64_t e = 0; e < E; ++e) {
         const int32_t* ord = orders->orders + 3 * nc * e;
@@ -298,7 +364,7 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
         max_pair = std::max(max_pair, d.kax[0] * d.kax[1] * d.kax[2]);
         max_elem_mom = std::max(max_elem_mom, L.n_pairs * d.kax[0] * d.kax[1] * d.kax[2]);
         L.gmax = std::max(L.gmax, G);
-        if (!moments_only) add_units(d, opts->types_mask, (int32_t)e, units, spec_n, tile);
+        if (!moments_only) add_units(d, opts->types_mask, (int32_t)e, units, spec_n, tile, ffb);
     }
     L.out_entries = out_off;
     L.mom_entries = mom_off;
@@ -307,7 +373,7 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
     // element order interleave the four, and CTAs running different paths on one SM starve
     // on instruction fetch.  Within chunks of kTypeChunk elements (whose moments stay in L2
     // across the passes) the units are ordered by type, elements in order within a type.
-    if (spec_n && !units.overflow()) {
+    if ((spec_n || ffb) && !units.overflow()) {
         ContractUnit* first = units.vec ? units.vec->data() : units.buf;
         if (first) {
             constexpr int32_t kTypeChunk = 1024;
@@ -325,7 +391,6 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
         return dwm ? moments_dw_smem_bytes(L.n_pairs, L.kb, L.gmax, cap) : moments_smem_bytes(L.n_pairs, L.kb, L.gmax, cap);
     };
     size_t base = msmem(0);
-    size_t limit = std::min<size_t>(T.smem_optin, 227 * 1024) - 1024;  // room for static shared memory
     if (base + sizeof(double) * max_pair > limit) return fail(P2S_ERR_ORDER, "plan: moment accumulator too large");
     L.iacc_cap = (int)std::min<size_t>((limit - base) / sizeof(double), (size_t)max_elem_mom);
     size_t half = limit / 2 - 1024;  // two CTAs per SM when everything fits in half
@@ -337,8 +402,20 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
 
     // contraction launch shape of the general kernel (the specialised one replaces it below)
     if (moments_only) return P2S_OK;
-    rc = general_contract_shape(T, E, desc, nc, tile, !spec_n, limit, L);
+    rc = general_contract_shape(T, E, desc, nc, tile, !spec_n && !ffb, limit, L);
     if (rc) return rc;
+    if (ffb) {
+        L.ffb = 1;
+        L.a_cap = ffl.a_cap;
+        L.s1_cap = ffl.s1_cap;
+        L.b_cap = ffl.b_cap;
+        L.tile_cap = 0;
+        L.combo_cap = (size_t)ffl.combos;
+        L.tile_off = ffl.smem;
+        L.con_smem = ffl.smem;
+        L.con_threads = ffl.threads;
+        L.con_grid = ffl.grid;
+    }
 
     if (spec_n) {
         int m1n, n1n;
@@ -408,7 +485,7 @@ int run_moments(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_d
 int run_contract(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_desc, const ContractUnit* d_units,
                  unsigned long long* d_counter, const void* moments, double* out, cudaStream_t s,
                  const int8_t* elem_mask, const OpArrays* op) {
-    if (elem_mask && (PL.precision != P2S_FP64 || PL.spec_n))
+    if (elem_mask && (PL.precision != P2S_FP64 || PL.spec_n || PL.ffb))
         return fail(P2S_ERR_ARG, "contract: element masks need an FP64 plan");
     if (PL.n_units == 0) return P2S_OK;
     if (!moments || !out) return fail(P2S_ERR_ARG, "contract: NULL moments or out");
@@ -428,6 +505,7 @@ int run_contract(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_
     C.tile_off = (int)PL.tile_off;
     C.combo_off = (int)contract_combo_offset(PL.precision, PL.a_cap, PL.b_cap, PL.tile_cap);
     C.combo_cap = (int)PL.combo_cap;
+    C.s1_cap = (int)PL.s1_cap;
     C.elem_mask = elem_mask;
     C.op_terms = op ? op->terms : nullptr;
     C.op_scales = op ? op->scales : nullptr;
@@ -438,6 +516,8 @@ int run_contract(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_
         P2S_CUDA(launch_contract_opn(PL.spec_op, C, PL.con_grid, PL.con_threads, PL.con_smem, s));
     else if (PL.spec_n)
         P2S_CUDA(launch_contract_ffn(PL.spec_n, C, PL.con_grid, PL.con_threads, PL.con_smem, s));
+    else if (PL.ffb)
+        P2S_CUDA(launch_contract_ffb(C, PL.con_grid, PL.con_threads, PL.con_smem, s));
     else
         P2S_CUDA(launch_contract(PL.precision, C, PL.con_grid, PL.con_threads, PL.con_smem, s));
     return P2S_OK;
@@ -674,6 +754,7 @@ int p2s_plan_tile_config(const p2s_plan* p, p2s_tile_config* out) {
     out->combo_target = p->L.tile.combo_target;
     out->unit_kbytes = (int)(p->L.tile.unit_bytes / 1024);
     out->threads = p->L.con_threads;
+    out->kernel = p->L.tile.kernel;
     return P2S_OK;
 }
 
@@ -904,6 +985,7 @@ int p2s_operator_plan_create(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, 
     L.out_entries = out_off;
     L.n_units = (int64_t)units.size();
     L.spec_n = 0;
+    L.ffb = 0;
     L.op = 1;
     L.a_cap = L.b_cap = L.tile_cap = L.combo_cap = 1;
     const size_t limit = std::min<size_t>(ctx->T.smem_optin, 227 * 1024) - 1024;

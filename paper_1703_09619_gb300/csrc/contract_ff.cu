@@ -320,7 +320,7 @@ cudaError_t contract_ff_upload(const HostTables& T) {
         if (r != cudaSuccess) return r;
     e = contract_opn_upload(h, sizeof(h));
     if (e != cudaSuccess) return e;
-    return cudaSuccess;
+    return contract_ffb_upload(h, sizeof(h));
 }
 
 int contract_ff_max_order() { return kSpecMax; }

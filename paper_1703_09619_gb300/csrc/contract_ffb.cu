@@ -1,0 +1,316 @@
+// Mixed-precision contraction (step a4, Eq. (4) of arXiv:1703.09619) for batches whose
+// per-axis orders differ between elements and components, every order at most 8.
+//
+// Same work units and the same arithmetic, operation for operation, as k_contract<ArithFF>
+// (contract.cu), so the two give identical bits.  The orders are run-time values here, but
+// the loops over the v- and w-axis indices are unrolled to the bound 8 with warp-uniform
+// guards, which makes n2 and (p1, p2) compile-time constants in the unrolled bodies:
+//   - the Eq. (3) coefficient runs of stages 2 and 3 come from the closed forms of
+//     contract_ff_stages.cuh (checked by the host against its table), their values from
+//     __constant__ memory;
+//   - stage 1 takes one (m1, m2, l, q) per thread and stage 2 one (n1, m1, m2, q) column
+//     per thread over every n2, both through shared memory, so that either stage keeps
+//     most of the CTA busy between its barriers;
+//   - stage 3 gives each thread one (m1, n1, m2, n2) combination and up to 4 x 8 (p1, p2)
+//     results in registers (p1 rows in halves of 4 when N_w > 4), stored straight from
+//     registers in both orientations: no shared-memory tile and no write-out pass.
+// The next unit's moments arrive in shared memory by cp.async while stage 3 runs.
+#include "contract_ff_stages.cuh"
+
+namespace p2s {
+namespace {
+
+constexpr int kB = kSpecMax;      // largest order per axis (8)
+constexpr int kKB = 2 * kB - 1;  // largest moment count per axis
+
+// The run-time shape of one unit: block (gi, gj) orders and derived extents.
+struct FfbShape {
+    int Nu_i, Nv_i, Nw_i, Nu_j, Nv_j, Nw_j;
+    int Kv, Kw, Kwp, mjn;
+};
+
+__device__ __forceinline__ FfbShape ffb_shape(const ElemDesc* d, int gi, int gj) {
+    FfbShape s;
+    s.Nu_i = d->ord[gi][0];
+    s.Nv_i = d->ord[gi][1];
+    s.Nw_i = d->ord[gi][2];
+    s.Nu_j = d->ord[gj][0];
+    s.Nv_j = d->ord[gj][1];
+    s.Nw_j = d->ord[gj][2];
+    s.Kv = s.Nv_i + s.Nv_j - 1;
+    s.Kw = s.Nw_i + s.Nw_j - 1;
+    s.Kwp = s.Kw | 1;  // odd stage-2 row stride: stage 3's row reads spread over the banks
+    s.mjn = s.Nu_j * s.Nv_j;
+    return s;
+}
+
+__device__ __forceinline__ int unit_moment_count(const ElemDesc* d, int gi, int gj) {
+    int v = 1;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) v *= d->ord[gi][ax] + d->ord[gj][ax] - 1;
+    return v;
+}
+
+__device__ __forceinline__ const float2* ffb_moments(const ContractLaunch& L, const ContractUnit& u) {
+    const ElemDesc* d = L.desc + u.e;
+    return reinterpret_cast<const float2*>(L.mom) + d->mom_off + d->pair_off[pair_index(u.gi, u.gj, d->n_comp)];
+}
+
+// 8-byte asynchronous global -> shared copy (completes at cp_async_wait_all).
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Stage 1 of one unit (any type; runs from the table): items (im1, m2, l, q),
+//   A[im1][m2][l][q] = sum_k C[m1,m2,k] I[k][l][q].
+__device__ __forceinline__ void ffb_stage1(const ContractLaunch& L, int t, const float2* __restrict__ sI,
+                                           float2* __restrict__ sA, const FfbShape& s, int m1a, int m1n, int tid,
+                                           int nth) {
+    const int KvKw = s.Kv * s.Kw;
+    const int items = m1n * s.Nu_j * KvKw;
+    const float rKvKw = 1.f / (float)KvKw, rNuj = 1.f / (float)s.Nu_j;
+    const float2* __restrict__ lcoef = reinterpret_cast<const float2*>(L.lin_coef);
+    for (int it = tid; it < items; it += nth) {
+        const int mm = div_small(it, KvKw, rKvKw), lq = it - mm * KvKw;
+        const int im1 = div_small(mm, s.Nu_j, rNuj), m2 = mm - im1 * s.Nu_j;
+        const int32_t li = __ldg(L.lin_idx + lin_slot(t, m1a + im1, m2));
+        const int k0 = lin_kmin(li), cnt = lin_cnt(li), off = lin_off(li);
+        const float2* Ik = sI + k0 * KvKw + lq;
+        float2 acc = cnt > 0 ? ArithFF::mul(__ldg(lcoef + off), Ik[0]) : ArithFF::zero();
+        for (int r = 1; r < cnt; ++r) ArithFF::fma_acc(acc, __ldg(lcoef + off + r), Ik[2 * r * KvKw]);
+        sA[it] = ArithFF::finish(acc);
+    }
+}
+
+// Stage 2 of one unit, type TT: items (n1, im1, m2, q) with n1 outermost (the coefficient
+// reads of a warp then share n1), every n2 < Nv_j unrolled:
+//   Bt[(im1, n1, m2, n2)][q] = sum_l C[n1,n2,l] A[im1][m2][l][q].
+template <int TT>
+__device__ __forceinline__ void ffb_stage2(const float2* __restrict__ sA, float2* __restrict__ sB, const FfbShape& s,
+                                           int m1n, int tid, int nth) {
+    const int per_n1 = m1n * s.Nu_j * s.Kw;
+    const int items = s.Nv_i * per_n1;
+    const float rper = 1.f / (float)per_n1, rKw = 1.f / (float)s.Kw, rNuj = 1.f / (float)s.Nu_j;
+    for (int it = tid; it < items; it += nth) {
+        const int n1 = div_small(it, per_n1, rper), rest = it - n1 * per_n1;
+        const int mm = div_small(rest, s.Kw, rKw), q = rest - mm * s.Kw;
+        const int im1 = div_small(mm, s.Nu_j, rNuj), m2 = mm - im1 * s.Nu_j;
+        const float2* a = sA + (size_t)mm * s.Kv * s.Kw + q;  // A[im1][m2][l][q] at a[l Kw]
+        // combination (im1, n1, m2, n2) = ((im1 Nv_i + n1) Nu_j + m2) Nv_j + n2
+        float2* dst = sB + ((size_t)((im1 * s.Nv_i + n1) * s.Nu_j + m2) * s.Nv_j) * s.Kwp + q;
+#pragma unroll
+        for (int n2 = 0; n2 < kB; ++n2) {
+            if (n2 >= s.Nv_j) break;
+            const int l0 = run_kmin(TT, n1, n2), lc = run_cnt(TT, n1, n2);
+            const float2* cr = &c_runs[TT][n1][n2][0];
+            float2 acc = lc > 0 ? ArithFF::mul(cr[0], a[l0 * s.Kw]) : ArithFF::zero();
+#pragma unroll
+            for (int r = 1; r < kB; ++r)
+                if (r < lc) ArithFF::fma_acc(acc, cr[r], a[(l0 + 2 * r) * s.Kw]);
+            dst[n2 * s.Kwp] = ArithFF::finish(acc);
+        }
+    }
+}
+
+// Streaming store of one or two consecutive doubles; the pair goes as one 16-byte store
+// when its address allows.
+__device__ __forceinline__ void st_one_or_two(double* p, double a, double b, bool two) {
+    if (two && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+        __stcs(reinterpret_cast<double2*>(p), make_double2(a, b));
+    } else {
+        __stcs(p, a);
+        if (two) __stcs(p + 1, b);
+    }
+}
+
+// Stage 3 for rows p1 in [P1A, P1A + 4) of combination c of the unit, and both write-outs.
+// Mt points at (row rbase, column col0) of M_t; Mp (or nullptr) at (row col0, column rbase)
+// of the partner block; n is the row stride of the element's matrices.
+template <int TT, int P1A>
+__device__ __forceinline__ void ffb_stage3_rows(const float2* __restrict__ sB, const FfbShape& s, int c, float rmjn,
+                                                double* Mt, double* Mp, int64_t n) {
+    constexpr int NP = 4;
+    const int mn = div_small(c, s.mjn, rmjn), mj = c - mn * s.mjn;  // mn = im1 Nv_i + n1, mj = m2 Nv_j + n2
+    float2 b[kKB];
+    const float2* brow = sB + (size_t)c * s.Kwp;
+#pragma unroll
+    for (int q = 0; q < kKB; ++q) b[q] = q < s.Kw ? brow[q] : ArithFF::zero();
+    double v[NP][kB];
+#pragma unroll
+    for (int i = 0; i < NP; ++i)
+#pragma unroll
+        for (int p2 = 0; p2 < kB; ++p2) {
+            const int p1 = P1A + i;
+            if (p1 < s.Nw_i && p2 < s.Nw_j) {
+                const int q0 = run_kmin(TT, p1, p2), qc = run_cnt(TT, p1, p2);
+                float2 acc = qc > 0 ? ArithFF::mul(c_runs[TT][p1][p2][0], b[q0]) : ArithFF::zero();
+#pragma unroll
+                for (int r = 1; r < kB; ++r)
+                    if (r < qc) ArithFF::fma_acc(acc, c_runs[TT][p1][p2][r], b[q0 + 2 * r]);
+                v[i][p2] = ArithFF::to_double_fast(ArithFF::finish(acc));
+            } else {
+                v[i][p2] = 0.0;
+            }
+        }
+    // rows (mn, p1) of M_t: Nw_j consecutive doubles each, at column mj Nw_j
+    double* r1 = Mt + (int64_t)(mn * s.Nw_i + P1A) * n + mj * s.Nw_j;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        if (P1A + i >= s.Nw_i) break;
+#pragma unroll
+        for (int p2 = 0; p2 < kB; p2 += 2) {
+            if (p2 >= s.Nw_j) break;
+            st_one_or_two(r1 + i * n + p2, v[i][p2], v[i][p2 + 1], p2 + 1 < s.Nw_j);
+        }
+    }
+    // rows (mj, p2) of the partner block: the unit's p1 values are consecutive columns
+    if (Mp) {
+        double* r2 = Mp + (int64_t)(mj * s.Nw_j) * n + mn * s.Nw_i + P1A;
+#pragma unroll
+        for (int p2 = 0; p2 < kB; ++p2) {
+            if (p2 >= s.Nw_j) break;
+#pragma unroll
+            for (int i = 0; i < NP; i += 2) {
+                if (P1A + i >= s.Nw_i) break;
+                st_one_or_two(r2 + p2 * n + i, v[i][p2], v[i + 1][p2], P1A + i + 1 < s.Nw_i);
+            }
+        }
+    }
+}
+
+// Stage 3 of the unit: rows p1 < 4 of every combination, then (Nw_i > 4) rows 4..7.  (One
+// flat list of (half, combination) items measured slower on the uneven-order batch.)
+template <int TT>
+__device__ __forceinline__ void ffb_stage3(const float2* __restrict__ sB, const FfbShape& s, int ncombo, int tid,
+                                           int nth, double* Mt, double* Mp, int64_t n) {
+    const float rmjn = 1.f / (float)s.mjn;
+    for (int c = tid; c < ncombo; c += nth) ffb_stage3_rows<TT, 0>(sB, s, c, rmjn, Mt, Mp, n);
+    if (s.Nw_i > 4)
+        for (int c = tid; c < ncombo; c += nth) ffb_stage3_rows<TT, 4>(sB, s, c, rmjn, Mt, Mp, n);
+}
+
+__device__ __forceinline__ int type_slot_ffb(uint32_t mask, int t) { return __popc(mask & ((1u << t) - 1u)); }
+
+// Persistent CTAs take units from the queue.  Thread 0 keeps the current and the next unit in
+// shared slots indexed by iteration parity; the next unit's moments are copied into the
+// moment buffer (free once stage 1 is done) while stages 2 and 3 run.  Three barriers per
+// unit.  Shared memory: moments (a_cap), stage 1 (s1_cap), stage 2 (b_cap), in float2.
+__global__ void __launch_bounds__(512) k_contract_ffb(ContractLaunch L) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float2* sI = reinterpret_cast<float2*>(smraw);  // moments of the unit's pair, [k][l][q]
+    float2* sA = sI + L.a_cap;                          // stage 1, [im1][m2][l][q]
+    float2* sB = sA + L.s1_cap;                         // stage 2, [combination][q] (odd stride)
+    __shared__ ContractUnit s_cu[2], s_nx[2];  // e = -1: no unit
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const unsigned long long nu = (unsigned long long)L.n_units;
+
+    if (tid == 0) {
+        ContractUnit none{};
+        none.e = -1;
+        const unsigned long long a = atomicAdd(L.counter, 1ull), b = atomicAdd(L.counter, 1ull);
+        s_cu[0] = a < nu ? L.units[a] : none;
+        s_nx[0] = b < nu ? L.units[b] : none;
+    }
+    __syncthreads();
+    if (s_cu[0].e >= 0) {
+        const ContractUnit u = s_cu[0];
+        const float2* gI = ffb_moments(L, u);
+        const int cnt = unit_moment_count(L.desc + u.e, u.gi, u.gj);
+        for (int i = tid; i < cnt; i += nth) sI[i] = __ldg(gI + i);
+    }
+    __syncthreads();
+    for (int iter = 0;; ++iter) {
+        const int par = iter & 1;
+        const ContractUnit cu = s_cu[par];
+        if (cu.e < 0) break;
+        const ElemDesc* d = L.desc + cu.e;
+        const int gi = cu.gi, gj = cu.gj, t = cu.t, m1a = cu.m1a, m1n = cu.m1n;
+        const FfbShape s = ffb_shape(d, gi, gj);
+        const int64_t n = d->n;
+        ffb_stage1(L, t, sI, sA, s, m1a, m1n, tid, nth);
+        __syncthreads();  // stage-1 results complete; the moment buffer is free
+        const ContractUnit nx = s_nx[par];
+        if (nx.e >= 0) {
+            const float2* gN = ffb_moments(L, nx);
+            const int cnt = unit_moment_count(L.desc + nx.e, nx.gi, nx.gj);
+            for (int i = tid; i < cnt; i += nth) cp_async8(sI + i, gN + i);
+        }
+        switch (t) {
+        case 0: ffb_stage2<0>(sA, sB, s, m1n, tid, nth); break;
+        case 1: ffb_stage2<1>(sA, sB, s, m1n, tid, nth); break;
+        case 2: ffb_stage2<2>(sA, sB, s, m1n, tid, nth); break;
+        default: ffb_stage2<3>(sA, sB, s, m1n, tid, nth); break;
+        }
+        __syncthreads();  // stage-2 results complete
+        // the unit's results are rows [rbase, rbase + m1n Nv_i Nw_i) x columns [col0, col0 + n_j)
+        const int rbase = d->dof_off[gi] + m1a * s.Nv_i * s.Nw_i;
+        const int col0 = d->dof_off[gj];
+        double* Mt = L.out + d->out_off + (int64_t)type_slot_ffb(L.types_mask, t) * n * n + (int64_t)rbase * n + col0;
+        double* Mp = cu.tp >= 0 ? L.out + d->out_off + (int64_t)type_slot_ffb(L.types_mask, cu.tp) * n * n +
+                                      (int64_t)col0 * n + rbase
+                                : nullptr;
+        const int ncombo = m1n * s.Nv_i * s.mjn;
+        switch (t) {
+        case 0: ffb_stage3<0>(sB, s, ncombo, tid, nth, Mt, Mp, n); break;
+        case 1: ffb_stage3<1>(sB, s, ncombo, tid, nth, Mt, Mp, n); break;
+        case 2: ffb_stage3<2>(sB, s, ncombo, tid, nth, Mt, Mp, n); break;
+        default: ffb_stage3<3>(sB, s, ncombo, tid, nth, Mt, Mp, n); break;
+        }
+        if (tid == 0) {  // the unit after next, into the other slot
+            ContractUnit none{};
+            none.e = -1;
+            const unsigned long long c = atomicAdd(L.counter, 1ull);
+            s_cu[par ^ 1] = nx;
+            s_nx[par ^ 1] = c < nu ? L.units[c] : none;
+        }
+        cp_async_wait_all();
+        __syncthreads();  // the next unit's moments in place; the stage-2 buffer free
+    }
+}
+
+}  // namespace
+
+bool contract_ffb_fits(const int8_t* Ni, const int8_t* Nj) {
+    for (int ax = 0; ax < 3; ++ax)
+        if (Ni[ax] < 1 || Ni[ax] > kB || Nj[ax] < 1 || Nj[ax] > kB) return false;
+    return true;
+}
+
+void contract_ffb_shape(const int8_t* Ni, const int8_t* Nj, int m1n, size_t& a_cap, size_t& s1_cap, size_t& b_cap,
+                        int& combos) {
+    const int Ku = Ni[0] + Nj[0] - 1, Kv = Ni[1] + Nj[1] - 1, Kw = Ni[2] + Nj[2] - 1;
+    a_cap = (size_t)Ku * Kv * Kw;
+    s1_cap = (size_t)m1n * Nj[0] * Kv * Kw;
+    combos = m1n * Ni[1] * Nj[0] * Nj[1];
+    b_cap = (size_t)combos * (Kw | 1);
+}
+
+cudaError_t contract_ffb_upload(const void* runs, size_t bytes) {
+    if (bytes != sizeof(c_runs)) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemcpyToSymbol(c_runs, runs, bytes);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, k_contract_ffb);
+    if (e != cudaSuccess) return e;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_contract_ffb, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - (int)fa.sharedSizeBytes);
+}
+
+cudaError_t launch_contract_ffb(const ContractLaunch& L, int grid, int threads, size_t smem, cudaStream_t s) {
+    if (threads < 32 || threads > 512 || threads % 32) return cudaErrorInvalidValue;
+    k_contract_ffb<<<grid, threads, smem, s>>>(L);
+    return cudaGetLastError();
+}
+
+int contract_ffb_blocks_per_sm(int threads, size_t smem) {
+    int nb = 0;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_contract_ffb, threads, smem) == cudaSuccess ? nb : 0;
+}
+
+}  // namespace p2s

@@ -109,6 +109,7 @@ struct ContractLaunch {
     int tile_off;          // byte offset of the FP64 tile in shared memory
     int combo_off;         // general kernel: byte offset of the per-unit combination tables
     int combo_cap;         // entries of each combination table
+    int s1_cap;            // bounded-order kernel: float2 entries of the stage-1 buffer
     const int8_t* elem_mask;  // optional: units of elements with mask 0 are skipped (generic kernel)
     // operator mode (general kernel; op_terms == nullptr: the four uniform types): the terms of
     // block (gi, gj) are op_terms[op_block[2 (3 gi + gj)] + k], k < op_block[2 (3 gi + gj) + 1],
@@ -162,6 +163,15 @@ int contract_opn_max_order();
 void contract_ff_shape(int N, int m1n, size_t& a_cap, size_t& b_cap, size_t& tile_cap, int& combos);
 cudaError_t launch_contract_ffn(int N, const ContractLaunch& L, int grid, int threads, size_t smem, cudaStream_t s);
 int contract_ffn_blocks_per_sm(int N, int threads, size_t smem);
+// contract_ffb.cu: mixed contraction for uneven per-axis orders, each at most 8.  Units hold
+// full n1 ranges; a_cap / s1_cap / b_cap of the launch are the moment, stage-1 and stage-2
+// buffer sizes in float2.
+bool contract_ffb_fits(const int8_t* Ni, const int8_t* Nj);
+void contract_ffb_shape(const int8_t* Ni, const int8_t* Nj, int m1n, size_t& a_cap, size_t& s1_cap, size_t& b_cap,
+                        int& combos);
+cudaError_t contract_ffb_upload(const void* runs, size_t bytes);
+cudaError_t launch_contract_ffb(const ContractLaunch& L, int grid, int threads, size_t smem, cudaStream_t s);
+int contract_ffb_blocks_per_sm(int threads, size_t smem);
 // operator plans of one component and uniform order N (2..6), mixed precision (contract_ff.cu)
 cudaError_t launch_contract_opn(int N, const ContractLaunch& L, int grid, int threads, size_t smem, cudaStream_t s);
 int contract_opn_blocks_per_sm(int N, int threads, size_t smem);
@@ -197,6 +207,7 @@ struct TileParams {
     int combo_target = 256;             // stage-3 combinations per work unit
     size_t unit_bytes = 100 * 1024;     // shared memory of one unit (generic kernel)
     int threads = 0;                    // CTA size; 0: one thread per combination of the largest unit
+    int kernel = 0;                     // 0: library choice, 1: general, 2: bounded-order kernel
 };
 
 struct PlanLayout {
@@ -208,7 +219,7 @@ struct PlanLayout {
     int n_pairs = 1, kb = 1, gmax = 1, iacc_cap = 0;
     size_t mom_smem = 0;
     int mom_grid = 1;
-    size_t a_cap = 1, b_cap = 1, tile_cap = 1, combo_cap = 1;
+    size_t a_cap = 1, b_cap = 1, tile_cap = 1, combo_cap = 1, s1_cap = 0;
     int con_threads = 256;
     size_t con_smem = 0, tile_off = 0;
     int con_grid = 1;
@@ -216,6 +227,7 @@ struct PlanLayout {
     int op = 0;      // 1: an operator plan (term list), one n x n matrix per element
     int out_ff = 0;  // operator plans, mixed precision: entries written as (hi, lo) FP32 pairs
     int spec_op = 0; // > 0: an operator plan of one component and uniform order spec_op (k_contract_opn)
+    int ffb = 0;     // 1: the mixed contraction for uneven orders <= 8 (k_contract_ffb)
     TileParams tile;  // the tile configuration in effect
 };
 

@@ -62,10 +62,12 @@ class Term(ctypes.Structure):
 
 class TileConfig(ctypes.Structure):
     """p2s_tile_config: contraction work-unit shape (zero fields: library default)."""
-    _fields_ = [("combo_target", ctypes.c_int), ("unit_kbytes", ctypes.c_int), ("threads", ctypes.c_int)]
+    _fields_ = [("combo_target", ctypes.c_int), ("unit_kbytes", ctypes.c_int), ("threads", ctypes.c_int),
+                ("kernel", ctypes.c_int)]
 
     def as_dict(self):
-        return {"combo_target": self.combo_target, "unit_kbytes": self.unit_kbytes, "threads": self.threads}
+        return {"combo_target": self.combo_target, "unit_kbytes": self.unit_kbytes, "threads": self.threads,
+                "kernel": self.kernel}
 
 
 _lib = None
@@ -269,7 +271,7 @@ class Plan:
     """A p2s_plan: descriptors, work list and launch shapes for one batch shape."""
 
     def __init__(self, ctx: Context, orders, npts, precision=FP64, types_mask=TYPES_ALL, tile=None, graph=False):
-        """tile: a TileConfig or dict (combo_target, unit_kbytes, threads) for
+        """tile: a TileConfig or dict (combo_target, unit_kbytes, threads, kernel) for
         p2s_plan_create_tuned; graph: replay fills from a CUDA graph (p2s_plan_use_graph)."""
         lib = load()
         self.ctx = ctx

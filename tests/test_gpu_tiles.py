@@ -33,9 +33,9 @@ def uneven(n=24, G=6):
     return W.make("c4", n).with_npts(G)
 
 
-def fill(torch, ctx, wl, prec, tile=None, graph=False):
+def fill(torch, ctx, wl, prec, tile=None, graph=False, types_mask=p2s.TYPES_ALL):
     params, nodes, bulge = p2s.device_inputs(wl)
-    plan = p2s.Plan(ctx, wl.orders, int(wl.npts[0]), prec, tile=tile, graph=graph)
+    plan = p2s.Plan(ctx, wl.orders, int(wl.npts[0]), prec, types_mask=types_mask, tile=tile, graph=graph)
     out = torch.full((plan.output_entries,), float("nan"), dtype=torch.float64, device="cuda")
     plan.fill(wl.kind, params, nodes, bulge, out)
     assert ctx.sync_status() == 0
@@ -81,11 +81,83 @@ def test_spec_kernel_tile_configs_bitwise_equal(torch, ctx):
         assert np.array_equal(got, ref), tile
 
 
+def with_orders(wl, lo, hi, seed):
+    """The workload with per-component per-axis orders redrawn from U{lo..hi}."""
+    import dataclasses
+    rng = np.random.default_rng(seed)
+    return dataclasses.replace(wl, orders=rng.integers(lo, hi + 1, size=wl.orders.shape).astype(np.int32))
+
+
+@pytest.mark.parametrize("mask", [0xF, 0x1, 0x2, 0x4, 0x8, 0x6, 0x9])
+def test_bounded_order_kernel_matches_general_bitwise(torch, ctx, mask):
+    """Uneven orders 1..8, mixed: the bounded-order kernel (default) and the general kernel
+    compute every entry with the same operations in the same order -- identical bits, for
+    every product-type subset (vd alone is computed directly, not as a transpose)."""
+    wl = with_orders(uneven(20, 5), 1, 8, 17)
+    ref, cfg = fill(torch, ctx, wl, p2s.MIXED, tile={"kernel": 1}, types_mask=mask)
+    assert cfg["kernel"] == 1
+    for tile in (None, {"combo_target": 1, "threads": 64}, {"combo_target": 512, "threads": 256, "kernel": 2}):
+        got, cfg = fill(torch, ctx, wl, p2s.MIXED, tile=tile, types_mask=mask)
+        assert cfg["kernel"] == (tile or {}).get("kernel", 0)
+        assert np.array_equal(got, ref), (mask, tile)
+
+
+@pytest.mark.parametrize("name,N", [("c5", 4), ("c3", 8), ("c2", 6)])
+def test_uniform_orders_all_kernels_bitwise(torch, ctx, name, N):
+    """Uniform orders, mixed: the per-order kernel (default), the bounded-order kernel and the
+    general kernel give identical bits."""
+    wl = W.make(name, 3).with_npts(5)
+    assert (wl.orders == N).all()
+    ref, _ = fill(torch, ctx, wl, p2s.MIXED, tile={"kernel": 1})
+    for tile in (None, {"kernel": 2}, {"kernel": 2, "combo_target": 64, "threads": 128}):
+        got, _ = fill(torch, ctx, wl, p2s.MIXED, tile=tile)
+        assert np.array_equal(got, ref), (name, tile)
+
+
+def test_bounded_order_kernel_refuses_what_it_cannot_take(torch, ctx):
+    wl = with_orders(uneven(4, 5), 2, 8, 31)
+    with pytest.raises(p2s.P2SError) as ex:  # FP64
+        p2s.Plan(ctx, wl.orders, 5, p2s.FP64, tile={"kernel": 2})
+    assert ex.value.code == p2s.ERR_ORDER
+    wl.orders[0, 0, 0] = 9  # an order above the bound
+    with pytest.raises(p2s.P2SError) as ex:
+        p2s.Plan(ctx, wl.orders, 5, p2s.MIXED, tile={"kernel": 2})
+    assert ex.value.code == p2s.ERR_ORDER
+
+
+def test_bounded_order_kernel_against_oracle(torch, ctx):
+    """Orders 1..8 with every order-1 edge: element-wise parity with the oracle at the mixed
+    tolerance (1e-8 of max|M| per element and type)."""
+    wl = with_orders(uneven(6, 5), 1, 8, 23)
+    wl.orders[0, 0] = (1, 8, 1)
+    wl.orders[1, 2] = (8, 1, 8)
+    wl.orders[2] = 1
+    got, _ = fill(torch, ctx, wl, p2s.MIXED)
+    ref, off, _ = oracle.fill(wl.orders, wl.kind, wl.params, wl.nodes, wl.bulge, wl.npts)
+    assert not np.isnan(got).any()
+    for e in range(wl.n_elem):
+        n = int(np.sqrt((off[e + 1] - off[e]) // 4))
+        for t in range(4):
+            a = got[off[e] + t * n * n: off[e] + (t + 1) * n * n]
+            b = ref[off[e] + t * n * n: off[e] + (t + 1) * n * n]
+            assert np.abs(a - b).max() <= 1e-8 * np.abs(b).max(), (e, t)
+
+
+def test_order_above_bound_takes_general_kernel(torch, ctx):
+    """An order above 8 anywhere in the batch: the general kernel for the whole batch, same bits."""
+    wl = with_orders(uneven(8, 5), 2, 8, 29)
+    wl.orders[3, 1, 2] = 9
+    ref, _ = fill(torch, ctx, wl, p2s.MIXED, tile={"kernel": 1})
+    got, _ = fill(torch, ctx, wl, p2s.MIXED)
+    assert np.array_equal(got, ref)
+
+
 def test_bad_tile_config(torch, ctx):
     wl = uneven(2)
     for tile in ({"combo_target": -1, "unit_kbytes": 0, "threads": 0},
                  {"combo_target": 0, "unit_kbytes": 0, "threads": 100},
-                 {"combo_target": 0, "unit_kbytes": 300, "threads": 0}):
+                 {"combo_target": 0, "unit_kbytes": 300, "threads": 0},
+                 {"combo_target": 0, "unit_kbytes": 0, "threads": 0, "kernel": 3}):
         with pytest.raises(p2s.P2SError) as ex:
             p2s.Plan(ctx, wl.orders, 4, p2s.FP64, tile=tile)
         assert ex.value.code == p2s.ERR_ARG
