@@ -349,13 +349,14 @@ def stage_times(p2s, ctx, wl, npts, prec, params, nodes, bulge, dev, stream, flu
     return float(np.mean(m)), float(np.mean(c))
 
 
-def mixed_contract_kernel(orders, kernel=0):
-    """The mixed contraction kernel a plan takes (the library's rule for tile kernel 0)."""
+def contract_kernel(orders, mixed=True, kernel=0):
+    """The contraction kernel a plan takes (the library's rule for tile kernel 0)."""
     o = np.asarray(orders)
+    arith = "ArithFF" if mixed else "ArithF64"
     if kernel == 1 or o.max() > 8:
-        return "k_contract<ArithFF>"
-    if kernel == 2 or not (o == o.flat[0]).all() or o.flat[0] < 2:
-        return "k_contract_ffb"
+        return "k_contract<%s>" % arith
+    if not mixed or kernel == 2 or not (o == o.flat[0]).all() or o.flat[0] < 2:
+        return "k_contract_ffb<%s>" % arith
     return "k_contract_ffn<%d>" % o.flat[0]
 
 
@@ -389,13 +390,14 @@ def roofline_for(wl, npts, prec, mom_ms, con_ms, peaks, src, kernel=0):
                 "flop_model": "2 x sum-factorised moment MACs + %d FP64 flop per point for alpha" % ALPHA_FLOP_PER_POINT}
     if prec == 0:
         ach = 2 * fmas / (con_ms * 1e-3) / 1e12
-        return {"bound": "alu", "kernel": "k_contract<ArithF64>", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+        return {"bound": "alu", "kernel": contract_kernel(wl.orders, False, kernel), "achieved": ach,
+                "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
                 "algorithmic_flop_per_launch": 2 * fmas,
                 "hbm_write_GBs": 8 * entries / (con_ms * 1e-3) / 1e9}
     ach = 8 * entries / (con_ms * 1e-3) / 1e9
-    kname = mixed_contract_kernel(wl.orders, kernel)
+    kname = contract_kernel(wl.orders, True, kernel)
     return {"bound": "hbm", "kernel": kname, "achieved": ach,
             "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
             "peak_source": "%s copy bandwidth (MEASURED_PEAKS.json)" % src, "algorithmic_bytes_per_launch": 8 * entries}

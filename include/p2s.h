@@ -171,13 +171,13 @@ int p2s_plan_fill(p2s_plan* plan, const p2s_geometry* geom, const p2s_material* 
  *                 one per combination of the largest unit);
  *   kernel        which contraction kernel (every one computes each entry with the same
  *                 operations in the same order):
- *                 0 (default) the library's choice: for mixed precision with every order
- *                   <= 8 a kernel specialised on the coefficient runs (uniform orders: one
- *                   compiled per order; uneven orders: the bounded-order kernel), else the
- *                   general kernel;
+ *                 0 (default) the library's choice: with every order <= 8 a kernel
+ *                   specialised on the coefficient runs (mixed precision with uniform
+ *                   orders: one compiled per order; otherwise the bounded-order kernel, in
+ *                   either precision), else the general kernel;
  *                 1 the general kernel;
- *                 2 the bounded-order kernel (mixed precision, every order <= 8; plan
- *                   creation fails with P2S_ERR_ORDER otherwise). */
+ *                 2 the bounded-order kernel (every order <= 8; plan creation fails with
+ *                   P2S_ERR_ORDER otherwise). */
 typedef struct {
     int combo_target;
     int unit_kbytes;
@@ -196,8 +196,8 @@ int p2s_plan_create_tuned(p2s_ctx* ctx, int64_t n_elem, const p2s_orders* orders
 int p2s_plan_tile_config(const p2s_plan* plan, p2s_tile_config* out);
 
 /* Autotuner: builds a plan per candidate configuration (combo targets 64..512 x budgets
- * 24/48/100 KiB x derived/128/256-thread CTAs with the library's kernel choice; for mixed
- * precision also the bounded-order kernel at each combo target and CTA size) on the first
+ * 24/48/100 KiB x derived/128/256-thread CTAs with the library's kernel choice, and the
+ * bounded-order kernel at each combo target and CTA size) on the first
  * `sample` elements of the batch
  * (<= 0: all), computes their moments once, times `reps` contractions of each candidate
  * with CUDA events on `stream` (median) and writes the fastest to *best (host), its time

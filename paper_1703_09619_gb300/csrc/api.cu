@@ -205,7 +205,7 @@ struct FfbLaunch {
     int combos = 1, threads = 0, grid = 0;
 };
 bool ffb_launch_shape(const DeviceTables& T, int64_t E, const p2s_orders* orders, const TileParams& tile,
-                      size_t limit, FfbLaunch& F) {
+                      size_t limit, int precision, FfbLaunch& F) {
     const int nc = orders->n_comp;
     for (int64_t e = 0; e < E; ++e) {
         const int32_t* ord = orders->orders + 3 * nc * e;
@@ -227,9 +227,9 @@ bool ffb_launch_shape(const DeviceTables& T, int64_t E, const p2s_orders* orders
             }
     }
     F.threads = tile.threads ? tile.threads : std::min(512, std::max(64, (F.combos + 31) / 32 * 32));
-    F.smem = (F.a_cap + F.s1_cap + F.b_cap) * sizeof(float2);
+    F.smem = (F.a_cap + F.s1_cap + F.b_cap) * sizeof(double);  // 8-byte words in either precision
     if (F.smem > limit) return false;
-    const int per_sm = contract_ffb_blocks_per_sm(F.threads, F.smem);
+    const int per_sm = contract_ffb_blocks_per_sm(precision, F.threads, F.smem);
     if (per_sm < 1) return false;
     F.grid = T.sm_count * per_sm;
     return true;
@@ -308,23 +308,27 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
     const int nt = ntypes(opts->types_mask);
     int64_t out_off = 0, mom_off = 0;
     int max_pair = 1, max_elem_mom = 1;
-    // the specialised mixed kernels, once the compile-time coefficient runs are verified
-    // against the table: every order of the batch equal to one N in 2..8 (contract_ff.cu),
-    // else every order at most 8 (contract_ffb.cu), unless the tile configuration names one
+    // the kernels specialised on the coefficient runs, once the compile-time runs are verified
+    // against the table: for mixed precision with every order of the batch equal to one N in
+    // 2..8 the per-order kernel (contract_ff.cu), else with every order at most 8 the
+    // bounded-order kernel (contract_ffb.cu, either precision), unless the tile configuration
+    // names a kernel
     const size_t limit = std::min<size_t>(T.smem_optin, 227 * 1024) - 1024;  // room for static shared memory
     int spec_n = 0;
     bool ffb = false;
     FfbLaunch ffl;
-    if (tile.kernel == 2 && !moments_only) {
-        if (!(L.precision == P2S_MIXED && T.spec_ok && E > 0 && ffb_launch_shape(T, E, orders, tile, limit, ffl)))
-            return fail(P2S_ERR_ORDER, "plan: the bounded-order kernel needs mixed precision, orders <= 8 and a fitting unit");
+    if (tile.kernel == 2 && E > 0 && !moments_only) {
+        if (!(T.spec_ok && ffb_launch_shape(T, E, orders, tile, limit, L.precision, ffl)))
+            return fail(P2S_ERR_ORDER, "plan: the bounded-order kernel needs orders <= 8 and a fitting unit");
         ffb = true;
-    } else if (L.precision == P2S_MIXED && T.spec_ok && E > 0 && tile.kernel == 0 && !moments_only) {
-        const int N = orders->orders[0];
-        bool uniform = N >= 2 && N <= contract_ff_max_order();
-        for (int64_t i = 0; uniform && i < E * 3 * nc; ++i) uniform = orders->orders[i] == N;
-        if (uniform) spec_n = N;
-        else ffb = ffb_launch_shape(T, E, orders, tile, limit, ffl);
+    } else if (T.spec_ok && E > 0 && tile.kernel == 0 && !moments_only) {
+        if (L.precision == P2S_MIXED) {
+            const int N = orders->orders[0];
+            bool uniform = N >= 2 && N <= contract_ff_max_order();
+            for (int64_t i = 0; uniform && i < E * 3 * nc; ++i) uniform = orders->orders[i] == N;
+            if (uniform) spec_n = N;
+        }
+        if (!spec_n) ffb = ffb_launch_shape(T, E, orders, tile, limit, L.precision, ffl);
     }
     for (int64_t e = 0; e < E; ++e) {
         const int32_t* ord = orders->orders + 3 * nc * e;
@@ -485,7 +489,7 @@ int run_moments(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_d
 int run_contract(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_desc, const ContractUnit* d_units,
                  unsigned long long* d_counter, const void* moments, double* out, cudaStream_t s,
                  const int8_t* elem_mask, const OpArrays* op) {
-    if (elem_mask && (PL.precision != P2S_FP64 || PL.spec_n || PL.ffb))
+    if (elem_mask && (PL.precision != P2S_FP64 || PL.spec_n))
         return fail(P2S_ERR_ARG, "contract: element masks need an FP64 plan");
     if (PL.n_units == 0) return P2S_OK;
     if (!moments || !out) return fail(P2S_ERR_ARG, "contract: NULL moments or out");
@@ -517,7 +521,7 @@ int run_contract(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_
     else if (PL.spec_n)
         P2S_CUDA(launch_contract_ffn(PL.spec_n, C, PL.con_grid, PL.con_threads, PL.con_smem, s));
     else if (PL.ffb)
-        P2S_CUDA(launch_contract_ffb(C, PL.con_grid, PL.con_threads, PL.con_smem, s));
+        P2S_CUDA(launch_contract_ffb(PL.precision, C, PL.con_grid, PL.con_threads, PL.con_smem, s));
     else
         P2S_CUDA(launch_contract(PL.precision, C, PL.con_grid, PL.con_threads, PL.con_smem, s));
     return P2S_OK;

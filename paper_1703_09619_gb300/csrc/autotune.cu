@@ -4,8 +4,8 @@
 // The contraction splits each (element, block, type) into work units of m1/n1 slabs.  How
 // many stage-3 combinations a unit holds, how much shared memory it may stage and how many
 // threads a CTA has trade occupancy against barrier count and redundant stage-1/2 work, and
-// the best point depends on the batch's order mix; for mixed precision the kernel itself is a
-// candidate too (the per-order or general kernel, or the bounded-order kernel).  The tuner builds one plan per candidate
+// the best point depends on the batch's order mix; the kernel itself is a candidate too (the
+// library's choice or the bounded-order kernel).  The tuner builds one plan per candidate
 // on a leading sample of the batch, computes the sample's moments once (the moment layout
 // does not depend on the tiles), times each candidate's contraction with CUDA events on the
 // caller's stream and returns the fastest.  Every candidate computes the same entries with
@@ -27,9 +27,9 @@ struct Candidate {
 
 // combo targets x shared-memory budgets, each with the derived CTA size (one thread per
 // combination of the largest unit) and with fixed 128- and 256-thread CTAs, with the library's
-// kernel choice; for mixed precision also the bounded-order kernel (no shared-memory tile, so
-// no budget) at each combo target and CTA size
-std::vector<Candidate> candidates(bool mixed) {
+// kernel choice, and the bounded-order kernel (no shared-memory tile, so no budget) at each
+// combo target and CTA size
+std::vector<Candidate> candidates() {
     std::vector<Candidate> c;
     const int combos[] = {64, 128, 256, 512};
     const int kbytes[] = {24, 48, 100};
@@ -37,9 +37,8 @@ std::vector<Candidate> candidates(bool mixed) {
     for (int co : combos)
         for (int kb : kbytes)
             for (int th : threads) c.push_back({co, kb, th, 0});
-    if (mixed)
-        for (int co : combos)
-            for (int th : threads) c.push_back({co, 0, th, 2});
+    for (int co : combos)
+        for (int th : threads) c.push_back({co, 0, th, 2});
     return c;
 }
 
@@ -71,7 +70,7 @@ extern "C" int p2s_autotune_tiles(p2s_ctx* ctx, const p2s_geometry* geom, const 
 
     double best_t = 1e300;
     int tried = 0;
-    for (const Candidate& c : candidates(opts->precision == P2S_MIXED)) {
+    for (const Candidate& c : candidates()) {
         if (rc) break;
         p2s_tile_config cfg{c.combo, c.kbytes, c.threads, c.kernel};
         p2s_plan* p = nullptr;

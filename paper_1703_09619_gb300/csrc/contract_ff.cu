@@ -304,6 +304,7 @@ bool contract_ff_runs_match(const HostTables& T) {
 
 cudaError_t contract_ff_upload(const HostTables& T) {
     static float2 h[4][kSpec][kSpec][kSpec];
+    static double h64[4][kSpec][kSpec][kSpec];
     for (int t = 0; t < 4; ++t)
         for (int a = 0; a < kSpec; ++a)
             for (int b = 0; b < kSpec; ++b)
@@ -312,6 +313,7 @@ cudaError_t contract_ff_upload(const HostTables& T) {
                     h[t][a][b][r] = r < lin_cnt(li)
                                         ? make_float2(T.lin_coef_ff[2 * (lin_off(li) + r)], T.lin_coef_ff[2 * (lin_off(li) + r) + 1])
                                         : make_float2(0.f, 0.f);
+                    h64[t][a][b][r] = r < lin_cnt(li) ? T.lin_coef[lin_off(li) + r] : 0.0;
                 }
     cudaError_t e = cudaMemcpyToSymbol(c_runs, h, sizeof(h));
     if (e != cudaSuccess) return e;
@@ -320,7 +322,7 @@ cudaError_t contract_ff_upload(const HostTables& T) {
         if (r != cudaSuccess) return r;
     e = contract_opn_upload(h, sizeof(h));
     if (e != cudaSuccess) return e;
-    return contract_ffb_upload(h, sizeof(h));
+    return contract_ffb_upload(h, sizeof(h), &h64[0][0][0][0], sizeof(h64));
 }
 
 int contract_ff_max_order() { return kSpecMax; }

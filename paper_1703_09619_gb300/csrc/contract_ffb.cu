@@ -1,20 +1,22 @@
-// Mixed-precision contraction (step a4, Eq. (4) of arXiv:1703.09619) for batches whose
-// per-axis orders differ between elements and components, every order at most 8.
+// Contraction (step a4, Eq. (4) of arXiv:1703.09619) for batches whose per-axis orders are at
+// most 8, uniform or not, in either arithmetic (FP64 or float-float).
 //
-// Same work units and the same arithmetic, operation for operation, as k_contract<ArithFF>
+// Same work units and the same arithmetic, operation for operation, as k_contract<A>
 // (contract.cu), so the two give identical bits.  The orders are run-time values here, but
 // the loops over the v- and w-axis indices are unrolled to the bound 8 with warp-uniform
 // guards, which makes n2 and (p1, p2) compile-time constants in the unrolled bodies:
 //   - the Eq. (3) coefficient runs of stages 2 and 3 come from the closed forms of
 //     contract_ff_stages.cuh (checked by the host against its table), their values from
-//     __constant__ memory;
+//     __constant__ memory (a float-float and an FP64 copy);
 //   - stage 1 takes one (m1, m2, l, q) per thread and stage 2 one (n1, m1, m2, q) column
 //     per thread over every n2, both through shared memory, so that either stage keeps
 //     most of the CTA busy between its barriers;
 //   - stage 3 gives each thread one (m1, n1, m2, n2) combination and up to 4 x 8 (p1, p2)
-//     results in registers (p1 rows in halves of 4 when N_w > 4), stored straight from
-//     registers in both orientations: no shared-memory tile and no write-out pass.
+//     results in registers (2 x 8 in FP64; further p1 rows in later passes), stored straight
+//     from registers in both orientations: no shared-memory tile and no write-out pass.
 // The next unit's moments arrive in shared memory by cp.async while stage 3 runs.
+#include <type_traits>
+
 #include "contract_ff_stages.cuh"
 
 namespace p2s {
@@ -22,6 +24,15 @@ namespace {
 
 constexpr int kB = kSpecMax;      // largest order per axis (8)
 constexpr int kKB = 2 * kB - 1;  // largest moment count per axis
+__constant__ double c_runs64[4][kSpec][kSpec][kSpec];  // FP64 values of c_runs
+
+// Coefficient r of the run of (t, a, b) in the arithmetic's own type (compile-time indices).
+template <class A>
+__device__ __forceinline__ typename A::C run_coef(int t, int a, int b, int r);
+template <>
+__device__ __forceinline__ float2 run_coef<ArithFF>(int t, int a, int b, int r) { return c_runs[t][a][b][r]; }
+template <>
+__device__ __forceinline__ double run_coef<ArithF64>(int t, int a, int b, int r) { return c_runs64[t][a][b][r]; }
 
 // The run-time shape of one unit: block (gi, gj) orders and derived extents.
 struct FfbShape {
@@ -51,9 +62,10 @@ __device__ __forceinline__ int unit_moment_count(const ElemDesc* d, int gi, int 
     return v;
 }
 
-__device__ __forceinline__ const float2* ffb_moments(const ContractLaunch& L, const ContractUnit& u) {
+// First moment (8-byte word) of the unit's component pair.
+__device__ __forceinline__ size_t ffb_moments(const ContractLaunch& L, const ContractUnit& u) {
     const ElemDesc* d = L.desc + u.e;
-    return reinterpret_cast<const float2*>(L.mom) + d->mom_off + d->pair_off[pair_index(u.gi, u.gj, d->n_comp)];
+    return (size_t)d->mom_off + d->pair_off[pair_index(u.gi, u.gj, d->n_comp)];
 }
 
 // 8-byte asynchronous global -> shared copy (completes at cp_async_wait_all).
@@ -65,31 +77,33 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // Stage 1 of one unit (any type; runs from the table): items (im1, m2, l, q),
 //   A[im1][m2][l][q] = sum_k C[m1,m2,k] I[k][l][q].
-__device__ __forceinline__ void ffb_stage1(const ContractLaunch& L, int t, const float2* __restrict__ sI,
-                                           float2* __restrict__ sA, const FfbShape& s, int m1a, int m1n, int tid,
-                                           int nth) {
+template <class A>
+__device__ __forceinline__ void ffb_stage1(const ContractLaunch& L, int t, const typename A::T* __restrict__ sI,
+                                           typename A::T* __restrict__ sA, const FfbShape& s, int m1a, int m1n,
+                                           int tid, int nth) {
+    using T = typename A::T;
     const int KvKw = s.Kv * s.Kw;
     const int items = m1n * s.Nu_j * KvKw;
     const float rKvKw = 1.f / (float)KvKw, rNuj = 1.f / (float)s.Nu_j;
-    const float2* __restrict__ lcoef = reinterpret_cast<const float2*>(L.lin_coef);
     for (int it = tid; it < items; it += nth) {
         const int mm = div_small(it, KvKw, rKvKw), lq = it - mm * KvKw;
         const int im1 = div_small(mm, s.Nu_j, rNuj), m2 = mm - im1 * s.Nu_j;
         const int32_t li = __ldg(L.lin_idx + lin_slot(t, m1a + im1, m2));
         const int k0 = lin_kmin(li), cnt = lin_cnt(li), off = lin_off(li);
-        const float2* Ik = sI + k0 * KvKw + lq;
-        float2 acc = cnt > 0 ? ArithFF::mul(__ldg(lcoef + off), Ik[0]) : ArithFF::zero();
-        for (int r = 1; r < cnt; ++r) ArithFF::fma_acc(acc, __ldg(lcoef + off + r), Ik[2 * r * KvKw]);
-        sA[it] = ArithFF::finish(acc);
+        const T* Ik = sI + k0 * KvKw + lq;
+        T acc = cnt > 0 ? A::mul(A::load_coef(L.lin_coef, off), Ik[0]) : A::zero();
+        for (int r = 1; r < cnt; ++r) A::fma_acc(acc, A::load_coef(L.lin_coef, off + r), Ik[2 * r * KvKw]);
+        sA[it] = A::finish(acc);
     }
 }
 
 // Stage 2 of one unit, type TT: items (n1, im1, m2, q) with n1 outermost (the coefficient
 // reads of a warp then share n1), every n2 < Nv_j unrolled:
 //   Bt[(im1, n1, m2, n2)][q] = sum_l C[n1,n2,l] A[im1][m2][l][q].
-template <int TT>
-__device__ __forceinline__ void ffb_stage2(const float2* __restrict__ sA, float2* __restrict__ sB, const FfbShape& s,
-                                           int m1n, int tid, int nth) {
+template <class A, int TT>
+__device__ __forceinline__ void ffb_stage2(const typename A::T* __restrict__ sA, typename A::T* __restrict__ sB,
+                                           const FfbShape& s, int m1n, int tid, int nth) {
+    using T = typename A::T;
     const int per_n1 = m1n * s.Nu_j * s.Kw;
     const int items = s.Nv_i * per_n1;
     const float rper = 1.f / (float)per_n1, rKw = 1.f / (float)s.Kw, rNuj = 1.f / (float)s.Nu_j;
@@ -97,19 +111,20 @@ __device__ __forceinline__ void ffb_stage2(const float2* __restrict__ sA, float2
         const int n1 = div_small(it, per_n1, rper), rest = it - n1 * per_n1;
         const int mm = div_small(rest, s.Kw, rKw), q = rest - mm * s.Kw;
         const int im1 = div_small(mm, s.Nu_j, rNuj), m2 = mm - im1 * s.Nu_j;
-        const float2* a = sA + (size_t)mm * s.Kv * s.Kw + q;  // A[im1][m2][l][q] at a[l Kw]
+        const T* a = sA + (size_t)mm * s.Kv * s.Kw + q;  // A[im1][m2][l][q] at a[l Kw]
         // combination (im1, n1, m2, n2) = ((im1 Nv_i + n1) Nu_j + m2) Nv_j + n2
-        float2* dst = sB + ((size_t)((im1 * s.Nv_i + n1) * s.Nu_j + m2) * s.Nv_j) * s.Kwp + q;
+        T* dst = sB + ((size_t)((im1 * s.Nv_i + n1) * s.Nu_j + m2) * s.Nv_j) * s.Kwp + q;
+        // n1 is a run-time index here; it is outermost in the item order, so the constant-memory
+        // reads of a warp mostly share one address
 #pragma unroll
         for (int n2 = 0; n2 < kB; ++n2) {
             if (n2 >= s.Nv_j) break;
             const int l0 = run_kmin(TT, n1, n2), lc = run_cnt(TT, n1, n2);
-            const float2* cr = &c_runs[TT][n1][n2][0];
-            float2 acc = lc > 0 ? ArithFF::mul(cr[0], a[l0 * s.Kw]) : ArithFF::zero();
+            T acc = lc > 0 ? A::mul(run_coef<A>(TT, n1, n2, 0), a[l0 * s.Kw]) : A::zero();
 #pragma unroll
             for (int r = 1; r < kB; ++r)
-                if (r < lc) ArithFF::fma_acc(acc, cr[r], a[(l0 + 2 * r) * s.Kw]);
-            dst[n2 * s.Kwp] = ArithFF::finish(acc);
+                if (r < lc) A::fma_acc(acc, run_coef<A>(TT, n1, n2, r), a[(l0 + 2 * r) * s.Kw]);
+            dst[n2 * s.Kwp] = A::finish(acc);
         }
     }
 }
@@ -128,15 +143,16 @@ __device__ __forceinline__ void st_one_or_two(double* p, double a, double b, boo
 // Stage 3 for rows p1 in [P1A, P1A + 4) of combination c of the unit, and both write-outs.
 // Mt points at (row rbase, column col0) of M_t; Mp (or nullptr) at (row col0, column rbase)
 // of the partner block; n is the row stride of the element's matrices.
-template <int TT, int P1A>
-__device__ __forceinline__ void ffb_stage3_rows(const float2* __restrict__ sB, const FfbShape& s, int c, float rmjn,
-                                                double* Mt, double* Mp, int64_t n) {
-    constexpr int NP = 4;
+template <class A, int TT, int P1A, int NP>
+__device__ __forceinline__ void ffb_stage3_rows(const typename A::T* __restrict__ sB, const FfbShape& s, int c,
+                                                float rmjn, double* Mt, double* Mp, int64_t n) {
+    static_assert(NP % 2 == 0, "row pairs");
+    using T = typename A::T;
     const int mn = div_small(c, s.mjn, rmjn), mj = c - mn * s.mjn;  // mn = im1 Nv_i + n1, mj = m2 Nv_j + n2
-    float2 b[kKB];
-    const float2* brow = sB + (size_t)c * s.Kwp;
+    T b[kKB];
+    const T* brow = sB + (size_t)c * s.Kwp;
 #pragma unroll
-    for (int q = 0; q < kKB; ++q) b[q] = q < s.Kw ? brow[q] : ArithFF::zero();
+    for (int q = 0; q < kKB; ++q) b[q] = q < s.Kw ? brow[q] : A::zero();
     double v[NP][kB];
 #pragma unroll
     for (int i = 0; i < NP; ++i)
@@ -145,11 +161,11 @@ __device__ __forceinline__ void ffb_stage3_rows(const float2* __restrict__ sB, c
             const int p1 = P1A + i;
             if (p1 < s.Nw_i && p2 < s.Nw_j) {
                 const int q0 = run_kmin(TT, p1, p2), qc = run_cnt(TT, p1, p2);
-                float2 acc = qc > 0 ? ArithFF::mul(c_runs[TT][p1][p2][0], b[q0]) : ArithFF::zero();
+                T acc = qc > 0 ? A::mul(run_coef<A>(TT, p1, p2, 0), b[q0]) : A::zero();
 #pragma unroll
                 for (int r = 1; r < kB; ++r)
-                    if (r < qc) ArithFF::fma_acc(acc, c_runs[TT][p1][p2][r], b[q0 + 2 * r]);
-                v[i][p2] = ArithFF::to_double_fast(ArithFF::finish(acc));
+                    if (r < qc) A::fma_acc(acc, run_coef<A>(TT, p1, p2, r), b[q0 + 2 * r]);
+                v[i][p2] = A::to_double_fast(A::finish(acc));
             } else {
                 v[i][p2] = 0.0;
             }
@@ -182,13 +198,24 @@ __device__ __forceinline__ void ffb_stage3_rows(const float2* __restrict__ sB, c
 
 // Stage 3 of the unit: rows p1 < 4 of every combination, then (Nw_i > 4) rows 4..7.  (One
 // flat list of (half, combination) items measured slower on the uneven-order batch.)
-template <int TT>
-__device__ __forceinline__ void ffb_stage3(const float2* __restrict__ sB, const FfbShape& s, int ncombo, int tid,
-                                           int nth, double* Mt, double* Mp, int64_t n) {
-    const float rmjn = 1.f / (float)s.mjn;
-    for (int c = tid; c < ncombo; c += nth) ffb_stage3_rows<TT, 0>(sB, s, c, rmjn, Mt, Mp, n);
-    if (s.Nw_i > 4)
-        for (int c = tid; c < ncombo; c += nth) ffb_stage3_rows<TT, 4>(sB, s, c, rmjn, Mt, Mp, n);
+// Rows per pass: 4 in float-float; 2 in FP64, whose DFMA chains keep more registers in flight
+// (4 rows spill there).
+template <class A>
+constexpr int ffb_rows() { return std::is_same<typename A::T, double>::value ? 2 : 4; }
+
+template <class A, int TT>
+__device__ __forceinline__ void ffb_stage3(const typename A::T* __restrict__ sB, const FfbShape& s, int ncombo,
+                                           int tid, int nth, double* Mt, double* Mp, int64_t n, float rmjn) {
+    constexpr int NP = ffb_rows<A>();
+    for (int c = tid; c < ncombo; c += nth) ffb_stage3_rows<A, TT, 0, NP>(sB, s, c, rmjn, Mt, Mp, n);
+    if (s.Nw_i > NP)
+        for (int c = tid; c < ncombo; c += nth) ffb_stage3_rows<A, TT, NP, NP>(sB, s, c, rmjn, Mt, Mp, n);
+    if constexpr (NP == 2) {
+        if (s.Nw_i > 4)
+            for (int c = tid; c < ncombo; c += nth) ffb_stage3_rows<A, TT, 4, NP>(sB, s, c, rmjn, Mt, Mp, n);
+        if (s.Nw_i > 6)
+            for (int c = tid; c < ncombo; c += nth) ffb_stage3_rows<A, TT, 6, NP>(sB, s, c, rmjn, Mt, Mp, n);
+    }
 }
 
 __device__ __forceinline__ int type_slot_ffb(uint32_t mask, int t) { return __popc(mask & ((1u << t) - 1u)); }
@@ -196,12 +223,17 @@ __device__ __forceinline__ int type_slot_ffb(uint32_t mask, int t) { return __po
 // Persistent CTAs take units from the queue.  Thread 0 keeps the current and the next unit in
 // shared slots indexed by iteration parity; the next unit's moments are copied into the
 // moment buffer (free once stage 1 is done) while stages 2 and 3 run.  Three barriers per
-// unit.  Shared memory: moments (a_cap), stage 1 (s1_cap), stage 2 (b_cap), in float2.
+// unit.  Shared memory: moments (a_cap), stage 1 (s1_cap), stage 2 (b_cap), in 8-byte words
+// (FP64 values or (hi, lo) FP32 pairs).  Units of elements whose mask entry is 0 (elem_mask,
+// optional) are taken from the queue and skipped.
+template <class A>
 __global__ void __launch_bounds__(512) k_contract_ffb(ContractLaunch L) {
+    using T = typename A::T;
+    static_assert(sizeof(T) == 8, "8-byte words");
     extern __shared__ __align__(16) unsigned char smraw[];
-    float2* sI = reinterpret_cast<float2*>(smraw);  // moments of the unit's pair, [k][l][q]
-    float2* sA = sI + L.a_cap;                          // stage 1, [im1][m2][l][q]
-    float2* sB = sA + L.s1_cap;                         // stage 2, [combination][q] (odd stride)
+    T* sI = reinterpret_cast<T*>(smraw);  // moments of the unit's pair, [k][l][q]
+    T* sA = sI + L.a_cap;                  // stage 1, [im1][m2][l][q]
+    T* sB = sA + L.s1_cap;                 // stage 2, [combination][q] (odd stride)
     __shared__ ContractUnit s_cu[2], s_nx[2];  // e = -1: no unit
     const int tid = threadIdx.x, nth = blockDim.x;
     const unsigned long long nu = (unsigned long long)L.n_units;
@@ -216,9 +248,9 @@ __global__ void __launch_bounds__(512) k_contract_ffb(ContractLaunch L) {
     __syncthreads();
     if (s_cu[0].e >= 0) {
         const ContractUnit u = s_cu[0];
-        const float2* gI = ffb_moments(L, u);
+        const size_t m0 = ffb_moments(L, u);
         const int cnt = unit_moment_count(L.desc + u.e, u.gi, u.gj);
-        for (int i = tid; i < cnt; i += nth) sI[i] = __ldg(gI + i);
+        for (int i = tid; i < cnt; i += nth) sI[i] = A::load_moment(L.mom, m0 + i);
     }
     __syncthreads();
     for (int iter = 0;; ++iter) {
@@ -229,19 +261,22 @@ __global__ void __launch_bounds__(512) k_contract_ffb(ContractLaunch L) {
         const int gi = cu.gi, gj = cu.gj, t = cu.t, m1a = cu.m1a, m1n = cu.m1n;
         const FfbShape s = ffb_shape(d, gi, gj);
         const int64_t n = d->n;
-        ffb_stage1(L, t, sI, sA, s, m1a, m1n, tid, nth);
+        const bool skip = L.elem_mask && !L.elem_mask[cu.e];  // uniform: cu is shared
+        if (!skip) ffb_stage1<A>(L, t, sI, sA, s, m1a, m1n, tid, nth);
         __syncthreads();  // stage-1 results complete; the moment buffer is free
         const ContractUnit nx = s_nx[par];
         if (nx.e >= 0) {
-            const float2* gN = ffb_moments(L, nx);
+            const T* gN = reinterpret_cast<const T*>(L.mom) + ffb_moments(L, nx);
             const int cnt = unit_moment_count(L.desc + nx.e, nx.gi, nx.gj);
             for (int i = tid; i < cnt; i += nth) cp_async8(sI + i, gN + i);
         }
-        switch (t) {
-        case 0: ffb_stage2<0>(sA, sB, s, m1n, tid, nth); break;
-        case 1: ffb_stage2<1>(sA, sB, s, m1n, tid, nth); break;
-        case 2: ffb_stage2<2>(sA, sB, s, m1n, tid, nth); break;
-        default: ffb_stage2<3>(sA, sB, s, m1n, tid, nth); break;
+        if (!skip) {
+            switch (t) {
+            case 0: ffb_stage2<A, 0>(sA, sB, s, m1n, tid, nth); break;
+            case 1: ffb_stage2<A, 1>(sA, sB, s, m1n, tid, nth); break;
+            case 2: ffb_stage2<A, 2>(sA, sB, s, m1n, tid, nth); break;
+            default: ffb_stage2<A, 3>(sA, sB, s, m1n, tid, nth); break;
+            }
         }
         __syncthreads();  // stage-2 results complete
         // the unit's results are rows [rbase, rbase + m1n Nv_i Nw_i) x columns [col0, col0 + n_j)
@@ -251,12 +286,13 @@ __global__ void __launch_bounds__(512) k_contract_ffb(ContractLaunch L) {
         double* Mp = cu.tp >= 0 ? L.out + d->out_off + (int64_t)type_slot_ffb(L.types_mask, cu.tp) * n * n +
                                       (int64_t)col0 * n + rbase
                                 : nullptr;
-        const int ncombo = m1n * s.Nv_i * s.mjn;
+        const int ncombo = skip ? 0 : m1n * s.Nv_i * s.mjn;
+        const float rmjn = 1.f / (float)s.mjn;
         switch (t) {
-        case 0: ffb_stage3<0>(sB, s, ncombo, tid, nth, Mt, Mp, n); break;
-        case 1: ffb_stage3<1>(sB, s, ncombo, tid, nth, Mt, Mp, n); break;
-        case 2: ffb_stage3<2>(sB, s, ncombo, tid, nth, Mt, Mp, n); break;
-        default: ffb_stage3<3>(sB, s, ncombo, tid, nth, Mt, Mp, n); break;
+        case 0: ffb_stage3<A, 0>(sB, s, ncombo, tid, nth, Mt, Mp, n, rmjn); break;
+        case 1: ffb_stage3<A, 1>(sB, s, ncombo, tid, nth, Mt, Mp, n, rmjn); break;
+        case 2: ffb_stage3<A, 2>(sB, s, ncombo, tid, nth, Mt, Mp, n, rmjn); break;
+        default: ffb_stage3<A, 3>(sB, s, ncombo, tid, nth, Mt, Mp, n, rmjn); break;
         }
         if (tid == 0) {  // the unit after next, into the other slot
             ContractUnit none{};
@@ -287,30 +323,44 @@ void contract_ffb_shape(const int8_t* Ni, const int8_t* Nj, int m1n, size_t& a_c
     b_cap = (size_t)combos * (Kw | 1);
 }
 
-cudaError_t contract_ffb_upload(const void* runs, size_t bytes) {
-    if (bytes != sizeof(c_runs)) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemcpyToSymbol(c_runs, runs, bytes);
-    if (e != cudaSuccess) return e;
+template <class A>
+cudaError_t ffb_set_attr() {
     cudaFuncAttributes fa;
-    e = cudaFuncGetAttributes(&fa, k_contract_ffb);
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_contract_ffb<A>);
     if (e != cudaSuccess) return e;
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_contract_ffb, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_contract_ffb<A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 optin - (int)fa.sharedSizeBytes);
 }
 
-cudaError_t launch_contract_ffb(const ContractLaunch& L, int grid, int threads, size_t smem, cudaStream_t s) {
+cudaError_t contract_ffb_upload(const void* runs_ff, size_t bytes_ff, const double* runs64, size_t bytes64) {
+    if (bytes_ff != sizeof(c_runs) || bytes64 != sizeof(c_runs64)) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemcpyToSymbol(c_runs, runs_ff, bytes_ff);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_runs64, runs64, bytes64);
+    if (e == cudaSuccess) e = ffb_set_attr<ArithFF>();
+    if (e == cudaSuccess) e = ffb_set_attr<ArithF64>();
+    return e;
+}
+
+cudaError_t launch_contract_ffb(int precision, const ContractLaunch& L, int grid, int threads, size_t smem,
+                                cudaStream_t s) {
     if (threads < 32 || threads > 512 || threads % 32) return cudaErrorInvalidValue;
-    k_contract_ffb<<<grid, threads, smem, s>>>(L);
+    if (precision == P2S_MIXED)
+        k_contract_ffb<ArithFF><<<grid, threads, smem, s>>>(L);
+    else
+        k_contract_ffb<ArithF64><<<grid, threads, smem, s>>>(L);
     return cudaGetLastError();
 }
 
-int contract_ffb_blocks_per_sm(int threads, size_t smem) {
+int contract_ffb_blocks_per_sm(int precision, int threads, size_t smem) {
     int nb = 0;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_contract_ffb, threads, smem) == cudaSuccess ? nb : 0;
+    const cudaError_t e =
+        precision == P2S_MIXED ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_contract_ffb<ArithFF>, threads, smem)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_contract_ffb<ArithF64>, threads, smem);
+    return e == cudaSuccess ? nb : 0;
 }
 
 }  // namespace p2s

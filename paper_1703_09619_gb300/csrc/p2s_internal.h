@@ -163,15 +163,17 @@ int contract_opn_max_order();
 void contract_ff_shape(int N, int m1n, size_t& a_cap, size_t& b_cap, size_t& tile_cap, int& combos);
 cudaError_t launch_contract_ffn(int N, const ContractLaunch& L, int grid, int threads, size_t smem, cudaStream_t s);
 int contract_ffn_blocks_per_sm(int N, int threads, size_t smem);
-// contract_ffb.cu: mixed contraction for uneven per-axis orders, each at most 8.  Units hold
-// full n1 ranges; a_cap / s1_cap / b_cap of the launch are the moment, stage-1 and stage-2
-// buffer sizes in float2.
+// contract_ffb.cu: contraction for per-axis orders at most 8, FP64 or mixed.  Units hold full
+// n1 ranges; a_cap / s1_cap / b_cap of the launch are the moment, stage-1 and stage-2 buffer
+// sizes in 8-byte words.
 bool contract_ffb_fits(const int8_t* Ni, const int8_t* Nj);
 void contract_ffb_shape(const int8_t* Ni, const int8_t* Nj, int m1n, size_t& a_cap, size_t& s1_cap, size_t& b_cap,
                         int& combos);
-cudaError_t contract_ffb_upload(const void* runs, size_t bytes);
-cudaError_t launch_contract_ffb(const ContractLaunch& L, int grid, int threads, size_t smem, cudaStream_t s);
-int contract_ffb_blocks_per_sm(int threads, size_t smem);
+// the coefficient runs ([4][8][8][8]) as (hi, lo) FP32 pairs and as FP64 values
+cudaError_t contract_ffb_upload(const void* runs_ff, size_t bytes_ff, const double* runs64, size_t bytes64);
+cudaError_t launch_contract_ffb(int precision, const ContractLaunch& L, int grid, int threads, size_t smem,
+                                cudaStream_t s);
+int contract_ffb_blocks_per_sm(int precision, int threads, size_t smem);
 // operator plans of one component and uniform order N (2..6), mixed precision (contract_ff.cu)
 cudaError_t launch_contract_opn(int N, const ContractLaunch& L, int grid, int threads, size_t smem, cudaStream_t s);
 int contract_opn_blocks_per_sm(int N, int threads, size_t smem);
@@ -227,7 +229,7 @@ struct PlanLayout {
     int op = 0;      // 1: an operator plan (term list), one n x n matrix per element
     int out_ff = 0;  // operator plans, mixed precision: entries written as (hi, lo) FP32 pairs
     int spec_op = 0; // > 0: an operator plan of one component and uniform order spec_op (k_contract_opn)
-    int ffb = 0;     // 1: the mixed contraction for uneven orders <= 8 (k_contract_ffb)
+    int ffb = 0;     // 1: the contraction for orders <= 8 (k_contract_ffb)
     TileParams tile;  // the tile configuration in effect
 };
 

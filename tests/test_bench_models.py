@@ -102,17 +102,21 @@ def test_library_run_counts_match_numpy():
                 assert cnt[t, a, b] == nnz_runs(d1, d2, a, b), (t, a, b)
 
 
-def test_bench_names_the_mixed_kernel_the_library_picks():
-    """The bench labels its roofline with the contraction kernel the plan runs: the per-order
-    kernel for uniform orders 2..8, the bounded-order kernel for uneven orders <= 8, the
-    general kernel above 8 or when the tile names it."""
-    k = bench.mixed_contract_kernel
+def test_bench_names_the_kernel_the_library_picks():
+    """The bench labels its roofline with the contraction kernel the plan runs: mixed, the
+    per-order kernel for uniform orders 2..8 and the bounded-order kernel for uneven orders
+    <= 8; FP64, the bounded-order kernel for orders <= 8; the general kernel above 8 or when
+    the tile names it."""
+    k = bench.contract_kernel
     assert k(np.full((3, 3, 3), 4)) == "k_contract_ffn<4>"
     assert k(np.full((3, 1, 3), 8)) == "k_contract_ffn<8>"
-    assert k(np.full((3, 1, 3), 8), kernel=2) == "k_contract_ffb"
+    assert k(np.full((3, 1, 3), 8), kernel=2) == "k_contract_ffb<ArithFF>"
     assert k(np.full((3, 3, 3), 4), kernel=1) == "k_contract<ArithFF>"
+    assert k(np.full((3, 3, 3), 6), mixed=False) == "k_contract_ffb<ArithF64>"
+    assert k(np.full((3, 3, 3), 6), mixed=False, kernel=1) == "k_contract<ArithF64>"
     uneven = np.array([[[2, 3, 8], [8, 8, 8], [1, 2, 3]]])
-    assert k(uneven) == "k_contract_ffb"
-    assert k(np.full((2, 1, 3), 1)) == "k_contract_ffb"
+    assert k(uneven) == "k_contract_ffb<ArithFF>"
+    assert k(np.full((2, 1, 3), 1)) == "k_contract_ffb<ArithFF>"
     uneven[0, 1, 2] = 9
     assert k(uneven) == "k_contract<ArithFF>"
+    assert k(uneven, mixed=False) == "k_contract<ArithF64>"

@@ -88,40 +88,42 @@ def with_orders(wl, lo, hi, seed):
     return dataclasses.replace(wl, orders=rng.integers(lo, hi + 1, size=wl.orders.shape).astype(np.int32))
 
 
+@pytest.mark.parametrize("prec", [p2s.FP64, p2s.MIXED])
 @pytest.mark.parametrize("mask", [0xF, 0x1, 0x2, 0x4, 0x8, 0x6, 0x9])
-def test_bounded_order_kernel_matches_general_bitwise(torch, ctx, mask):
-    """Uneven orders 1..8, mixed: the bounded-order kernel (default) and the general kernel
-    compute every entry with the same operations in the same order -- identical bits, for
-    every product-type subset (vd alone is computed directly, not as a transpose)."""
+def test_bounded_order_kernel_matches_general_bitwise(torch, ctx, mask, prec):
+    """Uneven orders 1..8: the bounded-order kernel (default) and the general kernel compute
+    every entry with the same operations in the same order -- identical bits, in either
+    precision and for every product-type subset (vd alone is computed directly, not as a
+    transpose)."""
     wl = with_orders(uneven(20, 5), 1, 8, 17)
-    ref, cfg = fill(torch, ctx, wl, p2s.MIXED, tile={"kernel": 1}, types_mask=mask)
+    ref, cfg = fill(torch, ctx, wl, prec, tile={"kernel": 1}, types_mask=mask)
     assert cfg["kernel"] == 1
     for tile in (None, {"combo_target": 1, "threads": 64}, {"combo_target": 512, "threads": 256, "kernel": 2}):
-        got, cfg = fill(torch, ctx, wl, p2s.MIXED, tile=tile, types_mask=mask)
+        got, cfg = fill(torch, ctx, wl, prec, tile=tile, types_mask=mask)
         assert cfg["kernel"] == (tile or {}).get("kernel", 0)
         assert np.array_equal(got, ref), (mask, tile)
 
 
+@pytest.mark.parametrize("prec", [p2s.FP64, p2s.MIXED])
 @pytest.mark.parametrize("name,N", [("c5", 4), ("c3", 8), ("c2", 6)])
-def test_uniform_orders_all_kernels_bitwise(torch, ctx, name, N):
-    """Uniform orders, mixed: the per-order kernel (default), the bounded-order kernel and the
-    general kernel give identical bits."""
+def test_uniform_orders_all_kernels_bitwise(torch, ctx, name, N, prec):
+    """Uniform orders: the library's kernel (mixed: per-order; FP64: bounded-order), the
+    bounded-order kernel and the general kernel give identical bits."""
     wl = W.make(name, 3).with_npts(5)
     assert (wl.orders == N).all()
-    ref, _ = fill(torch, ctx, wl, p2s.MIXED, tile={"kernel": 1})
+    ref, _ = fill(torch, ctx, wl, prec, tile={"kernel": 1})
     for tile in (None, {"kernel": 2}, {"kernel": 2, "combo_target": 64, "threads": 128}):
-        got, _ = fill(torch, ctx, wl, p2s.MIXED, tile=tile)
+        got, _ = fill(torch, ctx, wl, prec, tile=tile)
         assert np.array_equal(got, ref), (name, tile)
 
 
-def test_bounded_order_kernel_refuses_what_it_cannot_take(torch, ctx):
+@pytest.mark.parametrize("prec", [p2s.FP64, p2s.MIXED])
+def test_bounded_order_kernel_refuses_orders_above_its_bound(torch, ctx, prec):
     wl = with_orders(uneven(4, 5), 2, 8, 31)
-    with pytest.raises(p2s.P2SError) as ex:  # FP64
-        p2s.Plan(ctx, wl.orders, 5, p2s.FP64, tile={"kernel": 2})
-    assert ex.value.code == p2s.ERR_ORDER
-    wl.orders[0, 0, 0] = 9  # an order above the bound
+    p2s.Plan(ctx, wl.orders, 5, prec, tile={"kernel": 2}).close()
+    wl.orders[0, 0, 0] = 9
     with pytest.raises(p2s.P2SError) as ex:
-        p2s.Plan(ctx, wl.orders, 5, p2s.MIXED, tile={"kernel": 2})
+        p2s.Plan(ctx, wl.orders, 5, prec, tile={"kernel": 2})
     assert ex.value.code == p2s.ERR_ORDER
 
 
@@ -143,12 +145,13 @@ def test_bounded_order_kernel_against_oracle(torch, ctx):
             assert np.abs(a - b).max() <= 1e-8 * np.abs(b).max(), (e, t)
 
 
-def test_order_above_bound_takes_general_kernel(torch, ctx):
+@pytest.mark.parametrize("prec", [p2s.FP64, p2s.MIXED])
+def test_order_above_bound_takes_general_kernel(torch, ctx, prec):
     """An order above 8 anywhere in the batch: the general kernel for the whole batch, same bits."""
     wl = with_orders(uneven(8, 5), 2, 8, 29)
     wl.orders[3, 1, 2] = 9
-    ref, _ = fill(torch, ctx, wl, p2s.MIXED, tile={"kernel": 1})
-    got, _ = fill(torch, ctx, wl, p2s.MIXED)
+    ref, _ = fill(torch, ctx, wl, prec, tile={"kernel": 1})
+    got, _ = fill(torch, ctx, wl, prec)
     assert np.array_equal(got, ref)
 
 
