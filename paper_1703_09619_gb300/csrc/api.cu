@@ -404,7 +404,7 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
     if (per_sm < 1) return fail(P2S_ERR_ORDER, "plan: moment kernel does not fit");
     L.mom_grid = (int)std::max<int64_t>(1, std::min<int64_t>(E, (int64_t)T.sm_count * per_sm));
 
-    // contraction launch shape of the general kernel (the specialised one replaces it below)
+    // contraction launch shape of the general kernel (a specialised kernel's shape replaces it below)
     if (moments_only) return P2S_OK;
     rc = general_contract_shape(T, E, desc, nc, tile, !spec_n && !ffb, limit, L);
     if (rc) return rc;
