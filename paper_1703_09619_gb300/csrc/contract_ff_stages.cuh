@@ -1,8 +1,8 @@
-// Shared pieces of the specialised mixed-precision contractions (contract_ff.cu: the four uniform
-// product types; contract_opn.cu: operator term lists): the compile-time coefficient runs of
+// Shared pieces of the specialised contractions (contract_ff.cu: the four uniform product types;
+// contract_ffb.cu: orders up to 8; contract_opn.cu: operator term lists): the compile-time coefficient runs of
 // Eq. (3) for Legendre products, the coefficient table in constant memory (one copy per
-// translation unit, both filled by contract_ff_upload), stages 1 and 2 of the contraction of
-// Eq. (4), and a 256-bit streaming store.
+// translation unit, all filled by contract_ff_upload), stages 1 and 2 of the contraction of
+// Eq. (4), an asynchronous 8-byte copy into shared memory and a 256-bit streaming store.
 #pragma once
 
 #include "arith.cuh"
@@ -77,9 +77,13 @@ __device__ __forceinline__ void stages12(const float2* __restrict__ sI, float2* 
     }
 }
 
-// Stage 3 and both write-outs for one (m1, n1, m2, n2) combination per thread.
-// Mt points at (row rbase, column col0) of M_t; Mp (or nullptr) at (row col0, column
-// rbase) of the partner block; n is the row stride of the element's matrices.
+// 8-byte asynchronous global -> shared copy (complete after cp_async_wait_all).
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    const unsigned sh = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sh), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Streaming 256-bit store of four doubles (a whole 32-byte sector; p 32-byte aligned).  Two
 // 16-byte stores per sector would send each sector to L2 in two halves.
 __device__ __forceinline__ void st_cs_v4(double* p, double a, double b, double c, double d) {

@@ -68,13 +68,6 @@ __device__ __forceinline__ size_t ffb_moments(const ContractLaunch& L, const Con
     return (size_t)d->mom_off + d->pair_off[pair_index(u.gi, u.gj, d->n_comp)];
 }
 
-// 8-byte asynchronous global -> shared copy (completes at cp_async_wait_all).
-__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 // Stage 1 of one unit (any type; runs from the table): items (im1, m2, l, q),
 //   A[im1][m2][l][q] = sum_k C[m1,m2,k] I[k][l][q].
 template <class A>
