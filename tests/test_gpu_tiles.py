@@ -166,15 +166,17 @@ def test_bad_tile_config(torch, ctx):
         assert ex.value.code == p2s.ERR_ARG
 
 
-def test_autotune_picks_a_fitting_config(torch, ctx):
+@pytest.mark.parametrize("prec", [p2s.FP64, p2s.MIXED])
+def test_autotune_picks_a_fitting_config(torch, ctx, prec):
+    """The tuner's pick (shape and kernel) fits and gives the default plan's bits."""
     wl = uneven(96, 8)
     params, nodes, bulge = p2s.device_inputs(wl)
-    best, ms, tried = p2s.autotune_tiles(ctx, wl.orders, 8, wl.kind, params, nodes, bulge, p2s.MIXED,
+    best, ms, tried = p2s.autotune_tiles(ctx, wl.orders, 8, wl.kind, params, nodes, bulge, prec,
                                          sample=48, reps=2)
     assert tried >= 1 and ms > 0
-    assert 1 <= best["combo_target"] <= 4096 and 64 <= best["threads"] <= 512
-    got, cfg = fill(torch, ctx, wl, p2s.MIXED, tile=best)
-    ref, _ = fill(torch, ctx, wl, p2s.MIXED)
+    assert 1 <= best["combo_target"] <= 4096 and 64 <= best["threads"] <= 512 and best["kernel"] in (0, 2)
+    got, cfg = fill(torch, ctx, wl, prec, tile=best)
+    ref, _ = fill(torch, ctx, wl, prec)
     assert np.array_equal(got, ref)
     assert cfg["threads"] == best["threads"]
 
