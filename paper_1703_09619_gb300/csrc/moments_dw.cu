@@ -132,13 +132,6 @@ __device__ __forceinline__ bool metric_alpha_dw(const dw* geo, const dw* row, co
 struct Chunk {
     int c, b0, nbc;
 };
-__device__ __forceinline__ Chunk chunk_of(int t, int ncp, float rncp, int nb, int G) {
-    Chunk ch;
-    ch.c = div_small(t, ncp, rncp);
-    ch.b0 = (t - ch.c * ncp) * nb;
-    ch.nbc = min(nb, G - ch.b0);
-    return ch;
-}
 
 // n / d with d a compile-time constant when D > 0 (a multiply-shift), else by the FP32
 // reciprocal rd of the runtime d.
@@ -205,7 +198,6 @@ __device__ __forceinline__ void element_pipeline(const MomentLaunch& L, const Sm
     const int Ku = kSpec ? KC : d.kax[0], Kv = kSpec ? KC : d.kax[1], Kw = kSpec ? KC : d.kax[2];
     const int Kb = kSpec ? KC : max(Ku, max(Kv, Kw));
     constexpr int KCs = kSpec ? KC : 0;
-    constexpr int KK = kSpec ? KC * KC : 0;
     constexpr int HC = kSpec ? (GC + 1) / 2 : 0, LRC = 2 * HC;
     constexpr int NBC = kSpec ? (kChunk / LRC < GC ? (kChunk / LRC > 0 ? kChunk / LRC : 1) : GC) : 0;
     constexpr int NCPC = kSpec ? (GC + NBC - 1) / NBC : 0;
