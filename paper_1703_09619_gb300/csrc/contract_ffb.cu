@@ -14,7 +14,8 @@
 //   - stage 3 gives each thread one (m1, n1, m2, n2) combination and up to 4 x 8 (p1, p2)
 //     results in registers (2 x 8 in FP64; further p1 rows in later passes), stored straight
 //     from registers in both orientations: no shared-memory tile and no write-out pass.
-// The next unit's moments arrive in shared memory by cp.async while stage 3 runs.
+// The next unit's moments arrive in shared memory by cp.async while stages 2 and 3 run, and
+// units of elements whose mask entry is 0 (optional) are skipped.
 #include <type_traits>
 
 #include "contract_ff_stages.cuh"
