@@ -174,7 +174,7 @@ cudaError_t contract_ffb_upload(const void* runs_ff, size_t bytes_ff, const doub
 cudaError_t launch_contract_ffb(int precision, const ContractLaunch& L, int grid, int threads, size_t smem,
                                 cudaStream_t s);
 int contract_ffb_blocks_per_sm(int precision, int threads, size_t smem);
-// operator plans of one component and uniform order N (2..6), mixed precision (contract_ff.cu)
+// operator plans of one component and uniform order N (2..6), mixed precision (contract_opn.cu)
 cudaError_t launch_contract_opn(int N, const ContractLaunch& L, int grid, int threads, size_t smem, cudaStream_t s);
 int contract_opn_blocks_per_sm(int N, int threads, size_t smem);
 // fills contract_opn.cu's copy of the coefficient runs ([4][8][8][8] (hi, lo) pairs)
