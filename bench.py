@@ -288,12 +288,22 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+L2_BYTES = 129 << 20  # GB300 L2 (126 MiB usable, 129 MB nominal)
+
+
+def l2_note(out_bytes):
+    """How a step's output relates to L2 (between timed steps the bench writes 256 MB to flush it)."""
+    size = "%.1f GB" % (out_bytes / 1e9) if out_bytes >= 1e8 else "%.2f MB" % (out_bytes / 1e6)
+    rel = "exceed L2; L2 also flushed" if out_bytes > L2_BYTES else "fit in L2; L2 flushed"
+    return "outputs (%s) %s (256 MB write) between steps" % (size, rel)
+
+
 def workload_config(args, wl):
     o = wl.orders
     cfg = {"workload": "%s: %s" % (args.workload, wl.description), "elements": wl.n_elem,
            "n_comp": wl.n_comp, "orders": "uniform %d" % o[0, 0, 0] if (o == o[0, 0, 0]).all() else "mixed",
            "mode": args.mode, "entries_per_step": wl.entries(),
-           "l2": "outputs (%.1f GB) exceed L2; L2 also flushed (256 MB write) between steps" % (8e-9 * wl.entries())}
+           "l2": l2_note(8 * wl.entries())}
     if args.mode == "learned":
         cfg.update({"npts": "learned per element, classes 8/12/16/24/32/48", "plain_npts": 48,
                     "precision": "mixed (float-float contraction, FP64 output)", "risk": RISK,
