@@ -11,9 +11,13 @@
 // 18.3 MiB), present on every GPU that loads this library until the process exits.
 // It holds the moment tensors between the two kernels, the per-element descriptors,
 // the contraction work list and the two work-queue counters (contraction units, moment
-// elements).  Its device address is taken
-// once per device with cudaGetSymbolAddress (the host-side name of the array is only a
-// stand-in and must never be passed to a kernel).
+// elements).  Its device address is taken once per device with cudaGetSymbolAddress, by
+// p2s_create (noalloc_prepare below), with that device current: the host-side name of
+// the array is only a stand-in and must never be passed to a kernel.  Doing the look-up
+// there matters because the runtime may load this file's module (and place the array in
+// device memory) only when the address is first asked for; a caller that has handed all
+// free device memory to its own pool after p2s_create must not meet that load inside
+// the fill.
 #include <cstring>
 #include <mutex>
 
@@ -42,6 +46,19 @@ ElemDesc g_na_desc[kNaMaxElems];         // host staging of the descriptors
 ContractUnit g_na_units[kNaMaxUnits];    // host staging of the work list
 
 }  // namespace
+
+// Called by p2s_create with `device` current: look the array up once for this device.
+int noalloc_prepare(int device) {
+    if (device < 0 || device >= kNaMaxDevices) return P2S_OK;  // the fill refuses such devices
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (g_na_addr[device]) return P2S_OK;
+    void* ptr = nullptr;
+    const cudaError_t ce = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (ce != cudaSuccess) return fail(P2S_ERR_CUDA, "p2s_create: cudaGetSymbolAddress of the no-alloc scratch", ce);
+    g_na_addr[device] = static_cast<unsigned char*>(ptr);
+    return P2S_OK;
+}
+
 }  // namespace p2s
 
 using namespace p2s;
@@ -62,13 +79,8 @@ extern "C" int p2s_fill_elements_noalloc(p2s_ctx* ctx, const p2s_geometry* geom,
     std::lock_guard<std::mutex> lock(g_na_mutex);
     cudaError_t ce = cudaSetDevice(T->device);
     if (ce != cudaSuccess) return fail(P2S_ERR_CUDA, "p2s_fill_elements_noalloc: cudaSetDevice", ce);
-    if (!g_na_addr[T->device]) {  // first call on this device: look the array up
-        void* ptr = nullptr;
-        ce = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (ce != cudaSuccess) return fail(P2S_ERR_CUDA, "p2s_fill_elements_noalloc: cudaGetSymbolAddress", ce);
-        g_na_addr[T->device] = static_cast<unsigned char*>(ptr);
-    }
-    unsigned char* base = g_na_addr[T->device];
+    unsigned char* base = g_na_addr[T->device];  // looked up by p2s_create
+    if (!base) return fail(P2S_ERR_CUDA, "p2s_fill_elements_noalloc: scratch address missing for this device");
     void* d_mom = base;
     ElemDesc* d_desc = reinterpret_cast<ElemDesc*>(base + kNaMomBytes);
     ContractUnit* d_units = reinterpret_cast<ContractUnit*>(base + kNaMomBytes + kNaDescBytes);

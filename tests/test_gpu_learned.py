@@ -195,3 +195,55 @@ def test_training_gains_over_full_order(torch, ctx):
     assert acc > 0.5, acc
     assert under < 0.25, under
     assert work_ratio > 3.0, work_ratio
+
+
+RISK = 0.002  # the class rule the benchmark uses (R13)
+
+
+def test_learned_fill_matches_oracle_multiclass(torch, ctx):
+    """The committed network on a c5 subset whose predictions span at least three classes
+    (G = 32 among them), with a judge tolerance no fill can meet so that the fallback runs:
+    every element that kept its learned fill equals the oracle at the G reported for it
+    (Eq. (2) at that rule, <= 1e-8, the mixed bar), and every judged element that failed
+    equals the oracle at 48 points (<= 1e-12, the plain FP64 bar).  This runs the device
+    side class assignment (per-element G, class-grouped element queue) with several
+    classes in one launch."""
+    P, _ = LN.load_checkpoint()
+    pool = W.make("c5", 4096)
+    pred = LN.predict(ctx, P, LN.features(ctx, pool), risk=RISK)
+    pick = []
+    for G in sorted(set(pred.tolist())):
+        pick += np.flatnonzero(pred == G)[:3].tolist()
+    assert len(set(pred[pick].tolist())) >= 3 and 32 in pred[pick], np.unique(pred, return_counts=True)
+    sub = pool.subset(sorted(pick))
+    E = sub.n_elem
+    # a seed whose judged set leaves an unjudged element of every class
+    cls_of = pred[sorted(pick)]
+    for seed in range(1, 200):
+        js = p2s.judge_select(E, 0.5, seed)
+        if js.any() and all((~js & (cls_of == G)).any() for G in set(cls_of.tolist())):
+            break
+    params, nodes, bulge = p2s.device_inputs(sub)
+    lp = p2s.LearnedPlan(ctx, sub.orders, margin=0, precision=p2s.MIXED, judge_frac=0.5, seed=seed,
+                         judge_tol=1e-15, risk=RISK)
+    out = torch.full((lp.output_entries,), float("nan"), dtype=torch.float64, device="cuda")
+    npts = torch.empty(E, dtype=torch.int32, device="cuda")
+    lp.fill(sub.kind, params, nodes, bulge, torch.as_tensor(P, device="cuda"), out, npts)
+    rep = lp.report(judge_state=True)
+    st = rep["judge_state"]
+    lp.close()
+    g_used = npts.cpu().numpy()
+    assert np.array_equal(g_used, cls_of)  # the same prediction inside the fill
+    assert rep["failed"] == int((st == 2).sum()) and rep["failed"] > 0
+    o = out.cpu().numpy()
+    off = oracle.output_offsets(sub.orders)
+    for e in range(E):
+        one = sub.subset([e])
+        G = 48 if st[e] == 2 else int(g_used[e])
+        ref, roff, _ = oracle.fill(one.orders, one.kind, one.params, one.nodes, one.bulge, G)
+        got = o[off[e]:off[e + 1]]
+        mg = oracle.element_matrices(got, roff, one.orders, 0)
+        mr = oracle.element_matrices(ref, roff, one.orders, 0)
+        err = max(np.abs(mg[t] - mr[t]).max() / np.abs(mr[t]).max() for t in mr)
+        tol = 1e-12 if st[e] == 2 else 1e-8
+        assert err <= tol, (e, int(g_used[e]), int(st[e]), err)
