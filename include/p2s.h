@@ -283,8 +283,9 @@ int p2s_fill_elements(p2s_ctx* ctx, const p2s_geometry* geom, const p2s_material
  *   contraction work units; larger requests return P2S_ERR_BUFFER with a message in
  *   p2s_last_error and launch nothing -- split the batch.  (Three-component N = 6
  *   elements fit 262 per call, N = 4 elements 1019.)
- *   Set-up: the first call on each device looks up the array's device address with that
- *   device current; make that first call before any stream capture.
+ *   Set-up: p2s_create looks up the array's device address for its device (that look-up
+ *   may load the library's module for the array, which places the array in device
+ *   memory), so this call itself loads nothing and allocates nothing.
  *   Sharing: every call uses the same array, which keeps the previous call's contents
  *   (each call rewrites what it reads, and clears its counter).  Calls whose kernels
  *   overlap on the GPU -- on different streams or from different threads without
@@ -492,6 +493,25 @@ int p2s_sync_status(p2s_ctx* ctx, void* stream);
  * p2s_gauss_legendre: the G-point rule the kernels use (x ascending). */
 int p2s_linearisation(int t, int m1, int m2, int kmax, double* C);
 int p2s_gauss_legendre(int G, double* x, double* w);
+
+/* Device throughput probes.  The paper measures on a CPU and has no counterpart; these
+ * are the denominators of the roofline fractions that a fill's kernels are reported
+ * against (FP64 pipe, FP32 pipe, store-only HBM stream).
+ *   fp64_fma_tflops / fp32_fma_tflops: independent FMA chains on 2048 threads per SM,
+ *     2 flop per FMA, best of 5 timed launches (CUDA events) after one warm-up launch;
+ *   hbm_write_gbs: 16-byte streaming stores over a device buffer of write_bytes
+ *     (>= 1 MiB; use several times the L2 size), best of 5.
+ * fp32_ms, fp64_ms, write_ms: the kept launch times; write_bytes: the buffer used.
+ * The call allocates and frees a device buffer of write_bytes, runs on `stream` and
+ * synchronises it.  Errors: P2S_ERR_ARG, P2S_ERR_OOM, P2S_ERR_CUDA. */
+typedef struct {
+    double fp64_fma_tflops;
+    double fp32_fma_tflops;
+    double hbm_write_gbs;
+    double fp64_ms, fp32_ms, write_ms;
+    int64_t write_bytes;
+} p2s_peaks;
+int p2s_measure_peaks(p2s_ctx* ctx, int64_t write_bytes, p2s_peaks* out, void* stream);
 
 /* Static description of an error code. */
 const char* p2s_error_string(int code);

@@ -593,7 +593,7 @@ static int ctx_init(p2s_ctx* c, int device) {
     P2S_CUDA(learned_init_attributes());
     D.spec_ok = contract_ff_runs_match(T);
     if (D.spec_ok) P2S_CUDA(contract_ff_upload(T));
-    return P2S_OK;
+    return noalloc_prepare(device);
 }
 
 int p2s_create(p2s_ctx** out, int device) {
@@ -1074,6 +1074,12 @@ int p2s_sync_status(p2s_ctx* ctx, void* stream) {
     P2S_CUDA(cudaMemcpy(&h, ctx->T.err, sizeof(int), cudaMemcpyDeviceToHost));
     if (h != 0) P2S_CUDA(cudaMemset(ctx->T.err, 0, sizeof(int)));
     return h;
+}
+
+int p2s_measure_peaks(p2s_ctx* ctx, int64_t write_bytes, p2s_peaks* out, void* stream) {
+    if (!ctx) return fail(P2S_ERR_ARG, "p2s_measure_peaks: NULL context");
+    if (set_device(ctx->T.device)) return P2S_ERR_CUDA;
+    return measure_peaks(ctx->T, write_bytes, out, (cudaStream_t)stream);
 }
 
 }  // extern "C"

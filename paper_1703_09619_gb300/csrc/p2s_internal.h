@@ -276,6 +276,11 @@ struct OpArrays {
     const int32_t* block;
     int nalpha;
 };
+// Looks up the allocation-free fill's fixed scratch array for `device` (current), once per
+// device; p2s_create calls it so that the fill itself never triggers the array's load.
+int noalloc_prepare(int device);
+// Throughput probes behind p2s_measure_peaks (peaks.cu).
+int measure_peaks(const DeviceTables& T, int64_t write_bytes, p2s_peaks* out, cudaStream_t s);
 int run_contract(const DeviceTables& T, const PlanLayout& L, const ElemDesc* d_desc, const ContractUnit* d_units,
                  unsigned long long* d_counter, const void* moments, double* out, cudaStream_t s,
                  const int8_t* elem_mask = nullptr, const OpArrays* op = nullptr);

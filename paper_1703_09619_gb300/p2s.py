@@ -140,10 +140,17 @@ SIGNATURES = {
     "p2s_learned_plan_output_entries": (_I64, [_P]),
     "p2s_learned_fill": (ctypes.c_int, [_P, ctypes.POINTER(Geometry), ctypes.POINTER(Material), _P, _P, _P, _P]),
     "p2s_learned_report_get": (ctypes.c_int, [_P, _P, _P, _P]),
+    "p2s_measure_peaks": (ctypes.c_int, [_P, _I64, _P, _P]),
 }
 
 MLP_IN, MLP_HIDDEN, MLP_CLASSES, MLP_PARAMS = 576, 64, 6, 41478
 CLASS_NPTS = (8, 12, 16, 24, 32, 48)
+
+
+class Peaks(ctypes.Structure):
+    _fields_ = [("fp64_fma_tflops", ctypes.c_double), ("fp32_fma_tflops", ctypes.c_double),
+                ("hbm_write_gbs", ctypes.c_double), ("fp64_ms", ctypes.c_double), ("fp32_ms", ctypes.c_double),
+                ("write_ms", ctypes.c_double), ("write_bytes", ctypes.c_int64)]
 
 
 class LearnedOpts(ctypes.Structure):
@@ -625,3 +632,12 @@ class LearnedPlan:
         if judge_state:
             d["judge_state"] = js[: self.n_elem]
         return d
+
+
+def measure_peaks(ctx: Context, write_bytes=4 << 30, stream=None):
+    """p2s_measure_peaks: FP64 and FP32 FMA rates (TFLOP/s) and the store-only HBM rate (GB/s)
+    measured by the library's probe kernels on the context's device."""
+    pk = Peaks()
+    _check(load().p2s_measure_peaks(ctx.handle, int(write_bytes), ctypes.byref(pk), _stream(stream)),
+           "p2s_measure_peaks")
+    return {f: getattr(pk, f) for f, _ in Peaks._fields_}
