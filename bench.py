@@ -36,8 +36,9 @@ from paper_1703_09619_gb300 import workloads as W  # noqa: E402
 
 METRIC = "matrix entries/s: learned+mixed-prec vs plain FP64 fill, one GB300, rel err ≤1e-8"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 FMA rate of the part: 152 SMs x 2 DFMA/clk/SM (a throughput probe measured
-# 0.598 TFMA/s at the running clock), at the 2070 MHz maximum SM clock:
+# FP64 FMA, FP32 FMA and store-only HBM rates are measured in every run by the library's
+# probe kernels (p2s_measure_peaks); the values below are the unit-count fallbacks used only
+# if that call fails (152 SMs, 2 DFMA / 128 FFMA per clock per SM, 2070 MHz).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # FP64 operations per quadrature point of the metric coupling factor in the moment kernel
 # (Jacobian 45, phase 9, sin ~25, cofactors 18, det 3, products 18, division ~10, scale 6)
@@ -53,15 +54,18 @@ ALPHA_FLOP_PER_POINT = 134
 #   the scalar coupling factor at one point: 14;
 #   the parity fold of the first mode product, per point and pair: one sum (11) and two
 #   shuffles; the first mode product then runs over ceil(G/2) points per row.
-FP32_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
+FP32_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12  # FP32 issue slots (lane operations / s), unit counts
 # DRAM bytes (read + write) per element of the double-word moment kernel, from the full-size
 # ncu capture of the c5 learned fill (profiles/c5_learned_dram_full_size.md): 496,681,216
 # bytes for the 32,768-element launch.  It scales with elements (inputs in, moments out).
 MOMENTS_DW_DRAM_BYTES_PER_ELEMENT = 496681216 / 32768
 DW_MAC_OPS, DW_ALPHA_OPS_METRIC, DW_ALPHA_OPS_SCALAR, DW_FOLD_OPS = 12, 839, 14, 13
-# Learned-fill settings: judge share and tolerance; risk of the class rule (the largest
-# value of the sweep 0.02 .. 0.0005 with no element of the batch above 1e-8).
-JUDGE_FRAC, JUDGE_TOL, RISK = 0.02, 1e-9, 0.002
+# Learned-fill settings: judge share and tolerance.  The class rule's risk comes from the
+# checkpoint's metadata, where `python -m paper_1703_09619_gb300.learned --calibrate` keeps the
+# largest risk of its sweep whose held-out elements (shard 1 of the training recipe, neither
+# trained on nor benchmarked) all stay within 1e-8 of their 48-point FP64 fill.
+JUDGE_FRAC, JUDGE_TOL = 0.02, 1e-9
+RISK_DEFAULT = 0.002  # only for a checkpoint without a calibrated risk
 
 
 def log(*a):
@@ -74,6 +78,45 @@ def load_peaks():
             return json.load(f), "measured"
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+_DEV = {}  # this run's probe results (device_peaks)
+
+
+def fp64_peak():
+    """FP64 FMA rate (TFLOP/s) measured in this run, else the unit-count figure."""
+    return _DEV.get("fp64_fma_tflops") or FP64_PEAK_TFLOPS
+
+
+def fp32_issue_peak():
+    """FP32 lane operations per second (T/s): the measured FMA issue rate (half the measured
+    FP32 FMA flop rate), else the unit-count figure."""
+    v = _DEV.get("fp32_fma_tflops")
+    return v / 2 if v else FP32_PEAK_TOPS
+
+
+def peak_source(kind):
+    measured = bool(_DEV.get("fp64_fma_tflops")) and "probes failed" not in _DEV.get("source", "")
+    if kind == "fp64":
+        return ("FP64 FMA rate of this GPU, measured in this run (p2s_measure_peaks)" if measured
+                else "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (unit counts)")
+    return ("FP32 FMA issue rate of this GPU, measured in this run (p2s_measure_peaks), one lane operation per FMA"
+            if measured else "FP32 issue: 152 SMs x 128 lanes x 2.07 GHz (unit counts)")
+
+
+def device_peaks(p2s, ctx):
+    """FP64 / FP32 FMA and store-only HBM rates of this GPU from the library's probe kernels
+    (CUDA events, best of 5); the unit-count figures if the probes fail."""
+    try:
+        pk = p2s.measure_peaks(ctx, 4 << 30)
+        pk["source"] = "p2s_measure_peaks on this GPU in this run (probe kernels, CUDA events, best of 5)"
+        _DEV.clear()
+        _DEV.update(pk)
+        return pk
+    except Exception as e:  # noqa: BLE001
+        log("peak probes failed: %s" % e)
+        return {"fp64_fma_tflops": FP64_PEAK_TFLOPS, "fp32_fma_tflops": 2 * FP32_PEAK_TOPS, "hbm_write_gbs": None,
+                "source": "unit counts (probes failed)"}
 
 
 # ----------------------------------------------------------------------------- counting
@@ -243,18 +286,37 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- oracle legs
-def oracle_sample(wl, n_elem, seed=5):
-    """Time the CPU oracle on a seeded element sample; returns (entries/s, seconds, desc, threads)."""
-    import oracle
+def sample_indices(wl, n_elem, seed=5):
     rng = np.random.default_rng(seed)
-    idx = np.sort(rng.choice(wl.n_elem, size=min(n_elem, wl.n_elem), replace=False))
+    return np.sort(rng.choice(wl.n_elem, size=min(n_elem, wl.n_elem), replace=False))
+
+
+def oracle_sample(wl, n_elem, seed=5, keep=False):
+    """Time the CPU oracle on a seeded element sample; returns (entries/s, seconds, desc,
+    threads), plus (indices, oracle output, its offsets) with ``keep``."""
+    import oracle
+    idx = sample_indices(wl, n_elem, seed)
     sub = wl.subset(idx)
     threads = oracle.default_threads()
     t0 = time.perf_counter()
-    oracle.fill(sub.orders, sub.kind, sub.params, sub.nodes, sub.bulge, sub.npts, sub.types_mask, threads)
+    out, off, _ = oracle.fill(sub.orders, sub.kind, sub.params, sub.nodes, sub.bulge, sub.npts, sub.types_mask,
+                              threads)
     dt = time.perf_counter() - t0
-    return sub.entries() / dt, dt, "%d of %d elements (seed %d) at G=%s, every entry, all types" % (
-        idx.size, wl.n_elem, seed, ",".join(str(g) for g in sorted(set(sub.npts.tolist())))), threads
+    res = (sub.entries() / dt, dt, "%d of %d elements (seed %d) at G=%s, every entry, all types" % (
+        idx.size, wl.n_elem, seed, ",".join(str(g) for g in sorted(set(sub.npts.tolist())))), threads)
+    return res + ((idx, out, off, sub) if keep else ())
+
+
+def errors_vs_oracle(got_slices, ref, ref_off, sub):
+    """Per element max over product types of max|dM| / max|M| (R8) of GPU element slices
+    against the oracle's output of the same elements."""
+    import oracle
+    errs = []
+    for e, g in enumerate(got_slices):
+        mg = oracle.element_matrices(g, [0], sub.orders[e:e + 1], 0, sub.types_mask)
+        mr = oracle.element_matrices(ref, ref_off, sub.orders, e, sub.types_mask)
+        errs.append(float(max(np.abs(mg[t] - mr[t]).max() / max(np.abs(mr[t]).max(), 1e-300) for t in mr)))
+    return errs
 
 
 def cpu_sample_size(name):
@@ -298,7 +360,7 @@ def l2_note(out_bytes):
     return "outputs (%s) %s (256 MB write) between steps" % (size, rel)
 
 
-def workload_config(args, wl):
+def workload_config(args, wl, risk=None, risk_src=None):
     o = wl.orders
     cfg = {"workload": "%s: %s" % (args.workload, wl.description), "elements": wl.n_elem,
            "n_comp": wl.n_comp, "orders": "uniform %d" % o[0, 0, 0] if (o == o[0, 0, 0]).all() else "mixed",
@@ -306,7 +368,10 @@ def workload_config(args, wl):
            "l2": l2_note(8 * wl.entries())}
     if args.mode == "learned":
         cfg.update({"npts": "learned per element, classes 8/12/16/24/32/48", "plain_npts": 48,
-                    "precision": "mixed (float-float contraction, FP64 output)", "risk": RISK,
+                    "precision": "mixed (float-float contraction, FP64 output)",
+                    "risk": RISK_DEFAULT if risk is None else risk,
+                    "risk_source": ("held-out calibration kept in the checkpoint: %s" % risk_src.get("holdout")
+                                    if risk_src else "default (checkpoint without a calibrated risk)"),
                     "judge": "%.0f%% seeded, re-filled at 48 points in the fill's precision (side stream), tol %.0e; "
                              "failures replaced by the 48-point FP64 fill" % (100 * JUDGE_FRAC, JUDGE_TOL)})
     else:
@@ -371,46 +436,69 @@ def contract_kernel(orders, mixed=True, kernel=0):
 
 
 def roofline_for(wl, npts, prec, mom_ms, con_ms, peaks, src, kernel=0):
-    """Roofline object of the dominant kernel of a fill (the slower of the two stages)."""
+    """Roofline object of the dominant kernel of a fill (the slower of the two stages).
+
+    Moment stage (a1 + a2): the method's work is 2 x (K G^3 + K^2 G^2 + K^3 G) flop per
+    coupling pair (sum-factorised Eq. (4), first mode product unfolded) plus the coupling
+    factor's FP64-equivalent operations per point (ALPHA_FLOP_PER_POINT); the mixed form is
+    reported against the BF16 dense tensor peak (the roofline the moment contraction is
+    assigned) and, beside it, against the measured FP32 FMA rate; `issue_frac` is the
+    double-word kernel's FP32 instruction model over the measured FP32 issue rate.  The
+    FP64 form is reported against the measured FP64 FMA rate.  Contraction (a4): mixed
+    against HBM (8 B per stored entry over the copy bandwidth, and the store-only rate
+    beside it), FP64 against the measured FP64 FMA rate."""
     entries = wl.entries()
     fmas = contract_fma_count(wl.orders, wl.types_mask)
     metric = wl.kind == W.KIND_METRIC_EPS
     npts = np.broadcast_to(np.asarray(npts), (wl.n_elem,))
-    if mom_ms >= con_ms and prec != 0:
-        macs, pts, npairs = moment_mac_points(wl.orders, npts, folded=True)
-        per_point = (DW_ALPHA_OPS_METRIC if metric else DW_ALPHA_OPS_SCALAR) + DW_FOLD_OPS * npairs
-        ops = DW_MAC_OPS * macs + per_point * pts
-        ach = ops / (mom_ms * 1e-3) / 1e12
-        traffic = MOMENTS_DW_DRAM_BYTES_PER_ELEMENT * wl.n_elem if metric and (wl.orders == 4).all() else None
-        return {"bound": "alu", "kernel": "k_moments_dw", "achieved": ach, "peak": FP32_PEAK_TOPS,
-                "unit": "T FP32 lane-op/s", "frac": ach / FP32_PEAK_TOPS, "traffic": traffic,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the full-size c5 learned launch, "
-                                  "per element" if traffic else None,
-                "peak_source": "FP32 issue: 152 SMs x 128 lanes x 2.07 GHz (recipe unit counts and clock)",
-                "algorithmic_ops_per_launch": int(ops),
-                "op_model": "%d per double-word MAC x %d MACs (first mode product folded) + %d per point x %d points" % (
-                    DW_MAC_OPS, macs, per_point, pts)}
     if mom_ms >= con_ms:
-        mflop = moment_flop_count(wl.orders, npts, metric)
-        ach = mflop / (mom_ms * 1e-3) / 1e12
-        return {"bound": "alu", "kernel": "k_moments_fp64", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (2 DFMA/clk/SM probe-measured)",
-                "algorithmic_flop_per_launch": mflop,
-                "flop_model": "2 x sum-factorised moment MACs + %d FP64 flop per point for alpha" % ALPHA_FLOP_PER_POINT}
+        macs, pts, npairs = moment_mac_points(wl.orders, npts, folded=False)
+        alpha_flop = (ALPHA_FLOP_PER_POINT if metric else 8) * pts
+        flop = 2 * macs + alpha_flop
+        ach = flop / (mom_ms * 1e-3) / 1e12
+        model = ("2 x %d MACs (K G^3 + K^2 G^2 + K^3 G per coupling pair, %d pairs) + %d flop per point x %d points"
+                 % (macs, npairs, ALPHA_FLOP_PER_POINT if metric else 8, pts))
+        if prec == 0:
+            pk = fp64_peak()
+            return {"bound": "alu", "kernel": "k_moments_fp64", "achieved": ach, "peak": pk,
+                    "unit": "TFLOP/s", "frac": ach / pk, "traffic": None, "peak_source": peak_source("fp64"),
+                    "algorithmic_flop_per_launch": int(flop), "flop_model": model}
+        fmacs, _, _ = moment_mac_points(wl.orders, npts, folded=True)
+        per_point = (DW_ALPHA_OPS_METRIC if metric else DW_ALPHA_OPS_SCALAR) + DW_FOLD_OPS * npairs
+        ops = DW_MAC_OPS * fmacs + per_point * pts
+        iss = ops / (mom_ms * 1e-3) / 1e12
+        fp32 = 2 * fp32_issue_peak()
+        bf16 = peaks["bf16_tflops"]
+        traffic = MOMENTS_DW_DRAM_BYTES_PER_ELEMENT * wl.n_elem if metric and (wl.orders == 4).all() else None
+        return {"bound": "tensor", "kernel": "k_moments_dw", "achieved": ach, "peak": bf16, "unit": "TFLOP/s",
+                "frac": ach / bf16, "traffic": traffic,
+                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per element of a 1024-element "
+                                   "c5 capture, scaled to the launch's elements") if traffic else None,
+                "peak_source": "%s BF16 dense burst (MEASURED_PEAKS.json)" % src,
+                "algorithmic_flop_per_launch": int(flop), "flop_model": model,
+                "vs_fp32_fma": {"peak": fp32, "frac": ach / fp32, "unit": "TFLOP/s",
+                                "peak_source": peak_source("fp32").replace("issue rate", "rate") + " (2 flop per FMA)"},
+                "issue_frac": iss / fp32_issue_peak(),
+                "issue": {"achieved": iss, "peak": fp32_issue_peak(), "unit": "T FP32 lane-op/s",
+                          "peak_source": peak_source("fp32"), "ops_per_launch": int(ops),
+                          "op_model": "%d per double-word MAC x %d MACs (first mode product folded) + %d per point x "
+                                      "%d points" % (DW_MAC_OPS, fmacs, per_point, pts)}}
     if prec == 0:
         ach = 2 * fmas / (con_ms * 1e-3) / 1e12
+        pk = fp64_peak()
         return {"bound": "alu", "kernel": contract_kernel(wl.orders, False, kernel), "achieved": ach,
-                "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                "peak": pk, "unit": "TFLOP/s", "frac": ach / pk, "traffic": None, "peak_source": peak_source("fp64"),
                 "algorithmic_flop_per_launch": 2 * fmas,
                 "hbm_write_GBs": 8 * entries / (con_ms * 1e-3) / 1e9}
     ach = 8 * entries / (con_ms * 1e-3) / 1e9
     kname = contract_kernel(wl.orders, True, kernel)
-    return {"bound": "hbm", "kernel": kname, "achieved": ach,
+    roof = {"bound": "hbm", "kernel": kname, "achieved": ach,
             "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
             "peak_source": "%s copy bandwidth (MEASURED_PEAKS.json)" % src, "algorithmic_bytes_per_launch": 8 * entries}
+    if _DEV.get("hbm_write_gbs"):
+        roof["vs_store_only"] = {"peak": _DEV["hbm_write_gbs"], "frac": ach / _DEV["hbm_write_gbs"],
+                                 "peak_source": "store-only stream measured in this run (p2s_measure_peaks)"}
+    return roof
 
 
 # ----------------------------------------------------------------------------- learned (headline)
@@ -423,13 +511,15 @@ def run_learned(args, wl):
     world, rank, local = dist_setup()
     dev = torch.device("cuda", local)
     ctx = p2s.Context(local)
+    device_peaks(p2s, ctx)
     mlp_params, meta = LN.ensure_trained(ctx)
+    risk = float(meta.get("risk", RISK_DEFAULT))
     P = torch.as_tensor(mlp_params, device=dev)
     params, nodes, bulge = p2s.device_inputs(wl, dev)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     lp = p2s.LearnedPlan(ctx, wl.orders, precision=p2s.MIXED, judge_frac=JUDGE_FRAC, seed=1703,
-                         judge_tol=JUDGE_TOL, risk=RISK)
+                         judge_tol=JUDGE_TOL, risk=risk)
     out = torch.empty(lp.output_entries, dtype=torch.float64, device=dev)
     npts_d = torch.empty(wl.n_elem, dtype=torch.int32, device=dev)
     step = lambda: lp.fill(wl.kind, params, nodes, bulge, P, out, npts_d, stream=stream)
@@ -463,7 +553,28 @@ def run_learned(args, wl):
     p2s.element_errors(ctx, out, off_d, ref, off_d, 4, err, stream=stream)
     err_h = err.cpu().numpy()
     plain.close()
-    del ref
+    # the method without the network: the smallest uniform class G whose mixed fill keeps every
+    # element of this batch within 1e-8 of the 48-point FP64 fill (chosen on the batch itself)
+    uniform = None
+    uout = torch.empty_like(out)
+    for G in p2s.CLASS_NPTS:
+        up = p2s.Plan(ctx, wl.orders, G, p2s.MIXED)
+        up.fill(wl.kind, params, nodes, bulge, uout, stream=stream)
+        p2s.element_errors(ctx, uout, off_d, ref, off_d, 4, err, stream=stream)
+        uerr = err.cpu().numpy()
+        if uerr.max() <= 1e-8 or G == p2s.CLASS_NPTS[-1]:
+            ums = time_steps(lambda: up.fill(wl.kind, params, nodes, bulge, uout, stream=stream), ksteps, stream, flush)
+            ums = max_over_ranks(float(np.mean(ums)), world, dev)
+            uniform = {"npts": G, "ms_per_step": ums, "max_rel_err_vs_plain48": float(uerr.max()),
+                       "rule": "smallest class G with every element of the batch <= 1e-8 (mixed fill, same plan "
+                               "calls as the learned fill's contraction)"}
+            up.close()
+            break
+        up.close()
+    del uout, ref
+    # the learned fill's elements of the oracle's CPU sample, for the oracle comparison below
+    cpu_idx = sample_indices(wl, cpu_sample_size(args.workload))
+    cpu_got = [out[int(off[e]):int(off[e + 1])].cpu().numpy() for e in cpu_idx]
     # stage breakdown at the learned G (moments, contraction); the learned fill's moment queue
     # takes elements grouped by G, largest first, so the breakdown fills them in that order
     order = np.argsort(-npts, kind="stable")
@@ -478,15 +589,17 @@ def run_learned(args, wl):
     job_elems = D.sum_over_ranks(wl.n_elem, world, dev)
     value = job_entries * args.steps / (total_ms * 1e-3)
     hist = np.bincount([p2s.CLASS_NPTS.index(int(g)) for g in npts], minlength=6).tolist()
-    e2e = None if args.no_e2e else measure_e2e_learned(args, wl, ctx, P, dev)
+    e2e = None if args.no_e2e else measure_e2e_learned(args, wl, ctx, P, dev, risk)
     line = None
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args, wl),
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32x2", "data": "synthetic",
+            "config": workload_config(args, wl, risk=risk, risk_src=meta.get("risk_calibration")),
             "elements_per_s": job_elems * args.steps / (total_ms * 1e-3),
+            "uniform_mixed": dict(uniform, value=job_entries / (uniform["ms_per_step"] * 1e-3), unit="entries/s",
+                                  learned_speedup=uniform["ms_per_step"] / (total_ms / args.steps)),
             "plain_fp64": {"value": job_entries / (plain_ms * 1e-3), "unit": "entries/s", "ms_per_step": plain_ms,
                            "npts": 48},
             "speedup_vs_plain_fp64": plain_ms / (total_ms / args.steps),
@@ -506,10 +619,17 @@ def run_learned(args, wl):
     del out
     lp.close()
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, dt, desc, threads = oracle_sample(wl.with_npts(48), cpu_sample_size(args.workload))
+        v, dt, desc, threads, idx, ro, roff, sub = oracle_sample(wl.with_npts(48), cpu_sample_size(args.workload),
+                                                                 keep=True)
         line["cpu_baseline"] = {"value": v, "unit": "entries/s", "cores": threads, "kind": "oracle",
                                 "sample": desc + " (%.1f s)" % dt}
+        ev = errors_vs_oracle(cpu_got, ro, roff, sub)
+        line["accuracy"]["vs_oracle48_sample"] = {
+            "elements": idx.tolist(), "learned_G": [int(npts[e]) for e in idx], "rel_err": ev,
+            "note": "learned fill of the oracle's CPU-sample elements against the oracle's direct triple sums at 48 "
+                    "points (quadrature difference of the learned rule plus arithmetic)"}
     if rank == 0:
+        line["device_peaks"] = dict(_DEV) or None
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -517,7 +637,7 @@ def run_learned(args, wl):
         dist.destroy_process_group()
 
 
-def measure_e2e_learned(args, wl, ctx, P, dev, chunk_elems=4096):
+def measure_e2e_learned(args, wl, ctx, P, dev, risk, chunk_elems=4096):
     """Learned fill through the public API with host buffers: per chunk of elements, pinned
     host inputs -> device, learned fill, every FP64 entry -> pinned host memory; two chunks
     in flight on two streams."""
@@ -527,7 +647,7 @@ def measure_e2e_learned(args, wl, ctx, P, dev, chunk_elems=4096):
     E = wl.n_elem
     subs = [wl.subset(np.arange(s, min(E, s + chunk_elems))) for s in range(0, E, chunk_elems)]
     plans = [p2s.LearnedPlan(ctx, w.orders, precision=p2s.MIXED, judge_frac=JUDGE_FRAC, seed=1703,
-                             judge_tol=JUDGE_TOL, risk=RISK) for w in subs]
+                             judge_tol=JUDGE_TOL, risk=risk) for w in subs]
     return _e2e_pipeline(args, wl, subs, plans, dev,
                          lambda p, w, di, o, s: p.fill(w.kind, di[0], di[1], di[2], P, o, stream=s))
 
@@ -569,13 +689,36 @@ def _e2e_pipeline(args, wl, subs, plans, dev, fill):
     dt = D.max_over_ranks((time.perf_counter() - t0) / steps, world, dev)
     for p in plans:
         p.close()
-    # the host link bounds this figure: every FP64 entry crosses it once
-    link = d2h_bandwidth(host_out[0], dev_out[0])
+    # the host link bounds this figure: every FP64 entry crosses it once.  Its ceiling is taken
+    # the way the pipeline uses it: the same two streams copying their chunk buffers at once.
+    link = d2h_bandwidth_streams(host_out, dev_out, streams, [p.output_entries for p in plans[:2]])
+    single = d2h_bandwidth(host_out[0], dev_out[0])
     return {"value": D.sum_over_ranks(wl.entries(), world, dev) / dt, "unit": "entries/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "steps": steps, "chunks": len(subs),
-            "d2h_link_gbs": link, "d2h_achieved_gbs": d2h / dt / 1e9, "frac_of_link": d2h / dt / 1e9 / link,
+            "d2h_link_gbs": link, "d2h_single_copy_gbs": single, "d2h_achieved_gbs": d2h / dt / 1e9,
+            "frac_of_link": d2h / dt / 1e9 / link,
             "note": "pinned host inputs in, every FP64 entry back to pinned host memory, 2-stream pipeline; "
-                    "d2h_link_gbs = one large device-to-host copy measured in the same process"}
+                    "d2h_link_gbs = the two pipeline streams copying a chunk each, concurrently, device to pinned "
+                    "host (best of 3), measured in the same process; d2h_single_copy_gbs = one copy alone"}
+
+
+def d2h_bandwidth_streams(host, devbuf, streams, counts):
+    """GB/s of concurrent device-to-host copies, one per stream, of `counts` doubles each
+    (best of 3 rounds, after one warm-up round)."""
+    import torch
+    best = 0.0
+    for r in range(4):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for h, d, s, n in zip(host, devbuf, streams, counts):
+            with torch.cuda.stream(s):
+                h[:n].copy_(d[:n], non_blocking=True)
+        for s in streams:
+            s.synchronize()
+        dt = time.perf_counter() - t0
+        if r > 0:
+            best = max(best, 8 * sum(counts) / dt / 1e9)
+    return best
 
 
 def d2h_bandwidth(host, devbuf, nbytes=2 << 30):
@@ -601,6 +744,7 @@ def run_fixed(args, wl):
     world, rank, local = dist_setup()
     dev = torch.device("cuda", local)
     ctx = p2s.Context(local)
+    device_peaks(p2s, ctx)
     prec = p2s.MIXED if args.mode == "mixed" else p2s.FP64
     npts = int(wl.npts[0]) if (wl.npts == wl.npts[0]).all() else wl.npts
     params, nodes, bulge = p2s.device_inputs(wl, dev)
@@ -646,12 +790,17 @@ def run_fixed(args, wl):
     job_elems = D.sum_over_ranks(wl.n_elem, world, dev)
     value = job_entries * args.steps / (total_ms * 1e-3)
     e2e = None if args.no_e2e else measure_e2e_fixed(args, wl, ctx, prec, dev, tile, bool(tune or args.tile))
+    # the elements of the oracle's CPU sample, for the per-element comparison below
+    n_, off_ = p2s.output_entries(wl.orders, wl.types_mask, offsets=True)
+    cpu_idx = sample_indices(wl, cpu_sample_size(args.workload))
+    cpu_got = [out[int(off_[e]):int(off_[e + 1])].cpu().numpy() for e in cpu_idx]
     line = None
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32x2" if prec == p2s.MIXED else "f64",
+            "data": "synthetic",
             "config": workload_config(args, wl),
             "elements_per_s": job_elems * args.steps / (total_ms * 1e-3),
             "roofline": roof, "stages": {"moments_ms": mom_ms, "contract_ms": con_ms}, "clocks": clocks,
@@ -665,10 +814,16 @@ def run_fixed(args, wl):
     del out
     plan.close()
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, dt, desc, threads = oracle_sample(wl, cpu_sample_size(args.workload))
+        v, dt, desc, threads, idx, ro, roff, sub = oracle_sample(wl, cpu_sample_size(args.workload), keep=True)
         line["cpu_baseline"] = {"value": v, "unit": "entries/s", "cores": threads, "kind": "oracle",
                                 "sample": desc + " (%.1f s)" % dt}
+        ev = errors_vs_oracle(cpu_got, ro, roff, sub)
+        line["accuracy"] = {"vs_oracle": {"elements": idx.tolist(), "rel_err": ev, "max_rel_err": max(ev),
+                                          "bar": 1e-12 if prec == p2s.FP64 else 1e-8,
+                                          "metric": "per element max over types of max|dM|/max|M| against the "
+                                                    "oracle's direct triple sums at the same rule"}}
     if rank == 0:
+        line["device_peaks"] = dict(_DEV) or None
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -686,6 +841,7 @@ def run_operator(args, wl):
     world, rank, local = dist_setup()
     dev = torch.device("cuda", local)
     ctx = p2s.Context(local)
+    device_peaks(p2s, ctx)
     prec = p2s.MIXED if args.precision == "mixed" else p2s.FP64
     orders = np.ascontiguousarray(wl.orders[:, :1, :])
     terms, scales = W.diffusion_terms()
@@ -726,8 +882,8 @@ def run_operator(args, wl):
     if prec == p2s.FP64:
         ach = 2 * fmas / (con_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": "k_contract<ArithF64> (operator terms)", "achieved": ach,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                "peak": fp64_peak(), "unit": "TFLOP/s", "frac": ach / fp64_peak(), "traffic": None,
+                "peak_source": peak_source("fp64"),
                 "algorithmic_flop_per_launch": 2 * fmas}
     else:  # float-float MACs: bound by FP32 issue (12 lane operations per MAC, as the moment kernel)
         ops = DW_MAC_OPS * fmas
@@ -735,8 +891,8 @@ def run_operator(args, wl):
         uniform = bool((orders == orders[0, 0, 0]).all()) and 2 <= int(orders[0, 0, 0]) <= 6
         kname = "k_contract_opn<%d> (operator terms)" % orders[0, 0, 0] if uniform else "k_contract<ArithFF> (operator terms)"
         roof = {"bound": "alu", "kernel": kname, "achieved": ach,
-                "peak": FP32_PEAK_TOPS, "unit": "T FP32 lane-op/s", "frac": ach / FP32_PEAK_TOPS, "traffic": None,
-                "peak_source": "FP32 issue: 152 SMs x 128 lanes x 2.07 GHz (recipe unit counts and clock)",
+                "peak": fp32_issue_peak(), "unit": "T FP32 lane-op/s", "frac": ach / fp32_issue_peak(), "traffic": None,
+                "peak_source": peak_source("fp32"),
                 "algorithmic_ops_per_launch": ops,
                 "op_model": "%d per float-float MAC x %d MACs of the three sparse stages" % (DW_MAC_OPS, fmas),
                 "hbm_write_GBs": 8 * entries / (con_ms * 1e-3) / 1e9}
@@ -769,6 +925,7 @@ def run_operator(args, wl):
         line["cpu_baseline"] = {"value": float(off[-1]) / dt, "unit": "entries/s", "cores": threads, "kind": "oracle",
                                 "sample": "first %d elements, every entry of the operator (%.1f s)" % (sub.n_elem, dt)}
     if rank == 0:
+        line["device_peaks"] = dict(_DEV) or None
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -787,6 +944,7 @@ def run_assembly(args):
     world, rank, local = dist_setup()
     dev = torch.device("cuda", local)
     ctx = p2s.Context(local)
+    device_peaks(p2s, ctx)
     prec = p2s.FP64 if args.precision == "fp64" else p2s.MIXED
     nx, ny, nz = (int(x) for x in args.mesh.split(","))
     N, G = args.order, args.npts or 8
@@ -827,8 +985,8 @@ def run_assembly(args):
         ops = DW_MAC_OPS * fmas
         ach = ops / (add_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": "k_opn_assemble<%d> (memset + 8 colour launches)" % N, "achieved": ach,
-                "peak": FP32_PEAK_TOPS, "unit": "T FP32 lane-op/s", "frac": ach / FP32_PEAK_TOPS, "traffic": None,
-                "peak_source": "FP32 issue: 152 SMs x 128 lanes x 2.07 GHz (recipe unit counts and clock)",
+                "peak": fp32_issue_peak(), "unit": "T FP32 lane-op/s", "frac": ach / fp32_issue_peak(), "traffic": None,
+                "peak_source": peak_source("fp32"),
                 "algorithmic_ops_per_launch": ops,
                 "op_model": "%d per float-float MAC x %d MACs of the operator contraction (basis change and "
                             "scatter not counted)" % (DW_MAC_OPS, fmas),
@@ -845,10 +1003,10 @@ def run_assembly(args):
     else:  # the FP64 basis change: 12 FP64 operations per entry (6 axes x subtract + scale)
         ops = 12 * contributions
         ach = ops / (add_ms * 1e-3) / 1e12
-        peak = FP64_PEAK_TFLOPS / 2
+        peak = fp64_peak() / 2
         roof = {"bound": "alu", "kernel": "k_assemble_staged<%d, FP64> (memset + 8 colour launches)" % N,
                 "achieved": ach, "peak": peak, "unit": "T FP64 op/s", "frac": ach / peak, "traffic": None,
-                "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (one op per DADD/DMUL)",
+                "peak_source": peak_source("fp64") + ", one operation per DADD/DMUL",
                 "algorithmic_ops_per_launch": ops, "op_model": "12 FP64 operations per element-matrix entry"}
     job = D.sum_over_ranks(contributions, world, dev)
     line = None
@@ -888,6 +1046,7 @@ def run_assembly(args):
         line["cpu_baseline"] = {"value": sw.n_elem * n * n / dt, "unit": "entries/s", "cores": threads, "kind": "oracle",
                                 "sample": "a 6x6x6 mesh of the same recipe: oracle fill + dense assembly (%.1f s)" % dt}
     if rank == 0:
+        line["device_peaks"] = dict(_DEV) or None
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -912,6 +1071,7 @@ def run_cheb2d(args):
     world, rank, local = dist_setup()
     dev = torch.device("cuda", local)
     ctx = p2s.Context(local)
+    device_peaks(p2s, ctx)
     nx, ny = (int(x) for x in args.mesh2d.split(","))
     orders = [int(x) for x in args.orders.split(",")]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -959,7 +1119,8 @@ def run_cheb2d(args):
     macs = entries * G * G  # the direct method: one multiply-add per point and entry (Sec. IV)
     dach = 2 * macs / (times["direct_fp64"] * 1e-3) / 1e12
     roof_direct = {"bound": "alu", "kernel": "k_cheb2d_direct (order %d)" % M, "achieved": dach,
-                   "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": dach / FP64_PEAK_TFLOPS,
+                   "peak": fp64_peak(), "unit": "TFLOP/s", "frac": dach / fp64_peak(),
+                   "peak_source": peak_source("fp64"),
                    "flop_model": "2 flop per Gauss point and entry (the paper's direct count)"}
     if rank == 0:
         line = {
@@ -981,6 +1142,7 @@ def run_cheb2d(args):
             dt = time.perf_counter() - t0
             line["cpu_baseline"] = {"value": 2 * n * n / dt, "unit": "entries/s", "cores": 1, "kind": "oracle",
                                     "sample": "element 0 at order %d: S and M by direct sums in numpy (%.1f s)" % (M, dt)}
+        line["device_peaks"] = dict(_DEV) or None
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

@@ -25,6 +25,9 @@ thread_local char g_last_error[256] = "";
 }
 
 int fail(int code, const char* where, cudaError_t ce) {
+    // a failed allocation also sets the runtime's last-error state; clear it, or the error
+    // check after the next kernel launch on this thread would report it as that launch's
+    if (code == P2S_ERR_OOM) (void)cudaGetLastError();
     if (ce != cudaSuccess)
         std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", where, cudaGetErrorString(ce),
                       cudaGetErrorName(ce));
@@ -478,6 +481,7 @@ int run_moments(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_d
     M.elem_mask = elem_mask;
     M.counter = counter;
     M.order = order;
+    NvtxRange range(M.out_ff ? "p2s moments a1+a2 (double word)" : "p2s moments a1+a2 (FP64)");
     if (counter) P2S_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
     if (M.out_ff)
         P2S_CUDA(launch_moments_dw(M, PL.mom_grid, PL.mom_smem, s));
@@ -493,6 +497,7 @@ int run_contract(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_
         return fail(P2S_ERR_ARG, "contract: element masks need an FP64 plan");
     if (PL.n_units == 0) return P2S_OK;
     if (!moments || !out) return fail(P2S_ERR_ARG, "contract: NULL moments or out");
+    NvtxRange range("p2s contraction a4");
     P2S_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), s));
     ContractLaunch C;
     C.desc = d_desc;

@@ -735,7 +735,9 @@ int p2s_learned_fill(p2s_learned_plan* L, const p2s_geometry* geom, const p2s_ma
     p2s_material m2 = {P2S_ALPHA_METRIC_EPS, jp};
     // The judge's 48-point fill does not depend on the prediction: it starts first, on the
     // side stream, and the main path's kernels fill the SMs its last elements leave idle.
+    NvtxRange whole("p2s learned fill");
     if (L->nJ) {
+        NvtxRange r("p2s learned: judge 48-point fill (side stream)");
         P2S_LCUDA(cudaEventRecord(L->ev_fork, s));
         P2S_LCUDA(cudaStreamWaitEvent(L->side, L->ev_fork, 0));
         k_gather_inputs<<<gj, 32, 0, L->side>>>(geom->nodes, geom->bulge, mat->params, L->d_jidx, L->nJ, jn, jb, jp);
@@ -747,6 +749,7 @@ int p2s_learned_fill(p2s_learned_plan* L, const p2s_geometry* geom, const p2s_ma
             return jrc;
         }
     }
+    nvtxRangePushA("p2s learned: features, prediction, class order");
     int rc = p2s_coarse_features(L->ctx, geom, mat, L->d_feat, stream);
     if (rc == P2S_OK) rc = p2s_mlp_predict(L->ctx, params, L->d_feat, L->E, L->margin, L->risk, L->d_npts, nullptr, stream);
     if (rc == P2S_OK) {
@@ -763,10 +766,12 @@ int p2s_learned_fill(p2s_learned_plan* L, const p2s_geometry* geom, const p2s_ma
         const cudaError_t ce = cudaMemcpyAsync(npts_out, L->d_npts, sizeof(int32_t) * L->E, cudaMemcpyDeviceToDevice, s);
         if (ce != cudaSuccess) rc = fail(P2S_ERR_CUDA, "p2s_learned_fill: npts copy", ce);
     }
+    nvtxRangePop();
     if (rc == P2S_OK) rc = p2s_plan_fill(L->main, geom, mat, out, nullptr, stream);
     if (L->nJ) P2S_LCUDA(cudaStreamWaitEvent(s, L->ev_join, 0));  // joined on every path
     if (rc) return rc;
     if (L->nJ) {
+        NvtxRange r("p2s learned: judge comparison and fallback");
         rc = p2s_element_errors(L->ctx, out, L->d_off_main, L->d_jout, L->d_off_j, L->nJ, 4, L->d_jerr, stream);
         if (rc) return rc;
         // judged elements above the tolerance: their plain-method fill, then the copy into out

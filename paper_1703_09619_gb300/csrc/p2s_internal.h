@@ -6,10 +6,20 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "p2s.h"
 
 namespace p2s {
+
+// NVTX range over a scope of host code (the enqueue of one stage of the path); a profiler
+// that records NVTX shows the stages by name, and without one the calls cost nothing.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr int kMaxOrder = P2S_MAX_ORDER;       // N per axis
 constexpr int kMaxK = 2 * kMaxOrder - 1;       // moments per axis

@@ -159,6 +159,51 @@ def train_default(ctx, n_train=65536, epochs=60, seed=0, verbose=False):
     return params, meta
 
 
+RISK_SWEEP = (0.05, 0.02, 0.01, 0.005, 0.002, 0.001, 0.0005, 0.0002, 0.0001)
+
+
+def learned_errors(ctx, params, wl, risk, margin=0, ref=None, device="cuda"):
+    """Per-element relative error of the learned mixed fill (judge off: the network's rule
+    alone) against the 48-point FP64 fill, and the G it chose per element."""
+    torch = _torch()
+    P = torch.as_tensor(params, dtype=torch.float32, device=device)
+    prm, nodes, bulge = p2s.device_inputs(wl, device)
+    n, off = p2s.output_entries(wl.orders, offsets=True)
+    off_d = torch.as_tensor(off, device=device)
+    if ref is None:
+        ref = torch.empty(n, dtype=torch.float64, device=device)
+        plan = p2s.Plan(ctx, wl.orders, CLASS_NPTS[-1], p2s.FP64)
+        plan.fill(wl.kind, prm, nodes, bulge, ref)
+        plan.close()
+    lp = p2s.LearnedPlan(ctx, wl.orders, margin=margin, precision=p2s.MIXED, judge_frac=0.0, seed=1, risk=risk)
+    out = torch.empty(n, dtype=torch.float64, device=device)
+    npts = torch.empty(wl.n_elem, dtype=torch.int32, device=device)
+    lp.fill(wl.kind, prm, nodes, bulge, P, out, npts)
+    err = torch.empty(wl.n_elem, dtype=torch.float64, device=device)
+    p2s.element_errors(ctx, out, off_d, ref, off_d, 4, err)
+    e, g = err.cpu().numpy(), npts.cpu().numpy()
+    lp.close()
+    return e, g, ref
+
+
+def calibrate_risk(ctx, params, n_elem=8192, tol=1e-8, sweep=RISK_SWEEP):
+    """Choose the class rule's risk (R13) on held-out elements: shard 1 of the training
+    recipe (another seed; neither trained on nor benchmarked).  The learned mixed fill runs
+    with the judge off at each risk of the sweep, every element is compared with its
+    48-point FP64 fill, and the largest risk whose worst element stays within `tol` is
+    kept (the smallest risk of the sweep if none does).  Returns (risk, table)."""
+    wl = W.make("c5train", n_elem, shard=1)
+    ref = None
+    table = []
+    for r in sorted(sweep, reverse=True):
+        e, g, ref = learned_errors(ctx, params, wl, r, ref=ref)
+        table.append({"risk": r, "max_err": float(e.max()), "above_tol": int((e > tol).sum()),
+                      "mean_G3": float(np.mean(g.astype(float) ** 3))})
+    ok = [t["risk"] for t in table if t["max_err"] <= tol]
+    risk = max(ok) if ok else min(sweep)
+    return risk, {"holdout": "c5train shard 1, %d elements" % n_elem, "tol": tol, "sweep": table}
+
+
 def ensure_trained(ctx, path=CHECKPOINT, verbose=False):
     """Load the committed checkpoint, or train one and save it."""
     if os.path.exists(path):
@@ -171,7 +216,15 @@ def ensure_trained(ctx, path=CHECKPOINT, verbose=False):
 if __name__ == "__main__":
     import sys
     ctx = p2s.Context(0)
+    if "--calibrate" in sys.argv:  # held-out risk for the committed checkpoint, kept in its metadata
+        rest = [a for a in sys.argv[1:] if a != "--calibrate"]
+        params, meta = load_checkpoint()
+        meta["risk"], meta["risk_calibration"] = calibrate_risk(ctx, params)
+        save(rest[0] if rest else CHECKPOINT, params, meta)
+        print(json.dumps(meta))
+        sys.exit(0)
     params, meta = train_default(ctx, verbose=True)
+    meta["risk"], meta["risk_calibration"] = calibrate_risk(ctx, params)
     out = sys.argv[1] if len(sys.argv) > 1 else CHECKPOINT
     save(out, params, meta)
     print(json.dumps(meta))

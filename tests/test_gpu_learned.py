@@ -177,9 +177,11 @@ def test_judge_replaces_planted_mispredictions(torch, ctx):
     lp.close()
 
 
-def test_training_gains_over_full_order(torch, ctx):
+def test_training_gains_over_uniform_rule(torch, ctx):
     """Train on 4096 method-labelled elements, predict on 1024 held-out c5 elements: most
-    predictions are right or conservative, and the learned rule uses far fewer points."""
+    predictions are right or conservative, and the learned rule needs fewer points than the
+    method without the network, i.e. the smallest uniform class rule that meets every
+    held-out element's label (not merely fewer than the 48-point rule)."""
     tr = W.make("c5train", 4096)
     y = LN.labels_from_errors(LN.class_errors(ctx, tr))
     X = LN.features(ctx, tr)
@@ -190,11 +192,12 @@ def test_training_gains_over_full_order(torch, ctx):
     pred = LN.classes_of(LN.predict(ctx, params, LN.features(ctx, te)))
     acc = (pred == yt).mean()
     under = (pred < yt).mean()
-    g_learn = np.array(LN.CLASS_NPTS)[pred].astype(float)
-    work_ratio = (48.0 ** 3) / np.mean(g_learn ** 3)
+    g = np.array(LN.CLASS_NPTS, dtype=float)
+    uniform_G = g[yt.max()]
+    work_ratio = uniform_G ** 3 / np.mean(g[pred] ** 3)
     assert acc > 0.5, acc
     assert under < 0.25, under
-    assert work_ratio > 3.0, work_ratio
+    assert work_ratio > 1.5, (uniform_G, work_ratio)
 
 
 RISK = 0.002  # the class rule the benchmark uses (R13)

@@ -185,6 +185,20 @@ def test_c5_specialised_moment_bodies_against_oracle(torch_cuda, ctx, prec, G):
     check(torch_cuda, ctx, wl, precision=prec)
 
 
+def test_plan_beyond_device_memory_is_oom(torch_cuda, ctx):
+    """A plan whose moment scratch exceeds the device's memory is refused at creation with
+    P2S_ERR_OOM (nothing is launched), and the context fills correctly afterwards."""
+    _, total = torch_cuda.cuda.mem_get_info()
+    per_elem = 6 * 15 ** 3 * 8  # three components at N = 8: six pairs of 15^3 FP64 moments
+    E = int(1.05 * total) // per_elem + 1
+    orders = np.full((E, 3, 3), 8, dtype=np.int32)
+    tile = {"combo_target": 4096, "unit_kbytes": 0, "threads": 0, "kernel": 2}  # one work unit per block
+    with pytest.raises(p2s.P2SError) as ei:
+        p2s.Plan(ctx, orders, 2, p2s.FP64, types_mask=0x1, tile=tile)
+    assert ei.value.code == p2s.ERR_OOM
+    check(torch_cuda, ctx, W.make("c1"))
+
+
 def test_empty_batch(torch_cuda, ctx):
     wl = W.make("c4", 1).subset([])
     plan = p2s.Plan(ctx, wl.orders, 4)
