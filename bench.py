@@ -756,12 +756,14 @@ def run_fixed(args, wl):
         tile = dict(zip(("combo_target", "unit_kbytes", "threads", "kernel"), vals))
         tune_info = {"tile": tile, "candidates": 0, "note": "given on the command line"}
     elif tune:
+        from paper_1703_09619_gb300 import tunecache
         sample = min(wl.n_elem, 1024)
-        tile, best_ms, tried = p2s.autotune_tiles(ctx, wl.orders, npts, wl.kind, params, nodes, bulge, prec,
-                                                  wl.types_mask, sample=sample, reps=3)
-        tune_info = {"tile": tile, "candidates": tried, "sample_elements": sample,
-                     "sample_contract_ms": best_ms}
-        log("autotune: %s (%d candidates, %.3f ms on %d elements)" % (tile, tried, best_ms, sample))
+        key = tunecache.signature(wl.orders, npts, prec, wl.types_mask, torch.cuda.get_device_name(dev))
+        tile, tune_info = tunecache.tuned_tile(
+            lambda: p2s.autotune_tiles(ctx, wl.orders, npts, wl.kind, params, nodes, bulge, prec, wl.types_mask,
+                                       sample=sample, reps=3),
+            key, sample_elements=sample, workload=args.workload)
+        log("autotune (%s): %s" % (tune_info["cache"], tile))
     plan = p2s.Plan(ctx, wl.orders, npts, prec, wl.types_mask, tile=tile, graph=bool(tune or args.tile))
     out = torch.empty(plan.output_entries, dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
