@@ -192,7 +192,8 @@ def test_plan_beyond_device_memory_is_oom(torch_cuda, ctx):
     per_elem = 6 * 15 ** 3 * 8  # three components at N = 8: six pairs of 15^3 FP64 moments
     E = int(1.05 * total) // per_elem + 1
     orders = np.full((E, 3, 3), 8, dtype=np.int32)
-    tile = {"combo_target": 4096, "unit_kbytes": 0, "threads": 0, "kernel": 2}  # one work unit per block
+    # bounded-order kernel, two m1 rows per unit (the largest unit that fits shared memory at N = 8)
+    tile = {"combo_target": 1024, "unit_kbytes": 0, "threads": 512, "kernel": 2}
     with pytest.raises(p2s.P2SError) as ei:
         p2s.Plan(ctx, orders, 2, p2s.FP64, types_mask=0x1, tile=tile)
     assert ei.value.code == p2s.ERR_OOM
