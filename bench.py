@@ -1164,6 +1164,66 @@ def measure_e2e_fixed(args, wl, ctx, prec, dev, tile=None, graph=False):
                          lambda p, w, di, o, s: p.fill(w.kind, di[0], di[1], di[2], o, stream=s))
 
 
+def run_mode1(args, n_src=65536, n_rows=1 << 24):
+    """The first mode product of the moments (the a-axis sum of Eq. (4), K = 7) in its two
+    forms on the same rows: double-word SIMT (the moment kernel's phase B) and the
+    split-precision tensor-core form (tcgen05, 4 and 5 slices).  Rows are double-word
+    samples of a c5-like coupling factor, read from a 65 536-row source (L2-resident) so
+    that arithmetic, not HBM, is timed; 16.8 M rows per launch, CUDA events, L2 flushed
+    between launches.  Reports time per row and per point for each G of the learned classes."""
+    import torch
+
+    from paper_1703_09619_gb300 import p2s
+
+    world, rank, local = dist_setup()
+    dev = torch.device("cuda", local)
+    ctx = p2s.Context(local)
+    device_peaks(p2s, ctx)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    out = torch.empty((n_rows, 8, 2), dtype=torch.float32, device=dev)
+    rng = np.random.default_rng(17)
+    res = {}
+    for G in (16, 24, 32, 48):
+        u = np.polynomial.legendre.leggauss(G)[0]
+        x = 1 + 0.8 * np.sin(rng.uniform(1, 40, (n_src, 1)) * u + rng.uniform(0, 6, (n_src, 1)))
+        x *= rng.uniform(0.5, 2.0, (n_src, 1))
+        hi = x.astype(np.float32)
+        xs = np.stack([hi, (x - hi).astype(np.float32)], axis=-1)
+        xd = torch.as_tensor(np.ascontiguousarray(xs), device=dev)
+        row = {}
+        ref = None
+        for name, method, sl in (("simt", p2s.MODE1_SIMT, 4), ("tc4", p2s.MODE1_TC, 4), ("tc5", p2s.MODE1_TC, 5)):
+            call = lambda: p2s.mode1_product(ctx, method, G, xd, n_rows, out, slices=sl, stream=stream)
+            for _ in range(args.warmup):
+                call()
+            ms = float(np.median(time_steps(call, max(3, args.steps), stream, flush)))
+            o = out[:n_src].double()
+            T = (o[..., 0] + o[..., 1]).cpu().numpy()
+            if ref is None:
+                ref = T
+            row[name] = {"ms": ms, "ns_per_row": 1e6 * ms / n_rows, "ns_per_point": 1e6 * ms / (n_rows * G),
+                         "max_rel_diff_vs_simt": float(np.abs(T - ref).max() / np.abs(ref).max())}
+        row["tc4_speedup"] = row["simt"]["ms"] / row["tc4"]["ms"]
+        row["tc5_speedup"] = row["simt"]["ms"] / row["tc5"]["ms"]
+        res["G%d" % G] = row
+        log("mode1 G=%d: %s" % (G, json.dumps(row)))
+    rc = ctx.sync_status()
+    line = None
+    if rank == 0:
+        g = res["G24"]
+        line = {"metric": "first-mode moment product rows/s (Eq. (4) a-axis sum, K = 7), tensor core vs SIMT",
+                "value": n_rows / (g["tc4"]["ms"] * 1e-3), "unit": "rows/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": g["tc4"]["ms"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f16x4 slices, f32 accumulate", "data": "synthetic",
+                "config": {"workload": "mode1: %d rows per launch from a %d-row L2-resident source, G = 16..48"
+                                       % (n_rows, n_src), "rows": n_rows},
+                "results": res, "device_status": rc, "gpu_launches": 3 * 4 * (args.warmup + max(3, args.steps))}
+        line["device_peaks"] = dict(_DEV) or None
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1171,7 +1231,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c5", choices=["c1", "c2", "c3", "c4", "c5"])
-    ap.add_argument("--mode", default=None, choices=["learned", "plain", "mixed", "operator", "assembly", "cheb2d"])
+    ap.add_argument("--mode", default=None, choices=["learned", "plain", "mixed", "operator", "assembly", "cheb2d", "mode1"])
     ap.add_argument("--mesh2d", default="32,32", help="cheb2d mode: elements nx,ny (ny even)")
     ap.add_argument("--orders", default="3,4,6,8,10,12,14,16,18", help="cheb2d mode: orders M = N (Table I)")
     ap.add_argument("--mesh", default="32,32,32", help="assembly mode: elements per axis nx,ny,nz")
@@ -1195,6 +1255,9 @@ def main():
         return
     if args.mode == "cheb2d" and args.impl == "ours":
         run_cheb2d(args)
+        return
+    if args.mode == "mode1" and args.impl == "ours":
+        run_mode1(args)
         return
     wl = W.make(args.workload, args.elements, shard=D.env()[1])  # weak scaling: a batch per rank
     if args.npts:

@@ -513,6 +513,29 @@ typedef struct {
 } p2s_peaks;
 int p2s_measure_peaks(p2s_ctx* ctx, int64_t write_bytes, p2s_peaks* out, void* stream);
 
+/* First mode product of the sum-factorised moments (Eq. (4): the a-axis sum of the
+ * starting-point integrals) on rows of double-word samples, by one of two methods; a
+ * measurement of the tensor-core form against the SIMT form on the same work (the fill's
+ * moment kernel uses the SIMT form, fused with the coupling factor).
+ *   T[r][k] = sum_{a<G} B[k][a] x[r][a],  B[k][a] = w_a P_k(u_a) (the G-point
+ *   Gauss-Legendre rule of the fill), k < 7 (order 4).
+ * method: P2S_MODE1_SIMT -- parity fold and double-word dot products (FP32 pipe);
+ *         P2S_MODE1_TC   -- parity fold, per-row power-of-two scaling, `slices` (4 or 5)
+ *           8-bit integer slices of the samples and of B in FP16, tcgen05.mma with FP32
+ *           accumulation in tensor memory (exact: every level sum is an integer below
+ *           2^24), level sums recombined into a double word; error about 2^(-8 slices)
+ *           of max|B| max|x| per term.
+ * x: device, n_src rows of G (hi, lo) FP32 pairs ([n_src][G][2] floats); row r of the
+ *    product reads source row r mod n_src.  G in {8, 12, 16, 24, 32, 48}.
+ * out: device, [n_rows][8][2] floats: T[r][k] as (hi, lo) for k < 7, slot 7 zero.
+ * Synchronises `stream`.  A tensor-core wait that exceeds its clock budget sets the
+ * context's flag to P2S_ERR_TIMEOUT (p2s_sync_status).  Errors: P2S_ERR_ARG,
+ * P2S_ERR_ORDER, P2S_ERR_CUDA. */
+#define P2S_MODE1_SIMT 0
+#define P2S_MODE1_TC 1
+int p2s_mode1_product(p2s_ctx* ctx, int method, int G, int slices, const float* x, int64_t n_src, int64_t n_rows,
+                      float* out, void* stream);
+
 /* Static description of an error code. */
 const char* p2s_error_string(int code);
 

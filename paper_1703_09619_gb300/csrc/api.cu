@@ -1087,6 +1087,13 @@ int p2s_measure_peaks(p2s_ctx* ctx, int64_t write_bytes, p2s_peaks* out, void* s
     return measure_peaks(ctx->T, write_bytes, out, (cudaStream_t)stream);
 }
 
+int p2s_mode1_product(p2s_ctx* ctx, int method, int G, int slices, const float* x, int64_t n_src, int64_t n_rows,
+                      float* out, void* stream) {
+    if (!ctx) return fail(P2S_ERR_ARG, "p2s_mode1_product: NULL context");
+    if (set_device(ctx->T.device)) return P2S_ERR_CUDA;
+    return mode1_product(ctx->T, method, G, slices, x, n_src, n_rows, out, (cudaStream_t)stream);
+}
+
 }  // extern "C"
 
 namespace p2s {

@@ -291,6 +291,9 @@ struct OpArrays {
 int noalloc_prepare(int device);
 // Throughput probes behind p2s_measure_peaks (peaks.cu).
 int measure_peaks(const DeviceTables& T, int64_t write_bytes, p2s_peaks* out, cudaStream_t s);
+// First mode product behind p2s_mode1_product (mode1_tc.cu).
+int mode1_product(const DeviceTables& T, int method, int G, int slices, const float* x, int64_t n_src, int64_t n_rows,
+                  float* out, cudaStream_t s);
 int run_contract(const DeviceTables& T, const PlanLayout& L, const ElemDesc* d_desc, const ContractUnit* d_units,
                  unsigned long long* d_counter, const void* moments, double* out, cudaStream_t s,
                  const int8_t* elem_mask = nullptr, const OpArrays* op = nullptr);

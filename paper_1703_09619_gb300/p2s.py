@@ -141,7 +141,9 @@ SIGNATURES = {
     "p2s_learned_fill": (ctypes.c_int, [_P, ctypes.POINTER(Geometry), ctypes.POINTER(Material), _P, _P, _P, _P]),
     "p2s_learned_report_get": (ctypes.c_int, [_P, _P, _P, _P]),
     "p2s_measure_peaks": (ctypes.c_int, [_P, _I64, _P, _P]),
+    "p2s_mode1_product": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _I64, _I64, _P, _P]),
 }
+MODE1_SIMT, MODE1_TC = 0, 1
 
 MLP_IN, MLP_HIDDEN, MLP_CLASSES, MLP_PARAMS = 576, 64, 6, 41478
 CLASS_NPTS = (8, 12, 16, 24, 32, 48)
@@ -641,3 +643,11 @@ def measure_peaks(ctx: Context, write_bytes=4 << 30, stream=None):
     _check(load().p2s_measure_peaks(ctx.handle, int(write_bytes), ctypes.byref(pk), _stream(stream)),
            "p2s_measure_peaks")
     return {f: getattr(pk, f) for f, _ in Peaks._fields_}
+
+
+def mode1_product(ctx: Context, method, G, x, n_rows, out, slices=4, stream=None):
+    """p2s_mode1_product: T[r][k] = sum_a B[k][a] x[r mod n_src][a] for k < 7 on the G-point
+    rule; x: float32 device tensor [n_src][G][2] (hi, lo), out: float32 [n_rows][8][2]."""
+    n_src = int(x.shape[0])
+    _check(load().p2s_mode1_product(ctx.handle, int(method), int(G), int(slices), _dptr(x), n_src, int(n_rows),
+                                    _dptr(out), _stream(stream)), "p2s_mode1_product")
