@@ -189,19 +189,35 @@ def learned_errors(ctx, params, wl, risk, margin=0, ref=None, device="cuda"):
 def calibrate_risk(ctx, params, n_elem=8192, tol=1e-8, sweep=RISK_SWEEP):
     """Choose the class rule's risk (R13) on held-out elements: shard 1 of the training
     recipe (another seed; neither trained on nor benchmarked).  The learned mixed fill runs
-    with the judge off at each risk of the sweep, every element is compared with its
-    48-point FP64 fill, and the largest risk whose worst element stays within `tol` is
-    kept (the smallest risk of the sweep if none does).  Returns (risk, table)."""
+    with the judge off at each risk of the sweep and every element is compared with its
+    48-point FP64 fill.  Kept: the largest risk among those with the fewest held-out
+    elements above `tol` (and, among those, the smallest worst error): a smaller risk buys
+    more points only where it removes a failure.  Returns (risk, table); the table also
+    lists, for the kept risk, each held-out element above `tol` with the G chosen, the G
+    its label asks for (the smallest class whose FP64 fill is within 1e-10 of 48 points)
+    and its wavenumber."""
     wl = W.make("c5train", n_elem, shard=1)
     ref = None
-    table = []
+    table, fails = [], {}
     for r in sorted(sweep, reverse=True):
         e, g, ref = learned_errors(ctx, params, wl, r, ref=ref)
         table.append({"risk": r, "max_err": float(e.max()), "above_tol": int((e > tol).sum()),
                       "mean_G3": float(np.mean(g.astype(float) ** 3))})
-    ok = [t["risk"] for t in table if t["max_err"] <= tol]
-    risk = max(ok) if ok else min(sweep)
-    return risk, {"holdout": "c5train shard 1, %d elements" % n_elem, "tol": tol, "sweep": table}
+        fails[r] = [(int(i), int(g[i]), float(e[i])) for i in np.flatnonzero(e > tol)]
+    fewest = min(t["above_tol"] for t in table)
+    best = [t for t in table if t["above_tol"] == fewest]
+    lowest = min(t["max_err"] for t in best)
+    risk = max(t["risk"] for t in best if t["max_err"] <= lowest * (1 + 1e-9))
+    del ref
+    detail = []
+    if fails[risk]:
+        idx = [i for i, _, _ in fails[risk]]
+        lab = labels_from_errors(class_errors(ctx, wl.subset(idx)))
+        for (i, gi, ei), li in zip(fails[risk], lab):
+            detail.append({"element": i, "G": gi, "label_G": CLASS_NPTS[int(li)], "err": ei,
+                           "k": float(np.linalg.norm(wl.params[i, 1:]))})
+    return risk, {"holdout": "c5train shard 1, %d elements" % n_elem, "tol": tol, "rule": "fewest above tol, then "
+                  "smallest worst error, then largest risk", "sweep": table, "above_tol_at_risk": detail}
 
 
 def ensure_trained(ctx, path=CHECKPOINT, verbose=False):
