@@ -24,6 +24,14 @@ __host__ __device__ constexpr int run_cnt(int t, int a, int b) {
                   : ((a == 0 || b == 0) ? 0 : (a + b - 2 - run_kmin(3, a, b)) / 2 + 1);
 }
 
+// Longest run of type t over the first index a < 8 for a fixed second index b: the bound of
+// a stage-2 coefficient loop whose n1 is a run-time value but whose n2 is unrolled.
+__host__ __device__ constexpr int max_run_over_a(int t, int b) {
+    int m = 0;
+    for (int a = 0; a < 8; ++a) m = run_cnt(t, a, b) > m ? run_cnt(t, a, b) : m;
+    return m;
+}
+
 namespace {
 
 constexpr int kSpec = 8;     // coefficient table extent

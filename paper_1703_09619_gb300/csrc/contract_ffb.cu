@@ -115,9 +115,13 @@ __device__ __forceinline__ void ffb_stage2(const typename A::T* __restrict__ sA,
             if (n2 >= s.Nv_j) break;
             const int l0 = run_kmin(TT, n1, n2), lc = run_cnt(TT, n1, n2);
             T acc = lc > 0 ? A::mul(run_coef<A>(TT, n1, n2, 0), a[l0 * s.Kw]) : A::zero();
+            // bounded by the longest run of (TT, ., n2), a constant in this unrolled body, so
+            // the multiply-adds no n1 can reach are not issued
 #pragma unroll
-            for (int r = 1; r < kB; ++r)
+            for (int r = 1; r < kB; ++r) {
+                if (r >= max_run_over_a(TT, n2)) break;
                 if (r < lc) A::fma_acc(acc, run_coef<A>(TT, n1, n2, r), a[(l0 + 2 * r) * s.Kw]);
+            }
             dst[n2 * s.Kwp] = A::finish(acc);
         }
     }
