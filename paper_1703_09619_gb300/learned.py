@@ -140,19 +140,34 @@ def load_checkpoint(path=CHECKPOINT):
     return d["params"].astype(np.float32), json.loads(str(d["meta"]))
 
 
-def train_default(ctx, n_train=65536, epochs=60, seed=0, verbose=False):
-    """Labels on the seeded training set (the c5 recipe, its own seed) and a trained network."""
+def balanced_weights(y):
+    """Class weights sqrt(n / (6 n_c)) clipped to [0.5, 10]: rare high-G classes count more."""
+    cnt = np.bincount(y, minlength=len(CLASS_NPTS)).astype(float)
+    w = np.sqrt(y.size / (len(CLASS_NPTS) * np.maximum(cnt, 1.0)))
+    return np.clip(w, 0.5, 10.0).astype(np.float32)
+
+
+def train_default(ctx, n_train=65536, epochs=60, seed=0, verbose=False, shards=(0,), balance=False):
+    """Labels on the seeded training sets (the c5 recipe with its own seed: shards of
+    c5train, shard 1 excluded as the held-out set) and a trained network."""
+    torch = _torch()
+    assert 1 not in shards, "shard 1 is the held-out set"
     t0 = time.time()
-    wl = W.make("c5train", n_train)
-    err = class_errors(ctx, wl)
-    y = labels_from_errors(err)
+    Xs, ys = [], []
+    for sh in shards:
+        wl = W.make("c5train", n_train, shard=sh)
+        ys.append(labels_from_errors(class_errors(ctx, wl)))
+        Xs.append(features(ctx, wl))
+    y = np.concatenate(ys)
     t1 = time.time()
-    X = features(ctx, wl)
+    X = torch.cat(Xs)
+    cw = balanced_weights(y) if balance else None
     params, hist = train(ctx, X, y, epochs=epochs, batch=1024, lr=2e-3, seed=seed, log_every=20 if verbose else 0,
-                         weight_decay=1e-3)
+                         weight_decay=1e-3, class_weight=cw)
     t2 = time.time()
     pred = classes_of(predict(ctx, params, X))
-    meta = {"n_train": int(n_train), "epochs": int(epochs), "label_tol": LABEL_TOL,
+    meta = {"n_train": int(y.size), "shards": list(shards), "epochs": int(epochs), "label_tol": LABEL_TOL,
+            "class_weight": None if cw is None else cw.tolist(),
             "label_hist": np.bincount(y, minlength=6).tolist(), "train_acc": float((pred == y).mean()),
             "train_under": float((pred < y).mean()), "final_loss": float(hist[-1]),
             "label_seconds": t1 - t0, "train_seconds": t2 - t1}
@@ -186,7 +201,7 @@ def learned_errors(ctx, params, wl, risk, margin=0, ref=None, device="cuda"):
     return e, g, ref
 
 
-def calibrate_risk(ctx, params, n_elem=8192, tol=1e-8, sweep=RISK_SWEEP):
+def calibrate_risk(ctx, params, n_elem=32768, tol=1e-8, sweep=RISK_SWEEP):
     """Choose the class rule's risk (R13) on held-out elements: shard 1 of the training
     recipe (another seed; neither trained on nor benchmarked).  The learned mixed fill runs
     with the judge off at each risk of the sweep and every element is compared with its
@@ -239,8 +254,17 @@ if __name__ == "__main__":
         save(rest[0] if rest else CHECKPOINT, params, meta)
         print(json.dumps(meta))
         sys.exit(0)
-    params, meta = train_default(ctx, verbose=True)
+    # python -m paper_1703_09619_gb300.learned [--shards 0,2,3,4] [--balance] [out.npz]
+    args = sys.argv[1:]
+    shards = (0,)
+    if "--shards" in args:
+        i = args.index("--shards")
+        shards = tuple(int(v) for v in args[i + 1].split(","))
+        del args[i:i + 2]
+    balance = "--balance" in args
+    args = [a for a in args if a != "--balance"]
+    params, meta = train_default(ctx, verbose=True, shards=shards, balance=balance)
     meta["risk"], meta["risk_calibration"] = calibrate_risk(ctx, params)
-    out = sys.argv[1] if len(sys.argv) > 1 else CHECKPOINT
+    out = args[0] if args else CHECKPOINT
     save(out, params, meta)
     print(json.dumps(meta))
