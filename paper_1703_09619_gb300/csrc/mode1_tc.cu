@@ -386,10 +386,9 @@ cudaError_t launch_tc(const float2* x, int64_t n_rows, int64_t n_src, float2* ou
     const size_t smem = tc_smem<G, S>();
     cudaError_t e = cudaFuncSetAttribute(k_mode1_tc<G, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int per = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mode1_tc<G, S>, kM1Threads, smem);
-    if (e != cudaSuccess) return e;
-    per = std::max(1, std::min(per, 4));  // TMEM: 4 x 64 columns per SM at most
+    // CTAs per SM: as many as shared memory holds (about 220 KB per SM), at most 4 (4 x 64
+    // TMEM columns of 512), so that several CTAs' serial phases overlap
+    const int per = (int)std::max<size_t>(1, std::min<size_t>(4, (220u << 10) / (smem + 2048)));
     const int64_t tiles = (n_rows + 127) / 128;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * per));
     k_mode1_tc<G, S><<<grid, kM1Threads, smem, s>>>(x, n_rows, n_src, out, err);
