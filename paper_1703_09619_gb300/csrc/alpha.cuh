@@ -55,23 +55,4 @@ __device__ __forceinline__ bool metric_alpha(const double* geo, double u, double
     return det > 0.0;
 }
 
-
-// The element constants above from nodes [8][3], bulge (a, b) and params (A, k) (one thread).
-__device__ __forceinline__ void metric_geo(const double* X, const double* bg, const double* p, double* geo) {
-    for (int i = 0; i < 3; ++i) {
-        double c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int nd = 0; nd < 8; ++nd) {
-            double su = (nd & 1) ? 1.0 : -1.0, sv = (nd & 2) ? 1.0 : -1.0, sw = (nd & 4) ? 1.0 : -1.0;
-            double xv = 0.125 * X[3 * nd + i];
-            c[0] += xv; c[1] += su * xv; c[2] += sv * xv; c[3] += sw * xv;
-            c[4] += su * sv * xv; c[5] += su * sw * xv; c[6] += sv * sw * xv; c[7] += su * sv * sw * xv;
-        }
-        for (int j = 0; j < 8; ++j) geo[8 * i + j] = c[j];
-        geo[24 + i] = bg ? bg[0] * bg[1 + i] : 0.0;
-    }
-    for (int j = 0; j < 8; ++j) geo[31 + j] = p[1] * geo[j] + p[2] * geo[8 + j] + p[3] * geo[16 + j];
-    geo[27] = p[0];
-    geo[39] = p[1] * geo[24] + p[2] * geo[25] + p[3] * geo[26];
-}
-
 }  // namespace p2s

@@ -101,6 +101,17 @@ __device__ __forceinline__ dw dw_div_fast(dw x, dw y) {
     return fast_two_sum(q1, __fdiv_rn(r, y.hi));
 }
 
+// Sums without the final renormalisation: (s, e + x.lo + y.lo) with s + e = x.hi + y.hi
+// exactly (TwoSum).  The pair still represents the sum to O(u^2 (|x| + |y|)); its low word may
+// exceed half an ulp of the high one, which every _fast and _lazy operation here accepts in
+// an operand (products take both words of each operand, sums TwoSum the high words).
+__device__ __forceinline__ dw dw_add_lazy(dw x, dw y) {
+    const dw s = two_sum(x.hi, y.hi);
+    return dw{s.hi, s.lo + (x.lo + y.lo)};
+}
+__device__ __forceinline__ dw dw_sub_lazy(dw x, dw y) { return dw_add_lazy(x, dw_neg(y)); }
+__device__ __forceinline__ dw dw_fma_lazy(dw x, dw y, dw z) { return dw_add_lazy(dw_mul_fast(x, y), z); }
+
 // Accumulator for sums of products: the leading words sum with TwoSum, every rounding
 // error and lower-order product term goes to the second word; renormalise at the end.
 struct dw_acc {

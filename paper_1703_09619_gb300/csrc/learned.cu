@@ -52,8 +52,9 @@ __device__ __forceinline__ double warp_max_d(double v) {
 }
 
 // Four elements per CTA, 64 threads (one coarse point each) per element.  The cosines and
-// sines of the four positions are computed once per CTA; the element constants by one
-// thread of each element; the trace mean by warp shuffles.
+// sines of the four positions are computed once per CTA; the element constants (the geo[]
+// layout of alpha.cuh) by 27 threads of each element, one trilinear coefficient or bulge
+// entry each, then the phase coefficients by 10; the trace mean by warp shuffles.
 constexpr int kFeatElems = 4;
 __global__ void __launch_bounds__(64 * kFeatElems) k_features(const double* __restrict__ nodes,
                                                                const double* __restrict__ bulge,
@@ -68,7 +69,29 @@ __global__ void __launch_bounds__(64 * kFeatElems) k_features(const double* __re
     for (int64_t e0 = (int64_t)blockIdx.x * kFeatElems; e0 < E; e0 += (int64_t)gridDim.x * kFeatElems) {
         const int64_t e = e0 + sub;
         const bool on = e < E;
-        if (on && p == 0) metric_geo(nodes + 24 * e, bulge ? bulge + 4 * e : nullptr, params + 4 * e, geo[sub]);
+        if (on && p < 24) {  // coefficient j of coordinate i: signed sum over the 8 nodes
+            const int i = p >> 3, j = p & 7;
+            const double* X = nodes + 24 * e;
+            double c = 0.0;
+            for (int nd = 0; nd < 8; ++nd) {
+                const double su = (nd & 1) ? 1.0 : -1.0, sv = (nd & 2) ? 1.0 : -1.0, sw = (nd & 4) ? 1.0 : -1.0;
+                const double sg = j == 0 ? 1.0 : j == 1 ? su : j == 2 ? sv : j == 3 ? sw
+                                : j == 4 ? su * sv : j == 5 ? su * sw : j == 6 ? sv * sw : su * sv * sw;
+                const double xv = 0.125 * X[3 * nd + i];
+                c += j == 0 ? xv : sg * xv;
+            }
+            geo[sub][p] = c;
+        } else if (on && p < 27) {
+            geo[sub][p] = bulge ? bulge[4 * e] * bulge[4 * e + 1 + (p - 24)] : 0.0;
+        }
+        __syncthreads();
+        if (on && p < 10) {
+            const double* pr = params + 4 * e;
+            const double* g = geo[sub];
+            if (p < 8) geo[sub][31 + p] = pr[1] * g[p] + pr[2] * g[8 + p] + pr[3] * g[16 + p];
+            else if (p == 8) geo[sub][39] = pr[1] * g[24] + pr[2] * g[25] + pr[3] * g[26];
+            else geo[sub][27] = pr[0];
+        }
         __syncthreads();
         const int a = p & 3, b = (p >> 2) & 3, c = p >> 4;
         double K[6] = {0, 0, 0, 0, 0, 0};
