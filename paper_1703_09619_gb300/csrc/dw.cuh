@@ -155,30 +155,23 @@ __device__ __forceinline__ dw dw_sin(dw x) {
     r = dw_add_f(r, -n * C4);
     const dw z = dw_mul_fast(r, r);
     const int q = ((int)n) & 3;
-    dw res;
-    if (q & 1) {
-        // cos r = 1 - z/2 + z^2/24 - z^3/720 + z^4/40320 - z^5/3628800 + z^6/479001600 - ...
-        const float zf = z.hi;
-        float t = fmaf(zf, 2.08767569878680990e-9f, -2.75573192239858907e-7f);
-        t = fmaf(zf, t, 2.48015873015873016e-5f);
-        t = fmaf(zf, t, -1.38888888888888889e-3f);  // tail: z^2 (1/24 ...) handled below
-        // cos r = 1 - z/2 + z^2 (1/24 + z t)
-        const dw c24 = dw_make(0.041666667908430099f, -1.2417634698280722e-09f);  // 1/24
-        const dw w = dw_add_f(c24, zf * t);
-        const dw z2 = dw_mul_fast(z, z);
-        res = dw_add_fast(dw_add_f(dw_make(-0.5f * z.hi, -0.5f * z.lo), 1.f), dw_mul_fast(z2, w));
-    } else {
-        // sin r = r - r^3/6 + r^5/120 - r^7/5040 + r^9/362880 - r^11/39916800 + r^13/6227020800
-        const float zf = z.hi;
-        float t = fmaf(zf, 1.60590438368216146e-10f, -2.50521083854417188e-8f);
-        t = fmaf(zf, t, 2.75573192239858907e-6f);
-        t = fmaf(zf, t, -1.98412698412698413e-4f);
-        // sin r = r + r z (-1/6 + z (1/120 + z t))
-        const dw c120 = dw_make(0.0083333337679505348f, -4.3461720333759502e-10f);  // 1/120
-        const dw c6 = dw_make(-0.1666666716337204f, 4.9670538793122887e-09f);       // -1/6
-        const dw inner = dw_add_fast(c6, dw_mul_fast(z, dw_add_f(c120, zf * t)));
-        res = dw_add_fast(r, dw_mul_fast(dw_mul_fast(r, z), inner));
-    }
+    // One branch-free evaluation for both quadrant parities (lanes of a warp take different
+    // quadrants): res = A + B z (c1 + z (c2 + z t(z))) with
+    //   sin r: A = B = r, c1 = -1/6, c2 = 1/120, t = -1/5040 + z/362880 - z^2/39916800 + z^3/6227020800;
+    //   cos r: A = B = 1, c1 = -1/2, c2 = 1/24,  t = -1/720 + z/40320 - z^2/3628800 + z^3/479001600
+    // (the leading terms in double word, the tail, below 1e-3 in magnitude, in FP32).
+    const bool c = q & 1;
+    const float zf = z.hi;
+    float t = fmaf(zf, c ? 2.08767569878680990e-9f : 1.60590438368216146e-10f,
+                   c ? -2.75573192239858907e-7f : -2.50521083854417188e-8f);
+    t = fmaf(zf, t, c ? 2.48015873015873016e-5f : 2.75573192239858907e-6f);
+    t = fmaf(zf, t, c ? -1.38888888888888889e-3f : -1.98412698412698413e-4f);
+    const dw c2 = c ? dw_make(0.041666667908430099f, -1.2417634698280722e-09f)    // 1/24
+                    : dw_make(0.0083333337679505348f, -4.3461720333759502e-10f);  // 1/120
+    const dw c1 = c ? dw_make(-0.5f, 0.f) : dw_make(-0.1666666716337204f, 4.9670538793122887e-09f);  // -1/2, -1/6
+    const dw A = c ? dw_make(1.f, 0.f) : r;
+    const dw inner = dw_add_fast(c1, dw_mul_fast(z, dw_add_f(c2, zf * t)));
+    const dw res = dw_add_fast(A, dw_mul_fast(dw_mul_fast(A, z), inner));
     return (q & 2) ? dw_neg(res) : res;
 }
 
