@@ -22,8 +22,9 @@
 // Operands live in shared memory in the no-swizzle K-major layout: 8 x 16-byte core
 // matrices, k-adjacent core matrices 128 B apart (LBO), 8-row groups KA/8 x 128 B apart
 // (SBO).  Rows x come from a source array of n_src rows, row r reading source row r mod
-// n_src, so that a small source can stay in L2 and the kernels' arithmetic is what is
-// timed.  This is a measurement of the tensor-core form against the SIMT form on the
+// n_src, so that a small source can stay in L2; both forms stage each tile of 128 rows in
+// shared memory with coalesced loads (the fused moment kernel holds its samples there too),
+// so that the kernels' arithmetic is what is timed.  This is a measurement of the tensor-core form against the SIMT form on the
 // same work (p2s_mode1_product); the fused moment kernel keeps the SIMT form.
 #include <cmath>
 #include <cstring>
@@ -114,40 +115,63 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
 __device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
 
 template <int G>
-__device__ __forceinline__ void load_pair(const float2* __restrict__ row, int p, dw& a, dw& b) {
-    const float2 u = __ldg(row + p), v = __ldg(row + G - 1 - p);
+__device__ __forceinline__ void load_pair(const float2* row, int p, dw& a, dw& b) {
+    const float2 u = row[p], v = row[G - 1 - p];
     a = dw{u.x, u.y};
     b = dw{v.x, v.y};
+}
+
+// Row stride (float2) of a staged tile: odd, so that a warp's row-per-thread reads spread
+// over the banks.
+__host__ __device__ constexpr int tile_ld(int G) { return G + 1; }
+
+// The 128 rows of tile t into shared memory, coalesced (consecutive threads take
+// consecutive samples); rows past n_rows are zero.  As in the fused moment kernel, the
+// samples a thread works on then come from shared memory.
+template <int G>
+__device__ __forceinline__ void stage_tile(const float2* __restrict__ x, int64_t n_rows, int64_t n_src, int64_t t,
+                                           float2* sX) {
+    for (int i = threadIdx.x; i < 128 * G; i += kM1Threads) {
+        const int rr = i / G, a = i - rr * G;
+        const int64_t r = t * 128 + rr;
+        sX[rr * tile_ld(G) + a] = r < n_rows ? __ldg(x + (r % n_src) * G + a) : make_float2(0.f, 0.f);
+    }
 }
 
 template <int G>
 __global__ void __launch_bounds__(kM1Threads) k_mode1_simt(const float2* __restrict__ x, int64_t n_rows,
                                                            int64_t n_src, float2* __restrict__ out) {
     constexpr int H = G / 2;
+    extern __shared__ __align__(16) unsigned char sm_simt[];
+    float2* sX = reinterpret_cast<float2*>(sm_simt);
     const int64_t tiles = (n_rows + kM1Threads - 1) / kM1Threads;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        stage_tile<G>(x, n_rows, n_src, t, sX);
+        __syncthreads();
         const int64_t r = t * kM1Threads + threadIdx.x;
-        if (r >= n_rows) continue;
-        const float2* row = x + (r % n_src) * G;
-        dw_acc acc[kM1K];
+        if (r < n_rows) {
+            const float2* row = sX + threadIdx.x * tile_ld(G);
+            dw_acc acc[kM1K];
 #pragma unroll 4
-        for (int p = 0; p < H; ++p) {
-            dw a, b;
-            load_pair<G>(row, p, a, b);
-            const dw E = dw_add_fast(a, b), O = dw_sub_fast(a, b);
+            for (int p = 0; p < H; ++p) {
+                dw a, b;
+                load_pair<G>(row, p, a, b);
+                const dw E = dw_add_fast(a, b), O = dw_sub_fast(a, b);
 #pragma unroll
-            for (int k = 0; k < kM1K; ++k) {
-                const float2 b = c_m1_B[k][p];
-                acc[k].fma(dw{b.x, b.y}, (k & 1) ? O : E);
+                for (int k = 0; k < kM1K; ++k) {
+                    const float2 bk = c_m1_B[k][p];
+                    acc[k].fma(dw{bk.x, bk.y}, (k & 1) ? O : E);
+                }
             }
+            float4* o = reinterpret_cast<float4*>(out + r * 8);
+            dw v[8];
+#pragma unroll
+            for (int k = 0; k < kM1K; ++k) v[k] = acc[k].value();
+            v[7] = dw{0.f, 0.f};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) o[q] = make_float4(v[2 * q].hi, v[2 * q].lo, v[2 * q + 1].hi, v[2 * q + 1].lo);
         }
-        float4* o = reinterpret_cast<float4*>(out + r * 8);
-        dw v[8];
-#pragma unroll
-        for (int k = 0; k < kM1K; ++k) v[k] = acc[k].value();
-        v[7] = dw{0.f, 0.f};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) o[i] = make_float4(v[2 * i].hi, v[2 * i].lo, v[2 * i + 1].hi, v[2 * i + 1].lo);
+        __syncthreads();  // the tile buffer is free
     }
 }
 
@@ -178,6 +202,7 @@ __global__ void __launch_bounds__(kM1Threads) k_mode1_tc(const float2* __restric
     unsigned char* sAO = sAE + 128 * KA * 2;         // odd part
     unsigned char* sBE = sAO + 128 * KA * 2;         // kNE x KA
     unsigned char* sBO = sBE + kNE * KA * 2;         // kNO x KA
+    float2* sX = reinterpret_cast<float2*>(sBO + kNO * KA * 2);  // 128 x tile_ld(G) samples
     __shared__ __align__(8) unsigned long long s_bar;
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail;
@@ -212,12 +237,14 @@ __global__ void __launch_bounds__(kM1Threads) k_mode1_tc(const float2* __restric
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
         const int64_t r = t * 128 + tid;
         const bool live = r < n_rows;
-        const float2* row = x + ((live ? r : 0) % n_src) * G;
+        stage_tile<G>(x, n_rows, n_src, t, sX);
+        __syncthreads();
+        const float2* row = sX + tid * tile_ld(G);
         // bound of the folded row: max_p |x_p| + |x_q| >= max(|E_p|, |O_p|)
         float m = 0.f;
 #pragma unroll 4
         for (int p = 0; p < H; ++p) {
-            const float2 u = __ldg(row + p), v = __ldg(row + G - 1 - p);
+            const float2 u = row[p], v = row[G - 1 - p];
             m = fmaxf(m, fabsf(u.x) + fabsf(v.x));
         }
         int e = 0;
@@ -319,7 +346,7 @@ __global__ void __launch_bounds__(kM1Threads) k_mode1_tc(const float2* __restric
 
 template <int G, int S>
 size_t tc_smem() {
-    return (size_t)(2 * 128 + kNE + kNO) * ka_of(G, S) * 2;
+    return (size_t)(2 * 128 + kNE + kNO) * ka_of(G, S) * 2 + sizeof(float2) * 128 * tile_ld(G);
 }
 
 // Host tables of one rule: B[k][p] (p < G/2) and the TC images with their column exponents.
@@ -397,9 +424,13 @@ cudaError_t launch_tc(const float2* x, int64_t n_rows, int64_t n_src, float2* ou
 
 template <int G>
 cudaError_t launch_simt(const float2* x, int64_t n_rows, int64_t n_src, float2* out, int sms, cudaStream_t s) {
+    const size_t smem = sizeof(float2) * 128 * tile_ld(G);
+    cudaError_t e = cudaFuncSetAttribute(k_mode1_simt<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int per = (int)std::max<size_t>(1, std::min<size_t>(16, (220u << 10) / (smem + 1024)));
     const int64_t tiles = (n_rows + kM1Threads - 1) / kM1Threads;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * 16));
-    k_mode1_simt<G><<<grid, kM1Threads, 0, s>>>(x, n_rows, n_src, out);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * per));
+    k_mode1_simt<G><<<grid, kM1Threads, smem, s>>>(x, n_rows, n_src, out);
     return cudaGetLastError();
 }
 
