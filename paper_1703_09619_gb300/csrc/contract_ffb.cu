@@ -218,12 +218,17 @@ __device__ __forceinline__ void ffb_stage3(const typename A::T* __restrict__ sB,
 
 __device__ __forceinline__ int type_slot_ffb(uint32_t mask, int t) { return __popc(mask & ((1u << t) - 1u)); }
 
-// Persistent CTAs take units from the queue.  Thread 0 keeps the current and the next unit in
-// shared slots indexed by iteration parity; the next unit's moments are copied into the
-// moment buffer (free once stage 1 is done) while stages 2 and 3 run.  Three barriers per
-// unit.  Shared memory: moments (a_cap), stage 1 (s1_cap), stage 2 (b_cap), in 8-byte words
-// (FP64 values or (hi, lo) FP32 pairs).  Units of elements whose mask entry is 0 (elem_mask,
-// optional) are taken from the queue and skipped.
+// Persistent CTAs take units from the queue.  The stages are software-pipelined over units:
+// one interval between two CTA barriers runs stage 2 of unit u while the moments of unit u+1
+// arrive by cp.async (into the moment buffer, free once stage 1 of u is done), and the next
+// interval runs stage 3 of unit u and stage 1 of unit u+1 together (they touch different
+// buffers), so a unit costs two barriers and threads with no stage-3 combination go on to
+// the next unit's stage 1.  Thread 0 keeps the units in a ring of three shared slots (the
+// unit of iteration i in slot i mod 3) and fetches unit u+2 during iteration u.  Shared
+// memory: moments (a_cap), stage 1 (s1_cap), stage 2 (b_cap), in 8-byte words (FP64 values
+// or (hi, lo) FP32 pairs).  Units of elements whose mask entry is 0 (elem_mask, optional) are
+// taken from the queue and skipped.  Every entry is computed by the same operations in the
+// same order as in the unpipelined loop.
 template <class A>
 __global__ void __launch_bounds__(512) k_contract_ffb(ContractLaunch L) {
     using T = typename A::T;
@@ -232,37 +237,47 @@ __global__ void __launch_bounds__(512) k_contract_ffb(ContractLaunch L) {
     T* sI = reinterpret_cast<T*>(smraw);  // moments of the unit's pair, [k][l][q]
     T* sA = sI + L.a_cap;                  // stage 1, [im1][m2][l][q]
     T* sB = sA + L.s1_cap;                 // stage 2, [combination][q] (odd stride)
-    __shared__ ContractUnit s_cu[2], s_nx[2];  // e = -1: no unit
+    __shared__ ContractUnit s_u[3];        // e = -1: no unit
     const int tid = threadIdx.x, nth = blockDim.x;
     const unsigned long long nu = (unsigned long long)L.n_units;
-
-    if (tid == 0) {
+    auto fetch = [&](ContractUnit& slot) {
         ContractUnit none{};
         none.e = -1;
-        const unsigned long long a = atomicAdd(L.counter, 1ull), b = atomicAdd(L.counter, 1ull);
-        s_cu[0] = a < nu ? L.units[a] : none;
-        s_nx[0] = b < nu ? L.units[b] : none;
+        const unsigned long long a = atomicAdd(L.counter, 1ull);
+        slot = a < nu ? L.units[a] : none;
+    };
+    auto skipped = [&](const ContractUnit& u) { return L.elem_mask && !L.elem_mask[u.e]; };
+    auto stage1 = [&](const ContractUnit& u) {
+        const ElemDesc* d = L.desc + u.e;
+        ffb_stage1<A>(L, u.t, sI, sA, ffb_shape(d, u.gi, u.gj), u.m1a, u.m1n, tid, nth);
+    };
+
+    if (tid == 0) {
+        fetch(s_u[0]);
+        fetch(s_u[1]);
     }
     __syncthreads();
-    if (s_cu[0].e >= 0) {
-        const ContractUnit u = s_cu[0];
-        const size_t m0 = ffb_moments(L, u);
-        const int cnt = unit_moment_count(L.desc + u.e, u.gi, u.gj);
-        for (int i = tid; i < cnt; i += nth) sI[i] = A::load_moment(L.mom, m0 + i);
+    {  // prologue: moments and stage 1 of the first unit
+        const ContractUnit u = s_u[0];
+        if (u.e >= 0) {
+            const size_t m0 = ffb_moments(L, u);
+            const int cnt = unit_moment_count(L.desc + u.e, u.gi, u.gj);
+            for (int i = tid; i < cnt; i += nth) sI[i] = A::load_moment(L.mom, m0 + i);
+        }
+        __syncthreads();
+        if (u.e >= 0 && !skipped(u)) stage1(u);
+        __syncthreads();
     }
-    __syncthreads();
     for (int iter = 0;; ++iter) {
-        const int par = iter & 1;
-        const ContractUnit cu = s_cu[par];
+        const ContractUnit cu = s_u[iter % 3];
         if (cu.e < 0) break;
+        const ContractUnit nx = s_u[(iter + 1) % 3];
         const ElemDesc* d = L.desc + cu.e;
         const int gi = cu.gi, gj = cu.gj, t = cu.t, m1a = cu.m1a, m1n = cu.m1n;
         const FfbShape s = ffb_shape(d, gi, gj);
         const int64_t n = d->n;
-        const bool skip = L.elem_mask && !L.elem_mask[cu.e];  // uniform: cu is shared
-        if (!skip) ffb_stage1<A>(L, t, sI, sA, s, m1a, m1n, tid, nth);
-        __syncthreads();  // stage-1 results complete; the moment buffer is free
-        const ContractUnit nx = s_nx[par];
+        const bool skip = skipped(cu);  // uniform: cu is shared
+        // the next unit's moments into the moment buffer (stage 1 of cu is done)
         if (nx.e >= 0) {
             const T* gN = reinterpret_cast<const T*>(L.mom) + ffb_moments(L, nx);
             const int cnt = unit_moment_count(L.desc + nx.e, nx.gi, nx.gj);
@@ -276,7 +291,9 @@ __global__ void __launch_bounds__(512) k_contract_ffb(ContractLaunch L) {
             default: ffb_stage2<A, 3>(sA, sB, s, m1n, tid, nth); break;
             }
         }
-        __syncthreads();  // stage-2 results complete
+        if (tid == 0) fetch(s_u[(iter + 2) % 3]);  // that slot held unit iter - 1, finished
+        cp_async_wait_all();
+        __syncthreads();  // stage 2 of cu complete; the moments of nx in place
         // the unit's results are rows [rbase, rbase + m1n Nv_i Nw_i) x columns [col0, col0 + n_j)
         const int rbase = d->dof_off[gi] + m1a * s.Nv_i * s.Nw_i;
         const int col0 = d->dof_off[gj];
@@ -292,15 +309,8 @@ __global__ void __launch_bounds__(512) k_contract_ffb(ContractLaunch L) {
         case 2: ffb_stage3<A, 2>(sB, s, ncombo, tid, nth, Mt, Mp, n, rmjn); break;
         default: ffb_stage3<A, 3>(sB, s, ncombo, tid, nth, Mt, Mp, n, rmjn); break;
         }
-        if (tid == 0) {  // the unit after next, into the other slot
-            ContractUnit none{};
-            none.e = -1;
-            const unsigned long long c = atomicAdd(L.counter, 1ull);
-            s_cu[par ^ 1] = nx;
-            s_nx[par ^ 1] = c < nu ? L.units[c] : none;
-        }
-        cp_async_wait_all();
-        __syncthreads();  // the next unit's moments in place; the stage-2 buffer free
+        if (nx.e >= 0 && !skipped(nx)) stage1(nx);  // into the stage-1 buffer, read by stage 2 above already
+        __syncthreads();  // stage 1 of nx complete; the stage-2 and moment buffers free
     }
 }
 

@@ -103,7 +103,10 @@ HostTables* build() {
         int d1 = t & 1, d2 = (t >> 1) & 1;
         for (int m1 = 0; m1 < kMaxOrder; ++m1)
             for (int m2 = 0; m2 < kMaxOrder; ++m2) {
-                product_dense(d1, d2, m1, m2, dense);
+                // the product is commutative: compute it with its factors in one canonical
+                // order, so that (t, m1, m2) and its mirror (t', m2, m1) get the same bits
+                if (d1 > d2 || (d1 == d2 && m1 > m2)) product_dense(d2, d1, m2, m1, dense);
+                else product_dense(d1, d2, m1, m2, dense);
                 int kmax = m1 + m2 - d1 - d2;
                 int kmin = -1;
                 for (int k = (kmax >= 0 ? kmax % 2 : 0); k <= kmax; k += 2)

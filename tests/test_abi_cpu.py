@@ -104,3 +104,14 @@ def test_argument_errors_on_host():
     with pytest.raises(p2s.P2SError):
         p2s.linearisation(4, 0, 0, 3)
     assert p2s.error_string(p2s.ERR_JACOBIAN).startswith("detJ")
+
+
+def test_linearisation_tables_mirror_bit_for_bit():
+    """P^(d1)_m1 P^(d2)_m2 = P^(d2)_m2 P^(d1)_m1: the table of (vv, m1, m2) equals that of
+    (vv, m2, m1), dv that of vd mirrored, dd its mirror, bit for bit (the kernels that
+    compute a block in its own orientation rely on it to match the transposed write-out)."""
+    n = p2s.MAX_ORDER
+    for a in range(n):
+        for b in range(n):
+            for t, tm in ((0, 0), (1, 2), (3, 3)):
+                assert np.array_equal(p2s.linearisation(t, a, b, 2 * n), p2s.linearisation(tm, b, a, 2 * n)), (t, a, b)
