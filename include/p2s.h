@@ -177,12 +177,7 @@ int p2s_plan_fill(p2s_plan* plan, const p2s_geometry* geom, const p2s_material* 
  *                   either precision), else the general kernel;
  *                 1 the general kernel;
  *                 2 the bounded-order kernel (every order <= 8; plan creation fails with
- *                   P2S_ERR_ORDER otherwise);
- *                 3 the bounded-order kernel with every block of every type computed in
- *                   its own orientation: no block is written as the transpose of another
- *                   (vv(j,i) = vv(i,j)^T and the like still hold: the same operations in
- *                   the same order give them), which writes every row of a unit in whole
- *                   contiguous segments at the price of computing those blocks twice. */
+ *                   P2S_ERR_ORDER otherwise). */
 typedef struct {
     int combo_target;
     int unit_kbytes;
@@ -202,8 +197,7 @@ int p2s_plan_tile_config(const p2s_plan* plan, p2s_tile_config* out);
 
 /* Autotuner: builds a plan per candidate configuration (combo targets 64..512 x budgets
  * 24/48/100 KiB x derived/128/256-thread CTAs with the library's kernel choice, and the
- * bounded-order kernel, with and without transposed write-out, at each combo target and
- * CTA size) on the first
+ * bounded-order kernel at each combo target and CTA size) on the first
  * `sample` elements of the batch
  * (<= 0: all), computes their moments once, times `reps` contractions of each candidate
  * with CUDA events on `stream` (median) and writes the fastest to *best (host), its time

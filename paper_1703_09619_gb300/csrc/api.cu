@@ -183,15 +183,8 @@ void push_block(const ElemDesc& d, int32_t e, int gi, int gj, int t, int tp, Uni
 }
 
 void add_units(const ElemDesc& d, uint32_t mask, int32_t e, UnitSink& units, int spec_n, const TileParams& tile,
-               bool ffb, bool direct = false) {
+               bool ffb) {
     const int nc = d.n_comp;
-    if (direct) {  // every selected block and type in its own orientation: no transposed write-out
-        for (int t = 0; t < kNumTypes; ++t)
-            if (mask & (1u << t))
-                for (int gi = 0; gi < nc; ++gi)
-                    for (int gj = 0; gj < nc; ++gj) push_block(d, e, gi, gj, t, -1, units, spec_n, tile, ffb);
-        return;
-    }
     for (int t : {0, 3}) {  // vv, dd: upper blocks, transposed into the lower ones
         if (!(mask & (1u << t))) continue;
         for (int gi = 0; gi < nc; ++gi)
@@ -289,7 +282,7 @@ int tile_params_from(const p2s_tile_config* c, TileParams& tp) {
     if (c->combo_target < 0 || c->combo_target > 4096 || c->unit_kbytes < 0 || c->unit_kbytes > 227 ||
         c->threads < 0 || c->threads > 512 || (c->threads && (c->threads < 64 || c->threads % 32)))
         return fail(P2S_ERR_ARG, "tile config: combo_target 0..4096, unit_kbytes 0..227, threads 0 or 64..512 in steps of 32");
-    if (c->kernel < 0 || c->kernel > 3) return fail(P2S_ERR_ARG, "tile config: kernel 0, 1, 2 or 3");
+    if (c->kernel < 0 || c->kernel > 2) return fail(P2S_ERR_ARG, "tile config: kernel 0, 1 or 2");
     if (c->combo_target) tp.combo_target = c->combo_target;
     if (c->unit_kbytes) tp.unit_bytes = (size_t)c->unit_kbytes * 1024;
     tp.threads = c->threads;
@@ -327,7 +320,7 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
     int spec_n = 0;
     bool ffb = false;
     FfbLaunch ffl;
-    if ((tile.kernel == 2 || tile.kernel == 3) && E > 0 && !moments_only) {
+    if (tile.kernel == 2 && E > 0 && !moments_only) {
         if (!(T.spec_ok && ffb_launch_shape(T, E, orders, tile, limit, L.precision, ffl)))
             return fail(P2S_ERR_ORDER, "plan: the bounded-order kernel needs orders <= 8 and a fitting unit");
         ffb = true;
@@ -378,7 +371,7 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
         max_pair = std::max(max_pair, d.kax[0] * d.kax[1] * d.kax[2]);
         max_elem_mom = std::max(max_elem_mom, L.n_pairs * d.kax[0] * d.kax[1] * d.kax[2]);
         L.gmax = std::max(L.gmax, G);
-        if (!moments_only) add_units(d, opts->types_mask, (int32_t)e, units, spec_n, tile, ffb, tile.kernel == 3);
+        if (!moments_only) add_units(d, opts->types_mask, (int32_t)e, units, spec_n, tile, ffb);
     }
     L.out_entries = out_off;
     L.mom_entries = mom_off;

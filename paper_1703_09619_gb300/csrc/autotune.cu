@@ -27,8 +27,8 @@ struct Candidate {
 
 // combo targets x shared-memory budgets, each with the derived CTA size (one thread per
 // combination of the largest unit) and with fixed 128- and 256-thread CTAs, with the library's
-// kernel choice, and the bounded-order kernel (no shared-memory tile, so no budget), with and
-// without transposed write-out, at each combo target and CTA size
+// kernel choice, and the bounded-order kernel (no shared-memory tile, so no budget) at each
+// combo target and CTA size
 std::vector<Candidate> candidates() {
     std::vector<Candidate> c;
     const int combos[] = {64, 128, 256, 512};
@@ -38,10 +38,7 @@ std::vector<Candidate> candidates() {
         for (int kb : kbytes)
             for (int th : threads) c.push_back({co, kb, th, 0});
     for (int co : combos)
-        for (int th : threads) {
-            c.push_back({co, 0, th, 2});
-            c.push_back({co, 0, th, 3});
-        }
+        for (int th : threads) c.push_back({co, 0, th, 2});
     return c;
 }
 

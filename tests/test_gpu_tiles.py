@@ -98,8 +98,7 @@ def test_bounded_order_kernel_matches_general_bitwise(torch, ctx, mask, prec):
     wl = with_orders(uneven(20, 5), 1, 8, 17)
     ref, cfg = fill(torch, ctx, wl, prec, tile={"kernel": 1}, types_mask=mask)
     assert cfg["kernel"] == 1
-    for tile in (None, {"combo_target": 1, "threads": 64}, {"combo_target": 512, "threads": 256, "kernel": 2},
-                 {"combo_target": 512, "threads": 512, "kernel": 3}, {"combo_target": 64, "threads": 128, "kernel": 3}):
+    for tile in (None, {"combo_target": 1, "threads": 64}, {"combo_target": 512, "threads": 256, "kernel": 2}):
         got, cfg = fill(torch, ctx, wl, prec, tile=tile, types_mask=mask)
         assert cfg["kernel"] == (tile or {}).get("kernel", 0)
         assert np.array_equal(got, ref), (mask, tile)
@@ -113,7 +112,7 @@ def test_uniform_orders_all_kernels_bitwise(torch, ctx, name, N, prec):
     wl = W.make(name, 3).with_npts(5)
     assert (wl.orders == N).all()
     ref, _ = fill(torch, ctx, wl, prec, tile={"kernel": 1})
-    for tile in (None, {"kernel": 2}, {"kernel": 2, "combo_target": 64, "threads": 128}, {"kernel": 3}):
+    for tile in (None, {"kernel": 2}, {"kernel": 2, "combo_target": 64, "threads": 128}):
         got, _ = fill(torch, ctx, wl, prec, tile=tile)
         assert np.array_equal(got, ref), (name, tile)
 
@@ -161,7 +160,7 @@ def test_bad_tile_config(torch, ctx):
     for tile in ({"combo_target": -1, "unit_kbytes": 0, "threads": 0},
                  {"combo_target": 0, "unit_kbytes": 0, "threads": 100},
                  {"combo_target": 0, "unit_kbytes": 300, "threads": 0},
-                 {"combo_target": 0, "unit_kbytes": 0, "threads": 0, "kernel": 4}):
+                 {"combo_target": 0, "unit_kbytes": 0, "threads": 0, "kernel": 3}):
         with pytest.raises(p2s.P2SError) as ex:
             p2s.Plan(ctx, wl.orders, 4, p2s.FP64, tile=tile)
         assert ex.value.code == p2s.ERR_ARG
