@@ -85,8 +85,9 @@ def labels_from_errors(err, tol=LABEL_TOL):
 
 
 def train(ctx, feats, labels, epochs=300, batch=512, lr=2e-3, class_weight=None, seed=0, params=None,
-          log_every=0, weight_decay=0.0):
-    """Adam training with the library's gradient and update kernels; returns FP32 params (numpy)."""
+          log_every=0, weight_decay=0.0, cosine=False):
+    """Adam training with the library's gradient and update kernels; returns FP32 params (numpy).
+    With ``cosine`` the step size follows a cosine from lr down to lr / 20 over the epochs."""
     torch = _torch()
     dev = feats.device
     P = torch.as_tensor(init_params(seed) if params is None else params, dtype=torch.float32, device=dev).clone()
@@ -105,11 +106,12 @@ def train(ctx, feats, labels, epochs=300, batch=512, lr=2e-3, class_weight=None,
         Xp = feats[perm].contiguous()
         yp = y[perm].contiguous()
         tot = 0.0
+        lr_ep = lr * (0.05 + 0.95 * 0.5 * (1.0 + np.cos(np.pi * ep / epochs))) if cosine else lr
         for b0 in range(0, n, batch):
             xb, yb = Xp[b0:b0 + batch], yp[b0:b0 + batch]
             p2s.mlp_grad(ctx, P, xb, yb, g, loss, cw)
             step += 1
-            p2s.mlp_adam(P, g, m, v, lr, step, weight_decay=weight_decay)
+            p2s.mlp_adam(P, g, m, v, lr_ep, step, weight_decay=weight_decay)
             tot += float(loss.item()) * xb.shape[0]
         history.append(tot / n)
         if log_every and (ep % log_every == 0 or ep == epochs - 1):
@@ -147,7 +149,8 @@ def balanced_weights(y):
     return np.clip(w, 0.5, 10.0).astype(np.float32)
 
 
-def train_default(ctx, n_train=65536, epochs=60, seed=0, verbose=False, shards=(0, 2, 3, 4), balance=False):
+def train_default(ctx, n_train=65536, epochs=60, seed=0, verbose=False, shards=(0, 2, 3, 4), balance=False,
+                  cosine=False):
     """Labels on the seeded training sets (the c5 recipe with its own seed: shards of
     c5train, shard 1 excluded as the held-out set) and a trained network."""
     torch = _torch()
@@ -163,10 +166,11 @@ def train_default(ctx, n_train=65536, epochs=60, seed=0, verbose=False, shards=(
     X = torch.cat(Xs)
     cw = balanced_weights(y) if balance else None
     params, hist = train(ctx, X, y, epochs=epochs, batch=1024, lr=2e-3, seed=seed, log_every=20 if verbose else 0,
-                         weight_decay=1e-3, class_weight=cw)
+                         weight_decay=1e-3, class_weight=cw, cosine=cosine)
     t2 = time.time()
     pred = classes_of(predict(ctx, params, X))
-    meta = {"n_train": int(y.size), "shards": list(shards), "epochs": int(epochs), "label_tol": LABEL_TOL,
+    meta = {"n_train": int(y.size), "shards": list(shards), "epochs": int(epochs), "cosine": bool(cosine),
+            "label_tol": LABEL_TOL,
             "class_weight": None if cw is None else cw.tolist(),
             "label_hist": np.bincount(y, minlength=6).tolist(), "train_acc": float((pred == y).mean()),
             "train_under": float((pred < y).mean()), "final_loss": float(hist[-1]),
@@ -232,6 +236,16 @@ def calibrate_risk(ctx, params, n_elem=32768, tol=1e-8, sweep=RISK_SWEEP):
                   "held-out elements above tol", "sweep": table, "above_tol_at_risk": detail}
 
 
+def evaluate(ctx, params, risk, shard=9, n_elem=32768, tol=1e-8):
+    """The learned rule (judge off) on another held-out batch of the training recipe: the
+    number of elements above `tol` of their 48-point FP64 fill, the worst error and the
+    mean G^3 (points per element)."""
+    wl = W.make("c5train", n_elem, shard=shard)
+    e, g, _ = learned_errors(ctx, params, wl, risk)
+    return {"shard": shard, "n_elem": n_elem, "risk": risk, "above_tol": int((e > tol).sum()),
+            "max_err": float(e.max()), "mean_G3": float(np.mean(g.astype(float) ** 3))}
+
+
 def ensure_trained(ctx, path=CHECKPOINT, verbose=False):
     """Load the committed checkpoint, or train one and save it."""
     if os.path.exists(path):
@@ -251,17 +265,23 @@ if __name__ == "__main__":
         save(rest[0] if rest else CHECKPOINT, params, meta)
         print(json.dumps(meta))
         sys.exit(0)
-    # python -m paper_1703_09619_gb300.learned [--shards 0,2,3,4] [--balance] [out.npz]
+    # python -m paper_1703_09619_gb300.learned [--shards 0,2,3,4] [--epochs 60] [--cosine] [--balance] [out.npz]
     args = sys.argv[1:]
     shards = (0, 2, 3, 4)
     if "--shards" in args:
         i = args.index("--shards")
         shards = tuple(int(v) for v in args[i + 1].split(","))
         del args[i:i + 2]
-    balance = "--balance" in args
-    args = [a for a in args if a != "--balance"]
-    params, meta = train_default(ctx, verbose=True, shards=shards, balance=balance)
+    epochs = 60
+    if "--epochs" in args:
+        i = args.index("--epochs")
+        epochs = int(args[i + 1])
+        del args[i:i + 2]
+    balance, cosine = "--balance" in args, "--cosine" in args
+    args = [a for a in args if a not in ("--balance", "--cosine")]
+    params, meta = train_default(ctx, verbose=True, shards=shards, balance=balance, epochs=epochs, cosine=cosine)
     meta["risk"], meta["risk_calibration"] = calibrate_risk(ctx, params)
+    meta["evaluation"] = evaluate(ctx, params, meta["risk"])
     out = args[0] if args else CHECKPOINT
     save(out, params, meta)
     print(json.dumps(meta))
