@@ -48,18 +48,15 @@ ALPHA_FLOP_PER_POINT = 134
 # counted as the FP32 instructions that the double-word algorithms need per operation of the
 # method (an FMA counts once):
 #   one multiply-accumulate into the lazy accumulator: 12;
-#   the metric coupling factor at one point, with the _fast double-word operations (add 11,
-#   product 4, fused 15, division 11): 839 (Jacobian from row constants 241, phase 30,
-#   sin 110 + scale 14, cofactors 171, det 34, division 11, six products 228);
+#   the metric coupling factor at one point, with the _fast and _lazy double-word operations
+#   (sum 11, sum without renormalisation 8, product 4, fused 15 / 12, division 11): 725
+#   (Jacobian from row constants 196, phase 30, sin 110 + scale 14, cofactors 144, det 28,
+#   division 11, six products 192);
 #   the scalar coupling factor at one point: 14;
 #   the parity fold of the first mode product, per point and pair: one sum (11) and two
 #   shuffles; the first mode product then runs over ceil(G/2) points per row.
 FP32_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12  # FP32 issue slots (lane operations / s), unit counts
-# DRAM bytes (read + write) per element of the double-word moment kernel, from the full-size
-# ncu capture of the c5 learned fill (profiles/c5_learned_dram_full_size.md): 496,681,216
-# bytes for the 32,768-element launch.  It scales with elements (inputs in, moments out).
-MOMENTS_DW_DRAM_BYTES_PER_ELEMENT = 496681216 / 32768
-DW_MAC_OPS, DW_ALPHA_OPS_METRIC, DW_ALPHA_OPS_SCALAR, DW_FOLD_OPS = 12, 839, 14, 13
+DW_MAC_OPS, DW_ALPHA_OPS_METRIC, DW_ALPHA_OPS_SCALAR, DW_FOLD_OPS = 12, 725, 14, 13
 # Learned-fill settings: judge share and tolerance.  The class rule's risk comes from the
 # checkpoint's metadata, where `python -m paper_1703_09619_gb300.learned --calibrate` keeps the
 # largest risk of its sweep whose held-out elements (shard 1 of the training recipe, neither
@@ -469,11 +466,11 @@ def roofline_for(wl, npts, prec, mom_ms, con_ms, peaks, src, kernel=0):
         iss = ops / (mom_ms * 1e-3) / 1e12
         fp32 = 2 * fp32_issue_peak()
         bf16 = peaks["bf16_tflops"]
-        traffic = MOMENTS_DW_DRAM_BYTES_PER_ELEMENT * wl.n_elem if metric and (wl.orders == 4).all() else None
         return {"bound": "tensor", "kernel": "k_moments_dw", "achieved": ach, "peak": bf16, "unit": "TFLOP/s",
-                "frac": ach / bf16, "traffic": traffic,
-                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per element of a 1024-element "
-                                   "c5 capture, scaled to the launch's elements") if traffic else None,
+                "frac": ach / bf16, "traffic": None,
+                "traffic_note": "not scalable from a capture of the allowed size: at 1024 elements the moments stay "
+                                "in L2 for the contraction (0.45 MB read, 0 written); the full launch writes its "
+                                "moments (16.5 KB per element) to DRAM",
                 "peak_source": "%s BF16 dense burst (MEASURED_PEAKS.json)" % src,
                 "algorithmic_flop_per_launch": int(flop), "flop_model": model,
                 "vs_fp32_fma": {"peak": fp32, "frac": ach / fp32, "unit": "TFLOP/s",
