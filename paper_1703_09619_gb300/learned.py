@@ -169,7 +169,7 @@ def train_default(ctx, n_train=65536, epochs=60, seed=0, verbose=False, shards=(
                          weight_decay=1e-3, class_weight=cw, cosine=cosine)
     t2 = time.time()
     pred = classes_of(predict(ctx, params, X))
-    meta = {"n_train": int(y.size), "shards": list(shards), "epochs": int(epochs), "cosine": bool(cosine),
+    meta = {"n_train": int(y.size), "shards": list(shards), "epochs": int(epochs), "cosine": bool(cosine), "seed": seed,
             "label_tol": LABEL_TOL,
             "class_weight": None if cw is None else cw.tolist(),
             "label_hist": np.bincount(y, minlength=6).tolist(), "train_acc": float((pred == y).mean()),
@@ -270,21 +270,27 @@ if __name__ == "__main__":
         save(rest[0] if rest else CHECKPOINT, params, meta)
         print(json.dumps(meta))
         sys.exit(0)
-    # python -m paper_1703_09619_gb300.learned [--shards 0,2,3,4] [--epochs 60] [--cosine] [--balance] [out.npz]
+    # python -m paper_1703_09619_gb300.learned [--shards 0,2,3,4] [--epochs 60] [--cosine] [--balance] [--seed 0]
+    #                                          [out.npz]
     args = sys.argv[1:]
     shards = (0, 2, 3, 4)
     if "--shards" in args:
         i = args.index("--shards")
         shards = tuple(int(v) for v in args[i + 1].split(","))
         del args[i:i + 2]
-    epochs = 60
+    epochs, seed = 60, 0
     if "--epochs" in args:
         i = args.index("--epochs")
         epochs = int(args[i + 1])
         del args[i:i + 2]
+    if "--seed" in args:
+        i = args.index("--seed")
+        seed = int(args[i + 1])
+        del args[i:i + 2]
     balance, cosine = "--balance" in args, "--cosine" in args
     args = [a for a in args if a not in ("--balance", "--cosine")]
-    params, meta = train_default(ctx, verbose=True, shards=shards, balance=balance, epochs=epochs, cosine=cosine)
+    params, meta = train_default(ctx, verbose=True, shards=shards, balance=balance, epochs=epochs, cosine=cosine,
+                                 seed=seed)
     meta["risk"], meta["risk_calibration"] = calibrate_risk(ctx, params)
     meta["evaluation"] = evaluate(ctx, params, meta["risk"])
     out = args[0] if args else CHECKPOINT
