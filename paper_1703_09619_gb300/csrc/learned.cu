@@ -352,68 +352,74 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
 }
 
 // ------------------------------------------------------------------ per-element errors
-// One element per CTA of 256 threads; per type 16-byte loads (when both segments allow them)
-// four deep per thread, maxima reduced by warp shuffles.
+// One (element, type) per CTA of 256 threads, so that a few hundred judged elements still
+// spread over every SM; 16-byte loads (when both segments allow them) four deep per thread,
+// maxima reduced by warp shuffles.
 __global__ void __launch_bounds__(256) k_elem_err(const double* __restrict__ a, const int64_t* __restrict__ offa,
                                                   const double* __restrict__ b, const int64_t* __restrict__ offb,
                                                   int64_t E, int n_types, double* __restrict__ err) {
+    // err[e] (zeroed by the launcher) takes the largest ratio of its types by an atomic
+    // maximum on the bit patterns (non-negative doubles order as their bits)
     __shared__ double sd[8], sm[8];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+    for (int64_t it = blockIdx.x; it < E * n_types; it += gridDim.x) {
+        const int64_t e = it / n_types;
+        const int t = (int)(it - e * n_types);
         const int64_t len = (offb[e + 1] - offb[e]) / n_types;
-        double worst = 0.0;
-        for (int t = 0; t < n_types; ++t) {
-            const double* pa = a + offa[e] + t * len;
-            const double* pb = b + offb[e] + t * len;
-            double d = 0.0, m = 0.0;
-            if (((reinterpret_cast<uintptr_t>(pa) | reinterpret_cast<uintptr_t>(pb)) & 15) == 0) {
-                const double2* qa = reinterpret_cast<const double2*>(pa);
-                const double2* qb = reinterpret_cast<const double2*>(pb);
-                const int64_t n2 = len / 2;
-                int64_t i = tid;
-                for (; i + 768 < n2; i += 1024) {
-                    double2 va[4], vb[4];
+        const double* pa = a + offa[e] + t * len;
+        const double* pb = b + offb[e] + t * len;
+        double d = 0.0, m = 0.0;
+        if (((reinterpret_cast<uintptr_t>(pa) | reinterpret_cast<uintptr_t>(pb)) & 15) == 0) {
+            const double2* qa = reinterpret_cast<const double2*>(pa);
+            const double2* qb = reinterpret_cast<const double2*>(pb);
+            const int64_t n2 = len / 2;
+            int64_t i = tid;
+            for (; i + 768 < n2; i += 1024) {
+                double2 va[4], vb[4];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        va[j] = __ldcs(qa + i + 256 * j);
-                        vb[j] = __ldcs(qb + i + 256 * j);
-                    }
+                for (int j = 0; j < 4; ++j) {
+                    va[j] = __ldcs(qa + i + 256 * j);
+                    vb[j] = __ldcs(qb + i + 256 * j);
+                }
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        d = fmax(d, fmax(fabs(va[j].x - vb[j].x), fabs(va[j].y - vb[j].y)));
-                        m = fmax(m, fmax(fabs(vb[j].x), fabs(vb[j].y)));
-                    }
-                }
-                for (; i < n2; i += 256) {
-                    const double2 va = __ldcs(qa + i), vb = __ldcs(qb + i);
-                    d = fmax(d, fmax(fabs(va.x - vb.x), fabs(va.y - vb.y)));
-                    m = fmax(m, fmax(fabs(vb.x), fabs(vb.y)));
-                }
-                if ((len & 1) && tid == 0) {
-                    d = fmax(d, fabs(pa[len - 1] - pb[len - 1]));
-                    m = fmax(m, fabs(pb[len - 1]));
-                }
-            } else {
-                for (int64_t i = tid; i < len; i += 256) {
-                    d = fmax(d, fabs(pa[i] - pb[i]));
-                    m = fmax(m, fabs(pb[i]));
+                for (int j = 0; j < 4; ++j) {
+                    d = fmax(d, fmax(fabs(va[j].x - vb[j].x), fabs(va[j].y - vb[j].y)));
+                    m = fmax(m, fmax(fabs(vb[j].x), fabs(vb[j].y)));
                 }
             }
-            d = warp_max_d(d);
-            m = warp_max_d(m);
-            if (lane == 0) {
-                sd[warp] = d;
-                sm[warp] = m;
+            for (; i < n2; i += 256) {
+                const double2 va = __ldcs(qa + i), vb = __ldcs(qb + i);
+                d = fmax(d, fmax(fabs(va.x - vb.x), fabs(va.y - vb.y)));
+                m = fmax(m, fmax(fabs(vb.x), fabs(vb.y)));
             }
-            __syncthreads();
-            if (warp == 0) {
-                d = warp_max_d(lane < 8 ? sd[lane] : 0.0);
-                m = warp_max_d(lane < 8 ? sm[lane] : 0.0);
-                worst = fmax(worst, m > 0.0 ? d / m : d);
+            if ((len & 1) && tid == 0) {
+                d = fmax(d, fabs(pa[len - 1] - pb[len - 1]));
+                m = fmax(m, fabs(pb[len - 1]));
             }
-            __syncthreads();
+        } else {
+            for (int64_t i = tid; i < len; i += 256) {
+                d = fmax(d, fabs(pa[i] - pb[i]));
+                m = fmax(m, fabs(pb[i]));
+            }
         }
-        if (tid == 0) err[e] = worst;
+        d = warp_max_d(d);
+        m = warp_max_d(m);
+        if (lane == 0) {
+            sd[warp] = d;
+            sm[warp] = m;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            d = 0.0;
+            m = 0.0;
+            for (int w = 0; w < 8; ++w) {
+                d = fmax(d, sd[w]);
+                m = fmax(m, sm[w]);
+            }
+            const double r = m > 0.0 ? d / m : d;
+            atomicMax(reinterpret_cast<unsigned long long*>(err + e), (unsigned long long)__double_as_longlong(r));
+        }
+        __syncthreads();
     }
 }
 
@@ -512,7 +518,8 @@ int p2s_element_errors(p2s_ctx* ctx, const double* a, const int64_t* offsets_a, 
     if (n_elem == 0) return P2S_OK;
     if (!a || !b || !offsets_a || !offsets_b || !err) return fail(P2S_ERR_ARG, "p2s_element_errors: NULL array");
     P2S_LCUDA(cudaSetDevice(T->device));
-    const int grid = (int)std::min<int64_t>(n_elem, (int64_t)T->sm_count * 8);
+    const int grid = (int)std::min<int64_t>(n_elem * n_types, (int64_t)T->sm_count * 8);
+    P2S_LCUDA(cudaMemsetAsync(err, 0, sizeof(double) * n_elem, (cudaStream_t)stream));
     k_elem_err<<<grid, 256, 0, (cudaStream_t)stream>>>(a, offsets_a, b, offsets_b, n_elem, n_types, err);
     P2S_LCUDA(cudaGetLastError());
     return P2S_OK;
