@@ -205,6 +205,13 @@ def learned_errors(ctx, params, wl, risk, margin=0, ref=None, device="cuda"):
     return e, g, ref
 
 
+def choose_risk(table):
+    """The largest risk among the sweep entries with the fewest held-out elements above the
+    calibration tolerance (`table`: dicts with "risk" and "above_tol")."""
+    fewest = min(t["above_tol"] for t in table)
+    return max(t["risk"] for t in table if t["above_tol"] == fewest)
+
+
 CALIBRATION_TOL = 5e-9  # half the fill's 1e-8 bar: a held-out sample of finite size, a safety factor of 2
 
 
@@ -226,8 +233,7 @@ def calibrate_risk(ctx, params, n_elem=32768, tol=CALIBRATION_TOL, sweep=RISK_SW
         table.append({"risk": r, "max_err": float(e.max()), "above_tol": int((e > tol).sum()),
                       "mean_G3": float(np.mean(g.astype(float) ** 3))})
         fails[r] = [(int(i), int(g[i]), float(e[i])) for i in np.flatnonzero(e > tol)]
-    fewest = min(t["above_tol"] for t in table)
-    risk = max(t["risk"] for t in table if t["above_tol"] == fewest)
+    risk = choose_risk(table)
     del ref
     detail = []
     if fails[risk]:

@@ -1,0 +1,45 @@
+"""Host logic of the learned order (no GPU): the risk rule's choice over a calibration sweep,
+the class weights and the class lookup."""
+import numpy as np
+
+from paper_1703_09619_gb300 import learned as LN
+
+
+def sweep(*rows):
+    return [{"risk": r, "above_tol": n, "max_err": 0.0, "mean_G3": 0.0} for r, n in rows]
+
+
+def test_choose_risk_takes_the_largest_risk_without_failures():
+    assert LN.choose_risk(sweep((0.05, 7), (0.02, 2), (0.01, 0), (0.005, 0), (0.001, 0))) == 0.01
+
+
+def test_choose_risk_when_no_risk_is_clean_keeps_the_fewest_failures():
+    # a confident mistake that no risk removes: the largest risk with that one failure
+    assert LN.choose_risk(sweep((0.05, 8), (0.02, 2), (0.01, 1), (0.002, 1), (0.0001, 1))) == 0.01
+
+
+def test_choose_risk_ignores_sweep_order():
+    t = sweep((0.001, 0), (0.05, 3), (0.002, 0), (0.01, 1))
+    assert LN.choose_risk(t) == 0.002
+    assert LN.choose_risk(list(reversed(t))) == 0.002
+
+
+def test_balanced_weights_favour_rare_classes_within_bounds():
+    y = np.array([1] * 1000 + [2] * 4000 + [3] * 1500 + [4] * 20)
+    w = LN.balanced_weights(y)
+    assert w.shape == (6,) and np.all(w >= 0.5) and np.all(w <= 10.0)
+    assert w[4] > w[3] > w[2] and w[1] > w[2]
+    assert w[0] == 10.0 and w[5] == 10.0  # classes without samples take the cap
+
+
+def test_classes_of_inverts_the_class_table():
+    assert LN.classes_of(np.array(LN.CLASS_NPTS)).tolist() == list(range(6))
+
+
+def test_committed_checkpoint_carries_its_calibration():
+    P, meta = LN.load_checkpoint()
+    assert P.shape == (41478,)
+    cal = meta["risk_calibration"]
+    assert meta["risk"] == LN.choose_risk(cal["sweep"])
+    assert cal["tol"] <= 1e-8 and "shard 1" in cal["holdout"]
+    assert meta["evaluation"]["above_tol"] == 0
