@@ -69,14 +69,11 @@ __device__ __forceinline__ size_t ffb_moments(const ContractLaunch& L, const Con
     return (size_t)d->mom_off + d->pair_off[pair_index(u.gi, u.gj, d->n_comp)];
 }
 
-// Stage 1 of one unit (any type): items (im1, m2, l, q),
-//   A[im1][m2][l][q] = sum_k C[m1,m2,k] I[k][l][q],
-// with (m1, m2) run-time values: the run from its closed form, the coefficients from the
-// CTA's shared copy of the run table (sC[t][a][b][r], the values of the constant-memory
-// table, so no global load waits in the item loop).
+// Stage 1 of one unit (any type; runs from the table): items (im1, m2, l, q),
+//   A[im1][m2][l][q] = sum_k C[m1,m2,k] I[k][l][q].
 template <class A>
-__device__ __forceinline__ void ffb_stage1(int t, const typename A::T* __restrict__ sI, typename A::T* __restrict__ sA,
-                                           const typename A::C* __restrict__ sC, const FfbShape& s, int m1a, int m1n,
+__device__ __forceinline__ void ffb_stage1(const ContractLaunch& L, int t, const typename A::T* __restrict__ sI,
+                                           typename A::T* __restrict__ sA, const FfbShape& s, int m1a, int m1n,
                                            int tid, int nth) {
     using T = typename A::T;
     const int KvKw = s.Kv * s.Kw;
@@ -85,12 +82,11 @@ __device__ __forceinline__ void ffb_stage1(int t, const typename A::T* __restric
     for (int it = tid; it < items; it += nth) {
         const int mm = div_small(it, KvKw, rKvKw), lq = it - mm * KvKw;
         const int im1 = div_small(mm, s.Nu_j, rNuj), m2 = mm - im1 * s.Nu_j;
-        const int m1 = m1a + im1;
-        const int k0 = run_kmin(t, m1, m2), cnt = run_cnt(t, m1, m2);
-        const typename A::C* cf = sC + ((t * kSpec + m1) * kSpec + m2) * kSpec;
+        const int32_t li = __ldg(L.lin_idx + lin_slot(t, m1a + im1, m2));
+        const int k0 = lin_kmin(li), cnt = lin_cnt(li), off = lin_off(li);
         const T* Ik = sI + k0 * KvKw + lq;
-        T acc = cnt > 0 ? A::mul(cf[0], Ik[0]) : A::zero();
-        for (int r = 1; r < cnt; ++r) A::fma_acc(acc, cf[r], Ik[2 * r * KvKw]);
+        T acc = cnt > 0 ? A::mul(A::load_coef(L.lin_coef, off), Ik[0]) : A::zero();
+        for (int r = 1; r < cnt; ++r) A::fma_acc(acc, A::load_coef(L.lin_coef, off + r), Ik[2 * r * KvKw]);
         sA[it] = A::finish(acc);
     }
 }
@@ -242,12 +238,7 @@ __global__ void __launch_bounds__(512) k_contract_ffb(ContractLaunch L) {
     T* sA = sI + L.a_cap;                  // stage 1, [im1][m2][l][q]
     T* sB = sA + L.s1_cap;                 // stage 2, [combination][q] (odd stride)
     __shared__ ContractUnit s_u[3];        // e = -1: no unit
-    __shared__ typename A::C sC[4 * kSpec * kSpec * kSpec];  // the run table, for stage 1
     const int tid = threadIdx.x, nth = blockDim.x;
-    for (int i = tid; i < 4 * kSpec * kSpec * kSpec; i += nth) {
-        const int r = i % kSpec, b = (i / kSpec) % kSpec, a = (i / (kSpec * kSpec)) % kSpec, tt = i / (kSpec * kSpec * kSpec);
-        sC[i] = run_coef<A>(tt, a, b, r);
-    }
     const unsigned long long nu = (unsigned long long)L.n_units;
     auto fetch = [&](ContractUnit& slot) {
         ContractUnit none{};
@@ -258,7 +249,7 @@ __global__ void __launch_bounds__(512) k_contract_ffb(ContractLaunch L) {
     auto skipped = [&](const ContractUnit& u) { return L.elem_mask && !L.elem_mask[u.e]; };
     auto stage1 = [&](const ContractUnit& u) {
         const ElemDesc* d = L.desc + u.e;
-        ffb_stage1<A>(u.t, sI, sA, sC, ffb_shape(d, u.gi, u.gj), u.m1a, u.m1n, tid, nth);
+        ffb_stage1<A>(L, u.t, sI, sA, ffb_shape(d, u.gi, u.gj), u.m1a, u.m1n, tid, nth);
     };
 
     if (tid == 0) {
