@@ -17,8 +17,10 @@
 //         are dropped: the relative error is about 2^(-8S) of max|B| max|x| per term.
 //
 // One CTA of 128 threads takes tiles of 128 rows (one row per thread, TMEM lane = row);
-// thread 0 issues the MMAs and commits them to an mbarrier that every thread waits on
-// (bounded by a clock budget: on expiry the kernel sets an error flag and leaves the tile).
+// the B images reach shared memory once per CTA by a bulk asynchronous copy (TMA) that
+// completes on an mbarrier; thread 0 issues the MMAs and commits them to a second mbarrier
+// that every thread waits on (each wait bounded by a clock budget: on expiry the kernel sets
+// an error flag and leaves its tiles).
 // Operands live in shared memory in the no-swizzle K-major layout: 8 x 16-byte core
 // matrices, k-adjacent core matrices 128 B apart (LBO), 8-row groups KA/8 x 128 B apart
 // (SBO).  Rows x come from a source array of n_src rows, row r reading source row r mod
@@ -208,14 +210,23 @@ __global__ void __launch_bounds__(kM1Threads) k_mode1_tc(const float2* __restric
     __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5;
 
-    // B images (host-built, K-major layout) into shared memory; zero A (its padding stays 0)
-    for (int i = tid; i < (kNE + kNO) * KA * 2 / 16; i += kM1Threads)
-        reinterpret_cast<uint4*>(sBE)[i] = reinterpret_cast<const uint4*>(g_m1_bimg)[i];
+    // zero A (its padding stays 0); the B images (host-built, K-major layout) arrive by one
+    // bulk asynchronous copy (TMA, untiled) completing on s_tma
     for (int i = tid; i < 2 * 128 * KA * 2 / 16; i += kM1Threads) reinterpret_cast<uint4*>(sAE)[i] = make_uint4(0, 0, 0, 0);
+    __shared__ __align__(8) unsigned long long s_tma;
+    constexpr uint32_t kBBytes = (kNE + kNO) * KA * 2;  // a multiple of 16 (KA is)
     if (tid == 0) {
         s_fail = 0;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_tma)));
         asm volatile("fence.mbarrier_init.release.cluster;");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&s_tma)), "r"(kBBytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(sBE)),
+            "l"(reinterpret_cast<uint64_t>(g_m1_bimg)), "r"(kBBytes), "r"(smem_u32(&s_tma))
+            : "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
@@ -227,14 +238,19 @@ __global__ void __launch_bounds__(kM1Threads) k_mode1_tc(const float2* __restric
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = s_tmem, tE = tmem, tO = tmem + kNE;
     const uint32_t bar = smem_u32(&s_bar);
+    const long long budget = 2000000000ll;  // about a second at the running clock
+    if (!mbar_wait(smem_u32(&s_tma), 0, budget)) {  // the B images in place
+        if (tid == 0) atomicExch(err, P2S_ERR_TIMEOUT);
+        s_fail = 1;
+    }
+    __syncthreads();
     const uint32_t sbo = (KA / 8) * 128;
     const uint32_t aE = smem_u32(sAE), aO = smem_u32(sAO), bE = smem_u32(sBE), bO = smem_u32(sBO);
     constexpr uint32_t idE = idesc_f16(128, kNE), idO = idesc_f16(128, kNO);
-    const long long budget = 2000000000ll;  // about a second at the running clock
 
     const int64_t tiles = (n_rows + 127) / 128;
     uint32_t phase = 0;
-    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    for (int64_t t = s_fail ? tiles : blockIdx.x; t < tiles; t += gridDim.x) {
         const int64_t r = t * 128 + tid;
         const bool live = r < n_rows;
         stage_tile<G>(x, n_rows, n_src, t, sX);
