@@ -150,7 +150,7 @@ def balanced_weights(y):
 
 
 def train_default(ctx, n_train=65536, epochs=60, seed=0, verbose=False, shards=(0, 2, 3, 4), balance=False,
-                  cosine=False):
+                  cosine=False, batch=1024, lr=2e-3, weight_decay=1e-3):
     """Labels on the seeded training sets (the c5 recipe with its own seed: shards of
     c5train, shard 1 excluded as the held-out set) and a trained network."""
     torch = _torch()
@@ -165,11 +165,12 @@ def train_default(ctx, n_train=65536, epochs=60, seed=0, verbose=False, shards=(
     t1 = time.time()
     X = torch.cat(Xs)
     cw = balanced_weights(y) if balance else None
-    params, hist = train(ctx, X, y, epochs=epochs, batch=1024, lr=2e-3, seed=seed, log_every=20 if verbose else 0,
-                         weight_decay=1e-3, class_weight=cw, cosine=cosine)
+    params, hist = train(ctx, X, y, epochs=epochs, batch=batch, lr=lr, seed=seed, log_every=20 if verbose else 0,
+                         weight_decay=weight_decay, class_weight=cw, cosine=cosine)
     t2 = time.time()
     pred = classes_of(predict(ctx, params, X))
     meta = {"n_train": int(y.size), "shards": list(shards), "epochs": int(epochs), "cosine": bool(cosine), "seed": seed,
+            "batch": batch, "lr": lr, "weight_decay": weight_decay,
             "label_tol": LABEL_TOL,
             "class_weight": None if cw is None else cw.tolist(),
             "label_hist": np.bincount(y, minlength=6).tolist(), "train_acc": float((pred == y).mean()),
@@ -277,7 +278,7 @@ if __name__ == "__main__":
         print(json.dumps(meta))
         sys.exit(0)
     # python -m paper_1703_09619_gb300.learned [--shards 0,2,3,4] [--epochs 60] [--cosine] [--balance] [--seed 0]
-    #                                          [out.npz]
+    #                                          [--batch 1024] [--lr 2e-3] [--wd 1e-3] [out.npz]
     args = sys.argv[1:]
     shards = (0, 2, 3, 4)
     if "--shards" in args:
@@ -293,10 +294,16 @@ if __name__ == "__main__":
         i = args.index("--seed")
         seed = int(args[i + 1])
         del args[i:i + 2]
+    extra = {}
+    for flag, key, conv in (("--batch", "batch", int), ("--lr", "lr", float), ("--wd", "weight_decay", float)):
+        if flag in args:
+            i = args.index(flag)
+            extra[key] = conv(args[i + 1])
+            del args[i:i + 2]
     balance, cosine = "--balance" in args, "--cosine" in args
     args = [a for a in args if a not in ("--balance", "--cosine")]
     params, meta = train_default(ctx, verbose=True, shards=shards, balance=balance, epochs=epochs, cosine=cosine,
-                                 seed=seed)
+                                 seed=seed, **extra)
     meta["risk"], meta["risk_calibration"] = calibrate_risk(ctx, params)
     meta["evaluation"] = evaluate(ctx, params, meta["risk"])
     out = args[0] if args else CHECKPOINT
