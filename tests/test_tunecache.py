@@ -41,3 +41,15 @@ def test_tuned_tile_tunes_once_then_hits(tmp_path, monkeypatch):
     assert info2["cache"] == "hit" and len(calls) == 1 and tile2 == tile
     d = json.loads(path.read_text())
     assert d[key]["tile"]["kernel"] == 2 and d[key]["candidates"] == 40
+
+
+def test_shipped_table_is_valid():
+    """The shipped picks parse and name tile shapes the library accepts."""
+    d = json.loads(open(TC.SHIPPED).read())
+    assert d
+    for key, e in d.items():
+        assert key.count("|") == 5 and key.split("|")[1] in ("p0", "p1")
+        t = e["tile"]
+        assert 0 <= t["combo_target"] <= 4096 and 0 <= t["unit_kbytes"] <= 227
+        assert t["threads"] == 0 or (64 <= t["threads"] <= 512 and t["threads"] % 32 == 0)
+        assert t["kernel"] in (0, 1, 2)
