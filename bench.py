@@ -609,7 +609,10 @@ def run_learned(args, wl):
             "stages": {"moments_ms": mom_ms, "contract_ms": con_ms,
                        "learned_other_ms": total_ms / args.steps - mom_ms - con_ms},
             "clocks": clocks,
-            "gpu_launches": 10 * args.steps,
+            # per learned fill (launch list): gather, judge moments + contraction, features, predict,
+            # set_npts, order_by_class, main moments + contraction, elem_err, judge_mask, fallback
+            # moments + contraction (masked), judge_fix
+            "gpu_launches": 14 * args.steps,
         }
         if e2e:
             line["e2e"] = e2e
