@@ -21,7 +21,8 @@
 #include <cstring>
 #include <vector>
 
-#include "alpha.cuh"
+#include "alpha_dw.cuh"
+#include "dw.cuh"
 #include "p2s_internal.h"
 
 namespace p2s {
@@ -51,10 +52,12 @@ __device__ __forceinline__ double warp_max_d(double v) {
     return v;
 }
 
-// Four elements per CTA, 64 threads (one coarse point each) per element.  The cosines and
-// sines of the four positions are computed once per CTA; the element constants (the geo[]
-// layout of alpha.cuh) by 27 threads of each element, one trilinear coefficient or bulge
-// entry each, then the phase coefficients by 10; the trace mean by warp shuffles.
+// Four elements per CTA, 64 threads (one coarse point each) per element.  The element
+// constants (the geo[] layout of alpha.cuh) are formed in FP64 by 27 threads of each element,
+// one trilinear coefficient or bulge entry each, then the phase coefficients by 10, and
+// split into double words; each thread then forms its point's row and plane constants and
+// the coupling factor in double words (alpha_dw.cuh, the moment kernel's arithmetic) on the
+// FP32 pipe; the trace mean by warp shuffles in FP64.
 constexpr int kFeatElems = 4;
 __global__ void __launch_bounds__(64 * kFeatElems) k_features(const double* __restrict__ nodes,
                                                                const double* __restrict__ bulge,
@@ -62,10 +65,17 @@ __global__ void __launch_bounds__(64 * kFeatElems) k_features(const double* __re
                                                                float* __restrict__ feat, int32_t* __restrict__ bad) {
     const double* x4 = c_coarse_x;
     __shared__ double geo[kFeatElems][48];
+    __shared__ dw geo_dw[kFeatElems][40];
     __shared__ double half_tr[kFeatElems][2];
-    __shared__ double cs4[4], sn4[4];
+    __shared__ dw xq[4], cs4[4], dc4[4];  // positions, cos(pi x / 2), d/dx cos(pi x / 2)
     const int sub = threadIdx.x >> 6, p = threadIdx.x & 63, warp = p >> 5, lane = p & 31;
-    if (threadIdx.x < 4) sincos(1.5707963267948966 * x4[threadIdx.x], &sn4[threadIdx.x], &cs4[threadIdx.x]);
+    if (threadIdx.x < 4) {
+        double sx, cx;
+        sincos(1.5707963267948966 * x4[threadIdx.x], &sx, &cx);
+        xq[threadIdx.x] = dw_from_double(x4[threadIdx.x]);
+        cs4[threadIdx.x] = dw_from_double(cx);
+        dc4[threadIdx.x] = dw_from_double(-1.5707963267948966 * sx);
+    }
     for (int64_t e0 = (int64_t)blockIdx.x * kFeatElems; e0 < E; e0 += (int64_t)gridDim.x * kFeatElems) {
         const int64_t e = e0 + sub;
         const bool on = e < E;
@@ -93,11 +103,35 @@ __global__ void __launch_bounds__(64 * kFeatElems) k_features(const double* __re
             else geo[sub][27] = pr[0];
         }
         __syncthreads();
+        if (on && p < 40) geo_dw[sub][p] = dw_from_double(p < 28 || p >= 31 ? geo[sub][p] : 0.0);
+        __syncthreads();
         const int a = p & 3, b = (p >> 2) & 3, c = p >> 4;
         double K[6] = {0, 0, 0, 0, 0, 0};
         if (on) {
-            const bool ok = metric_alpha(geo[sub], x4[a], x4[b], x4[c], cs4[a], sn4[a], cs4[b], sn4[b], cs4[c], sn4[c], K);
+            // the row constants of (v, w) = (x_b, x_c) and the plane constants of w
+            const dw* cf = geo_dw[sub];
+            const dw v = xq[b], w = xq[c], vw = dw_mul_fast(v, w);
+            dw row[14], plane[6];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const dw* ci = cf + 8 * i;
+                row[i] = dw_fma_fast(ci[7], vw, dw_fma_fast(ci[5], w, dw_fma_fast(ci[4], v, ci[1])));
+                row[3 + i] = dw_fma_fast(ci[6], v, ci[3]);
+                row[6 + i] = dw_fma_fast(ci[7], v, ci[5]);
+                plane[i] = dw_fma_fast(ci[6], w, ci[2]);
+                plane[3 + i] = dw_fma_fast(ci[7], w, ci[4]);
+            }
+            const dw* th = cf + 31;
+            row[9] = dw_fma_fast(th[6], vw, dw_fma_fast(th[3], w, dw_fma_fast(th[2], v, th[0])));
+            row[10] = dw_fma_fast(th[7], vw, dw_fma_fast(th[5], w, dw_fma_fast(th[4], v, th[1])));
+            row[11] = dw_mul_fast(cs4[b], cs4[c]);
+            row[12] = dw_mul_fast(dc4[b], cs4[c]);
+            row[13] = dw_mul_fast(cs4[b], dc4[c]);
+            dw Kd[6];
+            const bool ok = metric_alpha_dw(cf, row, plane, xq[a], cs4[a], dc4[a], Kd);
             if (!ok && bad) bad[e] = 1;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) K[q] = dw_to_double(Kd[q]);
         }
         const double t = warp_sum_d((K[0] + K[3] + K[5]) / 3.0);
         if (lane == 0) half_tr[sub][warp] = t;
