@@ -88,6 +88,15 @@ __device__ __forceinline__ void pair_comps_dw(int s, int n_comp, int& gi, int& g
     gj = tgj[s];
 }
 
+// Rows per chunk: as few chunks per plane as the 256 lanes allow
+// (lr lanes per row), with the rows spread evenly over them (G = 24: 8 + 8 + 8 rather than
+// 10 + 10 + 4; G = 48 keeps 5 rows, as 4 would add two chunks per plane).
+__host__ __device__ constexpr int rows_per_chunk(int G, int lr) {
+    const int cap = kChunk / lr < 1 ? 1 : (kChunk / lr < G ? kChunk / lr : G);
+    const int ncp = (G + cap - 1) / cap;
+    return (G + ncp - 1) / ncp;
+}
+
 // Chunk t of an element: plane c, first row b0, nbc rows.
 struct Chunk {
     int c, b0, nbc;
@@ -159,13 +168,13 @@ __device__ __forceinline__ void element_pipeline(const MomentLaunch& L, const Sm
     const int Kb = kSpec ? KC : max(Ku, max(Kv, Kw));
     constexpr int KCs = kSpec ? KC : 0;
     constexpr int HC = kSpec ? (GC + 1) / 2 : 0, LRC = 2 * HC;
-    constexpr int NBC = kSpec ? (kChunk / LRC < GC ? (kChunk / LRC > 0 ? kChunk / LRC : 1) : GC) : 0;
+    constexpr int NBC = kSpec ? rows_per_chunk(GC, LRC) : 0;
     constexpr int NCPC = kSpec ? (GC + NBC - 1) / NBC : 0;
     const int per_pair = Ku * Kv * Kw;
     const int ppg = kSpec ? 6 : max(1, min(np, L.iacc_cap / per_pair));
     const int H = (G + 1) / 2, LR = 2 * H, Hs = H | 1;  // folded half, lanes per row, row stride
     const float rKu = 1.f / (float)Ku, rKv = 1.f / (float)Kv, rLR = 1.f / (float)LR;
-    const int nb = kSpec ? NBC : max(1, min(G, kChunk / LR));
+    const int nb = kSpec ? NBC : rows_per_chunk(G, LR);
     const int ncp = kSpec ? NCPC : (G + nb - 1) / nb;  // chunks per plane
     const float rncp = 1.f / (float)ncp;
     const int T = G * ncp;

@@ -6,14 +6,22 @@ plane whose last chunk was t-3, on buffers indexed by chunk parity (row constant
 T1) and plane parity (T2).  This test walks the same schedule for every G the library
 accepts and checks that no buffer is written and read by different steps in one interval,
 that every read sees the data of the chunk (or plane) it needs, and that the moments end
-complete.  The chunking is the kernel's: nb = max(1, min(G, 256 // (2 ceil(G/2)))) rows of
-one plane, a lane pair per mirrored pair of points of a row."""
+complete.  The chunking is the kernel's, a lane pair per mirrored pair of points of a row:
+at most cap = max(1, min(G, 256 // (2 ceil(G/2)))) rows of one plane per chunk, as few chunks
+as that allows, the rows spread evenly over them: nb = ceil(G / ceil(G / cap))."""
 import pytest
+
+def rows_cap(G, chunk=256):
+    return max(1, min(G, chunk // (2 * ((G + 1) // 2))))
+
+
+def rows_per_chunk(G, chunk=256):
+    cap = rows_cap(G, chunk)
+    return -(-G // -(-G // cap))
 
 
 def schedule_ok(G, chunk=256):
-    lanes_per_row = 2 * ((G + 1) // 2)
-    nb = max(1, min(G, chunk // lanes_per_row))
+    nb = rows_per_chunk(G, chunk)
     ncp = (G + nb - 1) // nb
     T = G * ncp
     state = {}
@@ -55,3 +63,17 @@ def schedule_ok(G, chunk=256):
 @pytest.mark.parametrize("G", range(1, 65))
 def test_moment_pipeline_schedule(G):
     assert schedule_ok(G)
+
+
+@pytest.mark.parametrize("G", range(1, 65))
+def test_chunks_are_few_even_and_fit(G):
+    # The chunking keeps the fewest chunks per plane that the 256 lanes allow, fits them,
+    # and leaves no chunk emptier than it must: G = 24 gets 8 rows (three full chunks rather
+    # than 10 + 10 + 4), G = 48 keeps 5 (ten chunks, the last of 3 rows).
+    cap, nb = rows_cap(G), rows_per_chunk(G)
+    ncp = -(-G // nb)
+    assert ncp == -(-G // cap) and nb <= cap and nb * 2 * ((G + 1) // 2) <= max(256, 2 * ((G + 1) // 2))
+    assert G - (ncp - 1) * nb >= G - (ncp - 1) * cap
+    assert nb - (G - (ncp - 1) * nb) < ncp  # the last chunk is short by fewer rows than there are chunks
+    if G in (24, 48):
+        assert nb == {24: 8, 48: 5}[G]
