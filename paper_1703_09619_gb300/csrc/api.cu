@@ -397,11 +397,15 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
     auto msmem = [&](int cap) {
         return dwm ? moments_dw_smem_bytes(L.n_pairs, L.kb, L.gmax, cap) : moments_smem_bytes(L.n_pairs, L.kb, L.gmax, cap);
     };
+    // (the double-word kernel's accumulator holds whole pair slots: two pairs each, at least one)
+    const size_t need_min = dwm ? 2 * (size_t)max_pair : (size_t)max_pair;
+    const size_t need_all = dwm ? (size_t)moments_dw_iacc_words(L.n_pairs, max_pair) : (size_t)max_elem_mom;
     size_t base = msmem(0);
-    if (base + sizeof(double) * max_pair > limit) return fail(P2S_ERR_ORDER, "plan: moment accumulator too large");
-    L.iacc_cap = (int)std::min<size_t>((limit - base) / sizeof(double), (size_t)max_elem_mom);
+    if (base + sizeof(double) * need_min > limit) return fail(P2S_ERR_ORDER, "plan: moment accumulator too large");
+    L.iacc_cap = (int)std::min<size_t>((limit - base) / sizeof(double), need_all);
+    if (dwm) L.iacc_cap &= ~1;
     size_t half = limit / 2 - 1024;  // two CTAs per SM when everything fits in half
-    if (base + sizeof(double) * max_elem_mom <= half) L.iacc_cap = max_elem_mom;
+    if (base + sizeof(double) * need_all <= half) L.iacc_cap = (int)need_all;
     L.mom_smem = msmem(L.iacc_cap);
     int per_sm = dwm ? moments_dw_blocks_per_sm(L.mom_smem) : moments_blocks_per_sm(L.mom_smem);
     if (per_sm < 1) return fail(P2S_ERR_ORDER, "plan: moment kernel does not fit");

@@ -29,6 +29,7 @@
 #include "alpha.cuh"
 #include "alpha_dw.cuh"
 #include "dw.cuh"
+#include "dw2.cuh"
 #include "p2s_internal.h"
 
 namespace p2s {
@@ -41,8 +42,14 @@ constexpr int kRow = 14;   // per-row constants: B_i, F_i, H_i (9), T0, T1, P1, 
 constexpr int kPlane = 6;  // per-plane constants: D_i, E_i
 constexpr int kGeoDW = 40;
 
+// The B table, the alpha, T1 and T2 buffers and the moment accumulator hold coupling pairs
+// in pair slots: slot sp carries pairs 2 sp and 2 sp + 1 as one dw2 (lanes x and y), so that
+// phases B, C and D advance both pairs with one packed instruction per FP32 operation.  The B
+// table entries are duplicated into both lanes.  A group with an odd number of pairs leaves
+// lane y of its last slot zero and never stores it.
 struct SmemDW {
-    dw *B, *xq, *t0, *t1, *t2, *alpha, *T1, *T2, *Iacc, *geo, *row, *plane;
+    dw2 *B, *alpha, *T1, *T2, *Iacc;
+    dw *xq, *t0, *t1, *t2, *geo, *row, *plane;
     double* geo64;
 };
 
@@ -50,31 +57,35 @@ struct SmemDW {
 // same column of different rows hit different banks.
 __host__ __device__ __forceinline__ int padded_stride(int gmax) { return gmax | 1; }
 
-// Sizes (double-words) of one buffer of each double-buffered array.
+// Pair slots of n_pairs coupling pairs.
+__host__ __device__ __forceinline__ int pair_slots(int n_pairs) { return (n_pairs + 1) / 2; }
+
+// Sizes (16-byte pair-slot entries) of one buffer of each double-buffered array.
 // Folded alpha of a chunk, per pair: the even part E[bb][p] = alpha(p) + alpha(G-1-p) and the
 // odd part O[bb][p] = alpha(p) - alpha(G-1-p), p < H = ceil(G/2) (for odd G the middle point
 // has E = alpha, O = 0), each in rows of odd stride (H | 1) so that phase-B reads of different
-// rows fall in different banks.  nb * (H | 1) <= 160 for every G; the odd part starts 168
-// double-words (16 banks) after the even one, so the two parities of a row do not collide.
-constexpr int kFoldHalf = 168;
+// rows fall in different banks.  nb * (H | 1) <= 160 for every G; the odd part starts 164
+// entries (656 words: 16 banks) after the even one, so the two parities of a row do not collide.
+constexpr int kFoldHalf = 164;
 constexpr int kAlphaPair = 2 * kFoldHalf;
-__host__ __device__ __forceinline__ int alpha_buf(int n_pairs) { return n_pairs * kAlphaPair; }
-__host__ __device__ __forceinline__ int t1_buf(int n_pairs, int kb) { return n_pairs * kNB * kb; }
-__host__ __device__ __forceinline__ int t2_buf(int n_pairs, int kb) { return n_pairs * kb * kb; }
+__host__ __device__ __forceinline__ int alpha_buf(int n_pairs) { return pair_slots(n_pairs) * kAlphaPair; }
+__host__ __device__ __forceinline__ int t1_buf(int n_pairs, int kb) { return pair_slots(n_pairs) * kNB * kb; }
+__host__ __device__ __forceinline__ int t2_buf(int n_pairs, int kb) { return pair_slots(n_pairs) * kb * kb; }
 
+// iacc_cap counts double-words (two per pair-slot entry; even); the dw2 arrays come first, so
+// every one starts on a 16-byte boundary.
 __device__ __forceinline__ SmemDW carve_dw(unsigned char* sm, int n_pairs, int kb, int gmax, int iacc_cap) {
     SmemDW S;
-    dw* p = reinterpret_cast<dw*>(sm);
-    S.B = p;
-    S.xq = S.B + kb * padded_stride(gmax);
-    S.t0 = S.xq + gmax;
-    S.t1 = S.t0 + gmax;
-    S.t2 = S.t1 + gmax;
-    S.alpha = S.t2 + gmax;
+    S.B = reinterpret_cast<dw2*>(sm);
+    S.alpha = S.B + kb * padded_stride(gmax);
     S.T1 = S.alpha + 2 * alpha_buf(n_pairs);
     S.T2 = S.T1 + 2 * t1_buf(n_pairs, kb);
     S.Iacc = S.T2 + 2 * t2_buf(n_pairs, kb);
-    S.geo = S.Iacc + iacc_cap;
+    S.xq = reinterpret_cast<dw*>(S.Iacc + iacc_cap / 2);
+    S.t0 = S.xq + gmax;
+    S.t1 = S.t0 + gmax;
+    S.t2 = S.t1 + gmax;
+    S.geo = S.t2 + gmax;
     S.row = S.geo + kGeoDW;
     S.plane = S.row + 2 * kNB * kRow;
     S.geo64 = reinterpret_cast<double*>(S.plane + 2 * kPlane);
@@ -158,7 +169,8 @@ __device__ __forceinline__ void metric_constants_task(const SmemDW& S, const Chu
 // the element at run time.
 template <int GC, int KC>
 __device__ __forceinline__ void element_pipeline(const MomentLaunch& L, const SmemDW& S, const ElemDesc& d, int Grt,
-                                                 bool metric_rt, int gstride, int aS, int t1S, int t2S, int* bad_jac) {
+                                                 bool metric_rt, int gstride, int aS, int t1S, int t2S, int* bad_jac,
+                                                 int* item_ctr) {
     constexpr bool kSpec = GC > 0 && KC > 0;
     const int tid = threadIdx.x;
     const int G = kSpec ? GC : Grt;
@@ -171,7 +183,9 @@ __device__ __forceinline__ void element_pipeline(const MomentLaunch& L, const Sm
     constexpr int NBC = kSpec ? rows_per_chunk(GC, LRC) : 0;
     constexpr int NCPC = kSpec ? (GC + NBC - 1) / NBC : 0;
     const int per_pair = Ku * Kv * Kw;
-    const int ppg = kSpec ? 6 : max(1, min(np, L.iacc_cap / per_pair));
+    // pairs per group: whole pair slots of the accumulator (the host sizes it for at least
+    // one slot, so groups of several pairs start at even pairs)
+    const int ppg = kSpec ? 6 : max(1, min(np, 2 * (L.iacc_cap / (2 * per_pair))));
     const int H = (G + 1) / 2, LR = 2 * H, Hs = H | 1;  // folded half, lanes per row, row stride
     const float rKu = 1.f / (float)Ku, rKv = 1.f / (float)Kv, rLR = 1.f / (float)LR;
     const int nb = kSpec ? NBC : rows_per_chunk(G, LR);
@@ -179,7 +193,7 @@ __device__ __forceinline__ void element_pipeline(const MomentLaunch& L, const Sm
     const float rncp = 1.f / (float)ncp;
     const int T = G * ncp;
     for (int s0 = 0; s0 < np; s0 += ppg) {
-        const int ns = min(np, s0 + ppg) - s0;
+        const int ns = min(np, s0 + ppg) - s0, nsp = pair_slots(ns);
         for (int step = -1; step < T + 3; ++step) {
             // row / plane constants of chunk step + 1 (tasks on the highest threads)
             if (step + 1 < T) {
@@ -199,7 +213,7 @@ __device__ __forceinline__ void element_pipeline(const MomentLaunch& L, const Sm
             if (step >= 0 && step < T) {
                 const Chunk ch = chunk_of_ct<NCPC>(step, ncp, rncp, nb, G);
                 const dw* row = S.row + (step & 1) * kNB * kRow;
-                dw* al = S.alpha + (step & 1) * aS;
+                dw2* al = S.alpha + (step & 1) * aS;
                 const bool lane_on = tid < ch.nbc * LR;
                 const int bb = div_ct<LRC>(tid, LR, rLR), r = tid - bb * LR, p = r >> 1, side = r & 1;
                 const bool middle = 2 * p + 1 == G;  // odd G: its middle point, taken by the even lane
@@ -218,13 +232,17 @@ __device__ __forceinline__ void element_pipeline(const MomentLaunch& L, const Sm
                     }
                 }
                 const int ia = (side ? kFoldHalf : 0) + bb * Hs + p;
+                // pairs sa and sa + 1 in one slot (s0 is even whenever a group holds several pairs)
 #pragma unroll
-                for (int s = 0; s < 6; ++s) {
-                    if (s >= s0 && s < s0 + ns) {  // uniform across the CTA: every lane shuffles
-                        const dw o = dw_make(__shfl_xor_sync(0xffffffffu, K[s].hi, 1),
-                                             __shfl_xor_sync(0xffffffffu, K[s].lo, 1));
-                        const dw f = side ? (middle ? dw_from_float(0.f) : dw_sub_fast(o, K[s])) : dw_add_fast(K[s], o);
-                        if (lane_on) al[(s - s0) * kAlphaPair + ia] = f;
+                for (int sa = 0; sa < 6; sa += 2) {
+                    if (sa >= s0 && sa < s0 + ns) {  // uniform across the CTA: every lane shuffles
+                        const dw2 k2 = dw2_make(K[sa], sa + 1 < s0 + ns ? K[sa + 1] : dw_from_float(0.f));
+                        const dw2 o = dw2{f2{__shfl_xor_sync(0xffffffffu, k2.hi.v, 1)},
+                                          f2{__shfl_xor_sync(0xffffffffu, k2.lo.v, 1)}};
+                        // even lane K + o, odd lane o + (-K) (dw_add_fast / dw_sub_fast per pair)
+                        dw2 f = dw2_add_fast(side ? o : k2, side ? dw2_neg(k2) : o);
+                        if (side && middle) f = dw2_zero();
+                        if (lane_on) al[((sa - s0) >> 1) * kAlphaPair + ia] = f;
                     }
                 }
             }
@@ -234,68 +252,83 @@ __device__ __forceinline__ void element_pipeline(const MomentLaunch& L, const Sm
             int nB = 0, nC = 0, nD = 0, pd = -1;
             if (tb >= 0 && tb < T) {
                 cb = chunk_of_ct<NCPC>(tb, ncp, rncp, nb, G);
-                nB = ns * cb.nbc * Ku;
+                nB = nsp * cb.nbc * Ku;
             }
             if (tc >= 0 && tc < T) {
                 cc = chunk_of_ct<NCPC>(tc, ncp, rncp, nb, G);
-                nC = ns * Ku * Kv;
+                nC = nsp * Ku * Kv;
             }
             if (td >= 0 && td < T) {
                 const int pt = div_ct<NCPC>(td, ncp, rncp);
                 if (td - pt * ncp == ncp - 1) pd = pt;
             }
             if (pd >= 0) {
-                nD = ns * Ku * Kv;
+                nD = nsp * Ku * Kv;
             }
-            const dw* alB = S.alpha + (tb & 1) * aS;
-            dw* t1B = S.T1 + (tb & 1) * t1S;
-            const dw* t1C = S.T1 + (tc & 1) * t1S;
-            dw* t2C = S.T2 + (cc.c & 1) * t2S;
-            const dw* t2D = S.T2 + (pd & 1) * t2S;
+            // items run on pair slots sp: both pairs of a slot advance together
+            const dw2* alB = S.alpha + (tb & 1) * aS;
+            dw2* t1B = S.T1 + (tb & 1) * t1S;
+            const dw2* t1C = S.T1 + (tc & 1) * t1S;
+            dw2* t2C = S.T2 + (cc.c & 1) * t2S;
+            const dw2* t2D = S.T2 + (pd & 1) * t2S;
             const float r_nbc = 1.f / (float)max(cb.nbc, 1);
-            for (int j = tid; j < nB + nC + nD; j += kThreads) {
-                if (j < nB) {
-                    // T1[s][bb][k] = sum_a B[k][a] alpha[s][bb][a]
-                    //              = sum_{p<H} B[k][p] (k even ? E : O)[s][bb][p],
-                    // since B[k][G-1-p] = (-1)^k B[k][p] on the symmetric rule; k fastest
-                    // across threads, so the folded reads are near-broadcasts and the B rows
-                    // (odd stride) spread
-                    const int sb = div_ct<KCs>(j, Ku, rKu), k = j - sb * Ku;
-                    const int s = div_small(sb, cb.nbc, r_nbc), bb = sb - s * cb.nbc;
-                    const dw* al = alB + s * kAlphaPair + (k & 1) * kFoldHalf + bb * Hs;
-                    const dw* Bk = S.B + k * gstride;
-                    dw_acc acc;
+            // The items go to warps as they come free (a warp takes 32 at a time from the
+            // step's counter), so the threads without a point in this chunk, and those done
+            // with alpha first, take more of them.  The counters alternate with the step;
+            // thread 0 clears the one the next step uses, which no thread touches in this one.
+            const int nItems = nB + nC + nD;
+            int* ctr = item_ctr + (step & 1);
+            if (tid == 0) item_ctr[(step + 1) & 1] = 0;
+            for (;;) {
+                int base = nItems;
+                if ((tid & 31) == 0 && nItems > 0) base = atomicAdd(ctr, 32);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (base >= nItems) break;
+                const int j = base + (tid & 31);
+                if (j < nItems) {
+                    if (j < nB) {
+                        // T1[s][bb][k] = sum_a B[k][a] alpha[s][bb][a]
+                        //              = sum_{p<H} B[k][p] (k even ? E : O)[s][bb][p],
+                        // since B[k][G-1-p] = (-1)^k B[k][p] on the symmetric rule; k fastest
+                        // across threads, so the folded reads are near-broadcasts and the B rows
+                        // (odd stride) spread
+                        const int sb = div_ct<KCs>(j, Ku, rKu), k = j - sb * Ku;
+                        const int sp = div_small(sb, cb.nbc, r_nbc), bb = sb - sp * cb.nbc;
+                        const dw2* al = alB + sp * kAlphaPair + (k & 1) * kFoldHalf + bb * Hs;
+                        const dw2* Bk = S.B + k * gstride;
+                        dw2_acc acc;
 #pragma unroll 4
-                    for (int p = 0; p < H; ++p) acc.fma(Bk[p], al[p]);
-                    t1B[(s * kNB + bb) * Kb + k] = acc.value();
-                } else if (j < nB + nC) {
-                    // T2[s][k][l] (+)= sum_bb B[l][b0 + bb] T1[s][bb][k]
-                    const int i = j - nB;
-                    const int sk = div_ct<KCs>(i, Kv, rKv), l = i - sk * Kv;
-                    const int s = div_ct<KCs>(sk, Ku, rKu), k = sk - s * Ku;
-                    const dw* t1 = t1C + s * kNB * Kb + k;
-                    const dw* Bl = S.B + l * gstride + cc.b0;
-                    dw_acc acc;
-                    if (cc.b0 > 0) {
-                        acc.s = t2C[i].hi;
-                        acc.c = t2C[i].lo;
-                    }
-                    for (int bb = 0; bb < cc.nbc; ++bb) acc.fma(Bl[bb], t1[bb * Kb]);
-                    t2C[i] = acc.value();
-                } else {
-                    // I[s][k][l][q] (+)= B[q][c] T2_c[s][k][l] for all q of one (s, k, l)
-                    const int skl = j - nB - nC;
-                    const dw t2 = t2D[skl];
-                    dw* I = S.Iacc + skl * Kw;
-#pragma unroll
-                    for (int q = 0; q < (kSpec ? KC : Kw); ++q) {
-                        dw_acc acc;
-                        if (pd > 0) {
-                            acc.s = I[q].hi;
-                            acc.c = I[q].lo;
+                        for (int p = 0; p < H; ++p) acc.fma(Bk[p], al[p]);
+                        t1B[(sp * kNB + bb) * Kb + k] = acc.value();
+                    } else if (j < nB + nC) {
+                        // T2[s][k][l] (+)= sum_bb B[l][b0 + bb] T1[s][bb][k]
+                        const int i = j - nB;
+                        const int sk = div_ct<KCs>(i, Kv, rKv), l = i - sk * Kv;
+                        const int sp = div_ct<KCs>(sk, Ku, rKu), k = sk - sp * Ku;
+                        const dw2* t1 = t1C + sp * kNB * Kb + k;
+                        const dw2* Bl = S.B + l * gstride + cc.b0;
+                        dw2_acc acc;
+                        if (cc.b0 > 0) {
+                            acc.s = t2C[i].hi;
+                            acc.c = t2C[i].lo;
                         }
-                        acc.fma(S.B[q * gstride + pd], t2);
-                        I[q] = acc.value();
+                        for (int bb = 0; bb < cc.nbc; ++bb) acc.fma(Bl[bb], t1[bb * Kb]);
+                        t2C[i] = acc.value();
+                    } else {
+                        // I[s][k][l][q] (+)= B[q][c] T2_c[s][k][l] for all q of one (s, k, l)
+                        const int skl = j - nB - nC;
+                        const dw2 t2 = t2D[skl];
+                        dw2* I = S.Iacc + skl * Kw;
+#pragma unroll
+                        for (int q = 0; q < (kSpec ? KC : Kw); ++q) {
+                            dw2_acc acc;
+                            if (pd > 0) {
+                                acc.s = I[q].hi;
+                                acc.c = I[q].lo;
+                            }
+                            acc.fma(S.B[q * gstride + pd], t2);
+                            I[q] = acc.value();
+                        }
                     }
                 }
             }
@@ -307,10 +340,11 @@ __device__ __forceinline__ void element_pipeline(const MomentLaunch& L, const Sm
             const int ku = d.ord[gi][0] + d.ord[gj][0] - 1, kv = d.ord[gi][1] + d.ord[gj][1] - 1,
                       kw = d.ord[gi][2] + d.ord[gj][2] - 1;
             float2* dst = reinterpret_cast<float2*>(L.mom + d.mom_off + d.pair_off[s0 + s]);
-            const dw* src = S.Iacc + s * per_pair;
+            const dw2* src = S.Iacc + (s >> 1) * per_pair;
             for (int i = tid; i < ku * kv * kw; i += kThreads) {
                 const int k = i / (kv * kw), r = i - k * kv * kw, l = r / kw, q = r - l * kw;
-                const dw v = src[(k * Kv + l) * Kw + q];
+                const dw2 v2 = src[(k * Kv + l) * Kw + q];
+                const dw v = (s & 1) ? dw2_y(v2) : dw2_x(v2);
                 dst[i] = make_float2(v.hi, v.lo);
             }
         }
@@ -328,6 +362,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_moments_dw(MomentLaunch L) {
     const int aS = alpha_buf(L.n_pairs), t1S = t1_buf(L.n_pairs, L.kb), t2S = t2_buf(L.n_pairs, L.kb);
 
     __shared__ long long s_elem;
+    __shared__ int s_item[2];  // per-step item counters of the element pipeline
     __shared__ int s_tabG, s_tabK;  // G and K of the 1-D tables in shared memory (-1: none yet)
     if (tid == 0) {
         s_tabG = -1;
@@ -358,11 +393,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_moments_dw(MomentLaunch L) {
             const double x = L.gl_x[G * kMaxG + tid], w = L.gl_w[G * kMaxG + tid];
             S.xq[tid] = dw_from_double(x);
             double p0 = 1.0, p1 = x;
-            S.B[tid] = dw_from_double(w);
-            if (Kb > 1) S.B[gstride + tid] = dw_from_double(w * x);
+            S.B[tid] = dw2_dup(dw_from_double(w));
+            if (Kb > 1) S.B[gstride + tid] = dw2_dup(dw_from_double(w * x));
             for (int k = 1; k + 1 < Kb; ++k) {
                 const double p2 = ((2 * k + 1) * x * p1 - k * p0) / (k + 1);
-                S.B[(k + 1) * gstride + tid] = dw_from_double(w * p2);
+                S.B[(k + 1) * gstride + tid] = dw2_dup(dw_from_double(w * p2));
                 p0 = p1;
                 p1 = p2;
             }
@@ -414,13 +449,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_moments_dw(MomentLaunch L) {
 
         const bool spec = metric && np == 6 && Ku == 7 && Kv == 7 && Kw == 7 && L.iacc_cap >= 6 * 343;
         switch (spec ? G : 0) {
-        case 8: element_pipeline<8, 7>(L, S, d, G, metric, gstride, aS, t1S, t2S, &bad_jac); break;
-        case 12: element_pipeline<12, 7>(L, S, d, G, metric, gstride, aS, t1S, t2S, &bad_jac); break;
-        case 16: element_pipeline<16, 7>(L, S, d, G, metric, gstride, aS, t1S, t2S, &bad_jac); break;
-        case 24: element_pipeline<24, 7>(L, S, d, G, metric, gstride, aS, t1S, t2S, &bad_jac); break;
-        case 32: element_pipeline<32, 7>(L, S, d, G, metric, gstride, aS, t1S, t2S, &bad_jac); break;
-        case 48: element_pipeline<48, 7>(L, S, d, G, metric, gstride, aS, t1S, t2S, &bad_jac); break;
-        default: element_pipeline<0, 0>(L, S, d, G, metric, gstride, aS, t1S, t2S, &bad_jac); break;
+        case 8: element_pipeline<8, 7>(L, S, d, G, metric, gstride, aS, t1S, t2S, &bad_jac, s_item); break;
+        case 12: element_pipeline<12, 7>(L, S, d, G, metric, gstride, aS, t1S, t2S, &bad_jac, s_item); break;
+        case 16: element_pipeline<16, 7>(L, S, d, G, metric, gstride, aS, t1S, t2S, &bad_jac, s_item); break;
+        case 24: element_pipeline<24, 7>(L, S, d, G, metric, gstride, aS, t1S, t2S, &bad_jac, s_item); break;
+        case 32: element_pipeline<32, 7>(L, S, d, G, metric, gstride, aS, t1S, t2S, &bad_jac, s_item); break;
+        case 48: element_pipeline<48, 7>(L, S, d, G, metric, gstride, aS, t1S, t2S, &bad_jac, s_item); break;
+        default: element_pipeline<0, 0>(L, S, d, G, metric, gstride, aS, t1S, t2S, &bad_jac, s_item); break;
         }
         if (tid == 0) {
             if (L.elem_status) L.elem_status[e] = bad_jac ? P2S_ERR_JACOBIAN : P2S_OK;
@@ -433,11 +468,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_moments_dw(MomentLaunch L) {
 }  // namespace
 
 size_t moments_dw_smem_bytes(int n_pairs, int kb, int gmax, int iacc_cap) {
-    size_t d = (size_t)kb * padded_stride(gmax) + 4 * (size_t)gmax + 2 * (size_t)alpha_buf(n_pairs) +
-               2 * (size_t)t1_buf(n_pairs, kb) + 2 * (size_t)t2_buf(n_pairs, kb) + (size_t)iacc_cap + kGeoDW +
-               2 * kNB * kRow + 2 * kPlane;
+    const size_t e2 = (size_t)kb * padded_stride(gmax) + 2 * (size_t)alpha_buf(n_pairs) +
+                      2 * (size_t)t1_buf(n_pairs, kb) + 2 * (size_t)t2_buf(n_pairs, kb);  // dw2 entries
+    const size_t d = 2 * e2 + (size_t)iacc_cap + 4 * (size_t)gmax + kGeoDW + 2 * kNB * kRow + 2 * kPlane;
     return d * sizeof(dw) + 48 * sizeof(double);
 }
+
+// Accumulator of the double-word kernel in double-words: whole pair slots (two pairs each),
+// at least one, for pairs of up to max_pair moments.
+int moments_dw_iacc_words(int n_pairs, int max_pair) { return 2 * pair_slots(n_pairs) * max_pair; }
 
 cudaError_t launch_moments_dw(const MomentLaunch& L, int grid, size_t smem, cudaStream_t s) {
     k_moments_dw<<<grid, kThreads, smem, s>>>(L);

@@ -102,6 +102,7 @@ size_t moments_smem_bytes(int n_pairs, int kb, int gmax, int iacc_cap);
 cudaError_t launch_moments_fp64(const MomentLaunch& L, int grid, size_t smem, cudaStream_t s);
 // moments_dw.cu: the same step in double-word arithmetic (mixed path; writes (hi, lo) pairs)
 size_t moments_dw_smem_bytes(int n_pairs, int kb, int gmax, int iacc_cap);
+int moments_dw_iacc_words(int n_pairs, int max_pair);
 cudaError_t launch_moments_dw(const MomentLaunch& L, int grid, size_t smem, cudaStream_t s);
 int moments_dw_blocks_per_sm(size_t smem);
 
