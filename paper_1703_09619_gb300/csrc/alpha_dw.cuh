@@ -19,8 +19,8 @@ namespace p2s {
 // alpha (metric kind) at one point from the row/plane constants; returns detJ > 0.  Every
 // operation is a _fast or _lazy one (dw.cuh): the error of each factor is O(u^2) against the
 // scale of its operands, which the normwise error of the element matrices tolerates.  The
-// Jacobian, cofactor, determinant and Gram sums skip the renormalisation of their result
-// (_lazy); the phase is renormalised before the sine's range reduction.
+// Jacobian, cofactor, determinant, Gram, phase and eps sums skip the renormalisation of
+// their result (_lazy): every later operation takes both words of an operand.
 __device__ __forceinline__ bool metric_alpha_dw(const dw* geo, const dw* row, const dw* plane, dw u, dw Ca,
                                                 dw Sa, dw* K) {
     const dw beta = dw_mul_fast(Ca, row[11]);
@@ -35,8 +35,8 @@ __device__ __forceinline__ bool metric_alpha_dw(const dw* geo, const dw* row, co
         J[i][1] = dw_fma_lazy(g, dbv, dw_fma_lazy(u, plane[3 + i], plane[i]));
         J[i][2] = dw_fma_lazy(g, dbw, dw_fma_lazy(u, row[6 + i], row[3 + i]));
     }
-    const dw theta = dw_fma_fast(geo[39], beta, dw_fma_fast(u, row[10], row[9]));
-    const dw eps = dw_add_f(dw_mul_fast(geo[27], dw_sin(theta)), 1.f);
+    const dw theta = dw_fma_lazy(geo[39], beta, dw_fma_lazy(u, row[10], row[9]));
+    const dw eps = dw_add_f_lazy(dw_mul_fast(geo[27], dw_sin(theta)), 1.f);
     dw C[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)

@@ -81,8 +81,10 @@ __device__ __forceinline__ dw dw_div(dw x, dw y) {
 //                 TwoSum, the low words join the rounding error, one Fast2Sum renormalises;
 //   dw_mul_fast - DWTimesDW with FMA, without the final renormalisation: the pair returned
 //                 has |lo| <= ~3u |hi| and every operation here accepts it as an operand;
-//   dw_div_fast - the FP32 quotient plus one Newton correction computed from the exact
-//                 remainder (x.hi - q y.hi is exact by Sterbenz): error about 5u^2.
+//   dw_div_fast - an FP32 quotient from the hardware reciprocal (a few ulp) plus one Newton
+//                 correction computed from the remainder (x.hi - q y.hi is exact by Sterbenz,
+//                 the correction's own error is a few ulp of a term of order u |x / y|):
+//                 error about 12 u^2.
 __device__ __forceinline__ dw dw_add_fast(dw x, dw y) {
     const dw s = two_sum(x.hi, y.hi);
     return fast_two_sum(s.hi, s.lo + (x.lo + y.lo));
@@ -94,11 +96,12 @@ __device__ __forceinline__ dw dw_mul_fast(dw x, dw y) {
 }
 __device__ __forceinline__ dw dw_fma_fast(dw x, dw y, dw z) { return dw_add_fast(dw_mul_fast(x, y), z); }
 __device__ __forceinline__ dw dw_div_fast(dw x, dw y) {
-    const float q1 = __fdiv_rn(x.hi, y.hi);
+    const float ry = __fdividef(1.f, y.hi);
+    const float q1 = x.hi * ry;
     const float ph = y.hi * q1;
     const float pl = fmaf(y.lo, q1, fmaf(y.hi, q1, -ph));
     const float r = (x.hi - ph) + (x.lo - pl);
-    return fast_two_sum(q1, __fdiv_rn(r, y.hi));
+    return fast_two_sum(q1, r * ry);
 }
 
 // Sums without the final renormalisation: (s, e + x.lo + y.lo) with s + e = x.hi + y.hi
@@ -111,6 +114,10 @@ __device__ __forceinline__ dw dw_add_lazy(dw x, dw y) {
 }
 __device__ __forceinline__ dw dw_sub_lazy(dw x, dw y) { return dw_add_lazy(x, dw_neg(y)); }
 __device__ __forceinline__ dw dw_fma_lazy(dw x, dw y, dw z) { return dw_add_lazy(dw_mul_fast(x, y), z); }
+__device__ __forceinline__ dw dw_add_f_lazy(dw x, float y) {
+    const dw s = two_sum(x.hi, y);
+    return dw{s.hi, s.lo + x.lo};
+}
 
 // Accumulator for sums of products: the leading words sum with TwoSum, every rounding
 // error and lower-order product term goes to the second word; renormalise at the end.
@@ -135,12 +142,14 @@ struct dw_acc {
     __device__ __forceinline__ dw value() const { return fast_two_sum(s, c); }
 };
 
-// sin of a double-word argument |x| <= ~6e3.  Cody-Waite reduction by pi/2 with a
-// four-part constant (the first two parts have 12 significant bits, so n * part is exact
-// for |n| < 2^12), then Taylor polynomials on |r| <= pi/4 (the leading terms in
-// double-word, the tail, below 1e-3 in magnitude, in FP32).  The reduction is accurate to
-// the last bit of the double word; the polynomials use the _fast operations (absolute error
-// a few u^2 on a result of magnitude <= 1).
+// sin of a double-word argument |x| <= ~6e3 (its words need not be normalised).  Cody-Waite
+// reduction by pi/2 with a four-part constant (the first two parts have 12 significant bits,
+// so n * part is exact for |n| < 2^12), then Taylor polynomials on |r| <= pi/4 (the leading
+// terms in double-word, the tail, below 1e-3 in magnitude, in FP32).  The reduction is
+// accurate to the last bit of the double word; its partial sums and the polynomial's sums
+// skip their renormalisation except before the square (every later operation takes both
+// words), and the result is returned unnormalised (absolute error a few u^2 on a result of
+// magnitude <= 1).
 __device__ __forceinline__ dw dw_sin(dw x) {
     // pi/2 = C1 + C2 + C3 + C4 (C1, C2 with 12 significant bits; C3, C4 FP32 roundings of the rest)
     const float C1 = 1.57080078125f;
@@ -149,9 +158,9 @@ __device__ __forceinline__ dw dw_sin(dw x) {
     const float C4 = 5.721188916458728e-18f;
     const float n = rintf(x.hi * 0.63661974668502808f);
     // r = x - n (C1 + C2 + C3 + C4), n C1 and n C2 exact
-    dw r = dw_add_f(x, -n * C1);
-    r = dw_add_f(r, -n * C2);
-    r = dw_add_fast(r, dw_neg(two_prod(n, C3)));
+    dw r = dw_add_f_lazy(x, -n * C1);
+    r = dw_add_f_lazy(r, -n * C2);
+    r = dw_add_lazy(r, dw_neg(two_prod(n, C3)));
     r = dw_add_f(r, -n * C4);
     const dw z = dw_mul_fast(r, r);
     const int q = ((int)n) & 3;
@@ -170,8 +179,8 @@ __device__ __forceinline__ dw dw_sin(dw x) {
                     : dw_make(0.0083333337679505348f, -4.3461720333759502e-10f);  // 1/120
     const dw c1 = c ? dw_make(-0.5f, 0.f) : dw_make(-0.1666666716337204f, 4.9670538793122887e-09f);  // -1/2, -1/6
     const dw A = c ? dw_make(1.f, 0.f) : r;
-    const dw inner = dw_add_fast(c1, dw_mul_fast(z, dw_add_f(c2, zf * t)));
-    const dw res = dw_add_fast(A, dw_mul_fast(dw_mul_fast(A, z), inner));
+    const dw inner = dw_add_lazy(c1, dw_mul_fast(z, dw_add_f_lazy(c2, zf * t)));
+    const dw res = dw_add_lazy(A, dw_mul_fast(dw_mul_fast(A, z), inner));
     return (q & 2) ? dw_neg(res) : res;
 }
 
