@@ -168,7 +168,8 @@ int p2s_plan_fill(p2s_plan* plan, const p2s_geometry* geom, const p2s_material* 
  *   unit_kbytes   shared memory of one work unit in KiB, stage-1/2 buffers plus the staged
  *                 output tile (general kernel only; default 100; up to 227);
  *   threads       threads per CTA of the contraction, 64..512 in steps of 32 (default:
- *                 one per combination of the largest unit);
+ *                 one per combination of the largest unit, at most 128 for the kernel
+ *                 compiled per uniform order);
  *   kernel        which contraction kernel (every one computes each entry with the same
  *                 operations in the same order):
  *                 0 (default) the library's choice: with every order <= 8 a kernel

@@ -434,7 +434,10 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
         size_t a, bcap, tl;
         int combos;
         contract_ff_shape(spec_n, m1n, a, bcap, tl, combos);
-        const int threads = tile.threads ? tile.threads : std::min(512, std::max(64, (combos + 31) / 32 * 32));
+        // default CTA: one thread per stage-3 combination up to 128 (two combinations per thread
+        // beyond); eight 128-thread CTAs per SM keep more barrier groups in flight than four of
+        // 256 (c5 at N = 4: 6.89 against 7.88 ms; c2 at N = 6: 27.3 against 28.2 ms)
+        const int threads = tile.threads ? tile.threads : std::min(128, std::max(64, (combos + 31) / 32 * 32));
         const size_t smem = (a + bcap) * sizeof(float2);
         const int per_sm = smem <= limit ? contract_ffn_blocks_per_sm(spec_n, threads, smem) : 0;
         if (per_sm < 1) return fail(P2S_ERR_ORDER, "plan: specialised contraction kernel does not fit");

@@ -81,6 +81,16 @@ def test_spec_kernel_tile_configs_bitwise_equal(torch, ctx):
         assert np.array_equal(got, ref), tile
 
 
+def test_spec_kernel_default_cta(torch, ctx):
+    """The uniform-order kernel's default CTA holds at most 128 threads (two stage-3
+    combinations per thread at N = 4); it gives the one-thread-per-combination CTA's bits."""
+    wl = W.make("c5", 40).with_npts(12)
+    ref, cfg = fill(torch, ctx, wl, p2s.MIXED)
+    assert cfg["threads"] == 128
+    got, cfg2 = fill(torch, ctx, wl, p2s.MIXED, tile={"combo_target": 0, "unit_kbytes": 0, "threads": 256})
+    assert cfg2["threads"] == 256 and np.array_equal(got, ref)
+
+
 def with_orders(wl, lo, hi, seed):
     """The workload with per-component per-axis orders redrawn from U{lo..hi}."""
     import dataclasses
