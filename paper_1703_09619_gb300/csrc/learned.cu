@@ -389,17 +389,12 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
 // One (element, type) per CTA of 256 threads, so that a few hundred judged elements still
 // spread over every SM; 16-byte loads (when both segments allow them) four deep per thread,
 // maxima reduced by warp shuffles.
-// One (element, type) block per CTA iteration, 1024 threads: few blocks per CTA, so the last
-// wave of blocks is short.
-constexpr int kErrThreads = 1024;
-
-__global__ void __launch_bounds__(kErrThreads, 2) k_elem_err(const double* __restrict__ a, const int64_t* __restrict__ offa,
-                                                          const double* __restrict__ b, const int64_t* __restrict__ offb,
-                                                          int64_t E, int n_types, double* __restrict__ err) {
+__global__ void __launch_bounds__(256) k_elem_err(const double* __restrict__ a, const int64_t* __restrict__ offa,
+                                                  const double* __restrict__ b, const int64_t* __restrict__ offb,
+                                                  int64_t E, int n_types, double* __restrict__ err) {
     // err[e] (zeroed by the launcher) takes the largest ratio of its types by an atomic
     // maximum on the bit patterns (non-negative doubles order as their bits)
-    constexpr int NW = kErrThreads / 32;
-    __shared__ double sd[NW], sm[NW];
+    __shared__ double sd[8], sm[8];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int64_t it = blockIdx.x; it < E * n_types; it += gridDim.x) {
         const int64_t e = it / n_types;
@@ -413,12 +408,12 @@ __global__ void __launch_bounds__(kErrThreads, 2) k_elem_err(const double* __res
             const double2* qb = reinterpret_cast<const double2*>(pb);
             const int64_t n2 = len / 2;
             int64_t i = tid;
-            for (; i + 3 * kErrThreads < n2; i += 4 * kErrThreads) {
+            for (; i + 768 < n2; i += 1024) {
                 double2 va[4], vb[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    va[j] = __ldcs(qa + i + kErrThreads * j);
-                    vb[j] = __ldcs(qb + i + kErrThreads * j);
+                    va[j] = __ldcs(qa + i + 256 * j);
+                    vb[j] = __ldcs(qb + i + 256 * j);
                 }
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
@@ -426,7 +421,7 @@ __global__ void __launch_bounds__(kErrThreads, 2) k_elem_err(const double* __res
                     m = fmax(m, fmax(fabs(vb[j].x), fabs(vb[j].y)));
                 }
             }
-            for (; i < n2; i += kErrThreads) {
+            for (; i < n2; i += 256) {
                 const double2 va = __ldcs(qa + i), vb = __ldcs(qb + i);
                 d = fmax(d, fmax(fabs(va.x - vb.x), fabs(va.y - vb.y)));
                 m = fmax(m, fmax(fabs(vb.x), fabs(vb.y)));
@@ -436,7 +431,7 @@ __global__ void __launch_bounds__(kErrThreads, 2) k_elem_err(const double* __res
                 m = fmax(m, fabs(pb[len - 1]));
             }
         } else {
-            for (int64_t i = tid; i < len; i += kErrThreads) {
+            for (int64_t i = tid; i < len; i += 256) {
                 d = fmax(d, fabs(pa[i] - pb[i]));
                 m = fmax(m, fabs(pb[i]));
             }
@@ -451,7 +446,7 @@ __global__ void __launch_bounds__(kErrThreads, 2) k_elem_err(const double* __res
         if (tid == 0) {
             d = 0.0;
             m = 0.0;
-            for (int w = 0; w < NW; ++w) {
+            for (int w = 0; w < 8; ++w) {
                 d = fmax(d, sd[w]);
                 m = fmax(m, sm[w]);
             }
@@ -557,9 +552,9 @@ int p2s_element_errors(p2s_ctx* ctx, const double* a, const int64_t* offsets_a, 
     if (n_elem == 0) return P2S_OK;
     if (!a || !b || !offsets_a || !offsets_b || !err) return fail(P2S_ERR_ARG, "p2s_element_errors: NULL array");
     P2S_LCUDA(cudaSetDevice(T->device));
-    const int grid = (int)std::min<int64_t>(n_elem * n_types, (int64_t)T->sm_count * 2);
+    const int grid = (int)std::min<int64_t>(n_elem * n_types, (int64_t)T->sm_count * 8);
     P2S_LCUDA(cudaMemsetAsync(err, 0, sizeof(double) * n_elem, (cudaStream_t)stream));
-    k_elem_err<<<grid, kErrThreads, 0, (cudaStream_t)stream>>>(a, offsets_a, b, offsets_b, n_elem, n_types, err);
+    k_elem_err<<<grid, 256, 0, (cudaStream_t)stream>>>(a, offsets_a, b, offsets_b, n_elem, n_types, err);
     P2S_LCUDA(cudaGetLastError());
     return P2S_OK;
 }
