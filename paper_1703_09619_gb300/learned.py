@@ -150,7 +150,7 @@ def balanced_weights(y):
 
 
 def train_default(ctx, n_train=65536, epochs=60, seed=0, verbose=False, shards=(0, 2, 3, 4), balance=False,
-                  cosine=False, batch=1024, lr=2e-3, weight_decay=1e-3):
+                  cosine=False, batch=1024, lr=2e-3, weight_decay=1e-3, label_tol=LABEL_TOL):
     """Labels on the seeded training sets (the c5 recipe with its own seed: shards of
     c5train, shard 1 excluded as the held-out set) and a trained network."""
     torch = _torch()
@@ -159,7 +159,7 @@ def train_default(ctx, n_train=65536, epochs=60, seed=0, verbose=False, shards=(
     Xs, ys = [], []
     for sh in shards:
         wl = W.make("c5train", n_train, shard=sh)
-        ys.append(labels_from_errors(class_errors(ctx, wl)))
+        ys.append(labels_from_errors(class_errors(ctx, wl), label_tol))
         Xs.append(features(ctx, wl))
     y = np.concatenate(ys)
     t1 = time.time()
@@ -171,7 +171,7 @@ def train_default(ctx, n_train=65536, epochs=60, seed=0, verbose=False, shards=(
     pred = classes_of(predict(ctx, params, X))
     meta = {"n_train": int(y.size), "shards": list(shards), "epochs": int(epochs), "cosine": bool(cosine), "seed": seed,
             "batch": batch, "lr": lr, "weight_decay": weight_decay,
-            "label_tol": LABEL_TOL,
+            "label_tol": label_tol,
             "class_weight": None if cw is None else cw.tolist(),
             "label_hist": np.bincount(y, minlength=6).tolist(), "train_acc": float((pred == y).mean()),
             "train_under": float((pred < y).mean()), "final_loss": float(hist[-1]),
@@ -278,7 +278,7 @@ if __name__ == "__main__":
         print(json.dumps(meta))
         sys.exit(0)
     # python -m paper_1703_09619_gb300.learned [--shards 0,2,3,4] [--epochs 60] [--cosine] [--balance] [--seed 0]
-    #                                          [--batch 1024] [--lr 2e-3] [--wd 1e-3] [out.npz]
+    #                                          [--batch 1024] [--lr 2e-3] [--wd 1e-3] [--label-tol 1e-10] [out.npz]
     args = sys.argv[1:]
     shards = (0, 2, 3, 4)
     if "--shards" in args:
@@ -295,7 +295,8 @@ if __name__ == "__main__":
         seed = int(args[i + 1])
         del args[i:i + 2]
     extra = {}
-    for flag, key, conv in (("--batch", "batch", int), ("--lr", "lr", float), ("--wd", "weight_decay", float)):
+    for flag, key, conv in (("--batch", "batch", int), ("--lr", "lr", float), ("--wd", "weight_decay", float),
+                            ("--label-tol", "label_tol", float)):
         if flag in args:
             i = args.index(flag)
             extra[key] = conv(args[i + 1])

@@ -200,7 +200,6 @@ def test_training_gains_over_uniform_rule(torch, ctx):
     assert work_ratio > 1.5, (uniform_G, work_ratio)
 
 
-RISK = 0.002  # the class rule the benchmark uses (R13)
 
 
 def test_learned_fill_matches_oracle_multiclass(torch, ctx):
@@ -211,7 +210,8 @@ def test_learned_fill_matches_oracle_multiclass(torch, ctx):
     equals the oracle at 48 points (<= 1e-12, the plain FP64 bar).  This runs the device
     side class assignment (per-element G, class-grouped element queue) with several
     classes in one launch."""
-    P, _ = LN.load_checkpoint()
+    P, meta = LN.load_checkpoint()
+    RISK = float(meta["risk"])  # the class rule the benchmark uses (R13): the checkpoint's calibrated risk
     pool = W.make("c5", 4096)
     pred = LN.predict(ctx, P, LN.features(ctx, pool), risk=RISK)
     pick = []
