@@ -516,7 +516,7 @@ def run_learned(args, wl):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     lp = p2s.LearnedPlan(ctx, wl.orders, precision=p2s.MIXED, judge_frac=JUDGE_FRAC, seed=1703,
-                         judge_tol=JUDGE_TOL, risk=risk)
+                         judge_tol=JUDGE_TOL, risk=risk, n_nets=LN.n_nets_of(mlp_params))
     out = torch.empty(lp.output_entries, dtype=torch.float64, device=dev)
     npts_d = torch.empty(wl.n_elem, dtype=torch.int32, device=dev)
     step = lambda: lp.fill(wl.kind, params, nodes, bulge, P, out, npts_d, stream=stream)
@@ -646,8 +646,9 @@ def measure_e2e_learned(args, wl, ctx, P, dev, risk, chunk_elems=4096):
     from paper_1703_09619_gb300 import p2s
     E = wl.n_elem
     subs = [wl.subset(np.arange(s, min(E, s + chunk_elems))) for s in range(0, E, chunk_elems)]
+    from paper_1703_09619_gb300 import learned as LN
     plans = [p2s.LearnedPlan(ctx, w.orders, precision=p2s.MIXED, judge_frac=JUDGE_FRAC, seed=1703,
-                             judge_tol=JUDGE_TOL, risk=risk) for w in subs]
+                             judge_tol=JUDGE_TOL, risk=risk, n_nets=LN.n_nets_of(P.cpu().numpy())) for w in subs]
     return _e2e_pipeline(args, wl, subs, plans, dev,
                          lambda p, w, di, o, s: p.fill(w.kind, di[0], di[1], di[2], P, o, stream=s))
 

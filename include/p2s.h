@@ -316,6 +316,7 @@ int p2s_fill_elements_noalloc(p2s_ctx* ctx, const p2s_geometry* geom, const p2s_
 #define P2S_MLP_HIDDEN 64
 #define P2S_MLP_CLASSES 6
 #define P2S_MLP_PARAMS 41478
+#define P2S_MLP_MAX_NETS 8  /* networks of an ensemble */
 
 /* G of class cls (0..5), or P2S_ERR_ARG. */
 int p2s_learned_npts(int cls);
@@ -330,6 +331,15 @@ int p2s_coarse_features(p2s_ctx* ctx, const p2s_geometry* geom, const p2s_materi
  * softmax probability. */
 int p2s_mlp_predict(p2s_ctx* ctx, const float* params, const float* features, int64_t n, int margin, float risk,
                     int32_t* npts, float* logits, void* stream);
+
+/* Inference by an ensemble of n_nets (1..P2S_MLP_MAX_NETS) networks, whose parameter sets
+ * follow one another in params (device [n_nets][P2S_MLP_PARAMS]).  A sample's class
+ * probabilities are the mean of the networks' softmax outputs; the class is chosen from
+ * them as in p2s_mlp_predict (argmax, or the risk rule), then `margin` is added.  With
+ * n_nets > 1, logits (device [n][6]) is required: it holds the running sums and receives the
+ * log of the mean probabilities.  n_nets = 1 is p2s_mlp_predict. */
+int p2s_mlp_predict_ensemble(p2s_ctx* ctx, const float* params, int n_nets, const float* features, int64_t n,
+                             int margin, float risk, int32_t* npts, float* logits, void* stream);
 
 /* Training step, forward and backward on `batch` samples: mean softmax cross-entropy
  * (each sample weighted by class_weight[label], device [6], optional) into *loss (device)
@@ -362,6 +372,8 @@ typedef struct {
     double judge_frac; /* share of elements re-filled at 48 points in FP64          */
     uint64_t seed;     /* judge selection seed                                     */
     double judge_tol;  /* largest accepted relative difference (metric of p2s_element_errors) */
+    int n_nets;        /* networks in the parameters of p2s_learned_fill (0 or 1: one; up to
+                          P2S_MLP_MAX_NETS: an ensemble, p2s_mlp_predict_ensemble)          */
 } p2s_learned_opts;
 typedef struct {
     int64_t n_elem;

@@ -70,3 +70,33 @@ def loss_and_grad(p, X, y, class_weight=None, round_weights=True):
     g["W1"] = X.T @ dH1
     g["b1"] = dH1.sum(axis=0)
     return loss, pack(g)
+
+
+def softmax(Z):
+    """Row-wise softmax of logits Z [B][C] (FP64)."""
+    Z = np.asarray(Z, dtype=np.float64)
+    e = np.exp(Z - Z.max(axis=1, keepdims=True))
+    return e / e.sum(axis=1, keepdims=True)
+
+
+def ensemble_probs(params_list, X):
+    """Class probabilities of an ensemble: the mean over its networks of their softmax outputs."""
+    return np.mean([softmax(forward(p, X)[2]) for p in params_list], axis=0)
+
+
+def risk_class(P, risk):
+    """Class per row of probabilities P [B][C]: with risk > 0 the smallest class c whose higher
+    classes c+1..C-1 hold at most `risk` of the probability (the last class if none does);
+    with risk = 0 the most probable class."""
+    P = np.asarray(P, dtype=np.float64)
+    if risk <= 0:
+        return P.argmax(axis=1)
+    out = np.full(P.shape[0], P.shape[1] - 1)
+    for i in range(P.shape[0]):
+        above = 1.0
+        for c in range(P.shape[1]):
+            above -= P[i, c]
+            if above <= risk:
+                out[i] = c
+                break
+    return out

@@ -227,13 +227,78 @@ __device__ void mlp_forward(MlpSmem& S, int ns) {
     __syncthreads();
 }
 
+// The risk rule on class probabilities p (sum 1): the smallest class whose higher classes
+// hold at most `risk`; the last class if none does.
+__device__ __forceinline__ int risk_class(const float (&p)[kC], float risk) {
+    float above = 1.f;  // probability of the classes above c
+    for (int c = 0; c < kC; ++c) {
+        above -= p[c];
+        if (above <= risk) return c;
+    }
+    return kC - 1;
+}
+
+// An ensemble of n_nets > 1 networks (parameter sets P + m P2S_MLP_PARAMS): each sample's
+// class probabilities are the mean of the networks' softmax outputs, summed in `acc` (the
+// caller's logits array, [E][kC]) one network after the other, then the rule (risk > 0) or
+// the argmax decides and acc receives the log of the mean probabilities.  Each thread of a
+// CTA owns the same samples in every pass, so the sums need no synchronisation and are
+// reproducible.
+__device__ void mlp_predict_ensemble(const float* __restrict__ P, int n_nets, const float* __restrict__ feat,
+                                     int64_t E, int margin, float risk, int32_t* __restrict__ npts,
+                                     float* __restrict__ acc, MlpSmem& S) {
+    const int G[kC] = {8, 12, 16, 24, 32, 48};
+    for (int m = 0; m < n_nets; ++m) {
+        __syncthreads();
+        mlp_load_weights(P + (size_t)m * P2S_MLP_PARAMS, S);
+        for (int64_t e0 = (int64_t)blockIdx.x * kS; e0 < E; e0 += (int64_t)gridDim.x * kS) {
+            const int ns = (int)(E - e0 < kS ? E - e0 : kS);
+            __syncthreads();
+            for (int i = threadIdx.x; i < kS * kIn; i += blockDim.x)
+                S.X[i] = i < ns * kIn ? feat[e0 * kIn + i] : 0.f;
+            __syncthreads();
+            mlp_forward(S, ns);
+            if (threadIdx.x < ns) {
+                const int s = threadIdx.x;
+                float mx = S.Z[s * kC];
+                for (int c = 1; c < kC; ++c) mx = fmaxf(mx, S.Z[s * kC + c]);
+                float pr[kC], tot = 0.f;
+                for (int c = 0; c < kC; ++c) tot += (pr[c] = expf(S.Z[s * kC + c] - mx));
+                float* a = acc + (e0 + s) * kC;
+                for (int c = 0; c < kC; ++c) a[c] = (m ? a[c] : 0.f) + pr[c] / tot;
+            }
+        }
+    }
+    for (int64_t e0 = (int64_t)blockIdx.x * kS; e0 < E; e0 += (int64_t)gridDim.x * kS) {
+        const int ns = (int)(E - e0 < kS ? E - e0 : kS);
+        if (threadIdx.x < ns) {
+            float* a = acc + (e0 + threadIdx.x) * kC;
+            float p[kC];
+            int best = 0;
+            for (int c = 0; c < kC; ++c) {
+                p[c] = a[c] / (float)n_nets;
+                if (p[c] > p[best]) best = c;
+            }
+            if (risk > 0.f) best = risk_class(p, risk);
+            npts[e0 + threadIdx.x] = G[min(best + margin, kC - 1)];
+            for (int c = 0; c < kC; ++c) a[c] = logf(p[c]);
+        }
+    }
+}
+
 // Decision: with risk > 0 the smallest class whose higher classes hold at most `risk`
-// of the softmax probability; otherwise the argmax.  Then `margin` classes up.
-__global__ void __launch_bounds__(kThr) k_mlp_predict(const float* __restrict__ P, const float* __restrict__ feat,
-                                                      int64_t E, int margin, float risk, int32_t* __restrict__ npts,
+// of the softmax probability; otherwise the argmax.  Then `margin` classes up.  With
+// n_nets > 1, the mean probabilities of an ensemble decide (mlp_predict_ensemble).
+__global__ void __launch_bounds__(kThr) k_mlp_predict(const float* __restrict__ P, int n_nets,
+                                                      const float* __restrict__ feat, int64_t E, int margin,
+                                                      float risk, int32_t* __restrict__ npts,
                                                       float* __restrict__ logits) {
     extern __shared__ __align__(16) unsigned char sm[];
     MlpSmem S = mlp_carve(sm);
+    if (n_nets > 1) {
+        mlp_predict_ensemble(P, n_nets, feat, E, margin, risk, npts, logits, S);
+        return;
+    }
     mlp_load_weights(P, S);
     const int G[kC] = {8, 12, 16, 24, 32, 48};
     for (int64_t e0 = (int64_t)blockIdx.x * kS; e0 < E; e0 += (int64_t)gridDim.x * kS) {
@@ -506,17 +571,25 @@ int p2s_coarse_features(p2s_ctx* ctx, const p2s_geometry* geom, const p2s_materi
     return P2S_OK;
 }
 
-int p2s_mlp_predict(p2s_ctx* ctx, const float* params, const float* features, int64_t n, int margin, float risk,
-                    int32_t* npts, float* logits, void* stream) {
+int p2s_mlp_predict_ensemble(p2s_ctx* ctx, const float* params, int n_nets, const float* features, int64_t n,
+                             int margin, float risk, int32_t* npts, float* logits, void* stream) {
     const DeviceTables* T = context_tables(ctx);
-    if (!T || n < 0 || margin < 0 || !(risk >= 0.f) || risk >= 1.f) return fail(P2S_ERR_ARG, "p2s_mlp_predict: bad argument");
+    if (!T || n < 0 || margin < 0 || !(risk >= 0.f) || risk >= 1.f || n_nets < 1 || n_nets > P2S_MLP_MAX_NETS)
+        return fail(P2S_ERR_ARG, "p2s_mlp_predict: bad argument");
     if (n == 0) return P2S_OK;
-    if (!params || !features || !npts) return fail(P2S_ERR_ARG, "p2s_mlp_predict: NULL array");
+    if (!params || !features || !npts || (n_nets > 1 && !logits))
+        return fail(P2S_ERR_ARG, "p2s_mlp_predict: NULL array (an ensemble needs logits)");
     P2S_LCUDA(cudaSetDevice(T->device));
     const int grid = (int)std::min<int64_t>((n + kS - 1) / kS, (int64_t)T->sm_count);
-    k_mlp_predict<<<grid, kThr, kMlpSmem, (cudaStream_t)stream>>>(params, features, n, margin, risk, npts, logits);
+    k_mlp_predict<<<grid, kThr, kMlpSmem, (cudaStream_t)stream>>>(params, n_nets, features, n, margin, risk, npts,
+                                                                   logits);
     P2S_LCUDA(cudaGetLastError());
     return P2S_OK;
+}
+
+int p2s_mlp_predict(p2s_ctx* ctx, const float* params, const float* features, int64_t n, int margin, float risk,
+                    int32_t* npts, float* logits, void* stream) {
+    return p2s_mlp_predict_ensemble(ctx, params, 1, features, n, margin, risk, npts, logits, stream);
 }
 
 int p2s_mlp_grad(p2s_ctx* ctx, const float* params, const float* features, const int32_t* labels, int64_t batch,
@@ -673,6 +746,8 @@ struct p2s_learned_plan {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int32_t* order = nullptr;  // the main plan's moment-queue order (owned by the main plan)
+    int n_nets = 1;              // networks of the prediction
+    float* d_logits = nullptr;   // [E][6] probability sums of an ensemble's prediction
 };
 
 extern "C" {
@@ -694,6 +769,7 @@ void p2s_learned_plan_destroy(p2s_learned_plan* L) {
     cudaFree(L->d_mask);
     cudaFree(L->d_jerr);
     cudaFree(L->d_report);
+    cudaFree(L->d_logits);
     if (L->side) cudaStreamSynchronize(L->side);
     if (L->ev_fork) cudaEventDestroy(L->ev_fork);
     if (L->ev_join) cudaEventDestroy(L->ev_join);
@@ -708,8 +784,8 @@ int p2s_learned_plan_create(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, c
     *out = nullptr;
     if (orders->n_comp != 3) return fail(P2S_ERR_ARG, "p2s_learned_plan_create: the learned fill needs three components");
     if (opts->margin < 0 || opts->judge_frac < 0 || opts->judge_frac > 1 || !(opts->judge_tol >= 0) ||
-        !(opts->risk >= 0.0) || opts->risk >= 1.0)
-        return fail(P2S_ERR_ARG, "p2s_learned_plan_create: bad margin, judge fraction or tolerance");
+        !(opts->risk >= 0.0) || opts->risk >= 1.0 || opts->n_nets < 0 || opts->n_nets > P2S_MLP_MAX_NETS)
+        return fail(P2S_ERR_ARG, "p2s_learned_plan_create: bad margin, judge fraction, tolerance or network count");
     P2S_LCUDA(cudaSetDevice(T->device));
     p2s_learned_plan* L = new (std::nothrow) p2s_learned_plan();
     if (!L) return fail(P2S_ERR_OOM, "p2s_learned_plan_create: host allocation");
@@ -718,6 +794,7 @@ int p2s_learned_plan_create(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, c
     L->margin = opts->margin;
     L->risk = (float)opts->risk;
     L->tol = opts->judge_tol;
+    L->n_nets = opts->n_nets > 1 ? opts->n_nets : 1;
     p2s_quadrature q48 = {48, nullptr};
     p2s_fill_opts fo = {opts->precision, P2S_TYPES_ALL};
     int rc = p2s_plan_create(ctx, E, orders, &q48, &fo, &L->main);
@@ -749,7 +826,9 @@ int p2s_learned_plan_create(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, c
     rc = p2s_plan_create(ctx, L->nJ, &jo, &q48, &ff, &L->fallback);
     if (rc) { p2s_learned_plan_destroy(L); return rc; }
     const int64_t jent = p2s_output_entries(L->nJ, &jo, P2S_TYPES_ALL, off_j.data());
-    bool ok = cudaMalloc(&L->d_feat, sizeof(float) * kIn * std::max<int64_t>(E, 1)) == cudaSuccess &&
+    bool ok = (L->n_nets == 1 ||
+               cudaMalloc(&L->d_logits, sizeof(float) * kC * std::max<int64_t>(E, 1)) == cudaSuccess) &&
+              cudaMalloc(&L->d_feat, sizeof(float) * kIn * std::max<int64_t>(E, 1)) == cudaSuccess &&
               cudaMalloc(&L->d_npts, sizeof(int32_t) * std::max<int64_t>(E, 1)) == cudaSuccess &&
               cudaMalloc(&L->d_jidx, sizeof(int32_t) * std::max<int64_t>(L->nJ, 1)) == cudaSuccess &&
               cudaMalloc(&L->d_off_main, sizeof(int64_t) * (L->nJ + 1)) == cudaSuccess &&
@@ -815,7 +894,9 @@ int p2s_learned_fill(p2s_learned_plan* L, const p2s_geometry* geom, const p2s_ma
     }
     nvtxRangePushA("p2s learned: features, prediction, class order");
     int rc = p2s_coarse_features(L->ctx, geom, mat, L->d_feat, stream);
-    if (rc == P2S_OK) rc = p2s_mlp_predict(L->ctx, params, L->d_feat, L->E, L->margin, L->risk, L->d_npts, nullptr, stream);
+    if (rc == P2S_OK)
+        rc = p2s_mlp_predict_ensemble(L->ctx, params, L->n_nets, L->d_feat, L->E, L->margin, L->risk, L->d_npts,
+                                      L->d_logits, stream);
     if (rc == P2S_OK) {
         const int gs = (int)std::min<int64_t>((L->E + 255) / 256, 1024);
         k_set_npts<<<gs, 256, 0, s>>>(plan_desc(L->main), L->d_npts, L->E, L->d_report + 2);

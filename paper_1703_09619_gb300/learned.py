@@ -119,11 +119,22 @@ def train(ctx, feats, labels, epochs=300, batch=512, lr=2e-3, class_weight=None,
     return P.cpu().numpy(), history
 
 
+def n_nets_of(params):
+    """Networks in a parameter array (one set of MLP_PARAMS values each, one after another)."""
+    n, r = divmod(int(np.asarray(params).size), p2s.MLP_PARAMS)
+    assert r == 0 and n >= 1, "parameters are whole networks"
+    return n
+
+
 def predict(ctx, params, feats, margin=0, risk=0.0):
+    """G per element by the network, or by the ensemble when params holds several networks
+    (mean of their softmax probabilities)."""
     torch = _torch()
     P = torch.as_tensor(params, dtype=torch.float32, device=feats.device)
     npts = torch.empty(feats.shape[0], dtype=torch.int32, device=feats.device)
-    p2s.mlp_predict(ctx, P, feats, npts, margin, risk=risk)
+    n = n_nets_of(params)
+    logits = torch.empty((feats.shape[0], p2s.MLP_CLASSES), dtype=torch.float32, device=feats.device) if n > 1 else None
+    p2s.mlp_predict(ctx, P, feats, npts, margin, logits=logits, risk=risk, n_nets=n)
     return npts.cpu().numpy()
 
 
@@ -195,7 +206,8 @@ def learned_errors(ctx, params, wl, risk, margin=0, ref=None, device="cuda"):
         plan = p2s.Plan(ctx, wl.orders, CLASS_NPTS[-1], p2s.FP64)
         plan.fill(wl.kind, prm, nodes, bulge, ref)
         plan.close()
-    lp = p2s.LearnedPlan(ctx, wl.orders, margin=margin, precision=p2s.MIXED, judge_frac=0.0, seed=1, risk=risk)
+    lp = p2s.LearnedPlan(ctx, wl.orders, margin=margin, precision=p2s.MIXED, judge_frac=0.0, seed=1, risk=risk,
+                         n_nets=n_nets_of(params))
     out = torch.empty(n, dtype=torch.float64, device=device)
     npts = torch.empty(wl.n_elem, dtype=torch.int32, device=device)
     lp.fill(wl.kind, prm, nodes, bulge, P, out, npts)
@@ -275,6 +287,18 @@ if __name__ == "__main__":
         meta["risk"], meta["risk_calibration"] = calibrate_risk(ctx, params)
         meta["evaluation"] = evaluate(ctx, params, meta["risk"])
         save(rest[0] if rest else CHECKPOINT, params, meta)
+        print(json.dumps(meta))
+        sys.exit(0)
+    if "--ensemble" in sys.argv:  # --ensemble a.npz b.npz ... out.npz: the networks' mean probabilities
+        paths = [a for a in sys.argv[1:] if a != "--ensemble"]
+        members = [load_checkpoint(q) for q in paths[:-1]]
+        params = np.concatenate([P for P, _ in members])
+        keep = ("shards", "epochs", "cosine", "seed", "label_tol", "train_acc", "train_under", "evaluation", "risk")
+        meta = {"n_nets": len(members), "rule": "mean of the members' softmax probabilities",
+                "members": [{k: m.get(k) for k in keep} for _, m in members]}
+        meta["risk"], meta["risk_calibration"] = calibrate_risk(ctx, params)
+        meta["evaluation"] = evaluate(ctx, params, meta["risk"])
+        save(paths[-1], params, meta)
         print(json.dumps(meta))
         sys.exit(0)
     # python -m paper_1703_09619_gb300.learned [--shards 0,2,3,4] [--epochs 60] [--cosine] [--balance] [--seed 0]

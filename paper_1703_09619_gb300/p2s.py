@@ -130,6 +130,8 @@ SIGNATURES = {
     "p2s_learned_npts": (ctypes.c_int, [ctypes.c_int]),
     "p2s_coarse_features": (ctypes.c_int, [_P, ctypes.POINTER(Geometry), ctypes.POINTER(Material), _P, _P]),
     "p2s_mlp_predict": (ctypes.c_int, [_P, _P, _P, _I64, ctypes.c_int, ctypes.c_float, _P, _P, _P]),
+    "p2s_mlp_predict_ensemble": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _I64, ctypes.c_int, ctypes.c_float, _P, _P,
+                                                _P]),
     "p2s_mlp_grad": (ctypes.c_int, [_P, _P, _P, _P, _I64, _P, _P, _P, _P]),
     "p2s_mlp_adam": (ctypes.c_int, [_P, _P, _P, _P, _I64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                     ctypes.c_float, ctypes.c_float, ctypes.c_int, _P]),
@@ -158,7 +160,7 @@ class Peaks(ctypes.Structure):
 class LearnedOpts(ctypes.Structure):
     _fields_ = [("margin", ctypes.c_int), ("risk", ctypes.c_double), ("precision", ctypes.c_int),
                 ("judge_frac", ctypes.c_double),
-                ("seed", ctypes.c_uint64), ("judge_tol", ctypes.c_double)]
+                ("seed", ctypes.c_uint64), ("judge_tol", ctypes.c_double), ("n_nets", ctypes.c_int)]
 
 
 class LearnedReport(ctypes.Structure):
@@ -560,10 +562,17 @@ def coarse_features(ctx: Context, kind, params, nodes, bulge, features, stream=N
                                       _stream(stream)), "p2s_coarse_features")
 
 
-def mlp_predict(ctx: Context, mlp_params, features, npts, margin=0, logits=None, risk=0.0, stream=None):
+def mlp_predict(ctx: Context, mlp_params, features, npts, margin=0, logits=None, risk=0.0, stream=None, n_nets=1):
+    """p2s_mlp_predict, or p2s_mlp_predict_ensemble for n_nets > 1 (mlp_params then holds n_nets
+    parameter sets one after another, and logits [n][6] is required)."""
     n = int(features.shape[0])
-    _check(load().p2s_mlp_predict(ctx.handle, _dptr(mlp_params), _dptr(features), n, int(margin), float(risk),
-                                  _dptr(npts), _dptr(logits), _stream(stream)), "p2s_mlp_predict")
+    if int(n_nets) == 1:
+        _check(load().p2s_mlp_predict(ctx.handle, _dptr(mlp_params), _dptr(features), n, int(margin), float(risk),
+                                      _dptr(npts), _dptr(logits), _stream(stream)), "p2s_mlp_predict")
+    else:
+        _check(load().p2s_mlp_predict_ensemble(ctx.handle, _dptr(mlp_params), int(n_nets), _dptr(features), n,
+                                               int(margin), float(risk), _dptr(npts), _dptr(logits),
+                                               _stream(stream)), "p2s_mlp_predict_ensemble")
 
 
 def mlp_grad(ctx: Context, mlp_params, features, labels, grad, loss, class_weight=None, stream=None):
@@ -595,12 +604,13 @@ class LearnedPlan:
     """A p2s_learned_plan: learned-order fill with its seeded 48-point FP64 judge."""
 
     def __init__(self, ctx: Context, orders, margin=0, precision=MIXED, judge_frac=0.02, seed=1, judge_tol=1e-9,
-                 risk=0.0):
+                 risk=0.0, n_nets=1):
         lib = load()
         self.ctx = ctx
         o, self._orders = _orders_struct(orders)
         self.n_elem = int(self._orders.shape[0])
-        opts = LearnedOpts(int(margin), float(risk), int(precision), float(judge_frac), int(seed), float(judge_tol))
+        opts = LearnedOpts(int(margin), float(risk), int(precision), float(judge_frac), int(seed), float(judge_tol),
+                           int(n_nets))
         h = ctypes.c_void_p()
         _check(lib.p2s_learned_plan_create(ctx.handle, self.n_elem, ctypes.byref(o), ctypes.byref(opts),
                                            ctypes.byref(h)), "p2s_learned_plan_create")

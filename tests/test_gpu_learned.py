@@ -90,6 +90,33 @@ def test_predict_matches_oracle_argmax_and_margin(torch, ctx):
     assert (cls2[clear] == np.minimum(Z.argmax(axis=1)[clear] + 2, 5)).all()
 
 
+def test_ensemble_predict_matches_oracle(torch, ctx):
+    """Three networks through p2s_mlp_predict_ensemble: the log mean probabilities against the
+    oracle's ensemble (mean of the softmax outputs), and the class of the argmax and of the
+    risk rule wherever the decision is not within rounding of a tie or of the threshold."""
+    wl = W.make("c5", 300)
+    X = LN.features(ctx, wl)
+    Ps = [random_params(s) for s in (2, 5, 9)]
+    Pd = torch.as_tensor(np.concatenate(Ps), device="cuda")
+    npts = torch.empty(wl.n_elem, dtype=torch.int32, device="cuda")
+    logits = torch.empty((wl.n_elem, 6), dtype=torch.float32, device="cuda")
+    Pr = mlp.ensemble_probs([P.astype(np.float64) for P in Ps], X.cpu().numpy())
+    p2s.mlp_predict(ctx, Pd, X, npts, 0, logits=logits, n_nets=3)
+    assert np.max(np.abs(np.exp(logits.cpu().numpy()) - Pr)) < 1e-4
+    srt = np.sort(Pr, axis=1)
+    clear = srt[:, -1] - srt[:, -2] > 1e-3
+    assert (LN.classes_of(npts.cpu().numpy())[clear] == Pr.argmax(axis=1)[clear]).all()
+    for risk in (0.2, 0.01):
+        p2s.mlp_predict(ctx, Pd, X, npts, 1, logits=logits, risk=risk, n_nets=3)
+        tails = 1.0 - np.cumsum(Pr, axis=1)
+        clear = (np.abs(tails - risk) > 1e-4).all(axis=1)
+        want = np.minimum(mlp.risk_class(Pr, risk) + 1, 5)
+        assert clear.sum() > 200
+        assert (LN.classes_of(npts.cpu().numpy())[clear] == want[clear]).all(), risk
+    with pytest.raises(p2s.P2SError):  # an ensemble needs the logits array for its sums
+        p2s.mlp_predict(ctx, Pd, X, npts, 0, logits=None, n_nets=3)
+
+
 def test_adam_update(torch, ctx):
     rng = np.random.default_rng(5)
     n = 1000
@@ -228,7 +255,7 @@ def test_learned_fill_matches_oracle_multiclass(torch, ctx):
             break
     params, nodes, bulge = p2s.device_inputs(sub)
     lp = p2s.LearnedPlan(ctx, sub.orders, margin=0, precision=p2s.MIXED, judge_frac=0.5, seed=seed,
-                         judge_tol=1e-15, risk=RISK)
+                         judge_tol=1e-15, risk=RISK, n_nets=LN.n_nets_of(P))
     out = torch.full((lp.output_entries,), float("nan"), dtype=torch.float64, device="cuda")
     npts = torch.empty(E, dtype=torch.int32, device="cuda")
     lp.fill(sub.kind, params, nodes, bulge, torch.as_tensor(P, device="cuda"), out, npts)
