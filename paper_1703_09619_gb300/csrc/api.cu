@@ -410,6 +410,7 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
     int per_sm = dwm ? moments_dw_blocks_per_sm(L.mom_smem) : moments_blocks_per_sm(L.mom_smem);
     if (per_sm < 1) return fail(P2S_ERR_ORDER, "plan: moment kernel does not fit");
     L.mom_grid = (int)std::max<int64_t>(1, std::min<int64_t>(E, (int64_t)T.sm_count * per_sm));
+    L.split_grid = dwm ? 0 : T.sm_count * std::max(1, moments_split_blocks_per_sm(L.mom_smem));
 
     // contraction launch shape of the general kernel (a specialised kernel's shape replaces it below)
     if (moments_only) return P2S_OK;
@@ -455,8 +456,11 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
 
 int run_moments(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_desc, const p2s_geometry* geom,
                 const p2s_material* mat, void* moments, int32_t* elem_status, cudaStream_t s,
-                unsigned long long* counter, const int8_t* elem_mask, const int32_t* order) {
+                unsigned long long* counter, const int8_t* elem_mask, const int32_t* order, const MomentSplit* split) {
     if (elem_mask && PL.precision != P2S_FP64) return fail(P2S_ERR_ARG, "moments: element masks need an FP64 plan");
+    if (split && (PL.precision != P2S_FP64 || elem_status || !split->list || !split->count || !split->part ||
+                  split->grid < 1))
+        return fail(P2S_ERR_ARG, "moments: split launches need an FP64 plan, an element list and part buffers");
     if (!geom || !mat) return fail(P2S_ERR_ARG, "moments: NULL geometry or material");
     if (geom->n_elem != PL.n_elem) return fail(P2S_ERR_ARG, "moments: n_elem differs from the plan");
     if (PL.n_elem == 0) return P2S_OK;
@@ -489,6 +493,10 @@ int run_moments(const DeviceTables& T, const PlanLayout& PL, const ElemDesc* d_d
     M.counter = counter;
     M.order = order;
     NvtxRange range(M.out_ff ? "p2s moments a1+a2 (double word)" : "p2s moments a1+a2 (FP64)");
+    if (split) {
+        P2S_CUDA(launch_moments_fp64_split(M, *split, PL.mom_smem, s));
+        return P2S_OK;
+    }
     if (counter) P2S_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
     if (M.out_ff)
         P2S_CUDA(launch_moments_dw(M, PL.mom_grid, PL.mom_smem, s));
@@ -1153,11 +1161,16 @@ int32_t* plan_order(p2s_plan* p) {
 }
 
 int plan_fill_masked(p2s_plan* p, const p2s_geometry* geom, const p2s_material* mat, double* out,
-                     const int8_t* mask, cudaStream_t s) {
+                     const int8_t* mask, cudaStream_t s, const int32_t* list, const int* count, double* part) {
     if (!p) return fail(P2S_ERR_ARG, "plan_fill_masked: NULL plan");
+    MomentSplit sp = {list, count, part, p->Lm.split_grid};
     int rc = run_moments(p->ctx->T, p->Lm, p->d_mdesc, geom, mat, p->d_mom, nullptr, s, p->d_counter + 1, mask,
-                         p->d_order);
+                         p->d_order, list ? &sp : nullptr);
     if (rc) return rc;
     return run_contract(p->ctx->T, p->L, p->d_desc, p->d_units, p->d_counter, p->d_mom, out, s, mask);
+}
+
+size_t plan_split_part_doubles(const p2s_plan* p) {
+    return p ? moments_split_part_doubles(p->Lm.split_grid, p->Lm.n_pairs, p->Lm.kb) : 0;
 }
 }  // namespace p2s

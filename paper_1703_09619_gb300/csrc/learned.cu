@@ -692,30 +692,48 @@ __global__ void k_gather_inputs(const double* __restrict__ nodes, const double* 
     }
 }
 
-__global__ void k_judge_mask(const double* __restrict__ err, int64_t nJ, double tol, int8_t* __restrict__ mask) {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nJ; k += (int64_t)gridDim.x * blockDim.x)
-        mask[k] = !(err[k] <= tol);
+// The judged elements whose check failed: mask[k] = 1, and their indices in list[0 .. *count)
+// (in no particular order; *count zeroed by the caller) for the split fallback moments.
+__global__ void k_judge_mask(const double* __restrict__ err, int64_t nJ, double tol, int8_t* __restrict__ mask,
+                             int32_t* __restrict__ list, int* __restrict__ count) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nJ; k += (int64_t)gridDim.x * blockDim.x) {
+        const bool bad = !(err[k] <= tol);
+        mask[k] = bad;
+        if (bad) list[atomicAdd(count, 1)] = (int32_t)k;
+    }
 }
 
 // report: [0] judged, [1] failed, [2..7] per class, [8] max judged error (double bits).
-// Judged elements whose check failed take their 48-point FP64 fill (jout).
+// Judged elements whose check failed (list[0 .. *count), from k_judge_mask) take their 48-point
+// FP64 fill (jout): every CTA copies its share of each of them, so that a few failures still use
+// the whole grid.
 __global__ void k_judge_fix(double* __restrict__ out, const int64_t* __restrict__ off_main, const double* __restrict__ jout,
-                            const int64_t* __restrict__ off_j, const double* __restrict__ err, int64_t nJ, double tol,
+                            const int64_t* __restrict__ off_j, const double* __restrict__ err, int64_t nJ,
+                            const int32_t* __restrict__ list, const int* __restrict__ count,
                             unsigned long long* report) {
-    for (int64_t k = blockIdx.x; k < nJ; k += gridDim.x) {
-        const double ek = err[k];
-        const bool bad = !(ek <= tol);
+    const int nf = *count;
+    if (blockIdx.x == 0) {  // the report: block maximum of the error bits (non-negative doubles order as their bits)
+        __shared__ unsigned long long wmax[32];
+        unsigned long long mb = 0;
+        for (int64_t k = threadIdx.x; k < nJ; k += blockDim.x)
+            mb = max(mb, (unsigned long long)__double_as_longlong(err[k]));
+        for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+        if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mb;
+        __syncthreads();
         if (threadIdx.x == 0) {
-            atomicAdd(report + 0, 1ull);
-            if (bad) atomicAdd(report + 1, 1ull);
-            atomicMax(report + 8, (unsigned long long)__double_as_longlong(ek));
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mb = max(mb, wmax[w]);
+            report[0] = (unsigned long long)nJ;
+            report[1] = (unsigned long long)nf;
+            report[8] = mb;
         }
-        if (bad) {
-            const int64_t len = off_j[k + 1] - off_j[k];
-            double* dst = out + off_main[k];
-            const double* src = jout + off_j[k];
-            for (int64_t i = threadIdx.x; i < len; i += blockDim.x) dst[i] = src[i];
-        }
+    }
+    for (int f = 0; f < nf; ++f) {
+        const int64_t k = list[f];
+        const int64_t len = off_j[k + 1] - off_j[k];
+        double* dst = out + off_main[k];
+        const double* src = jout + off_j[k];
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+            dst[i] = src[i];
     }
 }
 
@@ -740,6 +758,9 @@ struct p2s_learned_plan {
     double* d_jout = nullptr;  // judge fill
     double* d_jfb = nullptr;   // plain-method fill of the judged elements that failed
     int8_t* d_mask = nullptr;  // [nJ] judged element failed
+    int32_t* d_flist = nullptr;  // [nJ] the failed judged elements, and their number (d_fcount)
+    int* d_fcount = nullptr;
+    double* d_fpart = nullptr;   // partial moments of the split fallback (plan_split_part_doubles)
     double* d_jerr = nullptr;
     unsigned long long* d_report = nullptr;
     // the judge's 48-point fill runs on a side stream, forked from and joined to the caller's
@@ -767,6 +788,9 @@ void p2s_learned_plan_destroy(p2s_learned_plan* L) {
     cudaFree(L->d_jout);
     cudaFree(L->d_jfb);
     cudaFree(L->d_mask);
+    cudaFree(L->d_flist);
+    cudaFree(L->d_fcount);
+    cudaFree(L->d_fpart);
     cudaFree(L->d_jerr);
     cudaFree(L->d_report);
     cudaFree(L->d_logits);
@@ -837,6 +861,10 @@ int p2s_learned_plan_create(p2s_ctx* ctx, int64_t E, const p2s_orders* orders, c
               cudaMalloc(&L->d_jout, sizeof(double) * std::max<int64_t>(jent, 1)) == cudaSuccess &&
               cudaMalloc(&L->d_jfb, sizeof(double) * std::max<int64_t>(jent, 1)) == cudaSuccess &&
               cudaMalloc(&L->d_mask, std::max<int64_t>(L->nJ, 1)) == cudaSuccess &&
+              cudaMalloc(&L->d_flist, sizeof(int32_t) * std::max<int64_t>(L->nJ, 1)) == cudaSuccess &&
+              cudaMalloc(&L->d_fcount, sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&L->d_fpart, sizeof(double) * std::max<size_t>(plan_split_part_doubles(L->fallback), 1)) ==
+                  cudaSuccess &&
               cudaMalloc(&L->d_jerr, sizeof(double) * std::max<int64_t>(L->nJ, 1)) == cudaSuccess &&
               cudaMalloc(&L->d_report, sizeof(unsigned long long) * 16) == cudaSuccess;
     if (!ok) { p2s_learned_plan_destroy(L); return fail(P2S_ERR_OOM, "p2s_learned_plan_create: device allocation"); }
@@ -920,11 +948,14 @@ int p2s_learned_fill(p2s_learned_plan* L, const p2s_geometry* geom, const p2s_ma
         rc = p2s_element_errors(L->ctx, out, L->d_off_main, L->d_jout, L->d_off_j, L->nJ, 4, L->d_jerr, stream);
         if (rc) return rc;
         // judged elements above the tolerance: their plain-method fill, then the copy into out
-        k_judge_mask<<<(int)std::min<int64_t>((L->nJ + 255) / 256, 1024), 256, 0, s>>>(L->d_jerr, L->nJ, L->tol, L->d_mask);
+        P2S_LCUDA(cudaMemsetAsync(L->d_fcount, 0, sizeof(int), s));
+        k_judge_mask<<<(int)std::min<int64_t>((L->nJ + 255) / 256, 1024), 256, 0, s>>>(L->d_jerr, L->nJ, L->tol, L->d_mask,
+                                                                                     L->d_flist, L->d_fcount);
         P2S_LCUDA(cudaGetLastError());
-        rc = plan_fill_masked(L->fallback, &g2, &m2, L->d_jfb, L->d_mask, s);
+        rc = plan_fill_masked(L->fallback, &g2, &m2, L->d_jfb, L->d_mask, s, L->d_flist, L->d_fcount, L->d_fpart);
         if (rc) return rc;
-        k_judge_fix<<<gj, 256, 0, s>>>(out, L->d_off_main, L->d_jfb, L->d_off_j, L->d_jerr, L->nJ, L->tol, L->d_report);
+        k_judge_fix<<<gj, 256, 0, s>>>(out, L->d_off_main, L->d_jfb, L->d_off_j, L->d_jerr, L->nJ, L->d_flist, L->d_fcount,
+                                       L->d_report);
         P2S_LCUDA(cudaGetLastError());
     }
     return P2S_OK;

@@ -100,6 +100,19 @@ struct MomentLaunch {
 };
 size_t moments_smem_bytes(int n_pairs, int kb, int gmax, int iacc_cap);
 cudaError_t launch_moments_fp64(const MomentLaunch& L, int grid, size_t smem, cudaStream_t s);
+// FP64 moments of a device-side list of elements (*count of them), each cut into parts of its
+// w-planes so that a few elements still occupy `grid` CTAs; the parts' accumulators go to `part`
+// (moments_split_part_doubles(grid, ...) doubles) and a second kernel sums them in part order.
+// The launch needs elem_status == nullptr and FP64 moments (out_ff == 0).
+struct MomentSplit {
+    const int32_t* list;
+    const int* count;
+    double* part;
+    int grid;
+};
+size_t moments_split_part_doubles(int grid, int n_pairs, int kb);
+int moments_split_blocks_per_sm(size_t smem);
+cudaError_t launch_moments_fp64_split(const MomentLaunch& L, const MomentSplit& Sp, size_t smem, cudaStream_t s);
 // moments_dw.cu: the same step in double-word arithmetic (mixed path; writes (hi, lo) pairs)
 size_t moments_dw_smem_bytes(int n_pairs, int kb, int gmax, int iacc_cap);
 int moments_dw_iacc_words(int n_pairs, int max_pair);
@@ -232,6 +245,7 @@ struct PlanLayout {
     int n_pairs = 1, kb = 1, gmax = 1, iacc_cap = 0;
     size_t mom_smem = 0;
     int mom_grid = 1;
+    int split_grid = 0;  // FP64 plans: resident CTAs of the split moment kernel on the whole GPU
     size_t a_cap = 1, b_cap = 1, tile_cap = 1, combo_cap = 1, s1_cap = 0;
     int con_threads = 256;
     size_t con_smem = 0, tile_off = 0;
@@ -279,7 +293,8 @@ int build_layout(const DeviceTables& T, int64_t E, const p2s_orders* orders, con
 // `order` (device [E], optional): the order in which the queue hands out elements.
 int run_moments(const DeviceTables& T, const PlanLayout& L, const ElemDesc* d_desc, const p2s_geometry* geom,
                 const p2s_material* mat, void* moments, int32_t* elem_status, cudaStream_t s,
-                unsigned long long* counter, const int8_t* elem_mask = nullptr, const int32_t* order = nullptr);
+                unsigned long long* counter, const int8_t* elem_mask = nullptr, const int32_t* order = nullptr,
+                const MomentSplit* split = nullptr);
 // Device arrays of an operator plan's term list (see ContractLaunch).
 struct OpArrays {
     const int32_t* terms;
@@ -319,8 +334,13 @@ int plan_spec_op(const p2s_plan* p);
 int plan_run_moments(p2s_plan* p, const p2s_geometry* geom, const p2s_material* mat, cudaStream_t s);
 int plan_op_launch(p2s_plan* p, ContractLaunch& C);
 unsigned long long* plan_counter(p2s_plan* p);
+// With `list` and `count` (device: the masked elements and their number) and `part` (device,
+// plan_split_part_doubles(p) doubles), the moments of the masked elements run split over the
+// whole GPU (launch_moments_fp64_split) rather than one CTA per element.
 int plan_fill_masked(p2s_plan* p, const p2s_geometry* geom, const p2s_material* mat, double* out,
-                     const int8_t* mask, cudaStream_t s);
+                     const int8_t* mask, cudaStream_t s, const int32_t* list = nullptr, const int* count = nullptr,
+                     double* part = nullptr);
+size_t plan_split_part_doubles(const p2s_plan* p);
 cudaError_t learned_init_attributes();
 
 }  // namespace p2s

@@ -198,10 +198,47 @@ def test_judge_replaces_planted_mispredictions(torch, ctx):
     for e in range(wl.n_elem):
         sl = slice(off[e], off[e + 1])
         if st[e] == 2:
-            assert np.array_equal(o[sl], r48[sl])
+            # the plain method; its sums over w-planes split over CTAs when few elements fail
+            assert np.abs(o[sl] - r48[sl]).max() <= 1e-13 * np.abs(r48[sl]).max()
         else:
             assert np.array_equal(o[sl], r8[sl])
     lp.close()
+
+
+@pytest.mark.parametrize("n_elem,frac", [(16, 0.5), (96, 1.0), (600, 1.0)])
+def test_fallback_split_matches_plain_fill(torch, ctx, n_elem, frac):
+    """Every judged element fails (a tolerance no fill meets), so the fallback fills all of
+    them: with few failures each element's w-planes are cut into parts on separate CTAs and
+    the parts' sums are added in part order (within FP64 rounding of the plain fill); with
+    more failures than half the moment grid each element keeps one CTA and the result is the
+    plain 48-point FP64 fill bit for bit."""
+    wl = W.make("c5", n_elem)
+    params, nodes, bulge = p2s.device_inputs(wl)
+    P = np.zeros(p2s.MLP_PARAMS, dtype=np.float32)
+    P[-6] = 10.0  # every element at G = 8
+    lp = p2s.LearnedPlan(ctx, wl.orders, margin=0, precision=p2s.MIXED, judge_frac=frac, seed=5, judge_tol=1e-300)
+    out = torch.empty(lp.output_entries, dtype=torch.float64, device="cuda")
+    npts = torch.empty(wl.n_elem, dtype=torch.int32, device="cuda")
+    lp.fill(wl.kind, params, nodes, bulge, torch.as_tensor(P, device="cuda"), out, npts)
+    rep = lp.report(judge_state=True)
+    st = rep["judge_state"]
+    lp.close()
+    assert rep["judged"] == int(p2s.judge_select(n_elem, frac, 5).sum()) > 0
+    assert rep["failed"] == rep["judged"] == int((st == 2).sum())
+    ref = torch.empty_like(out)
+    p2s.Plan(ctx, wl.orders, 48, p2s.FP64).fill(wl.kind, params, nodes, bulge, ref)
+    torch.cuda.synchronize()
+    _, off = p2s.output_entries(wl.orders, offsets=True)
+    o, r = out.cpu().numpy(), ref.cpu().numpy()
+    # 600 failures: more than half the split moment kernel's grid (152 SMs x 2 or 3 resident CTAs), one part each
+    whole = rep["failed"] >= 600
+    worst = 0.0
+    for e in np.flatnonzero(st == 2):
+        sl = slice(off[e], off[e + 1])
+        if whole:
+            assert np.array_equal(o[sl], r[sl]), e
+        worst = max(worst, np.abs(o[sl] - r[sl]).max() / np.abs(r[sl]).max())
+    assert worst <= 1e-13, worst
 
 
 def test_training_gains_over_uniform_rule(torch, ctx):
