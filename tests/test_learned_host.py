@@ -38,7 +38,10 @@ def test_classes_of_inverts_the_class_table():
 
 def test_committed_checkpoint_carries_its_calibration():
     P, meta = LN.load_checkpoint()
-    assert P.shape == (41478,)
+    n = meta.get("n_nets", 1)  # an ensemble stores its networks one after another
+    assert 1 <= n <= 8 and P.shape == (n * 41478,) and LN.n_nets_of(P) == n
+    if n > 1:
+        assert len(meta["members"]) == n
     cal = meta["risk_calibration"]
     assert meta["risk"] == LN.choose_risk(cal["sweep"])
     assert cal["tol"] <= 1e-8 and "shard 1" in cal["holdout"]
