@@ -161,17 +161,19 @@ struct MlpSmem {
 constexpr size_t kMlpSmem = sizeof(__half) * kIn * kH + sizeof(float) * (kH * kH + kH * kC + 2 * kH + kC + kS * kIn +
                                                                           2 * kS * kH + kS * kC);
 
+// W1, then the row-major activations X, H1, H2 (each row 16-byte aligned for float4 reads),
+// then W2 (8-byte pairs), W3, the biases and Z.
 __device__ MlpSmem mlp_carve(unsigned char* sm) {
     MlpSmem S;
     S.W1 = reinterpret_cast<__half*>(sm);
     float* f = reinterpret_cast<float*>(sm + sizeof(__half) * kIn * kH);
-    S.W2 = f;
-    S.W3 = S.W2 + kH * kH;
-    S.b = S.W3 + kH * kC;
-    S.X = S.b + 2 * kH + kC;
+    S.X = f;
     S.H1 = S.X + kS * kIn;
     S.H2 = S.H1 + kS * kH;
-    S.Z = S.H2 + kS * kH;
+    S.W2 = S.H2 + kS * kH;
+    S.W3 = S.W2 + kH * kH;
+    S.b = S.W3 + kH * kC;
+    S.Z = S.b + 2 * kH + kC;
     return S;
 }
 
@@ -188,34 +190,79 @@ __device__ void mlp_load_weights(const float* __restrict__ P, MlpSmem& S) {
     if (threadIdx.x < kC) S.b[2 * kH + threadIdx.x] = P[oB3 + threadIdx.x];
 }
 
-// H1, H2 (post-ReLU) and logits Z for the ns samples in S.X.
+// H1, H2 (post-ReLU) and logits Z for the ns samples in S.X.  In the two hidden layers each
+// thread owns two neighbouring outputs j = 2 jp, 2 jp + 1 of four samples sg + 8 k: per four
+// inputs it reads four weight pairs and one float4 of each sample's row (the same row across
+// a warp, a broadcast).  Every output still accumulates its inputs in order 0, 1, 2, ... with
+// one FMA each, so the results do not depend on this blocking.
 __device__ void mlp_forward(MlpSmem& S, int ns) {
     const int t = threadIdx.x;
-    const int j = t & (kH - 1), g = t / kH;  // 4 groups of 64 threads, 8 samples each
+    const int jp = t & 31, sg = t >> 5;  // 8 warps: samples sg, sg + 8, sg + 16, sg + 24
+    static_assert(kThr == 256 && kS == 32 && kH == 64 && kIn % 4 == 0, "forward blocking");
     {
-        float acc[8];
+        const __half2* W1 = reinterpret_cast<const __half2*>(S.W1);  // [576][32] pairs
+        float a0[4], a1[4];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] = S.b[j];
-        for (int i = 0; i < kIn; ++i) {
-            const float w = __half2float(S.W1[i * kH + j]);
+        for (int k = 0; k < 4; ++k) {
+            a0[k] = S.b[2 * jp];
+            a1[k] = S.b[2 * jp + 1];
+        }
+        for (int i = 0; i < kIn; i += 4) {
+            float2 w[4];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) acc[k] = fmaf(S.X[(g + 4 * k) * kIn + i], w, acc[k]);
+            for (int u = 0; u < 4; ++u) w[u] = __half22float2(W1[(i + u) * (kH / 2) + jp]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float4 x = *reinterpret_cast<const float4*>(S.X + (sg + 8 * k) * kIn + i);
+                a0[k] = fmaf(x.x, w[0].x, a0[k]);
+                a1[k] = fmaf(x.x, w[0].y, a1[k]);
+                a0[k] = fmaf(x.y, w[1].x, a0[k]);
+                a1[k] = fmaf(x.y, w[1].y, a1[k]);
+                a0[k] = fmaf(x.z, w[2].x, a0[k]);
+                a1[k] = fmaf(x.z, w[2].y, a1[k]);
+                a0[k] = fmaf(x.w, w[3].x, a0[k]);
+                a1[k] = fmaf(x.w, w[3].y, a1[k]);
+            }
         }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) S.H1[(g + 4 * k) * kH + j] = (g + 4 * k) < ns ? fmaxf(acc[k], 0.f) : 0.f;
+        for (int k = 0; k < 4; ++k) {
+            const int sm = sg + 8 * k;
+            *reinterpret_cast<float2*>(S.H1 + sm * kH + 2 * jp) =
+                sm < ns ? make_float2(fmaxf(a0[k], 0.f), fmaxf(a1[k], 0.f)) : make_float2(0.f, 0.f);
+        }
     }
     __syncthreads();
     {
-        float acc[8];
+        const float2* W2 = reinterpret_cast<const float2*>(S.W2);  // [64][32] pairs
+        float a0[4], a1[4];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] = S.b[kH + j];
-        for (int i = 0; i < kH; ++i) {
-            const float w = S.W2[i * kH + j];
+        for (int k = 0; k < 4; ++k) {
+            a0[k] = S.b[kH + 2 * jp];
+            a1[k] = S.b[kH + 2 * jp + 1];
+        }
+        for (int i = 0; i < kH; i += 4) {
+            float2 w[4];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) acc[k] = fmaf(S.H1[(g + 4 * k) * kH + i], w, acc[k]);
+            for (int u = 0; u < 4; ++u) w[u] = W2[(i + u) * (kH / 2) + jp];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float4 h = *reinterpret_cast<const float4*>(S.H1 + (sg + 8 * k) * kH + i);
+                a0[k] = fmaf(h.x, w[0].x, a0[k]);
+                a1[k] = fmaf(h.x, w[0].y, a1[k]);
+                a0[k] = fmaf(h.y, w[1].x, a0[k]);
+                a1[k] = fmaf(h.y, w[1].y, a1[k]);
+                a0[k] = fmaf(h.z, w[2].x, a0[k]);
+                a1[k] = fmaf(h.z, w[2].y, a1[k]);
+                a0[k] = fmaf(h.w, w[3].x, a0[k]);
+                a1[k] = fmaf(h.w, w[3].y, a1[k]);
+            }
         }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) S.H2[(g + 4 * k) * kH + j] = (g + 4 * k) < ns ? fmaxf(acc[k], 0.f) : 0.f;
+        for (int k = 0; k < 4; ++k) {
+            const int sm = sg + 8 * k;
+            *reinterpret_cast<float2*>(S.H2 + sm * kH + 2 * jp) =
+                sm < ns ? make_float2(fmaxf(a0[k], 0.f), fmaxf(a1[k], 0.f)) : make_float2(0.f, 0.f);
+        }
     }
     __syncthreads();
     if (t < kS * kC) {
