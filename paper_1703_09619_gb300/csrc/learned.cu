@@ -190,6 +190,30 @@ __device__ void mlp_load_weights(const float* __restrict__ P, MlpSmem& S) {
     if (threadIdx.x < kC) S.b[2 * kH + threadIdx.x] = P[oB3 + threadIdx.x];
 }
 
+// The features of samples e0 .. e0 + ns - 1 into S.X, zero rows after them.  Every thread
+// issues all of its loads before its first store (18 float4 per thread when the rows are
+// 16-byte aligned), so one memory latency covers the whole chunk even at one CTA per SM.
+__device__ __forceinline__ void mlp_load_x(MlpSmem& S, const float* __restrict__ feat, int64_t e0, int ns) {
+    static_assert((kS * kIn) % (4 * kThr) == 0, "feature chunk in whole float4 rounds");
+    constexpr int kR = kS * kIn / (4 * kThr);
+    const float* src = feat + e0 * kIn;
+    const int lim = ns * kIn;
+    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        const float4* s4 = reinterpret_cast<const float4*>(src);
+        float4 v[kR];
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            const int i = r * kThr + threadIdx.x;
+            v[r] = 4 * i < lim ? __ldg(s4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        float4* d4 = reinterpret_cast<float4*>(S.X);
+#pragma unroll
+        for (int r = 0; r < kR; ++r) d4[r * kThr + threadIdx.x] = v[r];
+    } else {
+        for (int i = threadIdx.x; i < kS * kIn; i += blockDim.x) S.X[i] = i < lim ? src[i] : 0.f;
+    }
+}
+
 // H1, H2 (post-ReLU) and logits Z for the ns samples in S.X.  In the two hidden layers each
 // thread owns two neighbouring outputs j = 2 jp, 2 jp + 1 of four samples sg + 8 k: per four
 // inputs it reads four weight pairs and one float4 of each sample's row (the same row across
@@ -301,8 +325,7 @@ __device__ void mlp_predict_ensemble(const float* __restrict__ P, int n_nets, co
         for (int64_t e0 = (int64_t)blockIdx.x * kS; e0 < E; e0 += (int64_t)gridDim.x * kS) {
             const int ns = (int)(E - e0 < kS ? E - e0 : kS);
             __syncthreads();
-            for (int i = threadIdx.x; i < kS * kIn; i += blockDim.x)
-                S.X[i] = i < ns * kIn ? feat[e0 * kIn + i] : 0.f;
+            mlp_load_x(S, feat, e0, ns);
             __syncthreads();
             mlp_forward(S, ns);
             if (threadIdx.x < ns) {
@@ -351,8 +374,7 @@ __global__ void __launch_bounds__(kThr) k_mlp_predict(const float* __restrict__ 
     for (int64_t e0 = (int64_t)blockIdx.x * kS; e0 < E; e0 += (int64_t)gridDim.x * kS) {
         const int ns = (int)(E - e0 < kS ? E - e0 : kS);
         __syncthreads();
-        for (int i = threadIdx.x; i < kS * kIn; i += blockDim.x)
-            S.X[i] = i < ns * kIn ? feat[e0 * kIn + i] : 0.f;
+        mlp_load_x(S, feat, e0, ns);
         __syncthreads();
         mlp_forward(S, ns);
         if (threadIdx.x < ns) {
@@ -390,7 +412,7 @@ __global__ void __launch_bounds__(kThr) k_mlp_grad(const float* __restrict__ P, 
     mlp_load_weights(P, S);
     const int64_t e0 = (int64_t)blockIdx.x * kS;
     const int ns = (int)(B - e0 < kS ? B - e0 : kS);
-    for (int i = threadIdx.x; i < kS * kIn; i += blockDim.x) S.X[i] = i < ns * kIn ? feat[e0 * kIn + i] : 0.f;
+    mlp_load_x(S, feat, e0, ns);
     __syncthreads();
     mlp_forward(S, ns);
     const int t = threadIdx.x;
@@ -499,9 +521,10 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
 
 // ------------------------------------------------------------------ per-element errors
 // One (element, type) per CTA of 256 threads, so that a few hundred judged elements still
-// spread over every SM; 16-byte loads (when both segments allow them) four deep per thread,
-// maxima reduced by warp shuffles.
-__global__ void __launch_bounds__(256) k_elem_err(const double* __restrict__ a, const int64_t* __restrict__ offa,
+// spread over every SM; at most 32 registers, so that the launch's 8 CTAs per SM are all
+// resident (a persistent CTA that starts late holds up its later items); 16-byte loads
+// (when both segments allow them) four deep per thread, maxima reduced by warp shuffles.
+__global__ void __launch_bounds__(256, 8) k_elem_err(const double* __restrict__ a, const int64_t* __restrict__ offa,
                                                   const double* __restrict__ b, const int64_t* __restrict__ offb,
                                                   int64_t E, int n_types, double* __restrict__ err) {
     // err[e] (zeroed by the launcher) takes the largest ratio of its types by an atomic
