@@ -269,6 +269,20 @@ def evaluate(ctx, params, risk, shard=9, n_elem=32768, tol=1e-8):
             "max_err": float(e.max()), "mean_G3": float(np.mean(g.astype(float) ** 3))}
 
 
+def combine_ensemble(members):
+    """Parameters and metadata of an ensemble of trained networks ((params, meta) pairs, each
+    params one network or an ensemble itself): the parameter sets one after another, and per
+    member its recipe and its own evaluation.  The risk is calibrated afterwards, on the
+    ensemble's mean probabilities."""
+    if not 2 <= sum(n_nets_of(P) for P, _ in members) <= p2s.MLP_MAX_NETS:
+        raise ValueError("an ensemble holds 2 to %d networks" % p2s.MLP_MAX_NETS)
+    params = np.concatenate([np.asarray(P, dtype=np.float32) for P, _ in members])
+    keep = ("shards", "epochs", "cosine", "seed", "label_tol", "train_acc", "train_under", "evaluation", "risk")
+    meta = {"n_nets": n_nets_of(params), "rule": "mean of the members' softmax probabilities",
+            "members": [{k: m.get(k) for k in keep} for _, m in members]}
+    return params, meta
+
+
 def ensure_trained(ctx, path=CHECKPOINT, verbose=False):
     """Load the committed checkpoint, or train one and save it."""
     if os.path.exists(path):
@@ -291,11 +305,7 @@ if __name__ == "__main__":
         sys.exit(0)
     if "--ensemble" in sys.argv:  # --ensemble a.npz b.npz ... out.npz: the networks' mean probabilities
         paths = [a for a in sys.argv[1:] if a != "--ensemble"]
-        members = [load_checkpoint(q) for q in paths[:-1]]
-        params = np.concatenate([P for P, _ in members])
-        keep = ("shards", "epochs", "cosine", "seed", "label_tol", "train_acc", "train_under", "evaluation", "risk")
-        meta = {"n_nets": len(members), "rule": "mean of the members' softmax probabilities",
-                "members": [{k: m.get(k) for k in keep} for _, m in members]}
+        params, meta = combine_ensemble([load_checkpoint(q) for q in paths[:-1]])
         meta["risk"], meta["risk_calibration"] = calibrate_risk(ctx, params)
         meta["evaluation"] = evaluate(ctx, params, meta["risk"])
         save(paths[-1], params, meta)

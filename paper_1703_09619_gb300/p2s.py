@@ -148,6 +148,7 @@ SIGNATURES = {
 MODE1_SIMT, MODE1_TC = 0, 1
 
 MLP_IN, MLP_HIDDEN, MLP_CLASSES, MLP_PARAMS = 576, 64, 6, 41478
+MLP_MAX_NETS = 8  # P2S_MLP_MAX_NETS: networks of one ensemble
 CLASS_NPTS = (8, 12, 16, 24, 32, 48)
 
 

@@ -1,8 +1,10 @@
 """Host logic of the learned order (no GPU): the risk rule's choice over a calibration sweep,
-the class weights and the class lookup."""
+the class weights, the class lookup and the assembly of an ensemble checkpoint."""
 import numpy as np
+import pytest
 
 from paper_1703_09619_gb300 import learned as LN
+from paper_1703_09619_gb300 import p2s
 
 
 def sweep(*rows):
@@ -46,3 +48,32 @@ def test_committed_checkpoint_carries_its_calibration():
     assert meta["risk"] == LN.choose_risk(cal["sweep"])
     assert cal["tol"] <= 1e-8 and "shard 1" in cal["holdout"]
     assert meta["evaluation"]["above_tol"] == 0
+
+
+def test_combine_ensemble_concatenates_members():
+    a = (LN.init_params(1), {"seed": 1, "epochs": 150, "risk": 0.001, "extra": "dropped"})
+    b = (LN.init_params(2), {"seed": 2, "epochs": 150, "risk": 0.0005})
+    P, meta = LN.combine_ensemble([a, b])
+    assert P.dtype == np.float32 and P.shape == (2 * p2s.MLP_PARAMS,)
+    assert np.array_equal(P[:p2s.MLP_PARAMS], a[0]) and np.array_equal(P[p2s.MLP_PARAMS:], b[0])
+    assert meta["n_nets"] == LN.n_nets_of(P) == 2
+    assert [m["seed"] for m in meta["members"]] == [1, 2] and "extra" not in meta["members"][0]
+    # an ensemble can take an ensemble as a member; sizes outside 2..MLP_MAX_NETS are refused
+    P3, meta3 = LN.combine_ensemble([(P, meta), (LN.init_params(3), {})])
+    assert meta3["n_nets"] == 3
+    with pytest.raises(ValueError):
+        LN.combine_ensemble([a])
+    with pytest.raises(ValueError):
+        LN.combine_ensemble([(LN.init_params(s), {}) for s in range(p2s.MLP_MAX_NETS + 1)])
+    with pytest.raises(AssertionError):
+        LN.n_nets_of(np.zeros(p2s.MLP_PARAMS + 1, dtype=np.float32))
+
+
+def test_binding_mlp_constants_match_header():
+    import os
+    import re
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "p2s.h")).read()
+    defs = dict(re.findall(r"#define\s+(P2S_MLP_\w+)\s+(\d+)", hdr))
+    assert int(defs["P2S_MLP_MAX_NETS"]) == p2s.MLP_MAX_NETS
+    assert int(defs["P2S_MLP_PARAMS"]) == p2s.MLP_PARAMS
+    assert int(defs["P2S_MLP_IN"]) == p2s.MLP_IN and int(defs["P2S_MLP_CLASSES"]) == p2s.MLP_CLASSES
