@@ -46,11 +46,6 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
-__device__ __forceinline__ double warp_max_d(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
 
 // Four elements per CTA, 64 threads (one coarse point each) per element.  The element
 // constants (the geo[] layout of alpha.cuh) are formed in FP64 by 27 threads of each element,
@@ -520,16 +515,30 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
 }
 
 // ------------------------------------------------------------------ per-element errors
+// |x| as the bit pattern of a non-negative double: such patterns order as the values, so the
+// maxima below run on the integer pipe (FP64 min/max would share the FP64 unit with the
+// subtraction, about 2 operations per clock per SM on this part).  A NaN entry orders above
+// every number, so it makes the element's error NaN, which fails every tolerance.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
 // One (element, type) per CTA of 256 threads, so that a few hundred judged elements still
 // spread over every SM; at most 32 registers, so that the launch's 8 CTAs per SM are all
 // resident (a persistent CTA that starts late holds up its later items); 16-byte loads
-// (when both segments allow them) four deep per thread, maxima reduced by warp shuffles.
+// (when both segments allow them) two deep per thread; one FP64 subtraction per entry,
+// the maxima on bit patterns, reduced by warp shuffles.
 __global__ void __launch_bounds__(256, 8) k_elem_err(const double* __restrict__ a, const int64_t* __restrict__ offa,
-                                                  const double* __restrict__ b, const int64_t* __restrict__ offb,
-                                                  int64_t E, int n_types, double* __restrict__ err) {
+                                                     const double* __restrict__ b, const int64_t* __restrict__ offb,
+                                                     int64_t E, int n_types, double* __restrict__ err) {
     // err[e] (zeroed by the launcher) takes the largest ratio of its types by an atomic
-    // maximum on the bit patterns (non-negative doubles order as their bits)
-    __shared__ double sd[8], sm[8];
+    // maximum on the bit patterns
+    __shared__ unsigned long long sd[8], sm[8];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int64_t it = blockIdx.x; it < E * n_types; it += gridDim.x) {
         const int64_t e = it / n_types;
@@ -537,55 +546,54 @@ __global__ void __launch_bounds__(256, 8) k_elem_err(const double* __restrict__ 
         const int64_t len = (offb[e + 1] - offb[e]) / n_types;
         const double* pa = a + offa[e] + t * len;
         const double* pb = b + offb[e] + t * len;
-        double d = 0.0, m = 0.0;
+        unsigned long long d = 0, m = 0;
         if (((reinterpret_cast<uintptr_t>(pa) | reinterpret_cast<uintptr_t>(pb)) & 15) == 0) {
             const double2* qa = reinterpret_cast<const double2*>(pa);
             const double2* qb = reinterpret_cast<const double2*>(pb);
             const int64_t n2 = len / 2;
             int64_t i = tid;
-            for (; i + 768 < n2; i += 1024) {
-                double2 va[4], vb[4];
+            for (; i + 256 < n2; i += 512) {
+                double2 va[2], vb[2];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < 2; ++j) {
                     va[j] = __ldcs(qa + i + 256 * j);
                     vb[j] = __ldcs(qb + i + 256 * j);
                 }
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    d = fmax(d, fmax(fabs(va[j].x - vb[j].x), fabs(va[j].y - vb[j].y)));
-                    m = fmax(m, fmax(fabs(vb[j].x), fabs(vb[j].y)));
+                for (int j = 0; j < 2; ++j) {
+                    d = max(d, max(abs_bits(va[j].x - vb[j].x), abs_bits(va[j].y - vb[j].y)));
+                    m = max(m, max(abs_bits(vb[j].x), abs_bits(vb[j].y)));
                 }
             }
             for (; i < n2; i += 256) {
                 const double2 va = __ldcs(qa + i), vb = __ldcs(qb + i);
-                d = fmax(d, fmax(fabs(va.x - vb.x), fabs(va.y - vb.y)));
-                m = fmax(m, fmax(fabs(vb.x), fabs(vb.y)));
+                d = max(d, max(abs_bits(va.x - vb.x), abs_bits(va.y - vb.y)));
+                m = max(m, max(abs_bits(vb.x), abs_bits(vb.y)));
             }
             if ((len & 1) && tid == 0) {
-                d = fmax(d, fabs(pa[len - 1] - pb[len - 1]));
-                m = fmax(m, fabs(pb[len - 1]));
+                d = max(d, abs_bits(pa[len - 1] - pb[len - 1]));
+                m = max(m, abs_bits(pb[len - 1]));
             }
         } else {
             for (int64_t i = tid; i < len; i += 256) {
-                d = fmax(d, fabs(pa[i] - pb[i]));
-                m = fmax(m, fabs(pb[i]));
+                d = max(d, abs_bits(pa[i] - pb[i]));
+                m = max(m, abs_bits(pb[i]));
             }
         }
-        d = warp_max_d(d);
-        m = warp_max_d(m);
+        d = warp_max_u64(d);
+        m = warp_max_u64(m);
         if (lane == 0) {
             sd[warp] = d;
             sm[warp] = m;
         }
         __syncthreads();
         if (tid == 0) {
-            d = 0.0;
-            m = 0.0;
-            for (int w = 0; w < 8; ++w) {
-                d = fmax(d, sd[w]);
-                m = fmax(m, sm[w]);
+            for (int w = 1; w < 8; ++w) {
+                d = max(d, sd[w]);
+                m = max(m, sm[w]);
             }
-            const double r = m > 0.0 ? d / m : d;
+            const double dd = __longlong_as_double((long long)d), mm = __longlong_as_double((long long)m);
+            const double r = mm > 0.0 ? dd / mm : dd;
             atomicMax(reinterpret_cast<unsigned long long*>(err + e), (unsigned long long)__double_as_longlong(r));
         }
         __syncthreads();

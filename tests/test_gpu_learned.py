@@ -136,8 +136,10 @@ def test_adam_update(torch, ctx):
 
 
 def test_element_errors(torch, ctx):
+    """Per element, the largest over its four type segments of max|a - b| / max|b|: short and
+    unaligned segments (scalar path), long ones (16-byte loads, two deep) and an odd length."""
     rng = np.random.default_rng(6)
-    sizes = [4 * 9, 4 * 64, 4 * 1, 4 * 100]
+    sizes = [4 * 9, 4 * 64, 4 * 1, 4 * 100, 4 * 4000, 4 * 2001]
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
     b = rng.normal(size=off[-1])
     a = b + rng.normal(size=off[-1]) * 1e-9
@@ -148,7 +150,12 @@ def test_element_errors(torch, ctx):
         seg = s // 4
         ref = max(np.abs(a[off[e] + t * seg:off[e] + (t + 1) * seg] - b[off[e] + t * seg:off[e] + (t + 1) * seg]).max() /
                   np.abs(b[off[e] + t * seg:off[e] + (t + 1) * seg]).max() for t in range(4))
-        assert abs(err[e].item() - ref) <= 1e-15 * max(ref, 1e-300) + 1e-300
+        assert err[e].item() == ref, (e, err[e].item(), ref)
+    # a NaN entry makes its element's error NaN, which no tolerance accepts
+    a[off[4] + 4000 + 17] = np.nan
+    p2s.element_errors(ctx, torch.as_tensor(a, device="cuda"), od, torch.as_tensor(b, device="cuda"), od, 4, err)
+    e_h = err.cpu().numpy()
+    assert np.isnan(e_h[4]) and not np.isnan(e_h[[0, 1, 2, 3, 5]]).any()
 
 
 def test_labels_against_oracle(torch, ctx):
