@@ -51,10 +51,12 @@ __device__ __forceinline__ Smem carve(double* sm, int n_pairs, int kb, int gmax,
 // [part G / nparts, (part + 1) G / nparts).  Whole elements, and parts with slot == nullptr
 // (nparts 1), store the pairs' sub-tensors in L.mom and write the element status; otherwise the
 // accumulator of every pair goes to slot[pair * slot_stride + i] for the split reduction, and a
-// Jacobian failure only raises the error flag.
+// Jacobian failure only raises the error flag.  tid is threadIdx.x, gstride the B rows' stride
+// (gmax | 1), bad_jac the CTA's shared Jacobian flag.
 template <bool kPart>
 __device__ __forceinline__ void element_moments(const MomentLaunch& L, const Smem& S, int64_t e, int part, int nparts,
-                                                double* slot, int64_t slot_stride, const int tid, const int gstride, int& bad_jac) {
+                                                double* slot, int64_t slot_stride, const int tid, const int gstride,
+                                                int& bad_jac) {
     const ElemDesc& d = L.desc[e];
     const int G = d.G, nc = d.n_comp, np = (nc == 1) ? 1 : 6;
     const int Ku = d.kax[0], Kv = d.kax[1], Kw = d.kax[2];
