@@ -356,7 +356,9 @@ int p2s_mlp_adam(float* params, const float* grad, float* m, float* v, int64_t n
 
 /* err[k] (device [n]) = max over the n_types product types of max|a - b| / max|b| over
  * element k's matrices, a starting at offsets_a[k] and b at offsets_b[k]..offsets_b[k+1]
- * (device arrays, offsets_b of length n+1).  Used for the labels and by the judge. */
+ * (device arrays, offsets_b of length n+1); max|a - b| itself where b is zero throughout.
+ * A NaN in either array makes err[k] NaN, which no tolerance accepts.  Used for the labels
+ * and by the judge. */
 int p2s_element_errors(p2s_ctx* ctx, const double* a, const int64_t* offsets_a, const double* b,
                        const int64_t* offsets_b, int64_t n, int n_types, double* err, void* stream);
 
@@ -393,7 +395,8 @@ int64_t p2s_learned_plan_output_entries(const p2s_learned_plan* plan);
 
 /* Learned fill, asynchronous on `stream`: features, prediction, fill at the predicted G,
  * judge fill at 48 points and comparison, FP64 fill of the judged elements that failed and
- * their replacement in `out`.  npts_out (device [E], optional) receives the G used per
+ * their replacement in `out` (when few fail, each one's moment sums over w-planes are split
+ * over several CTAs and added in a fixed order: the FP64 48-point fill up to rounding).  npts_out (device [E], optional) receives the G used per
  * element before any replacement.  The judge's 48-point fill, which does not depend on the
  * prediction, runs on a stream of the plan that is forked from `stream` when the call
  * starts and joined to it before the comparison: work queued on `stream` after the call
